@@ -1,0 +1,417 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+The paper (Sec. 3.1-3.3, Sec. 5) works on real photographs, the Basel/AlbedoMM
+statistical face models and a landmark detector; none of those is available, so
+every input here is synthetic and seeded.  This module only *draws* inputs: a
+mean face mesh with its topology and UV layout, shape/expression bases, UV
+textures, light-stage emitter geometry, and parameter vectors.  It contains none
+of the method's arithmetic (no morph, pose, projection, shading or loss); the
+renderer under test and the FP64 oracle both consume exactly these arrays.
+
+Units: model space is roughly a unit head centred at the origin, looking down +z
+(towards the camera); the camera sits at T = (0, 0, 4.5) looking down -z, so the
+pose v' = R^-1 (v - T) of Sec. 3.1 puts the face at z' ~ -4.5.
+
+Emitter record (one row per light, float32[11]):
+    [type, cx, cy, cz, e1x, e1y, e1z, e2x, e2y, e2z, reserved]
+type 0 = quad  : z = c + (u - 1/2) e1 + (v - 1/2) e2
+type 1 = tri   : vertices c, c + e1, c + e2
+type 2 = disk  : centre c, orthogonal radius vectors e1, e2 (|e1| = |e2| = R)
+The emitting side is the one that e1 x e2 points to.  Each light also carries
+its distance d_j and relative area a_j of Eq. (lightIntensity).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+LIGHT_QUAD, LIGHT_TRI, LIGHT_DISK = 0, 1, 2
+
+# Camera translation that places the head in front of the camera (Sec. 3.1).
+DEFAULT_T = (0.0, 0.0, 4.5)
+# Light-stage centre in camera space: the nominal head position.
+STAGE_CENTRE = (0.0, 0.0, -4.5)
+
+
+@dataclasses.dataclass
+class Scene:
+    """Everything that is fixed for a reconstruction: mesh, bases, lights, image."""
+    mean: np.ndarray        # float32 [N, 3] mean shape a_s (model space)
+    basis: np.ndarray       # float32 [K, N, 3] columns of [Sigma_s | Sigma_e]
+    n_shape: int            # K_s
+    n_expr: int             # K_e
+    faces: np.ndarray       # int32 [T, 3], counter-clockwise seen from outside
+    uv: np.ndarray          # float32 [N, 2] in [0, 1]^2
+    lights: np.ndarray      # float32 [N_L, 11] emitter records (module doc)
+    light_d: np.ndarray     # float32 [N_L] distance d_j
+    light_a: np.ndarray     # float32 [N_L] relative area a_j
+    width: int
+    height: int
+    spp: int
+    tex_size: int           # M
+    fov_deg: float
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self.mean.shape[0])
+
+    @property
+    def n_triangles(self) -> int:
+        return int(self.faces.shape[0])
+
+    @property
+    def n_basis(self) -> int:
+        return int(self.basis.shape[0])
+
+    @property
+    def n_lights(self) -> int:
+        return int(self.lights.shape[0])
+
+    def focal_px(self) -> float:
+        """Pinhole focal length in pixels for the horizontal field of view."""
+        return 0.5 * self.width / math.tan(math.radians(self.fov_deg) * 0.5)
+
+
+@dataclasses.dataclass
+class Params:
+    """The optimised parameter set chi-hat (Sec. 4) for one face."""
+    coef: np.ndarray        # float32 [K]  (alpha then delta)
+    rot: np.ndarray         # float32 [3]  Euler angles (x, y, z)
+    trans: np.ndarray       # float32 [3]  T
+    focal: np.ndarray       # float32 [1]  focal length in pixels
+    light_i: np.ndarray     # float32 [N_L, 3] perceived intensities i_j
+    diffuse: np.ndarray     # float32 [M, M, 3]
+    specular: np.ndarray    # float32 [M, M, 3]
+    roughness: np.ndarray   # float32 [M, M]
+
+    def copy(self) -> "Params":
+        return Params(**{f.name: getattr(self, f.name).copy()
+                         for f in dataclasses.fields(self)})
+
+    def as_dict(self) -> dict:
+        return {f.name: getattr(self, f.name) for f in dataclasses.fields(self)}
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+
+def icosphere(level: int):
+    """Unit icosphere: 10*4^level + 2 vertices, 20*4^level triangles."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0),
+         (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+             (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+             (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+             (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                p = verts[a] + verts[b]
+                verts.append(p / np.linalg.norm(p))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return np.array(verts), np.array(faces, dtype=np.int32)
+
+
+def _bump(p, centre, amp, width):
+    c = np.asarray(centre, dtype=np.float64)
+    c = c / np.linalg.norm(c)
+    d2 = np.sum((p - c) ** 2, axis=1)
+    return amp * np.exp(-d2 / (2.0 * width * width))
+
+
+def _face_features(p):
+    """Radial relief on the unit sphere: nose, brows, cheekbones, eye sockets."""
+    r = np.zeros(p.shape[0])
+    r += _bump(p, (0.0, -0.05, 1.0), 0.30, 0.16)            # nose
+    for s in (-1.0, 1.0):
+        r += _bump(p, (0.35 * s, 0.35, 0.87), 0.10, 0.14)   # brow ridge
+        r += _bump(p, (0.50 * s, -0.12, 0.85), 0.08, 0.20)  # cheekbone
+        r += _bump(p, (0.30 * s, 0.18, 0.93), -0.09, 0.11)  # eye socket
+    r += _bump(p, (0.0, -0.55, 0.83), 0.06, 0.18)           # chin
+    return r
+
+
+def _rbf_columns(rng, unit_pts, normals, k_count, rms0):
+    """K smooth displacement fields along the normal (16 Gaussian RBFs each),
+    column k scaled to RMS rms0 / (1 + k)."""
+    n = unit_pts.shape[0]
+    cols = np.zeros((k_count, n, 3))
+    for k in range(k_count):
+        centres = rng.normal(size=(16, 3))
+        centres /= np.linalg.norm(centres, axis=1, keepdims=True)
+        amps = rng.normal(size=16)
+        widths = rng.uniform(0.3, 0.6, size=16)
+        field = np.zeros(n)
+        for m in range(16):
+            d2 = np.sum((unit_pts - centres[m]) ** 2, axis=1)
+            field += amps[m] * np.exp(-d2 / (2.0 * widths[m] ** 2))
+        disp = field[:, None] * normals
+        rms = np.sqrt(np.mean(np.sum(disp * disp, axis=1)))
+        cols[k] = disp * (rms0 / (1.0 + k) / max(rms, 1e-12))
+    return cols
+
+
+def face_icosphere(rng, level=4, n_shape=20, n_expr=0):
+    """Closed 'face' mesh: icosphere warped into an ellipsoidal head with relief.
+
+    Level 4 gives 2,562 vertices / 5,120 triangles."""
+    p, faces = icosphere(level)
+    radial = 1.0 + _face_features(p)
+    scale = np.array([0.75, 0.95, 0.70])
+    mean = p * radial[:, None] * scale
+    uv = np.stack([(p[:, 0] + 1.0) * 0.5, (1.0 - p[:, 1]) * 0.5], axis=1)
+    basis = _rbf_columns(rng, p, p, n_shape + n_expr, 0.05)
+    return mean, basis, faces, uv
+
+
+def _disk_rings(n_vertices, n_boundary):
+    """Ring sizes (centre vertex excluded) for a disk mesh with exactly
+    n_vertices vertices and n_boundary vertices on the outer ring."""
+    target = n_vertices - 1
+    sizes = []
+    i = 1
+    while True:
+        s = min(6 * i, n_boundary)
+        rest = target - sum(sizes)
+        if rest - s < n_boundary:
+            break
+        sizes.append(s)
+        i += 1
+    rest = target - sum(sizes)
+    # rest >= n_boundary here; close with rings of n_boundary and one filler ring
+    fill = rest - n_boundary
+    while fill > n_boundary:
+        sizes.append(n_boundary)
+        fill -= n_boundary
+    if fill > 0:
+        if fill < 3:            # merge a too-small filler into the previous ring
+            sizes[-1] += fill
+        else:
+            sizes.append(fill)
+            sizes.sort()
+    sizes.append(n_boundary)
+    assert sum(sizes) == target
+    return sizes
+
+
+def face_disk(rng, n_vertices=35709, n_boundary=627, n_shape=80, n_expr=64):
+    """Open disk-topology height-field face.
+
+    Concentric rings around a centre vertex, stitched by angle.  With V
+    vertices and b boundary vertices a disk triangulation has 2V - b - 2
+    triangles, so (35,709, 627) gives 70,789 triangles and, by Euler's formula,
+    106,497 edges."""
+    sizes = _disk_rings(n_vertices, n_boundary)
+    n_rings = len(sizes)
+    xs, ys = [0.0], [0.0]
+    ring_start = []
+    angles = []
+    for r, n in enumerate(sizes):
+        rad = (r + 1) / n_rings
+        phase = 0.5 * (r % 2) * 2.0 * math.pi / n
+        a = phase + 2.0 * math.pi * np.arange(n) / n
+        ring_start.append(len(xs))
+        angles.append(a)
+        xs += list(rad * np.cos(a))
+        ys += list(rad * np.sin(a))
+    X = np.array(xs)
+    Y = np.array(ys)
+    faces = []
+    n1 = sizes[0]
+    for j in range(n1):
+        faces.append((0, ring_start[0] + j, ring_start[0] + (j + 1) % n1))
+    for r in range(n_rings - 1):
+        na, nb = sizes[r], sizes[r + 1]
+        sa, sb = ring_start[r], ring_start[r + 1]
+        pa, pb = angles[r][0], angles[r + 1][0]
+        ia = ib = 0
+        while ia < na or ib < nb:
+            next_a = pa + 2.0 * math.pi * (ia + 1) / na
+            next_b = pb + 2.0 * math.pi * (ib + 1) / nb
+            if ib >= nb or (ia < na and next_a <= next_b):
+                faces.append((sa + ia % na, sb + ib % nb, sa + (ia + 1) % na))
+                ia += 1
+            else:
+                faces.append((sa + ia % na, sb + ib % nb, sb + (ib + 1) % nb))
+                ib += 1
+    faces = np.array(faces, dtype=np.int32)
+    # counter-clockwise seen from +z
+    e1 = np.stack([X[faces[:, 1]] - X[faces[:, 0]], Y[faces[:, 1]] - Y[faces[:, 0]]], 1)
+    e2 = np.stack([X[faces[:, 2]] - X[faces[:, 0]], Y[faces[:, 2]] - Y[faces[:, 0]]], 1)
+    cz = e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]
+    flip = cz < 0
+    faces[flip] = faces[flip][:, [0, 2, 1]]
+    # height field: dome plus facial relief
+    r2 = X * X + Y * Y
+    dome = 0.55 * np.sqrt(np.maximum(1.0 - 0.85 * r2, 0.0))
+    unit = np.stack([X, Y, np.sqrt(np.maximum(1.0 - np.minimum(r2, 1.0), 0.0))], 1)
+    relief = _face_features(unit)
+    Z = dome + 0.9 * relief
+    mean = np.stack([0.75 * X, 0.95 * Y, Z], 1)
+    uv = np.stack([(X + 1.0) * 0.5, (1.0 - Y) * 0.5], axis=1)
+    normals = np.tile(np.array([0.0, 0.0, 1.0]), (X.shape[0], 1))
+    basis = _rbf_columns(rng, unit, normals, n_shape + n_expr, 0.05)
+    return mean, basis, faces, uv
+
+
+# --------------------------------------------------------------------------
+# lights, textures, parameters
+# --------------------------------------------------------------------------
+
+def _fibonacci_dirs(n, hemisphere):
+    g = math.pi * (3.0 - math.sqrt(5.0))
+    out = []
+    for i in range(n):
+        z = 1.0 - (i + 0.5) / n if hemisphere else 1.0 - (2.0 * i + 1.0) / n
+        r = math.sqrt(max(0.0, 1.0 - z * z))
+        out.append((r * math.cos(g * i), r * math.sin(g * i), z))
+    return np.array(out)
+
+
+def light_stage(n_lights, radius=3.0, side=0.5, hemisphere=False,
+                centre=STAGE_CENTRE, kind=LIGHT_QUAD):
+    """Area lights on a (hemi)sphere around the head, each facing the centre."""
+    dirs = _fibonacci_dirs(n_lights, hemisphere)
+    c0 = np.asarray(centre, dtype=np.float64)
+    rec = np.zeros((n_lights, 11), dtype=np.float32)
+    for j, dvec in enumerate(dirs):
+        inward = -dvec
+        up = np.array([0.0, 1.0, 0.0]) if abs(inward[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
+        a1 = np.cross(up, inward)
+        a1 /= np.linalg.norm(a1)
+        a2 = np.cross(inward, a1)          # a1 x a2 = inward
+        c = c0 + radius * dvec
+        if kind == LIGHT_QUAD:
+            e1, e2 = side * a1, side * a2
+        elif kind == LIGHT_DISK:
+            e1, e2 = 0.5 * side * a1, 0.5 * side * a2
+        else:  # triangle with centroid at c
+            e1, e2 = side * a1, side * a2
+            c = c - (e1 + e2) / 3.0
+        rec[j, 0] = kind
+        rec[j, 1:4] = c
+        rec[j, 4:7] = e1
+        rec[j, 7:10] = e2
+    return rec
+
+
+def smooth_field(rng, m, channels, sigma, lo, hi):
+    """White noise blurred by a Gaussian of std `sigma` texels (periodic, FFT),
+    rescaled per channel to [lo, hi]."""
+    noise = rng.normal(size=(m, m, channels))
+    f = np.fft.fftfreq(m)
+    g = np.exp(-2.0 * (math.pi * sigma) ** 2 * (f[:, None] ** 2 + f[None, :] ** 2))
+    out = np.empty_like(noise)
+    for c in range(channels):
+        out[:, :, c] = np.real(np.fft.ifft2(np.fft.fft2(noise[:, :, c]) * g))
+        mn, mx = out[:, :, c].min(), out[:, :, c].max()
+        out[:, :, c] = lo + (hi - lo) * (out[:, :, c] - mn) / max(mx - mn, 1e-12)
+    return out
+
+
+def textures(rng, m):
+    diffuse = smooth_field(rng, m, 3, m / 16.0, 0.2, 0.8)
+    specular = np.full((m, m, 3), 0.05)
+    roughness = rng.uniform(0.3, 0.6, size=(m, m))
+    return (diffuse.astype(np.float32), specular.astype(np.float32),
+            roughness.astype(np.float32))
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
+    """Scenes shaped like the workloads:
+
+    c1   : 2,562 verts / 5,120 tris, K = 20, 64x64, 4 spp, 8 quads on a
+           hemisphere of radius 3, 128^2 textures.
+    c2   : 35,709 verts / 70,789 tris, K = 80 + 64, 256x256, 16 spp,
+           40 quads on a sphere, 512^2 textures.
+    tiny : a small closed mesh for fast CPU tests (162 verts / 320 tris, K = 6,
+           24x24, 2 spp, 4 lights).
+    Keyword overrides replace width/height/spp/tex_size/n_lights/light kind."""
+    rng = np.random.default_rng(seed)
+    if config == "c1":
+        mean, basis, faces, uv = face_icosphere(rng, 4, 20, 0)
+        ks, ke = 20, 0
+        w = h = 64
+        spp, m, nl, hemi = 4, 128, 8, True
+    elif config == "c2":
+        mean, basis, faces, uv = face_disk(rng, 35709, 627, 80, 64)
+        ks, ke = 80, 64
+        w = h = 256
+        spp, m, nl, hemi = 16, 512, 40, False
+    elif config == "tiny":
+        mean, basis, faces, uv = face_icosphere(rng, 2, 4, 2)
+        ks, ke = 4, 2
+        w = h = 24
+        spp, m, nl, hemi = 2, 16, 4, True
+    else:
+        raise ValueError(config)
+    w = over.get("width", w)
+    h = over.get("height", h)
+    spp = over.get("spp", spp)
+    m = over.get("tex_size", m)
+    nl = over.get("n_lights", nl)
+    kind = over.get("light_kind", LIGHT_QUAD)
+    side = over.get("light_side", 0.5 if kind != LIGHT_DISK else 1.0)
+    lights = light_stage(nl, 3.0, side, hemi, STAGE_CENTRE, kind)
+    return Scene(mean=_f32(mean), basis=_f32(basis), n_shape=ks, n_expr=ke,
+                 faces=np.ascontiguousarray(faces.astype(np.int32)), uv=_f32(uv),
+                 lights=lights, light_d=np.full(nl, 3.0, np.float32),
+                 light_a=np.ones(nl, np.float32), width=int(w), height=int(h),
+                 spp=int(spp), tex_size=int(m), fov_deg=30.0)
+
+
+def init_params(scene: Scene, seed: int = 0) -> Params:
+    """Optimisation start: mean shape, neutral expression, frontal pose,
+    uniform lights, flat textures (Sec. 4 initialisation)."""
+    rng = np.random.default_rng(seed + 1000)
+    m = scene.tex_size
+    del rng
+    return Params(coef=np.zeros(scene.n_basis, np.float32),
+                  rot=np.zeros(3, np.float32),
+                  trans=np.array(DEFAULT_T, np.float32),
+                  focal=np.array([scene.focal_px()], np.float32),
+                  light_i=np.full((scene.n_lights, 3), 0.8, np.float32),
+                  diffuse=np.full((m, m, 3), 0.5, np.float32),
+                  specular=np.full((m, m, 3), 0.05, np.float32),
+                  roughness=np.full((m, m), 0.45, np.float32))
+
+
+def random_params(scene: Scene, seed: int = 0, coef_scale: float = 1.0) -> Params:
+    """Ground-truth parameters for a synthetic target image."""
+    rng = np.random.default_rng(seed + 7)
+    m = scene.tex_size
+    coef = np.zeros(scene.n_basis)
+    coef[:scene.n_shape] = rng.normal(size=scene.n_shape) * coef_scale
+    coef[scene.n_shape:] = rng.uniform(0.0, 0.5, size=scene.n_expr)
+    diffuse, specular, roughness = textures(rng, m)
+    return Params(coef=_f32(coef),
+                  rot=_f32(rng.uniform(-0.04, 0.04, size=3)),
+                  trans=_f32(np.array(DEFAULT_T) + rng.normal(0.0, 0.03, size=3)),
+                  focal=_f32([scene.focal_px()]),
+                  light_i=_f32(rng.uniform(0.2, 1.5, size=(scene.n_lights, 3))),
+                  diffuse=diffuse, specular=specular, roughness=roughness)
+
+
+def pixel_noise(rng_seed: int, shape, sigma: float = 0.01) -> np.ndarray:
+    """N(0, sigma) pixel noise added to synthetic targets."""
+    return _f32(np.random.default_rng(rng_seed).normal(0.0, sigma, size=shape))

@@ -1,0 +1,37 @@
+"""Hand-built scenes for closed-form pins (inputs only; no method arithmetic)."""
+import numpy as np
+
+from paper_2101_05356_gb300 import synth
+
+
+def make(verts, faces, basis, lights, width=16, height=16, spp=4, tex=4,
+         light_i=None, diffuse=(0.7, 0.5, 0.3)):
+    """Scene whose model space is camera space (rot = 0, T = 0)."""
+    verts = np.asarray(verts, np.float32)
+    n = verts.shape[0]
+    basis = np.asarray(basis, np.float32).reshape(-1, n, 3)
+    lights = np.asarray(lights, np.float32).reshape(-1, 11)
+    nl = lights.shape[0]
+    uv = np.stack([np.linspace(0.1, 0.9, n), np.linspace(0.9, 0.1, n)], 1).astype(np.float32)
+    sc = synth.Scene(mean=verts, basis=basis, n_shape=basis.shape[0], n_expr=0,
+                     faces=np.asarray(faces, np.int32), uv=uv, lights=lights,
+                     light_d=np.ones(nl, np.float32), light_a=np.ones(nl, np.float32),
+                     width=width, height=height, spp=spp, tex_size=tex, fov_deg=60.0)
+    li = np.ones((nl, 3), np.float32) if light_i is None else np.asarray(light_i, np.float32)
+    pr = synth.Params(coef=np.zeros(basis.shape[0], np.float32), rot=np.zeros(3, np.float32),
+                      trans=np.zeros(3, np.float32), focal=np.array([16.0], np.float32),
+                      light_i=li,
+                      diffuse=np.tile(np.asarray(diffuse, np.float32), (tex, tex, 1)),
+                      specular=np.zeros((tex, tex, 3), np.float32),
+                      roughness=np.full((tex, tex), 0.5, np.float32))
+    return sc, pr
+
+
+def quad_light(c, e1, e2, kind=synth.LIGHT_QUAD):
+    r = np.zeros(11, np.float32)
+    r[0] = kind
+    r[1:4], r[4:7], r[7:10] = c, e1, e2
+    return r
+
+
+FAR_TRIANGLE = [[100.0, 100.0, 100.0], [101.0, 100.0, 100.0], [100.0, 101.0, 100.0]]
