@@ -1,0 +1,205 @@
+/*
+ * facert: differentiable Monte Carlo ray-traced rendering of a morphable face
+ * lit by a virtual light stage (Dib et al., "Practical Face Reconstruction via
+ * Differentiable Ray Tracing", Eurographics 2021), as a C-ABI library of
+ * hand-written CUDA kernels for sm_103a.
+ *
+ * Problem statement (Sec. 4, Eq. energy): for parameters chi, render the image
+ * p^S = F(chi) with the Monte Carlo estimator F of the rendering equation
+ * (direct light from every light-stage emitter, shadow rays, Cook-Torrance
+ * reflectance of App. A), compare it with a target through the L1 photometric
+ * loss E_ph after the 3x3 Gaussian smoothing of Sec. 4 ("Variance Reduction"),
+ * and return dE/dchi including the edge-sampling boundary terms (Sec. 4,
+ * "Edge Sampling").
+ *
+ * Conventions shared by every call
+ *  - Return value: FR_OK (0) or an error code; no exceptions cross the ABI.
+ *    Argument checks happen synchronously before anything is enqueued.
+ *    fr_last_error() describes the last failure of a context.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Compute calls only enqueue work on it and return; they never allocate.
+ *  - Device-side problems (traversal stack overflow, bounded waits that ran
+ *    out) set a status word that fr_sync_status() reads; no kernel traps.
+ *  - Ownership: the caller owns every buffer it passes (parameters, targets,
+ *    images, gradients) and the stream; the context owns its own scratch (mesh
+ *    copies, BVH, edge lists, adjoint accumulators), sized at fr_create /
+ *    fr_set_mesh / fr_set_lights and freed by fr_destroy.
+ *  - A context is not re-entrant: calls on one context must be serialised on
+ *    one stream.  Separate contexts are independent.
+ *  - Layouts are C-contiguous float32 unless stated: image/target [H][W][3];
+ *    textures diffuse/specular [M][M][3], roughness [M][M] (row = v axis).
+ */
+#ifndef FACERT_H
+#define FACERT_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t fr_status;
+#define FR_OK        0
+#define FR_EINVAL    1   /* bad argument (null pointer, size out of range, state) */
+#define FR_ENOMEM    2   /* device allocation failed at create/set time */
+#define FR_ECUDA     3   /* a CUDA runtime call failed */
+#define FR_EOVERFLOW 4   /* device status: traversal stack overflowed (rays dropped) */
+#define FR_ETIMEOUT  5   /* device status: a bounded wait gave up */
+
+/* config flags */
+#define FR_FLAG_GGX              1u   /* GGX D + exact GGX Smith G1 instead of App. A's Blinn-Phong/Walter */
+#define FR_FLAG_SCHLICK_LINEAR   2u   /* Fresnel exactly as printed in App. A (no 5th power) */
+#define FR_FLAG_FLAT             4u   /* debug: radiance = diffuse albedo at the hit, no lights */
+#define FR_FLAG_NO_INTERIOR     16u   /* gradient: skip the interior (visibility-fixed) term */
+#define FR_FLAG_NO_PRIMARY_EDGE 32u   /* gradient: skip the primary-visibility boundary term */
+#define FR_FLAG_NO_SHADOW_EDGE  64u   /* gradient: skip the shadow boundary term */
+
+/* emitter types in light records */
+#define FR_LIGHT_QUAD 0
+#define FR_LIGHT_TRI  1
+#define FR_LIGHT_DISK 2
+
+typedef struct fr_ctx fr_ctx;
+
+typedef struct fr_config {
+    int32_t width, height;   /* image size, 1..8192 each */
+    int32_t spp;             /* camera samples per pixel: a power of two, 1..1024 */
+    int32_t tex_size;        /* M: textures are M x M, 1..8192 */
+    int32_t edge_spp;        /* primary-edge samples per pixel (0..64) */
+    uint32_t flags;          /* FR_FLAG_* */
+    uint32_t seed;           /* Philox key word 0 */
+} fr_config;
+
+/* Face model of Sec. 3.1 (host pointers, copied into the context):
+ *   mean  [N][3]      mean shape a_s (model space)
+ *   basis [K][N][3]   columns of [Sigma_s | Sigma_e]; v = mean + basis^T coef
+ *   faces [T][3]      triangle vertex indices (manifold: each edge in <= 2 faces)
+ *   uv    [N][2]      texture coordinates (u, v) in [0, 1]  (Sec. 3.2) */
+typedef struct fr_mesh {
+    int32_t n_vertices, n_triangles, n_basis;
+    const float* mean;
+    const float* basis;
+    const int32_t* faces;
+    const float* uv;
+} fr_mesh;
+
+/* Virtual light stage of Sec. 3.3 (host pointers, copied):
+ *   records [N_L][11] = {type, c[3], e1[3], e2[3], unused}; quad: c + (u-1/2) e1 +
+ *   (v-1/2) e2; triangle: c, c+e1, c+e2; disk: centre c, radius vectors e1, e2.
+ *   The emitting side is the one e1 x e2 points to.  Geometry is in camera space.
+ *   d [N_L], a [N_L]: distance and relative area of Eq. (lightIntensity); the
+ *   emitted radiance is (d^2 / a) * i_j.  N_L <= 64. */
+typedef struct fr_light_stage {
+    int32_t n_lights;
+    const float* records;
+    const float* d;
+    const float* a;
+} fr_light_stage;
+
+/* Parameters chi-hat of Sec. 4 (device pointers, float32):
+ *   coef [K] (alpha then delta), rot [3] Euler angles with R = Rz Ry Rx,
+ *   trans [3] T (pose v' = R^T (v - T), Sec. 3.1), focal [1] in pixels,
+ *   light_i [N_L][3] perceived intensities i_j, diffuse [M][M][3],
+ *   specular [M][M][3], roughness [M][M]. */
+typedef struct fr_params {
+    const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+} fr_params;
+
+/* Gradients, same shapes as fr_params (device pointers).  Every call ADDS
+ * into them; the caller zeroes them.  A NULL member skips that group's
+ * output (the work is still done). */
+typedef struct fr_grads {
+    float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+} fr_grads;
+
+/* Create a context for one image configuration.  Allocates nothing on the
+ * device yet.  Errors: FR_EINVAL (bad sizes), FR_ECUDA. */
+fr_status fr_create(fr_ctx** out, const fr_config* cfg);
+
+/* Copy a face model (Sec. 3.1) and build its static topology (vertex->face
+ * lists, the undirected edge list sorted by (min vertex, max vertex)); sizes the
+ * context's scratch.  Synchronous.  Errors: FR_EINVAL (indices out of range,
+ * non-manifold edge, T < 1, K > 256), FR_ENOMEM, FR_ECUDA. */
+fr_status fr_set_mesh(fr_ctx* ctx, const fr_mesh* mesh);
+
+/* Copy the light-stage emitters (Sec. 3.3).  Synchronous.  Errors: FR_EINVAL. */
+fr_status fr_set_lights(fr_ctx* ctx, const fr_light_stage* stage);
+
+/* Forward render (Sec. 4, F): morph, pose, normals, LBVH build, primary rays,
+ * Cook-Torrance shading (App. A) with one area sample and one shadow ray per
+ * light per camera sample.  image [H][W][3] receives the per-pixel mean.
+ * `iteration` and `face_id` enter the Philox counters, so a call is a pure
+ * function of (params, iteration, face_id, seed). */
+fr_status fr_forward(fr_ctx* ctx, const fr_params* p, float* image, uint32_t iteration,
+                     uint32_t face_id, void* stream);
+
+/* Adjoint of fr_forward: adds d(sum adj_image * image)/dchi into g.  Re-traces
+ * with the same Philox counters instead of storing hit records, and includes
+ * the primary-visibility and shadow boundary terms (edge sampling, Sec. 4)
+ * unless disabled by flags.  adj_image [H][W][3] (device). */
+fr_status fr_backward(fr_ctx* ctx, const fr_params* p, const float* adj_image, fr_grads* g,
+                      uint32_t iteration, uint32_t face_id, void* stream);
+
+/* Photometric loss of Sec. 4: blurred = G3x3 * image (sigma 1, normalised,
+ * replicate border); *loss = sum |blurred - target| (FP64 reduction, device
+ * double); adj_image = dloss/dimage.  blurred may be NULL. */
+fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* loss,
+                  float* adj_image, float* blurred, void* stream);
+
+/* One full step of the hot path: fr_forward, fr_loss against `target`, and (if
+ * g != NULL) fr_backward with the loss adjoint.  loss is a device double. */
+fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
+                    double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
+                    void* stream);
+
+/* Synchronise `stream`, read and clear the device status word.
+ * Returns FR_OK, FR_EOVERFLOW or FR_ETIMEOUT (or FR_ECUDA). */
+fr_status fr_sync_status(fr_ctx* ctx, void* stream);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char* fr_last_error(const fr_ctx* ctx);
+
+/* Free every device buffer of the context (synchronises the device first). */
+void fr_destroy(fr_ctx* ctx);
+
+/* ---- diagnostics (used by the parity tests; same rules as above) ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out[i][0..3] =
+ * philox(key=(k0,k1), counter=counters[i][0..3]) for i < n (device arrays). */
+fr_status fr_philox(uint32_t k0, uint32_t k1, const uint32_t* counters, int32_t n,
+                    uint32_t* out, void* stream);
+
+/* Camera-space vertices v' [N][3] and unit vertex normals [N][3] (device) of
+ * the morph + pose of Sec. 3.1 for parameters p. */
+fr_status fr_debug_geometry(fr_ctx* ctx, const fr_params* p, float* v_cam, float* n_vert,
+                            void* stream);
+
+/* Closest hit of n rays (device org [n][3], dir [n][3]) through the LBVH built
+ * for p: tri [n] (-1 = miss), t [n] (-1 on a miss). */
+fr_status fr_debug_trace(fr_ctx* ctx, const fr_params* p, const float* org, const float* dir,
+                         int32_t n, int32_t* tri, float* t, void* stream);
+
+/* Forward render that also writes per-sample records: tri_rec [H*W*spp] hit
+ * triangle (-1 miss) and mask_rec [H*W*spp] bit j = shadow ray to light j
+ * traced and unoccluded; record index = (y*W + x)*spp + sample. */
+fr_status fr_debug_records(fr_ctx* ctx, const fr_params* p, float* image, int32_t* tri_rec,
+                           uint64_t* mask_rec, uint32_t iteration, uint32_t face_id,
+                           void* stream);
+
+/* Ordered silhouette lists after a forward pass for p: prim [E] primary
+ * silhouette edge ids, n_prim [1]; per_light [N_L][E] shadow candidates,
+ * counts [N_L] (all device int32). */
+fr_status fr_debug_silhouettes(fr_ctx* ctx, const fr_params* p, int32_t* prim, int32_t* n_prim,
+                               int32_t* per_light, int32_t* counts, void* stream);
+
+/* BVH validity check for p: writes out[0] = number of leaves reachable from the
+ * root, out[1] = number of parent boxes that fail to contain a child box,
+ * out[2] = maximum depth (device int32[3]). */
+fr_status fr_debug_bvh(fr_ctx* ctx, const fr_params* p, int32_t* out, void* stream);
+
+/* Edge count E of the mesh set on ctx (host int). */
+int32_t fr_num_edges(const fr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,130 @@
+// Shared device definitions of the facert CUDA library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FR_HD __host__ __device__ __forceinline__
+#define FR_D __device__ __forceinline__
+
+// device status word bits (read by fr_sync_status)
+#define FR_STATUS_STACK_OVERFLOW 1
+#define FR_STATUS_TIMEOUT 2
+#define FR_STATUS_BAD_BVH 4
+
+constexpr int FR_MAX_LIGHTS = 64;
+constexpr int FR_MAX_BASIS = 256;
+constexpr int FR_STACK = 64;           // traversal stack entries per thread
+constexpr float FR_PI = 3.14159265358979323846f;
+
+// ---------------------------------------------------------------------------
+// small vector algebra
+// ---------------------------------------------------------------------------
+FR_HD float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+FR_HD float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+FR_HD float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+FR_HD float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+FR_HD float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+FR_HD float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+FR_HD float3& operator+=(float3& a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+FR_HD float3& operator-=(float3& a, float3 b) { a.x -= b.x; a.y -= b.y; a.z -= b.z; return a; }
+FR_HD float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+FR_HD float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+FR_HD float length(float3 a) { return sqrtf(dot(a, a)); }
+FR_HD float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+FR_HD float comp(float3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies, key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+FR_D uint4 philox4x32_10(uint2 key, uint4 c) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { key.x += 0x9E3779B9u; key.y += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ key.x, lo1, hi0 ^ c.w ^ key.y, lo0);
+    }
+    return c;
+}
+
+// 24-bit uniform in [0, 1): (x >> 8) * 2^-24, exact in float.
+FR_D float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// Sample stream: key (seed, tag), counter (index, (sample << 16) | block,
+// iteration, face).  Dimension d lives in word d % 4 of block d / 4.
+enum { FR_STREAM_PRIMARY = 0, FR_STREAM_EDGE_PRIMARY = 1, FR_STREAM_EDGE_SHADOW = 2 };
+
+struct Sampler {
+    uint2 key;
+    uint32_t index, sample, iteration, face;
+    FR_D uint4 block(int b) const {
+        return philox4x32_10(key, make_uint4(index, (sample << 16) | (uint32_t)b, iteration, face));
+    }
+    // two consecutive dims starting at an even dim d (same block)
+    FR_D float2 pair(int d) const {
+        uint4 w = block(d >> 2);
+        return (d & 2) ? make_float2(u24(w.z), u24(w.w)) : make_float2(u24(w.x), u24(w.y));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// device-side scene description (plain pointers, passed by value to kernels)
+// ---------------------------------------------------------------------------
+struct LightDev {
+    float3 c, e1, e2, n;   // n: unit normal of the emitting side
+    float area, scale;     // scale = d^2 / a  (Eq. lightIntensity)
+    int type, pad;
+};
+
+// Binary BVH node holding both children's boxes (64 B, four 16-B loads).
+struct __align__(16) BvhNode {
+    float4 a;   // lo0.x lo0.y lo0.z hi0.x
+    float4 b;   // hi0.y hi0.z lo1.x lo1.y
+    float4 c;   // lo1.z hi1.x hi1.y hi1.z
+    int4 d;     // child0, child1 (>= 0 internal, < 0 leaf ~slot), pad, pad
+};
+
+struct DevScene {
+    int N, T, K, NL, E, W, H, spp, M, edge_spp;
+    uint32_t flags, seed;
+    const float4* v;        // camera-space vertices [N]
+    const float4* vn;       // unit vertex normals [N]
+    const float2* uv;       // [N]
+    const int4* faces;      // [T]
+    const BvhNode* nodes;   // [max(T - 1, 1)]
+    const float4* tris;     // [3T] triangles in BVH leaf order; tris[3s].w = id bits
+    const LightDev* lights; // [NL]
+    int* status;
+};
+
+struct DevParams {
+    const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+};
+
+struct DevGrads {
+    float* d_v;            // [N][3] dE/dv' (camera space)
+    float* d_n;            // [N][3] dE/dn (unit vertex normals)
+    float *diffuse, *specular, *roughness;   // texture gradients (may be null)
+    double* small;         // [1 + 3 N_L]: focal, then light intensities (FP64)
+};
+
+FR_D void set_status(int* status, int bit) { atomicOr(status, bit); }
+
+// Warp-aggregated atomic add: lanes sharing `key` sum first, one lane adds.
+FR_D void warp_agg_add(float* addr, float val, uint32_t key, uint32_t active) {
+    const uint32_t peers = __match_any_sync(active, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    // reduce over the peer set by shuffling along the set bits
+    float sum = 0.0f;
+    uint32_t m = peers;
+    while (m) {
+        const int src = __ffs(m) - 1;
+        sum += __shfl_sync(peers, val, src);
+        m &= m - 1;
+    }
+    if (lane == leader && sum != 0.0f) atomicAdd(addr, sum);
+}

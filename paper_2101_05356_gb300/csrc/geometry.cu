@@ -1,0 +1,334 @@
+// Morph (Sec. 3.1: v = a_s + Sigma_s alpha + Sigma_e delta), pose
+// (Gamma(v) = R^-1 (v - T)), face/vertex normals, Morton keys, and the reverse
+// of each step (normals, pose, morph transpose with FP64 reductions).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+// R = Rz(t2) Ry(t1) Rx(t0), row-major
+FR_D void euler_R(const float* rot, float R[9]) {
+    float sx, cx, sy, cy, sz, cz;
+    sincosf(rot[0], &sx, &cx);
+    sincosf(rot[1], &sy, &cy);
+    sincosf(rot[2], &sz, &cz);
+    R[0] = cz * cy; R[1] = cz * sy * sx - sz * cx; R[2] = cz * sy * cx + sz * sx;
+    R[3] = sz * cy; R[4] = sz * sy * sx + cz * cx; R[5] = sz * sy * cx - cz * sx;
+    R[6] = -sy;     R[7] = cy * sx;                R[8] = cy * cx;
+}
+
+// Coalesced, float4-vectorised morph: thread i owns float4 i of the padded
+// [3N] vector; coefficients sit in shared memory; basis rows are 16-B aligned.
+__global__ void __launch_bounds__(256) k_morph(const float4* __restrict__ mean, const float* __restrict__ basis,
+                                               int ld4, int K, const float* __restrict__ coef,
+                                               float4* __restrict__ out) {
+    __shared__ float c[FR_MAX_BASIS];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = coef[k];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ld4) return;
+    float4 acc = mean[i];
+    const float4* b = reinterpret_cast<const float4*>(basis) + i;
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+        const float4 b0 = __ldcs(b + (size_t)(k + 0) * ld4), b1 = __ldcs(b + (size_t)(k + 1) * ld4);
+        const float4 b2 = __ldcs(b + (size_t)(k + 2) * ld4), b3 = __ldcs(b + (size_t)(k + 3) * ld4);
+        acc.x += c[k] * b0.x + c[k + 1] * b1.x + c[k + 2] * b2.x + c[k + 3] * b3.x;
+        acc.y += c[k] * b0.y + c[k + 1] * b1.y + c[k + 2] * b2.y + c[k + 3] * b3.y;
+        acc.z += c[k] * b0.z + c[k + 1] * b1.z + c[k + 2] * b2.z + c[k + 3] * b3.z;
+        acc.w += c[k] * b0.w + c[k + 1] * b1.w + c[k + 2] * b2.w + c[k + 3] * b3.w;
+    }
+    for (; k < K; ++k) {
+        const float4 bk = __ldcs(b + (size_t)k * ld4);
+        acc.x += c[k] * bk.x; acc.y += c[k] * bk.y; acc.z += c[k] * bk.z; acc.w += c[k] * bk.w;
+    }
+    out[i] = acc;
+}
+
+FR_D unsigned ordered(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+FR_D float unordered(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void k_aabb_reset(unsigned* aabb) {
+    if (threadIdx.x < 3) aabb[threadIdx.x] = 0xffffffffu;
+    else if (threadIdx.x < 6) aabb[threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_pose(const float* __restrict__ v_model, int N, const float* rot,
+                                              const float* trans, float4* __restrict__ v_cam, unsigned* aabb) {
+    __shared__ float R[9], T[3];
+    __shared__ unsigned bmin[3], bmax[3];
+    if (threadIdx.x == 0) {
+        euler_R(rot, R);
+        T[0] = trans[0]; T[1] = trans[1]; T[2] = trans[2];
+        for (int k = 0; k < 3; ++k) { bmin[k] = 0xffffffffu; bmax[k] = 0u; }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        const float wx = v_model[3 * i] - T[0], wy = v_model[3 * i + 1] - T[1], wz = v_model[3 * i + 2] - T[2];
+        // v' = R^T w
+        const float x = R[0] * wx + R[3] * wy + R[6] * wz;
+        const float y = R[1] * wx + R[4] * wy + R[7] * wz;
+        const float z = R[2] * wx + R[5] * wy + R[8] * wz;
+        v_cam[i] = make_float4(x, y, z, 0.0f);
+        atomicMin(&bmin[0], ordered(x)); atomicMin(&bmin[1], ordered(y)); atomicMin(&bmin[2], ordered(z));
+        atomicMax(&bmax[0], ordered(x)); atomicMax(&bmax[1], ordered(y)); atomicMax(&bmax[2], ordered(z));
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        atomicMin(&aabb[threadIdx.x], bmin[threadIdx.x]);
+        atomicMax(&aabb[3 + threadIdx.x], bmax[threadIdx.x]);
+    }
+}
+
+FR_D uint32_t spread10(uint32_t x) {
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void __launch_bounds__(256) k_faces(const float4* __restrict__ v, const int4* __restrict__ faces, int T,
+                                               const unsigned* aabb, float4* __restrict__ n_face,
+                                               uint32_t* __restrict__ keys, int* __restrict__ vals) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    const int4 t = faces[f];
+    const float3 a = xyz(v[t.x]), b = xyz(v[t.y]), c = xyz(v[t.z]);
+    const float3 n = cross(b - a, c - a);
+    n_face[f] = make_float4(n.x, n.y, n.z, 0.0f);
+    const float3 lo = f3(unordered(aabb[0]), unordered(aabb[1]), unordered(aabb[2]));
+    const float3 hi = f3(unordered(aabb[3]), unordered(aabb[4]), unordered(aabb[5]));
+    const float3 cen = (a + b + c) * (1.0f / 3.0f);
+    uint32_t code = 0;
+    for (int k = 0; k < 3; ++k) {
+        const float ext = comp(hi, k) - comp(lo, k);
+        float u = ext > 0.0f ? (comp(cen, k) - comp(lo, k)) / ext : 0.5f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        const uint32_t q = min((uint32_t)(u * 1024.0f), 1023u);
+        code |= spread10(q) << (2 - k);
+    }
+    keys[f] = code;
+    vals[f] = f;
+}
+
+// Vertex normal = normalised sum of its faces' un-normalised normals, gathered
+// in face-index order through the vertex->face CSR (no atomics).  w = |sum|.
+__global__ void __launch_bounds__(256) k_vertex_normals(const float4* __restrict__ n_face, const int* __restrict__ off,
+                                                        const int* __restrict__ idx, int N, float4* __restrict__ vn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float3 m = f3(0.0f, 0.0f, 0.0f);
+    for (int k = off[i]; k < off[i + 1]; ++k) m += xyz(n_face[idx[k]]);
+    const float len = length(m);
+    const float inv = len > 0.0f ? 1.0f / len : 0.0f;
+    vn[i] = make_float4(m.x * inv, m.y * inv, m.z * inv, len);
+}
+
+// dE/dm_i = (I - n n^T) dE/dn_i / |m_i|
+__global__ void k_normals_adj_a(const float4* __restrict__ vn, const float* __restrict__ d_n, int N,
+                                float* __restrict__ dm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 n4 = vn[i];
+    const float3 n = xyz(n4);
+    const float3 g = f3(d_n[3 * i], d_n[3 * i + 1], d_n[3 * i + 2]);
+    const float inv = n4.w > 0.0f ? 1.0f / n4.w : 0.0f;
+    const float3 r = (g - n * dot(n, g)) * inv;
+    dm[3 * i] = r.x; dm[3 * i + 1] = r.y; dm[3 * i + 2] = r.z;
+}
+
+// Face normal n_f = (b - a) x (c - a) feeds m of its three vertices; gather the
+// cross-product adjoint back to each vertex over its faces.
+__global__ void k_normals_adj_b(const float4* __restrict__ v, const int4* __restrict__ faces,
+                                const int* __restrict__ off, const int* __restrict__ idx, int N,
+                                const float* __restrict__ dm, float* __restrict__ d_v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float3 acc = f3(0.0f, 0.0f, 0.0f);
+    for (int k = off[i]; k < off[i + 1]; ++k) {
+        const int4 t = faces[idx[k]];
+        const float3 G = f3(dm[3 * t.x] + dm[3 * t.y] + dm[3 * t.z], dm[3 * t.x + 1] + dm[3 * t.y + 1] + dm[3 * t.z + 1],
+                            dm[3 * t.x + 2] + dm[3 * t.y + 2] + dm[3 * t.z + 2]);
+        const float3 a = xyz(v[t.x]), b = xyz(v[t.y]), c = xyz(v[t.z]);
+        const float3 gu = cross(c - a, G);     // d/d(b - a)
+        const float3 gw = cross(G, b - a);     // d/d(c - a)
+        if (i == t.x) acc -= gu + gw;
+        else if (i == t.y) acc += gu;
+        else acc += gw;
+    }
+    d_v[3 * i] += acc.x;
+    d_v[3 * i + 1] += acc.y;
+    d_v[3 * i + 2] += acc.z;
+}
+
+// dE/dv = R dE/dv'; accumulates M'[r][c] = sum_i g_r w_c and sum_i g (FP64).
+__global__ void __launch_bounds__(256) k_pose_adj(const float* __restrict__ v_model, int N, const float* rot,
+                                                  const float* trans, const float* __restrict__ d_v,
+                                                  float* __restrict__ d_vmodel, double* acc12) {
+    __shared__ float R[9], T[3];
+    __shared__ double part[8][12];
+    if (threadIdx.x == 0) {
+        euler_R(rot, R);
+        T[0] = trans[0]; T[1] = trans[1]; T[2] = trans[2];
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double loc[12];
+    for (int k = 0; k < 12; ++k) loc[k] = 0.0;
+    if (i < N) {
+        const float g[3] = {d_v[3 * i], d_v[3 * i + 1], d_v[3 * i + 2]};
+        const float w[3] = {v_model[3 * i] - T[0], v_model[3 * i + 1] - T[1], v_model[3 * i + 2] - T[2]};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) loc[3 * r + c] = (double)g[r] * (double)w[c];
+        for (int r = 0; r < 3; ++r) loc[9 + r] = g[r];
+        for (int c = 0; c < 3; ++c) d_vmodel[3 * i + c] = R[3 * c + 0] * g[0] + R[3 * c + 1] * g[1] + R[3 * c + 2] * g[2];
+    }
+    for (int k = 0; k < 12; ++k)
+        for (int o = 16; o > 0; o >>= 1) loc[k] += __shfl_xor_sync(0xffffffffu, loc[k], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 12; ++k) part[threadIdx.x >> 5][k] = loc[k];
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        double s = 0.0;
+        for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += part[wv][threadIdx.x];
+        atomicAdd(&acc12[threadIdx.x], s);
+    }
+}
+
+// dE/dtheta_a = sum_rc M'[r][c] dR[c][r]/dtheta_a ; dE/dT = -R sum g; plus the
+// FP64 focal and light-intensity accumulators.
+__global__ void k_pose_finish(const float* rot, const double* acc12, const double* small, int NL, float* g_rot,
+                              float* g_trans, float* g_focal, float* g_light) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        const double a = rot[0], b = rot[1], c = rot[2];
+        const double sx = sin(a), cx = cos(a), sy = sin(b), cy = cos(b), sz = sin(c), cz = cos(c);
+        double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx}, dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
+        double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy}, dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
+        double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1}, dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
+        auto mul = [](const double* A, const double* B, double* C) {
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double s = 0.0;
+                    for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+                    C[3 * i + j] = s;
+                }
+        };
+        double tmp[9], D[3][9], R[9];
+        mul(Ry, Rx, tmp); mul(Rz, tmp, R);
+        mul(Ry, dRx, tmp); mul(Rz, tmp, D[0]);
+        mul(dRy, Rx, tmp); mul(Rz, tmp, D[1]);
+        mul(Ry, Rx, tmp); mul(dRz, tmp, D[2]);
+        for (int q = 0; q < 3; ++q) {
+            double s = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int c2 = 0; c2 < 3; ++c2) s += acc12[3 * r + c2] * D[q][3 * c2 + r];
+            if (g_rot) g_rot[q] += (float)s;
+        }
+        for (int c2 = 0; c2 < 3; ++c2) {
+            double s = 0.0;
+            for (int r = 0; r < 3; ++r) s += R[3 * c2 + r] * acc12[9 + r];
+            if (g_trans) g_trans[c2] += (float)(-s);
+        }
+        if (g_focal) g_focal[0] += (float)small[0];
+    }
+    if (g_light)
+        for (int k = t; k < 3 * NL; k += blockDim.x) g_light[k] += (float)small[1 + k];
+}
+
+// dE/dcoef_k = sum_i basis[k][i] dE/dv_i, one block per k, FP64 accumulation.
+__global__ void __launch_bounds__(512) k_morph_adj(const float* __restrict__ basis, int ld4, int n3,
+                                                   const float* __restrict__ d_vmodel, float* g_coef) {
+    __shared__ double part[16];
+    const int k = blockIdx.x;
+    const float4* b = reinterpret_cast<const float4*>(basis) + (size_t)k * ld4;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < ld4; i += blockDim.x) {
+        const float4 bb = __ldcs(b + i);
+        const int e = 4 * i;
+        float s = 0.0f;
+        if (e + 0 < n3) s += bb.x * d_vmodel[e + 0];
+        if (e + 1 < n3) s += bb.y * d_vmodel[e + 1];
+        if (e + 2 < n3) s += bb.z * d_vmodel[e + 2];
+        if (e + 3 < n3) s += bb.w * d_vmodel[e + 3];
+        acc += (double)s;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        g_coef[k] += (float)s;
+    }
+}
+
+__global__ void k_philox(uint2 key, const uint4* counters, int n, uint4* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(key, counters[i]);
+}
+
+int nb(long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_morph(const float* mean, const float* basis, int ld, int K, const float* coef, float* v_model,
+                  cudaStream_t st) {
+    const int ld4 = ld / 4;
+    k_morph<<<nb(ld4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), basis, ld4, K, coef,
+                                          reinterpret_cast<float4*>(v_model));
+}
+
+void launch_pose(const float* v_model, int N, const float* rot, const float* trans, float4* v_cam,
+                 unsigned* aabb, cudaStream_t st) {
+    k_aabb_reset<<<1, 32, 0, st>>>(aabb);
+    k_pose<<<nb(N, 256), 256, 0, st>>>(v_model, N, rot, trans, v_cam, aabb);
+}
+
+void launch_faces(const float4* v_cam, const int4* faces, int T, const unsigned* aabb, float4* n_face,
+                  uint32_t* keys, int* vals, cudaStream_t st) {
+    k_faces<<<nb(T, 256), 256, 0, st>>>(v_cam, faces, T, aabb, n_face, keys, vals);
+}
+
+void launch_vertex_normals(const float4* n_face, const int* vf_off, const int* vf_idx, int N, float4* vn,
+                           cudaStream_t st) {
+    k_vertex_normals<<<nb(N, 256), 256, 0, st>>>(n_face, vf_off, vf_idx, N, vn);
+}
+
+void launch_normals_adjoint(const float4* v_cam, const float4* vn, const float* d_n, const int4* faces,
+                            const int* vf_off, const int* vf_idx, int N, float* dm, float* d_v,
+                            cudaStream_t st) {
+    k_normals_adj_a<<<nb(N, 256), 256, 0, st>>>(vn, d_n, N, dm);
+    k_normals_adj_b<<<nb(N, 256), 256, 0, st>>>(v_cam, faces, vf_off, vf_idx, N, dm, d_v);
+}
+
+void launch_pose_adjoint(const float* v_model, int N, int ld, const float* rot, const float* trans,
+                         const float* d_v, float* d_vmodel, double* acc12, cudaStream_t st) {
+    (void)ld;
+    k_pose_adj<<<nb(N, 256), 256, 0, st>>>(v_model, N, rot, trans, d_v, d_vmodel, acc12);
+}
+
+void launch_pose_finish(const float* rot, const double* acc12, const double* small, int NL, float* g_rot,
+                        float* g_trans, float* g_focal, float* g_light, cudaStream_t st) {
+    k_pose_finish<<<1, 64, 0, st>>>(rot, acc12, small, NL, g_rot, g_trans, g_focal, g_light);
+}
+
+void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const float* d_vmodel, float* g_coef,
+                          cudaStream_t st) {
+    if (K <= 0) return;
+    k_morph_adj<<<K, 512, 0, st>>>(basis, ld / 4, n3, d_vmodel, g_coef);
+}
+
+void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* counters, int n, uint32_t* out, cudaStream_t st) {
+    if (n <= 0) return;
+    k_philox<<<nb(n, 256), 256, 0, st>>>(make_uint2(k0, k1), reinterpret_cast<const uint4*>(counters), n,
+                                         reinterpret_cast<uint4*>(out));
+}

@@ -1,0 +1,269 @@
+// Linear BVH over the camera-space triangles, rebuilt every call: Morton keys
+// of the centroids (geometry.cu), a stable LSD radix sort (4 x 8-bit passes),
+// the radix-tree construction of Karras (HPG 2012) with index tie-breaks, and a
+// bottom-up box pass with one atomic flag per internal node.  Leaves are single
+// triangles; nodes store both children's boxes for two-wide tests.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int SORT_TILE = 256;
+
+__global__ void __launch_bounds__(SORT_TILE) k_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                                                    int n_tiles, int* __restrict__ hist) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * SORT_TILE + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    __syncthreads();
+    hist[threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of hist[256 * n_tiles] in place (digit-major), one block
+__global__ void __launch_bounds__(1024) k_scan(int* hist, int m) {
+    __shared__ int warp_sum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < m; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < m ? hist[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int s = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sum[lane] = s;
+        }
+        __syncthreads();
+        const int before = carry + (wid ? warp_sum[wid - 1] : 0);
+        if (i < m) hist[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_sum[31];
+        __syncthreads();
+    }
+}
+
+// Stable scatter: rank among equal digits = earlier warps' counts + earlier
+// lanes of the same warp with that digit.
+__global__ void __launch_bounds__(SORT_TILE) k_scatter(const uint32_t* __restrict__ keys, const int* __restrict__ vals,
+                                                       int n, int shift, int n_tiles, const int* __restrict__ off,
+                                                       uint32_t* __restrict__ keys_out, int* __restrict__ vals_out) {
+    constexpr int NW = SORT_TILE / 32;
+    __shared__ int cnt[NW][256];
+    for (int k = threadIdx.x; k < NW * 256; k += SORT_TILE) (&cnt[0][0])[k] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * SORT_TILE + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool ok = i < n;
+    const uint32_t key = ok ? keys[i] : 0u;
+    const int digit = ok ? (int)((key >> shift) & 255u) : 256 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (ok && rank == 0) cnt[wid][digit] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        int s = 0;
+        for (int w = 0; w < NW; ++w) {
+            const int c = cnt[w][threadIdx.x];
+            cnt[w][threadIdx.x] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+    if (ok) {
+        const int pos = off[digit * n_tiles + blockIdx.x] + cnt[wid][digit] + rank;
+        keys_out[pos] = key;
+        vals_out[pos] = vals[i];
+    }
+}
+
+// common prefix length of sorted keys i and j, ties broken by index
+FR_D int delta(const uint32_t* k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    const uint32_t a = k[i], b = k[j];
+    if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+    return __clz(a ^ b);
+}
+
+// Karras 2012: internal node i covers a key range found from the direction of
+// the larger common prefix and split at the highest differing bit.
+__global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ k, int n, int* __restrict__ child,
+                                                int* __restrict__ parent_int, int* __restrict__ parent_leaf,
+                                                int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(k, n, i, i - d);
+    int lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta(k, n, i, j);
+    int s = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const int left = (lo == gamma) ? ~gamma : gamma;
+    const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    if (gamma < 0 || gamma + 1 > n - 1 || (left >= 0 && left >= n - 1) || (right >= 0 && right >= n - 1)) {
+        set_status(status, FR_STATUS_BAD_BVH);      // cannot happen for sorted keys
+        return;
+    }
+    child[2 * i] = left;
+    child[2 * i + 1] = right;
+    if (left < 0) parent_leaf[~left] = i; else parent_int[left] = i;
+    if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
+}
+
+// Leaf boxes + sorted triangle records, then climb: the second child to arrive
+// at a node merges both boxes and continues upward.
+__global__ void __launch_bounds__(256) k_boxes(const float4* __restrict__ v, const int4* __restrict__ faces,
+                                               const int* __restrict__ vals, int n, const int* __restrict__ child,
+                                               const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
+                                               int* flag, float4* box_int, float4* box_leaf, float4* __restrict__ tris,
+                                               int* status) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int id = vals[s];
+    const int4 t = faces[id];
+    const float4 a = v[t.x], b = v[t.y], c = v[t.z];
+    tris[3 * s] = make_float4(a.x, a.y, a.z, __int_as_float(id));
+    tris[3 * s + 1] = make_float4(b.x, b.y, b.z, 0.0f);
+    tris[3 * s + 2] = make_float4(c.x, c.y, c.z, 0.0f);
+    float3 lo = f3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
+    float3 hi = f3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
+    // pad so that the FP32 slab test never culls a triangle the exact test hits
+    lo = f3(lo.x - 1e-5f - 1e-6f * fabsf(lo.x), lo.y - 1e-5f - 1e-6f * fabsf(lo.y), lo.z - 1e-5f - 1e-6f * fabsf(lo.z));
+    hi = f3(hi.x + 1e-5f + 1e-6f * fabsf(hi.x), hi.y + 1e-5f + 1e-6f * fabsf(hi.y), hi.z + 1e-5f + 1e-6f * fabsf(hi.z));
+    box_leaf[2 * s] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+    box_leaf[2 * s + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+    if (n == 1) return;
+    __threadfence();
+    int node = parent_leaf[s];
+    for (int guard = 0; node >= 0; ++guard) {
+        if (guard > 128 || node >= n - 1) { set_status(status, FR_STATUS_BAD_BVH); return; }
+        if (atomicAdd(&flag[node], 1) == 0) return;     // sibling not done yet
+        __threadfence();
+        float3 l2 = f3(INFINITY, INFINITY, INFINITY), h2 = f3(-INFINITY, -INFINITY, -INFINITY);
+        for (int q = 0; q < 2; ++q) {
+            const int ch = child[2 * node + q];
+            if (ch >= n - 1 || ~ch >= n) { set_status(status, FR_STATUS_BAD_BVH); return; }
+            const float4* bx = ch < 0 ? &box_leaf[2 * (~ch)] : &box_int[2 * ch];
+            const float4 cl = __ldcg(bx), chh = __ldcg(bx + 1);
+            l2 = f3(fminf(l2.x, cl.x), fminf(l2.y, cl.y), fminf(l2.z, cl.z));
+            h2 = f3(fmaxf(h2.x, chh.x), fmaxf(h2.y, chh.y), fmaxf(h2.z, chh.z));
+        }
+        __stcg(&box_int[2 * node], make_float4(l2.x, l2.y, l2.z, 0.0f));
+        __stcg(&box_int[2 * node + 1], make_float4(h2.x, h2.y, h2.z, 0.0f));
+        __threadfence();
+        node = node == 0 ? -1 : parent_int[node];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pack(int n, const int* __restrict__ child, const float4* __restrict__ box_int,
+                                              const float4* __restrict__ box_leaf, BvhNode* __restrict__ nodes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n == 1) {
+        if (i == 0) {
+            const float4 l = box_leaf[0], h = box_leaf[1];
+            nodes[0].a = make_float4(l.x, l.y, l.z, h.x);
+            nodes[0].b = make_float4(h.y, h.z, INFINITY, INFINITY);
+            nodes[0].c = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
+            nodes[0].d = make_int4(~0, ~0, 0, 0);
+        }
+        return;
+    }
+    if (i >= n - 1) return;
+    const int c0 = child[2 * i], c1 = child[2 * i + 1];
+    const float4* b0 = c0 < 0 ? &box_leaf[2 * (~c0)] : &box_int[2 * c0];
+    const float4* b1 = c1 < 0 ? &box_leaf[2 * (~c1)] : &box_int[2 * c1];
+    const float4 l0 = b0[0], h0 = b0[1], l1 = b1[0], h1 = b1[1];
+    nodes[i].a = make_float4(l0.x, l0.y, l0.z, h0.x);
+    nodes[i].b = make_float4(h0.y, h0.z, l1.x, l1.y);
+    nodes[i].c = make_float4(l1.z, h1.x, h1.y, h1.z);
+    nodes[i].d = make_int4(c0, c1, 0, 0);
+}
+
+// Validity: every leaf referenced exactly once, child boxes inside the parent's
+// stored box, depth of each leaf.
+__global__ void k_check(const BvhNode* nodes, const int* child, const int* parent_int, const int* parent_leaf,
+                        const float4* box_int, int n, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n == 1) { if (i == 0) { out[0] = 1; out[1] = 0; out[2] = 1; } return; }
+    if (i < n - 1) {
+        const int cc[2] = {nodes[i].d.x, nodes[i].d.y};
+        for (int q = 0; q < 2; ++q) {
+            if (cc[q] < 0) { atomicAdd(&out[0], 1); continue; }
+            // the child's own children boxes must lie inside this node's box for it
+            const BvhNode& ch = nodes[cc[q]];
+            const float4 pa = nodes[i].a, pb = nodes[i].b, pc = nodes[i].c;
+            const float3 plo = q == 0 ? f3(pa.x, pa.y, pa.z) : f3(pb.z, pb.w, pc.x);
+            const float3 phi = q == 0 ? f3(pa.w, pb.x, pb.y) : f3(pc.y, pc.z, pc.w);
+            const float3 lo0 = f3(ch.a.x, ch.a.y, ch.a.z), hi0 = f3(ch.a.w, ch.b.x, ch.b.y);
+            const float3 lo1 = f3(ch.b.z, ch.b.w, ch.c.x), hi1 = f3(ch.c.y, ch.c.z, ch.c.w);
+            const bool in = lo0.x >= plo.x && lo0.y >= plo.y && lo0.z >= plo.z && hi0.x <= phi.x && hi0.y <= phi.y &&
+                            hi0.z <= phi.z && lo1.x >= plo.x && lo1.y >= plo.y && lo1.z >= plo.z && hi1.x <= phi.x &&
+                            hi1.y <= phi.y && hi1.z <= phi.z;
+            if (!in) atomicAdd(&out[1], 1);
+        }
+    }
+    if (i < n) {
+        int depth = 1, node = parent_leaf[i];
+        while (node > 0 && depth < 4096) { node = parent_int[node]; ++depth; }
+        atomicMax(&out[2], depth);
+    }
+}
+
+int nb(long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_lbvh(const float4* v_cam, const int4* faces, int T, BvhScratch& B, BvhNode* nodes, float4* tris,
+                 int* status, cudaStream_t st) {
+    const int n_tiles = nb(T, SORT_TILE);
+    uint32_t *ka = B.keys, *kb = B.keys_alt;
+    int *va = B.vals, *vb = B.vals_alt;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        k_hist<<<n_tiles, SORT_TILE, 0, st>>>(ka, T, shift, n_tiles, B.hist);
+        k_scan<<<1, 1024, 0, st>>>(B.hist, 256 * n_tiles);
+        k_scatter<<<n_tiles, SORT_TILE, 0, st>>>(ka, va, T, shift, n_tiles, B.hist, kb, vb);
+        uint32_t* tk = ka; ka = kb; kb = tk;
+        int* tv = va; va = vb; vb = tv;
+    }
+    // after an even number of passes the sorted data is back in keys/vals
+    if (T > 1) {
+        cudaMemsetAsync(B.flag, 0, sizeof(int) * (size_t)(T - 1), st);
+        cudaMemsetAsync(B.parent_int, 0xff, sizeof(int) * (size_t)(T - 1), st);
+        cudaMemsetAsync(B.parent_leaf, 0xff, sizeof(int) * (size_t)T, st);
+        // unwritten child slots read as leaf 0, never as an ancestor
+        cudaMemsetAsync(B.child, 0xff, sizeof(int) * 2 * (size_t)(T - 1), st);
+        k_karras<<<nb(T - 1, 256), 256, 0, st>>>(ka, T, B.child, B.parent_int, B.parent_leaf, status);
+    }
+    k_boxes<<<nb(T, 256), 256, 0, st>>>(v_cam, faces, va, T, B.child, B.parent_int, B.parent_leaf, B.flag,
+                                        B.box_int, B.box_leaf, tris, status);
+    k_pack<<<nb(T > 1 ? T - 1 : 1, 256), 256, 0, st>>>(T, B.child, B.box_int, B.box_leaf, nodes);
+}
+
+void launch_bvh_check(const BvhNode* nodes, const BvhScratch& B, int T, int* out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, sizeof(int) * 3, st);
+    k_check<<<nb(T, 256), 256, 0, st>>>(nodes, B.child, B.parent_int, B.parent_leaf, B.box_int, T, out);
+}

@@ -1,0 +1,706 @@
+// Forward render, adjoint (interior + shadow-boundary terms), primary-edge
+// boundary term and silhouette classification (Sec. 4: the Monte Carlo
+// estimator F with shadow rays, differentiated with edge sampling).
+//
+// One thread per camera sample (pixel, sample).  Shadow rays of a warp are
+// compacted through a 64-entry ring in shared memory so that every traversal
+// launched runs 32 lanes wide; the visibility outcome lands in a per-lane
+// bitmask and each lane then sums its own visible lights in light order, so the
+// result does not depend on the compaction order.
+#include "common.cuh"
+#include "kernels.h"
+#include "shade.cuh"
+#include "trace.cuh"
+
+namespace {
+
+constexpr int RT_THREADS = 128;
+constexpr int RT_WARPS = RT_THREADS / 32;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr float SHADOW_EPS = 1e-4f;     // shadow segment trimmed to (eps, 1 - eps)
+
+struct WarpQueue {
+    float4 job[64][2];                  // (y.xyz, z.x) (z.y, z.z, skip, owner | light << 8)
+    unsigned long long vis[32];
+};
+
+struct RtShared {
+    int stack[FR_STACK * RT_THREADS];
+    WarpQueue wq[RT_WARPS];
+    double acc[1 + 3 * FR_MAX_LIGHTS];  // focal, light intensities (block partials)
+};
+
+FR_D Stack my_stack(RtShared& sh) { return Stack{&sh.stack[threadIdx.x], RT_THREADS}; }
+
+struct SampleState {
+    bool hit;
+    int tri;
+    float b1, b2;
+    float3 d;          // camera ray direction (not normalised)
+    float3 y, ns, o;
+    float2 uv;
+    Material m;
+    Tap tap;
+};
+
+// Primary ray through screen point (sx, sy) and the shading state at its hit.
+FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
+                        Stack st, SampleState& ss) {
+    ss.hit = false;
+    ss.tri = -1;
+    if (!active) return;
+    const float f = __ldg(P.focal);
+    ss.d = f3((sx - 0.5f * S.W) / f, -(sy - 0.5f * S.H) / f, -1.0f);
+    const RayPre r = ray_setup(f3(0.0f, 0.0f, 0.0f), ss.d);
+    const Hit h = trace_closest(S, r, 0.0f, INFINITY, st);
+    if (h.tri < 0) return;
+    ss.hit = true;
+    ss.tri = h.tri;
+    ss.b1 = h.b1;
+    ss.b2 = h.b2;
+    const int4 fc = __ldg(&S.faces[h.tri]);
+    const float b0 = 1.0f - h.b1 - h.b2;
+    const float3 v0 = xyz(__ldg(&S.v[fc.x])), v1 = xyz(__ldg(&S.v[fc.y])), v2 = xyz(__ldg(&S.v[fc.z]));
+    const float3 n0 = xyz(__ldg(&S.vn[fc.x])), n1 = xyz(__ldg(&S.vn[fc.y])), n2 = xyz(__ldg(&S.vn[fc.z]));
+    ss.y = v0 * b0 + v1 * h.b1 + v2 * h.b2;
+    const float3 m = n0 * b0 + n1 * h.b1 + n2 * h.b2;
+    ss.ns = m * (1.0f / length(m));
+    ss.o = -ss.d * (1.0f / length(ss.d));
+    const float2 t0 = __ldg(&S.uv[fc.x]), t1 = __ldg(&S.uv[fc.y]), t2 = __ldg(&S.uv[fc.z]);
+    ss.uv = make_float2(b0 * t0.x + h.b1 * t1.x + h.b2 * t2.x, b0 * t0.y + h.b1 * t1.y + h.b2 * t2.y);
+    ss.tap = make_tap(S.M, ss.uv.x, ss.uv.y);
+    ss.m.c = f3(tap_fetch(P.diffuse, 3, 0, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.diffuse, 3, 1, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.diffuse, 3, 2, ss.tap, S.M, nullptr, nullptr));
+    ss.m.s = f3(tap_fetch(P.specular, 3, 0, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.specular, 3, 1, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.specular, 3, 2, ss.tap, S.M, nullptr, nullptr));
+    ss.m.r = tap_fetch(P.roughness, 1, 0, ss.tap, S.M, nullptr, nullptr);
+}
+
+// Light-sample dims of a sampler, cached per Philox block (warp-uniform).
+struct DimCache {
+    int b = -1;
+    uint4 w;
+    FR_D float2 pair(const Sampler& s, int d) {
+        const int bb = d >> 2;
+        if (bb != b) { w = s.block(bb); b = bb; }
+        return (d & 2) ? make_float2(u24(w.z), u24(w.w)) : make_float2(u24(w.x), u24(w.y));
+    }
+};
+
+FR_D bool light_visible_geometry(const LightDev& L, float3 z, const SampleState& ss) {
+    const float3 lv = z - ss.y;
+    return dot(ss.ns, lv) > 0.0f && -dot(L.n, lv) > 0.0f;
+}
+
+// Trace the queued jobs [head, head + n) of this warp's ring (lane k takes job k).
+FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st) {
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const float4 a = q.job[(head + lane) & 63][0], b = q.job[(head + lane) & 63][1];
+        const float3 y = f3(a.x, a.y, a.z), z = f3(a.w, b.x, b.y);
+        const int skip = __float_as_int(b.z), tag = __float_as_int(b.w);
+        const RayPre r = ray_setup(y, z - y);
+        if (!trace_any(S, r, SHADOW_EPS, 1.0f - SHADOW_EPS, skip, st))
+            atomicOr(&q.vis[tag & 31], 1ull << (tag >> 8));
+    }
+    __syncwarp();
+}
+
+// Warp-cooperative shadow visibility for every light: bit j set when the shadow
+// ray to this lane's light-j sample is traced and unoccluded.  All 32 lanes
+// must call this together.
+FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sampler& smp, int dim0,
+                          WarpQueue& q, Stack st) {
+    const int lane = threadIdx.x & 31;
+    q.vis[lane] = 0ull;
+    __syncwarp();
+    const bool want = ss.hit && dot(ss.ns, ss.o) > 0.0f && !(S.flags & FR_FLAG_FLAT_D);
+    int head = 0, count = 0;
+    DimCache dc;
+    for (int j = 0; j < S.NL; ++j) {
+        bool need = false;
+        float3 z = f3(0.0f, 0.0f, 0.0f);
+        if (want) {
+            const LightDev& L = S.lights[j];
+            const float2 u = dc.pair(smp, dim0 + 2 * j);
+            z = light_point(L, u.x, u.y);
+            need = light_visible_geometry(L, z, ss);
+        }
+        const unsigned ballot = __ballot_sync(FULL, need);
+        if (need) {
+            const int slot = (head + count + __popc(ballot & ((1u << lane) - 1u))) & 63;
+            q.job[slot][0] = make_float4(ss.y.x, ss.y.y, ss.y.z, z.x);
+            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.tri), __int_as_float(lane | (j << 8)));
+        }
+        count += __popc(ballot);
+        __syncwarp();
+        if (count >= 32) {
+            drain(S, q, head, 32, st);
+            head = (head + 32) & 63;
+            count -= 32;
+        }
+    }
+    if (count > 0) drain(S, q, head, count, st);
+    return q.vis[lane];
+}
+
+// Unoccluded contribution of light j at z (without the 1/pdf area factor):
+// h = f_r cos_s cos_l / |z - y|^2 (RGB).  With ADJ, the upstream gradient gh
+// (dE/dh per channel) flows into g (n, o, c, s, r) and into gy.
+template <bool ADJ>
+FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleState& ss, float3 gh,
+                    ShadeAdj* g, float3* gy) {
+    const float3 lv = z - ss.y;
+    const float d2 = dot(lv, lv);
+    const float inv_len = 1.0f / sqrtf(d2);
+    const float3 l = lv * inv_len;
+    const float cos_s = dot(ss.ns, l), cos_l = -dot(L.n, l);
+    if (!(cos_s > 0.0f) || !(cos_l > 0.0f) || !(dot(ss.ns, ss.o) > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    const float geo = cos_s * cos_l / d2;
+    float3 f;
+    if (ADJ) {
+        const float3 gf = f3(gh.x * geo, gh.y * geo, gh.z * geo);
+        const float3 keep_l = g->l;
+        g->l = f3(0.0f, 0.0f, 0.0f);
+        f = brdf<true>(flags, ss.ns, l, ss.o, ss.m, gf, g);
+        const float ggeo = gh.x * f.x + gh.y * f.y + gh.z * f.z;
+        const float gcs = ggeo * cos_l / d2, gcl = ggeo * cos_s / d2, gd2 = -ggeo * geo / d2;
+        g->n += l * gcs;
+        const float3 gl = g->l + ss.ns * gcs - L.n * gcl;
+        g->l = keep_l;
+        const float3 glv = (gl - l * dot(l, gl)) * inv_len + lv * (2.0f * gd2);
+        *gy -= glv;
+    } else {
+        f = brdf<false>(flags, ss.ns, l, ss.o, ss.m, f3(0, 0, 0), nullptr);
+    }
+    return f * geo;
+}
+
+FR_D float3 intensity(const DevScene& S, const DevParams& P, int j) {
+    const float sc = S.lights[j].scale;
+    return f3(sc * __ldg(&P.light_i[3 * j]), sc * __ldg(&P.light_i[3 * j + 1]), sc * __ldg(&P.light_i[3 * j + 2]));
+}
+
+// Radiance of this lane's sample given its state and visibility mask.
+FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleState& ss, uint64_t vis,
+                          const Sampler& smp, int dim0) {
+    float3 Lo = f3(0.0f, 0.0f, 0.0f);
+    if (!ss.hit) return Lo;
+    if (S.flags & FR_FLAG_FLAT_D) return ss.m.c;
+    DimCache dc;
+    for (int j = 0; j < S.NL; ++j) {
+        if (!((vis >> j) & 1ull)) continue;
+        const LightDev& L = S.lights[j];
+        const float2 u = dc.pair(smp, dim0 + 2 * j);
+        const float3 z = light_point(L, u.x, u.y);
+        const float3 h = light_h<false>(S.flags, L, z, ss, f3(0, 0, 0), nullptr, nullptr);
+        const float3 I = intensity(S, P, j);
+        Lo += f3(h.x * I.x, h.y * I.y, h.z * I.z) * L.area;
+    }
+    return Lo;
+}
+
+// Full warp-cooperative radiance evaluation at screen point (sx, sy).
+FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
+                        const Sampler& smp, int dim0, RtShared& sh, SampleState& ss, uint64_t& vis) {
+    primary_state(S, P, active, sx, sy, my_stack(sh), ss);
+    vis = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], my_stack(sh));
+    return radiance_from(S, P, ss, vis, smp, dim0);
+}
+
+FR_D float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// sum over aligned groups of `width` lanes (width a power of two <= 32)
+FR_D float group_sum(float v, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_forward(DevScene S, DevParams P, float* image,
+                                                        int32_t* tri_rec, uint64_t* mask_rec,
+                                                        uint32_t iteration, uint32_t face) {
+    __shared__ RtShared sh;
+    const long total = (long)S.W * S.H * S.spp;
+    const long q = (long)blockIdx.x * RT_THREADS + threadIdx.x;
+    const bool valid = q < total;
+    const int pixel = valid ? (int)(q / S.spp) : 0;
+    const int s = valid ? (int)(q % S.spp) : 0;
+    const Sampler smp{make_uint2(S.seed, FR_STREAM_PRIMARY), (uint32_t)pixel, (uint32_t)s, iteration, face};
+    const float2 jit = smp.pair(0);
+    SampleState ss;
+    uint64_t vis;
+    const float3 Lo = radiance_at(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
+                                  smp, 2, sh, ss, vis);
+    if (valid && tri_rec) tri_rec[q] = ss.tri;
+    if (valid && mask_rec) mask_rec[q] = vis;
+    const int width = S.spp < 32 ? S.spp : 32;
+    const float rx = group_sum(Lo.x, width), ry = group_sum(Lo.y, width), rz = group_sum(Lo.z, width);
+    const float inv = 1.0f / (float)S.spp;
+    if (valid && (s % width) == 0) {
+        float* px = image + 3 * (size_t)pixel;
+        if (S.spp <= 32) {
+            px[0] = rx * inv; px[1] = ry * inv; px[2] = rz * inv;
+        } else {
+            atomicAdd(&px[0], rx * inv); atomicAdd(&px[1], ry * inv); atomicAdd(&px[2], rz * inv);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+FR_D void block_acc_init(RtShared& sh, int n) {
+    for (int i = threadIdx.x; i < n; i += RT_THREADS) sh.acc[i] = 0.0;
+    __syncthreads();
+}
+
+FR_D void block_acc_flush(RtShared& sh, int n, double* out) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += RT_THREADS)
+        if (sh.acc[i] != 0.0) atomicAdd(&out[i], sh.acc[i]);
+}
+
+FR_D void add_vec(float* base, int vertex, float3 g, bool on) {
+    if (!on) return;
+    atomicAdd(&base[3 * vertex + 0], g.x);
+    atomicAdd(&base[3 * vertex + 1], g.y);
+    atomicAdd(&base[3 * vertex + 2], g.z);
+}
+
+// Warp-aggregated scatter of a per-vertex 3-vector (lanes hitting the same
+// vertex combine first).
+FR_D void scatter_vertex(float* base, int vertex, float3 g, bool on) {
+    const unsigned act = __ballot_sync(FULL, on);
+    if (!on) return;
+    warp_agg_add(&base[3 * vertex + 0], g.x, (uint32_t)vertex, act);
+    warp_agg_add(&base[3 * vertex + 1], g.y, (uint32_t)vertex, act);
+    warp_agg_add(&base[3 * vertex + 2], g.z, (uint32_t)vertex, act);
+}
+
+FR_D void scatter_texel(float* base, int C, int texel, int ch, float g, bool on) {
+    const unsigned act = __ballot_sync(FULL, on);
+    if (!on || base == nullptr) return;
+    warp_agg_add(&base[texel * C + ch], g, (uint32_t)texel, act);
+}
+
+// One shadow-boundary edge sample at this lane's shading point (edge sampling
+// for visibility of the emitter, Sec. 4).  Adds C * dz/dy . m to gy and
+// scatters the edge-vertex terms.  Returns nothing; inactive lanes do nothing.
+FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL, const SampleState& ss,
+                      const Sampler& sm2, float3 w, float3& gy, float* d_v, Stack st) {
+    const uint4 blk = sm2.block(0);
+    const float u0 = u24(blk.x), u1 = u24(blk.y), u2 = u24(blk.z);
+    const int j = min((int)(u0 * (float)S.NL), S.NL - 1);
+    const int Sj = EL.light_count[j];
+    if (Sj == 0) return;
+    const int eid = EL.light_list[(size_t)j * S.E + min((int)(u1 * (float)Sj), Sj - 1)];
+    const int4 E = EL.edges[eid];
+    const int4 fc = S.faces[ss.tri];
+    const bool ha = (E.x == fc.x || E.x == fc.y || E.x == fc.z);
+    const bool hb = (E.y == fc.x || E.y == fc.y || E.y == fc.z);
+    if (ha && hb) return;
+    const float3 A = xyz(S.v[E.x]), B = xyz(S.v[E.y]);
+    if (E.w >= 0) {
+        // silhouette w.r.t. y, in FP64
+        const int4 f1 = S.faces[E.z], f2 = S.faces[E.w];
+        const double ax = A.x, ay = A.y, az = A.z;
+        const double yx = (double)ss.y.x - ax, yy = (double)ss.y.y - ay, yz = (double)ss.y.z - az;
+        int sg[2];
+        const int4 ff[2] = {f1, f2};
+        for (int k = 0; k < 2; ++k) {
+            const float4 p0 = S.v[ff[k].x], p1 = S.v[ff[k].y], p2 = S.v[ff[k].z];
+            const double e1x = (double)p1.x - p0.x, e1y = (double)p1.y - p0.y, e1z = (double)p1.z - p0.z;
+            const double e2x = (double)p2.x - p0.x, e2y = (double)p2.y - p0.y, e2z = (double)p2.z - p0.z;
+            const double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+            const double dd = nx * yx + ny * yy + nz * yz;
+            sg[k] = (dd > 0.0) - (dd < 0.0);
+        }
+        if (sg[0] == sg[1]) return;
+    }
+    const LightDev& L = S.lights[j];
+    const float t = u2;
+    const float3 e = B - A;
+    const float3 pe = A + e * t;
+    const float3 q = pe - ss.y;
+    const float den = dot(q, L.n);
+    const float num = dot(L.c - ss.y, L.n);
+    if (den == 0.0f) return;
+    const float sc = num / den;
+    if (!(sc > 1.0f)) return;
+    const float3 z = ss.y + q * sc;
+    if (!inside_emitter(L, z)) return;
+    const float3 h = light_h<false>(S.flags, L, z, ss, f3(0, 0, 0), nullptr, nullptr);
+    if (h.x == 0.0f && h.y == 0.0f && h.z == 0.0f) return;
+    const float3 tan = (e - q * (dot(e, L.n) / den)) * sc;
+    const float tl = length(tan);
+    if (!(tl > 0.0f)) return;
+    const float3 m = cross(L.n, tan) * (1.0f / tl);
+    const float3 zp = z + m * SHADOW_EPS, zm = z - m * SHADOW_EPS;
+    const bool vp = !trace_any(S, ray_setup(ss.y, zp - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st);
+    const bool vm = !trace_any(S, ray_setup(ss.y, zm - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st);
+    const float dV = (float)vp - (float)vm;
+    if (dV == 0.0f) return;
+    const float3 I = intensity(S, P, j);
+    const float scale = -dV * (float)S.NL * (float)Sj * tl;
+    const float C = scale * (w.x * h.x * I.x + w.y * h.y * I.y + w.z * h.z * I.z);
+    const float mq = dot(m, q);
+    const float3 g_y = m * (1.0f - sc) + L.n * (mq * (sc - 1.0f) / den);
+    const float3 g_p = m * sc - L.n * (mq * sc / den);
+    gy += g_y * C;
+    add_vec(d_v, E.x, g_p * (C * (1.0f - t)), true);
+    add_vec(d_v, E.y, g_p * (C * t), true);
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_adjoint(DevScene S, DevParams P, DevGrads G, EdgeLists EL,
+                                                        const float* adj_image, uint32_t iteration,
+                                                        uint32_t face) {
+    __shared__ RtShared sh;
+    block_acc_init(sh, 1 + 3 * S.NL);
+    const long total = (long)S.W * S.H * S.spp;
+    const long qi = (long)blockIdx.x * RT_THREADS + threadIdx.x;
+    bool valid = qi < total;
+    const int pixel = valid ? (int)(qi / S.spp) : 0;
+    const int s = valid ? (int)(qi % S.spp) : 0;
+    float3 w = f3(0.0f, 0.0f, 0.0f);
+    if (valid) {
+        const float inv = 1.0f / (float)S.spp;
+        w = f3(adj_image[3 * (size_t)pixel] * inv, adj_image[3 * (size_t)pixel + 1] * inv,
+               adj_image[3 * (size_t)pixel + 2] * inv);
+        if (w.x == 0.0f && w.y == 0.0f && w.z == 0.0f) valid = false;
+    }
+    const Sampler smp{make_uint2(S.seed, FR_STREAM_PRIMARY), (uint32_t)pixel, (uint32_t)s, iteration, face};
+    const float2 jit = smp.pair(0);
+    const float sx = (float)(pixel % S.W) + jit.x, sy = (float)(pixel / S.W) + jit.y;
+    SampleState ss;
+    primary_state(S, P, valid, sx, sy, my_stack(sh), ss);
+    const uint64_t vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh));
+    const bool interior = !(S.flags & FR_FLAG_NO_INTERIOR_D);
+    ShadeAdj g;
+    g.n = g.l = g.o = g.c = g.s = f3(0.0f, 0.0f, 0.0f);
+    g.r = 0.0f;
+    float3 gy = f3(0.0f, 0.0f, 0.0f);
+    if (S.flags & FR_FLAG_FLAT_D) {
+        if (ss.hit && interior) g.c = w;
+    } else {
+        DimCache dc;
+        for (int j = 0; j < S.NL; ++j) {                       // warp-uniform loop
+            float3 gI = f3(0.0f, 0.0f, 0.0f);
+            if (interior && ss.hit && ((vis >> j) & 1ull)) {
+                const LightDev& L = S.lights[j];
+                const float2 u = dc.pair(smp, 2 + 2 * j);
+                const float3 z = light_point(L, u.x, u.y);
+                const float3 I = intensity(S, P, j);
+                const float3 gh = f3(w.x * I.x, w.y * I.y, w.z * I.z) * L.area;
+                const float3 h = light_h<true>(S.flags, L, z, ss, gh, &g, &gy);
+                gI = f3(w.x * h.x, w.y * h.y, w.z * h.z) * (L.area * L.scale);
+            }
+            const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
+            if ((threadIdx.x & 31) == 0 && (sx_ != 0.0f || sy_ != 0.0f || sz_ != 0.0f)) {
+                atomicAdd(&sh.acc[1 + 3 * j], (double)sx_);
+                atomicAdd(&sh.acc[1 + 3 * j + 1], (double)sy_);
+                atomicAdd(&sh.acc[1 + 3 * j + 2], (double)sz_);
+            }
+        }
+        if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit) {
+            const Sampler sm2{make_uint2(S.seed, FR_STREAM_EDGE_SHADOW), (uint32_t)pixel, (uint32_t)s, iteration, face};
+            shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, my_stack(sh));
+        }
+    }
+    // ---- chain rule back to the hit triangle, its normals and the camera ----
+    const bool on = ss.hit;
+    int4 fc = make_int4(0, 0, 0, 0);
+    float gfocal = 0.0f;
+    float3 gv0 = f3(0, 0, 0), gv1 = f3(0, 0, 0), gv2 = f3(0, 0, 0);
+    float3 gn0 = f3(0, 0, 0), gn1 = f3(0, 0, 0), gn2 = f3(0, 0, 0);
+    float gtex[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (on) {
+        fc = S.faces[ss.tri];
+        const float3 v0 = xyz(S.v[fc.x]), v1 = xyz(S.v[fc.y]), v2 = xyz(S.v[fc.z]);
+        const float3 n0 = xyz(S.vn[fc.x]), n1 = xyz(S.vn[fc.y]), n2 = xyz(S.vn[fc.z]);
+        const float2 t0 = S.uv[fc.x], t1 = S.uv[fc.y], t2 = S.uv[fc.z];
+        // intersection quantities (Moller-Trumbore form, ray origin at the camera)
+        const float3 e1 = v1 - v0, e2 = v2 - v0, sv = -v0;
+        const float3 pv = cross(ss.d, e2), qv = cross(sv, e1);
+        const float det = dot(e1, pv);
+        const float b1 = dot(sv, pv) / det, b2 = dot(ss.d, qv) / det, b0 = 1.0f - b1 - b2;
+        // textures: value gradients and d/d(uv)
+        float gu = 0.0f, gvv = 0.0f;
+        for (int ch = 0; ch < 3; ++ch) {
+            float du, dv;
+            tap_fetch(P.diffuse, 3, ch, ss.tap, S.M, &du, &dv);
+            const float gc = comp(g.c, ch);
+            gu += gc * du; gvv += gc * dv;
+            tap_fetch(P.specular, 3, ch, ss.tap, S.M, &du, &dv);
+            const float gs = comp(g.s, ch);
+            gu += gs * du; gvv += gs * dv;
+            gtex[ch] = gc;
+            gtex[3 + ch] = gs;
+        }
+        {
+            float du, dv;
+            tap_fetch(P.roughness, 1, 0, ss.tap, S.M, &du, &dv);
+            gu += g.r * du; gvv += g.r * dv;
+            gtex[6] = g.r;
+        }
+        float gb0 = gu * t0.x + gvv * t0.y, gb1 = gu * t1.x + gvv * t1.y, gb2 = gu * t2.x + gvv * t2.y;
+        // shading normal ns = m / |m|, m = sum b_k n_k
+        const float3 mm = n0 * b0 + n1 * b1 + n2 * b2;
+        const float inv_m = 1.0f / length(mm);
+        const float3 nsh = mm * inv_m;
+        const float3 gm = (g.n - nsh * dot(nsh, g.n)) * inv_m;
+        gn0 = gm * b0; gn1 = gm * b1; gn2 = gm * b2;
+        gb0 += dot(n0, gm); gb1 += dot(n1, gm); gb2 += dot(n2, gm);
+        // y = sum b_k v_k
+        gv0 = gy * b0; gv1 = gy * b1; gv2 = gy * b2;
+        gb0 += dot(v0, gy); gb1 += dot(v1, gy); gb2 += dot(v2, gy);
+        // view direction o = -d / |d|
+        const float inv_d = 1.0f / length(ss.d);
+        const float3 od = -ss.d * inv_d;
+        float3 gd = -(g.o - od * dot(od, g.o)) * inv_d;
+        // barycentrics from the intersection
+        const float G1 = gb1 - gb0, G2 = gb2 - gb0;
+        const float gsp = G1 / det, gdq = G2 / det, gdet = -(G1 * b1 + G2 * b2) / det;
+        float3 gs = pv * gsp;
+        float3 gp = sv * gsp + e1 * gdet;
+        gd += qv * gdq;
+        const float3 gq = ss.d * gdq;
+        float3 ge1 = pv * gdet;
+        gs += cross(e1, gq);
+        ge1 += cross(gq, sv);
+        gd += cross(e2, gp);
+        const float3 ge2 = cross(gp, ss.d);
+        gv0 += -gs - ge1 - ge2;
+        gv1 += ge1;
+        gv2 += ge2;
+        // d = ((sx - W/2)/f, -(sy - H/2)/f, -1)
+        const float f = P.focal[0];
+        gfocal = -(gd.x * ss.d.x + gd.y * ss.d.y) / f;
+    }
+    scatter_vertex(G.d_v, fc.x, gv0, on);
+    scatter_vertex(G.d_v, fc.y, gv1, on);
+    scatter_vertex(G.d_v, fc.z, gv2, on);
+    scatter_vertex(G.d_n, fc.x, gn0, on);
+    scatter_vertex(G.d_n, fc.y, gn1, on);
+    scatter_vertex(G.d_n, fc.z, gn2, on);
+    // bilinear texture scatter (4 taps), warp-aggregated by texel
+    const bool tex_on = on && interior;
+    const int taps[4] = {ss.tap.i00, ss.tap.i10, ss.tap.i01, ss.tap.i11};
+    const float tw[4] = {(1.0f - ss.tap.fx) * (1.0f - ss.tap.fy), ss.tap.fx * (1.0f - ss.tap.fy),
+                         (1.0f - ss.tap.fx) * ss.tap.fy, ss.tap.fx * ss.tap.fy};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        for (int ch = 0; ch < 3; ++ch) {
+            scatter_texel(G.diffuse, 3, taps[k], ch, gtex[ch] * tw[k], tex_on);
+            scatter_texel(G.specular, 3, taps[k], ch, gtex[3 + ch] * tw[k], tex_on);
+        }
+        scatter_texel(G.roughness, 1, taps[k], 0, gtex[6] * tw[k], tex_on);
+    }
+    const float gf_w = warp_sum(gfocal);
+    if ((threadIdx.x & 31) == 0 && gf_w != 0.0f) atomicAdd(&sh.acc[0], (double)gf_w);
+    block_acc_flush(sh, 1 + 3 * S.NL, G.small);
+}
+
+// ---------------------------------------------------------------------------
+// primary-visibility boundary term: edge samples in screen space
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(RT_THREADS) k_edge_primary(DevScene S, DevParams P, DevGrads G, EdgeLists EL,
+                                                             const float* adj_image, uint32_t iteration,
+                                                             uint32_t face) {
+    __shared__ RtShared sh;
+    block_acc_init(sh, 1);
+    const long n_edge = (long)S.W * S.H * S.edge_spp;
+    const long e = (long)blockIdx.x * RT_THREADS + threadIdx.x;
+    bool active = e < n_edge;
+    const int Sn = *EL.prim_count;
+    if (Sn == 0) active = false;
+    const Sampler smp{make_uint2(S.seed, FR_STREAM_EDGE_PRIMARY), (uint32_t)(active ? e : 0), 0u, iteration, face};
+    const uint4 blk = smp.block(0);
+    int4 E = make_int4(0, 0, 0, 0);
+    float3 A = f3(0, 0, 0), B = f3(0, 0, 0), p = f3(0, 0, 0);
+    float t = 0.0f, X = 0.0f, Y = 0.0f, mx = 0.0f, my = 0.0f, tl = 0.0f, wz = 1.0f;
+    float3 adj = f3(0, 0, 0);
+    const float f = P.focal[0];
+    if (active) {
+        E = EL.edges[EL.prim_list[min((int)(u24(blk.x) * (float)Sn), Sn - 1)]];
+        A = xyz(S.v[E.x]);
+        B = xyz(S.v[E.y]);
+        t = u24(blk.y);
+        const float3 ed = B - A;
+        p = A + ed * t;
+        if (!(p.z < 0.0f)) active = false;
+        if (active) {
+            wz = -p.z;
+            X = 0.5f * S.W + f * p.x / wz;
+            Y = 0.5f * S.H - f * p.y / wz;
+            if (!(X >= 0.0f && X < (float)S.W && Y >= 0.0f && Y < (float)S.H)) active = false;
+        }
+        if (active) {
+            const int pix = (int)floorf(Y) * S.W + (int)floorf(X);
+            adj = f3(adj_image[3 * (size_t)pix], adj_image[3 * (size_t)pix + 1], adj_image[3 * (size_t)pix + 2]);
+            if (adj.x == 0.0f && adj.y == 0.0f && adj.z == 0.0f) active = false;
+            const float tx = f * (ed.x * wz + p.x * ed.z) / (wz * wz);
+            const float ty = -f * (ed.y * wz + p.y * ed.z) / (wz * wz);
+            tl = sqrtf(tx * tx + ty * ty);
+            if (!(tl > 0.0f)) active = false;
+            mx = -ty / tl;
+            my = tx / tl;
+        }
+    }
+    const float eps = 1e-3f;
+    SampleState ssp, ssm;
+    uint64_t visp, vism;
+    const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, ssp, visp);
+    const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, ssm, vism);
+    float gf = 0.0f;
+    float3 gA = f3(0, 0, 0), gB = f3(0, 0, 0);
+    if (active) {
+        const float scale = (float)Sn * tl / (float)n_edge;
+        const float Wt = -(adj.x * (Lp.x - Lm.x) + adj.y * (Lp.y - Lm.y) + adj.z * (Lp.z - Lm.z)) * scale;
+        const float3 gp = f3(Wt * mx * f / wz, -Wt * my * f / wz, Wt * (mx * f * p.x - my * f * p.y) / (wz * wz));
+        gA = gp * (1.0f - t);
+        gB = gp * t;
+        gf = Wt * (mx * p.x - my * p.y) / wz;
+        if (Wt == 0.0f) active = false;
+    }
+    scatter_vertex(G.d_v, E.x, gA, active);
+    scatter_vertex(G.d_v, E.y, gB, active);
+    const float gw = warp_sum(gf);
+    if ((threadIdx.x & 31) == 0 && gw != 0.0f) atomicAdd(&sh.acc[0], (double)gw);
+    block_acc_flush(sh, 1, G.small);
+}
+
+// ---------------------------------------------------------------------------
+// silhouettes (FP64 classification) and ordered compaction
+// ---------------------------------------------------------------------------
+__device__ double3 face_normal_d(const DevScene& S, int f) {
+    const int4 t = S.faces[f];
+    const float4 p0 = S.v[t.x], p1 = S.v[t.y], p2 = S.v[t.z];
+    const double e1x = (double)p1.x - p0.x, e1y = (double)p1.y - p0.y, e1z = (double)p1.z - p0.z;
+    const double e2x = (double)p2.x - p0.x, e2y = (double)p2.y - p0.y, e2z = (double)p2.z - p0.z;
+    return make_double3(e1y * e2z - e1z * e2y, e1z * e2x - e1x * e2z, e1x * e2y - e1y * e2x);
+}
+
+__device__ int sgn_d(double x) { return (x > 0.0) - (x < 0.0); }
+
+// flags[list][E]: list 0 = primary silhouettes (w.r.t. the camera centre),
+// list 1 + j = conservative shadow candidates of light j.
+__global__ void k_classify(DevScene S, const int4* edges, uint8_t* flags) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S.E) return;
+    const int4 E = edges[e];
+    if (E.w < 0) {
+        for (int l = 0; l <= S.NL; ++l) flags[(size_t)l * S.E + e] = 1;
+        return;
+    }
+    const float4 pa = S.v[E.x];
+    const double ax = pa.x, ay = pa.y, az = pa.z;
+    const double3 n1 = face_normal_d(S, E.z), n2 = face_normal_d(S, E.w);
+    flags[e] = sgn_d(-(n1.x * ax + n1.y * ay + n1.z * az)) != sgn_d(-(n2.x * ax + n2.y * ay + n2.z * az));
+    const double3 nn[2] = {n1, n2};
+    for (int j = 0; j < S.NL; ++j) {
+        const LightDev& L = S.lights[j];
+        double lo[2], hi[2];
+        for (int q = 0; q < 2; ++q) {
+            const double base = nn[q].x * ((double)L.c.x - ax) + nn[q].y * ((double)L.c.y - ay) + nn[q].z * ((double)L.c.z - az);
+            const double g1 = nn[q].x * L.e1.x + nn[q].y * L.e1.y + nn[q].z * L.e1.z;
+            const double g2 = nn[q].x * L.e2.x + nn[q].y * L.e2.y + nn[q].z * L.e2.z;
+            if (L.type == 0) {
+                const double h = 0.5 * fabs(g1) + 0.5 * fabs(g2);
+                lo[q] = base - h; hi[q] = base + h;
+            } else if (L.type == 1) {
+                lo[q] = base + fmin(0.0, fmin(g1, g2)); hi[q] = base + fmax(0.0, fmax(g1, g2));
+            } else {
+                const double r = sqrt(g1 * g1 + g2 * g2);
+                lo[q] = base - r; hi[q] = base + r;
+            }
+        }
+        const bool pos = lo[0] > 0.0 && lo[1] > 0.0;
+        const bool neg = hi[0] < 0.0 && hi[1] < 0.0;
+        flags[(size_t)(1 + j) * S.E + e] = !(pos || neg);
+    }
+}
+
+// One block per list: ordered compaction of flagged edge ids with warp ballots.
+__global__ void __launch_bounds__(1024) k_compact(int E, const uint8_t* flags, int* lists, int* counts) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int list = blockIdx.x;
+    const uint8_t* fl = flags + (size_t)list * E;
+    int* out = lists + (size_t)list * E;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < E; base += 1024) {
+        const int i = base + threadIdx.x;
+        const bool on = i < E && fl[i];
+        const unsigned b = __ballot_sync(FULL, on);
+        if (lane == 0) warp_tot[wid] = __popc(b);
+        __syncthreads();
+        int before = carry;
+        for (int w2 = 0; w2 < wid; ++w2) before += warp_tot[w2];
+        if (on) out[before + __popc(b & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w2 = 0; w2 < 32; ++w2) tot += warp_tot[w2];
+            carry += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[list] = carry;
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_trace_rays(DevScene S, const float* org, const float* dir, int n,
+                                                           int32_t* tri, float* tout) {
+    __shared__ int stack[FR_STACK * RT_THREADS];
+    const int i = blockIdx.x * RT_THREADS + threadIdx.x;
+    if (i >= n) return;
+    const RayPre r = ray_setup(f3(org[3 * i], org[3 * i + 1], org[3 * i + 2]), f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]));
+    const Hit h = trace_closest(S, r, 0.0f, INFINITY, Stack{&stack[threadIdx.x], RT_THREADS});
+    tri[i] = h.tri;
+    tout[i] = h.tri >= 0 ? h.t : -1.0f;
+}
+
+int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_forward(const DevScene& S, const DevParams& P, float* image, int32_t* tri_rec, uint64_t* mask_rec,
+                    uint32_t iteration, uint32_t face, cudaStream_t st) {
+    const long total = (long)S.W * S.H * S.spp;
+    if (S.spp > 32) cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)S.W * S.H, st);
+    k_forward<<<blocks_for(total, RT_THREADS), RT_THREADS, 0, st>>>(S, P, image, tri_rec, mask_rec, iteration, face);
+}
+
+void launch_adjoint(const DevScene& S, const DevParams& P, const DevGrads& G, const EdgeLists& EL,
+                    const float* adj_image, uint32_t iteration, uint32_t face, cudaStream_t st) {
+    const long total = (long)S.W * S.H * S.spp;
+    k_adjoint<<<blocks_for(total, RT_THREADS), RT_THREADS, 0, st>>>(S, P, G, EL, adj_image, iteration, face);
+}
+
+void launch_edge_primary(const DevScene& S, const DevParams& P, const DevGrads& G, const EdgeLists& EL,
+                         const float* adj_image, uint32_t iteration, uint32_t face, cudaStream_t st) {
+    const long n = (long)S.W * S.H * S.edge_spp;
+    if (n == 0) return;
+    k_edge_primary<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(S, P, G, EL, adj_image, iteration, face);
+}
+
+void launch_classify(const DevScene& S, const EdgeLists& EL, uint8_t* flags, cudaStream_t st) {
+    k_classify<<<blocks_for(S.E, 256), 256, 0, st>>>(S, EL.edges, flags);
+    k_compact<<<1 + S.NL, 1024, 0, st>>>(S.E, flags, EL.prim_list, EL.prim_count);
+}
+
+void launch_trace_rays(const DevScene& S, const float* org, const float* dir, int n, int32_t* tri, float* t,
+                       cudaStream_t st) {
+    if (n <= 0) return;
+    k_trace_rays<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(S, org, dir, n, tri, t);
+}

@@ -1,0 +1,203 @@
+// Ray traversal of the LBVH with a per-thread stack in shared memory, and the
+// watertight ray/triangle test of Woop, Benthin and Wald (JCGT 2013): FP32 edge
+// functions, re-evaluated in FP64 when one of them is exactly zero.
+#pragma once
+#include "common.cuh"
+
+struct RayPre {
+    float3 o, d, inv;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+FR_D RayPre ray_setup(float3 o, float3 d) {
+    RayPre r;
+    r.o = o;
+    r.d = d;
+    const float ex = fabsf(d.x) > 1e-30f ? d.x : copysignf(1e-30f, d.x);
+    const float ey = fabsf(d.y) > 1e-30f ? d.y : copysignf(1e-30f, d.y);
+    const float ez = fabsf(d.z) > 1e-30f ? d.z : copysignf(1e-30f, d.z);
+    r.inv = f3(1.0f / ex, 1.0f / ey, 1.0f / ez);
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    r.kx = r.kz == 2 ? 0 : r.kz + 1;
+    r.ky = r.kx == 2 ? 0 : r.kx + 1;
+    if (comp(d, r.kz) < 0.0f) { int t = r.kx; r.kx = r.ky; r.ky = t; }
+    r.Sz = 1.0f / comp(d, r.kz);
+    r.Sx = comp(d, r.kx) * r.Sz;
+    r.Sy = comp(d, r.ky) * r.Sz;
+    return r;
+}
+
+// Watertight test.  On a hit with tmin < t <= tmax returns true with t and the
+// barycentrics (b1, b2) of v1, v2 (hit = b0 v0 + b1 v1 + b2 v2); both facings
+// are accepted.
+FR_D bool hit_triangle(const RayPre& r, float3 v0, float3 v1, float3 v2, float tmin, float tmax,
+                       float& t, float& b1, float& b2) {
+    const float3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
+    const float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    const float Ax = comp(A, r.kx) - r.Sx * Akz, Ay = comp(A, r.ky) - r.Sy * Akz;
+    const float Bx = comp(B, r.kx) - r.Sx * Bkz, By = comp(B, r.ky) - r.Sy * Bkz;
+    const float Cx = comp(C, r.kx) - r.Sx * Ckz, Cy = comp(C, r.ky) - r.Sy * Ckz;
+    float U = Cx * By - Cy * Bx;
+    float V = Ax * Cy - Ay * Cx;
+    float W = Bx * Ay - By * Ax;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    const float det = U + V + W;
+    if (det == 0.0f) return false;
+    const float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    const float inv = 1.0f / det;
+    t = T * inv;
+    if (!(t > tmin && t <= tmax)) return false;
+    b1 = V * inv;
+    b2 = W * inv;
+    return true;
+}
+
+FR_D bool box_hit(const RayPre& r, float3 lo, float3 hi, float tmin, float tmax, float& tnear) {
+    const float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
+    const float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
+    const float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    tnear = tn;
+    return tn <= tf;
+}
+
+struct Hit {
+    float t, b1, b2;
+    int tri;   // original triangle index, -1 on a miss
+};
+
+FR_D void load_node(const BvhNode* nodes, int i, float3& lo0, float3& hi0, float3& lo1, float3& hi1,
+                    int& c0, int& c1) {
+    const float4 a = __ldg(&nodes[i].a), b = __ldg(&nodes[i].b), c = __ldg(&nodes[i].c);
+    const int4 d = __ldg(&nodes[i].d);
+    lo0 = f3(a.x, a.y, a.z);
+    hi0 = f3(a.w, b.x, b.y);
+    lo1 = f3(b.z, b.w, c.x);
+    hi1 = f3(c.y, c.z, c.w);
+    c0 = d.x;
+    c1 = d.y;
+}
+
+// stack: this thread's column of a [FR_STACK][blockDim] shared array.
+struct Stack {
+    int* base;
+    int stride;
+    FR_D void put(int i, int v) { base[i * stride] = v; }
+    FR_D int get(int i) const { return base[i * stride]; }
+};
+
+// Closest hit in (tmin, tmax); ties on t go to the lower triangle index.
+FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tmax, Stack st) {
+    Hit h;
+    h.t = tmax;
+    h.tri = -1;
+    h.b1 = h.b2 = 0.0f;
+    int sp = 0;
+    int node = 0;
+    // a valid tree visits each of its 2T - 1 nodes at most once per ray
+    for (int guard = 2 * s.T + 8; guard > 0; --guard) {
+        float3 lo0, hi0, lo1, hi1;
+        int c0, c1;
+        load_node(s.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
+        float tn0, tn1;
+        bool h0 = box_hit(r, lo0, hi0, tmin, h.t, tn0);
+        bool h1 = box_hit(r, lo1, hi1, tmin, h.t, tn1);
+        // leaves are single triangles: test them right away
+        if (h0 && c0 < 0) {
+            const int slot = ~c0;
+            const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+            float t, b1, b2;
+            const int id = __float_as_int(a.w);
+            if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
+                (t < h.t || id < h.tri || h.tri < 0)) {
+                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
+            }
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            const int slot = ~c1;
+            const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+            float t, b1, b2;
+            const int id = __float_as_int(a.w);
+            if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
+                (t < h.t || id < h.tri || h.tri < 0)) {
+                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
+            }
+            h1 = false;
+        }
+        if (h0 && tn0 > h.t) h0 = false;
+        if (h1 && tn1 > h.t) h1 = false;
+        if (h0 && h1) {
+            int near = c0, far = c1;
+            if (tn1 < tn0) { near = c1; far = c0; }
+            if (sp >= FR_STACK) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return h; }
+            st.put(sp++, far);
+            node = near;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
+            if (sp == 0) return h;
+            node = st.get(--sp);
+        }
+    }
+    set_status(s.status, FR_STATUS_BAD_BVH);
+    return h;
+}
+
+// Any hit in (tmin, tmax), skipping triangle `skip` (shadow rays).
+FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, int skip, Stack st) {
+    int sp = 0;
+    int node = 0;
+    for (int guard = 2 * s.T + 8; guard > 0; --guard) {
+        float3 lo0, hi0, lo1, hi1;
+        int c0, c1;
+        load_node(s.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
+        float tn0, tn1;
+        bool h0 = box_hit(r, lo0, hi0, tmin, tmax, tn0);
+        bool h1 = box_hit(r, lo1, hi1, tmin, tmax, tn1);
+        if (h0 && c0 < 0) {
+            const int slot = ~c0;
+            const float4 a = __ldg(&s.tris[3 * slot]);
+            if (__float_as_int(a.w) != skip) {
+                const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+                float t, b1, b2;
+                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
+            }
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            const int slot = ~c1;
+            const float4 a = __ldg(&s.tris[3 * slot]);
+            if (__float_as_int(a.w) != skip) {
+                const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+                float t, b1, b2;
+                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
+            }
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp >= FR_STACK) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return false; }
+            st.put(sp++, c1);
+            node = c0;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
+            if (sp == 0) return false;
+            node = st.get(--sp);
+        }
+    }
+    set_status(s.status, FR_STATUS_BAD_BVH);
+    return false;
+}

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libfacert.so (include/facert.h), same call names.
+
+Only argument marshalling lives here: every step of the render, the loss and
+the adjoint runs in the library's CUDA kernels.  PyTorch provides device memory
+and the current stream.  Importing this module does not need a GPU; loading the
+library fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfacert.so")
+
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EOVERFLOW, FR_ETIMEOUT = 0, 1, 2, 3, 4, 5
+FLAG_GGX, FLAG_SCHLICK_LINEAR, FLAG_FLAT = 1, 2, 4
+FLAG_NO_INTERIOR, FLAG_NO_PRIMARY_EDGE, FLAG_NO_SHADOW_EDGE = 16, 32, 64
+
+_vp = ctypes.c_void_p
+
+
+class FrConfig(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("spp", ctypes.c_int32),
+                ("tex_size", ctypes.c_int32), ("edge_spp", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint32)]
+
+
+class FrMesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32),
+                ("n_basis", ctypes.c_int32), ("mean", _vp), ("basis", _vp), ("faces", _vp),
+                ("uv", _vp)]
+
+
+class FrLightStage(ctypes.Structure):
+    _fields_ = [("n_lights", ctypes.c_int32), ("records", _vp), ("d", _vp), ("a", _vp)]
+
+
+PARAM_NAMES = ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness")
+
+
+class FrParams(ctypes.Structure):
+    _fields_ = [(n, _vp) for n in PARAM_NAMES]
+
+
+class FrGrads(ctypes.Structure):
+    _fields_ = [(n, _vp) for n in PARAM_NAMES]
+
+
+class FacertError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("facert error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libfacert.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfacert.so is missing: build it with __graft_entry__.build() "
+                               "(nvcc for sm_103a); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.fr_create.argtypes = [P(_vp), P(FrConfig)]
+        L.fr_set_mesh.argtypes = [_vp, P(FrMesh)]
+        L.fr_set_lights.argtypes = [_vp, P(FrLightStage)]
+        L.fr_forward.argtypes = [_vp, P(FrParams), _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]
+        L.fr_backward.argtypes = [_vp, P(FrParams), _vp, P(FrGrads), ctypes.c_uint32, ctypes.c_uint32, _vp]
+        L.fr_loss.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.fr_render.argtypes = [_vp, P(FrParams), _vp, _vp, _vp, P(FrGrads), ctypes.c_uint32,
+                                ctypes.c_uint32, _vp]
+        L.fr_sync_status.argtypes = [_vp, _vp]
+        L.fr_last_error.argtypes = [_vp]
+        L.fr_last_error.restype = ctypes.c_char_p
+        L.fr_destroy.argtypes = [_vp]
+        L.fr_destroy.restype = None
+        L.fr_philox.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _vp, ctypes.c_int32, _vp, _vp]
+        L.fr_debug_geometry.argtypes = [_vp, P(FrParams), _vp, _vp, _vp]
+        L.fr_debug_trace.argtypes = [_vp, P(FrParams), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]
+        L.fr_debug_records.argtypes = [_vp, P(FrParams), _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]
+        L.fr_debug_silhouettes.argtypes = [_vp, P(FrParams), _vp, _vp, _vp, _vp, _vp]
+        L.fr_debug_bvh.argtypes = [_vp, P(FrParams), _vp, _vp]
+        L.fr_num_edges.argtypes = [_vp]
+        L.fr_num_edges.restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def check(code, ctx=None):
+    if code != FR_OK:
+        msg = lib().fr_last_error(ctx)
+        raise FacertError(code, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ---- same-named wrappers -------------------------------------------------
+
+def fr_create(width, height, spp, tex_size, edge_spp=1, flags=0, seed=0):
+    h = ctypes.c_void_p()
+    cfg = FrConfig(width, height, spp, tex_size, edge_spp, flags, seed)
+    check(lib().fr_create(ctypes.byref(h), ctypes.byref(cfg)))
+    return h
+
+
+def fr_set_mesh(ctx, mean, basis, faces, uv):
+    mean = np.ascontiguousarray(mean, np.float32)
+    basis = np.ascontiguousarray(basis, np.float32)
+    faces = np.ascontiguousarray(faces, np.int32)
+    uv = np.ascontiguousarray(uv, np.float32)
+    m = FrMesh(mean.shape[0], faces.shape[0], basis.shape[0], mean.ctypes.data, basis.ctypes.data,
+               faces.ctypes.data, uv.ctypes.data)
+    check(lib().fr_set_mesh(ctx, ctypes.byref(m)), ctx)
+
+
+def fr_set_lights(ctx, records, d, a):
+    records = np.ascontiguousarray(records, np.float32)
+    d = np.ascontiguousarray(d, np.float32)
+    a = np.ascontiguousarray(a, np.float32)
+    ls = FrLightStage(records.shape[0], records.ctypes.data, d.ctypes.data, a.ctypes.data)
+    check(lib().fr_set_lights(ctx, ctypes.byref(ls)), ctx)
+
+
+def _params(p):
+    return FrParams(*[_ptr(p.get(n)) for n in PARAM_NAMES])
+
+
+def _grads(g):
+    return FrGrads(*[_ptr(g.get(n)) for n in PARAM_NAMES])
+
+
+def fr_forward(ctx, params, image, iteration=0, face_id=0):
+    pp = _params(params)
+    check(lib().fr_forward(ctx, ctypes.byref(pp), _ptr(image), iteration, face_id, _stream()), ctx)
+
+
+def fr_backward(ctx, params, adj_image, grads, iteration=0, face_id=0):
+    pp, gg = _params(params), _grads(grads)
+    check(lib().fr_backward(ctx, ctypes.byref(pp), _ptr(adj_image), ctypes.byref(gg), iteration, face_id,
+                            _stream()), ctx)
+
+
+def fr_loss(ctx, image, target, loss, adj_image=None, blurred=None):
+    check(lib().fr_loss(ctx, _ptr(image), _ptr(target), _ptr(loss), _ptr(adj_image), _ptr(blurred),
+                        _stream()), ctx)
+
+
+def fr_render(ctx, params, target, image, loss, grads=None, iteration=0, face_id=0):
+    pp = _params(params)
+    gg = _grads(grads) if grads is not None else None
+    check(lib().fr_render(ctx, ctypes.byref(pp), _ptr(target), _ptr(image), _ptr(loss),
+                          ctypes.byref(gg) if gg is not None else None, iteration, face_id, _stream()), ctx)
+
+
+def fr_sync_status(ctx):
+    return lib().fr_sync_status(ctx, _stream())
+
+
+def fr_destroy(ctx):
+    lib().fr_destroy(ctx)
+
+
+def fr_philox(k0, k1, counters, out):
+    check(lib().fr_philox(k0, k1, _ptr(counters), counters.shape[0], _ptr(out), _stream()))
+
+
+def fr_debug_geometry(ctx, params, v_cam, n_vert):
+    pp = _params(params)
+    check(lib().fr_debug_geometry(ctx, ctypes.byref(pp), _ptr(v_cam), _ptr(n_vert), _stream()), ctx)
+
+
+def fr_debug_trace(ctx, params, org, dirs, tri, t):
+    pp = _params(params)
+    check(lib().fr_debug_trace(ctx, ctypes.byref(pp), _ptr(org), _ptr(dirs), org.shape[0], _ptr(tri), _ptr(t),
+                               _stream()), ctx)
+
+
+def fr_debug_records(ctx, params, image, tri_rec, mask_rec, iteration=0, face_id=0):
+    pp = _params(params)
+    check(lib().fr_debug_records(ctx, ctypes.byref(pp), _ptr(image), _ptr(tri_rec), _ptr(mask_rec), iteration,
+                                 face_id, _stream()), ctx)
+
+
+def fr_debug_silhouettes(ctx, params, prim, n_prim, per_light, counts):
+    pp = _params(params)
+    check(lib().fr_debug_silhouettes(ctx, ctypes.byref(pp), _ptr(prim), _ptr(n_prim), _ptr(per_light),
+                                     _ptr(counts), _stream()), ctx)
+
+
+def fr_debug_bvh(ctx, params, out):
+    pp = _params(params)
+    check(lib().fr_debug_bvh(ctx, ctypes.byref(pp), _ptr(out), _stream()), ctx)
+
+
+def fr_num_edges(ctx):
+    return int(lib().fr_num_edges(ctx))
+
+
+# ---- convenience: one context bound to a synthetic scene ------------------
+
+class Renderer:
+    """A library context for one scene (mesh, light stage, image config),
+    with torch device buffers for parameters, images and gradients."""
+
+    def __init__(self, scene, edge_spp=1, flags=0, seed=0):
+        import torch
+        self.torch = torch
+        self.scene = scene
+        self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed)
+        fr_set_mesh(self.ctx, scene.mean, scene.basis, scene.faces, scene.uv)
+        fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a)
+        self.n_edges = fr_num_edges(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            fr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_params(self, params):
+        t = self.torch
+        return {n: t.as_tensor(np.ascontiguousarray(getattr(params, n), np.float32)).cuda()
+                for n in PARAM_NAMES}
+
+    def zero_grads(self, dparams):
+        return {n: self.torch.zeros_like(v) for n, v in dparams.items()}
+
+    def image_buffer(self):
+        s = self.scene
+        return self.torch.zeros((s.height, s.width, 3), dtype=self.torch.float32, device="cuda")
+
+    def forward(self, dparams, iteration=0, face_id=0):
+        img = self.image_buffer()
+        fr_forward(self.ctx, dparams, img, iteration, face_id)
+        return img
+
+    def backward(self, dparams, adj_image, iteration=0, face_id=0, grads=None):
+        g = self.zero_grads(dparams) if grads is None else grads
+        fr_backward(self.ctx, dparams, adj_image.contiguous(), g, iteration, face_id)
+        return g
+
+    def loss(self, image, target):
+        t = self.torch
+        loss = t.zeros(1, dtype=t.float64, device="cuda")
+        adj = t.empty_like(image)
+        bl = t.empty_like(image)
+        fr_loss(self.ctx, image, target, loss, adj, bl)
+        return loss, adj, bl
+
+    def render(self, dparams, target, iteration=0, face_id=0, grads=None, with_grad=True):
+        t = self.torch
+        img = self.image_buffer()
+        loss = t.zeros(1, dtype=t.float64, device="cuda")
+        g = (self.zero_grads(dparams) if grads is None else grads) if with_grad else None
+        fr_render(self.ctx, dparams, target, img, loss, g, iteration, face_id)
+        return img, loss, g
+
+    def records(self, dparams, iteration=0, face_id=0):
+        t = self.torch
+        s = self.scene
+        n = s.width * s.height * s.spp
+        img = self.image_buffer()
+        tri = t.empty(n, dtype=t.int32, device="cuda")
+        mask = t.empty(n, dtype=t.int64, device="cuda")
+        fr_debug_records(self.ctx, dparams, img, tri, mask, iteration, face_id)
+        return img, tri, mask
+
+    def status(self):
+        return fr_sync_status(self.ctx)

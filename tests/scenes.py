@@ -35,3 +35,31 @@ def quad_light(c, e1, e2, kind=synth.LIGHT_QUAD):
 
 
 FAR_TRIANGLE = [[100.0, 100.0, 100.0], [101.0, 100.0, 100.0], [100.0, 101.0, 100.0]]
+
+
+def shadow_box(width=32, height=32, spp=4, tex=8, seed=0):
+    """Floor at z = -4 facing the camera, an occluding triangle above it and two
+    emitters (a quad and a disk) between the occluder and the camera, so that
+    soft shadows and their boundaries cover much of the image.  Model space is
+    camera space (rot = 0, T = 0); the basis moves occluder and floor vertices."""
+    verts = [[-1.6, -1.6, -4.0], [1.6, -1.6, -4.0], [1.6, 1.6, -4.0], [-1.6, 1.6, -4.0],
+             [-0.35, -0.25, -3.1], [0.55, 0.05, -3.2], [0.0, 0.6, -3.05]]
+    faces = [[0, 1, 2], [0, 2, 3], [4, 5, 6]]
+    basis = np.zeros((4, 7, 3))
+    basis[0, 4, 0] = 1.0
+    basis[1, 5, 1] = 1.0
+    basis[2, 6, 2] = 1.0
+    basis[3, 2, 0] = 0.5
+    basis[3, 2, 1] = 0.5
+    lights = [quad_light([0.3, 0.2, -1.6], [0.9, 0.0, 0.0], [0.0, -0.9, 0.0]),
+              quad_light([-0.4, -0.3, -1.9], [0.0, 0.35, 0.0], [0.35, 0.0, 0.0], synth.LIGHT_DISK)]
+    rng = np.random.default_rng(seed)
+    sc, pr = make(verts, faces, basis, lights, width=width, height=height, spp=spp, tex=tex,
+                  light_i=[(2.0, 1.6, 1.2), (1.0, 1.4, 1.8)])
+    sc.uv = rng.uniform(0.05, 0.95, size=(7, 2)).astype(np.float32)
+    pr.focal = np.array([float(width)], np.float32)
+    pr.diffuse = rng.uniform(0.2, 0.8, size=(tex, tex, 3)).astype(np.float32)
+    pr.specular = np.full((tex, tex, 3), 0.05, np.float32)
+    pr.roughness = rng.uniform(0.3, 0.6, size=(tex, tex)).astype(np.float32)
+    pr.coef = np.array([0.02, -0.03, 0.01, 0.05], np.float32)
+    return sc, pr
