@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Throughput of the differentiable ray-traced face render on GB300.
+
+One step = one pass of the hot path over one face: morph, pose + normals, LBVH
+build, camera + shadow rays with Cook-Torrance shading, blur + L1 loss, and the
+adjoint (re-trace, interior term, shadow-boundary and primary-edge terms, chain
+to the parameters).  Workload: the paper-scale single face (35,709 vertices /
+70,789 triangles, K = 80 + 64 bases, 256 x 256, 16 spp, 40 quad lights, 512^2
+textures), synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line.  `value` is rays traced per second over the timed steps
+(inputs resident in HBM, L2 flushed between steps); `e2e` is the same metric
+with host buffers copied in and the loss copied out inside the timed region.
+The reference arm times the FP64 CPU oracle on a bounded sample of the same
+workload.  Under torchrun each rank renders an independent face (replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/s fwd+adjoint"
+WORKLOAD = ("paper-scale single face: 35,709 verts / 70,789 tris, K=80+64, 256x256, 16 spp, "
+            "40 quad lights, 512^2 textures, 1 primary-edge sample/pixel")
+# ALU work per traversal step (algorithmic op counts, FP32 lane operations):
+# a node visit tests two child boxes (2 x (6 FMA slab + 10 min/max/compare)),
+# a Woop triangle test is ~30 operations (shear 6, edge functions 6, det 2,
+# distance 3, compares and the reciprocal ~13).
+OPS_PER_NODE = 32
+OPS_PER_TRI = 30
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(face_seed):
+    from paper_2101_05356_gb300 import synth
+    sc = synth.make_scene("c2")
+    target_params = synth.random_params(sc, 100 + face_seed)
+    params = synth.init_params(sc)
+    return sc, params, target_params
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2101_05356_gb300 import facert
+
+    dev = rank % max(torch.cuda.device_count(), 1)
+    torch.cuda.set_device(dev)
+    sc, params, tparams = make_workload(rank)
+    r = facert.Renderer(sc, edge_spp=1, seed=rank)
+    dp = r.device_params(params)
+    dt = r.device_params(tparams)
+    # synthetic target: the renderer's own image of the ground-truth parameters + noise
+    tgt = r.forward(dt, iteration=10 ** 6)
+    tgt = (tgt + torch.as_tensor(np.random.default_rng(7 + rank).normal(0, 0.01, tuple(tgt.shape)),
+                                 dtype=torch.float32, device="cuda")).contiguous()
+    grads = r.zero_grads(dp)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(it):
+        for g in grads.values():
+            g.zero_()
+        img, loss, _ = r.render(dp, tgt, iteration=it, face_id=rank, grads=grads)
+        return loss
+
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+    if r.status() != 0:
+        raise RuntimeError("device status error during warm-up")
+
+    # ---- device-resident timed region ----
+    facert.fr_counters(r.ctx, reset=True)
+    facert.fr_set_timing(r.ctx, True)
+    launches0 = facert.fr_kernel_launches()
+    clocks = ClockSampler(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, stage = [], []
+    for k in range(args.steps):
+        flush.zero_()                                   # L2 flush outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + k)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stage.append(facert.fr_get_timing(r.ctx))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = facert.fr_kernel_launches() - launches0 - 0
+    facert.fr_set_timing(r.ctx, False)
+    cnt = facert.fr_counters(r.ctx, reset=True)
+    status = r.status()
+    total_ms = float(np.sum(times))
+    rays = sum(v["rays"] for v in cnt.values())
+    if world > 1:
+        t = torch.tensor([total_ms, float(rays)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, rays_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_max, rays_all = total_ms, float(rays)
+    value = rays_all / (total_ms_max / 1000.0)
+
+    # ---- dominant kernel roofline (adjoint re-trace kernel) ----
+    pk, src = peaks()
+    adj_ms = float(np.mean([s["adjoint"] for s in stage]))
+    fwd_ms = float(np.mean([s["forward"] for s in stage]))
+    edge_ms = float(np.mean([s["edge_primary"] for s in stage]))
+    dom = "adjoint" if adj_ms >= max(fwd_ms, edge_ms) else ("forward" if fwd_ms >= edge_ms else "edge_primary")
+    dom_ms = {"adjoint": adj_ms, "forward": fwd_ms, "edge_primary": edge_ms}[dom]
+    c = cnt[dom]
+    ops_per_launch = (c["nodes"] * OPS_PER_NODE + c["tris"] * OPS_PER_TRI) / args.steps
+    peak_ops = SMS * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    achieved = ops_per_launch / (dom_ms / 1000.0)
+    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz (%s clocks)"
+                               % (SMS, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src),
+                "ops_per_launch": ops_per_launch, "launch_ms": dom_ms}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {n: torch.as_tensor(np.ascontiguousarray(getattr(params, n), np.float32)).pin_memory()
+                for n in facert.PARAM_NAMES}
+        host_tgt = tgt.cpu().pin_memory()
+        host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * 4 for t in host.values()) + host_tgt.numel() * 4
+        d2h = 8
+        facert.fr_counters(r.ctx, reset=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for k in range(args.e2e_steps):
+            flush.zero_()
+            e0.record(stream)
+            for n in facert.PARAM_NAMES:
+                dp[n].copy_(host[n], non_blocking=True)
+            tgt.copy_(host_tgt, non_blocking=True)
+            loss = step(10 ** 5 + k)
+            host_loss.copy_(loss, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        cnt2 = facert.fr_counters(r.ctx, reset=True)
+        rays2 = sum(v["rays"] for v in cnt2.values())
+        e2e = {"value": rays2 / (ms / 1000.0), "unit": "rays/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+    out = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "rays_per_step": rays / args.steps,
+                   "stage_ms": {k: float(np.mean([s[k] for s in stage])) for k in stage[0]}},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
+        "status": int(status),
+    }
+    return out
+
+
+def cpu_baseline(sample_pixels, threads=0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload:
+    forward + adjoint (all terms) restricted to `sample_pixels` random pixels."""
+    import oracle
+    sc, params, tparams = make_workload(0)
+    rng = np.random.default_rng(1)
+    npx = sc.width * sc.height
+    pix = np.sort(rng.choice(npx, size=sample_pixels, replace=False)).astype(np.int32)
+    adj = np.zeros((sc.height, sc.width, 3))
+    adj.reshape(-1, 3)[pix] = rng.uniform(0.2, 1.0, (sample_pixels, 3))
+    cores = threads or len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.build()
+    oracle.ray_count(reset=True)
+    t0 = time.perf_counter()
+    oracle.render(sc, params, pixels=pix, n_threads=cores)
+    oracle.grad(sc, params, adj, n_threads=cores, edge_spp=1)
+    dt = time.perf_counter() - t0
+    rays = oracle.ray_count(reset=True)
+    return {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d pixels of the workload (16 spp, 40 lights), forward + adjoint with all "
+                      "edge terms; %d rays in %.1f s" % (sample_pixels, npx, rays, dt),
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-pixels", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per = []
+        for k in range(args.warmup + args.steps):
+            b = cpu_baseline(max(4, args.cpu_pixels // 4))
+            if k >= args.warmup:
+                per.append(b)
+        v = float(np.mean([b["value"] for b in per]))
+        out = {"metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean([b["seconds"] for b in per])),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "impl": "reference",
+               "config": {"workload": WORKLOAD},
+               "cpu_baseline": {"value": v, "unit": "rays/s", "cores": per[0]["cores"], "kind": "oracle",
+                                "sample": per[0]["sample"]},
+               "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = gpu_arm(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.cpu_pixels).items() if k != "seconds"}
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

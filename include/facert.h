@@ -199,6 +199,25 @@ fr_status fr_debug_bvh(fr_ctx* ctx, const fr_params* p, int32_t* out, void* stre
 /* Edge count E of the mesh set on ctx (host int). */
 int32_t fr_num_edges(const fr_ctx* ctx);
 
+/* ---- measurement ---- */
+
+/* Traversal work accumulated on ctx since the last reset, per kernel: out[3k+0]
+ * rays traced, out[3k+1] BVH nodes visited, out[3k+2] ray/triangle tests, for
+ * k = 0 forward, 1 adjoint (re-trace + shadow-boundary rays), 2 primary-edge
+ * rays (host uint64[9]).  Synchronises `stream`; reset != 0 zeroes them. */
+fr_status fr_counters(fr_ctx* ctx, uint64_t* out, int32_t reset, void* stream);
+
+/* Enable (on != 0) CUDA-event marks between the stages of fr_render. */
+fr_status fr_set_timing(fr_ctx* ctx, int32_t on);
+
+/* Milliseconds of the stages of the last timed fr_render (synchronises):
+ * out[8] = {geometry+LBVH, forward, loss, classify, adjoint, primary edges,
+ * chain to parameters, total}. */
+fr_status fr_get_timing(fr_ctx* ctx, float* out);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t fr_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

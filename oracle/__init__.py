@@ -69,6 +69,8 @@ def lib():
         build()
         L = ctypes.CDLL(LIB)
         L.ora_philox.argtypes = [ctypes.c_uint32] * 6 + [u32p]
+        L.ora_ray_count.argtypes = [ctypes.c_int]
+        L.ora_ray_count.restype = ctypes.c_ulonglong
         L.ora_geometry.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams), f64p, f64p]
         L.ora_edges.argtypes = [ctypes.POINTER(OraScene), i32p, i32p]
         L.ora_silhouettes.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams),
@@ -123,6 +125,11 @@ class _Bound:
             self.params = OraParams(f(params.coef), f(params.rot), f(params.trans),
                                     f(params.focal), f(params.light_i), f(params.diffuse),
                                     f(params.specular), f(params.roughness))
+
+
+def ray_count(reset=False):
+    """Rays (camera, shadow and edge) traced by the oracle since the last reset."""
+    return int(lib().ora_ray_count(1 if reset else 0))
 
 
 def philox(k0, k1, c0, c1, c2, c3):

@@ -36,6 +36,7 @@
 #include "oracle.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -401,6 +402,8 @@ void classify(Prep& P) {
     }
 }
 
+std::atomic<unsigned long long> g_rays{0};   // rays traced (for throughput reports)
+
 // ---------------------------------------------------------------------------
 // Ray/triangle intersection (Moller-Trumbore), FP64, two-sided.
 // ---------------------------------------------------------------------------
@@ -422,6 +425,7 @@ bool intersect(P3 o, P3 d, P3 v0, P3 v1, P3 v2, double& t, double& b1, double& b
 
 // Closest hit over every triangle (brute force); ties -> lower triangle index.
 int closest_hit(const Prep& P, P3 o, P3 d, double& t_hit) {
+    g_rays.fetch_add(1, std::memory_order_relaxed);
     int best = -1;
     double bt = INFINITY;
     for (int f = 0; f < P.T; ++f) {
@@ -439,6 +443,7 @@ int closest_hit(const Prep& P, P3 o, P3 d, double& t_hit) {
 // Shadow ray y -> z: occluded if any triangle other than `skip` crosses the
 // segment at 1e-4 < t < 1 - 1e-4 (direction z - y, not normalised).
 bool occluded(const Prep& P, P3 y, P3 z, int skip) {
+    g_rays.fetch_add(1, std::memory_order_relaxed);
     P3 d = z - y;
     for (int f = 0; f < P.T; ++f) {
         if (f == skip) continue;
@@ -759,6 +764,12 @@ void gauss3(double w[3][3]) {
 // C API
 // ===========================================================================
 extern "C" {
+
+unsigned long long ora_ray_count(int reset) {
+    unsigned long long v = g_rays.load();
+    if (reset) g_rays.store(0);
+    return v;
+}
 
 void ora_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                 uint32_t out[4]) {

@@ -45,6 +45,9 @@ typedef struct OraParams {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
 } OraParams;
 
+/* rays traced by this library since the last reset (closest-hit + shadow) */
+unsigned long long ora_ray_count(int reset);
+
 void ora_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                 uint32_t c3, uint32_t out[4]);
 

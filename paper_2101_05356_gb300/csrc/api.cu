@@ -1,6 +1,7 @@
 // C-ABI of the facert library: context and scratch ownership, argument checks
 // and the orchestration of the hot path (include/facert.h documents each call).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -47,8 +48,15 @@ struct fr_ctx {
     float* sign = nullptr;
     float* adj_image = nullptr;
     int* status = nullptr;
+    unsigned long long* counters = nullptr;   // [kernel][rays, nodes, triangle tests]
+    // per-stage CUDA-event timing
+    bool timing = false;
+    cudaEvent_t ev[9] = {};
     std::vector<void*> owned;
 };
+
+static std::atomic<unsigned long long> g_launches{0};
+void fr_count_launches(int n) { g_launches += (unsigned long long)n; }
 
 namespace {
 
@@ -89,6 +97,12 @@ void free_all(fr_ctx* c) {
 
 cudaStream_t S_(void* s) { return static_cast<cudaStream_t>(s); }
 
+// stage marks: 0 start, 1 after build, 2 after forward, 3 after loss,
+// 4 after classify, 5 after adjoint, 6 after edge_primary, 7 after chain
+void mark(fr_ctx* c, int k, cudaStream_t st) {
+    if (c->timing) cudaEventRecord(c->ev[k], st);
+}
+
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 fr_status check_params(fr_ctx* c, const fr_params* p) {
@@ -107,7 +121,7 @@ DevScene scene_of(const fr_ctx* c) {
     s.edge_spp = c->cfg.edge_spp;
     s.flags = c->cfg.flags; s.seed = c->cfg.seed;
     s.v = c->v_cam; s.vn = c->vn; s.uv = c->uv; s.faces = c->faces; s.nodes = c->nodes; s.tris = c->tris;
-    s.lights = c->lights; s.status = c->status;
+    s.lights = c->lights; s.status = c->status; s.counters = c->counters;
     return s;
 }
 
@@ -149,6 +163,7 @@ fr_status adjoint_pass(fr_ctx* c, const fr_params* p, const float* adj_image, fr
     CK(c, cudaMemsetAsync(c->acc12, 0, sizeof(double) * 12, st));
     const bool need_edges = !(c->cfg.flags & FR_FLAG_NO_PRIMARY_EDGE) || !(c->cfg.flags & FR_FLAG_NO_SHADOW_EDGE);
     if (need_edges) launch_classify(S, EL, c->sil_flags, st);
+    mark(c, 4, st);
     DevGrads G;
     G.d_v = c->d_v;
     G.d_n = c->d_n;
@@ -157,12 +172,15 @@ fr_status adjoint_pass(fr_ctx* c, const fr_params* p, const float* adj_image, fr
     G.roughness = g->roughness;
     G.small = c->small;
     launch_adjoint(S, P, G, EL, adj_image, iteration, face, st);
+    mark(c, 5, st);
     if (!(c->cfg.flags & FR_FLAG_NO_PRIMARY_EDGE) && c->cfg.edge_spp > 0)
         launch_edge_primary(S, P, G, EL, adj_image, iteration, face, st);
+    mark(c, 6, st);
     launch_normals_adjoint(c->v_cam, c->vn, c->d_n, c->faces, c->vf_off, c->vf_idx, c->N, c->dm, c->d_v, st);
     launch_pose_adjoint(c->v_model, c->N, c->ld, p->rot, p->trans, c->d_v, c->d_vmodel, c->acc12, st);
     launch_pose_finish(p->rot, c->acc12, c->small, c->NL, g->rot, g->trans, g->focal, g->light_i, st);
     if (g->coef) launch_morph_adjoint(c->basis, c->ld, c->K, 3 * c->N, c->d_vmodel, g->coef, st);
+    mark(c, 7, st);
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -219,7 +237,9 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
         return fail(nullptr, FR_EINVAL, "too many samples per call");
     fr_ctx* c = new fr_ctx();
     c->cfg = *cfg;
-    if (dalloc(c, &c->status, 1) != FR_OK || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+    if (dalloc(c, &c->status, 1) != FR_OK || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+        dalloc(c, &c->counters, 9) != FR_OK ||
+        cudaMemset(c->counters, 0, 9 * sizeof(unsigned long long)) != cudaSuccess) {
         g_err = c->err;
         free_all(c);
         delete c;
@@ -359,9 +379,13 @@ fr_status fr_render(fr_ctx* c, const fr_params* p, const float* target, float* i
     TRY(check_params(c, p));
     if (!image || !target || !loss) return fail(c, FR_EINVAL, "null argument");
     const cudaStream_t st = S_(stream);
+    mark(c, 0, st);
     TRY(build_geometry(c, p, st));
+    mark(c, 1, st);
     launch_forward(scene_of(c), params_of(p), image, nullptr, nullptr, iteration, face_id, st);
+    mark(c, 2, st);
     launch_loss(c->cfg.height, c->cfg.width, image, target, loss, c->sign, nullptr, g ? c->adj_image : nullptr, st);
+    mark(c, 3, st);
     CK(c, cudaGetLastError());
     if (g) return adjoint_pass(c, p, c->adj_image, g, iteration, face_id, st);
     return FR_OK;
@@ -384,6 +408,8 @@ const char* fr_last_error(const fr_ctx* c) { return c ? c->err.c_str() : g_err.c
 void fr_destroy(fr_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();
+    for (cudaEvent_t& e : c->ev)
+        if (e) cudaEventDestroy(e);
     free_all(c);
     delete c;
 }
@@ -453,5 +479,34 @@ fr_status fr_debug_bvh(fr_ctx* c, const fr_params* p, int32_t* out, void* stream
 }
 
 int32_t fr_num_edges(const fr_ctx* c) { return c ? c->E : 0; }
+
+fr_status fr_counters(fr_ctx* c, uint64_t* out, int32_t reset, void* stream) {
+    if (!c || !out) return fail(c, FR_EINVAL, "null argument");
+    CK(c, cudaStreamSynchronize(S_(stream)));
+    unsigned long long h[9];
+    CK(c, cudaMemcpy(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 9; ++k) out[k] = h[k];
+    if (reset) CK(c, cudaMemset(c->counters, 0, sizeof(h)));
+    return FR_OK;
+}
+
+fr_status fr_set_timing(fr_ctx* c, int32_t on) {
+    if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (on && !c->ev[0])
+        for (cudaEvent_t& e : c->ev) CK(c, cudaEventCreate(&e));
+    c->timing = on != 0;
+    return FR_OK;
+}
+
+fr_status fr_get_timing(fr_ctx* c, float* out) {
+    if (!c || !out) return fail(c, FR_EINVAL, "null argument");
+    if (!c->ev[0]) return fail(c, FR_EINVAL, "timing was never enabled");
+    CK(c, cudaEventSynchronize(c->ev[7]));
+    for (int k = 0; k < 7; ++k) CK(c, cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]));
+    CK(c, cudaEventElapsedTime(&out[7], c->ev[0], c->ev[7]));
+    return FR_OK;
+}
+
+uint64_t fr_kernel_launches(void) { return g_launches.load(); }
 
 }  // extern "C"

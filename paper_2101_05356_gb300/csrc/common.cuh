@@ -98,7 +98,27 @@ struct DevScene {
     const float4* tris;     // [3T] triangles in BVH leaf order; tris[3s].w = id bits
     const LightDev* lights; // [NL]
     int* status;
+    unsigned long long* counters;   // [3][3]: per kernel (forward, adjoint, primary edges) rays, nodes, triangle tests
 };
+
+// Per-thread traversal work, flushed once per warp at the end of a kernel.
+struct RayStats {
+    uint32_t rays = 0, nodes = 0, tris = 0;
+};
+
+FR_D void flush_stats(unsigned long long* counters, const RayStats& rs) {
+    unsigned long long v[3] = {rs.rays, rs.nodes, rs.tris};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if ((threadIdx.x & 31) == 0 && v[0]) {
+        atomicAdd(&counters[0], v[0]);
+        atomicAdd(&counters[1], v[1]);
+        atomicAdd(&counters[2], v[2]);
+    }
+}
 
 struct DevParams {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;

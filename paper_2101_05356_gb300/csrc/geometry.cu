@@ -285,22 +285,26 @@ void launch_morph(const float* mean, const float* basis, int ld, int K, const fl
     const int ld4 = ld / 4;
     k_morph<<<nb(ld4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), basis, ld4, K, coef,
                                           reinterpret_cast<float4*>(v_model));
+    fr_count_launches(1);
 }
 
 void launch_pose(const float* v_model, int N, const float* rot, const float* trans, float4* v_cam,
                  unsigned* aabb, cudaStream_t st) {
     k_aabb_reset<<<1, 32, 0, st>>>(aabb);
     k_pose<<<nb(N, 256), 256, 0, st>>>(v_model, N, rot, trans, v_cam, aabb);
+    fr_count_launches(2);
 }
 
 void launch_faces(const float4* v_cam, const int4* faces, int T, const unsigned* aabb, float4* n_face,
                   uint32_t* keys, int* vals, cudaStream_t st) {
     k_faces<<<nb(T, 256), 256, 0, st>>>(v_cam, faces, T, aabb, n_face, keys, vals);
+    fr_count_launches(1);
 }
 
 void launch_vertex_normals(const float4* n_face, const int* vf_off, const int* vf_idx, int N, float4* vn,
                            cudaStream_t st) {
     k_vertex_normals<<<nb(N, 256), 256, 0, st>>>(n_face, vf_off, vf_idx, N, vn);
+    fr_count_launches(1);
 }
 
 void launch_normals_adjoint(const float4* v_cam, const float4* vn, const float* d_n, const int4* faces,
@@ -308,27 +312,32 @@ void launch_normals_adjoint(const float4* v_cam, const float4* vn, const float* 
                             cudaStream_t st) {
     k_normals_adj_a<<<nb(N, 256), 256, 0, st>>>(vn, d_n, N, dm);
     k_normals_adj_b<<<nb(N, 256), 256, 0, st>>>(v_cam, faces, vf_off, vf_idx, N, dm, d_v);
+    fr_count_launches(2);
 }
 
 void launch_pose_adjoint(const float* v_model, int N, int ld, const float* rot, const float* trans,
                          const float* d_v, float* d_vmodel, double* acc12, cudaStream_t st) {
     (void)ld;
     k_pose_adj<<<nb(N, 256), 256, 0, st>>>(v_model, N, rot, trans, d_v, d_vmodel, acc12);
+    fr_count_launches(1);
 }
 
 void launch_pose_finish(const float* rot, const double* acc12, const double* small, int NL, float* g_rot,
                         float* g_trans, float* g_focal, float* g_light, cudaStream_t st) {
     k_pose_finish<<<1, 64, 0, st>>>(rot, acc12, small, NL, g_rot, g_trans, g_focal, g_light);
+    fr_count_launches(1);
 }
 
 void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const float* d_vmodel, float* g_coef,
                           cudaStream_t st) {
     if (K <= 0) return;
     k_morph_adj<<<K, 512, 0, st>>>(basis, ld / 4, n3, d_vmodel, g_coef);
+    fr_count_launches(1);
 }
 
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* counters, int n, uint32_t* out, cudaStream_t st) {
     if (n <= 0) return;
     k_philox<<<nb(n, 256), 256, 0, st>>>(make_uint2(k0, k1), reinterpret_cast<const uint4*>(counters), n,
                                          reinterpret_cast<uint4*>(out));
+    fr_count_launches(1);
 }

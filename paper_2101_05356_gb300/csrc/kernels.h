@@ -63,5 +63,8 @@ void launch_trace_rays(const DevScene& S, const float* org, const float* dir, in
 void launch_loss(int H, int W, const float* image, const float* target, double* loss, float* sign,
                  float* blurred, float* adj_image, cudaStream_t st);
 
+// process-wide count of kernels launched by this library (api.cu)
+void fr_count_launches(int n);
+
 // misc
 void launch_philox(uint32_t k0, uint32_t k1, const uint32_t* counters, int n, uint32_t* out, cudaStream_t st);

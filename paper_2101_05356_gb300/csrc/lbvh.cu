@@ -246,6 +246,7 @@ void launch_lbvh(const float4* v_cam, const int4* faces, int T, BvhScratch& B, B
         k_hist<<<n_tiles, SORT_TILE, 0, st>>>(ka, T, shift, n_tiles, B.hist);
         k_scan<<<1, 1024, 0, st>>>(B.hist, 256 * n_tiles);
         k_scatter<<<n_tiles, SORT_TILE, 0, st>>>(ka, va, T, shift, n_tiles, B.hist, kb, vb);
+        fr_count_launches(3);
         uint32_t* tk = ka; ka = kb; kb = tk;
         int* tv = va; va = vb; vb = tv;
     }
@@ -257,13 +258,16 @@ void launch_lbvh(const float4* v_cam, const int4* faces, int T, BvhScratch& B, B
         // unwritten child slots read as leaf 0, never as an ancestor
         cudaMemsetAsync(B.child, 0xff, sizeof(int) * 2 * (size_t)(T - 1), st);
         k_karras<<<nb(T - 1, 256), 256, 0, st>>>(ka, T, B.child, B.parent_int, B.parent_leaf, status);
+        fr_count_launches(1);
     }
     k_boxes<<<nb(T, 256), 256, 0, st>>>(v_cam, faces, va, T, B.child, B.parent_int, B.parent_leaf, B.flag,
                                         B.box_int, B.box_leaf, tris, status);
     k_pack<<<nb(T > 1 ? T - 1 : 1, 256), 256, 0, st>>>(T, B.child, B.box_int, B.box_leaf, nodes);
+    fr_count_launches(2);
 }
 
 void launch_bvh_check(const BvhNode* nodes, const BvhScratch& B, int T, int* out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, sizeof(int) * 3, st);
     k_check<<<nb(T, 256), 256, 0, st>>>(nodes, B.child, B.parent_int, B.parent_leaf, B.box_int, T, out);
+    fr_count_launches(1);
 }

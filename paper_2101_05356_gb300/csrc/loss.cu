@@ -67,5 +67,9 @@ void launch_loss(int H, int W, const float* image, const float* target, double* 
     const int n = H * W * 3;
     cudaMemsetAsync(loss, 0, sizeof(double), st);
     k_blur_loss<<<(n + 255) / 256, 256, 0, st>>>(H, W, image, target, loss, sign, blurred);
-    if (adj_image) k_blur_adjoint<<<(n + 255) / 256, 256, 0, st>>>(H, W, sign, adj_image);
+    fr_count_launches(1);
+    if (adj_image) {
+        k_blur_adjoint<<<(n + 255) / 256, 256, 0, st>>>(H, W, sign, adj_image);
+        fr_count_launches(1);
+    }
 }

@@ -45,14 +45,14 @@ struct SampleState {
 
 // Primary ray through screen point (sx, sy) and the shading state at its hit.
 FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
-                        Stack st, SampleState& ss) {
+                        Stack st, SampleState& ss, RayStats& rs) {
     ss.hit = false;
     ss.tri = -1;
     if (!active) return;
     const float f = __ldg(P.focal);
     ss.d = f3((sx - 0.5f * S.W) / f, -(sy - 0.5f * S.H) / f, -1.0f);
     const RayPre r = ray_setup(f3(0.0f, 0.0f, 0.0f), ss.d);
-    const Hit h = trace_closest(S, r, 0.0f, INFINITY, st);
+    const Hit h = trace_closest(S, r, 0.0f, INFINITY, st, rs);
     if (h.tri < 0) return;
     ss.hit = true;
     ss.tri = h.tri;
@@ -95,14 +95,14 @@ FR_D bool light_visible_geometry(const LightDev& L, float3 z, const SampleState&
 }
 
 // Trace the queued jobs [head, head + n) of this warp's ring (lane k takes job k).
-FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st) {
+FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st, RayStats& rs) {
     const int lane = threadIdx.x & 31;
     if (lane < n) {
         const float4 a = q.job[(head + lane) & 63][0], b = q.job[(head + lane) & 63][1];
         const float3 y = f3(a.x, a.y, a.z), z = f3(a.w, b.x, b.y);
         const int skip = __float_as_int(b.z), tag = __float_as_int(b.w);
         const RayPre r = ray_setup(y, z - y);
-        if (!trace_any(S, r, SHADOW_EPS, 1.0f - SHADOW_EPS, skip, st))
+        if (!trace_any(S, r, SHADOW_EPS, 1.0f - SHADOW_EPS, skip, st, rs))
             atomicOr(&q.vis[tag & 31], 1ull << (tag >> 8));
     }
     __syncwarp();
@@ -112,7 +112,7 @@ FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st) {
 // ray to this lane's light-j sample is traced and unoccluded.  All 32 lanes
 // must call this together.
 FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sampler& smp, int dim0,
-                          WarpQueue& q, Stack st) {
+                          WarpQueue& q, Stack st, RayStats& rs) {
     const int lane = threadIdx.x & 31;
     q.vis[lane] = 0ull;
     __syncwarp();
@@ -137,12 +137,12 @@ FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sample
         count += __popc(ballot);
         __syncwarp();
         if (count >= 32) {
-            drain(S, q, head, 32, st);
+            drain(S, q, head, 32, st, rs);
             head = (head + 32) & 63;
             count -= 32;
         }
     }
-    if (count > 0) drain(S, q, head, count, st);
+    if (count > 0) drain(S, q, head, count, st, rs);
     return q.vis[lane];
 }
 
@@ -204,9 +204,10 @@ FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleSta
 
 // Full warp-cooperative radiance evaluation at screen point (sx, sy).
 FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
-                        const Sampler& smp, int dim0, RtShared& sh, SampleState& ss, uint64_t& vis) {
-    primary_state(S, P, active, sx, sy, my_stack(sh), ss);
-    vis = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], my_stack(sh));
+                        const Sampler& smp, int dim0, RtShared& sh, SampleState& ss, uint64_t& vis,
+                        RayStats& rs) {
+    primary_state(S, P, active, sx, sy, my_stack(sh), ss, rs);
+    vis = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], my_stack(sh), rs);
     return radiance_from(S, P, ss, vis, smp, dim0);
 }
 
@@ -235,8 +236,10 @@ __global__ void __launch_bounds__(RT_THREADS) k_forward(DevScene S, DevParams P,
     const float2 jit = smp.pair(0);
     SampleState ss;
     uint64_t vis;
+    RayStats rs;
     const float3 Lo = radiance_at(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
-                                  smp, 2, sh, ss, vis);
+                                  smp, 2, sh, ss, vis, rs);
+    flush_stats(S.counters + 0, rs);
     if (valid && tri_rec) tri_rec[q] = ss.tri;
     if (valid && mask_rec) mask_rec[q] = vis;
     const int width = S.spp < 32 ? S.spp : 32;
@@ -293,7 +296,7 @@ FR_D void scatter_texel(float* base, int C, int texel, int ch, float g, bool on)
 // for visibility of the emitter, Sec. 4).  Adds C * dz/dy . m to gy and
 // scatters the edge-vertex terms.  Returns nothing; inactive lanes do nothing.
 FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL, const SampleState& ss,
-                      const Sampler& sm2, float3 w, float3& gy, float* d_v, Stack st) {
+                      const Sampler& sm2, float3 w, float3& gy, float* d_v, Stack st, RayStats& rs) {
     const uint4 blk = sm2.block(0);
     const float u0 = u24(blk.x), u1 = u24(blk.y), u2 = u24(blk.z);
     const int j = min((int)(u0 * (float)S.NL), S.NL - 1);
@@ -342,8 +345,8 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     if (!(tl > 0.0f)) return;
     const float3 m = cross(L.n, tan) * (1.0f / tl);
     const float3 zp = z + m * SHADOW_EPS, zm = z - m * SHADOW_EPS;
-    const bool vp = !trace_any(S, ray_setup(ss.y, zp - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st);
-    const bool vm = !trace_any(S, ray_setup(ss.y, zm - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st);
+    const bool vp = !trace_any(S, ray_setup(ss.y, zp - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st, rs);
+    const bool vm = !trace_any(S, ray_setup(ss.y, zm - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st, rs);
     const float dV = (float)vp - (float)vm;
     if (dV == 0.0f) return;
     const float3 I = intensity(S, P, j);
@@ -378,8 +381,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_adjoint(DevScene S, DevParams P,
     const float2 jit = smp.pair(0);
     const float sx = (float)(pixel % S.W) + jit.x, sy = (float)(pixel / S.W) + jit.y;
     SampleState ss;
-    primary_state(S, P, valid, sx, sy, my_stack(sh), ss);
-    const uint64_t vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh));
+    RayStats rs;
+    primary_state(S, P, valid, sx, sy, my_stack(sh), ss, rs);
+    const uint64_t vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs);
     const bool interior = !(S.flags & FR_FLAG_NO_INTERIOR_D);
     ShadeAdj g;
     g.n = g.l = g.o = g.c = g.s = f3(0.0f, 0.0f, 0.0f);
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_adjoint(DevScene S, DevParams P,
         }
         if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit) {
             const Sampler sm2{make_uint2(S.seed, FR_STREAM_EDGE_SHADOW), (uint32_t)pixel, (uint32_t)s, iteration, face};
-            shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, my_stack(sh));
+            shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, my_stack(sh), rs);
         }
     }
     // ---- chain rule back to the hit triangle, its normals and the camera ----
@@ -503,6 +507,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_adjoint(DevScene S, DevParams P,
     }
     const float gf_w = warp_sum(gfocal);
     if ((threadIdx.x & 31) == 0 && gf_w != 0.0f) atomicAdd(&sh.acc[0], (double)gf_w);
+    flush_stats(S.counters + 3, rs);
     block_acc_flush(sh, 1 + 3 * S.NL, G.small);
 }
 
@@ -555,8 +560,10 @@ __global__ void __launch_bounds__(RT_THREADS) k_edge_primary(DevScene S, DevPara
     const float eps = 1e-3f;
     SampleState ssp, ssm;
     uint64_t visp, vism;
-    const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, ssp, visp);
-    const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, ssm, vism);
+    RayStats rs;
+    const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, ssp, visp, rs);
+    const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, ssm, vism, rs);
+    flush_stats(S.counters + 6, rs);
     float gf = 0.0f;
     float3 gA = f3(0, 0, 0), gB = f3(0, 0, 0);
     if (active) {
@@ -662,7 +669,8 @@ __global__ void __launch_bounds__(RT_THREADS) k_trace_rays(DevScene S, const flo
     const int i = blockIdx.x * RT_THREADS + threadIdx.x;
     if (i >= n) return;
     const RayPre r = ray_setup(f3(org[3 * i], org[3 * i + 1], org[3 * i + 2]), f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]));
-    const Hit h = trace_closest(S, r, 0.0f, INFINITY, Stack{&stack[threadIdx.x], RT_THREADS});
+    RayStats rs;
+    const Hit h = trace_closest(S, r, 0.0f, INFINITY, Stack{&stack[threadIdx.x], RT_THREADS}, rs);
     tri[i] = h.tri;
     tout[i] = h.tri >= 0 ? h.t : -1.0f;
 }
@@ -679,12 +687,14 @@ void launch_forward(const DevScene& S, const DevParams& P, float* image, int32_t
     const long total = (long)S.W * S.H * S.spp;
     if (S.spp > 32) cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)S.W * S.H, st);
     k_forward<<<blocks_for(total, RT_THREADS), RT_THREADS, 0, st>>>(S, P, image, tri_rec, mask_rec, iteration, face);
+    fr_count_launches(1);
 }
 
 void launch_adjoint(const DevScene& S, const DevParams& P, const DevGrads& G, const EdgeLists& EL,
                     const float* adj_image, uint32_t iteration, uint32_t face, cudaStream_t st) {
     const long total = (long)S.W * S.H * S.spp;
     k_adjoint<<<blocks_for(total, RT_THREADS), RT_THREADS, 0, st>>>(S, P, G, EL, adj_image, iteration, face);
+    fr_count_launches(1);
 }
 
 void launch_edge_primary(const DevScene& S, const DevParams& P, const DevGrads& G, const EdgeLists& EL,
@@ -692,15 +702,18 @@ void launch_edge_primary(const DevScene& S, const DevParams& P, const DevGrads& 
     const long n = (long)S.W * S.H * S.edge_spp;
     if (n == 0) return;
     k_edge_primary<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(S, P, G, EL, adj_image, iteration, face);
+    fr_count_launches(1);
 }
 
 void launch_classify(const DevScene& S, const EdgeLists& EL, uint8_t* flags, cudaStream_t st) {
     k_classify<<<blocks_for(S.E, 256), 256, 0, st>>>(S, EL.edges, flags);
     k_compact<<<1 + S.NL, 1024, 0, st>>>(S.E, flags, EL.prim_list, EL.prim_count);
+    fr_count_launches(2);
 }
 
 void launch_trace_rays(const DevScene& S, const float* org, const float* dir, int n, int32_t* tri, float* t,
                        cudaStream_t st) {
     if (n <= 0) return;
     k_trace_rays<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(S, org, dir, n, tri, t);
+    fr_count_launches(1);
 }

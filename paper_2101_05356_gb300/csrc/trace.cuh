@@ -95,7 +95,8 @@ struct Stack {
 };
 
 // Closest hit in (tmin, tmax); ties on t go to the lower triangle index.
-FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tmax, Stack st) {
+FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tmax, Stack st, RayStats& rs) {
+    rs.rays++;
     Hit h;
     h.t = tmax;
     h.tri = -1;
@@ -107,6 +108,7 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
         float3 lo0, hi0, lo1, hi1;
         int c0, c1;
         load_node(s.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
+        rs.nodes++;
         float tn0, tn1;
         bool h0 = box_hit(r, lo0, hi0, tmin, h.t, tn0);
         bool h1 = box_hit(r, lo1, hi1, tmin, h.t, tn1);
@@ -116,6 +118,7 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
             const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
             float t, b1, b2;
             const int id = __float_as_int(a.w);
+            rs.tris++;
             if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
                 (t < h.t || id < h.tri || h.tri < 0)) {
                 h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
@@ -127,6 +130,7 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
             const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
             float t, b1, b2;
             const int id = __float_as_int(a.w);
+            rs.tris++;
             if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
                 (t < h.t || id < h.tri || h.tri < 0)) {
                 h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
@@ -155,13 +159,16 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
 }
 
 // Any hit in (tmin, tmax), skipping triangle `skip` (shadow rays).
-FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, int skip, Stack st) {
+FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, int skip, Stack st,
+                    RayStats& rs) {
+    rs.rays++;
     int sp = 0;
     int node = 0;
     for (int guard = 2 * s.T + 8; guard > 0; --guard) {
         float3 lo0, hi0, lo1, hi1;
         int c0, c1;
         load_node(s.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
+        rs.nodes++;
         float tn0, tn1;
         bool h0 = box_hit(r, lo0, hi0, tmin, tmax, tn0);
         bool h1 = box_hit(r, lo1, hi1, tmin, tmax, tn1);
@@ -171,6 +178,7 @@ FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, 
             if (__float_as_int(a.w) != skip) {
                 const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
                 float t, b1, b2;
+                rs.tris++;
                 if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
             }
             h0 = false;
@@ -181,6 +189,7 @@ FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, 
             if (__float_as_int(a.w) != skip) {
                 const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
                 float t, b1, b2;
+                rs.tris++;
                 if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
             }
             h1 = false;

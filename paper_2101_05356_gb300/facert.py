@@ -88,6 +88,11 @@ def lib():
         L.fr_debug_bvh.argtypes = [_vp, P(FrParams), _vp, _vp]
         L.fr_num_edges.argtypes = [_vp]
         L.fr_num_edges.restype = ctypes.c_int32
+        L.fr_counters.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
+        L.fr_set_timing.argtypes = [_vp, ctypes.c_int32]
+        L.fr_get_timing.argtypes = [_vp, _vp]
+        L.fr_kernel_launches.argtypes = []
+        L.fr_kernel_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -207,6 +212,34 @@ def fr_debug_bvh(ctx, params, out):
 
 def fr_num_edges(ctx):
     return int(lib().fr_num_edges(ctx))
+
+
+COUNTER_KERNELS = ("forward", "adjoint", "edge_primary")
+
+
+def fr_counters(ctx, reset=False):
+    """Per-kernel traversal work: {kernel: {rays, nodes, tris}}."""
+    out = np.zeros(9, np.uint64)
+    check(lib().fr_counters(ctx, out.ctypes.data, 1 if reset else 0, _stream()), ctx)
+    return {k: {"rays": int(out[3 * i]), "nodes": int(out[3 * i + 1]), "tris": int(out[3 * i + 2])}
+            for i, k in enumerate(COUNTER_KERNELS)}
+
+
+def fr_set_timing(ctx, on=True):
+    check(lib().fr_set_timing(ctx, 1 if on else 0), ctx)
+
+
+TIMING_STAGES = ("build", "forward", "loss", "classify", "adjoint", "edge_primary", "chain", "total")
+
+
+def fr_get_timing(ctx):
+    out = np.zeros(8, np.float32)
+    check(lib().fr_get_timing(ctx, out.ctypes.data), ctx)
+    return dict(zip(TIMING_STAGES, [float(x) for x in out]))
+
+
+def fr_kernel_launches():
+    return int(lib().fr_kernel_launches())
 
 
 # ---- convenience: one context bound to a synthetic scene ------------------
