@@ -111,8 +111,9 @@ typedef struct fr_grads {
     float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
 } fr_grads;
 
-/* Create a context for one image configuration.  Allocates nothing on the
- * device yet.  Errors: FR_EINVAL (bad sizes), FR_ECUDA. */
+/* Create a context for one image configuration.  Allocates the image-sized
+ * loss scratch and the status/counter words.  Errors: FR_EINVAL (bad sizes),
+ * FR_ENOMEM. */
 fr_status fr_create(fr_ctx** out, const fr_config* cfg);
 
 /* Copy a face model (Sec. 3.1) and build its static topology (vertex->face

@@ -215,9 +215,6 @@ fr_status alloc_scratch(fr_ctx* c) {
     TRY(dalloc(c, &c->dm, 3 * (size_t)N));
     TRY(dalloc(c, &c->small, 1 + 3 * FR_MAX_LIGHTS));
     TRY(dalloc(c, &c->acc12, 12));
-    const size_t px = (size_t)c->cfg.width * c->cfg.height * 3;
-    TRY(dalloc(c, &c->sign, px));
-    TRY(dalloc(c, &c->adj_image, px));
     return FR_OK;
 }
 
@@ -239,7 +236,9 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
     c->cfg = *cfg;
     if (dalloc(c, &c->status, 1) != FR_OK || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
         dalloc(c, &c->counters, 9) != FR_OK ||
-        cudaMemset(c->counters, 0, 9 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMemset(c->counters, 0, 9 * sizeof(unsigned long long)) != cudaSuccess ||
+        dalloc(c, &c->sign, (size_t)cfg->width * cfg->height * 3) != FR_OK ||
+        dalloc(c, &c->adj_image, (size_t)cfg->width * cfg->height * 3) != FR_OK) {
         g_err = c->err;
         free_all(c);
         delete c;
