@@ -219,6 +219,26 @@ fr_status fr_get_timing(fr_ctx* ctx, float* out);
 /* Number of kernels this library has launched in this process. */
 uint64_t fr_kernel_launches(void);
 
+/* ---- allocation-free variant ---- */
+
+/* The photometric loss of fr_loss for callers that cannot allocate device
+ * memory: a host application that owns the device memory budget through its
+ * own pool and forbids libraries to allocate behind it, or a latency-critical
+ * loop that cannot absorb an allocation.  The paper has no counterpart; this is
+ * an interface convenience.  No context is needed: the caller passes the image
+ * size (height * width <= 512 * 512, else FR_EINVAL) and its own buffers, with
+ * the same meaning and results as fr_loss.  The only scratch is a static device
+ * array (3 MiB, held by every GPU that loads the library until exit) shared by
+ * all calls: calls whose kernels overlap on the GPU race on it.  The first call
+ * on each device looks up the array's device address once, with that device
+ * current; make that first call before any stream capture.  Allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine. */
+fr_status fr_loss_noalloc(int32_t height, int32_t width, const float* image, const float* target,
+                          double* loss, float* adj_image, float* blurred, void* stream);
+
+/* Message of the last failed fr_loss_noalloc call on this host thread. */
+const char* fr_loss_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif

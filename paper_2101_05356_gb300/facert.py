@@ -93,6 +93,9 @@ def lib():
         L.fr_get_timing.argtypes = [_vp, _vp]
         L.fr_kernel_launches.argtypes = []
         L.fr_kernel_launches.restype = ctypes.c_uint64
+        L.fr_loss_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.fr_loss_noalloc_error.argtypes = []
+        L.fr_loss_noalloc_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -236,6 +239,16 @@ def fr_get_timing(ctx):
     out = np.zeros(8, np.float32)
     check(lib().fr_get_timing(ctx, out.ctypes.data), ctx)
     return dict(zip(TIMING_STAGES, [float(x) for x in out]))
+
+
+def fr_loss_noalloc(height, width, image, target, loss, adj_image=None, blurred=None):
+    """fr_loss without a context and without any device allocation (static
+    scratch, images up to 512 x 512); raises FacertError on a rejected call."""
+    code = lib().fr_loss_noalloc(height, width, _ptr(image), _ptr(target), _ptr(loss), _ptr(adj_image),
+                                 _ptr(blurred), _stream())
+    if code != FR_OK:
+        msg = lib().fr_loss_noalloc_error()
+        raise FacertError(code, msg.decode() if msg else "")
 
 
 def fr_kernel_launches():
