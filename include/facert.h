@@ -152,6 +152,10 @@ fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float*
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);
 
+/* Replace the FR_FLAG_* set of ctx for the following calls (e.g. drop the edge
+ * terms when only textures are optimised).  Errors: FR_EINVAL. */
+fr_status fr_set_flags(fr_ctx* ctx, uint32_t flags);
+
 /* Synchronise `stream`, read and clear the device status word.
  * Returns FR_OK, FR_EOVERFLOW or FR_ETIMEOUT (or FR_ECUDA). */
 fr_status fr_sync_status(fr_ctx* ctx, void* stream);
@@ -218,6 +222,44 @@ fr_status fr_get_timing(fr_ctx* ctx, float* out);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t fr_kernel_launches(void);
+
+/* ---- optimiser: Adam with the regularisers of Sec. 4 (Eq. loss1, loss3) ---- */
+
+#define FR_MAX_OPT_GROUPS 16
+#define FR_GROUP_PLAIN    0   /* Adam only */
+#define FR_GROUP_COEF     1   /* first n_prior elements: shape prior w_prior * x^2 (sigma_k = 1);
+                                 the rest: soft box [0, 1] (expression), w_box * dist^2 */
+#define FR_GROUP_LIGHT    2   /* intensities [N_L][3]: light prior w_prior * |I_j - m_j|^2 with
+                                 I_j = aux[j] * i_j and m_j = mean(I_j) held fixed; soft box i >= 0 */
+#define FR_GROUP_TEX_RGB  3   /* M x M x 3 texture: smoothness w_smooth * sum_i sum_{4-nbrs} |X_j - X_i|^2,
+                                 symmetry w_sym * sum |X - flip(X)|_1 (flip: column c -> M-1-c),
+                                 chromaticity w_chroma * sum |kappa(X) - kappa(aux)|_1 with
+                                 kappa(c) = c / (c_r + c_g + c_b + 1e-6), soft box [0, 1] (w_box) */
+#define FR_GROUP_TEX_MONO 4   /* M x M texture: smoothness, symmetry, soft box [0, 1] */
+
+/* One parameter group.  x, m, v (and g, aux when used) are device float32
+ * arrays of n elements (aux: N_L scales for LIGHT, the M x M x 3 reference
+ * albedo for TEX_RGB).  m and v must be zero before step 1.  After the update x
+ * is clamped to [clamp_lo, clamp_hi] when clamp_lo < clamp_hi. */
+typedef struct fr_opt_group {
+    float* x;
+    const float* g;
+    float* m;
+    float* v;
+    const float* aux;
+    int32_t n, kind, width, n_prior;
+    float lr, w_prior, w_box, w_sym, w_chroma, w_smooth, clamp_lo, clamp_hi;
+} fr_opt_group;
+
+/* One Adam step (Kingma & Ba; bias-corrected, step >= 1) over every group:
+ * gradient = g + gradient of the group's regularisers at the current x, then
+ * m = b1 m + (1 - b1) grad, v = b2 v + (1 - b2) grad^2,
+ * x -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Two launches on `stream` (moments, then update), so the stencils read the
+ * pre-step values.  If reg_energy (device double) is given it receives the
+ * regulariser energy at the pre-step values.  Errors: FR_EINVAL on bad groups. */
+fr_status fr_adam(const fr_opt_group* groups, int32_t n_groups, int32_t step, float beta1, float beta2,
+                  float eps, double* reg_energy, void* stream);
 
 /* ---- allocation-free variant ---- */
 

@@ -390,6 +390,12 @@ fr_status fr_render(fr_ctx* c, const fr_params* p, const float* target, float* i
     return FR_OK;
 }
 
+fr_status fr_set_flags(fr_ctx* c, uint32_t flags) {
+    if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    c->cfg.flags = flags;
+    return FR_OK;
+}
+
 fr_status fr_sync_status(fr_ctx* c, void* stream) {
     if (!c) return fail(nullptr, FR_EINVAL, "null context");
     CK(c, cudaStreamSynchronize(S_(stream)));

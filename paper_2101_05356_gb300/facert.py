@@ -49,6 +49,17 @@ class FrGrads(ctypes.Structure):
     _fields_ = [(n, _vp) for n in PARAM_NAMES]
 
 
+GROUP_PLAIN, GROUP_COEF, GROUP_LIGHT, GROUP_TEX_RGB, GROUP_TEX_MONO = 0, 1, 2, 3, 4
+
+
+class FrOptGroup(ctypes.Structure):
+    _fields_ = [("x", _vp), ("g", _vp), ("m", _vp), ("v", _vp), ("aux", _vp),
+                ("n", ctypes.c_int32), ("kind", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("n_prior", ctypes.c_int32), ("lr", ctypes.c_float), ("w_prior", ctypes.c_float),
+                ("w_box", ctypes.c_float), ("w_sym", ctypes.c_float), ("w_chroma", ctypes.c_float),
+                ("w_smooth", ctypes.c_float), ("clamp_lo", ctypes.c_float), ("clamp_hi", ctypes.c_float)]
+
+
 class FacertError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("facert error %d: %s" % (code, msg))
@@ -93,6 +104,9 @@ def lib():
         L.fr_get_timing.argtypes = [_vp, _vp]
         L.fr_kernel_launches.argtypes = []
         L.fr_kernel_launches.restype = ctypes.c_uint64
+        L.fr_set_flags.argtypes = [_vp, ctypes.c_uint32]
+        L.fr_adam.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, _vp, _vp]
         L.fr_loss_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fr_loss_noalloc_error.argtypes = []
         L.fr_loss_noalloc_error.restype = ctypes.c_char_p
@@ -239,6 +253,27 @@ def fr_get_timing(ctx):
     out = np.zeros(8, np.float32)
     check(lib().fr_get_timing(ctx, out.ctypes.data), ctx)
     return dict(zip(TIMING_STAGES, [float(x) for x in out]))
+
+
+def fr_set_flags(ctx, flags):
+    check(lib().fr_set_flags(ctx, flags), ctx)
+
+
+def opt_group(x, m, v, g=None, aux=None, kind=GROUP_PLAIN, lr=1e-3, width=0, n_prior=0, w_prior=0.0,
+              w_box=0.0, w_sym=0.0, w_chroma=0.0, w_smooth=0.0, clamp=None):
+    """One fr_opt_group over torch device tensors (views of x/g/m/v share storage)."""
+    lo, hi = clamp if clamp is not None else (0.0, 0.0)
+    grp = FrOptGroup(_ptr(x), _ptr(g), _ptr(m), _ptr(v), _ptr(aux), x.numel(), kind, width, n_prior, lr,
+                     w_prior, w_box, w_sym, w_chroma, w_smooth, lo, hi)
+    grp._keep = (x, g, m, v, aux)
+    return grp
+
+
+def fr_adam(groups, step, beta1=0.9, beta2=0.999, eps=1e-8, reg_energy=None):
+    arr = (FrOptGroup * len(groups))(*groups)
+    code = lib().fr_adam(ctypes.cast(arr, _vp), len(groups), step, beta1, beta2, eps, _ptr(reg_energy), _stream())
+    if code != FR_OK:
+        raise FacertError(code, "fr_adam: invalid parameter groups")
 
 
 def fr_loss_noalloc(height, width, image, target, loss, adj_image=None, blurred=None):

@@ -1,0 +1,134 @@
+"""GPU tests of the optimiser kernel (fr_adam) against its FP64 oracle, of the
+autograd.Function, and of the two-stage reconstruction loop."""
+import numpy as np
+import pytest
+
+from oracle import optim as ora
+from paper_2101_05356_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def test_adam_step_matches_oracle():
+    from paper_2101_05356_gb300 import facert
+    rng = np.random.default_rng(0)
+    M, NL, ks, ke = 12, 5, 7, 4
+    data = {
+        "coef": rng.normal(size=ks + ke) * 0.8,
+        "light": rng.uniform(-0.2, 1.5, (NL, 3)),
+        "dif": rng.uniform(-0.1, 1.1, (M, M, 3)),
+        "spec": rng.uniform(-0.1, 1.1, (M, M, 3)),
+        "rough": rng.uniform(0.0, 1.2, (M, M)),
+        "rot": rng.normal(size=3) * 0.1,
+    }
+    data["coef"][ks:] = rng.uniform(-0.3, 1.3, ke)
+    grads = {k: rng.normal(size=np.shape(v)) for k, v in data.items()}
+    mom = {k: rng.normal(size=np.shape(v)) * 0.1 for k, v in data.items()}
+    vel = {k: rng.uniform(0, 0.05, size=np.shape(v)) for k, v in data.items()}
+    scale = rng.uniform(1.0, 9.0, NL)
+    ref_d = rng.uniform(0.1, 0.9, (M, M, 3))
+    ref_s = rng.uniform(0.1, 0.9, (M, M, 3))
+    d = {k: (_t(data[k]), _t(grads[k]), _t(mom[k]), _t(vel[k])) for k in data}
+    sc_t, refd_t, refs_t = _t(scale), _t(ref_d), _t(ref_s)
+    X, G, Mo, V = 0, 1, 2, 3
+    groups = [
+        facert.opt_group(d["coef"][X][:ks], d["coef"][Mo][:ks], d["coef"][V][:ks], d["coef"][G][:ks],
+                         kind=facert.GROUP_COEF, lr=1e-2, n_prior=ks, w_prior=0.0025),
+        facert.opt_group(d["coef"][X][ks:], d["coef"][Mo][ks:], d["coef"][V][ks:], d["coef"][G][ks:],
+                         kind=facert.GROUP_COEF, lr=1e-3, n_prior=0, w_box=1.0),
+        facert.opt_group(d["light"][X], d["light"][Mo], d["light"][V], d["light"][G], aux=sc_t,
+                         kind=facert.GROUP_LIGHT, lr=1e-3, w_prior=0.01, w_box=1.0),
+        facert.opt_group(d["dif"][X], d["dif"][Mo], d["dif"][V], d["dif"][G], aux=refd_t, kind=facert.GROUP_TEX_RGB,
+                         width=M, lr=5e-3, w_sym=0.3, w_chroma=0.3, w_smooth=0.0002),
+        facert.opt_group(d["spec"][X], d["spec"][Mo], d["spec"][V], d["spec"][G], aux=refs_t, kind=facert.GROUP_TEX_RGB,
+                         width=M, lr=5e-3, w_sym=0.3, w_chroma=0.3, w_smooth=0.0002, w_box=1.0),
+        facert.opt_group(d["rough"][X], d["rough"][Mo], d["rough"][V], d["rough"][G], kind=facert.GROUP_TEX_MONO,
+                         width=M, lr=5e-3, w_smooth=0.0002, w_box=1.0, clamp=(0.02, 1.5)),
+        facert.opt_group(d["rot"][X], d["rot"][Mo], d["rot"][V], d["rot"][G], lr=1e-3),
+    ]
+    energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    step = 3
+    facert.fr_adam(groups, step, reg_energy=energy)
+    torch.cuda.synchronize()
+    # oracle: the same update in FP64 on the float32-rounded inputs
+    f = {k: np.asarray(data[k], np.float32).astype(np.float64) for k in data}
+    gf = {k: np.asarray(grads[k], np.float32).astype(np.float64) for k in data}
+    mf = {k: np.asarray(mom[k], np.float32).astype(np.float64) for k in data}
+    vf = {k: np.asarray(vel[k], np.float32).astype(np.float64) for k in data}
+    scf = np.asarray(scale, np.float32).astype(np.float64)
+    rdf = np.asarray(ref_d, np.float32).astype(np.float64)
+    rsf = np.asarray(ref_s, np.float32).astype(np.float64)
+    reg = {
+        "coef": ora.coef_grad(f["coef"], ks, 0.0025, 0.0) + np.concatenate(
+            [np.zeros(ks), ora.box_grad(f["coef"][ks:], 1.0)]),
+        "light": ora.light_grad(f["light"], scf, 0.01, 1.0),
+        "dif": ora.tex_grad(f["dif"], 0.0002, 0.3, 0.3, 0.0, rdf),
+        "spec": ora.tex_grad(f["spec"], 0.0002, 0.3, 0.3, 1.0, rsf),
+        "rough": ora.tex_grad(f["rough"], 0.0002, 0.0, 0.0, 1.0),
+        "rot": np.zeros(3),
+    }
+    e_want = (ora.coef_energy(f["coef"], ks, 0.0025, 1.0) + ora.light_energy(f["light"], scf, 0.01, 1.0)
+              + ora.tex_energy(f["dif"], 0.0002, 0.3, 0.3, 0.0, rdf) + ora.tex_energy(f["spec"], 0.0002, 0.3, 0.3, 1.0, rsf)
+              + ora.tex_energy(f["rough"], 0.0002, 0.0, 0.0, 1.0))
+    lrs = {"light": 1e-3, "dif": 5e-3, "spec": 5e-3, "rough": 5e-3, "rot": 1e-3}
+    for k in data:
+        if k == "coef":
+            xa, ma, va = ora.adam(f[k][:ks], gf[k][:ks] + reg[k][:ks], mf[k][:ks], vf[k][:ks], step, 1e-2)
+            xb, mb, vb = ora.adam(f[k][ks:], gf[k][ks:] + reg[k][ks:], mf[k][ks:], vf[k][ks:], step, 1e-3)
+            xw, mw, vw = np.concatenate([xa, xb]), np.concatenate([ma, mb]), np.concatenate([va, vb])
+        else:
+            clamp = (0.02, 1.5) if k == "rough" else None
+            xw, mw, vw = ora.adam(f[k], gf[k] + reg[k], mf[k], vf[k], step, lrs[k], clamp=clamp)
+        assert np.allclose(d[k][Mo].cpu().numpy(), mw, rtol=1e-5, atol=1e-6), k
+        assert np.allclose(d[k][V].cpu().numpy(), vw, rtol=1e-5, atol=1e-7), k
+        assert np.allclose(d[k][X].cpu().numpy(), xw, rtol=1e-5, atol=1e-6), k
+    assert energy.item() == pytest.approx(e_want, rel=1e-5)
+
+
+def test_autograd_function_matches_adjoint_and_linearity():
+    from paper_2101_05356_gb300 import autograd, facert
+    sc = synth.make_scene("tiny")
+    r = facert.Renderer(sc)
+    dp = r.device_params(synth.random_params(sc, 1))
+    w = torch.rand((sc.height, sc.width, 3), device="cuda")
+    leaves = {k: v.clone().requires_grad_(True) for k, v in dp.items()}
+    img = autograd.render(r, leaves, iteration=4)
+    (img * w).sum().backward()
+    direct = r.backward(dp, w, iteration=4)
+    for k in dp:
+        a, b = leaves[k].grad.cpu().numpy(), direct[k].cpu().numpy()
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-6 * max(np.abs(b).max(), 1e-12)), k
+    # the image is affine in the diffuse texture: a finite difference is exact
+    delta = torch.randn_like(dp["diffuse"]) * 0.05
+    hp, hm = dict(dp), dict(dp)
+    hp["diffuse"] = dp["diffuse"] + delta
+    hm["diffuse"] = dp["diffuse"] - delta
+    fd = ((r.forward(hp, 4) * w).sum() - (r.forward(hm, 4) * w).sum()).item() / 2.0
+    lin = (leaves["diffuse"].grad * ((hp["diffuse"] - hm["diffuse"]) / 2.0)).sum().item()
+    assert fd == pytest.approx(lin, rel=1e-3)
+
+
+def test_two_stage_reconstruction_reduces_loss():
+    from paper_2101_05356_gb300 import facert, optim
+    sc = synth.make_scene("c1")
+    r = facert.Renderer(sc)
+    gt = synth.random_params(sc, 3, coef_scale=0.5)
+    target = r.forward(r.device_params(gt), iteration=10 ** 6)
+    init = synth.init_params(sc)
+    rec = optim.Reconstruction(r, target, init, schedule=optim.Schedule(40, 20))
+    e0 = optim.photometric_loss(r, rec.p, target)
+    rec.run()
+    e1 = optim.photometric_loss(r, rec.p, target)
+    assert r.status() == 0
+    assert e1 < 0.8 * e0, (e0, e1)
