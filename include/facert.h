@@ -67,6 +67,8 @@ typedef struct fr_config {
     int32_t edge_spp;        /* primary-edge samples per pixel (0..64) */
     uint32_t flags;          /* FR_FLAG_* */
     uint32_t seed;           /* Philox key word 0 */
+    int32_t max_batch;       /* faces per fr_render_batch call, 0..32 (0 means 1); each gets a slot
+                                of scratch sized for width x height pixels */
 } fr_config;
 
 /* Face model of Sec. 3.1 (host pointers, copied into the context):
@@ -151,6 +153,29 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);
+
+/* One face of a batched call: its image configuration (width * height at most
+ * the context's width * height; spp a power of two <= 1024; edge_spp <= 64),
+ * flags, Philox iteration and face id, parameters (device), target image,
+ * output image [height][width][3], loss (device double) and gradients (NULL:
+ * forward + loss only; otherwise ADDED into, like fr_grads). */
+typedef struct fr_item {
+    int32_t width, height, spp, edge_spp;
+    uint32_t flags, iteration, face_id;
+    fr_params params;
+    const float* target;
+    float* image;
+    double* loss;
+    fr_grads* grads;
+} fr_item;
+
+/* fr_render for n faces at once (1 <= n <= max_batch), sharing the context's
+ * face model and light stage: item k uses slot k.  Each stage of the hot path
+ * (morph, pose and normals, LBVH build, forward, loss, adjoint, edge terms,
+ * chain to parameters) is one launch over all items, so faces of different
+ * sizes and sample counts share the GPU inside one launch.  Results equal n
+ * separate fr_render calls with the same arguments. */
+fr_status fr_render_batch(fr_ctx* ctx, const fr_item* items, int32_t n, void* stream);
 
 /* Replace the FR_FLAG_* set of ctx for the following calls (e.g. drop the edge
  * terms when only textures are optimised).  Errors: FR_EINVAL. */

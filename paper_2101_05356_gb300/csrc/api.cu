@@ -1,5 +1,11 @@
-// C-ABI of the facert library: context and scratch ownership, argument checks
+// C-ABI of the facert library: context, slot scratch ownership, argument checks
 // and the orchestration of the hot path (include/facert.h documents each call).
+//
+// A context holds one face model and light stage and `max_batch` slots of
+// per-face scratch (geometry, BVH, edge lists, adjoint accumulators, loss
+// scratch).  Every compute call is a batch: item k uses slot k, the item table
+// is written to device memory by one small kernel, and every stage is one
+// launch over all items.  The single-face calls are batches of one.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -11,12 +17,38 @@
 #include "common.cuh"
 #include "kernels.h"
 
+namespace {
+
+struct Slot {
+    float* v_model = nullptr;
+    float* d_vmodel = nullptr;
+    float4* v_cam = nullptr;
+    float4* vn = nullptr;
+    float4* n_face = nullptr;
+    BvhScratch B{};
+    BvhNode* nodes = nullptr;
+    float4* tris = nullptr;
+    uint8_t* sil_flags = nullptr;
+    int* lists = nullptr;
+    int* counts = nullptr;
+    float* d_v = nullptr;
+    float* d_n = nullptr;
+    float* dm = nullptr;
+    double* small = nullptr;
+    double* acc12 = nullptr;
+    float* sign = nullptr;
+    float* adj_image = nullptr;
+};
+
+}  // namespace
+
 struct fr_ctx {
     fr_config cfg{};
+    int max_batch = 1;
     int N = 0, T = 0, K = 0, NL = 0, E = 0, ld = 0;
     bool have_mesh = false, have_lights = false;
     std::string err;
-    // mesh and lights
+    // mesh and lights (shared by all slots)
     float* mean = nullptr;
     float* basis = nullptr;
     int4* faces = nullptr;
@@ -25,31 +57,11 @@ struct fr_ctx {
     int* vf_idx = nullptr;
     int4* edges = nullptr;
     LightDev* lights = nullptr;
-    // per-call geometry
-    float* v_model = nullptr;
-    float4* v_cam = nullptr;
-    float4* vn = nullptr;
-    float4* n_face = nullptr;
-    BvhScratch B{};
-    BvhNode* nodes = nullptr;
-    float4* tris = nullptr;
-    // edges
-    uint8_t* sil_flags = nullptr;
-    int* lists = nullptr;
-    int* counts = nullptr;
-    // adjoint
-    float* d_v = nullptr;
-    float* d_n = nullptr;
-    float* dm = nullptr;
-    float* d_vmodel = nullptr;
-    double* small = nullptr;
-    double* acc12 = nullptr;
-    // loss
-    float* sign = nullptr;
-    float* adj_image = nullptr;
+    std::vector<Slot> slots;
+    DevItem* d_items = nullptr;                // device item table [FR_MAX_BATCH]
+    std::vector<DevItem> h_items;
     int* status = nullptr;
     unsigned long long* counters = nullptr;   // [kernel][rays, nodes, triangle tests]
-    // per-stage CUDA-event timing
     bool timing = false;
     cudaEvent_t ev[9] = {};
     std::vector<void*> owned;
@@ -73,6 +85,12 @@ fr_status fail(fr_ctx* c, fr_status code, const std::string& msg) {
         if (e_ != cudaSuccess) return fail(ctx, FR_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
+#define TRY(x)                         \
+    do {                               \
+        fr_status s_ = (x);            \
+        if (s_ != FR_OK) return s_;    \
+    } while (0)
+
 template <class T>
 fr_status dalloc(fr_ctx* c, T** p, size_t count) {
     void* q = nullptr;
@@ -89,21 +107,15 @@ void free_all(fr_ctx* c) {
     c->owned.clear();
 }
 
-#define TRY(x)                         \
-    do {                               \
-        fr_status s_ = (x);            \
-        if (s_ != FR_OK) return s_;    \
-    } while (0)
-
 cudaStream_t S_(void* s) { return static_cast<cudaStream_t>(s); }
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 // stage marks: 0 start, 1 after build, 2 after forward, 3 after loss,
 // 4 after classify, 5 after adjoint, 6 after edge_primary, 7 after chain
 void mark(fr_ctx* c, int k, cudaStream_t st) {
     if (c->timing) cudaEventRecord(c->ev[k], st);
 }
-
-bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 fr_status check_params(fr_ctx* c, const fr_params* p) {
     if (!c) return fail(nullptr, FR_EINVAL, "null context");
@@ -114,108 +126,191 @@ fr_status check_params(fr_ctx* c, const fr_params* p) {
     return FR_OK;
 }
 
-DevScene scene_of(const fr_ctx* c) {
-    DevScene s;
+// Per-call description of one face before it becomes a DevItem.
+struct ItemArgs {
+    int W, H, spp, edge_spp;
+    uint32_t flags, iteration, face;
+    const fr_params* p;
+    const fr_grads* g;          // may be null
+    float* image;
+    const float* adj;           // image-space adjoint (null: the slot's loss adjoint)
+    int32_t* tri_rec;
+    uint64_t* mask_rec;
+};
+
+DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
+    const Slot& sl = c->slots[k];
+    DevItem it;
+    std::memset(&it, 0, sizeof(it));
+    DevScene& s = it.S;
     s.N = c->N; s.T = c->T; s.K = c->K; s.NL = c->NL; s.E = c->E;
-    s.W = c->cfg.width; s.H = c->cfg.height; s.spp = c->cfg.spp; s.M = c->cfg.tex_size;
-    s.edge_spp = c->cfg.edge_spp;
-    s.flags = c->cfg.flags; s.seed = c->cfg.seed;
-    s.v = c->v_cam; s.vn = c->vn; s.uv = c->uv; s.faces = c->faces; s.nodes = c->nodes; s.tris = c->tris;
+    s.W = a.W; s.H = a.H; s.spp = a.spp; s.M = c->cfg.tex_size; s.edge_spp = a.edge_spp;
+    s.flags = a.flags; s.seed = c->cfg.seed;
+    s.v = sl.v_cam; s.vn = sl.vn; s.uv = c->uv; s.faces = c->faces; s.nodes = sl.nodes; s.tris = sl.tris;
     s.lights = c->lights; s.status = c->status; s.counters = c->counters;
-    return s;
+    const fr_params* p = a.p;
+    it.P = DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness};
+    it.G.d_v = sl.d_v;
+    it.G.d_n = sl.d_n;
+    it.G.small = sl.small;
+    if (a.g) {
+        it.G.diffuse = a.g->diffuse;
+        it.G.specular = a.g->specular;
+        it.G.roughness = a.g->roughness;
+        it.g_coef = a.g->coef;
+        it.g_rot = a.g->rot;
+        it.g_trans = a.g->trans;
+        it.g_focal = a.g->focal;
+        it.g_light = a.g->light_i;
+    }
+    it.EL.edges = c->edges;
+    it.EL.prim_list = sl.lists;
+    it.EL.prim_count = sl.counts;
+    it.EL.light_list = sl.lists + c->E;
+    it.EL.light_count = sl.counts + 1;
+    it.B = sl.B;
+    it.nodes = sl.nodes;
+    it.tris = sl.tris;
+    it.v_cam = sl.v_cam;
+    it.vn = sl.vn;
+    it.v_model = sl.v_model;
+    it.d_vmodel = sl.d_vmodel;
+    it.n_face = sl.n_face;
+    it.dm = sl.dm;
+    it.acc12 = sl.acc12;
+    it.sil_flags = sl.sil_flags;
+    it.image = a.image;
+    it.adj = a.adj ? a.adj : sl.adj_image;
+    it.tri_rec = a.tri_rec;
+    it.mask_rec = a.mask_rec;
+    it.iteration = a.iteration;
+    it.face = a.face;
+    return it;
 }
 
-DevParams params_of(const fr_params* p) {
-    return DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness};
+BlockMap map_of(const fr_ctx* c, int n, bool edges) {
+    BlockMap m;
+    m.n = n;
+    int b = 0;
+    for (int k = 0; k < n; ++k) {
+        const DevScene& s = c->h_items[k].S;
+        m.block0[k] = b;
+        long work = (long)s.W * s.H * (edges ? ((s.flags & FR_FLAG_NO_PRIMARY_EDGE) ? 0 : s.edge_spp) : s.spp);
+        b += (int)((work + 127) / 128);
+    }
+    m.block0[n] = b;
+    return m;
 }
 
-EdgeLists lists_of(const fr_ctx* c) {
-    EdgeLists L;
-    L.edges = c->edges;
-    L.prim_list = c->lists;
-    L.prim_count = c->counts;
-    L.light_list = c->lists + c->E;
-    L.light_count = c->counts + 1;
-    return L;
+// Upload the item table for items [0, n) (one small kernel on the stream).
+fr_status upload(fr_ctx* c, int n, cudaStream_t st) {
+    launch_set_items(c->h_items.data(), n, c->d_items, st);
+    CK(c, cudaGetLastError());
+    return FR_OK;
 }
 
 // morph -> pose -> face normals + Morton keys -> vertex normals -> LBVH
-fr_status build_geometry(fr_ctx* c, const fr_params* p, cudaStream_t st) {
-    if (c->K > 0) launch_morph(c->mean, c->basis, c->ld, c->K, p->coef, c->v_model, st);
-    else CK(c, cudaMemcpyAsync(c->v_model, c->mean, sizeof(float) * c->ld, cudaMemcpyDeviceToDevice, st));
-    launch_pose(c->v_model, c->N, p->rot, p->trans, c->v_cam, c->B.aabb, st);
-    launch_faces(c->v_cam, c->faces, c->T, c->B.aabb, c->n_face, c->B.keys, c->B.vals, st);
-    launch_vertex_normals(c->n_face, c->vf_off, c->vf_idx, c->N, c->vn, st);
-    launch_lbvh(c->v_cam, c->faces, c->T, c->B, c->nodes, c->tris, c->status, st);
-    CK(c, cudaGetLastError());
+void build_geometry(fr_ctx* c, int n, cudaStream_t st) {
+    launch_morph(c->mean, c->basis, c->ld, c->K, c->d_items, n, st);
+    launch_pose(c->d_items, n, c->N, st);
+    launch_faces(c->d_items, n, c->faces, c->T, st);
+    launch_vertex_normals(c->d_items, n, c->vf_off, c->vf_idx, c->N, st);
+    launch_lbvh(c->d_items, n, c->faces, c->T, c->status, st);
+}
+
+fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
+    for (int k = 0; k < n; ++k) {
+        const DevItem& it = c->h_items[k];
+        if (it.S.spp > 32) CK(c, cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)it.S.W * it.S.H, st));
+    }
+    launch_forward(c->d_items, map_of(c, n, false), st);
     return FR_OK;
 }
 
-// reverse pass given geometry already built for p
-fr_status adjoint_pass(fr_ctx* c, const fr_params* p, const float* adj_image, fr_grads* g, uint32_t iteration,
-                       uint32_t face, cudaStream_t st) {
-    const DevScene S = scene_of(c);
-    const DevParams P = params_of(p);
-    const EdgeLists EL = lists_of(c);
-    CK(c, cudaMemsetAsync(c->d_v, 0, sizeof(float) * 3 * (size_t)c->N, st));
-    CK(c, cudaMemsetAsync(c->d_n, 0, sizeof(float) * 3 * (size_t)c->N, st));
-    CK(c, cudaMemsetAsync(c->small, 0, sizeof(double) * (1 + 3 * FR_MAX_LIGHTS), st));
-    CK(c, cudaMemsetAsync(c->acc12, 0, sizeof(double) * 12, st));
-    const bool need_edges = !(c->cfg.flags & FR_FLAG_NO_PRIMARY_EDGE) || !(c->cfg.flags & FR_FLAG_NO_SHADOW_EDGE);
-    if (need_edges) launch_classify(S, EL, c->sil_flags, st);
+// reverse pass for items [0, n) whose geometry is built
+void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
+    launch_zero_accumulators(c->d_items, n, c->N, st);
+    bool need_edges = false;
+    for (int k = 0; k < n; ++k) {
+        const uint32_t f = c->h_items[k].S.flags;
+        need_edges |= !(f & FR_FLAG_NO_PRIMARY_EDGE) || !(f & FR_FLAG_NO_SHADOW_EDGE);
+    }
+    if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, st);
     mark(c, 4, st);
-    DevGrads G;
-    G.d_v = c->d_v;
-    G.d_n = c->d_n;
-    G.diffuse = g->diffuse;
-    G.specular = g->specular;
-    G.roughness = g->roughness;
-    G.small = c->small;
-    launch_adjoint(S, P, G, EL, adj_image, iteration, face, st);
+    launch_adjoint(c->d_items, map_of(c, n, false), st);
     mark(c, 5, st);
-    if (!(c->cfg.flags & FR_FLAG_NO_PRIMARY_EDGE) && c->cfg.edge_spp > 0)
-        launch_edge_primary(S, P, G, EL, adj_image, iteration, face, st);
+    launch_edge_primary(c->d_items, map_of(c, n, true), st);
     mark(c, 6, st);
-    launch_normals_adjoint(c->v_cam, c->vn, c->d_n, c->faces, c->vf_off, c->vf_idx, c->N, c->dm, c->d_v, st);
-    launch_pose_adjoint(c->v_model, c->N, c->ld, p->rot, p->trans, c->d_v, c->d_vmodel, c->acc12, st);
-    launch_pose_finish(p->rot, c->acc12, c->small, c->NL, g->rot, g->trans, g->focal, g->light_i, st);
-    if (g->coef) launch_morph_adjoint(c->basis, c->ld, c->K, 3 * c->N, c->d_vmodel, g->coef, st);
+    launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
+    launch_pose_adjoint(c->d_items, n, c->N, st);
+    launch_pose_finish(c->d_items, n, c->NL, st);
+    launch_morph_adjoint(c->basis, c->ld, c->K, 3 * c->N, c->d_items, n, st);
     mark(c, 7, st);
-    CK(c, cudaGetLastError());
+}
+
+LossTable loss_table(fr_ctx* c, int n, const float* const* targets, double* const* losses, bool adjoint) {
+    LossTable t;
+    t.n = n;
+    t.max_px3 = 0;
+    for (int k = 0; k < n; ++k) {
+        const DevItem& it = c->h_items[k];
+        const Slot& sl = c->slots[k];
+        t.it[k] = LossItem{it.S.H, it.S.W, it.image, targets[k], losses[k], sl.sign, nullptr,
+                           adjoint ? sl.adj_image : nullptr};
+        t.max_px3 = std::max(t.max_px3, it.S.H * it.S.W * 3);
+    }
+    return t;
+}
+
+fr_status alloc_slot(fr_ctx* c, Slot& sl) {
+    const int N = c->N, T = c->T;
+    TRY(dalloc(c, &sl.v_model, c->ld));
+    TRY(dalloc(c, &sl.d_vmodel, c->ld));
+    TRY(dalloc(c, &sl.v_cam, N));
+    TRY(dalloc(c, &sl.vn, N));
+    TRY(dalloc(c, &sl.n_face, T));
+    const int n_tiles = (T + 255) / 256;
+    TRY(dalloc(c, &sl.B.keys, T));
+    TRY(dalloc(c, &sl.B.keys_alt, T));
+    TRY(dalloc(c, &sl.B.vals, T));
+    TRY(dalloc(c, &sl.B.vals_alt, T));
+    TRY(dalloc(c, &sl.B.hist, 256 * (size_t)n_tiles));
+    TRY(dalloc(c, &sl.B.child, 2 * (size_t)std::max(T - 1, 1)));
+    TRY(dalloc(c, &sl.B.parent_int, std::max(T - 1, 1)));
+    TRY(dalloc(c, &sl.B.parent_leaf, T));
+    TRY(dalloc(c, &sl.B.flag, std::max(T - 1, 1)));
+    TRY(dalloc(c, &sl.B.box_int, 2 * (size_t)std::max(T - 1, 1)));
+    TRY(dalloc(c, &sl.B.box_leaf, 2 * (size_t)T));
+    TRY(dalloc(c, &sl.B.aabb, 6));
+    TRY(dalloc(c, &sl.nodes, std::max(T - 1, 1)));
+    TRY(dalloc(c, &sl.tris, 3 * (size_t)T));
+    TRY(dalloc(c, &sl.sil_flags, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
+    TRY(dalloc(c, &sl.lists, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
+    TRY(dalloc(c, &sl.counts, 1 + FR_MAX_LIGHTS));
+    TRY(dalloc(c, &sl.d_v, 3 * (size_t)N));
+    TRY(dalloc(c, &sl.d_n, 3 * (size_t)N));
+    TRY(dalloc(c, &sl.dm, 3 * (size_t)N));
+    TRY(dalloc(c, &sl.small, 1 + 3 * FR_MAX_LIGHTS));
+    TRY(dalloc(c, &sl.acc12, 12));
     return FR_OK;
 }
 
-fr_status alloc_scratch(fr_ctx* c) {
-    const int N = c->N, T = c->T;
-    TRY(dalloc(c, &c->v_model, c->ld));
-    TRY(dalloc(c, &c->d_vmodel, c->ld));
-    TRY(dalloc(c, &c->v_cam, N));
-    TRY(dalloc(c, &c->vn, N));
-    TRY(dalloc(c, &c->n_face, T));
-    const int n_tiles = (T + 255) / 256;
-    TRY(dalloc(c, &c->B.keys, T));
-    TRY(dalloc(c, &c->B.keys_alt, T));
-    TRY(dalloc(c, &c->B.vals, T));
-    TRY(dalloc(c, &c->B.vals_alt, T));
-    TRY(dalloc(c, &c->B.hist, 256 * (size_t)n_tiles));
-    TRY(dalloc(c, &c->B.child, 2 * (size_t)std::max(T - 1, 1)));
-    TRY(dalloc(c, &c->B.parent_int, std::max(T - 1, 1)));
-    TRY(dalloc(c, &c->B.parent_leaf, T));
-    TRY(dalloc(c, &c->B.flag, std::max(T - 1, 1)));
-    TRY(dalloc(c, &c->B.box_int, 2 * (size_t)std::max(T - 1, 1)));
-    TRY(dalloc(c, &c->B.box_leaf, 2 * (size_t)T));
-    TRY(dalloc(c, &c->B.aabb, 6));
-    TRY(dalloc(c, &c->nodes, std::max(T - 1, 1)));
-    TRY(dalloc(c, &c->tris, 3 * (size_t)T));
-    TRY(dalloc(c, &c->sil_flags, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
-    TRY(dalloc(c, &c->lists, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
-    TRY(dalloc(c, &c->counts, 1 + FR_MAX_LIGHTS));
-    TRY(dalloc(c, &c->d_v, 3 * (size_t)N));
-    TRY(dalloc(c, &c->d_n, 3 * (size_t)N));
-    TRY(dalloc(c, &c->dm, 3 * (size_t)N));
-    TRY(dalloc(c, &c->small, 1 + 3 * FR_MAX_LIGHTS));
-    TRY(dalloc(c, &c->acc12, 12));
+fr_status check_image_args(fr_ctx* c, int W, int H, int spp, int edge_spp) {
+    if (W < 1 || H < 1 || (long)W * H > (long)c->cfg.width * c->cfg.height)
+        return fail(c, FR_EINVAL, "item image larger than the context's width x height");
+    if (!is_pow2(spp) || spp > 1024) return fail(c, FR_EINVAL, "spp must be a power of two <= 1024");
+    if (edge_spp < 0 || edge_spp > 64) return fail(c, FR_EINVAL, "edge_spp out of range");
+    if ((long)W * H * spp > (1L << 31) - 1024) return fail(c, FR_EINVAL, "too many samples per item");
     return FR_OK;
+}
+
+ItemArgs single(fr_ctx* c, const fr_params* p, const fr_grads* g, float* image, const float* adj, uint32_t iteration,
+                uint32_t face) {
+    ItemArgs a;
+    a.W = c->cfg.width; a.H = c->cfg.height; a.spp = c->cfg.spp; a.edge_spp = c->cfg.edge_spp;
+    a.flags = c->cfg.flags; a.iteration = iteration; a.face = face;
+    a.p = p; a.g = g; a.image = image; a.adj = adj; a.tri_rec = nullptr; a.mask_rec = nullptr;
+    return a;
 }
 
 }  // namespace
@@ -232,13 +327,20 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
     if (cfg->edge_spp < 0 || cfg->edge_spp > 64) return fail(nullptr, FR_EINVAL, "edge_spp out of range");
     if ((long)cfg->width * cfg->height * cfg->spp > (1L << 31) - 1024)
         return fail(nullptr, FR_EINVAL, "too many samples per call");
+    if (cfg->max_batch < 0 || cfg->max_batch > FR_MAX_BATCH) return fail(nullptr, FR_EINVAL, "max_batch out of range");
     fr_ctx* c = new fr_ctx();
     c->cfg = *cfg;
-    if (dalloc(c, &c->status, 1) != FR_OK || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
-        dalloc(c, &c->counters, 9) != FR_OK ||
-        cudaMemset(c->counters, 0, 9 * sizeof(unsigned long long)) != cudaSuccess ||
-        dalloc(c, &c->sign, (size_t)cfg->width * cfg->height * 3) != FR_OK ||
-        dalloc(c, &c->adj_image, (size_t)cfg->width * cfg->height * 3) != FR_OK) {
+    c->max_batch = std::max(1, cfg->max_batch);
+    c->slots.resize(c->max_batch);
+    c->h_items.resize(FR_MAX_BATCH);
+    const size_t px = (size_t)cfg->width * cfg->height * 3;
+    bool ok = dalloc(c, &c->status, 1) == FR_OK && cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
+              dalloc(c, &c->counters, 9) == FR_OK &&
+              cudaMemset(c->counters, 0, 9 * sizeof(unsigned long long)) == cudaSuccess &&
+              dalloc(c, &c->d_items, FR_MAX_BATCH) == FR_OK;
+    for (int k = 0; ok && k < c->max_batch; ++k)
+        ok = dalloc(c, &c->slots[k].sign, px) == FR_OK && dalloc(c, &c->slots[k].adj_image, px) == FR_OK;
+    if (!ok) {
         g_err = c->err;
         free_all(c);
         delete c;
@@ -310,7 +412,7 @@ fr_status fr_set_mesh(fr_ctx* c, const fr_mesh* m) {
     CK(c, cudaMemcpy(c->vf_off, deg.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->vf_idx, vf.data(), sizeof(int) * 3 * (size_t)T, cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->edges, edges.data(), sizeof(int4) * c->E, cudaMemcpyHostToDevice));
-    TRY(alloc_scratch(c));
+    for (Slot& sl : c->slots) TRY(alloc_slot(c, sl));
     c->have_mesh = true;
     return FR_OK;
 }
@@ -351,8 +453,11 @@ fr_status fr_forward(fr_ctx* c, const fr_params* p, float* image, uint32_t itera
                      void* stream) {
     TRY(check_params(c, p));
     if (!image) return fail(c, FR_EINVAL, "null image");
-    TRY(build_geometry(c, p, S_(stream)));
-    launch_forward(scene_of(c), params_of(p), image, nullptr, nullptr, iteration, face_id, S_(stream));
+    const cudaStream_t st = S_(stream);
+    c->h_items[0] = make_item(c, 0, single(c, p, nullptr, image, nullptr, iteration, face_id));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
+    TRY(forward_pass(c, 1, st));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -361,14 +466,19 @@ fr_status fr_backward(fr_ctx* c, const fr_params* p, const float* adj_image, fr_
                       uint32_t face_id, void* stream) {
     TRY(check_params(c, p));
     if (!adj_image || !g) return fail(c, FR_EINVAL, "null argument");
-    TRY(build_geometry(c, p, S_(stream)));
-    return adjoint_pass(c, p, adj_image, g, iteration, face_id, S_(stream));
+    const cudaStream_t st = S_(stream);
+    c->h_items[0] = make_item(c, 0, single(c, p, g, nullptr, adj_image, iteration, face_id));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
+    adjoint_pass(c, 1, st);
+    CK(c, cudaGetLastError());
+    return FR_OK;
 }
 
 fr_status fr_loss(fr_ctx* c, const float* image, const float* target, double* loss, float* adj_image,
                   float* blurred, void* stream) {
     if (!c || !image || !target || !loss) return fail(c, FR_EINVAL, "null argument");
-    launch_loss(c->cfg.height, c->cfg.width, image, target, loss, c->sign, blurred, adj_image, S_(stream));
+    launch_loss(c->cfg.height, c->cfg.width, image, target, loss, c->slots[0].sign, blurred, adj_image, S_(stream));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -379,14 +489,61 @@ fr_status fr_render(fr_ctx* c, const fr_params* p, const float* target, float* i
     if (!image || !target || !loss) return fail(c, FR_EINVAL, "null argument");
     const cudaStream_t st = S_(stream);
     mark(c, 0, st);
-    TRY(build_geometry(c, p, st));
+    c->h_items[0] = make_item(c, 0, single(c, p, g, image, nullptr, iteration, face_id));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
     mark(c, 1, st);
-    launch_forward(scene_of(c), params_of(p), image, nullptr, nullptr, iteration, face_id, st);
+    TRY(forward_pass(c, 1, st));
     mark(c, 2, st);
-    launch_loss(c->cfg.height, c->cfg.width, image, target, loss, c->sign, nullptr, g ? c->adj_image : nullptr, st);
+    const float* tg[1] = {target};
+    double* ls[1] = {loss};
+    launch_loss(loss_table(c, 1, tg, ls, g != nullptr), st);
     mark(c, 3, st);
+    if (g) adjoint_pass(c, 1, st);
     CK(c, cudaGetLastError());
-    if (g) return adjoint_pass(c, p, c->adj_image, g, iteration, face_id, st);
+    return FR_OK;
+}
+
+fr_status fr_render_batch(fr_ctx* c, const fr_item* items, int32_t n, void* stream) {
+    if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (!items || n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch items required");
+    const cudaStream_t st = S_(stream);
+    bool any_grad = false;
+    const float* tg[FR_MAX_BATCH];
+    double* ls[FR_MAX_BATCH];
+    for (int k = 0; k < n; ++k) {
+        const fr_item& x = items[k];
+        TRY(check_params(c, &x.params));
+        TRY(check_image_args(c, x.width, x.height, x.spp, x.edge_spp));
+        if (!x.image || !x.target || !x.loss) return fail(c, FR_EINVAL, "null image, target or loss");
+        ItemArgs a;
+        a.W = x.width; a.H = x.height; a.spp = x.spp; a.edge_spp = x.edge_spp;
+        a.flags = x.flags; a.iteration = x.iteration; a.face = x.face_id;
+        a.p = &x.params; a.g = x.grads; a.image = x.image; a.adj = nullptr; a.tri_rec = nullptr;
+        a.mask_rec = nullptr;
+        c->h_items[k] = make_item(c, k, a);
+        tg[k] = x.target;
+        ls[k] = x.loss;
+        any_grad |= x.grads != nullptr;
+    }
+    mark(c, 0, st);
+    TRY(upload(c, n, st));
+    build_geometry(c, n, st);
+    mark(c, 1, st);
+    TRY(forward_pass(c, n, st));
+    mark(c, 2, st);
+    launch_loss(loss_table(c, n, tg, ls, any_grad), st);
+    mark(c, 3, st);
+    if (any_grad) {
+        // items without gradients run the reverse pass on a zero adjoint; their
+        // parameter outputs are null, so nothing is written for them
+        for (int k = 0; k < n; ++k)
+            if (!items[k].grads)
+                CK(c, cudaMemsetAsync(c->slots[k].adj_image, 0,
+                                      sizeof(float) * 3 * (size_t)items[k].width * items[k].height, st));
+        adjoint_pass(c, n, st);
+    }
+    CK(c, cudaGetLastError());
     return FR_OK;
 }
 
@@ -428,13 +585,16 @@ fr_status fr_philox(uint32_t k0, uint32_t k1, const uint32_t* counters, int32_t 
 
 fr_status fr_debug_geometry(fr_ctx* c, const fr_params* p, float* v_cam, float* n_vert, void* stream) {
     TRY(check_params(c, p));
-    TRY(build_geometry(c, p, S_(stream)));
+    const cudaStream_t st = S_(stream);
+    c->h_items[0] = make_item(c, 0, single(c, p, nullptr, nullptr, nullptr, 0, 0));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
     if (v_cam)
-        CK(c, cudaMemcpy2DAsync(v_cam, 3 * sizeof(float), c->v_cam, sizeof(float4), 3 * sizeof(float), c->N,
-                                cudaMemcpyDeviceToDevice, S_(stream)));
+        CK(c, cudaMemcpy2DAsync(v_cam, 3 * sizeof(float), c->slots[0].v_cam, sizeof(float4), 3 * sizeof(float), c->N,
+                                cudaMemcpyDeviceToDevice, st));
     if (n_vert)
-        CK(c, cudaMemcpy2DAsync(n_vert, 3 * sizeof(float), c->vn, sizeof(float4), 3 * sizeof(float), c->N,
-                                cudaMemcpyDeviceToDevice, S_(stream)));
+        CK(c, cudaMemcpy2DAsync(n_vert, 3 * sizeof(float), c->slots[0].vn, sizeof(float4), 3 * sizeof(float), c->N,
+                                cudaMemcpyDeviceToDevice, st));
     return FR_OK;
 }
 
@@ -442,8 +602,11 @@ fr_status fr_debug_trace(fr_ctx* c, const fr_params* p, const float* org, const 
                          int32_t* tri, float* t, void* stream) {
     TRY(check_params(c, p));
     if (!org || !dir || !tri || !t || n < 0) return fail(c, FR_EINVAL, "bad argument");
-    TRY(build_geometry(c, p, S_(stream)));
-    launch_trace_rays(scene_of(c), org, dir, n, tri, t, S_(stream));
+    const cudaStream_t st = S_(stream);
+    c->h_items[0] = make_item(c, 0, single(c, p, nullptr, nullptr, nullptr, 0, 0));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
+    launch_trace_rays(c->d_items, org, dir, n, tri, t, st);
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -452,8 +615,14 @@ fr_status fr_debug_records(fr_ctx* c, const fr_params* p, float* image, int32_t*
                            uint32_t iteration, uint32_t face_id, void* stream) {
     TRY(check_params(c, p));
     if (!image) return fail(c, FR_EINVAL, "null image");
-    TRY(build_geometry(c, p, S_(stream)));
-    launch_forward(scene_of(c), params_of(p), image, tri_rec, mask_rec, iteration, face_id, S_(stream));
+    const cudaStream_t st = S_(stream);
+    ItemArgs a = single(c, p, nullptr, image, nullptr, iteration, face_id);
+    a.tri_rec = tri_rec;
+    a.mask_rec = mask_rec;
+    c->h_items[0] = make_item(c, 0, a);
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
+    TRY(forward_pass(c, 1, st));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -461,15 +630,17 @@ fr_status fr_debug_records(fr_ctx* c, const fr_params* p, float* image, int32_t*
 fr_status fr_debug_silhouettes(fr_ctx* c, const fr_params* p, int32_t* prim, int32_t* n_prim, int32_t* per_light,
                                int32_t* counts, void* stream) {
     TRY(check_params(c, p));
-    TRY(build_geometry(c, p, S_(stream)));
-    const EdgeLists EL = lists_of(c);
-    launch_classify(scene_of(c), EL, c->sil_flags, S_(stream));
     const cudaStream_t st = S_(stream);
-    if (prim) CK(c, cudaMemcpyAsync(prim, c->lists, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, st));
-    if (n_prim) CK(c, cudaMemcpyAsync(n_prim, c->counts, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    c->h_items[0] = make_item(c, 0, single(c, p, nullptr, nullptr, nullptr, 0, 0));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
+    launch_classify(c->d_items, 1, c->E, c->NL, st);
+    const Slot& sl = c->slots[0];
+    if (prim) CK(c, cudaMemcpyAsync(prim, sl.lists, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, st));
+    if (n_prim) CK(c, cudaMemcpyAsync(n_prim, sl.counts, sizeof(int), cudaMemcpyDeviceToDevice, st));
     if (per_light)
-        CK(c, cudaMemcpyAsync(per_light, c->lists + c->E, sizeof(int) * (size_t)c->NL * c->E, cudaMemcpyDeviceToDevice, st));
-    if (counts) CK(c, cudaMemcpyAsync(counts, c->counts + 1, sizeof(int) * c->NL, cudaMemcpyDeviceToDevice, st));
+        CK(c, cudaMemcpyAsync(per_light, sl.lists + c->E, sizeof(int) * (size_t)c->NL * c->E, cudaMemcpyDeviceToDevice, st));
+    if (counts) CK(c, cudaMemcpyAsync(counts, sl.counts + 1, sizeof(int) * c->NL, cudaMemcpyDeviceToDevice, st));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -477,8 +648,11 @@ fr_status fr_debug_silhouettes(fr_ctx* c, const fr_params* p, int32_t* prim, int
 fr_status fr_debug_bvh(fr_ctx* c, const fr_params* p, int32_t* out, void* stream) {
     TRY(check_params(c, p));
     if (!out) return fail(c, FR_EINVAL, "null out");
-    TRY(build_geometry(c, p, S_(stream)));
-    launch_bvh_check(c->nodes, c->B, c->T, out, S_(stream));
+    const cudaStream_t st = S_(stream);
+    c->h_items[0] = make_item(c, 0, single(c, p, nullptr, nullptr, nullptr, 0, 0));
+    TRY(upload(c, 1, st));
+    build_geometry(c, 1, st);
+    launch_bvh_check(c->d_items, c->T, out, st);
     CK(c, cudaGetLastError());
     return FR_OK;
 }

@@ -131,6 +131,69 @@ struct DevGrads {
     double* small;         // [1 + 3 N_L]: focal, then light intensities (FP64)
 };
 
+struct BvhScratch {
+    uint32_t *keys, *keys_alt;
+    int *vals, *vals_alt;
+    int* hist;           // [256][n_tiles]
+    int* child;          // [2 (T - 1)] child codes of internal nodes
+    int* parent_int;     // [T - 1]
+    int* parent_leaf;    // [T]
+    int* flag;           // [T - 1]
+    float4* box_int;     // [2 (T - 1)] lo, hi
+    float4* box_leaf;    // [2 T]
+    unsigned* aabb;      // [6] ordered-int scene bounds
+};
+
+struct EdgeLists {
+    const int4* edges;   // [E] (a, b, f1, f2), a < b, f2 = -1 on the boundary (shared)
+    int* prim_list;      // [E]   ordered primary silhouettes (compacted list 0)
+    int* prim_count;     // [1]
+    int* light_list;     // [NL][E] ordered shadow candidates (lists 1..NL)
+    int* light_count;    // [NL]
+};
+
+constexpr int FR_MAX_BATCH = 32;
+
+// Everything one face of a batched call needs: its slot's geometry and scratch,
+// its image configuration, its parameters and where its results go.  The table
+// of items lives in device memory; every kernel of a call reads its item from it
+// (geometry kernels by blockIdx.y, ray kernels through a BlockMap).
+struct DevItem {
+    DevScene S;             // slot geometry (read side) + W, H, spp, edge_spp, flags, seed
+    DevParams P;
+    DevGrads G;             // d_v, d_n (slot), texture gradients (caller), small (slot)
+    EdgeLists EL;
+    BvhScratch B;
+    BvhNode* nodes;         // slot BVH (write side of S.nodes)
+    float4* tris;           // slot triangles (write side of S.tris)
+    float4* v_cam;          // write side of S.v
+    float4* vn;             // write side of S.vn
+    float* v_model;
+    float* d_vmodel;
+    float4* n_face;
+    float* dm;
+    double* acc12;
+    uint8_t* sil_flags;
+    float* image;
+    const float* adj;       // image-space adjoint read by the ray kernels
+    int32_t* tri_rec;
+    uint64_t* mask_rec;
+    float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
+    uint32_t iteration, face;
+};
+
+// Blocks [block0[k], block0[k+1]) of a ray launch belong to item k.
+struct BlockMap {
+    int n;
+    int block0[FR_MAX_BATCH + 1];
+};
+
+FR_D int item_of_block(const BlockMap& m) {
+    int k = 0;
+    while (k + 1 < m.n && (int)blockIdx.x >= m.block0[k + 1]) ++k;
+    return k;
+}
+
 FR_D void set_status(int* status, int bit) { atomicOr(status, bit); }
 
 // Warp-aggregated atomic add: lanes sharing `key` sum first, one lane adds.

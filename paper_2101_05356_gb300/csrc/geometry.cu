@@ -1,6 +1,7 @@
 // Morph (Sec. 3.1: v = a_s + Sigma_s alpha + Sigma_e delta), pose
 // (Gamma(v) = R^-1 (v - T)), face/vertex normals, Morton keys, and the reverse
-// of each step (normals, pose, morph transpose with FP64 reductions).
+// of each step (normals, pose, morph transpose with FP64 reductions).  Every
+// kernel is batched over the items of a call through blockIdx.y.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,13 +18,38 @@ FR_D void euler_R(const float* rot, float R[9]) {
     R[6] = -sy;     R[7] = cy * sx;                R[8] = cy * cx;
 }
 
+struct ItemsParam {
+    int n;
+    DevItem it[FR_MAX_BATCH];
+};
+
+__global__ void k_set_items(ItemsParam p, DevItem* out) {
+    const int words = (int)(sizeof(DevItem) / sizeof(int));
+    for (int k = 0; k < p.n; ++k) {
+        const int* src = reinterpret_cast<const int*>(&p.it[k]);
+        int* dst = reinterpret_cast<int*>(&out[k]);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    }
+}
+
+// per-item accumulators of the adjoint: dE/dv', dE/dn, FP64 partials
+__global__ void k_zero_acc(const DevItem* items, int N) {
+    const DevItem& it = items[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3 * N) { it.G.d_v[i] = 0.0f; it.G.d_n[i] = 0.0f; }
+    if (blockIdx.x == 0) {
+        for (int k = threadIdx.x; k < 1 + 3 * FR_MAX_LIGHTS; k += blockDim.x) it.G.small[k] = 0.0;
+        if (threadIdx.x < 12) it.acc12[threadIdx.x] = 0.0;
+    }
+}
+
 // Coalesced, float4-vectorised morph: thread i owns float4 i of the padded
 // [3N] vector; coefficients sit in shared memory; basis rows are 16-B aligned.
 __global__ void __launch_bounds__(256) k_morph(const float4* __restrict__ mean, const float* __restrict__ basis,
-                                               int ld4, int K, const float* __restrict__ coef,
-                                               float4* __restrict__ out) {
+                                               int ld4, int K, const DevItem* items) {
     __shared__ float c[FR_MAX_BASIS];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = coef[k];
+    const DevItem& it = items[blockIdx.y];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = it.P.coef[k];
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ld4) return;
@@ -31,18 +57,23 @@ __global__ void __launch_bounds__(256) k_morph(const float4* __restrict__ mean, 
     const float4* b = reinterpret_cast<const float4*>(basis) + i;
     int k = 0;
     for (; k + 4 <= K; k += 4) {
-        const float4 b0 = __ldcs(b + (size_t)(k + 0) * ld4), b1 = __ldcs(b + (size_t)(k + 1) * ld4);
-        const float4 b2 = __ldcs(b + (size_t)(k + 2) * ld4), b3 = __ldcs(b + (size_t)(k + 3) * ld4);
+        const float4 b0 = __ldg(b + (size_t)(k + 0) * ld4), b1 = __ldg(b + (size_t)(k + 1) * ld4);
+        const float4 b2 = __ldg(b + (size_t)(k + 2) * ld4), b3 = __ldg(b + (size_t)(k + 3) * ld4);
         acc.x += c[k] * b0.x + c[k + 1] * b1.x + c[k + 2] * b2.x + c[k + 3] * b3.x;
         acc.y += c[k] * b0.y + c[k + 1] * b1.y + c[k + 2] * b2.y + c[k + 3] * b3.y;
         acc.z += c[k] * b0.z + c[k + 1] * b1.z + c[k + 2] * b2.z + c[k + 3] * b3.z;
         acc.w += c[k] * b0.w + c[k + 1] * b1.w + c[k + 2] * b2.w + c[k + 3] * b3.w;
     }
     for (; k < K; ++k) {
-        const float4 bk = __ldcs(b + (size_t)k * ld4);
+        const float4 bk = __ldg(b + (size_t)k * ld4);
         acc.x += c[k] * bk.x; acc.y += c[k] * bk.y; acc.z += c[k] * bk.z; acc.w += c[k] * bk.w;
     }
-    out[i] = acc;
+    reinterpret_cast<float4*>(it.v_model)[i] = acc;
+}
+
+__global__ void k_copy_mean(const float4* __restrict__ mean, int ld4, const DevItem* items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ld4) reinterpret_cast<float4*>(items[blockIdx.y].v_model)[i] = mean[i];
 }
 
 FR_D unsigned ordered(float f) {
@@ -53,36 +84,38 @@ FR_D float unordered(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-__global__ void k_aabb_reset(unsigned* aabb) {
+__global__ void k_aabb_reset(const DevItem* items) {
+    unsigned* aabb = items[blockIdx.x].B.aabb;
     if (threadIdx.x < 3) aabb[threadIdx.x] = 0xffffffffu;
     else if (threadIdx.x < 6) aabb[threadIdx.x] = 0u;
 }
 
-__global__ void __launch_bounds__(256) k_pose(const float* __restrict__ v_model, int N, const float* rot,
-                                              const float* trans, float4* __restrict__ v_cam, unsigned* aabb) {
+__global__ void __launch_bounds__(256) k_pose(const DevItem* items, int N) {
     __shared__ float R[9], T[3];
     __shared__ unsigned bmin[3], bmax[3];
+    const DevItem& it = items[blockIdx.y];
     if (threadIdx.x == 0) {
-        euler_R(rot, R);
-        T[0] = trans[0]; T[1] = trans[1]; T[2] = trans[2];
+        euler_R(it.P.rot, R);
+        T[0] = it.P.trans[0]; T[1] = it.P.trans[1]; T[2] = it.P.trans[2];
         for (int k = 0; k < 3; ++k) { bmin[k] = 0xffffffffu; bmax[k] = 0u; }
     }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
-        const float wx = v_model[3 * i] - T[0], wy = v_model[3 * i + 1] - T[1], wz = v_model[3 * i + 2] - T[2];
+        const float* vm = it.v_model;
+        const float wx = vm[3 * i] - T[0], wy = vm[3 * i + 1] - T[1], wz = vm[3 * i + 2] - T[2];
         // v' = R^T w
         const float x = R[0] * wx + R[3] * wy + R[6] * wz;
         const float y = R[1] * wx + R[4] * wy + R[7] * wz;
         const float z = R[2] * wx + R[5] * wy + R[8] * wz;
-        v_cam[i] = make_float4(x, y, z, 0.0f);
+        it.v_cam[i] = make_float4(x, y, z, 0.0f);
         atomicMin(&bmin[0], ordered(x)); atomicMin(&bmin[1], ordered(y)); atomicMin(&bmin[2], ordered(z));
         atomicMax(&bmax[0], ordered(x)); atomicMax(&bmax[1], ordered(y)); atomicMax(&bmax[2], ordered(z));
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        atomicMin(&aabb[threadIdx.x], bmin[threadIdx.x]);
-        atomicMax(&aabb[3 + threadIdx.x], bmax[threadIdx.x]);
+        atomicMin(&it.B.aabb[threadIdx.x], bmin[threadIdx.x]);
+        atomicMax(&it.B.aabb[3 + threadIdx.x], bmax[threadIdx.x]);
     }
 }
 
@@ -95,15 +128,16 @@ FR_D uint32_t spread10(uint32_t x) {
     return x;
 }
 
-__global__ void __launch_bounds__(256) k_faces(const float4* __restrict__ v, const int4* __restrict__ faces, int T,
-                                               const unsigned* aabb, float4* __restrict__ n_face,
-                                               uint32_t* __restrict__ keys, int* __restrict__ vals) {
+__global__ void __launch_bounds__(256) k_faces(const DevItem* items, const int4* __restrict__ faces, int T) {
+    const DevItem& it = items[blockIdx.y];
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= T) return;
     const int4 t = faces[f];
+    const float4* v = it.v_cam;
     const float3 a = xyz(v[t.x]), b = xyz(v[t.y]), c = xyz(v[t.z]);
     const float3 n = cross(b - a, c - a);
-    n_face[f] = make_float4(n.x, n.y, n.z, 0.0f);
+    it.n_face[f] = make_float4(n.x, n.y, n.z, 0.0f);
+    const unsigned* aabb = it.B.aabb;
     const float3 lo = f3(unordered(aabb[0]), unordered(aabb[1]), unordered(aabb[2]));
     const float3 hi = f3(unordered(aabb[3]), unordered(aabb[4]), unordered(aabb[5]));
     const float3 cen = (a + b + c) * (1.0f / 3.0f);
@@ -115,43 +149,47 @@ __global__ void __launch_bounds__(256) k_faces(const float4* __restrict__ v, con
         const uint32_t q = min((uint32_t)(u * 1024.0f), 1023u);
         code |= spread10(q) << (2 - k);
     }
-    keys[f] = code;
-    vals[f] = f;
+    it.B.keys[f] = code;
+    it.B.vals[f] = f;
 }
 
 // Vertex normal = normalised sum of its faces' un-normalised normals, gathered
 // in face-index order through the vertex->face CSR (no atomics).  w = |sum|.
-__global__ void __launch_bounds__(256) k_vertex_normals(const float4* __restrict__ n_face, const int* __restrict__ off,
-                                                        const int* __restrict__ idx, int N, float4* __restrict__ vn) {
+__global__ void __launch_bounds__(256) k_vertex_normals(const DevItem* items, const int* __restrict__ off,
+                                                        const int* __restrict__ idx, int N) {
+    const DevItem& it = items[blockIdx.y];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float3 m = f3(0.0f, 0.0f, 0.0f);
-    for (int k = off[i]; k < off[i + 1]; ++k) m += xyz(n_face[idx[k]]);
+    for (int k = off[i]; k < off[i + 1]; ++k) m += xyz(it.n_face[idx[k]]);
     const float len = length(m);
     const float inv = len > 0.0f ? 1.0f / len : 0.0f;
-    vn[i] = make_float4(m.x * inv, m.y * inv, m.z * inv, len);
+    it.vn[i] = make_float4(m.x * inv, m.y * inv, m.z * inv, len);
 }
 
 // dE/dm_i = (I - n n^T) dE/dn_i / |m_i|
-__global__ void k_normals_adj_a(const float4* __restrict__ vn, const float* __restrict__ d_n, int N,
-                                float* __restrict__ dm) {
+__global__ void k_normals_adj_a(const DevItem* items, int N) {
+    const DevItem& it = items[blockIdx.y];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float4 n4 = vn[i];
+    const float4 n4 = it.vn[i];
     const float3 n = xyz(n4);
+    const float* d_n = it.G.d_n;
     const float3 g = f3(d_n[3 * i], d_n[3 * i + 1], d_n[3 * i + 2]);
     const float inv = n4.w > 0.0f ? 1.0f / n4.w : 0.0f;
     const float3 r = (g - n * dot(n, g)) * inv;
-    dm[3 * i] = r.x; dm[3 * i + 1] = r.y; dm[3 * i + 2] = r.z;
+    it.dm[3 * i] = r.x; it.dm[3 * i + 1] = r.y; it.dm[3 * i + 2] = r.z;
 }
 
 // Face normal n_f = (b - a) x (c - a) feeds m of its three vertices; gather the
 // cross-product adjoint back to each vertex over its faces.
-__global__ void k_normals_adj_b(const float4* __restrict__ v, const int4* __restrict__ faces,
-                                const int* __restrict__ off, const int* __restrict__ idx, int N,
-                                const float* __restrict__ dm, float* __restrict__ d_v) {
+__global__ void k_normals_adj_b(const DevItem* items, const int4* __restrict__ faces, const int* __restrict__ off,
+                                const int* __restrict__ idx, int N) {
+    const DevItem& it = items[blockIdx.y];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const float* dm = it.dm;
+    const float4* v = it.v_cam;
     float3 acc = f3(0.0f, 0.0f, 0.0f);
     for (int k = off[i]; k < off[i + 1]; ++k) {
         const int4 t = faces[idx[k]];
@@ -164,32 +202,35 @@ __global__ void k_normals_adj_b(const float4* __restrict__ v, const int4* __rest
         else if (i == t.y) acc += gu;
         else acc += gw;
     }
+    float* d_v = it.G.d_v;
     d_v[3 * i] += acc.x;
     d_v[3 * i + 1] += acc.y;
     d_v[3 * i + 2] += acc.z;
 }
 
 // dE/dv = R dE/dv'; accumulates M'[r][c] = sum_i g_r w_c and sum_i g (FP64).
-__global__ void __launch_bounds__(256) k_pose_adj(const float* __restrict__ v_model, int N, const float* rot,
-                                                  const float* trans, const float* __restrict__ d_v,
-                                                  float* __restrict__ d_vmodel, double* acc12) {
+__global__ void __launch_bounds__(256) k_pose_adj(const DevItem* items, int N) {
     __shared__ float R[9], T[3];
     __shared__ double part[8][12];
+    const DevItem& it = items[blockIdx.y];
     if (threadIdx.x == 0) {
-        euler_R(rot, R);
-        T[0] = trans[0]; T[1] = trans[1]; T[2] = trans[2];
+        euler_R(it.P.rot, R);
+        T[0] = it.P.trans[0]; T[1] = it.P.trans[1]; T[2] = it.P.trans[2];
     }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double loc[12];
     for (int k = 0; k < 12; ++k) loc[k] = 0.0;
     if (i < N) {
+        const float* d_v = it.G.d_v;
+        const float* vm = it.v_model;
         const float g[3] = {d_v[3 * i], d_v[3 * i + 1], d_v[3 * i + 2]};
-        const float w[3] = {v_model[3 * i] - T[0], v_model[3 * i + 1] - T[1], v_model[3 * i + 2] - T[2]};
+        const float w[3] = {vm[3 * i] - T[0], vm[3 * i + 1] - T[1], vm[3 * i + 2] - T[2]};
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c) loc[3 * r + c] = (double)g[r] * (double)w[c];
         for (int r = 0; r < 3; ++r) loc[9 + r] = g[r];
-        for (int c = 0; c < 3; ++c) d_vmodel[3 * i + c] = R[3 * c + 0] * g[0] + R[3 * c + 1] * g[1] + R[3 * c + 2] * g[2];
+        for (int c = 0; c < 3; ++c)
+            it.d_vmodel[3 * i + c] = R[3 * c + 0] * g[0] + R[3 * c + 1] * g[1] + R[3 * c + 2] * g[2];
     }
     for (int k = 0; k < 12; ++k)
         for (int o = 16; o > 0; o >>= 1) loc[k] += __shfl_xor_sync(0xffffffffu, loc[k], o);
@@ -199,17 +240,19 @@ __global__ void __launch_bounds__(256) k_pose_adj(const float* __restrict__ v_mo
     if (threadIdx.x < 12) {
         double s = 0.0;
         for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += part[wv][threadIdx.x];
-        atomicAdd(&acc12[threadIdx.x], s);
+        atomicAdd(&it.acc12[threadIdx.x], s);
     }
 }
 
 // dE/dtheta_a = sum_rc M'[r][c] dR[c][r]/dtheta_a ; dE/dT = -R sum g; plus the
-// FP64 focal and light-intensity accumulators.
-__global__ void k_pose_finish(const float* rot, const double* acc12, const double* small, int NL, float* g_rot,
-                              float* g_trans, float* g_focal, float* g_light) {
+// FP64 focal and light-intensity accumulators.  One block per item.
+__global__ void k_pose_finish(const DevItem* items, int NL) {
+    const DevItem& it = items[blockIdx.x];
     const int t = threadIdx.x;
+    const double* acc12 = it.acc12;
+    const double* small = it.G.small;
     if (t == 0) {
-        const double a = rot[0], b = rot[1], c = rot[2];
+        const double a = it.P.rot[0], b = it.P.rot[1], c = it.P.rot[2];
         const double sx = sin(a), cx = cos(a), sy = sin(b), cy = cos(b), sz = sin(c), cz = cos(c);
         double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx}, dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
         double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy}, dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
@@ -231,34 +274,37 @@ __global__ void k_pose_finish(const float* rot, const double* acc12, const doubl
             double s = 0.0;
             for (int r = 0; r < 3; ++r)
                 for (int c2 = 0; c2 < 3; ++c2) s += acc12[3 * r + c2] * D[q][3 * c2 + r];
-            if (g_rot) g_rot[q] += (float)s;
+            if (it.g_rot) it.g_rot[q] += (float)s;
         }
         for (int c2 = 0; c2 < 3; ++c2) {
             double s = 0.0;
             for (int r = 0; r < 3; ++r) s += R[3 * c2 + r] * acc12[9 + r];
-            if (g_trans) g_trans[c2] += (float)(-s);
+            if (it.g_trans) it.g_trans[c2] += (float)(-s);
         }
-        if (g_focal) g_focal[0] += (float)small[0];
+        if (it.g_focal) it.g_focal[0] += (float)small[0];
     }
-    if (g_light)
-        for (int k = t; k < 3 * NL; k += blockDim.x) g_light[k] += (float)small[1 + k];
+    if (it.g_light)
+        for (int k = t; k < 3 * NL; k += blockDim.x) it.g_light[k] += (float)small[1 + k];
 }
 
-// dE/dcoef_k = sum_i basis[k][i] dE/dv_i, one block per k, FP64 accumulation.
+// dE/dcoef_k = sum_i basis[k][i] dE/dv_i, one block per (k, item), FP64 accumulation.
 __global__ void __launch_bounds__(512) k_morph_adj(const float* __restrict__ basis, int ld4, int n3,
-                                                   const float* __restrict__ d_vmodel, float* g_coef) {
+                                                   const DevItem* items) {
     __shared__ double part[16];
+    const DevItem& it = items[blockIdx.y];
+    if (!it.g_coef) return;
     const int k = blockIdx.x;
     const float4* b = reinterpret_cast<const float4*>(basis) + (size_t)k * ld4;
+    const float* dv = it.d_vmodel;
     double acc = 0.0;
     for (int i = threadIdx.x; i < ld4; i += blockDim.x) {
-        const float4 bb = __ldcs(b + i);
+        const float4 bb = __ldg(b + i);
         const int e = 4 * i;
         float s = 0.0f;
-        if (e + 0 < n3) s += bb.x * d_vmodel[e + 0];
-        if (e + 1 < n3) s += bb.y * d_vmodel[e + 1];
-        if (e + 2 < n3) s += bb.z * d_vmodel[e + 2];
-        if (e + 3 < n3) s += bb.w * d_vmodel[e + 3];
+        if (e + 0 < n3) s += bb.x * dv[e + 0];
+        if (e + 1 < n3) s += bb.y * dv[e + 1];
+        if (e + 2 < n3) s += bb.z * dv[e + 2];
+        if (e + 3 < n3) s += bb.w * dv[e + 3];
         acc += (double)s;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -267,7 +313,7 @@ __global__ void __launch_bounds__(512) k_morph_adj(const float* __restrict__ bas
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        g_coef[k] += (float)s;
+        it.g_coef[k] += (float)s;
     }
 }
 
@@ -280,58 +326,65 @@ int nb(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_morph(const float* mean, const float* basis, int ld, int K, const float* coef, float* v_model,
+void launch_set_items(const DevItem* host_items, int n, DevItem* dev_items, cudaStream_t st) {
+    ItemsParam p;
+    p.n = n;
+    for (int k = 0; k < n; ++k) p.it[k] = host_items[k];
+    k_set_items<<<1, 256, 0, st>>>(p, dev_items);
+    fr_count_launches(1);
+}
+
+void launch_zero_accumulators(const DevItem* items, int n, int N, cudaStream_t st) {
+    k_zero_acc<<<dim3(nb(3 * (long)N, 256), n), 256, 0, st>>>(items, N);
+    fr_count_launches(1);
+}
+
+void launch_morph(const float* mean, const float* basis, int ld, int K, const DevItem* items, int n,
                   cudaStream_t st) {
     const int ld4 = ld / 4;
-    k_morph<<<nb(ld4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), basis, ld4, K, coef,
-                                          reinterpret_cast<float4*>(v_model));
+    if (K > 0) k_morph<<<dim3(nb(ld4, 256), n), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), basis, ld4, K, items);
+    else k_copy_mean<<<dim3(nb(ld4, 256), n), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), ld4, items);
     fr_count_launches(1);
 }
 
-void launch_pose(const float* v_model, int N, const float* rot, const float* trans, float4* v_cam,
-                 unsigned* aabb, cudaStream_t st) {
-    k_aabb_reset<<<1, 32, 0, st>>>(aabb);
-    k_pose<<<nb(N, 256), 256, 0, st>>>(v_model, N, rot, trans, v_cam, aabb);
+void launch_pose(const DevItem* items, int n, int N, cudaStream_t st) {
+    k_aabb_reset<<<n, 32, 0, st>>>(items);
+    k_pose<<<dim3(nb(N, 256), n), 256, 0, st>>>(items, N);
     fr_count_launches(2);
 }
 
-void launch_faces(const float4* v_cam, const int4* faces, int T, const unsigned* aabb, float4* n_face,
-                  uint32_t* keys, int* vals, cudaStream_t st) {
-    k_faces<<<nb(T, 256), 256, 0, st>>>(v_cam, faces, T, aabb, n_face, keys, vals);
+void launch_faces(const DevItem* items, int n, const int4* faces, int T, cudaStream_t st) {
+    k_faces<<<dim3(nb(T, 256), n), 256, 0, st>>>(items, faces, T);
     fr_count_launches(1);
 }
 
-void launch_vertex_normals(const float4* n_face, const int* vf_off, const int* vf_idx, int N, float4* vn,
+void launch_vertex_normals(const DevItem* items, int n, const int* vf_off, const int* vf_idx, int N,
                            cudaStream_t st) {
-    k_vertex_normals<<<nb(N, 256), 256, 0, st>>>(n_face, vf_off, vf_idx, N, vn);
+    k_vertex_normals<<<dim3(nb(N, 256), n), 256, 0, st>>>(items, vf_off, vf_idx, N);
     fr_count_launches(1);
 }
 
-void launch_normals_adjoint(const float4* v_cam, const float4* vn, const float* d_n, const int4* faces,
-                            const int* vf_off, const int* vf_idx, int N, float* dm, float* d_v,
-                            cudaStream_t st) {
-    k_normals_adj_a<<<nb(N, 256), 256, 0, st>>>(vn, d_n, N, dm);
-    k_normals_adj_b<<<nb(N, 256), 256, 0, st>>>(v_cam, faces, vf_off, vf_idx, N, dm, d_v);
+void launch_normals_adjoint(const DevItem* items, int n, const int4* faces, const int* vf_off,
+                            const int* vf_idx, int N, cudaStream_t st) {
+    k_normals_adj_a<<<dim3(nb(N, 256), n), 256, 0, st>>>(items, N);
+    k_normals_adj_b<<<dim3(nb(N, 256), n), 256, 0, st>>>(items, faces, vf_off, vf_idx, N);
     fr_count_launches(2);
 }
 
-void launch_pose_adjoint(const float* v_model, int N, int ld, const float* rot, const float* trans,
-                         const float* d_v, float* d_vmodel, double* acc12, cudaStream_t st) {
-    (void)ld;
-    k_pose_adj<<<nb(N, 256), 256, 0, st>>>(v_model, N, rot, trans, d_v, d_vmodel, acc12);
+void launch_pose_adjoint(const DevItem* items, int n, int N, cudaStream_t st) {
+    k_pose_adj<<<dim3(nb(N, 256), n), 256, 0, st>>>(items, N);
     fr_count_launches(1);
 }
 
-void launch_pose_finish(const float* rot, const double* acc12, const double* small, int NL, float* g_rot,
-                        float* g_trans, float* g_focal, float* g_light, cudaStream_t st) {
-    k_pose_finish<<<1, 64, 0, st>>>(rot, acc12, small, NL, g_rot, g_trans, g_focal, g_light);
+void launch_pose_finish(const DevItem* items, int n, int NL, cudaStream_t st) {
+    k_pose_finish<<<n, 64, 0, st>>>(items, NL);
     fr_count_launches(1);
 }
 
-void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const float* d_vmodel, float* g_coef,
+void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const DevItem* items, int n,
                           cudaStream_t st) {
     if (K <= 0) return;
-    k_morph_adj<<<K, 512, 0, st>>>(basis, ld / 4, n3, d_vmodel, g_coef);
+    k_morph_adj<<<dim3(K, n), 512, 0, st>>>(basis, ld / 4, n3, items);
     fr_count_launches(1);
 }
 

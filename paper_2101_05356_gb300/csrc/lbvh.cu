@@ -10,9 +10,12 @@ namespace {
 
 constexpr int SORT_TILE = 256;
 
-__global__ void __launch_bounds__(SORT_TILE) k_hist(const uint32_t* __restrict__ keys, int n, int shift,
-                                                    int n_tiles, int* __restrict__ hist) {
+__global__ void __launch_bounds__(SORT_TILE) k_hist(const DevItem* items, int pass, int n, int shift,
+                                                    int n_tiles) {
     __shared__ int h[256];
+    const BvhScratch& B = items[blockIdx.y].B;
+    const uint32_t* keys = (pass & 1) ? B.keys_alt : B.keys;
+    int* hist = B.hist;
     h[threadIdx.x] = 0;
     __syncthreads();
     const int i = blockIdx.x * SORT_TILE + threadIdx.x;
@@ -22,8 +25,9 @@ __global__ void __launch_bounds__(SORT_TILE) k_hist(const uint32_t* __restrict__
 }
 
 // exclusive scan of hist[256 * n_tiles] in place (digit-major), one block
-__global__ void __launch_bounds__(1024) k_scan(int* hist, int m) {
+__global__ void __launch_bounds__(1024) k_scan(const DevItem* items, int m) {
     __shared__ int warp_sum[32];
+    int* hist = items[blockIdx.x].B.hist;
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -57,10 +61,15 @@ __global__ void __launch_bounds__(1024) k_scan(int* hist, int m) {
 
 // Stable scatter: rank among equal digits = earlier warps' counts + earlier
 // lanes of the same warp with that digit.
-__global__ void __launch_bounds__(SORT_TILE) k_scatter(const uint32_t* __restrict__ keys, const int* __restrict__ vals,
-                                                       int n, int shift, int n_tiles, const int* __restrict__ off,
-                                                       uint32_t* __restrict__ keys_out, int* __restrict__ vals_out) {
+__global__ void __launch_bounds__(SORT_TILE) k_scatter(const DevItem* items, int pass, int n, int shift,
+                                                       int n_tiles) {
     constexpr int NW = SORT_TILE / 32;
+    const BvhScratch& B = items[blockIdx.y].B;
+    const uint32_t* keys = (pass & 1) ? B.keys_alt : B.keys;
+    const int* vals = (pass & 1) ? B.vals_alt : B.vals;
+    uint32_t* keys_out = (pass & 1) ? B.keys : B.keys_alt;
+    int* vals_out = (pass & 1) ? B.vals : B.vals_alt;
+    const int* off = B.hist;
     __shared__ int cnt[NW][256];
     for (int k = threadIdx.x; k < NW * 256; k += SORT_TILE) (&cnt[0][0])[k] = 0;
     __syncthreads();
@@ -99,9 +108,12 @@ FR_D int delta(const uint32_t* k, int n, int i, int j) {
 
 // Karras 2012: internal node i covers a key range found from the direction of
 // the larger common prefix and split at the highest differing bit.
-__global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ k, int n, int* __restrict__ child,
-                                                int* __restrict__ parent_int, int* __restrict__ parent_leaf,
-                                                int* status) {
+__global__ void __launch_bounds__(256) k_karras(const DevItem* items, int n, int* status) {
+    const BvhScratch& B = items[blockIdx.y].B;
+    const uint32_t* k = B.keys;
+    int* child = B.child;
+    int* parent_int = B.parent_int;
+    int* parent_leaf = B.parent_leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -133,13 +145,34 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ k, 
     if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
 }
 
+// flags 0; parents and child codes -1 (an unwritten child reads as leaf 0,
+// never as an ancestor)
+__global__ void k_bvh_init(const DevItem* items, int n) {
+    const BvhScratch& B = items[blockIdx.y].B;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n - 1) {
+        B.flag[i] = 0;
+        B.parent_int[i] = -1;
+        B.child[2 * i] = -1;
+        B.child[2 * i + 1] = -1;
+    }
+    if (i < n) B.parent_leaf[i] = -1;
+}
+
 // Leaf boxes + sorted triangle records, then climb: the second child to arrive
 // at a node merges both boxes and continues upward.
-__global__ void __launch_bounds__(256) k_boxes(const float4* __restrict__ v, const int4* __restrict__ faces,
-                                               const int* __restrict__ vals, int n, const int* __restrict__ child,
-                                               const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
-                                               int* flag, float4* box_int, float4* box_leaf, float4* __restrict__ tris,
+__global__ void __launch_bounds__(256) k_boxes(const DevItem* items, const int4* __restrict__ faces, int n,
                                                int* status) {
+    const DevItem& it = items[blockIdx.y];
+    const float4* v = it.v_cam;
+    const int* vals = it.B.vals;
+    const int* child = it.B.child;
+    const int* parent_int = it.B.parent_int;
+    const int* parent_leaf = it.B.parent_leaf;
+    int* flag = it.B.flag;
+    float4* box_int = it.B.box_int;
+    float4* box_leaf = it.B.box_leaf;
+    float4* tris = it.tris;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int id = vals[s];
@@ -178,8 +211,12 @@ __global__ void __launch_bounds__(256) k_boxes(const float4* __restrict__ v, con
     }
 }
 
-__global__ void __launch_bounds__(256) k_pack(int n, const int* __restrict__ child, const float4* __restrict__ box_int,
-                                              const float4* __restrict__ box_leaf, BvhNode* __restrict__ nodes) {
+__global__ void __launch_bounds__(256) k_pack(const DevItem* items, int n) {
+    const DevItem& it = items[blockIdx.y];
+    const int* child = it.B.child;
+    const float4* box_int = it.B.box_int;
+    const float4* box_leaf = it.B.box_leaf;
+    BvhNode* nodes = it.nodes;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (n == 1) {
         if (i == 0) {
@@ -204,8 +241,11 @@ __global__ void __launch_bounds__(256) k_pack(int n, const int* __restrict__ chi
 
 // Validity: every leaf referenced exactly once, child boxes inside the parent's
 // stored box, depth of each leaf.
-__global__ void k_check(const BvhNode* nodes, const int* child, const int* parent_int, const int* parent_leaf,
-                        const float4* box_int, int n, int* out) {
+__global__ void k_check(const DevItem* items, int n, int* out) {
+    const DevItem& it = items[0];
+    const BvhNode* nodes = it.nodes;
+    const int* parent_int = it.B.parent_int;
+    const int* parent_leaf = it.B.parent_leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (n == 1) { if (i == 0) { out[0] = 1; out[1] = 0; out[2] = 1; } return; }
     if (i < n - 1) {
@@ -236,38 +276,28 @@ int nb(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_lbvh(const float4* v_cam, const int4* faces, int T, BvhScratch& B, BvhNode* nodes, float4* tris,
-                 int* status, cudaStream_t st) {
+void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, cudaStream_t st) {
     const int n_tiles = nb(T, SORT_TILE);
-    uint32_t *ka = B.keys, *kb = B.keys_alt;
-    int *va = B.vals, *vb = B.vals_alt;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
-        k_hist<<<n_tiles, SORT_TILE, 0, st>>>(ka, T, shift, n_tiles, B.hist);
-        k_scan<<<1, 1024, 0, st>>>(B.hist, 256 * n_tiles);
-        k_scatter<<<n_tiles, SORT_TILE, 0, st>>>(ka, va, T, shift, n_tiles, B.hist, kb, vb);
+        k_hist<<<dim3(n_tiles, n), SORT_TILE, 0, st>>>(items, pass, T, shift, n_tiles);
+        k_scan<<<n, 1024, 0, st>>>(items, 256 * n_tiles);
+        k_scatter<<<dim3(n_tiles, n), SORT_TILE, 0, st>>>(items, pass, T, shift, n_tiles);
         fr_count_launches(3);
-        uint32_t* tk = ka; ka = kb; kb = tk;
-        int* tv = va; va = vb; vb = tv;
     }
     // after an even number of passes the sorted data is back in keys/vals
     if (T > 1) {
-        cudaMemsetAsync(B.flag, 0, sizeof(int) * (size_t)(T - 1), st);
-        cudaMemsetAsync(B.parent_int, 0xff, sizeof(int) * (size_t)(T - 1), st);
-        cudaMemsetAsync(B.parent_leaf, 0xff, sizeof(int) * (size_t)T, st);
-        // unwritten child slots read as leaf 0, never as an ancestor
-        cudaMemsetAsync(B.child, 0xff, sizeof(int) * 2 * (size_t)(T - 1), st);
-        k_karras<<<nb(T - 1, 256), 256, 0, st>>>(ka, T, B.child, B.parent_int, B.parent_leaf, status);
-        fr_count_launches(1);
+        k_bvh_init<<<dim3(nb(T, 256), n), 256, 0, st>>>(items, T);
+        k_karras<<<dim3(nb(T - 1, 256), n), 256, 0, st>>>(items, T, status);
+        fr_count_launches(2);
     }
-    k_boxes<<<nb(T, 256), 256, 0, st>>>(v_cam, faces, va, T, B.child, B.parent_int, B.parent_leaf, B.flag,
-                                        B.box_int, B.box_leaf, tris, status);
-    k_pack<<<nb(T > 1 ? T - 1 : 1, 256), 256, 0, st>>>(T, B.child, B.box_int, B.box_leaf, nodes);
+    k_boxes<<<dim3(nb(T, 256), n), 256, 0, st>>>(items, faces, T, status);
+    k_pack<<<dim3(nb(T > 1 ? T - 1 : 1, 256), n), 256, 0, st>>>(items, T);
     fr_count_launches(2);
 }
 
-void launch_bvh_check(const BvhNode* nodes, const BvhScratch& B, int T, int* out, cudaStream_t st) {
+void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, sizeof(int) * 3, st);
-    k_check<<<nb(T, 256), 256, 0, st>>>(nodes, B.child, B.parent_int, B.parent_leaf, B.box_int, T, out);
+    k_check<<<nb(T, 256), 256, 0, st>>>(items, T, out);
     fr_count_launches(1);
 }

@@ -2,6 +2,7 @@
 // Reduction": 3x3 Gaussian, sigma 1): blurred = G * image (replicate border),
 // loss = sum |blurred - target| reduced in FP64, and its adjoint
 // dloss/dimage = G^T * sign(blurred - target) by gather (no atomics).
+// Batched over images through blockIdx.y; arguments travel by value.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -14,10 +15,14 @@ FR_D float gw(int dx, int dy) {
     return (r2 == 0 ? 1.0f : (r2 == 1 ? e1 : e2)) / z;
 }
 
-__global__ void __launch_bounds__(256) k_blur_loss(int H, int W, const float* __restrict__ img,
-                                                   const float* __restrict__ tgt, double* loss,
-                                                   float* __restrict__ sgn, float* __restrict__ blurred) {
+__global__ void k_loss_zero(LossTable t) {
+    if (threadIdx.x < t.n) *t.it[threadIdx.x].loss = 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_blur_loss(LossTable t) {
     __shared__ double part[8];
+    const LossItem& L = t.it[blockIdx.y];
+    const int H = L.H, W = L.W;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;   // over H * W * 3
     double l = 0.0;
     if (i < H * W * 3) {
@@ -26,12 +31,12 @@ __global__ void __launch_bounds__(256) k_blur_loss(int H, int W, const float* __
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
                 const int yy = min(max(y + dy, 0), H - 1), xx = min(max(x + dx, 0), W - 1);
-                acc += gw(dx, dy) * img[3 * (yy * W + xx) + k];
+                acc += gw(dx, dy) * L.image[3 * (yy * W + xx) + k];
             }
-        const float r = acc - tgt[i];
+        const float r = acc - L.target[i];
         l = fabs((double)r);
-        sgn[i] = (float)((r > 0.0f) - (r < 0.0f));
-        if (blurred) blurred[i] = acc;
+        L.sign[i] = (float)((r > 0.0f) - (r < 0.0f));
+        if (L.blurred) L.blurred[i] = acc;
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
@@ -39,13 +44,15 @@ __global__ void __launch_bounds__(256) k_blur_loss(int H, int W, const float* __
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        if (s != 0.0) atomicAdd(loss, s);
+        if (s != 0.0) atomicAdd(L.loss, s);
     }
 }
 
 // adj_q = sum over (p, delta) with clamp(p + delta) == q of w(delta) sgn_p
-__global__ void __launch_bounds__(256) k_blur_adjoint(int H, int W, const float* __restrict__ sgn,
-                                                      float* __restrict__ adj) {
+__global__ void __launch_bounds__(256) k_blur_adjoint(LossTable t) {
+    const LossItem& L = t.it[blockIdx.y];
+    if (!L.adj) return;
+    const int H = L.H, W = L.W;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= H * W * 3) return;
     const int k = i % 3, q = i / 3, qx = q % W, qy = q / W;
@@ -55,21 +62,27 @@ __global__ void __launch_bounds__(256) k_blur_adjoint(int H, int W, const float*
             for (int dy = -1; dy <= 1; ++dy) {
                 if (min(max(py + dy, 0), H - 1) != qy) continue;
                 for (int dx = -1; dx <= 1; ++dx)
-                    if (min(max(px + dx, 0), W - 1) == qx) acc += gw(dx, dy) * sgn[3 * (py * W + px) + k];
+                    if (min(max(px + dx, 0), W - 1) == qx) acc += gw(dx, dy) * L.sign[3 * (py * W + px) + k];
             }
-    adj[i] = acc;
+    L.adj[i] = acc;
 }
 
 }  // namespace
 
+void launch_loss(const LossTable& t, cudaStream_t st) {
+    if (t.n <= 0) return;
+    const dim3 grid((t.max_px3 + 255) / 256, t.n);
+    k_loss_zero<<<1, 32, 0, st>>>(t);
+    k_blur_loss<<<grid, 256, 0, st>>>(t);
+    k_blur_adjoint<<<grid, 256, 0, st>>>(t);
+    fr_count_launches(3);
+}
+
 void launch_loss(int H, int W, const float* image, const float* target, double* loss, float* sign,
                  float* blurred, float* adj_image, cudaStream_t st) {
-    const int n = H * W * 3;
-    cudaMemsetAsync(loss, 0, sizeof(double), st);
-    k_blur_loss<<<(n + 255) / 256, 256, 0, st>>>(H, W, image, target, loss, sign, blurred);
-    fr_count_launches(1);
-    if (adj_image) {
-        k_blur_adjoint<<<(n + 255) / 256, 256, 0, st>>>(H, W, sign, adj_image);
-        fr_count_launches(1);
-    }
+    LossTable t;
+    t.n = 1;
+    t.max_px3 = H * W * 3;
+    t.it[0] = LossItem{H, W, image, target, loss, sign, blurred, adj_image};
+    launch_loss(t, st);
 }

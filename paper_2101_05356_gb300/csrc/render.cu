@@ -223,12 +223,18 @@ FR_D float group_sum(float v, int width) {
     return v;
 }
 
-__global__ void __launch_bounds__(RT_THREADS) k_forward(DevScene S, DevParams P, float* image,
-                                                        int32_t* tri_rec, uint64_t* mask_rec,
-                                                        uint32_t iteration, uint32_t face) {
+__global__ void __launch_bounds__(RT_THREADS) k_forward(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
+    const int item = item_of_block(map);
+    const DevItem& it = items[item];
+    const DevScene& S = it.S;
+    const DevParams& P = it.P;
+    float* image = it.image;
+    int32_t* tri_rec = it.tri_rec;
+    uint64_t* mask_rec = it.mask_rec;
+    const uint32_t iteration = it.iteration, face = it.face;
     const long total = (long)S.W * S.H * S.spp;
-    const long q = (long)blockIdx.x * RT_THREADS + threadIdx.x;
+    const long q = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
     const bool valid = q < total;
     const int pixel = valid ? (int)(q / S.spp) : 0;
     const int s = valid ? (int)(q % S.spp) : 0;
@@ -360,13 +366,19 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     add_vec(d_v, E.y, g_p * (C * t), true);
 }
 
-__global__ void __launch_bounds__(RT_THREADS) k_adjoint(DevScene S, DevParams P, DevGrads G, EdgeLists EL,
-                                                        const float* adj_image, uint32_t iteration,
-                                                        uint32_t face) {
+__global__ void __launch_bounds__(RT_THREADS) k_adjoint(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
+    const int item = item_of_block(map);
+    const DevItem& it = items[item];
+    const DevScene& S = it.S;
+    const DevParams& P = it.P;
+    const DevGrads& G = it.G;
+    const EdgeLists& EL = it.EL;
+    const float* adj_image = it.adj;
+    const uint32_t iteration = it.iteration, face = it.face;
     block_acc_init(sh, 1 + 3 * S.NL);
     const long total = (long)S.W * S.H * S.spp;
-    const long qi = (long)blockIdx.x * RT_THREADS + threadIdx.x;
+    const long qi = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
     bool valid = qi < total;
     const int pixel = valid ? (int)(qi / S.spp) : 0;
     const int s = valid ? (int)(qi % S.spp) : 0;
@@ -514,13 +526,19 @@ __global__ void __launch_bounds__(RT_THREADS) k_adjoint(DevScene S, DevParams P,
 // ---------------------------------------------------------------------------
 // primary-visibility boundary term: edge samples in screen space
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RT_THREADS) k_edge_primary(DevScene S, DevParams P, DevGrads G, EdgeLists EL,
-                                                             const float* adj_image, uint32_t iteration,
-                                                             uint32_t face) {
+__global__ void __launch_bounds__(RT_THREADS) k_edge_primary(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
+    const int item = item_of_block(map);
+    const DevItem& it = items[item];
+    const DevScene& S = it.S;
+    const DevParams& P = it.P;
+    const DevGrads& G = it.G;
+    const EdgeLists& EL = it.EL;
+    const float* adj_image = it.adj;
+    const uint32_t iteration = it.iteration, face = it.face;
     block_acc_init(sh, 1);
     const long n_edge = (long)S.W * S.H * S.edge_spp;
-    const long e = (long)blockIdx.x * RT_THREADS + threadIdx.x;
+    const long e = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
     bool active = e < n_edge;
     const int Sn = *EL.prim_count;
     if (Sn == 0) active = false;
@@ -597,7 +615,11 @@ __device__ int sgn_d(double x) { return (x > 0.0) - (x < 0.0); }
 
 // flags[list][E]: list 0 = primary silhouettes (w.r.t. the camera centre),
 // list 1 + j = conservative shadow candidates of light j.
-__global__ void k_classify(DevScene S, const int4* edges, uint8_t* flags) {
+__global__ void k_classify(const DevItem* items) {
+    const DevItem& it = items[blockIdx.y];
+    const DevScene& S = it.S;
+    const int4* edges = it.EL.edges;
+    uint8_t* flags = it.sil_flags;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= S.E) return;
     const int4 E = edges[e];
@@ -634,9 +656,13 @@ __global__ void k_classify(DevScene S, const int4* edges, uint8_t* flags) {
 }
 
 // One block per list: ordered compaction of flagged edge ids with warp ballots.
-__global__ void __launch_bounds__(1024) k_compact(int E, const uint8_t* flags, int* lists, int* counts) {
+__global__ void __launch_bounds__(1024) k_compact(const DevItem* items, int E) {
     __shared__ int warp_tot[32];
     __shared__ int carry;
+    const DevItem& it = items[blockIdx.y];
+    const uint8_t* flags = it.sil_flags;
+    int* lists = it.EL.prim_list;
+    int* counts = it.EL.prim_count;
     const int list = blockIdx.x;
     const uint8_t* fl = flags + (size_t)list * E;
     int* out = lists + (size_t)list * E;
@@ -663,8 +689,9 @@ __global__ void __launch_bounds__(1024) k_compact(int E, const uint8_t* flags, i
     if (threadIdx.x == 0) counts[list] = carry;
 }
 
-__global__ void __launch_bounds__(RT_THREADS) k_trace_rays(DevScene S, const float* org, const float* dir, int n,
-                                                           int32_t* tri, float* tout) {
+__global__ void __launch_bounds__(RT_THREADS) k_trace_rays(const DevItem* items, const float* org, const float* dir,
+                                                           int n, int32_t* tri, float* tout) {
+    const DevScene& S = items[0].S;
     __shared__ int stack[FR_STACK * RT_THREADS];
     const int i = blockIdx.x * RT_THREADS + threadIdx.x;
     if (i >= n) return;
@@ -682,38 +709,35 @@ int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_forward(const DevScene& S, const DevParams& P, float* image, int32_t* tri_rec, uint64_t* mask_rec,
-                    uint32_t iteration, uint32_t face, cudaStream_t st) {
-    const long total = (long)S.W * S.H * S.spp;
-    if (S.spp > 32) cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)S.W * S.H, st);
-    k_forward<<<blocks_for(total, RT_THREADS), RT_THREADS, 0, st>>>(S, P, image, tri_rec, mask_rec, iteration, face);
+int map_blocks(const BlockMap& m) { return m.block0[m.n]; }
+
+void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) {
+    if (map_blocks(map) == 0) return;
+    k_forward<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
     fr_count_launches(1);
 }
 
-void launch_adjoint(const DevScene& S, const DevParams& P, const DevGrads& G, const EdgeLists& EL,
-                    const float* adj_image, uint32_t iteration, uint32_t face, cudaStream_t st) {
-    const long total = (long)S.W * S.H * S.spp;
-    k_adjoint<<<blocks_for(total, RT_THREADS), RT_THREADS, 0, st>>>(S, P, G, EL, adj_image, iteration, face);
+void launch_adjoint(const DevItem* items, const BlockMap& map, cudaStream_t st) {
+    if (map_blocks(map) == 0) return;
+    k_adjoint<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
     fr_count_launches(1);
 }
 
-void launch_edge_primary(const DevScene& S, const DevParams& P, const DevGrads& G, const EdgeLists& EL,
-                         const float* adj_image, uint32_t iteration, uint32_t face, cudaStream_t st) {
-    const long n = (long)S.W * S.H * S.edge_spp;
-    if (n == 0) return;
-    k_edge_primary<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(S, P, G, EL, adj_image, iteration, face);
+void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st) {
+    if (map_blocks(map) == 0) return;
+    k_edge_primary<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
     fr_count_launches(1);
 }
 
-void launch_classify(const DevScene& S, const EdgeLists& EL, uint8_t* flags, cudaStream_t st) {
-    k_classify<<<blocks_for(S.E, 256), 256, 0, st>>>(S, EL.edges, flags);
-    k_compact<<<1 + S.NL, 1024, 0, st>>>(S.E, flags, EL.prim_list, EL.prim_count);
+void launch_classify(const DevItem* items, int n, int E, int NL, cudaStream_t st) {
+    k_classify<<<dim3(blocks_for(E, 256), n), 256, 0, st>>>(items);
+    k_compact<<<dim3(1 + NL, n), 1024, 0, st>>>(items, E);
     fr_count_launches(2);
 }
 
-void launch_trace_rays(const DevScene& S, const float* org, const float* dir, int n, int32_t* tri, float* t,
+void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri, float* t,
                        cudaStream_t st) {
     if (n <= 0) return;
-    k_trace_rays<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(S, org, dir, n, tri, t);
+    k_trace_rays<<<blocks_for(n, RT_THREADS), RT_THREADS, 0, st>>>(items, org, dir, n, tri, t);
     fr_count_launches(1);
 }

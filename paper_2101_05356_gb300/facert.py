@@ -25,7 +25,7 @@ _vp = ctypes.c_void_p
 class FrConfig(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("spp", ctypes.c_int32),
                 ("tex_size", ctypes.c_int32), ("edge_spp", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint32), ("max_batch", ctypes.c_int32)]
 
 
 class FrMesh(ctypes.Structure):
@@ -58,6 +58,13 @@ class FrOptGroup(ctypes.Structure):
                 ("n_prior", ctypes.c_int32), ("lr", ctypes.c_float), ("w_prior", ctypes.c_float),
                 ("w_box", ctypes.c_float), ("w_sym", ctypes.c_float), ("w_chroma", ctypes.c_float),
                 ("w_smooth", ctypes.c_float), ("clamp_lo", ctypes.c_float), ("clamp_hi", ctypes.c_float)]
+
+
+class FrItem(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("spp", ctypes.c_int32),
+                ("edge_spp", ctypes.c_int32), ("flags", ctypes.c_uint32), ("iteration", ctypes.c_uint32),
+                ("face_id", ctypes.c_uint32), ("params", FrParams), ("target", _vp), ("image", _vp),
+                ("loss", _vp), ("grads", ctypes.POINTER(FrGrads))]
 
 
 class FacertError(RuntimeError):
@@ -105,6 +112,7 @@ def lib():
         L.fr_kernel_launches.argtypes = []
         L.fr_kernel_launches.restype = ctypes.c_uint64
         L.fr_set_flags.argtypes = [_vp, ctypes.c_uint32]
+        L.fr_render_batch.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
         L.fr_adam.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, _vp, _vp]
         L.fr_loss_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -131,9 +139,9 @@ def _stream():
 
 # ---- same-named wrappers -------------------------------------------------
 
-def fr_create(width, height, spp, tex_size, edge_spp=1, flags=0, seed=0):
+def fr_create(width, height, spp, tex_size, edge_spp=1, flags=0, seed=0, max_batch=1):
     h = ctypes.c_void_p()
-    cfg = FrConfig(width, height, spp, tex_size, edge_spp, flags, seed)
+    cfg = FrConfig(width, height, spp, tex_size, edge_spp, flags, seed, max_batch)
     check(lib().fr_create(ctypes.byref(h), ctypes.byref(cfg)))
     return h
 
@@ -185,6 +193,23 @@ def fr_render(ctx, params, target, image, loss, grads=None, iteration=0, face_id
     gg = _grads(grads) if grads is not None else None
     check(lib().fr_render(ctx, ctypes.byref(pp), _ptr(target), _ptr(image), _ptr(loss),
                           ctypes.byref(gg) if gg is not None else None, iteration, face_id, _stream()), ctx)
+
+
+def fr_render_batch(ctx, items):
+    """items: list of dicts with width, height, spp, edge_spp, flags, iteration,
+    face_id, params (dict of tensors), target, image, loss, grads (dict or None)."""
+    arr = (FrItem * len(items))()
+    keep = []
+    for k, it in enumerate(items):
+        g = None
+        if it.get("grads") is not None:
+            g = _grads(it["grads"])
+            keep.append(g)
+        arr[k] = FrItem(it["width"], it["height"], it["spp"], it.get("edge_spp", 1), it.get("flags", 0),
+                        it.get("iteration", 0), it.get("face_id", 0), _params(it["params"]),
+                        _ptr(it["target"]), _ptr(it["image"]), _ptr(it["loss"]),
+                        ctypes.pointer(g) if g is not None else None)
+    check(lib().fr_render_batch(ctx, ctypes.cast(arr, _vp), len(items), _stream()), ctx)
 
 
 def fr_sync_status(ctx):
@@ -296,11 +321,11 @@ class Renderer:
     """A library context for one scene (mesh, light stage, image config),
     with torch device buffers for parameters, images and gradients."""
 
-    def __init__(self, scene, edge_spp=1, flags=0, seed=0):
+    def __init__(self, scene, edge_spp=1, flags=0, seed=0, max_batch=1):
         import torch
         self.torch = torch
         self.scene = scene
-        self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed)
+        self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed, max_batch)
         fr_set_mesh(self.ctx, scene.mean, scene.basis, scene.faces, scene.uv)
         fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a)
         self.n_edges = fr_num_edges(self.ctx)
