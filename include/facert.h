@@ -52,6 +52,8 @@ typedef int32_t fr_status;
 #define FR_FLAG_NO_INTERIOR     16u   /* gradient: skip the interior (visibility-fixed) term */
 #define FR_FLAG_NO_PRIMARY_EDGE 32u   /* gradient: skip the primary-visibility boundary term */
 #define FR_FLAG_NO_SHADOW_EDGE  64u   /* gradient: skip the shadow boundary term */
+#define FR_FLAG_MORPH_BF16     128u   /* morph as one BF16 tensor-core GEMM over the batch (FP32
+                                         accumulate, FP32 mean); context-wide, read by every call */
 
 /* emitter types in light records */
 #define FR_LIGHT_QUAD 0
@@ -225,6 +227,12 @@ fr_status fr_debug_silhouettes(fr_ctx* ctx, const fr_params* p, int32_t* prim, i
  * root, out[1] = number of parent boxes that fail to contain a child box,
  * out[2] = maximum depth (device int32[3]). */
 fr_status fr_debug_bvh(fr_ctx* ctx, const fr_params* p, int32_t* out, void* stream);
+
+/* Morph only (Sec. 3.1), for n faces with parameters params[0..n) (host array
+ * of device-pointer sets): out [n][N][3] (device) receives each face's
+ * model-space vertices, through the BF16 tensor-core path when the context has
+ * FR_FLAG_MORPH_BF16, else the FP32 path.  1 <= n <= max_batch. */
+fr_status fr_debug_morph(fr_ctx* ctx, const fr_params* params, int32_t n, float* out, void* stream);
 
 /* Edge count E of the mesh set on ctx (host int). */
 int32_t fr_num_edges(const fr_ctx* ctx);

@@ -51,6 +51,9 @@ struct fr_ctx {
     // mesh and lights (shared by all slots)
     float* mean = nullptr;
     float* basis = nullptr;
+    uint16_t* basis_tiles = nullptr;          // BF16 tensor-core operand tiles [3N/128][128][Kp]
+    uint16_t* coef_tile = nullptr;            // BF16 [32][Kp] gathered coefficients
+    int Kp = 0;
     int4* faces = nullptr;
     float2* uv = nullptr;
     int* vf_off = nullptr;
@@ -209,9 +212,16 @@ fr_status upload(fr_ctx* c, int n, cudaStream_t st) {
     return FR_OK;
 }
 
+void morph(fr_ctx* c, int n, cudaStream_t st) {
+    if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && c->K > 0)
+        launch_morph_tc(c->basis_tiles, c->Kp, c->K, c->coef_tile, c->mean, 3 * c->N, c->d_items, n, c->status, st);
+    else
+        launch_morph(c->mean, c->basis, c->ld, c->K, c->d_items, n, st);
+}
+
 // morph -> pose -> face normals + Morton keys -> vertex normals -> LBVH
 void build_geometry(fr_ctx* c, int n, cudaStream_t st) {
-    launch_morph(c->mean, c->basis, c->ld, c->K, c->d_items, n, st);
+    morph(c, n, st);
     launch_pose(c->d_items, n, c->N, st);
     launch_faces(c->d_items, n, c->faces, c->T, st);
     launch_vertex_normals(c->d_items, n, c->vf_off, c->vf_idx, c->N, st);
@@ -404,6 +414,34 @@ fr_status fr_set_mesh(fr_ctx* c, const fr_mesh* m) {
         std::fill(pad.begin(), pad.end(), 0.0f);
         std::copy(m->basis + (size_t)k * 3 * N, m->basis + (size_t)(k + 1) * 3 * N, pad.begin());
         CK(c, cudaMemcpy(c->basis + (size_t)k * c->ld, pad.data(), sizeof(float) * c->ld, cudaMemcpyHostToDevice));
+    }
+    if (K > 0) {
+        // BF16 operand tiles for the tensor-core morph: tile t holds rows
+        // 128t..128t+127 of the [3N x Kp] basis in the no-swizzle K-major
+        // core-matrix layout (8 rows x 8 values per 128-byte core matrix).
+        c->Kp = ((K + 15) / 16) * 16;
+        const int n3 = 3 * N, tiles = (n3 + 127) / 128;
+        std::vector<uint16_t> bt((size_t)tiles * 128 * c->Kp, 0);
+        auto bf16 = [](float f) {
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            u += 0x7FFFu + ((u >> 16) & 1u);
+            return (uint16_t)(u >> 16);
+        };
+        for (int t = 0; t < tiles; ++t)
+            for (int rr = 0; rr < 128; ++rr) {
+                const int i = t * 128 + rr;
+                if (i >= n3) break;
+                const int g = rr >> 3, r = rr & 7;
+                for (int k = 0; k < K; ++k) {
+                    const int cc = k >> 3, kk = k & 7;
+                    const size_t off = (size_t)t * 128 * c->Kp + ((size_t)(g * (c->Kp / 8) + cc) * 128 + r * 16 + kk * 2) / 2;
+                    bt[off] = bf16(m->basis[(size_t)k * n3 + i]);
+                }
+            }
+        TRY(dalloc(c, &c->basis_tiles, bt.size()));
+        TRY(dalloc(c, &c->coef_tile, (size_t)32 * c->Kp));
+        CK(c, cudaMemcpy(c->basis_tiles, bt.data(), sizeof(uint16_t) * bt.size(), cudaMemcpyHostToDevice));
     }
     std::vector<int4> f4(T);
     for (int f = 0; f < T; ++f) f4[f] = make_int4(m->faces[3 * f], m->faces[3 * f + 1], m->faces[3 * f + 2], 0);
@@ -653,6 +691,22 @@ fr_status fr_debug_bvh(fr_ctx* c, const fr_params* p, int32_t* out, void* stream
     TRY(upload(c, 1, st));
     build_geometry(c, 1, st);
     launch_bvh_check(c->d_items, c->T, out, st);
+    CK(c, cudaGetLastError());
+    return FR_OK;
+}
+
+fr_status fr_debug_morph(fr_ctx* c, const fr_params* params, int32_t n, float* out, void* stream) {
+    if (!c || !params || !out || n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "bad argument");
+    const cudaStream_t st = S_(stream);
+    for (int k = 0; k < n; ++k) {
+        TRY(check_params(c, &params[k]));
+        c->h_items[k] = make_item(c, k, single(c, &params[k], nullptr, nullptr, nullptr, 0, 0));
+    }
+    TRY(upload(c, n, st));
+    morph(c, n, st);
+    for (int k = 0; k < n; ++k)
+        CK(c, cudaMemcpyAsync(out + (size_t)k * 3 * c->N, c->slots[k].v_model, sizeof(float) * 3 * c->N,
+                              cudaMemcpyDeviceToDevice, st));
     CK(c, cudaGetLastError());
     return FR_OK;
 }

@@ -23,6 +23,11 @@ void launch_pose_finish(const DevItem* items, int n, int NL, cudaStream_t st);
 void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const DevItem* items, int n,
                           cudaStream_t st);
 
+// morph_tc.cu
+int morph_tc_smem_bytes(int Kp);
+void launch_morph_tc(const uint16_t* basis_tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int n3,
+                     const DevItem* items, int n, int* status, cudaStream_t st);
+
 // lbvh.cu
 void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, cudaStream_t st);
 void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libfacert.so")
 FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EOVERFLOW, FR_ETIMEOUT = 0, 1, 2, 3, 4, 5
 FLAG_GGX, FLAG_SCHLICK_LINEAR, FLAG_FLAT = 1, 2, 4
 FLAG_NO_INTERIOR, FLAG_NO_PRIMARY_EDGE, FLAG_NO_SHADOW_EDGE = 16, 32, 64
+FLAG_MORPH_BF16 = 128
 
 _vp = ctypes.c_void_p
 
@@ -112,6 +113,7 @@ def lib():
         L.fr_kernel_launches.argtypes = []
         L.fr_kernel_launches.restype = ctypes.c_uint64
         L.fr_set_flags.argtypes = [_vp, ctypes.c_uint32]
+        L.fr_debug_morph.argtypes = [_vp, _vp, ctypes.c_int32, _vp, _vp]
         L.fr_render_batch.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
         L.fr_adam.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, _vp, _vp]
@@ -245,6 +247,11 @@ def fr_debug_silhouettes(ctx, params, prim, n_prim, per_light, counts):
     pp = _params(params)
     check(lib().fr_debug_silhouettes(ctx, ctypes.byref(pp), _ptr(prim), _ptr(n_prim), _ptr(per_light),
                                      _ptr(counts), _stream()), ctx)
+
+
+def fr_debug_morph(ctx, params_list, out):
+    arr = (FrParams * len(params_list))(*[_params(p) for p in params_list])
+    check(lib().fr_debug_morph(ctx, ctypes.cast(arr, _vp), len(params_list), _ptr(out), _stream()), ctx)
 
 
 def fr_debug_bvh(ctx, params, out):
