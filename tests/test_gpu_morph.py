@@ -1,8 +1,8 @@
 """The batched BF16 tensor-core morph (tcgen05.mma, FP32 accumulate, FP32 mean)
 against the FP64 oracle morph, with an error bound derived from BF16 rounding:
-basis and coefficients are each rounded to 8 significant bits (relative error
-<= 2^-9 each, so a product is off by <= 2^-8 relative), hence
-|v_bf16 - v| <= 2^-8 * sum_k |c_k| |B_ki| (+ FP32 accumulation, far smaller)."""
+basis and coefficients are each rounded to nearest with 8 significant bits
+(unit roundoff 2^-8), so each product is off by at most 2^-7 relative, hence
+|v_bf16 - v| <= 2^-7 * sum_k |c_k| |B_ki| (+ FP32 accumulation, far smaller)."""
 import numpy as np
 import pytest
 
@@ -44,7 +44,7 @@ def test_tensor_core_morph_within_bf16_bound(name, nfaces):
     worst = 0.0
     for k, pr in enumerate(prs):
         v = _exact(sc, pr)
-        bound = 2.0 ** -8 * np.tensordot(np.abs(pr.coef.astype(np.float64)), np.abs(B), axes=1) + 1e-6
+        bound = 2.0 ** -7 * np.tensordot(np.abs(pr.coef.astype(np.float64)), np.abs(B), axes=1) + 1e-6
         err_tc = np.abs(out_tc[k].cpu().numpy() - v)
         assert np.all(err_tc <= bound), (k, float(np.max(err_tc / bound)))
         worst = max(worst, float(np.max(err_tc / bound)))
