@@ -258,7 +258,7 @@ uint64_t fr_kernel_launches(void);
 
 /* ---- optimiser: Adam with the regularisers of Sec. 4 (Eq. loss1, loss3) ---- */
 
-#define FR_MAX_OPT_GROUPS 16
+#define FR_MAX_OPT_GROUPS 128
 #define FR_GROUP_PLAIN    0   /* Adam only */
 #define FR_GROUP_COEF     1   /* first n_prior elements: shape prior w_prior * x^2 (sigma_k = 1);
                                  the rest: soft box [0, 1] (expression), w_box * dist^2 */
@@ -273,7 +273,9 @@ uint64_t fr_kernel_launches(void);
 /* One parameter group.  x, m, v (and g, aux when used) are device float32
  * arrays of n elements (aux: N_L scales for LIGHT, the M x M x 3 reference
  * albedo for TEX_RGB).  m and v must be zero before step 1.  After the update x
- * is clamped to [clamp_lo, clamp_hi] when clamp_lo < clamp_hi. */
+ * is clamped to [clamp_lo, clamp_hi] when clamp_lo < clamp_hi.  step > 0 gives
+ * this group its own Adam step count (groups of different faces in one call);
+ * step = 0 uses the call's step. */
 typedef struct fr_opt_group {
     float* x;
     const float* g;
@@ -282,6 +284,7 @@ typedef struct fr_opt_group {
     const float* aux;
     int32_t n, kind, width, n_prior;
     float lr, w_prior, w_box, w_sym, w_chroma, w_smooth, clamp_lo, clamp_hi;
+    int32_t step;
 } fr_opt_group;
 
 /* One Adam step (Kingma & Ba; bias-corrected, step >= 1) over every group:

@@ -16,7 +16,8 @@ struct GroupTable {
     fr_opt_group g[FR_MAX_OPT_GROUPS];
     int block_start[FR_MAX_OPT_GROUPS + 1];
     int n_groups;
-    float beta1, beta2, eps, bc1, bc2;   // bias corrections 1 - beta^t
+    float beta1, beta2, eps;
+    float bc1[FR_MAX_OPT_GROUPS], bc2[FR_MAX_OPT_GROUPS];   // bias corrections 1 - beta^t per group
 };
 
 FR_D float sgnf(float x) { return (float)((x > 0.0f) - (x < 0.0f)); }
@@ -107,10 +108,18 @@ FR_D float reg_grad(const fr_opt_group& G, int i, float x, double* energy) {
 
 // Pass 1: gradient (render + regularisers) into m/v, reading x only; pass 2
 // applies the parameter update, so stencils read the pre-step values.
+FR_D int group_of_block(const GroupTable& T) {
+    int lo = 0, hi = T.n_groups - 1;          // last group whose start <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.block_start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(ADAM_THREADS) k_adam_moments(GroupTable T, double* energy) {
     __shared__ double part[ADAM_THREADS / 32];
-    int gi = 0;
-    while (gi + 1 < T.n_groups && (int)blockIdx.x >= T.block_start[gi + 1]) ++gi;
+    const int gi = group_of_block(T);
     const fr_opt_group& G = T.g[gi];
     const int i = (blockIdx.x - T.block_start[gi]) * ADAM_THREADS + threadIdx.x;
     double e = 0.0;
@@ -136,12 +145,11 @@ __global__ void __launch_bounds__(ADAM_THREADS) k_adam_moments(GroupTable T, dou
 }
 
 __global__ void __launch_bounds__(ADAM_THREADS) k_adam_apply(GroupTable T) {
-    int gi = 0;
-    while (gi + 1 < T.n_groups && (int)blockIdx.x >= T.block_start[gi + 1]) ++gi;
+    const int gi = group_of_block(T);
     const fr_opt_group& G = T.g[gi];
     const int i = (blockIdx.x - T.block_start[gi]) * ADAM_THREADS + threadIdx.x;
     if (i >= G.n) return;
-    const float mh = G.m[i] / T.bc1, vh = G.v[i] / T.bc2;
+    const float mh = G.m[i] / T.bc1[gi], vh = G.v[i] / T.bc2[gi];
     float x = G.x[i] - G.lr * mh / (sqrtf(vh) + T.eps);
     if (G.clamp_lo < G.clamp_hi) x = fminf(fmaxf(x, G.clamp_lo), G.clamp_hi);
     G.x[i] = x;
@@ -162,6 +170,9 @@ extern "C" fr_status fr_adam(const fr_opt_group* groups, int32_t n_groups, int32
             return FR_EINVAL;
         if (G.kind == FR_GROUP_LIGHT && (!G.aux || G.n % 3 != 0)) return FR_EINVAL;
         T.g[k] = G;
+        const int st_k = G.step > 0 ? G.step : step;
+        T.bc1[k] = (float)(1.0 - pow((double)beta1, st_k));
+        T.bc2[k] = (float)(1.0 - pow((double)beta2, st_k));
         T.block_start[k] = blocks;
         blocks += (G.n + ADAM_THREADS - 1) / ADAM_THREADS;
     }
@@ -170,8 +181,6 @@ extern "C" fr_status fr_adam(const fr_opt_group* groups, int32_t n_groups, int32
     T.beta1 = beta1;
     T.beta2 = beta2;
     T.eps = eps;
-    T.bc1 = (float)(1.0 - pow((double)beta1, step));
-    T.bc2 = (float)(1.0 - pow((double)beta2, step));
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (reg_energy) cudaMemsetAsync(reg_energy, 0, sizeof(double), st);
     if (blocks > 0) {

@@ -58,7 +58,8 @@ class FrOptGroup(ctypes.Structure):
                 ("n", ctypes.c_int32), ("kind", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("n_prior", ctypes.c_int32), ("lr", ctypes.c_float), ("w_prior", ctypes.c_float),
                 ("w_box", ctypes.c_float), ("w_sym", ctypes.c_float), ("w_chroma", ctypes.c_float),
-                ("w_smooth", ctypes.c_float), ("clamp_lo", ctypes.c_float), ("clamp_hi", ctypes.c_float)]
+                ("w_smooth", ctypes.c_float), ("clamp_lo", ctypes.c_float), ("clamp_hi", ctypes.c_float),
+                ("step", ctypes.c_int32)]
 
 
 class FrItem(ctypes.Structure):
@@ -292,16 +293,16 @@ def fr_set_flags(ctx, flags):
 
 
 def opt_group(x, m, v, g=None, aux=None, kind=GROUP_PLAIN, lr=1e-3, width=0, n_prior=0, w_prior=0.0,
-              w_box=0.0, w_sym=0.0, w_chroma=0.0, w_smooth=0.0, clamp=None):
+              w_box=0.0, w_sym=0.0, w_chroma=0.0, w_smooth=0.0, clamp=None, step=0):
     """One fr_opt_group over torch device tensors (views of x/g/m/v share storage)."""
     lo, hi = clamp if clamp is not None else (0.0, 0.0)
     grp = FrOptGroup(_ptr(x), _ptr(g), _ptr(m), _ptr(v), _ptr(aux), x.numel(), kind, width, n_prior, lr,
-                     w_prior, w_box, w_sym, w_chroma, w_smooth, lo, hi)
+                     w_prior, w_box, w_sym, w_chroma, w_smooth, lo, hi, step)
     grp._keep = (x, g, m, v, aux)
     return grp
 
 
-def fr_adam(groups, step, beta1=0.9, beta2=0.999, eps=1e-8, reg_energy=None):
+def fr_adam(groups, step=1, beta1=0.9, beta2=0.999, eps=1e-8, reg_energy=None):
     arr = (FrOptGroup * len(groups))(*groups)
     code = lib().fr_adam(ctypes.cast(arr, _vp), len(groups), step, beta1, beta2, eps, _ptr(reg_energy), _stream())
     if code != FR_OK:

@@ -4,20 +4,20 @@ Stage I optimises shape and expression coefficients, pose and light-stage
 intensities against E_ph + E_p + E_b (Eq. loss1); Stage II optimises the
 personalised diffuse, specular and roughness textures with geometry and lights
 fixed against E_ph + symmetry + chromaticity + smoothness + box terms
-(Eq. loss3).  Every step is one fused render/loss/adjoint call (fr_render)
-followed by one fused Adam + regulariser launch pair (fr_adam).  Learning
-rates and weights are the paper's (Sec. 5, "Implementation Details").
+(Eq. loss3).  Every step is one fused render/loss/adjoint call (fr_render, or
+one item of fr_render_batch when served) followed by one fused Adam +
+regulariser launch pair (fr_adam).  Learning rates and weights are the paper's
+(Sec. 5, "Implementation Details").
 """
 from __future__ import annotations
 
 import dataclasses
 
-import numpy as np
-
 from . import facert
 
 LR = dict(light=1e-3, identity=1e-2, expression=1e-3, rot=1e-3, trans=1e-3, texture=5e-3)
 W = dict(w_i=0.0025, w1=0.01, w2=0.3, w3=0.3, w4=0.0002, box=1.0)
+STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE
 
 
 @dataclasses.dataclass
@@ -26,13 +26,17 @@ class Schedule:
     stage2: int = 100
 
 
-class Reconstruction:
-    """One face: parameters, gradients and Adam moments live on the device."""
+class FaceState:
+    """Parameters, gradients, Adam moments and buffers of one face (device)."""
 
-    def __init__(self, renderer, target, init_params, face_id=0, schedule=Schedule(), flags=0):
+    def __init__(self, renderer, target, init_params, face_id=0, schedule=Schedule(), flags=0,
+                 width=None, height=None, spp=None):
         import torch
         self.torch = torch
-        self.r = renderer
+        sc = renderer.scene
+        self.width = width or sc.width
+        self.height = height or sc.height
+        self.spp = spp or sc.spp
         self.target = target
         self.face_id = face_id
         self.schedule = schedule
@@ -41,16 +45,22 @@ class Reconstruction:
         self.g = renderer.zero_grads(self.p)
         self.m = {n: torch.zeros_like(v) for n, v in self.p.items()}
         self.v = {n: torch.zeros_like(v) for n, v in self.p.items()}
-        sc = renderer.scene
         self.ks = sc.n_shape
+        self.tex = sc.tex_size
         self.light_scale = torch.as_tensor(sc.light_d ** 2 / sc.light_a, dtype=torch.float32).cuda()
         self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         self.reg = torch.zeros(1, dtype=torch.float64, device="cuda")
-        self.image = renderer.image_buffer()
+        self.image = torch.zeros((self.height, self.width, 3), dtype=torch.float32, device="cuda")
         self.it = 0
         self.ref_diffuse = None
         self.ref_specular = None
-        self.history = []
+
+    def nbytes(self):
+        """Device memory owned by this face's state."""
+        ts = list(self.p.values()) + list(self.g.values()) + list(self.m.values()) + list(self.v.values())
+        ts += [self.image, self.target]
+        b = sum(t.numel() * t.element_size() for t in ts)
+        return b + 2 * self.p["diffuse"].numel() * 4          # Stage II albedo references
 
     @property
     def stage(self):
@@ -60,55 +70,74 @@ class Reconstruction:
     def done(self):
         return self.it >= self.schedule.stage1 + self.schedule.stage2
 
-    def _groups_stage1(self):
-        p, g, m, v, ks = self.p, self.g, self.m, self.v, self.ks
-        out = []
-        if ks > 0:
-            out.append(facert.opt_group(p["coef"][:ks], m["coef"][:ks], v["coef"][:ks], g["coef"][:ks],
-                                        kind=facert.GROUP_COEF, lr=LR["identity"], n_prior=ks, w_prior=W["w_i"]))
-        if p["coef"].numel() > ks:
-            out.append(facert.opt_group(p["coef"][ks:], m["coef"][ks:], v["coef"][ks:], g["coef"][ks:],
-                                        kind=facert.GROUP_COEF, lr=LR["expression"], n_prior=0, w_box=W["box"]))
-        out.append(facert.opt_group(p["rot"], m["rot"], v["rot"], g["rot"], lr=LR["rot"]))
-        out.append(facert.opt_group(p["trans"], m["trans"], v["trans"], g["trans"], lr=LR["trans"]))
-        out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"], aux=self.light_scale,
-                                    kind=facert.GROUP_LIGHT, lr=LR["light"], w_prior=W["w1"], w_box=W["box"]))
-        return out
+    def begin_step(self):
+        """Zero gradients (and take the Stage I albedos as Stage II references)."""
+        if self.stage == 2 and self.ref_diffuse is None:
+            self.ref_diffuse = self.p["diffuse"].clone()
+            self.ref_specular = self.p["specular"].clone()
+        for t in self.g.values():
+            t.zero_()
 
-    def _groups_stage2(self):
-        p, g, m, v = self.p, self.g, self.m, self.v
-        M = self.r.scene.tex_size
+    def item_flags(self):
+        return self.flags | (STAGE2_FLAGS if self.stage == 2 else 0)
+
+    def item(self, edge_spp=1):
+        """This face's entry of an fr_render_batch call."""
+        return dict(width=self.width, height=self.height, spp=self.spp, edge_spp=edge_spp,
+                    flags=self.item_flags(), iteration=self.it, face_id=self.face_id, params=self.p,
+                    target=self.target, image=self.image, loss=self.loss, grads=self.g)
+
+    def groups(self):
+        """Adam + regulariser groups of the current stage, with this face's step."""
+        p, g, m, v, ks = self.p, self.g, self.m, self.v, self.ks
+        if self.stage == 1:
+            step = self.it + 1
+            out = []
+            if ks > 0:
+                out.append(facert.opt_group(p["coef"][:ks], m["coef"][:ks], v["coef"][:ks], g["coef"][:ks],
+                                            kind=facert.GROUP_COEF, lr=LR["identity"], n_prior=ks,
+                                            w_prior=W["w_i"], step=step))
+            if p["coef"].numel() > ks:
+                out.append(facert.opt_group(p["coef"][ks:], m["coef"][ks:], v["coef"][ks:], g["coef"][ks:],
+                                            kind=facert.GROUP_COEF, lr=LR["expression"], n_prior=0,
+                                            w_box=W["box"], step=step))
+            out.append(facert.opt_group(p["rot"], m["rot"], v["rot"], g["rot"], lr=LR["rot"], step=step))
+            out.append(facert.opt_group(p["trans"], m["trans"], v["trans"], g["trans"], lr=LR["trans"], step=step))
+            out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"],
+                                        aux=self.light_scale, kind=facert.GROUP_LIGHT, lr=LR["light"],
+                                        w_prior=W["w1"], w_box=W["box"], step=step))
+            return out
+        step = self.it - self.schedule.stage1 + 1
+        M = self.tex
         return [
             facert.opt_group(p["diffuse"], m["diffuse"], v["diffuse"], g["diffuse"], aux=self.ref_diffuse,
                              kind=facert.GROUP_TEX_RGB, width=M, lr=LR["texture"], w_sym=W["w2"],
-                             w_chroma=W["w3"], w_smooth=W["w4"]),
+                             w_chroma=W["w3"], w_smooth=W["w4"], step=step),
             facert.opt_group(p["specular"], m["specular"], v["specular"], g["specular"], aux=self.ref_specular,
                              kind=facert.GROUP_TEX_RGB, width=M, lr=LR["texture"], w_sym=W["w2"],
-                             w_chroma=W["w3"], w_smooth=W["w4"], w_box=W["box"]),
+                             w_chroma=W["w3"], w_smooth=W["w4"], w_box=W["box"], step=step),
             facert.opt_group(p["roughness"], m["roughness"], v["roughness"], g["roughness"],
                              kind=facert.GROUP_TEX_MONO, width=M, lr=LR["texture"], w_smooth=W["w4"],
-                             w_box=W["box"], clamp=(0.02, 1.5)),
+                             w_box=W["box"], clamp=(0.02, 1.5), step=step),
         ]
+
+
+class Reconstruction(FaceState):
+    """One face reconstructed alone through the single-face calls."""
+
+    def __init__(self, renderer, target, init_params, face_id=0, schedule=Schedule(), flags=0):
+        super().__init__(renderer, target, init_params, face_id, schedule, flags)
+        self.r = renderer
+        self.history = []
 
     def step(self):
         """One optimisation iteration (render + loss + adjoint + Adam)."""
         if self.done:
             return
-        stage = self.stage
-        if stage == 2 and self.ref_diffuse is None:
-            # Stage II starts from the Stage I albedos and keeps them as the
-            # chromaticity reference (Eq. loss3)
-            self.ref_diffuse = self.p["diffuse"].clone()
-            self.ref_specular = self.p["specular"].clone()
-            facert.fr_set_flags(self.r.ctx, self.flags | facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE)
-        elif stage == 1:
-            facert.fr_set_flags(self.r.ctx, self.flags)
-        for t in self.g.values():
-            t.zero_()
+        self.begin_step()
+        facert.fr_set_flags(self.r.ctx, self.item_flags())
         facert.fr_render(self.r.ctx, self.p, self.target, self.image, self.loss, self.g, self.it, self.face_id)
-        groups = self._groups_stage1() if stage == 1 else self._groups_stage2()
-        step = self.it + 1 if stage == 1 else self.it - self.schedule.stage1 + 1
-        facert.fr_adam(groups, step, reg_energy=self.reg)
+        facert.fr_adam(self.groups(), reg_energy=self.reg)
         self.it += 1
 
     def run(self, record_every=0):
@@ -116,12 +145,12 @@ class Reconstruction:
             self.step()
             if record_every and self.it % record_every == 0:
                 self.history.append((self.it, float(self.loss.item())))
+        facert.fr_set_flags(self.r.ctx, self.flags)
         return self
 
 
 def photometric_loss(renderer, params, target, iteration=10 ** 6, face_id=0):
     """E_ph of `params` against `target` with an evaluation Philox iteration."""
-    import torch
     img = renderer.forward(params, iteration, face_id)
     loss, _, _ = renderer.loss(img, target)
     return float(loss.item())
