@@ -244,6 +244,52 @@ def gpu_arm(args, rank, world):
     return out
 
 
+def serving_bench(n_requests, iters, rate, seed=0):
+    """Served (continuous batching, BF16 tensor-core morph, 8 slots) vs plain (one
+    face at a time, FP32 morph) on the same Poisson stream of two-stage
+    reconstructions of mixed image size and spp (a reduced form of the serving
+    workload: sizes {128,192,256}^2, spp {4,8,16}, iters + iters iterations)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2101_05356_gb300 import facert, optim, serve, synth
+    sc = synth.make_scene("c2")
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([128, 192, 256], size=n_requests)
+    spps = rng.choice([4, 8, 16], size=n_requests)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    targets = []
+    for k in range(n_requests):
+        s2 = dataclasses.replace(sc, width=int(sizes[k]), height=int(sizes[k]), spp=int(spps[k]))
+        r = facert.Renderer(s2)
+        gt = synth.random_params(s2, 500 + k, coef_scale=0.5)
+        targets.append(r.forward(r.device_params(gt), iteration=10 ** 7, face_id=k).cpu().numpy())
+        r.close()
+
+    def stream():
+        return [serve.Request(rid=k, target=targets[k], spp=int(spps[k]), schedule=optim.Schedule(iters, iters),
+                              arrival=float(arrivals[k]), init=synth.init_params(sc)) for k in range(n_requests)]
+
+    out = {}
+    for name, mk in (("served", lambda: serve.Server(sc, max_slots=8, max_width=256, max_height=256, max_spp=16)),
+                     ("plain", lambda: serve.Server(sc, max_slots=1, flags=0, max_width=256, max_height=256,
+                                                    max_spp=16))):
+        srv = mk()
+        reqs = srv.run(stream())
+        lat = serve.latency_stats(reqs)
+        out[name] = dict(faces_per_s=len(reqs) / srv.elapsed, elapsed_s=srv.elapsed, p50_s=lat["p50_s"],
+                         p99_s=lat["p99_s"], mean_final_loss=float(np.mean([q.final_loss for q in reqs])),
+                         mean_batch=float(np.mean(srv.batch_sizes)))
+        srv.r.close()
+        torch.cuda.synchronize()
+    out["faces_per_s_speedup"] = out["served"]["faces_per_s"] / out["plain"]["faces_per_s"]
+    out["final_loss_ratio"] = out["served"]["mean_final_loss"] / out["plain"]["mean_final_loss"]
+    out["workload"] = ("%d Poisson requests (rate %.0f/s), sizes {128,192,256}^2, spp {4,8,16}, %d+%d "
+                       "iterations, 35,709-vertex face, 40 lights" % (n_requests, rate, iters, iters))
+    return out
+
+
 def cpu_baseline(sample_pixels, threads=0):
     """The FP64 oracle as it stands, on a bounded sample of the same workload:
     forward + adjoint (all terms) restricted to `sample_pixels` random pixels."""
@@ -277,6 +323,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-pixels", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-iters", type=int, default=6)
+    ap.add_argument("--serve-rate", type=float, default=40.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -305,6 +354,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     out = gpu_arm(args, rank, world)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        out["serving"] = serving_bench(args.serve_requests, args.serve_iters, args.serve_rate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.cpu_pixels).items() if k != "seconds"}
     if world > 1:
