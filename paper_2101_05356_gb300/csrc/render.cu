@@ -16,6 +16,19 @@ namespace {
 
 constexpr int RT_THREADS = 128;
 constexpr int RT_WARPS = RT_THREADS / 32;
+
+// Traversal stack placement: a [FR_STACK][RT_THREADS] shared-memory array
+// (default) or a per-thread array in local memory (L1-cached).
+#ifndef FR_STACK_LOCAL
+#define FR_STACK_LOCAL 0
+#endif
+// minimum resident blocks per SM requested from the compiler (register cap)
+#ifndef FR_FWD_MIN_BLOCKS
+#define FR_FWD_MIN_BLOCKS 1
+#endif
+#ifndef FR_ADJ_MIN_BLOCKS
+#define FR_ADJ_MIN_BLOCKS 1
+#endif
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float SHADOW_EPS = 1e-4f;     // shadow segment trimmed to (eps, 1 - eps)
 
@@ -25,12 +38,20 @@ struct WarpQueue {
 };
 
 struct RtShared {
+#if !FR_STACK_LOCAL
     int stack[FR_STACK * RT_THREADS];
+#endif
     WarpQueue wq[RT_WARPS];
     double acc[1 + 3 * FR_MAX_LIGHTS];  // focal, light intensities (block partials)
 };
 
+#if FR_STACK_LOCAL
+#define FR_STACK_DECL int lstack_[FR_STACK];
+#define my_stack(sh) (Stack{lstack_, 1})
+#else
+#define FR_STACK_DECL
 FR_D Stack my_stack(RtShared& sh) { return Stack{&sh.stack[threadIdx.x], RT_THREADS}; }
+#endif
 
 struct SampleState {
     bool hit;
@@ -204,10 +225,10 @@ FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleSta
 
 // Full warp-cooperative radiance evaluation at screen point (sx, sy).
 FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
-                        const Sampler& smp, int dim0, RtShared& sh, SampleState& ss, uint64_t& vis,
+                        const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t& vis,
                         RayStats& rs) {
-    primary_state(S, P, active, sx, sy, my_stack(sh), ss, rs);
-    vis = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], my_stack(sh), rs);
+    primary_state(S, P, active, sx, sy, stk, ss, rs);
+    vis = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs);
     return radiance_from(S, P, ss, vis, smp, dim0);
 }
 
@@ -223,8 +244,9 @@ FR_D float group_sum(float v, int width) {
     return v;
 }
 
-__global__ void __launch_bounds__(RT_THREADS) k_forward(const DevItem* items, BlockMap map) {
+__global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
+    FR_STACK_DECL
     const int item = item_of_block(map);
     const DevItem& it = items[item];
     const DevScene& S = it.S;
@@ -244,7 +266,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_forward(const DevItem* items, Bl
     uint64_t vis;
     RayStats rs;
     const float3 Lo = radiance_at(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
-                                  smp, 2, sh, ss, vis, rs);
+                                  smp, 2, sh, my_stack(sh), ss, vis, rs);
     flush_stats(S.counters + 0, rs);
     if (valid && tri_rec) tri_rec[q] = ss.tri;
     if (valid && mask_rec) mask_rec[q] = vis;
@@ -366,8 +388,9 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     add_vec(d_v, E.y, g_p * (C * t), true);
 }
 
-__global__ void __launch_bounds__(RT_THREADS) k_adjoint(const DevItem* items, BlockMap map) {
+__global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
+    FR_STACK_DECL
     const int item = item_of_block(map);
     const DevItem& it = items[item];
     const DevScene& S = it.S;
@@ -526,8 +549,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_adjoint(const DevItem* items, Bl
 // ---------------------------------------------------------------------------
 // primary-visibility boundary term: edge samples in screen space
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RT_THREADS) k_edge_primary(const DevItem* items, BlockMap map) {
+__global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_edge_primary(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
+    FR_STACK_DECL
     const int item = item_of_block(map);
     const DevItem& it = items[item];
     const DevScene& S = it.S;
@@ -579,8 +603,8 @@ __global__ void __launch_bounds__(RT_THREADS) k_edge_primary(const DevItem* item
     SampleState ssp, ssm;
     uint64_t visp, vism;
     RayStats rs;
-    const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, ssp, visp, rs);
-    const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, ssm, vism, rs);
+    const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, my_stack(sh), ssp, visp, rs);
+    const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, my_stack(sh), ssm, vism, rs);
     flush_stats(S.counters + 6, rs);
     float gf = 0.0f;
     float3 gA = f3(0, 0, 0), gB = f3(0, 0, 0);
@@ -711,8 +735,18 @@ int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 // ---------------------------------------------------------------------------
 int map_blocks(const BlockMap& m) { return m.block0[m.n]; }
 
+void set_carveout() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_forward, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_adjoint, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_edge_primary, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    done = true;
+}
+
 void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
+    set_carveout();
     k_forward<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
     fr_count_launches(1);
 }
