@@ -79,16 +79,13 @@ struct LightDev {
     int type, pad;
 };
 
-// Four-wide BVH node (128 B): the boxes of up to four children in SoA form and
-// their codes (>= 0: wide node index, < 0: leaf ~slot, FR_EMPTY_CHILD: none).
-// Wide node i collapses binary node i with its internal children, so a
-// traversal from node 0 takes every second level of the binary LBVH.
+// Binary BVH node holding both children's boxes (64 B, four 16-B loads).
 struct __align__(16) BvhNode {
-    float4 lox, loy, loz, hix, hiy, hiz;
-    int4 child;
-    int4 pad;
+    float4 a;   // lo0.x lo0.y lo0.z hi0.x
+    float4 b;   // hi0.y hi0.z lo1.x lo1.y
+    float4 c;   // lo1.z hi1.x hi1.y hi1.z
+    int4 d;     // child0, child1 (>= 0 internal, < 0 leaf ~slot), pad, pad
 };
-constexpr int FR_EMPTY_CHILD = 0x7fffffff;
 
 struct DevScene {
     int N, T, K, NL, E, W, H, spp, M, edge_spp;

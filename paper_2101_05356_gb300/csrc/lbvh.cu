@@ -211,8 +211,6 @@ __global__ void __launch_bounds__(256) k_boxes(const DevItem* items, const int4*
     }
 }
 
-// Wide node i: the children of binary node i, each internal child replaced by
-// its own two children (so every wide node spans two binary levels).
 __global__ void __launch_bounds__(256) k_pack(const DevItem* items, int n) {
     const DevItem& it = items[blockIdx.y];
     const int* child = it.B.child;
@@ -220,48 +218,29 @@ __global__ void __launch_bounds__(256) k_pack(const DevItem* items, int n) {
     const float4* box_leaf = it.B.box_leaf;
     BvhNode* nodes = it.nodes;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int code[4] = {FR_EMPTY_CHILD, FR_EMPTY_CHILD, FR_EMPTY_CHILD, FR_EMPTY_CHILD};
-    int cnt = 0;
     if (n == 1) {
-        if (i != 0) return;
-        code[cnt++] = ~0;
-    } else {
-        if (i >= n - 1) return;
-        for (int q = 0; q < 2; ++q) {
-            const int c = child[2 * i + q];
-            if (c < 0) {
-                code[cnt++] = c;
-            } else {
-                code[cnt++] = child[2 * c];
-                code[cnt++] = child[2 * c + 1];
-            }
+        if (i == 0) {
+            const float4 l = box_leaf[0], h = box_leaf[1];
+            nodes[0].a = make_float4(l.x, l.y, l.z, h.x);
+            nodes[0].b = make_float4(h.y, h.z, INFINITY, INFINITY);
+            nodes[0].c = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
+            nodes[0].d = make_int4(~0, ~0, 0, 0);
         }
+        return;
     }
-    float lo[3][4], hi[3][4];
-    for (int k = 0; k < 4; ++k) {
-        float4 l = make_float4(INFINITY, INFINITY, INFINITY, 0.0f), h = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
-        if (code[k] != FR_EMPTY_CHILD) {
-            const float4* bx = code[k] < 0 ? &box_leaf[2 * (~code[k])] : &box_int[2 * code[k]];
-            l = bx[0];
-            h = bx[1];
-        }
-        lo[0][k] = l.x; lo[1][k] = l.y; lo[2][k] = l.z;
-        hi[0][k] = h.x; hi[1][k] = h.y; hi[2][k] = h.z;
-    }
-    BvhNode& N = nodes[i];
-    N.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
-    N.loy = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
-    N.loz = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
-    N.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
-    N.hiy = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
-    N.hiz = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
-    N.child = make_int4(code[0], code[1], code[2], code[3]);
-    N.pad = make_int4(0, 0, 0, 0);
+    if (i >= n - 1) return;
+    const int c0 = child[2 * i], c1 = child[2 * i + 1];
+    const float4* b0 = c0 < 0 ? &box_leaf[2 * (~c0)] : &box_int[2 * c0];
+    const float4* b1 = c1 < 0 ? &box_leaf[2 * (~c1)] : &box_int[2 * c1];
+    const float4 l0 = b0[0], h0 = b0[1], l1 = b1[0], h1 = b1[1];
+    nodes[i].a = make_float4(l0.x, l0.y, l0.z, h0.x);
+    nodes[i].b = make_float4(h0.y, h0.z, l1.x, l1.y);
+    nodes[i].c = make_float4(l1.z, h1.x, h1.y, h1.z);
+    nodes[i].d = make_int4(c0, c1, 0, 0);
 }
 
-// Validity of the wide tree reachable from node 0: every leaf referenced once,
-// each child's boxes inside the box its parent stores for it, leaf depth (in
-// binary levels, through the parent links).
+// Validity: every leaf referenced exactly once, child boxes inside the parent's
+// stored box, depth of each leaf.
 __global__ void k_check(const DevItem* items, int n, int* out) {
     const DevItem& it = items[0];
     const BvhNode* nodes = it.nodes;
@@ -269,32 +248,21 @@ __global__ void k_check(const DevItem* items, int n, int* out) {
     const int* parent_leaf = it.B.parent_leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (n == 1) { if (i == 0) { out[0] = 1; out[1] = 0; out[2] = 1; } return; }
-    // wide node i is reachable iff binary node i sits at an even binary depth
     if (i < n - 1) {
-        int d = 0;
-        for (int p = i; p > 0 && d < 4096; p = parent_int[p]) ++d;
-        if ((d & 1) == 0) {
-            const BvhNode& N = nodes[i];
-            const int code[4] = {N.child.x, N.child.y, N.child.z, N.child.w};
-            const float plx[4] = {N.lox.x, N.lox.y, N.lox.z, N.lox.w}, ply[4] = {N.loy.x, N.loy.y, N.loy.z, N.loy.w};
-            const float plz[4] = {N.loz.x, N.loz.y, N.loz.z, N.loz.w}, phx[4] = {N.hix.x, N.hix.y, N.hix.z, N.hix.w};
-            const float phy[4] = {N.hiy.x, N.hiy.y, N.hiy.z, N.hiy.w}, phz[4] = {N.hiz.x, N.hiz.y, N.hiz.z, N.hiz.w};
-            for (int k = 0; k < 4; ++k) {
-                if (code[k] == FR_EMPTY_CHILD) continue;
-                if (code[k] < 0) { atomicAdd(&out[0], 1); continue; }
-                const BvhNode& C = nodes[code[k]];
-                const float clx[4] = {C.lox.x, C.lox.y, C.lox.z, C.lox.w}, cly[4] = {C.loy.x, C.loy.y, C.loy.z, C.loy.w};
-                const float clz[4] = {C.loz.x, C.loz.y, C.loz.z, C.loz.w}, chx[4] = {C.hix.x, C.hix.y, C.hix.z, C.hix.w};
-                const float chy[4] = {C.hiy.x, C.hiy.y, C.hiy.z, C.hiy.w}, chz[4] = {C.hiz.x, C.hiz.y, C.hiz.z, C.hiz.w};
-                const int cc[4] = {C.child.x, C.child.y, C.child.z, C.child.w};
-                bool in = true;
-                for (int q = 0; q < 4; ++q) {
-                    if (cc[q] == FR_EMPTY_CHILD) continue;
-                    in = in && clx[q] >= plx[k] && cly[q] >= ply[k] && clz[q] >= plz[k] && chx[q] <= phx[k] &&
-                         chy[q] <= phy[k] && chz[q] <= phz[k];
-                }
-                if (!in) atomicAdd(&out[1], 1);
-            }
+        const int cc[2] = {nodes[i].d.x, nodes[i].d.y};
+        for (int q = 0; q < 2; ++q) {
+            if (cc[q] < 0) { atomicAdd(&out[0], 1); continue; }
+            // the child's own children boxes must lie inside this node's box for it
+            const BvhNode& ch = nodes[cc[q]];
+            const float4 pa = nodes[i].a, pb = nodes[i].b, pc = nodes[i].c;
+            const float3 plo = q == 0 ? f3(pa.x, pa.y, pa.z) : f3(pb.z, pb.w, pc.x);
+            const float3 phi = q == 0 ? f3(pa.w, pb.x, pb.y) : f3(pc.y, pc.z, pc.w);
+            const float3 lo0 = f3(ch.a.x, ch.a.y, ch.a.z), hi0 = f3(ch.a.w, ch.b.x, ch.b.y);
+            const float3 lo1 = f3(ch.b.z, ch.b.w, ch.c.x), hi1 = f3(ch.c.y, ch.c.z, ch.c.w);
+            const bool in = lo0.x >= plo.x && lo0.y >= plo.y && lo0.z >= plo.z && hi0.x <= phi.x && hi0.y <= phi.y &&
+                            hi0.z <= phi.z && lo1.x >= plo.x && lo1.y >= plo.y && lo1.z >= plo.z && hi1.x <= phi.x &&
+                            hi1.y <= phi.y && hi1.z <= phi.z;
+            if (!in) atomicAdd(&out[1], 1);
         }
     }
     if (i < n) {

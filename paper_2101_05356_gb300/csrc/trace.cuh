@@ -60,10 +60,32 @@ FR_D bool hit_triangle(const RayPre& r, float3 v0, float3 v1, float3 v2, float t
     return true;
 }
 
+FR_D bool box_hit(const RayPre& r, float3 lo, float3 hi, float tmin, float tmax, float& tnear) {
+    const float tx0 = fmaf(lo.x, r.inv.x, r.ood.x), tx1 = fmaf(hi.x, r.inv.x, r.ood.x);
+    const float ty0 = fmaf(lo.y, r.inv.y, r.ood.y), ty1 = fmaf(hi.y, r.inv.y, r.ood.y);
+    const float tz0 = fmaf(lo.z, r.inv.z, r.ood.z), tz1 = fmaf(hi.z, r.inv.z, r.ood.z);
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    tnear = tn;
+    return tn <= tf;
+}
+
 struct Hit {
     float t, b1, b2;
     int tri;   // original triangle index, -1 on a miss
 };
+
+FR_D void load_node(const BvhNode* nodes, int i, float3& lo0, float3& hi0, float3& lo1, float3& hi1,
+                    int& c0, int& c1) {
+    const float4 a = __ldg(&nodes[i].a), b = __ldg(&nodes[i].b), c = __ldg(&nodes[i].c);
+    const int4 d = __ldg(&nodes[i].d);
+    lo0 = f3(a.x, a.y, a.z);
+    hi0 = f3(a.w, b.x, b.y);
+    lo1 = f3(b.z, b.w, c.x);
+    hi1 = f3(c.y, c.z, c.w);
+    c0 = d.x;
+    c1 = d.y;
+}
 
 // stack: this thread's column of a [FR_STACK][blockDim] shared array.
 struct Stack {
@@ -73,34 +95,7 @@ struct Stack {
     FR_D int get(int i) const { return base[i * stride]; }
 };
 
-// Slab tests of a wide node's four child boxes against (tmin, tmax]:
-// tn[k] = entry distance, or +inf when child k is missed or absent.
-FR_D void wide_boxes(const BvhNode* node, const RayPre& r, float tmin, float tmax, float tn[4], int code[4]) {
-    const float4 lx = __ldg(&node->lox), ly = __ldg(&node->loy), lz = __ldg(&node->loz);
-    const float4 hx = __ldg(&node->hix), hy = __ldg(&node->hiy), hz = __ldg(&node->hiz);
-    const int4 ch = __ldg(&node->child);
-    const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, lya[4] = {ly.x, ly.y, ly.z, ly.w}, lza[4] = {lz.x, lz.y, lz.z, lz.w};
-    const float hxa[4] = {hx.x, hx.y, hx.z, hx.w}, hya[4] = {hy.x, hy.y, hy.z, hy.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
-    code[0] = ch.x; code[1] = ch.y; code[2] = ch.z; code[3] = ch.w;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float tx0 = fmaf(lxa[k], r.inv.x, r.ood.x), tx1 = fmaf(hxa[k], r.inv.x, r.ood.x);
-        const float ty0 = fmaf(lya[k], r.inv.y, r.ood.y), ty1 = fmaf(hya[k], r.inv.y, r.ood.y);
-        const float tz0 = fmaf(lza[k], r.inv.z, r.ood.z), tz1 = fmaf(hza[k], r.inv.z, r.ood.z);
-        const float tn_ = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
-        const float tf_ = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-        tn[k] = (tn_ <= tf_ && code[k] != FR_EMPTY_CHILD) ? tn_ : INFINITY;
-    }
-}
-
-FR_D void cswap(float& ta, int& ca, float& tb, int& cb) {
-    if (tb < ta) {
-        const float t = ta; ta = tb; tb = t;
-        const int c = ca; ca = cb; cb = c;
-    }
-}
-
-// Closest hit in (tmin, tmax]; ties on t go to the lower triangle index.
+// Closest hit in (tmin, tmax); ties on t go to the lower triangle index.
 FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tmax, Stack st, RayStats& rs) {
     rs.rays++;
     Hit h;
@@ -109,46 +104,56 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
     h.b1 = h.b2 = 0.0f;
     int sp = 0;
     int node = 0;
-    // a valid tree visits each of its T - 1 wide nodes at most once per ray
-    for (int guard = s.T + 8; guard > 0; --guard) {
+    // a valid tree visits each of its 2T - 1 nodes at most once per ray
+    for (int guard = 2 * s.T + 8; guard > 0; --guard) {
+        float3 lo0, hi0, lo1, hi1;
+        int c0, c1;
+        load_node(s.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
         rs.nodes++;
-        float tn[4];
-        int code[4];
-        wide_boxes(&s.nodes[node], r, tmin, h.t, tn, code);
+        float tn0, tn1;
+        bool h0 = box_hit(r, lo0, hi0, tmin, h.t, tn0);
+        bool h1 = box_hit(r, lo1, hi1, tmin, h.t, tn1);
         // leaves are single triangles: test them right away
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (tn[k] < INFINITY && code[k] < 0) {
-                const int slot = ~code[k];
-                const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
-                float t, b1, b2;
-                const int id = __float_as_int(a.w);
-                rs.tris++;
-                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
-                    (t < h.t || id < h.tri || h.tri < 0)) {
-                    h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
-                }
-                tn[k] = INFINITY;
+        if (h0 && c0 < 0) {
+            const int slot = ~c0;
+            const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+            float t, b1, b2;
+            const int id = __float_as_int(a.w);
+            rs.tris++;
+            if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
+                (t < h.t || id < h.tri || h.tri < 0)) {
+                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
             }
+            h0 = false;
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (tn[k] > h.t) tn[k] = INFINITY;
-        // order the internal children near to far
-        cswap(tn[0], code[0], tn[1], code[1]);
-        cswap(tn[2], code[2], tn[3], code[3]);
-        cswap(tn[0], code[0], tn[2], code[2]);
-        cswap(tn[1], code[1], tn[3], code[3]);
-        cswap(tn[1], code[1], tn[2], code[2]);
-        const int cnt = (tn[0] < INFINITY) + (tn[1] < INFINITY) + (tn[2] < INFINITY) + (tn[3] < INFINITY);
-        if (cnt == 0) {
+        if (h1 && c1 < 0) {
+            const int slot = ~c1;
+            const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+            float t, b1, b2;
+            const int id = __float_as_int(a.w);
+            rs.tris++;
+            if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
+                (t < h.t || id < h.tri || h.tri < 0)) {
+                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id;
+            }
+            h1 = false;
+        }
+        if (h0 && tn0 > h.t) h0 = false;
+        if (h1 && tn1 > h.t) h1 = false;
+        if (h0 && h1) {
+            int near = c0, far = c1;
+            if (tn1 < tn0) { near = c1; far = c0; }
+            if (sp >= FR_STACK) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return h; }
+            st.put(sp++, far);
+            node = near;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
             if (sp == 0) return h;
             node = st.get(--sp);
-            continue;
         }
-        if (sp + cnt - 1 > FR_STACK) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return h; }
-        for (int k = cnt - 1; k >= 1; --k) st.put(sp++, code[k]);
-        node = code[0];
     }
     set_status(s.status, FR_STATUS_BAD_BVH);
     return h;
@@ -160,36 +165,48 @@ FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, 
     rs.rays++;
     int sp = 0;
     int node = 0;
-    for (int guard = s.T + 8; guard > 0; --guard) {
+    for (int guard = 2 * s.T + 8; guard > 0; --guard) {
+        float3 lo0, hi0, lo1, hi1;
+        int c0, c1;
+        load_node(s.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
         rs.nodes++;
-        float tn[4];
-        int code[4];
-        wide_boxes(&s.nodes[node], r, tmin, tmax, tn, code);
-        int next = -1;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!(tn[k] < INFINITY)) continue;
-            if (code[k] < 0) {
-                const int slot = ~code[k];
-                const float4 a = __ldg(&s.tris[3 * slot]);
-                if (__float_as_int(a.w) != skip) {
-                    const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
-                    float t, b1, b2;
-                    rs.tris++;
-                    if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
-                }
-            } else if (next < 0) {
-                next = code[k];
-            } else {
-                if (sp >= FR_STACK) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return false; }
-                st.put(sp++, code[k]);
+        float tn0, tn1;
+        bool h0 = box_hit(r, lo0, hi0, tmin, tmax, tn0);
+        bool h1 = box_hit(r, lo1, hi1, tmin, tmax, tn1);
+        if (h0 && c0 < 0) {
+            const int slot = ~c0;
+            const float4 a = __ldg(&s.tris[3 * slot]);
+            if (__float_as_int(a.w) != skip) {
+                const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+                float t, b1, b2;
+                rs.tris++;
+                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
             }
+            h0 = false;
         }
-        if (next < 0) {
+        if (h1 && c1 < 0) {
+            const int slot = ~c1;
+            const float4 a = __ldg(&s.tris[3 * slot]);
+            if (__float_as_int(a.w) != skip) {
+                const float4 b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+                float t, b1, b2;
+                rs.tris++;
+                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
+            }
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp >= FR_STACK) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return false; }
+            st.put(sp++, c1);
+            node = c0;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
             if (sp == 0) return false;
-            next = st.get(--sp);
+            node = st.get(--sp);
         }
-        node = next;
     }
     set_status(s.status, FR_STATUS_BAD_BVH);
     return false;
