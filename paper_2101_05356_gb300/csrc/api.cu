@@ -284,7 +284,9 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.B.keys_alt, T));
     TRY(dalloc(c, &sl.B.vals, T));
     TRY(dalloc(c, &sl.B.vals_alt, T));
-    TRY(dalloc(c, &sl.B.hist, 256 * (size_t)n_tiles));
+    // radix histogram [256][n_tiles]; the silhouette compaction reuses it for
+    // [1 + 64 lists][E / 1024 chunks] counts
+    TRY(dalloc(c, &sl.B.hist, std::max(256 * (size_t)n_tiles, (size_t)(1 + FR_MAX_LIGHTS) * ((c->E + 1023) / 1024))));
     TRY(dalloc(c, &sl.B.child, 2 * (size_t)std::max(T - 1, 1)));
     TRY(dalloc(c, &sl.B.parent_int, std::max(T - 1, 1)));
     TRY(dalloc(c, &sl.B.parent_leaf, T));

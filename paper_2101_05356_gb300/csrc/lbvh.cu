@@ -24,39 +24,30 @@ __global__ void __launch_bounds__(SORT_TILE) k_hist(const DevItem* items, int pa
     hist[threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of hist[256 * n_tiles] in place (digit-major), one block
-__global__ void __launch_bounds__(1024) k_scan(const DevItem* items, int m) {
-    __shared__ int warp_sum[32];
+// Exclusive scan of hist[256][n_tiles] in digit-major order, one block of 256
+// threads per item: thread d scans digit d's row, then the 256 row totals are
+// scanned across the block and added back.
+__global__ void __launch_bounds__(256) k_scan(const DevItem* items, int n_tiles) {
+    __shared__ int tot[256];
     int* hist = items[blockIdx.x].B.hist;
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    const int d = threadIdx.x;
+    int* row = hist + d * n_tiles;
+    int run = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        const int v = row[t];
+        row[t] = run;
+        run += v;
+    }
+    tot[d] = run;
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = 0; base < m; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int v = i < m ? hist[i] : 0;
-        int x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sum[wid] = x;
+    for (int o = 1; o < 256; o <<= 1) {              // inclusive Hillis-Steele scan of the totals
+        const int v = d >= o ? tot[d - o] : 0;
         __syncthreads();
-        if (wid == 0) {
-            int s = warp_sum[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            warp_sum[lane] = s;
-        }
-        __syncthreads();
-        const int before = carry + (wid ? warp_sum[wid - 1] : 0);
-        if (i < m) hist[i] = before + x - v;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += warp_sum[31];
+        tot[d] += v;
         __syncthreads();
     }
+    const int base = d > 0 ? tot[d - 1] : 0;
+    for (int t = 0; t < n_tiles; ++t) row[t] += base;
 }
 
 // Stable scatter: rank among equal digits = earlier warps' counts + earlier
@@ -281,7 +272,7 @@ void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* sta
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         k_hist<<<dim3(n_tiles, n), SORT_TILE, 0, st>>>(items, pass, T, shift, n_tiles);
-        k_scan<<<n, 1024, 0, st>>>(items, 256 * n_tiles);
+        k_scan<<<n, 256, 0, st>>>(items, n_tiles);
         k_scatter<<<dim3(n_tiles, n), SORT_TILE, 0, st>>>(items, pass, T, shift, n_tiles);
         fr_count_launches(3);
     }
