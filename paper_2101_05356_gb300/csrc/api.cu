@@ -31,11 +31,12 @@ struct Slot {
     uint8_t* sil_flags = nullptr;
     int* lists = nullptr;
     int* counts = nullptr;
-    float* d_v = nullptr;
-    float* d_n = nullptr;
+    fix64* d_v = nullptr;
+    fix64* d_n = nullptr;
+    fix64* tex = nullptr;
     float* dm = nullptr;
-    double* small = nullptr;
-    double* acc12 = nullptr;
+    fix64* small = nullptr;
+    double* pose_part = nullptr;
     float* sign = nullptr;
     float* adj_image = nullptr;
 };
@@ -155,6 +156,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.P = DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness};
     it.G.d_v = sl.d_v;
     it.G.d_n = sl.d_n;
+    it.G.tex = sl.tex;
     it.G.small = sl.small;
     if (a.g) {
         it.G.diffuse = a.g->diffuse;
@@ -180,7 +182,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.d_vmodel = sl.d_vmodel;
     it.n_face = sl.n_face;
     it.dm = sl.dm;
-    it.acc12 = sl.acc12;
+    it.pose_part = sl.pose_part;
     it.sil_flags = sl.sil_flags;
     it.image = a.image;
     it.adj = a.adj ? a.adj : sl.adj_image;
@@ -239,7 +241,7 @@ fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
 
 // reverse pass for items [0, n) whose geometry is built
 void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
-    launch_zero_accumulators(c->d_items, n, c->N, st);
+    launch_zero_accumulators(c->d_items, n, c->N, c->cfg.tex_size, st);
     bool need_edges = false;
     for (int k = 0; k < n; ++k) {
         const uint32_t f = c->h_items[k].S.flags;
@@ -251,9 +253,10 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     mark(c, 5, st);
     launch_edge_primary(c->d_items, map_of(c, n, true), st);
     mark(c, 6, st);
+    launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
     launch_pose_adjoint(c->d_items, n, c->N, st);
-    launch_pose_finish(c->d_items, n, c->NL, st);
+    launch_pose_finish(c->d_items, n, c->NL, c->N, st);
     launch_morph_adjoint(c->basis, c->ld, c->K, 3 * c->N, c->d_items, n, st);
     mark(c, 7, st);
 }
@@ -301,9 +304,10 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.counts, 1 + FR_MAX_LIGHTS));
     TRY(dalloc(c, &sl.d_v, 3 * (size_t)N));
     TRY(dalloc(c, &sl.d_n, 3 * (size_t)N));
+    TRY(dalloc(c, &sl.tex, 7 * (size_t)c->cfg.tex_size * c->cfg.tex_size));
     TRY(dalloc(c, &sl.dm, 3 * (size_t)N));
     TRY(dalloc(c, &sl.small, 1 + 3 * FR_MAX_LIGHTS));
-    TRY(dalloc(c, &sl.acc12, 12));
+    TRY(dalloc(c, &sl.pose_part, 12 * (size_t)((N + 255) / 256)));
     return FR_OK;
 }
 

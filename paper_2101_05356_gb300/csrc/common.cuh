@@ -124,11 +124,25 @@ struct DevParams {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
 };
 
+// Gradient sums are kept in 64-bit fixed point (resolution 2^-32, range
+// +-2^31): integer addition is associative, so a sum does not depend on the
+// order in which atomics land, and every result is bitwise reproducible
+// whatever else shares the launch.
+typedef unsigned long long fix64;
+constexpr double FR_FIX_SCALE = 4294967296.0;
+FR_D long long to_fix(float v) { return __double2ll_rn((double)v * FR_FIX_SCALE); }
+FR_D long long to_fix_d(double v) { return __double2ll_rn(v * FR_FIX_SCALE); }
+FR_D double from_fix(fix64 v) { return (double)(long long)v * (1.0 / FR_FIX_SCALE); }
+FR_D void fix_add(fix64* a, float v) {
+    if (v != 0.0f) atomicAdd(a, (fix64)to_fix(v));
+}
+
 struct DevGrads {
-    float* d_v;            // [N][3] dE/dv' (camera space)
-    float* d_n;            // [N][3] dE/dn (unit vertex normals)
-    float *diffuse, *specular, *roughness;   // texture gradients (may be null)
-    double* small;         // [1 + 3 N_L]: focal, then light intensities (FP64)
+    fix64* d_v;            // [N][3] dE/dv' (camera space)
+    fix64* d_n;            // [N][3] dE/dn (unit vertex normals)
+    fix64* tex;            // [3 M^2] diffuse, [3 M^2] specular, [M^2] roughness
+    float *diffuse, *specular, *roughness;   // caller texture gradients (may be null)
+    fix64* small;          // [1 + 3 N_L]: focal, then light intensities
 };
 
 struct BvhScratch {
@@ -172,7 +186,7 @@ struct DevItem {
     float* d_vmodel;
     float4* n_face;
     float* dm;
-    double* acc12;
+    double* pose_part;      // [ceil(N / 256)][12] per-block pose-gradient partials
     uint8_t* sil_flags;
     float* image;
     const float* adj;       // image-space adjoint read by the ray kernels
@@ -196,8 +210,9 @@ FR_D int item_of_block(const BlockMap& m) {
 
 FR_D void set_status(int* status, int bit) { atomicOr(status, bit); }
 
-// Warp-aggregated atomic add: lanes sharing `key` sum first, one lane adds.
-FR_D void warp_agg_add(float* addr, float val, uint32_t key, uint32_t active) {
+// Warp-aggregated fixed-point add: lanes sharing `key` sum in lane order, one
+// lane adds the sum.
+FR_D void warp_agg_add(fix64* addr, float val, uint32_t key, uint32_t active) {
     const uint32_t peers = __match_any_sync(active, key);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
@@ -209,5 +224,5 @@ FR_D void warp_agg_add(float* addr, float val, uint32_t key, uint32_t active) {
         sum += __shfl_sync(peers, val, src);
         m &= m - 1;
     }
-    if (lane == leader && sum != 0.0f) atomicAdd(addr, sum);
+    if (lane == leader) fix_add(addr, sum);
 }

@@ -2,6 +2,8 @@
 // (Gamma(v) = R^-1 (v - T)), face/vertex normals, Morton keys, and the reverse
 // of each step (normals, pose, morph transpose with FP64 reductions).  Every
 // kernel is batched over the items of a call through blockIdx.y.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -32,15 +34,27 @@ __global__ void k_set_items(ItemsParam p, DevItem* out) {
     }
 }
 
-// per-item accumulators of the adjoint: dE/dv', dE/dn, FP64 partials
-__global__ void k_zero_acc(const DevItem* items, int N) {
+// per-item fixed-point accumulators of the adjoint: dE/dv', dE/dn, texture
+// gradients, focal and light partials
+__global__ void k_zero_acc(const DevItem* items, int N, int M) {
     const DevItem& it = items[blockIdx.y];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 3 * N) { it.G.d_v[i] = 0.0f; it.G.d_n[i] = 0.0f; }
-    if (blockIdx.x == 0) {
-        for (int k = threadIdx.x; k < 1 + 3 * FR_MAX_LIGHTS; k += blockDim.x) it.G.small[k] = 0.0;
-        if (threadIdx.x < 12) it.acc12[threadIdx.x] = 0.0;
-    }
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3L * N) { it.G.d_v[i] = 0ull; it.G.d_n[i] = 0ull; }
+    if (i < 7L * M * M) it.G.tex[i] = 0ull;
+    if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k < 1 + 3 * FR_MAX_LIGHTS; k += blockDim.x) it.G.small[k] = 0ull;
+}
+
+// add the fixed-point texture gradients into the caller's float gradients
+__global__ void k_tex_flush(const DevItem* items, int M) {
+    const DevItem& it = items[blockIdx.y];
+    const long M2 = (long)M * M;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 7 * M2) return;
+    const float g = (float)from_fix(it.G.tex[i]);
+    if (i < 3 * M2) { if (it.G.diffuse) it.G.diffuse[i] += g; }
+    else if (i < 6 * M2) { if (it.G.specular) it.G.specular[i - 3 * M2] += g; }
+    else if (it.G.roughness) it.G.roughness[i - 6 * M2] += g;
 }
 
 // Coalesced, float4-vectorised morph: thread i owns float4 i of the padded
@@ -174,8 +188,8 @@ __global__ void k_normals_adj_a(const DevItem* items, int N) {
     if (i >= N) return;
     const float4 n4 = it.vn[i];
     const float3 n = xyz(n4);
-    const float* d_n = it.G.d_n;
-    const float3 g = f3(d_n[3 * i], d_n[3 * i + 1], d_n[3 * i + 2]);
+    const fix64* d_n = it.G.d_n;
+    const float3 g = f3((float)from_fix(d_n[3 * i]), (float)from_fix(d_n[3 * i + 1]), (float)from_fix(d_n[3 * i + 2]));
     const float inv = n4.w > 0.0f ? 1.0f / n4.w : 0.0f;
     const float3 r = (g - n * dot(n, g)) * inv;
     it.dm[3 * i] = r.x; it.dm[3 * i + 1] = r.y; it.dm[3 * i + 2] = r.z;
@@ -202,13 +216,14 @@ __global__ void k_normals_adj_b(const DevItem* items, const int4* __restrict__ f
         else if (i == t.y) acc += gu;
         else acc += gw;
     }
-    float* d_v = it.G.d_v;
-    d_v[3 * i] += acc.x;
-    d_v[3 * i + 1] += acc.y;
-    d_v[3 * i + 2] += acc.z;
+    fix64* d_v = it.G.d_v;                       // one writer per vertex here
+    d_v[3 * i] += (fix64)to_fix(acc.x);
+    d_v[3 * i + 1] += (fix64)to_fix(acc.y);
+    d_v[3 * i + 2] += (fix64)to_fix(acc.z);
 }
 
-// dE/dv = R dE/dv'; accumulates M'[r][c] = sum_i g_r w_c and sum_i g (FP64).
+// dE/dv = R dE/dv'; per-block partials of M'[r][c] = sum_i g_r w_c and
+// sum_i g (FP64), summed in block order by k_pose_finish.
 __global__ void __launch_bounds__(256) k_pose_adj(const DevItem* items, int N) {
     __shared__ float R[9], T[3];
     __shared__ double part[8][12];
@@ -222,9 +237,9 @@ __global__ void __launch_bounds__(256) k_pose_adj(const DevItem* items, int N) {
     double loc[12];
     for (int k = 0; k < 12; ++k) loc[k] = 0.0;
     if (i < N) {
-        const float* d_v = it.G.d_v;
+        const fix64* d_v = it.G.d_v;
         const float* vm = it.v_model;
-        const float g[3] = {d_v[3 * i], d_v[3 * i + 1], d_v[3 * i + 2]};
+        const float g[3] = {(float)from_fix(d_v[3 * i]), (float)from_fix(d_v[3 * i + 1]), (float)from_fix(d_v[3 * i + 2])};
         const float w[3] = {vm[3 * i] - T[0], vm[3 * i + 1] - T[1], vm[3 * i + 2] - T[2]};
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c) loc[3 * r + c] = (double)g[r] * (double)w[c];
@@ -240,17 +255,23 @@ __global__ void __launch_bounds__(256) k_pose_adj(const DevItem* items, int N) {
     if (threadIdx.x < 12) {
         double s = 0.0;
         for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += part[wv][threadIdx.x];
-        atomicAdd(&it.acc12[threadIdx.x], s);
+        it.pose_part[blockIdx.x * 12 + threadIdx.x] = s;
     }
 }
 
 // dE/dtheta_a = sum_rc M'[r][c] dR[c][r]/dtheta_a ; dE/dT = -R sum g; plus the
 // FP64 focal and light-intensity accumulators.  One block per item.
-__global__ void k_pose_finish(const DevItem* items, int NL) {
+__global__ void k_pose_finish(const DevItem* items, int NL, int n_blocks) {
+    __shared__ double acc12[12];
     const DevItem& it = items[blockIdx.x];
     const int t = threadIdx.x;
-    const double* acc12 = it.acc12;
-    const double* small = it.G.small;
+    if (t < 12) {
+        double s = 0.0;
+        for (int b = 0; b < n_blocks; ++b) s += it.pose_part[b * 12 + t];
+        acc12[t] = s;
+    }
+    __syncthreads();
+    const fix64* small = it.G.small;
     if (t == 0) {
         const double a = it.P.rot[0], b = it.P.rot[1], c = it.P.rot[2];
         const double sx = sin(a), cx = cos(a), sy = sin(b), cy = cos(b), sz = sin(c), cz = cos(c);
@@ -281,10 +302,10 @@ __global__ void k_pose_finish(const DevItem* items, int NL) {
             for (int r = 0; r < 3; ++r) s += R[3 * c2 + r] * acc12[9 + r];
             if (it.g_trans) it.g_trans[c2] += (float)(-s);
         }
-        if (it.g_focal) it.g_focal[0] += (float)small[0];
+        if (it.g_focal) it.g_focal[0] += (float)from_fix(small[0]);
     }
     if (it.g_light)
-        for (int k = t; k < 3 * NL; k += blockDim.x) it.g_light[k] += (float)small[1 + k];
+        for (int k = t; k < 3 * NL; k += blockDim.x) it.g_light[k] += (float)from_fix(small[1 + k]);
 }
 
 // dE/dcoef_k = sum_i basis[k][i] dE/dv_i, one block per (k, item), FP64 accumulation.
@@ -334,8 +355,13 @@ void launch_set_items(const DevItem* host_items, int n, DevItem* dev_items, cuda
     fr_count_launches(1);
 }
 
-void launch_zero_accumulators(const DevItem* items, int n, int N, cudaStream_t st) {
-    k_zero_acc<<<dim3(nb(3 * (long)N, 256), n), 256, 0, st>>>(items, N);
+void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStream_t st) {
+    k_zero_acc<<<dim3(nb(std::max(3L * N, 7L * M * M), 256), n), 256, 0, st>>>(items, N, M);
+    fr_count_launches(1);
+}
+
+void launch_tex_flush(const DevItem* items, int n, int M, cudaStream_t st) {
+    k_tex_flush<<<dim3(nb(7L * M * M, 256), n), 256, 0, st>>>(items, M);
     fr_count_launches(1);
 }
 
@@ -376,8 +402,8 @@ void launch_pose_adjoint(const DevItem* items, int n, int N, cudaStream_t st) {
     fr_count_launches(1);
 }
 
-void launch_pose_finish(const DevItem* items, int n, int NL, cudaStream_t st) {
-    k_pose_finish<<<n, 64, 0, st>>>(items, NL);
+void launch_pose_finish(const DevItem* items, int n, int NL, int N, cudaStream_t st) {
+    k_pose_finish<<<n, 64, 0, st>>>(items, NL, nb(N, 256));
     fr_count_launches(1);
 }
 

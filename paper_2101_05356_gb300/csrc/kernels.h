@@ -9,7 +9,8 @@ void fr_count_launches(int n);
 
 // geometry.cu
 void launch_set_items(const DevItem* host_items, int n, DevItem* dev_items, cudaStream_t st);
-void launch_zero_accumulators(const DevItem* items, int n, int N, cudaStream_t st);
+void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStream_t st);
+void launch_tex_flush(const DevItem* items, int n, int M, cudaStream_t st);
 void launch_morph(const float* mean, const float* basis, int ld, int K, const DevItem* items, int n,
                   cudaStream_t st);
 void launch_pose(const DevItem* items, int n, int N, cudaStream_t st);
@@ -19,7 +20,7 @@ void launch_vertex_normals(const DevItem* items, int n, const int* vf_off, const
 void launch_normals_adjoint(const DevItem* items, int n, const int4* faces, const int* vf_off,
                             const int* vf_idx, int N, cudaStream_t st);
 void launch_pose_adjoint(const DevItem* items, int n, int N, cudaStream_t st);
-void launch_pose_finish(const DevItem* items, int n, int NL, cudaStream_t st);
+void launch_pose_finish(const DevItem* items, int n, int NL, int N, cudaStream_t st);
 void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const DevItem* items, int n,
                           cudaStream_t st);
 

@@ -45,7 +45,7 @@ struct RtShared {
     int stack[FR_STACK * RT_THREADS];
 #endif
     WarpQueue wq[RT_WARPS];
-    double acc[1 + 3 * FR_MAX_LIGHTS];  // focal, light intensities (block partials)
+    double acc[RT_WARPS][1 + 3 * FR_MAX_LIGHTS];  // per-warp focal / light partials
 };
 
 #if FR_STACK_LOCAL
@@ -290,26 +290,30 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
 // adjoint
 // ---------------------------------------------------------------------------
 FR_D void block_acc_init(RtShared& sh, int n) {
-    for (int i = threadIdx.x; i < n; i += RT_THREADS) sh.acc[i] = 0.0;
+    for (int i = threadIdx.x; i < RT_WARPS * n; i += RT_THREADS) sh.acc[i / n][i % n] = 0.0;
     __syncthreads();
 }
 
-FR_D void block_acc_flush(RtShared& sh, int n, double* out) {
+// per-warp partials summed in warp order, then one fixed-point add per value
+FR_D void block_acc_flush(RtShared& sh, int n, fix64* out) {
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += RT_THREADS)
-        if (sh.acc[i] != 0.0) atomicAdd(&out[i], sh.acc[i]);
+    for (int i = threadIdx.x; i < n; i += RT_THREADS) {
+        double s = 0.0;
+        for (int w = 0; w < RT_WARPS; ++w) s += sh.acc[w][i];
+        if (s != 0.0) atomicAdd(&out[i], (fix64)to_fix_d(s));
+    }
 }
 
-FR_D void add_vec(float* base, int vertex, float3 g, bool on) {
+FR_D void add_vec(fix64* base, int vertex, float3 g, bool on) {
     if (!on) return;
-    atomicAdd(&base[3 * vertex + 0], g.x);
-    atomicAdd(&base[3 * vertex + 1], g.y);
-    atomicAdd(&base[3 * vertex + 2], g.z);
+    fix_add(&base[3 * vertex + 0], g.x);
+    fix_add(&base[3 * vertex + 1], g.y);
+    fix_add(&base[3 * vertex + 2], g.z);
 }
 
 // Warp-aggregated scatter of a per-vertex 3-vector (lanes hitting the same
 // vertex combine first).
-FR_D void scatter_vertex(float* base, int vertex, float3 g, bool on) {
+FR_D void scatter_vertex(fix64* base, int vertex, float3 g, bool on) {
     const unsigned act = __ballot_sync(FULL, on);
     if (!on) return;
     warp_agg_add(&base[3 * vertex + 0], g.x, (uint32_t)vertex, act);
@@ -317,9 +321,9 @@ FR_D void scatter_vertex(float* base, int vertex, float3 g, bool on) {
     warp_agg_add(&base[3 * vertex + 2], g.z, (uint32_t)vertex, act);
 }
 
-FR_D void scatter_texel(float* base, int C, int texel, int ch, float g, bool on) {
+FR_D void scatter_texel(fix64* base, int C, int texel, int ch, float g, bool on) {
     const unsigned act = __ballot_sync(FULL, on);
-    if (!on || base == nullptr) return;
+    if (!on) return;
     warp_agg_add(&base[texel * C + ch], g, (uint32_t)texel, act);
 }
 
@@ -327,7 +331,7 @@ FR_D void scatter_texel(float* base, int C, int texel, int ch, float g, bool on)
 // for visibility of the emitter, Sec. 4).  Adds C * dz/dy . m to gy and
 // scatters the edge-vertex terms.  Returns nothing; inactive lanes do nothing.
 FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL, const SampleState& ss,
-                      const Sampler& sm2, float3 w, float3& gy, float* d_v, Stack st, RayStats& rs) {
+                      const Sampler& sm2, float3 w, float3& gy, fix64* d_v, Stack st, RayStats& rs) {
     const uint4 blk = sm2.block(0);
     const float u0 = u24(blk.x), u1 = u24(blk.y), u2 = u24(blk.z);
     const int j = min((int)(u0 * (float)S.NL), S.NL - 1);
@@ -443,10 +447,11 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
                 gI = f3(w.x * h.x, w.y * h.y, w.z * h.z) * (L.area * L.scale);
             }
             const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
-            if ((threadIdx.x & 31) == 0 && (sx_ != 0.0f || sy_ != 0.0f || sz_ != 0.0f)) {
-                atomicAdd(&sh.acc[1 + 3 * j], (double)sx_);
-                atomicAdd(&sh.acc[1 + 3 * j + 1], (double)sy_);
-                atomicAdd(&sh.acc[1 + 3 * j + 2], (double)sz_);
+            if ((threadIdx.x & 31) == 0) {
+                double* wa = sh.acc[threadIdx.x >> 5];
+                wa[1 + 3 * j] += (double)sx_;
+                wa[1 + 3 * j + 1] += (double)sy_;
+                wa[1 + 3 * j + 2] += (double)sz_;
             }
         }
         if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit) {
@@ -532,19 +537,20 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     scatter_vertex(G.d_n, fc.z, gn2, on);
     // bilinear texture scatter (4 taps), warp-aggregated by texel
     const bool tex_on = on && interior;
+    const size_t M2 = (size_t)S.M * S.M;
     const int taps[4] = {ss.tap.i00, ss.tap.i10, ss.tap.i01, ss.tap.i11};
     const float tw[4] = {(1.0f - ss.tap.fx) * (1.0f - ss.tap.fy), ss.tap.fx * (1.0f - ss.tap.fy),
                          (1.0f - ss.tap.fx) * ss.tap.fy, ss.tap.fx * ss.tap.fy};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         for (int ch = 0; ch < 3; ++ch) {
-            scatter_texel(G.diffuse, 3, taps[k], ch, gtex[ch] * tw[k], tex_on);
-            scatter_texel(G.specular, 3, taps[k], ch, gtex[3 + ch] * tw[k], tex_on);
+            scatter_texel(G.tex, 3, taps[k], ch, gtex[ch] * tw[k], tex_on);
+            scatter_texel(G.tex + 3 * M2, 3, taps[k], ch, gtex[3 + ch] * tw[k], tex_on);
         }
-        scatter_texel(G.roughness, 1, taps[k], 0, gtex[6] * tw[k], tex_on);
+        scatter_texel(G.tex + 6 * M2, 1, taps[k], 0, gtex[6] * tw[k], tex_on);
     }
     const float gf_w = warp_sum(gfocal);
-    if ((threadIdx.x & 31) == 0 && gf_w != 0.0f) atomicAdd(&sh.acc[0], (double)gf_w);
+    if ((threadIdx.x & 31) == 0) sh.acc[threadIdx.x >> 5][0] += (double)gf_w;
     flush_stats(S.counters + 3, rs);
     block_acc_flush(sh, 1 + 3 * S.NL, G.small);
 }
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_edge_primary(
     scatter_vertex(G.d_v, E.x, gA, active);
     scatter_vertex(G.d_v, E.y, gB, active);
     const float gw = warp_sum(gf);
-    if ((threadIdx.x & 31) == 0 && gw != 0.0f) atomicAdd(&sh.acc[0], (double)gw);
+    if ((threadIdx.x & 31) == 0) sh.acc[threadIdx.x >> 5][0] += (double)gw;
     block_acc_flush(sh, 1, G.small);
 }
 
