@@ -247,7 +247,7 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
         const uint32_t f = c->h_items[k].S.flags;
         need_edges |= !(f & FR_FLAG_NO_PRIMARY_EDGE) || !(f & FR_FLAG_NO_SHADOW_EDGE);
     }
-    if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, st);
+    if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, c->T, st);
     mark(c, 4, st);
     launch_adjoint(c->d_items, map_of(c, n, false), st);
     mark(c, 5, st);
@@ -290,6 +290,7 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     // radix histogram [256][n_tiles]; the silhouette compaction reuses it for
     // [1 + 64 lists][E / 1024 chunks] counts
     TRY(dalloc(c, &sl.B.hist, std::max(256 * (size_t)n_tiles, (size_t)(1 + FR_MAX_LIGHTS) * ((c->E + 1023) / 1024))));
+    TRY(dalloc(c, &sl.B.hist_base, 256));
     TRY(dalloc(c, &sl.B.child, 2 * (size_t)std::max(T - 1, 1)));
     TRY(dalloc(c, &sl.B.parent_int, std::max(T - 1, 1)));
     TRY(dalloc(c, &sl.B.parent_leaf, T));
@@ -299,7 +300,8 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.B.aabb, 6));
     TRY(dalloc(c, &sl.nodes, std::max(T - 1, 1)));
     TRY(dalloc(c, &sl.tris, 3 * (size_t)T));
-    TRY(dalloc(c, &sl.sil_flags, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
+    // [1 + 64 lists][E] edge flags, then [64 lights][T] per-face facing classes
+    TRY(dalloc(c, &sl.sil_flags, (size_t)(1 + FR_MAX_LIGHTS) * c->E + (size_t)FR_MAX_LIGHTS * T));
     TRY(dalloc(c, &sl.lists, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
     TRY(dalloc(c, &sl.counts, 1 + FR_MAX_LIGHTS));
     TRY(dalloc(c, &sl.d_v, 3 * (size_t)N));
@@ -678,7 +680,7 @@ fr_status fr_debug_silhouettes(fr_ctx* c, const fr_params* p, int32_t* prim, int
     c->h_items[0] = make_item(c, 0, single(c, p, nullptr, nullptr, nullptr, 0, 0));
     TRY(upload(c, 1, st));
     build_geometry(c, 1, st);
-    launch_classify(c->d_items, 1, c->E, c->NL, st);
+    launch_classify(c->d_items, 1, c->E, c->NL, c->T, st);
     const Slot& sl = c->slots[0];
     if (prim) CK(c, cudaMemcpyAsync(prim, sl.lists, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, st));
     if (n_prim) CK(c, cudaMemcpyAsync(n_prim, sl.counts, sizeof(int), cudaMemcpyDeviceToDevice, st));

@@ -149,6 +149,7 @@ struct BvhScratch {
     uint32_t *keys, *keys_alt;
     int *vals, *vals_alt;
     int* hist;           // [256][n_tiles]
+    int* hist_base;      // [256] digit bases
     int* child;          // [2 (T - 1)] child codes of internal nodes
     int* parent_int;     // [T - 1]
     int* parent_leaf;    // [T]

@@ -24,30 +24,60 @@ __global__ void __launch_bounds__(SORT_TILE) k_hist(const DevItem* items, int pa
     hist[threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of hist[256][n_tiles] in digit-major order, one block of 256
-// threads per item: thread d scans digit d's row, then the 256 row totals are
-// scanned across the block and added back.
-__global__ void __launch_bounds__(256) k_scan(const DevItem* items, int n_tiles) {
-    __shared__ int tot[256];
-    int* hist = items[blockIdx.x].B.hist;
-    const int d = threadIdx.x;
-    int* row = hist + d * n_tiles;
-    int run = 0;
-    for (int t = 0; t < n_tiles; ++t) {
-        const int v = row[t];
-        row[t] = run;
-        run += v;
+// Exclusive scan of hist[256][n_tiles] in digit-major order in two launches:
+// one block per (digit, item) scans its row and records the row total; one
+// block per item scans the 256 totals into digit bases (hist_base), which the
+// scatter adds.
+FR_D int block_scan_excl(int v, int* warp_tot, int& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    tot[d] = run;
+    if (lane == 31) warp_tot[wid] = x;
     __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {              // inclusive Hillis-Steele scan of the totals
-        const int v = d >= o ? tot[d - o] : 0;
+    if (wid == 0) {
+        int t = lane < nw ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    total = warp_tot[nw - 1];
+    const int r = (wid ? warp_tot[wid - 1] : 0) + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(512) k_scan_rows(const DevItem* items, int n_tiles) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const BvhScratch& B = items[blockIdx.y].B;
+    int* row = B.hist + blockIdx.x * n_tiles;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_tiles; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const int v = t < n_tiles ? row[t] : 0;
+        int tot;
+        const int ex = block_scan_excl(v, warp_tot, tot);
+        if (t < n_tiles) row[t] = carry + ex;
         __syncthreads();
-        tot[d] += v;
+        if (threadIdx.x == 0) carry += tot;
         __syncthreads();
     }
-    const int base = d > 0 ? tot[d - 1] : 0;
-    for (int t = 0; t < n_tiles; ++t) row[t] += base;
+    if (threadIdx.x == 0) B.hist_base[blockIdx.x] = carry;       // row total for now
+}
+
+__global__ void __launch_bounds__(256) k_scan_digits(const DevItem* items) {
+    __shared__ int warp_tot[32];
+    const BvhScratch& B = items[blockIdx.x].B;
+    int tot;
+    const int ex = block_scan_excl(B.hist_base[threadIdx.x], warp_tot, tot);
+    B.hist_base[threadIdx.x] = ex;
 }
 
 // Stable scatter: rank among equal digits = earlier warps' counts + earlier
@@ -61,6 +91,7 @@ __global__ void __launch_bounds__(SORT_TILE) k_scatter(const DevItem* items, int
     uint32_t* keys_out = (pass & 1) ? B.keys : B.keys_alt;
     int* vals_out = (pass & 1) ? B.vals : B.vals_alt;
     const int* off = B.hist;
+    const int* dbase = B.hist_base;
     __shared__ int cnt[NW][256];
     for (int k = threadIdx.x; k < NW * 256; k += SORT_TILE) (&cnt[0][0])[k] = 0;
     __syncthreads();
@@ -83,7 +114,7 @@ __global__ void __launch_bounds__(SORT_TILE) k_scatter(const DevItem* items, int
     }
     __syncthreads();
     if (ok) {
-        const int pos = off[digit * n_tiles + blockIdx.x] + cnt[wid][digit] + rank;
+        const int pos = dbase[digit] + off[digit * n_tiles + blockIdx.x] + cnt[wid][digit] + rank;
         keys_out[pos] = key;
         vals_out[pos] = vals[i];
     }
@@ -272,9 +303,10 @@ void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* sta
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         k_hist<<<dim3(n_tiles, n), SORT_TILE, 0, st>>>(items, pass, T, shift, n_tiles);
-        k_scan<<<n, 256, 0, st>>>(items, n_tiles);
+        k_scan_rows<<<dim3(256, n), 512, 0, st>>>(items, n_tiles);
+        k_scan_digits<<<n, 256, 0, st>>>(items);
         k_scatter<<<dim3(n_tiles, n), SORT_TILE, 0, st>>>(items, pass, T, shift, n_tiles);
-        fr_count_launches(3);
+        fr_count_launches(4);
     }
     // after an even number of passes the sorted data is back in keys/vals
     if (T > 1) {

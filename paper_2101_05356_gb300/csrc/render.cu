@@ -646,8 +646,41 @@ __device__ double3 face_normal_d(const DevScene& S, int f) {
 
 __device__ int sgn_d(double x) { return (x > 0.0) - (x < 0.0); }
 
-// flags[list][E]: list 0 = primary silhouettes (w.r.t. the camera centre),
-// list 1 + j = conservative shadow candidates of light j.
+// Facing class of face f over emitter j (FP64): 1 = every point of the emitter
+// is in front of the face's plane, 2 = every point behind, 3 = mixed.  The
+// signed distance is linear over the emitter, so its range follows from the
+// corners (quad, triangle) or the projected radius (disk).
+__global__ void k_face_class(const DevItem* items) {
+    const DevItem& it = items[blockIdx.y];
+    const DevScene& S = it.S;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= S.T) return;
+    const double3 n = face_normal_d(S, f);
+    const float4 p0 = S.v[S.faces[f].x];
+    const double d = n.x * p0.x + n.y * p0.y + n.z * p0.z;
+    for (int j = 0; j < S.NL; ++j) {
+        const LightDev& L = S.lights[j];
+        const double base = n.x * L.c.x + n.y * L.c.y + n.z * L.c.z - d;
+        const double g1 = n.x * L.e1.x + n.y * L.e1.y + n.z * L.e1.z;
+        const double g2 = n.x * L.e2.x + n.y * L.e2.y + n.z * L.e2.z;
+        double lo, hi;
+        if (L.type == 0) {
+            const double h = 0.5 * fabs(g1) + 0.5 * fabs(g2);
+            lo = base - h; hi = base + h;
+        } else if (L.type == 1) {
+            lo = base + fmin(0.0, fmin(g1, g2)); hi = base + fmax(0.0, fmax(g1, g2));
+        } else {
+            const double r = sqrt(g1 * g1 + g2 * g2);
+            lo = base - r; hi = base + r;
+        }
+        it.sil_flags[(size_t)(1 + FR_MAX_LIGHTS) * S.E + (size_t)j * S.T + f] = lo > 0.0 ? 1 : (hi < 0.0 ? 2 : 3);
+    }
+}
+
+// flags[list][E]: list 0 = primary silhouettes (w.r.t. the camera centre,
+// FP64 per edge), list 1 + j = conservative shadow candidates of light j
+// (edges whose two faces are not both entirely in front of or both entirely
+// behind emitter j).
 __global__ void k_classify(const DevItem* items) {
     const DevItem& it = items[blockIdx.y];
     const DevScene& S = it.S;
@@ -664,27 +697,10 @@ __global__ void k_classify(const DevItem* items) {
     const double ax = pa.x, ay = pa.y, az = pa.z;
     const double3 n1 = face_normal_d(S, E.z), n2 = face_normal_d(S, E.w);
     flags[e] = sgn_d(-(n1.x * ax + n1.y * ay + n1.z * az)) != sgn_d(-(n2.x * ax + n2.y * ay + n2.z * az));
-    const double3 nn[2] = {n1, n2};
+    const uint8_t* cls = flags + (size_t)(1 + FR_MAX_LIGHTS) * S.E;
     for (int j = 0; j < S.NL; ++j) {
-        const LightDev& L = S.lights[j];
-        double lo[2], hi[2];
-        for (int q = 0; q < 2; ++q) {
-            const double base = nn[q].x * ((double)L.c.x - ax) + nn[q].y * ((double)L.c.y - ay) + nn[q].z * ((double)L.c.z - az);
-            const double g1 = nn[q].x * L.e1.x + nn[q].y * L.e1.y + nn[q].z * L.e1.z;
-            const double g2 = nn[q].x * L.e2.x + nn[q].y * L.e2.y + nn[q].z * L.e2.z;
-            if (L.type == 0) {
-                const double h = 0.5 * fabs(g1) + 0.5 * fabs(g2);
-                lo[q] = base - h; hi[q] = base + h;
-            } else if (L.type == 1) {
-                lo[q] = base + fmin(0.0, fmin(g1, g2)); hi[q] = base + fmax(0.0, fmax(g1, g2));
-            } else {
-                const double r = sqrt(g1 * g1 + g2 * g2);
-                lo[q] = base - r; hi[q] = base + r;
-            }
-        }
-        const bool pos = lo[0] > 0.0 && lo[1] > 0.0;
-        const bool neg = hi[0] < 0.0 && hi[1] < 0.0;
-        flags[(size_t)(1 + j) * S.E + e] = !(pos || neg);
+        const uint8_t c1 = cls[(size_t)j * S.T + E.z], c2 = cls[(size_t)j * S.T + E.w];
+        flags[(size_t)(1 + j) * S.E + e] = !((c1 == 1 && c2 == 1) || (c1 == 2 && c2 == 2));
     }
 }
 
@@ -800,13 +816,14 @@ void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t
     fr_count_launches(1);
 }
 
-void launch_classify(const DevItem* items, int n, int E, int NL, cudaStream_t st) {
+void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st) {
+    k_face_class<<<dim3(blocks_for(T, 256), n), 256, 0, st>>>(items);
     k_classify<<<dim3(blocks_for(E, 256), n), 256, 0, st>>>(items);
     const int n_chunks = blocks_for(E, CMP_CHUNK);
     k_compact_count<<<dim3(n_chunks, 1 + NL, n), CMP_CHUNK, 0, st>>>(items, E, n_chunks);
     k_compact_scan<<<n, 128, 0, st>>>(items, 1 + NL, n_chunks);
     k_compact_scatter<<<dim3(n_chunks, 1 + NL, n), CMP_CHUNK, 0, st>>>(items, E, n_chunks);
-    fr_count_launches(4);
+    fr_count_launches(5);
 }
 
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri, float* t,
