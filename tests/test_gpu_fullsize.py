@@ -1,0 +1,82 @@
+"""Parity at the paper-scale workload (35,709 vertices / 70,789 triangles,
+K = 144, 256 x 256, 16 spp, 40 lights, 512^2 textures) in the launch
+configuration the benchmark times, on outputs the oracle can compute one by
+one: per-sample records and radiance at sampled pixels, and the gradient of an
+adjoint image that is non-zero on a few pixels only (all terms)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_05356_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def c2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_05356_gb300 import facert
+    sc = synth.make_scene("c2")
+    pr = synth.random_params(sc, 4)
+    r = facert.Renderer(sc, edge_spp=1)
+    return sc, pr, r
+
+
+def test_records_and_radiance_at_sampled_pixels(c2):
+    sc, pr, r = c2
+    dp = r.device_params(pr)
+    img, tri, mask = r.records(dp, iteration=7)
+    rng = np.random.default_rng(0)
+    # half the sample on the face, half anywhere
+    tri_np = tri.cpu().numpy().reshape(-1, sc.spp)
+    on_face = np.nonzero((tri_np >= 0).any(axis=1))[0]
+    pix = np.unique(np.concatenate([rng.choice(on_face, 32, replace=False),
+                                    rng.choice(sc.width * sc.height, 16, replace=False)])).astype(np.int32)
+    oi, ot, om = oracle.render(sc, pr, iteration=7, pixels=pix, records=True)
+    ot = ot.reshape(-1, sc.spp)[pix]
+    om = om.reshape(-1, sc.spp)[pix]
+    gt = tri_np[pix]
+    gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp)[pix]
+    agree = (gt == ot) & (gm == om)
+    assert np.mean(~agree) <= 2e-3, int(np.sum(~agree))
+    ok = agree.all(axis=1)
+    g = img.cpu().numpy().reshape(-1, 3)[pix]
+    o = oi.reshape(-1, 3)[pix]
+    scale = 1e-2 * max(o.mean(), 1e-6)
+    err = np.abs(g - o) / np.maximum(np.abs(o), scale)
+    assert np.max(err[ok]) <= 1e-4, float(np.max(err[ok]))
+
+
+def test_gradients_of_a_sparse_adjoint_image(c2):
+    sc, pr, r = c2
+    from paper_2101_05356_gb300 import facert
+    dp = r.device_params(pr)
+    E = r.n_edges
+    # the ordered silhouette lists must agree for the edge samples to match
+    prim = torch.empty(E, dtype=torch.int32, device="cuda")
+    npr = torch.empty(1, dtype=torch.int32, device="cuda")
+    facert.fr_debug_silhouettes(r.ctx, dp, prim, npr, None, None)
+    po, _ = oracle.silhouettes(sc, pr)
+    assert np.array_equal(prim.cpu().numpy()[: int(npr.item())], po)
+    img, tri, mask = r.records(dp, iteration=3)
+    tri_np = tri.cpu().numpy().reshape(-1, sc.spp)
+    on_face = np.nonzero((tri_np >= 0).all(axis=1))[0]
+    pix = np.random.default_rng(1).choice(on_face, 12, replace=False)
+    # keep pixels whose records agree with the oracle
+    _, ot, om = oracle.render(sc, pr, iteration=3, pixels=pix.astype(np.int32), records=True)
+    gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp)
+    keep = [p for p in pix if np.array_equal(tri_np[p], ot.reshape(-1, sc.spp)[p])
+            and np.array_equal(gm[p], om.reshape(-1, sc.spp)[p])]
+    assert len(keep) >= 10
+    adj = np.zeros((sc.height, sc.width, 3))
+    adj.reshape(-1, 3)[keep] = np.random.default_rng(2).uniform(0.3, 1.0, (len(keep), 3))
+    adj32 = adj.astype(np.float32)
+    gg = r.backward(dp, torch.as_tensor(adj32).cuda(), iteration=3)
+    go = oracle.grad(sc, pr, adj32.astype(np.float64), iteration=3, edge_spp=1)
+    for k in ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness"):
+        a = gg[k].cpu().numpy().astype(np.float64).ravel()
+        b = np.asarray(go[k]).ravel()
+        nb = np.linalg.norm(b)
+        assert np.linalg.norm(a - b) <= 2e-3 * max(nb, 1e-9), (k, float(np.linalg.norm(a - b) / max(nb, 1e-30)))
