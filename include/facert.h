@@ -91,7 +91,7 @@ typedef struct fr_mesh {
  *   (v-1/2) e2; triangle: c, c+e1, c+e2; disk: centre c, radius vectors e1, e2.
  *   The emitting side is the one e1 x e2 points to.  Geometry is in camera space.
  *   d [N_L], a [N_L]: distance and relative area of Eq. (lightIntensity); the
- *   emitted radiance is (d^2 / a) * i_j.  N_L <= 64. */
+ *   emitted radiance is (d^2 / a) * i_j.  N_L <= 128. */
 typedef struct fr_light_stage {
     int32_t n_lights;
     const float* records;
@@ -212,7 +212,7 @@ fr_status fr_debug_trace(fr_ctx* ctx, const fr_params* p, const float* org, cons
 
 /* Forward render that also writes per-sample records: tri_rec [H*W*spp] hit
  * triangle (-1 miss) and mask_rec [H*W*spp] bit j = shadow ray to light j
- * traced and unoccluded; record index = (y*W + x)*spp + sample. */
+ * traced and unoccluded (lights 0..63 only); record index = (y*W + x)*spp + sample. */
 fr_status fr_debug_records(fr_ctx* ctx, const fr_params* p, float* image, int32_t* tri_rec,
                            uint64_t* mask_rec, uint32_t iteration, uint32_t face_id,
                            void* stream);

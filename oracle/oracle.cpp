@@ -540,11 +540,13 @@ D bilinear(const float* tex, int M, int channels, int ch, const D& u, const D& v
 // One camera sample: the Monte Carlo estimator F of Sec. 4 (Eq. energy) for
 // direct lighting from every light-stage emitter with shadow rays (Sec. 3.3).
 // ---------------------------------------------------------------------------
+constexpr int ORA_MAX_LIGHTS = 128;  // lights with an intensity gradient
+
 struct SampleOut {
     int tri = -1;
-    uint64_t mask = 0;          // bit j: shadow ray to light j traced and unoccluded
+    uint64_t mask[2] = {0, 0};  // bit j of word j / 64: shadow ray to light j traced and unoccluded
     D L[3];                     // radiance (duals when gradients are requested)
-    double dLdi[64][3];         // d L / d i_j per channel (visible lights only)
+    double dLdi[ORA_MAX_LIGHTS][3];  // d L / d i_j per channel (visible lights only)
     Tap tap;                    // bilinear taps at the hit (texture gradients)
     P3 y;                       // hit point
     V3 yd;                      // hit point as duals
@@ -579,7 +581,7 @@ void hit_duals(const Prep& P, int tri, const V3& d, D& b1, D& b2, V3& y) {
 // light dimensions starting at `light_dim0`.  If `fixed_tri` >= 0 the hit
 // triangle and the visibility mask `fixed_mask` are imposed (gradient pass).
 void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim0, SampleOut& out,
-                  int fixed_tri = -2, uint64_t fixed_mask = 0) {
+                  int fixed_tri = -2, const uint64_t* fixed_mask = nullptr) {
     const OraScene* s = P.s;
     V3 dd = camera_dir(P, sx, sy);
     int tri;
@@ -590,9 +592,9 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
         tri = fixed_tri;
     }
     out.tri = tri;
-    out.mask = 0;
+    out.mask[0] = out.mask[1] = 0;
     for (int k = 0; k < 3; ++k) out.L[k] = D(0.0);
-    for (int j = 0; j < P.NL && j < 64; ++j) out.dLdi[j][0] = out.dLdi[j][1] = out.dLdi[j][2] = 0.0;
+    for (int j = 0; j < P.NL && j < ORA_MAX_LIGHTS; ++j) out.dLdi[j][0] = out.dLdi[j][1] = out.dLdi[j][2] = 0.0;
     if (tri < 0) return;
     D b1, b2;
     V3 y;
@@ -631,9 +633,9 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
         if (!(cos_s.v > 0.0) || !(cos_l.v > 0.0)) continue;
         bool vis;
         if (fixed_tri == -2) vis = !occluded(P, val(y), z, tri);
-        else vis = (fixed_mask >> j) & 1ull;
+        else vis = (fixed_mask[j >> 6] >> (j & 63)) & 1ull;
         if (!vis) continue;
-        if (j < 64) out.mask |= (1ull << j);
+        out.mask[j >> 6] |= (1ull << (j & 63));
         D f[3];
         brdf(s->flags, ns, l, o, c, sp, r, f);
         D geo = cos_s * cos_l / dist2 * Lj.area;
@@ -641,7 +643,7 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
             double I = Lj.scale * (double)P.p->light_i[3 * j + k];   // Eq. lightIntensity
             D term = f[k] * geo;
             out.L[k] = out.L[k] + term * I;
-            if (j < 64) out.dLdi[j][k] = term.v * Lj.scale;
+            if (j < ORA_MAX_LIGHTS) out.dLdi[j][k] = term.v * Lj.scale;
         }
     }
 }
@@ -856,7 +858,7 @@ int ora_render(const OraScene* s, const OraParams* p, uint32_t iteration, uint32
             for (int k = 0; k < 3; ++k) acc[k] += so.L[k].v;
             size_t rec = (size_t)pix * P.spp + smp;
             if (tri_rec) tri_rec[rec] = so.tri;
-            if (mask_rec) mask_rec[rec] = so.mask;
+            if (mask_rec) mask_rec[rec] = so.mask[0];   // lights 0..63
         }
         for (int k = 0; k < 3; ++k) image[(size_t)pix * 3 + k] = acc[k] / P.spp;
     });
@@ -904,7 +906,7 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
              const double* adjoint, uint32_t terms, double* g_coef, double* g_rot, double* g_trans,
              double* g_focal, double* g_light, double* g_diffuse, double* g_specular,
              double* g_roughness) {
-    if (s->n_basis + 15 > DMAX || s->n_lights > 64) return -1;
+    if (s->n_basis + 15 > DMAX || s->n_lights > ORA_MAX_LIGHTS) return -1;
     Prep P;
     prepare(P, s, p, s->n_basis + 15);
     classify(P);

@@ -249,7 +249,7 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     }
     if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, c->T, st);
     mark(c, 4, st);
-    launch_adjoint(c->d_items, map_of(c, n, false), st);
+    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, st);
     mark(c, 5, st);
     launch_edge_primary(c->d_items, map_of(c, n, true), st);
     mark(c, 6, st);
@@ -465,7 +465,7 @@ fr_status fr_set_mesh(fr_ctx* c, const fr_mesh* m) {
 
 fr_status fr_set_lights(fr_ctx* c, const fr_light_stage* ls) {
     if (!c || !ls || !ls->records || !ls->d || !ls->a) return fail(c, FR_EINVAL, "null argument");
-    if (ls->n_lights < 1 || ls->n_lights > FR_MAX_LIGHTS) return fail(c, FR_EINVAL, "1 <= n_lights <= 64");
+    if (ls->n_lights < 1 || ls->n_lights > FR_MAX_LIGHTS) return fail(c, FR_EINVAL, "1 <= n_lights <= 128");
     std::vector<LightDev> L(ls->n_lights);
     for (int j = 0; j < ls->n_lights; ++j) {
         const float* r = ls->records + 11 * j;

@@ -11,7 +11,7 @@
 #define FR_STATUS_TIMEOUT 2
 #define FR_STATUS_BAD_BVH 4
 
-constexpr int FR_MAX_LIGHTS = 64;
+constexpr int FR_MAX_LIGHTS = 128;
 constexpr int FR_MAX_BASIS = 256;
 constexpr int FR_STACK = 64;           // traversal stack entries per thread
 constexpr float FR_PI = 3.14159265358979323846f;

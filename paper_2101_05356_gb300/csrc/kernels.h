@@ -35,7 +35,7 @@ void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);
 
 // render.cu
 void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st);
-void launch_adjoint(const DevItem* items, const BlockMap& map, cudaStream_t st);
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, cudaStream_t st);
 void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri,

@@ -45,8 +45,11 @@ struct RtShared {
     int stack[FR_STACK * RT_THREADS];
 #endif
     WarpQueue wq[RT_WARPS];
-    double acc[RT_WARPS][1 + 3 * FR_MAX_LIGHTS];  // per-warp focal / light partials
 };
+
+// Per-warp focal / light-intensity partials of the adjoint kernels live in
+// dynamic shared memory: RT_WARPS rows of n = 1 + 3 N_L doubles.
+extern __shared__ double acc_dyn[];
 
 #if FR_STACK_LOCAL
 #define FR_STACK_DECL int lstack_[FR_STACK];
@@ -132,18 +135,19 @@ FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st, RayS
     __syncwarp();
 }
 
-// Warp-cooperative shadow visibility for every light: bit j set when the shadow
-// ray to this lane's light-j sample is traced and unoccluded.  All 32 lanes
-// must call this together.
+// Warp-cooperative shadow visibility for the lights [j0, j0 + 64): bit j - j0
+// is set when the shadow ray to this lane's light-j sample is traced and
+// unoccluded.  All 32 lanes must call this together.
 FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sampler& smp, int dim0,
-                          WarpQueue& q, Stack st, RayStats& rs) {
+                          WarpQueue& q, Stack st, RayStats& rs, int j0) {
     const int lane = threadIdx.x & 31;
     q.vis[lane] = 0ull;
     __syncwarp();
     const bool want = ss.hit && dot(ss.ns, ss.o) > 0.0f && !(S.flags & FR_FLAG_FLAT_D);
     int head = 0, count = 0;
     DimCache dc;
-    for (int j = 0; j < S.NL; ++j) {
+    const int j1 = min(S.NL, j0 + 64);
+    for (int j = j0; j < j1; ++j) {
         bool need = false;
         float3 z = f3(0.0f, 0.0f, 0.0f);
         if (want) {
@@ -156,7 +160,7 @@ FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sample
         if (need) {
             const int slot = (head + count + __popc(ballot & ((1u << lane) - 1u))) & 63;
             q.job[slot][0] = make_float4(ss.y.x, ss.y.y, ss.y.z, z.x);
-            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.tri), __int_as_float(lane | (j << 8)));
+            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.tri), __int_as_float(lane | ((j - j0) << 8)));
         }
         count += __popc(ballot);
         __syncwarp();
@@ -209,13 +213,14 @@ FR_D float3 intensity(const DevScene& S, const DevParams& P, int j) {
 
 // Radiance of this lane's sample given its state and visibility mask.
 FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleState& ss, uint64_t vis,
-                          const Sampler& smp, int dim0) {
+                          const Sampler& smp, int dim0, int j0) {
     float3 Lo = f3(0.0f, 0.0f, 0.0f);
     if (!ss.hit) return Lo;
-    if (S.flags & FR_FLAG_FLAT_D) return ss.m.c;
+    if (S.flags & FR_FLAG_FLAT_D) return j0 == 0 ? ss.m.c : Lo;
     DimCache dc;
-    for (int j = 0; j < S.NL; ++j) {
-        if (!((vis >> j) & 1ull)) continue;
+    const int j1 = min(S.NL, j0 + 64);
+    for (int j = j0; j < j1; ++j) {
+        if (!((vis >> (j - j0)) & 1ull)) continue;
         const LightDev& L = S.lights[j];
         const float2 u = dc.pair(smp, dim0 + 2 * j);
         const float3 z = light_point(L, u.x, u.y);
@@ -231,8 +236,13 @@ FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, floa
                         const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t& vis,
                         RayStats& rs) {
     primary_state(S, P, active, sx, sy, stk, ss, rs);
-    vis = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs);
-    return radiance_from(S, P, ss, vis, smp, dim0);
+    float3 Lo = f3(0.0f, 0.0f, 0.0f);
+    for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) {          // lights in chunks of 64 (warp-uniform)
+        const uint64_t v = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
+        if (j0 == 0) vis = v;                                  // records keep lights 0..63
+        Lo += radiance_from(S, P, ss, v, smp, dim0, j0);
+    }
+    return Lo;
 }
 
 FR_D float warp_sum(float v) {
@@ -289,17 +299,17 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
 // ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
-FR_D void block_acc_init(RtShared& sh, int n) {
-    for (int i = threadIdx.x; i < RT_WARPS * n; i += RT_THREADS) sh.acc[i / n][i % n] = 0.0;
+FR_D void block_acc_init(int n) {
+    for (int i = threadIdx.x; i < RT_WARPS * n; i += RT_THREADS) acc_dyn[i] = 0.0;
     __syncthreads();
 }
 
 // per-warp partials summed in warp order, then one fixed-point add per value
-FR_D void block_acc_flush(RtShared& sh, int n, fix64* out) {
+FR_D void block_acc_flush(int n, fix64* out) {
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += RT_THREADS) {
         double s = 0.0;
-        for (int w = 0; w < RT_WARPS; ++w) s += sh.acc[w][i];
+        for (int w = 0; w < RT_WARPS; ++w) s += acc_dyn[w * n + i];
         if (s != 0.0) atomicAdd(&out[i], (fix64)to_fix_d(s));
     }
 }
@@ -406,7 +416,8 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     const EdgeLists& EL = it.EL;
     const float* adj_image = it.adj;
     const uint32_t iteration = it.iteration, face = it.face;
-    block_acc_init(sh, 1 + 3 * S.NL);
+    const int n_acc = 1 + 3 * S.NL;
+    block_acc_init(n_acc);
     const long total = (long)S.W * S.H * S.spp;
     const long qi = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
     bool valid = qi < total;
@@ -425,7 +436,6 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     SampleState ss;
     RayStats rs;
     primary_state(S, P, valid, sx, sy, my_stack(sh), ss, rs);
-    const uint64_t vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs);
     const bool interior = !(S.flags & FR_FLAG_NO_INTERIOR_D);
     ShadeAdj g;
     g.n = g.l = g.o = g.c = g.s = f3(0.0f, 0.0f, 0.0f);
@@ -435,9 +445,12 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
         if (ss.hit && interior) g.c = w;
     } else {
         DimCache dc;
+        uint64_t vis = 0ull;
         for (int j = 0; j < S.NL; ++j) {                       // warp-uniform loop
+            if ((j & 63) == 0)                                 // lights in chunks of 64
+                vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
             float3 gI = f3(0.0f, 0.0f, 0.0f);
-            if (interior && ss.hit && ((vis >> j) & 1ull)) {
+            if (interior && ss.hit && ((vis >> (j & 63)) & 1ull)) {
                 const LightDev& L = S.lights[j];
                 const float2 u = dc.pair(smp, 2 + 2 * j);
                 const float3 z = light_point(L, u.x, u.y);
@@ -448,7 +461,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
             }
             const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
             if ((threadIdx.x & 31) == 0) {
-                double* wa = sh.acc[threadIdx.x >> 5];
+                double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc;
                 wa[1 + 3 * j] += (double)sx_;
                 wa[1 + 3 * j + 1] += (double)sy_;
                 wa[1 + 3 * j + 2] += (double)sz_;
@@ -550,9 +563,9 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
         scatter_texel(G.tex + 6 * M2, 1, taps[k], 0, gtex[6] * tw[k], tex_on);
     }
     const float gf_w = warp_sum(gfocal);
-    if ((threadIdx.x & 31) == 0) sh.acc[threadIdx.x >> 5][0] += (double)gf_w;
+    if ((threadIdx.x & 31) == 0) acc_dyn[(threadIdx.x >> 5) * n_acc] += (double)gf_w;
     flush_stats(S.counters + 3, rs);
-    block_acc_flush(sh, 1 + 3 * S.NL, G.small);
+    block_acc_flush(n_acc, G.small);
 }
 
 // ---------------------------------------------------------------------------
@@ -569,7 +582,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_edge_primary(
     const EdgeLists& EL = it.EL;
     const float* adj_image = it.adj;
     const uint32_t iteration = it.iteration, face = it.face;
-    block_acc_init(sh, 1);
+    block_acc_init(1);
     const long n_edge = (long)S.W * S.H * S.edge_spp;
     const long e = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
     bool active = e < n_edge;
@@ -629,8 +642,8 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_edge_primary(
     scatter_vertex(G.d_v, E.x, gA, active);
     scatter_vertex(G.d_v, E.y, gB, active);
     const float gw = warp_sum(gf);
-    if ((threadIdx.x & 31) == 0) sh.acc[threadIdx.x >> 5][0] += (double)gw;
-    block_acc_flush(sh, 1, G.small);
+    if ((threadIdx.x & 31) == 0) acc_dyn[threadIdx.x >> 5] += (double)gw;
+    block_acc_flush(1, G.small);
 }
 
 // ---------------------------------------------------------------------------
@@ -804,15 +817,16 @@ void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) 
     fr_count_launches(1);
 }
 
-void launch_adjoint(const DevItem* items, const BlockMap& map, cudaStream_t st) {
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    k_adjoint<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+    const size_t acc_bytes = sizeof(double) * RT_WARPS * (1 + 3 * (size_t)NL);
+    k_adjoint<<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
     fr_count_launches(1);
 }
 
 void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    k_edge_primary<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+    k_edge_primary<<<map_blocks(map), RT_THREADS, sizeof(double) * RT_WARPS, st>>>(items, map);
     fr_count_launches(1);
 }
 

@@ -180,6 +180,64 @@ def face_icosphere(rng, level=4, n_shape=20, n_expr=0):
     return mean, basis, faces, uv
 
 
+def bisect_edges(p, faces, n_edges, rng):
+    """Bisect `n_edges` edges of a closed mesh on the unit sphere, no two of
+    them on a common triangle: the new vertex is the edge midpoint pushed back
+    onto the sphere, and each of the edge's two triangles splits in two
+    (orientation kept), so the mesh gains n_edges vertices and 2 n_edges
+    triangles.  Edges are taken in a seeded random order."""
+    faces = [tuple(int(x) for x in f) for f in faces]
+    owner = {}                                   # directed edge (a, b) -> face
+    for fi, (a, b, c) in enumerate(faces):
+        owner[(a, b)] = fi
+        owner[(b, c)] = fi
+        owner[(c, a)] = fi
+    undirected = sorted((a, b) for (a, b) in owner if a < b)
+    used = np.zeros(len(faces), dtype=bool)
+    verts = [q for q in np.asarray(p, dtype=np.float64)]
+    done = 0
+    for idx in rng.permutation(len(undirected)):
+        if done == n_edges:
+            break
+        a, b = undirected[idx]
+        f1, f2 = owner[(a, b)], owner[(b, a)]
+        if used[f1] or used[f2]:
+            continue
+        used[f1] = used[f2] = True
+        q = verts[a] + verts[b]
+        verts.append(q / np.linalg.norm(q))
+        m = len(verts) - 1
+        for f, (s, t) in ((f1, (a, b)), (f2, (b, a))):
+            tri = faces[f]
+            k = tri.index(s)                     # rotate so the triangle reads (s, t, o)
+            o = tri[(k + 2) % 3]
+            faces[f] = (s, m, o)
+            faces.append((m, t, o))
+        done += 1
+    if done != n_edges:
+        raise ValueError("not enough independent edges")
+    return np.array(verts), np.array(faces, dtype=np.int32)
+
+
+def face_subdivided(rng, n_triangles=100_000, level=6, n_shape=20):
+    """The level-4 head of face_icosphere refined to `n_triangles`: the
+    icosphere is subdivided to `level` (81,920 triangles at level 6), then
+    (n_triangles - 20 * 4^level) / 2 independent edges are bisected, and the
+    head warp, UVs and shape basis are applied to the refined sphere.
+    100,000 triangles give 50,002 vertices."""
+    p, faces = icosphere(level)
+    extra = n_triangles - faces.shape[0]
+    if extra < 0 or extra % 2:
+        raise ValueError("n_triangles - 20 * 4^level must be even and >= 0")
+    p, faces = bisect_edges(p, faces, extra // 2, rng)
+    radial = 1.0 + _face_features(p)
+    scale = np.array([0.75, 0.95, 0.70])
+    mean = p * radial[:, None] * scale
+    uv = np.stack([(p[:, 0] + 1.0) * 0.5, (1.0 - p[:, 1]) * 0.5], axis=1)
+    basis = _rbf_columns(rng, p, p, n_shape, 0.05)
+    return mean, basis, faces, uv
+
+
 def _disk_rings(n_vertices, n_boundary):
     """Ring sizes (centre vertex excluded) for a disk mesh with exactly
     n_vertices vertices and n_boundary vertices on the outer ring."""
@@ -344,6 +402,8 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
            hemisphere of radius 3, 128^2 textures.
     c2   : 35,709 verts / 70,789 tris, K = 80 + 64, 256x256, 16 spp,
            40 quads on a sphere, 512^2 textures.
+    c5   : 50,002 verts / 100,000 tris refined from the c1 head, K = 20,
+           1024x1024, 64 spp, 80 quads on a sphere, 2048^2 textures.
     tiny : a small closed mesh for fast CPU tests (162 verts / 320 tris, K = 6,
            24x24, 2 spp, 4 lights).
     Keyword overrides replace width/height/spp/tex_size/n_lights/light kind."""
@@ -358,6 +418,11 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
         ks, ke = 80, 64
         w = h = 256
         spp, m, nl, hemi = 16, 512, 40, False
+    elif config == "c5":
+        mean, basis, faces, uv = face_subdivided(rng, 100_000, 6, 20)
+        ks, ke = 20, 0
+        w = h = 1024
+        spp, m, nl, hemi = 64, 2048, 80, False
     elif config == "tiny":
         mean, basis, faces, uv = face_icosphere(rng, 2, 4, 2)
         ks, ke = 4, 2

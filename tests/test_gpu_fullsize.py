@@ -1,8 +1,10 @@
-"""Parity at the paper-scale workload (35,709 vertices / 70,789 triangles,
-K = 144, 256 x 256, 16 spp, 40 lights, 512^2 textures) in the launch
-configuration the benchmark times, on outputs the oracle can compute one by
-one: per-sample records and radiance at sampled pixels, and the gradient of an
-adjoint image that is non-zero on a few pixels only (all terms)."""
+"""Parity at full size, on outputs the oracle can compute one by one:
+per-sample records and radiance at sampled pixels, and the gradient of an
+adjoint image that is non-zero on a few pixels only (all terms).  Two
+workloads: the paper-scale face (35,709 vertices / 70,789 triangles, K = 144,
+256 x 256, 16 spp, 40 lights, 512^2 textures) in the launch configuration the
+benchmark times, and the large one (50,002 vertices / 100,000 triangles,
+K = 20, 1024 x 1024, 64 spp, 80 lights, 2048^2 textures)."""
 import numpy as np
 import pytest
 
@@ -13,15 +15,21 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def c2():
+# (config, pixels on the face, pixels anywhere) for the radiance check
+SAMPLES = {"c2": (32, 16), "c5": (16, 8)}
+
+
+@pytest.fixture(scope="module", params=["c2", "c5"])
+def c2(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2101_05356_gb300 import facert
-    sc = synth.make_scene("c2")
+    sc = synth.make_scene(request.param)
     pr = synth.random_params(sc, 4)
     r = facert.Renderer(sc, edge_spp=1)
-    return sc, pr, r
+    yield sc, pr, r
+    r.close()
+    torch.cuda.empty_cache()
 
 
 def test_records_and_radiance_at_sampled_pixels(c2):
@@ -32,8 +40,9 @@ def test_records_and_radiance_at_sampled_pixels(c2):
     # half the sample on the face, half anywhere
     tri_np = tri.cpu().numpy().reshape(-1, sc.spp)
     on_face = np.nonzero((tri_np >= 0).any(axis=1))[0]
-    pix = np.unique(np.concatenate([rng.choice(on_face, 32, replace=False),
-                                    rng.choice(sc.width * sc.height, 16, replace=False)])).astype(np.int32)
+    n_face, n_any = SAMPLES["c5" if sc.width > 512 else "c2"]
+    pix = np.unique(np.concatenate([rng.choice(on_face, n_face, replace=False),
+                                    rng.choice(sc.width * sc.height, n_any, replace=False)])).astype(np.int32)
     oi, ot, om = oracle.render(sc, pr, iteration=7, pixels=pix, records=True)
     ot = ot.reshape(-1, sc.spp)[pix]
     om = om.reshape(-1, sc.spp)[pix]

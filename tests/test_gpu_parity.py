@@ -35,6 +35,8 @@ SCENES = {
     "c1": lambda: (synth.make_scene("c1"), None),
     "ragged": lambda: (synth.make_scene("tiny", width=37, height=29, spp=8), None),
     "box": lambda: scenes.shadow_box(),
+    # 80 lights: two 64-light visibility chunks
+    "many": lambda: (synth.make_scene("tiny", n_lights=80), None),
 }
 
 
@@ -122,7 +124,7 @@ def _records_and_image(sc, pr, r, dp, iteration=0):
     return img.cpu().numpy(), oi, agree, px_ok
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "ragged", "box"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "ragged", "box", "many"])
 def test_forward_parity(name):
     sc, pr = _scene(name)
     r = _renderer(sc)
@@ -204,7 +206,7 @@ def _compare_grads(gg, go, groups, rtol=1e-3):
         assert np.linalg.norm(a - b) <= rtol * nb, (k, np.linalg.norm(a - b) / nb)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "box"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "box", "many"])
 def test_interior_gradient_parity(name):
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)
@@ -228,7 +230,7 @@ def test_primary_edge_gradient_parity(name):
     _compare_grads(gg, go, ["coef", "rot", "trans", "focal"], rtol=2e-3)
 
 
-@pytest.mark.parametrize("name", ["tiny", "box"])
+@pytest.mark.parametrize("name", ["tiny", "box", "many"])
 def test_shadow_edge_gradient_parity(name):
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)

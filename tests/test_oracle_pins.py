@@ -443,6 +443,25 @@ def test_light_gradient_is_single_light_image(tiny):
     assert np.allclose(tot, oracle.render(sc, pr), rtol=1e-12, atol=1e-15)
 
 
+def test_light_gradient_beyond_64_lights():
+    """80 lights (the large light stage): the intensity gradient of lights past
+    the 64th is still the single-light image, and the lights sum to the image."""
+    sc = synth.make_scene("tiny", width=12, height=12, spp=2, n_lights=80)
+    pr = synth.random_params(sc, 3)
+    adj = np.random.default_rng(4).uniform(0.2, 1.0, (12, 12, 3))
+    g = oracle.grad(sc, pr, adj, terms=oracle.TERM_INTERIOR)
+    tot = np.zeros((12, 12, 3))
+    for j in range(sc.n_lights):
+        q = pr.copy()
+        q.light_i[:] = 0.0
+        q.light_i[j] = 1.0
+        img = oracle.render(sc, q)
+        assert np.allclose(g["light_i"][j], np.sum(adj * img, axis=(0, 1)), rtol=1e-10, atol=1e-14), j
+        tot += img * pr.light_i[j]
+    assert np.abs(g["light_i"][64:]).sum() > 0.0
+    assert np.allclose(tot, oracle.render(sc, pr), rtol=1e-12, atol=1e-15)
+
+
 @pytest.mark.parametrize("name", ["diffuse", "specular"])
 def test_texture_gradient_exact_by_linearity(tiny, name):
     sc, pr, adj = tiny
