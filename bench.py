@@ -3,16 +3,19 @@
 
 One step = one pass of the hot path over one face: morph, pose + normals, LBVH
 build, camera + shadow rays with Cook-Torrance shading, blur + L1 loss, and the
-adjoint (re-trace, interior term, shadow-boundary and primary-edge terms, chain
-to the parameters).  Workload: the paper-scale single face (35,709 vertices /
+adjoint (interior term from the forward's per-sample hit records, shadow-boundary
+and primary-edge terms, chain to the parameters).  Workload: the paper-scale single face (35,709 vertices /
 70,789 triangles, K = 80 + 64 bases, 256 x 256, 16 spp, 40 quad lights, 512^2
 textures), synthetic and seeded.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
 Prints one JSON line.  `value` is rays traced per second over the timed steps
-(inputs resident in HBM, L2 flushed between steps); `e2e` is the same metric
-with host buffers copied in and the loss copied out inside the timed region.
+(inputs resident in HBM, L2 flushed between steps; each ray of the step is
+traced once, the adjoint reading the forward's hit records); `e2e` is the same
+metric with host buffers copied in and the loss copied out inside the timed
+region; `retrace` times the same step with the adjoint re-tracing every camera
+and shadow ray instead (the form used when the records exceed their budget).
 The reference arm times the FP64 CPU oracle on a bounded sample of the same
 workload.  Under torchrun each rank renders an independent face (replicas).
 """
@@ -68,11 +71,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()                      # the timed region starts once sampling runs
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.skip = len(self.lines)           # samples taken before the timed region
 
     def _read(self):
         for line in self.proc.stdout:
@@ -88,7 +96,7 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], None, set()
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "skip", 0):]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -184,7 +192,7 @@ def gpu_arm(args, rank, world):
         total_ms_max, rays_all = total_ms, float(rays)
     value = rays_all / (total_ms_max / 1000.0)
 
-    # ---- dominant kernel roofline (adjoint re-trace kernel) ----
+    # ---- dominant kernel roofline ----
     pk, src = peaks()
     adj_ms = float(np.mean([s["adjoint"] for s in stage]))
     fwd_ms = float(np.mean([s["forward"] for s in stage]))
@@ -200,6 +208,34 @@ def gpu_arm(args, rank, world):
                 "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz (%s clocks)"
                                % (SMS, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src),
                 "ops_per_launch": ops_per_launch, "launch_ms": dom_ms}
+
+    # ---- the same step with the adjoint re-tracing its rays ----
+    retrace = None
+    if args.retrace_steps > 0:
+        facert.fr_set_flags(r.ctx, facert.FLAG_RECOMPUTE)
+        for w in range(3):
+            step(2 * 10 ** 5 + w)
+        facert.fr_counters(r.ctx, reset=True)
+        facert.fr_set_timing(r.ctx, True)
+        torch.cuda.synchronize()
+        rt, rst = [], []
+        for k in range(args.retrace_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(3 * 10 ** 5 + k)
+            e1.record(stream)
+            e1.synchronize()
+            rt.append(e0.elapsed_time(e1))
+            rst.append(facert.fr_get_timing(r.ctx))
+        facert.fr_set_timing(r.ctx, False)
+        cnt3 = facert.fr_counters(r.ctx, reset=True)
+        facert.fr_set_flags(r.ctx, 0)
+        rays3 = sum(v["rays"] for v in cnt3.values())
+        retrace = {"ms_per_step": float(np.mean(rt)), "rays_per_step": rays3 / args.retrace_steps,
+                   "rays_per_s": rays3 / (float(np.sum(rt)) / 1000.0), "steps": args.retrace_steps,
+                   "stage_ms": {k: float(np.mean([s_[k] for s_ in rst])) for k in rst[0]}}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -237,9 +273,10 @@ def gpu_arm(args, rank, world):
         "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "rays_per_step": rays / args.steps,
+                   "steps_per_s": 1000.0 * args.steps / total_ms_max,
                    "stage_ms": {k: float(np.mean([s[k] for s in stage])) for k in stage[0]}},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-        "status": int(status),
+        "retrace": retrace, "status": int(status),
     }
     return out
 
@@ -317,10 +354,11 @@ def cpu_baseline(sample_pixels, threads=0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--retrace-steps", type=int, default=5)
     ap.add_argument("--cpu-pixels", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=16)

@@ -54,6 +54,15 @@ typedef int32_t fr_status;
 #define FR_FLAG_NO_SHADOW_EDGE  64u   /* gradient: skip the shadow boundary term */
 #define FR_FLAG_MORPH_BF16     128u   /* morph as one BF16 tensor-core GEMM over the batch (FP32
                                          accumulate, FP32 mean); context-wide, read by every call */
+#define FR_FLAG_RECOMPUTE      256u   /* fused steps re-trace the adjoint's primary and shadow rays
+                                         even when the hit records fit (see fr_render) */
+
+/* Per-slot budget for the hit records of a fused step (bytes): a context whose
+ * width * height * spp * 20 bytes fit keeps, per slot, the forward's hit
+ * triangle and two 64-bit light-visibility words per camera sample, and the
+ * adjoint of the same step reads them instead of re-tracing.  Larger images
+ * recompute them (the adjoint re-traces with the same Philox counters). */
+#define FR_RECORDS_BUDGET (256u << 20)
 
 /* emitter types in light records */
 #define FR_LIGHT_QUAD 0
@@ -151,7 +160,10 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
                   float* adj_image, float* blurred, void* stream);
 
 /* One full step of the hot path: fr_forward, fr_loss against `target`, and (if
- * g != NULL) fr_backward with the loss adjoint.  loss is a device double. */
+ * g != NULL) fr_backward with the loss adjoint.  loss is a device double.
+ * Within the step the adjoint reuses the forward's per-sample hit records
+ * (hit triangle and shadow visibility) when they fit FR_RECORDS_BUDGET and
+ * FR_FLAG_RECOMPUTE is clear; the gradient is the same either way. */
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);

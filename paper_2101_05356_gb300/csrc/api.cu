@@ -39,6 +39,9 @@ struct Slot {
     double* pose_part = nullptr;
     float* sign = nullptr;
     float* adj_image = nullptr;
+    int32_t* rec_tri = nullptr;      // fused-step hit records (null when over FR_RECORDS_BUDGET)
+    uint64_t* rec_vis = nullptr;
+    long rec_samples = 0;
 };
 
 }  // namespace
@@ -140,6 +143,7 @@ struct ItemArgs {
     const float* adj;           // image-space adjoint (null: the slot's loss adjoint)
     int32_t* tri_rec;
     uint64_t* mask_rec;
+    bool records;               // fused step: the adjoint may reuse the forward's hit records
 };
 
 DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
@@ -188,6 +192,10 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.adj = a.adj ? a.adj : sl.adj_image;
     it.tri_rec = a.tri_rec;
     it.mask_rec = a.mask_rec;
+    if (a.records && sl.rec_tri && !(a.flags & FR_FLAG_RECOMPUTE) && (long)a.W * a.H * a.spp <= sl.rec_samples) {
+        it.rec_tri = sl.rec_tri;
+        it.rec_vis = sl.rec_vis;
+    }
     it.iteration = a.iteration;
     it.face = a.face;
     return it;
@@ -310,6 +318,13 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.dm, 3 * (size_t)N));
     TRY(dalloc(c, &sl.small, 1 + 3 * FR_MAX_LIGHTS));
     TRY(dalloc(c, &sl.pose_part, 12 * (size_t)((N + 255) / 256)));
+    // hit records of a fused step: triangle + two visibility words per sample
+    const long samples = (long)c->cfg.width * c->cfg.height * c->cfg.spp;
+    if (samples * (long)(sizeof(int32_t) + 2 * sizeof(uint64_t)) <= (long)FR_RECORDS_BUDGET) {
+        TRY(dalloc(c, &sl.rec_tri, (size_t)samples));
+        TRY(dalloc(c, &sl.rec_vis, 2 * (size_t)samples));
+        sl.rec_samples = samples;
+    }
     return FR_OK;
 }
 
@@ -328,6 +343,7 @@ ItemArgs single(fr_ctx* c, const fr_params* p, const fr_grads* g, float* image, 
     a.W = c->cfg.width; a.H = c->cfg.height; a.spp = c->cfg.spp; a.edge_spp = c->cfg.edge_spp;
     a.flags = c->cfg.flags; a.iteration = iteration; a.face = face;
     a.p = p; a.g = g; a.image = image; a.adj = adj; a.tri_rec = nullptr; a.mask_rec = nullptr;
+    a.records = false;
     return a;
 }
 
@@ -535,7 +551,9 @@ fr_status fr_render(fr_ctx* c, const fr_params* p, const float* target, float* i
     if (!image || !target || !loss) return fail(c, FR_EINVAL, "null argument");
     const cudaStream_t st = S_(stream);
     mark(c, 0, st);
-    c->h_items[0] = make_item(c, 0, single(c, p, g, image, nullptr, iteration, face_id));
+    ItemArgs a = single(c, p, g, image, nullptr, iteration, face_id);
+    a.records = g != nullptr;
+    c->h_items[0] = make_item(c, 0, a);
     TRY(upload(c, 1, st));
     build_geometry(c, 1, st);
     mark(c, 1, st);
@@ -567,6 +585,7 @@ fr_status fr_render_batch(fr_ctx* c, const fr_item* items, int32_t n, void* stre
         a.flags = x.flags; a.iteration = x.iteration; a.face = x.face_id;
         a.p = &x.params; a.g = x.grads; a.image = x.image; a.adj = nullptr; a.tri_rec = nullptr;
         a.mask_rec = nullptr;
+        a.records = true;
         c->h_items[k] = make_item(c, k, a);
         tg[k] = x.target;
         ls[k] = x.loss;

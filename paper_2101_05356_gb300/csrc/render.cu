@@ -71,15 +71,19 @@ struct SampleState {
 };
 
 // Primary ray through screen point (sx, sy) and the shading state at its hit.
+// rec >= -1 is this ray's recorded hit triangle (-1: miss) and replaces the
+// traversal; rec = REC_TRACE traces.
+constexpr int REC_TRACE = -2;
+
 FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
-                        Stack st, SampleState& ss, RayStats& rs) {
+                        Stack st, SampleState& ss, RayStats& rs, int rec = REC_TRACE) {
     ss.hit = false;
     ss.tri = -1;
     if (!active) return;
     const float f = __ldg(P.focal);
     ss.d = f3((sx - 0.5f * S.W) / f, -(sy - 0.5f * S.H) / f, -1.0f);
     const RayPre r = ray_setup(f3(0.0f, 0.0f, 0.0f), ss.d);
-    const Hit h = trace_closest(S, r, 0.0f, INFINITY, st, rs);
+    const Hit h = rec == REC_TRACE ? trace_closest(S, r, 0.0f, INFINITY, st, rs) : hit_record(S, r, rec);
     if (h.tri < 0) return;
     ss.hit = true;
     ss.tri = h.tri;
@@ -233,13 +237,14 @@ FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleSta
 
 // Full warp-cooperative radiance evaluation at screen point (sx, sy).
 FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
-                        const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t& vis,
+                        const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t* vis,
                         RayStats& rs) {
     primary_state(S, P, active, sx, sy, stk, ss, rs);
     float3 Lo = f3(0.0f, 0.0f, 0.0f);
+    vis[0] = vis[1] = 0ull;
     for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) {          // lights in chunks of 64 (warp-uniform)
         const uint64_t v = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
-        if (j0 == 0) vis = v;                                  // records keep lights 0..63
+        vis[j0 >> 6] = v;
         Lo += radiance_from(S, P, ss, v, smp, dim0, j0);
     }
     return Lo;
@@ -276,13 +281,17 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
     const Sampler smp{make_uint2(S.seed, FR_STREAM_PRIMARY), (uint32_t)pixel, (uint32_t)s, iteration, face};
     const float2 jit = smp.pair(0);
     SampleState ss;
-    uint64_t vis;
+    uint64_t vis[2];
     RayStats rs;
     const float3 Lo = radiance_at(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
                                   smp, 2, sh, my_stack(sh), ss, vis, rs);
     flush_stats(S.counters + 0, rs);
     if (valid && tri_rec) tri_rec[q] = ss.tri;
-    if (valid && mask_rec) mask_rec[q] = vis;
+    if (valid && mask_rec) mask_rec[q] = vis[0];
+    if (valid && it.rec_tri) {
+        it.rec_tri[q] = ss.tri;
+        reinterpret_cast<ulonglong2*>(it.rec_vis)[q] = make_ulonglong2(vis[0], vis[1]);
+    }
     const int width = S.spp < 32 ? S.spp : 32;
     const float rx = group_sum(Lo.x, width), ry = group_sum(Lo.y, width), rz = group_sum(Lo.z, width);
     const float inv = 1.0f / (float)S.spp;
@@ -435,7 +444,11 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     const float sx = (float)(pixel % S.W) + jit.x, sy = (float)(pixel / S.W) + jit.y;
     SampleState ss;
     RayStats rs;
-    primary_state(S, P, valid, sx, sy, my_stack(sh), ss, rs);
+    // the forward of a fused step may have recorded this sample's hit and
+    // shadow visibility; otherwise both are re-traced with the same counters
+    const bool recorded = it.rec_tri != nullptr;           // block-uniform
+    primary_state(S, P, valid, sx, sy, my_stack(sh), ss, rs,
+                  recorded ? (valid ? it.rec_tri[qi] : -1) : REC_TRACE);
     const bool interior = !(S.flags & FR_FLAG_NO_INTERIOR_D);
     ShadeAdj g;
     g.n = g.l = g.o = g.c = g.s = f3(0.0f, 0.0f, 0.0f);
@@ -447,8 +460,12 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
         DimCache dc;
         uint64_t vis = 0ull;
         for (int j = 0; j < S.NL; ++j) {                       // warp-uniform loop
-            if ((j & 63) == 0)                                 // lights in chunks of 64
-                vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
+            if ((j & 63) == 0) {                               // lights in chunks of 64
+                if (recorded)
+                    vis = valid ? it.rec_vis[2 * qi + (j >> 6)] : 0ull;
+                else
+                    vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
+            }
             float3 gI = f3(0.0f, 0.0f, 0.0f);
             if (interior && ss.hit && ((vis >> (j & 63)) & 1ull)) {
                 const LightDev& L = S.lights[j];
@@ -623,7 +640,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_edge_primary(
     }
     const float eps = 1e-3f;
     SampleState ssp, ssm;
-    uint64_t visp, vism;
+    uint64_t visp[2], vism[2];
     RayStats rs;
     const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, my_stack(sh), ssp, visp, rs);
     const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, my_stack(sh), ssm, vism, rs);

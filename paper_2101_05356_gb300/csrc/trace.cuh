@@ -159,6 +159,24 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
     return h;
 }
 
+// Closest-hit result of a camera ray whose hit triangle is known from a record
+// of the same ray: the same watertight test on the same triangle reproduces
+// the traversal's t and barycentrics.  tri < 0 is a miss.
+FR_D Hit hit_record(const DevScene& s, const RayPre& r, int tri) {
+    Hit h;
+    h.t = INFINITY;
+    h.tri = -1;
+    h.b1 = h.b2 = 0.0f;
+    if (tri < 0) return h;
+    const int4 fc = __ldg(&s.faces[tri]);
+    float t, b1, b2;
+    if (hit_triangle(r, xyz(__ldg(&s.v[fc.x])), xyz(__ldg(&s.v[fc.y])), xyz(__ldg(&s.v[fc.z])), 0.0f, INFINITY, t, b1,
+                     b2)) {
+        h.t = t; h.b1 = b1; h.b2 = b2; h.tri = tri;
+    }
+    return h;
+}
+
 // Any hit in (tmin, tmax), skipping triangle `skip` (shadow rays).
 FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, int skip, Stack st,
                     RayStats& rs) {

@@ -19,6 +19,7 @@ FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EOVERFLOW, FR_ETIMEOUT = 0, 1, 2, 3, 4
 FLAG_GGX, FLAG_SCHLICK_LINEAR, FLAG_FLAT = 1, 2, 4
 FLAG_NO_INTERIOR, FLAG_NO_PRIMARY_EDGE, FLAG_NO_SHADOW_EDGE = 16, 32, 64
 FLAG_MORPH_BF16 = 128
+FLAG_RECOMPUTE = 256
 
 _vp = ctypes.c_void_p
 
