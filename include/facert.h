@@ -138,6 +138,40 @@ fr_status fr_set_mesh(fr_ctx* ctx, const fr_mesh* mesh);
 /* Copy the light-stage emitters (Sec. 3.3).  Synchronous.  Errors: FR_EINVAL. */
 fr_status fr_set_lights(fr_ctx* ctx, const fr_light_stage* stage);
 
+/* Statistical albedo model of Sec. 3.2 in UV texture space (host pointers,
+ * copied): diffuse C = a_r + Sigma_r beta and specular S = a_b + Sigma_b gamma,
+ * each [M][M][3] with M = tex_size.  mean_* [M*M*3]; basis_* [K][M*M*3]
+ * (column k contiguous); 0 <= K <= 256 per model (K = 0: the mean alone).
+ * Stage I of Sec. 4 optimises beta and gamma through these; Stage II starts
+ * the per-texel albedos from the result.  Synchronous.  Errors: FR_EINVAL,
+ * FR_ENOMEM, FR_ECUDA. */
+typedef struct fr_albedo_model {
+    int32_t k_diffuse, k_specular;
+    const float* mean_diffuse;
+    const float* basis_diffuse;
+    const float* mean_specular;
+    const float* basis_specular;
+} fr_albedo_model;
+fr_status fr_set_albedo(fr_ctx* ctx, const fr_albedo_model* model);
+
+/* Statistical albedos of n faces (1 <= n <= max_batch; host arrays of n device
+ * pointers): diffuse[b] = a_r + Sigma_r beta[b] and specular[b] = a_b +
+ * Sigma_b gamma[b], textures [M][M][3] (16-byte aligned), beta[b] [K_r],
+ * gamma[b] [K_b].  One launch per model for the whole batch: BF16 x BF16 ->
+ * FP32 tensor-core GEMM when the context has FR_FLAG_MORPH_BF16, else FP32.
+ * A NULL diffuse or specular array skips that model.  Errors: FR_EINVAL (no
+ * model set, bad n, null or misaligned pointer). */
+fr_status fr_albedo_morph(fr_ctx* ctx, int32_t n, const float* const* beta, const float* const* gamma,
+                          float* const* diffuse, float* const* specular, void* stream);
+
+/* Transpose of fr_albedo_morph for the adjoint: g_beta[b] += Sigma_r^T
+ * g_diffuse[b] and g_gamma[b] += Sigma_b^T g_specular[b] (FP32 products, FP64
+ * sums in a fixed order, so results are reproducible).  g_diffuse/g_specular
+ * are texture gradients [M][M][3] as fr_render adds them (16-byte aligned).
+ * A NULL g_beta or g_gamma array skips that model. */
+fr_status fr_albedo_adjoint(fr_ctx* ctx, int32_t n, const float* const* g_diffuse, const float* const* g_specular,
+                            float* const* g_beta, float* const* g_gamma, void* stream);
+
 /* Forward render (Sec. 4, F): morph, pose, normals, LBVH build, primary rays,
  * Cook-Torrance shading (App. A) with one area sample and one shadow ray per
  * light per camera sample.  image [H][W][3] receives the per-pixel mean.

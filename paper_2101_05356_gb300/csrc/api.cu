@@ -7,6 +7,7 @@
 // is written to device memory by one small kernel, and every stage is one
 // launch over all items.  The single-face calls are batches of one.
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -44,20 +45,30 @@ struct Slot {
     long rec_samples = 0;
 };
 
+// A linear model y = mean + basis * coef (shape morph, statistical albedo):
+// FP32 mean [ld] and basis [K][ld] with rows padded to ld, the same basis as
+// BF16 tensor-core operand tiles, and the adjoint's FP64 partials.
+struct LinearModel {
+    int rows = 0, K = 0, ld = 0, Kp = 0;
+    float* mean = nullptr;
+    float* basis = nullptr;
+    uint16_t* tiles = nullptr;           // [ceil(rows / 128)][128][Kp] BF16, no-swizzle K-major core matrices
+    uint16_t* coef_tile = nullptr;       // BF16 [32][Kp] gathered coefficients
+    double* part = nullptr;              // [FR_MAX_BATCH][K][linear_adj_chunks(rows)]
+};
+
 }  // namespace
 
 struct fr_ctx {
     fr_config cfg{};
     int max_batch = 1;
-    int N = 0, T = 0, K = 0, NL = 0, E = 0, ld = 0;
+    int N = 0, T = 0, K = 0, NL = 0, E = 0, ld = 0;   // ld = shape.ld
     bool have_mesh = false, have_lights = false;
     std::string err;
     // mesh and lights (shared by all slots)
-    float* mean = nullptr;
-    float* basis = nullptr;
-    uint16_t* basis_tiles = nullptr;          // BF16 tensor-core operand tiles [3N/128][128][Kp]
-    uint16_t* coef_tile = nullptr;            // BF16 [32][Kp] gathered coefficients
-    int Kp = 0;
+    LinearModel shape;                         // rows 3N
+    LinearModel albedo[2];                     // diffuse, specular; rows 3 M^2 (optional)
+    bool have_albedo = false;
     int4* faces = nullptr;
     float2* uv = nullptr;
     int* vf_off = nullptr;
@@ -222,11 +233,79 @@ fr_status upload(fr_ctx* c, int n, cudaStream_t st) {
     return FR_OK;
 }
 
-void morph(fr_ctx* c, int n, cudaStream_t st) {
-    if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && c->K > 0)
-        launch_morph_tc(c->basis_tiles, c->Kp, c->K, c->coef_tile, c->mean, 3 * c->N, c->d_items, n, c->status, st);
+// out_b = mean + basis * coef_b for the n faces of `t`, on the tensor cores
+// when the context has FR_FLAG_MORPH_BF16, else in FP32
+void linear_forward(fr_ctx* c, const LinearModel& m, const LinearTable& t, cudaStream_t st) {
+    if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && m.K > 0)
+        launch_linear_tc(m.tiles, m.Kp, m.K, m.coef_tile, m.mean, m.rows, t, c->status, st);
     else
-        launch_morph(c->mean, c->basis, c->ld, c->K, c->d_items, n, st);
+        launch_linear(m.mean, m.basis, m.ld, m.rows, m.K, t, st);
+}
+
+void morph(fr_ctx* c, int n, cudaStream_t st) {
+    LinearTable t;
+    t.n = n;
+    for (int k = 0; k < n; ++k) {
+        t.coef[k] = c->h_items[k].P.coef;
+        t.out[k] = c->slots[k].v_model;
+    }
+    linear_forward(c, c->shape, t, st);
+}
+
+void morph_adjoint(fr_ctx* c, int n, cudaStream_t st) {
+    LinearAdjTable t;
+    t.n = n;
+    for (int k = 0; k < n; ++k) {
+        t.g[k] = c->slots[k].d_vmodel;
+        t.g_coef[k] = c->h_items[k].g_coef;
+    }
+    launch_linear_adjoint(c->shape.basis, c->shape.ld, c->shape.rows, c->shape.K, t, c->shape.part, st);
+}
+
+// Upload a linear model (host mean [rows], basis [K][rows]) and build its
+// BF16 operand tiles: tile t holds rows 128t..128t+127 of the [rows x Kp]
+// basis in the no-swizzle K-major core-matrix layout (8 rows x 8 values per
+// 128-byte core matrix).
+fr_status upload_model(fr_ctx* c, LinearModel& m, int rows, int K, const float* mean, const float* basis) {
+    m.rows = rows;
+    m.K = K;
+    m.ld = ((rows + 31) / 32) * 32;
+    TRY(dalloc(c, &m.mean, m.ld));
+    TRY(dalloc(c, &m.basis, (size_t)std::max(K, 1) * m.ld));
+    std::vector<float> pad((size_t)m.ld, 0.0f);
+    std::copy(mean, mean + (size_t)rows, pad.begin());
+    CK(c, cudaMemcpy(m.mean, pad.data(), sizeof(float) * m.ld, cudaMemcpyHostToDevice));
+    for (int k = 0; k < K; ++k) {
+        std::fill(pad.begin(), pad.end(), 0.0f);
+        std::copy(basis + (size_t)k * rows, basis + (size_t)(k + 1) * rows, pad.begin());
+        CK(c, cudaMemcpy(m.basis + (size_t)k * m.ld, pad.data(), sizeof(float) * m.ld, cudaMemcpyHostToDevice));
+    }
+    if (K == 0) return FR_OK;
+    TRY(dalloc(c, &m.part, (size_t)FR_MAX_BATCH * K * linear_adj_chunks(rows)));
+    m.Kp = ((K + 15) / 16) * 16;
+    const int n_tiles = (rows + 127) / 128;
+    std::vector<uint16_t> bt((size_t)n_tiles * 128 * m.Kp, 0);
+    auto bf16 = [](float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        u += 0x7FFFu + ((u >> 16) & 1u);
+        return (uint16_t)(u >> 16);
+    };
+    for (int t = 0; t < n_tiles; ++t)
+        for (int rr = 0; rr < 128; ++rr) {
+            const int i = t * 128 + rr;
+            if (i >= rows) break;
+            const int g = rr >> 3, r = rr & 7;
+            for (int k = 0; k < K; ++k) {
+                const int cc = k >> 3, kk = k & 7;
+                const size_t off = (size_t)t * 128 * m.Kp + ((size_t)(g * (m.Kp / 8) + cc) * 128 + r * 16 + kk * 2) / 2;
+                bt[off] = bf16(basis[(size_t)k * rows + i]);
+            }
+        }
+    TRY(dalloc(c, &m.tiles, bt.size()));
+    TRY(dalloc(c, &m.coef_tile, (size_t)32 * m.Kp));
+    CK(c, cudaMemcpy(m.tiles, bt.data(), sizeof(uint16_t) * bt.size(), cudaMemcpyHostToDevice));
+    return FR_OK;
 }
 
 // morph -> pose -> face normals + Morton keys -> vertex normals -> LBVH
@@ -265,7 +344,7 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
     launch_pose_adjoint(c->d_items, n, c->N, st);
     launch_pose_finish(c->d_items, n, c->NL, c->N, st);
-    launch_morph_adjoint(c->basis, c->ld, c->K, 3 * c->N, c->d_items, n, st);
+    morph_adjoint(c, n, st);
     mark(c, 7, st);
 }
 
@@ -423,50 +502,13 @@ fr_status fr_set_mesh(fr_ctx* c, const fr_mesh* m) {
         i = j;
     }
     c->N = N; c->T = T; c->K = K; c->E = (int)edges.size();
-    c->ld = ((3 * N + 31) / 32) * 32;
-    TRY(dalloc(c, &c->mean, c->ld));
-    TRY(dalloc(c, &c->basis, (size_t)std::max(K, 1) * c->ld));
+    TRY(upload_model(c, c->shape, 3 * N, K, m->mean, m->basis));
+    c->ld = c->shape.ld;
     TRY(dalloc(c, &c->faces, T));
     TRY(dalloc(c, &c->uv, N));
     TRY(dalloc(c, &c->vf_off, N + 1));
     TRY(dalloc(c, &c->vf_idx, 3 * (size_t)T));
     TRY(dalloc(c, &c->edges, c->E));
-    std::vector<float> pad((size_t)c->ld, 0.0f);
-    std::copy(m->mean, m->mean + 3 * (size_t)N, pad.begin());
-    CK(c, cudaMemcpy(c->mean, pad.data(), sizeof(float) * c->ld, cudaMemcpyHostToDevice));
-    for (int k = 0; k < K; ++k) {
-        std::fill(pad.begin(), pad.end(), 0.0f);
-        std::copy(m->basis + (size_t)k * 3 * N, m->basis + (size_t)(k + 1) * 3 * N, pad.begin());
-        CK(c, cudaMemcpy(c->basis + (size_t)k * c->ld, pad.data(), sizeof(float) * c->ld, cudaMemcpyHostToDevice));
-    }
-    if (K > 0) {
-        // BF16 operand tiles for the tensor-core morph: tile t holds rows
-        // 128t..128t+127 of the [3N x Kp] basis in the no-swizzle K-major
-        // core-matrix layout (8 rows x 8 values per 128-byte core matrix).
-        c->Kp = ((K + 15) / 16) * 16;
-        const int n3 = 3 * N, tiles = (n3 + 127) / 128;
-        std::vector<uint16_t> bt((size_t)tiles * 128 * c->Kp, 0);
-        auto bf16 = [](float f) {
-            uint32_t u;
-            std::memcpy(&u, &f, 4);
-            u += 0x7FFFu + ((u >> 16) & 1u);
-            return (uint16_t)(u >> 16);
-        };
-        for (int t = 0; t < tiles; ++t)
-            for (int rr = 0; rr < 128; ++rr) {
-                const int i = t * 128 + rr;
-                if (i >= n3) break;
-                const int g = rr >> 3, r = rr & 7;
-                for (int k = 0; k < K; ++k) {
-                    const int cc = k >> 3, kk = k & 7;
-                    const size_t off = (size_t)t * 128 * c->Kp + ((size_t)(g * (c->Kp / 8) + cc) * 128 + r * 16 + kk * 2) / 2;
-                    bt[off] = bf16(m->basis[(size_t)k * n3 + i]);
-                }
-            }
-        TRY(dalloc(c, &c->basis_tiles, bt.size()));
-        TRY(dalloc(c, &c->coef_tile, (size_t)32 * c->Kp));
-        CK(c, cudaMemcpy(c->basis_tiles, bt.data(), sizeof(uint16_t) * bt.size(), cudaMemcpyHostToDevice));
-    }
     std::vector<int4> f4(T);
     for (int f = 0; f < T; ++f) f4[f] = make_int4(m->faces[3 * f], m->faces[3 * f + 1], m->faces[3 * f + 2], 0);
     CK(c, cudaMemcpy(c->faces, f4.data(), sizeof(int4) * T, cudaMemcpyHostToDevice));
@@ -476,6 +518,73 @@ fr_status fr_set_mesh(fr_ctx* c, const fr_mesh* m) {
     CK(c, cudaMemcpy(c->edges, edges.data(), sizeof(int4) * c->E, cudaMemcpyHostToDevice));
     for (Slot& sl : c->slots) TRY(alloc_slot(c, sl));
     c->have_mesh = true;
+    return FR_OK;
+}
+
+fr_status fr_set_albedo(fr_ctx* c, const fr_albedo_model* am) {
+    if (!c || !am) return fail(c, FR_EINVAL, "null argument");
+    if (c->have_albedo) return fail(c, FR_EINVAL, "albedo model already set");
+    const int rows = 3 * c->cfg.tex_size * c->cfg.tex_size;
+    const int ks[2] = {am->k_diffuse, am->k_specular};
+    const float* means[2] = {am->mean_diffuse, am->mean_specular};
+    const float* bases[2] = {am->basis_diffuse, am->basis_specular};
+    for (int q = 0; q < 2; ++q) {
+        if (ks[q] < 0 || ks[q] > FR_MAX_BASIS) return fail(c, FR_EINVAL, "albedo basis size out of range");
+        if (!means[q] || (ks[q] > 0 && !bases[q])) return fail(c, FR_EINVAL, "null albedo mean or basis");
+    }
+    for (int q = 0; q < 2; ++q) TRY(upload_model(c, c->albedo[q], rows, ks[q], means[q], bases[q]));
+    c->have_albedo = true;
+    return FR_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+fr_status fr_albedo_morph(fr_ctx* c, int32_t n, const float* const* beta, const float* const* gamma,
+                          float* const* diffuse, float* const* specular, void* stream) {
+    if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (!c->have_albedo) return fail(c, FR_EINVAL, "albedo model not set");
+    if (n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch faces required");
+    const float* const* coefs[2] = {beta, gamma};
+    float* const* outs[2] = {diffuse, specular};
+    for (int q = 0; q < 2; ++q) {
+        if (!outs[q]) continue;
+        const LinearModel& m = c->albedo[q];
+        if (m.K > 0 && !coefs[q]) return fail(c, FR_EINVAL, "null coefficient array");
+        LinearTable t;
+        t.n = n;
+        for (int k = 0; k < n; ++k) {
+            if (!outs[q][k] || !aligned16(outs[q][k])) return fail(c, FR_EINVAL, "null or misaligned texture");
+            if (m.K > 0 && !coefs[q][k]) return fail(c, FR_EINVAL, "null coefficients");
+            t.coef[k] = m.K > 0 ? coefs[q][k] : nullptr;
+            t.out[k] = outs[q][k];
+        }
+        linear_forward(c, m, t, S_(stream));
+    }
+    CK(c, cudaGetLastError());
+    return FR_OK;
+}
+
+fr_status fr_albedo_adjoint(fr_ctx* c, int32_t n, const float* const* g_diffuse, const float* const* g_specular,
+                            float* const* g_beta, float* const* g_gamma, void* stream) {
+    if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (!c->have_albedo) return fail(c, FR_EINVAL, "albedo model not set");
+    if (n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch faces required");
+    const float* const* gs[2] = {g_diffuse, g_specular};
+    float* const* outs[2] = {g_beta, g_gamma};
+    for (int q = 0; q < 2; ++q) {
+        const LinearModel& m = c->albedo[q];
+        if (!outs[q] || m.K == 0) continue;
+        if (!gs[q]) return fail(c, FR_EINVAL, "null texture-gradient array");
+        LinearAdjTable t;
+        t.n = n;
+        for (int k = 0; k < n; ++k) {
+            if (!gs[q][k] || !aligned16(gs[q][k])) return fail(c, FR_EINVAL, "null or misaligned texture gradient");
+            t.g[k] = gs[q][k];
+            t.g_coef[k] = outs[q][k];
+        }
+        launch_linear_adjoint(m.basis, m.ld, m.rows, m.K, t, m.part, S_(stream));
+    }
+    CK(c, cudaGetLastError());
     return FR_OK;
 }
 

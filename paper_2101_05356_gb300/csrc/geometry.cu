@@ -1,7 +1,7 @@
-// Morph (Sec. 3.1: v = a_s + Sigma_s alpha + Sigma_e delta), pose
-// (Gamma(v) = R^-1 (v - T)), face/vertex normals, Morton keys, and the reverse
-// of each step (normals, pose, morph transpose with FP64 reductions).  Every
-// kernel is batched over the items of a call through blockIdx.y.
+// Pose (Gamma(v) = R^-1 (v - T), Sec. 3.1), face/vertex normals, Morton keys,
+// and the reverse of each step (normals, pose with FP64 reductions); the morph
+// and its transpose are in linear.cu.  Every kernel is batched over the items
+// of a call through blockIdx.y.
 #include <algorithm>
 
 #include "common.cuh"
@@ -55,39 +55,6 @@ __global__ void k_tex_flush(const DevItem* items, int M) {
     if (i < 3 * M2) { if (it.G.diffuse) it.G.diffuse[i] += g; }
     else if (i < 6 * M2) { if (it.G.specular) it.G.specular[i - 3 * M2] += g; }
     else if (it.G.roughness) it.G.roughness[i - 6 * M2] += g;
-}
-
-// Coalesced, float4-vectorised morph: thread i owns float4 i of the padded
-// [3N] vector; coefficients sit in shared memory; basis rows are 16-B aligned.
-__global__ void __launch_bounds__(256) k_morph(const float4* __restrict__ mean, const float* __restrict__ basis,
-                                               int ld4, int K, const DevItem* items) {
-    __shared__ float c[FR_MAX_BASIS];
-    const DevItem& it = items[blockIdx.y];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = it.P.coef[k];
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ld4) return;
-    float4 acc = mean[i];
-    const float4* b = reinterpret_cast<const float4*>(basis) + i;
-    int k = 0;
-    for (; k + 4 <= K; k += 4) {
-        const float4 b0 = __ldg(b + (size_t)(k + 0) * ld4), b1 = __ldg(b + (size_t)(k + 1) * ld4);
-        const float4 b2 = __ldg(b + (size_t)(k + 2) * ld4), b3 = __ldg(b + (size_t)(k + 3) * ld4);
-        acc.x += c[k] * b0.x + c[k + 1] * b1.x + c[k + 2] * b2.x + c[k + 3] * b3.x;
-        acc.y += c[k] * b0.y + c[k + 1] * b1.y + c[k + 2] * b2.y + c[k + 3] * b3.y;
-        acc.z += c[k] * b0.z + c[k + 1] * b1.z + c[k + 2] * b2.z + c[k + 3] * b3.z;
-        acc.w += c[k] * b0.w + c[k + 1] * b1.w + c[k + 2] * b2.w + c[k + 3] * b3.w;
-    }
-    for (; k < K; ++k) {
-        const float4 bk = __ldg(b + (size_t)k * ld4);
-        acc.x += c[k] * bk.x; acc.y += c[k] * bk.y; acc.z += c[k] * bk.z; acc.w += c[k] * bk.w;
-    }
-    reinterpret_cast<float4*>(it.v_model)[i] = acc;
-}
-
-__global__ void k_copy_mean(const float4* __restrict__ mean, int ld4, const DevItem* items) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ld4) reinterpret_cast<float4*>(items[blockIdx.y].v_model)[i] = mean[i];
 }
 
 FR_D unsigned ordered(float f) {
@@ -309,35 +276,6 @@ __global__ void k_pose_finish(const DevItem* items, int NL, int n_blocks) {
 }
 
 // dE/dcoef_k = sum_i basis[k][i] dE/dv_i, one block per (k, item), FP64 accumulation.
-__global__ void __launch_bounds__(512) k_morph_adj(const float* __restrict__ basis, int ld4, int n3,
-                                                   const DevItem* items) {
-    __shared__ double part[16];
-    const DevItem& it = items[blockIdx.y];
-    if (!it.g_coef) return;
-    const int k = blockIdx.x;
-    const float4* b = reinterpret_cast<const float4*>(basis) + (size_t)k * ld4;
-    const float* dv = it.d_vmodel;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < ld4; i += blockDim.x) {
-        const float4 bb = __ldg(b + i);
-        const int e = 4 * i;
-        float s = 0.0f;
-        if (e + 0 < n3) s += bb.x * dv[e + 0];
-        if (e + 1 < n3) s += bb.y * dv[e + 1];
-        if (e + 2 < n3) s += bb.z * dv[e + 2];
-        if (e + 3 < n3) s += bb.w * dv[e + 3];
-        acc += (double)s;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        it.g_coef[k] += (float)s;
-    }
-}
-
 __global__ void k_philox(uint2 key, const uint4* counters, int n, uint4* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = philox4x32_10(key, counters[i]);
@@ -362,14 +300,6 @@ void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStr
 
 void launch_tex_flush(const DevItem* items, int n, int M, cudaStream_t st) {
     k_tex_flush<<<dim3(nb(7L * M * M, 256), n), 256, 0, st>>>(items, M);
-    fr_count_launches(1);
-}
-
-void launch_morph(const float* mean, const float* basis, int ld, int K, const DevItem* items, int n,
-                  cudaStream_t st) {
-    const int ld4 = ld / 4;
-    if (K > 0) k_morph<<<dim3(nb(ld4, 256), n), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), basis, ld4, K, items);
-    else k_copy_mean<<<dim3(nb(ld4, 256), n), 256, 0, st>>>(reinterpret_cast<const float4*>(mean), ld4, items);
     fr_count_launches(1);
 }
 
@@ -404,13 +334,6 @@ void launch_pose_adjoint(const DevItem* items, int n, int N, cudaStream_t st) {
 
 void launch_pose_finish(const DevItem* items, int n, int NL, int N, cudaStream_t st) {
     k_pose_finish<<<n, 64, 0, st>>>(items, NL, nb(N, 256));
-    fr_count_launches(1);
-}
-
-void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const DevItem* items, int n,
-                          cudaStream_t st) {
-    if (K <= 0) return;
-    k_morph_adj<<<dim3(K, n), 512, 0, st>>>(basis, ld / 4, n3, items);
     fr_count_launches(1);
 }
 

@@ -11,8 +11,6 @@ void fr_count_launches(int n);
 void launch_set_items(const DevItem* host_items, int n, DevItem* dev_items, cudaStream_t st);
 void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStream_t st);
 void launch_tex_flush(const DevItem* items, int n, int M, cudaStream_t st);
-void launch_morph(const float* mean, const float* basis, int ld, int K, const DevItem* items, int n,
-                  cudaStream_t st);
 void launch_pose(const DevItem* items, int n, int N, cudaStream_t st);
 void launch_faces(const DevItem* items, int n, const int4* faces, int T, cudaStream_t st);
 void launch_vertex_normals(const DevItem* items, int n, const int* vf_off, const int* vf_idx, int N,
@@ -21,13 +19,31 @@ void launch_normals_adjoint(const DevItem* items, int n, const int4* faces, cons
                             const int* vf_idx, int N, cudaStream_t st);
 void launch_pose_adjoint(const DevItem* items, int n, int N, cudaStream_t st);
 void launch_pose_finish(const DevItem* items, int n, int NL, int N, cudaStream_t st);
-void launch_morph_adjoint(const float* basis, int ld, int K, int n3, const DevItem* items, int n,
-                          cudaStream_t st);
 
-// morph_tc.cu
+// linear.cu: y_b = mean + basis * coef_b for the faces of a batch (shape morph,
+// statistical albedo); basis [K][ld] FP32, mean [ld], rows <= ld, ld % 4 == 0,
+// outputs and adjoint inputs 16-byte aligned.  Tables are passed by value.
+struct LinearTable {
+    int n;
+    const float* coef[FR_MAX_BATCH];     // [K] per face (device)
+    float* out[FR_MAX_BATCH];            // [rows] per face (device)
+};
+struct LinearAdjTable {
+    int n;
+    const float* g[FR_MAX_BATCH];        // dE/dy_b [rows] (device)
+    float* g_coef[FR_MAX_BATCH];         // += basis^T g_b [K] (device; null: skipped)
+};
+int linear_adj_chunks(int rows);         // size of the adjoint's FP64 partials: n * K * chunks
+void launch_linear(const float* mean, const float* basis, int ld, int rows, int K, const LinearTable& t,
+                   cudaStream_t st);
+void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const LinearAdjTable& t, double* part,
+                           cudaStream_t st);
+
+// morph_tc.cu: the same forward as one BF16 tensor-core GEMM over the batch
+// (tiles: the basis as [ceil(rows / 128)][128][Kp] BF16 operand tiles)
 int morph_tc_smem_bytes(int Kp);
-void launch_morph_tc(const uint16_t* basis_tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int n3,
-                     const DevItem* items, int n, int* status, cudaStream_t st);
+void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int rows,
+                      const LinearTable& t, int* status, cudaStream_t st);
 
 // lbvh.cu
 void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, cudaStream_t st);

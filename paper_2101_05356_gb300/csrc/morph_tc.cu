@@ -1,7 +1,9 @@
-// Batched morph on the 5th-generation tensor cores (Sec. 3.1: v = a_s +
-// [Sigma_s | Sigma_e] [alpha; delta] for every face of a batch at once):
+// Batched linear model on the 5th-generation tensor cores, for every face of a
+// batch at once: the morph of Sec. 3.1 (v = a_s + [Sigma_s | Sigma_e]
+// [alpha; delta]) and the statistical albedos of Sec. 3.2 (C = a_r +
+// Sigma_r beta, S = a_b + Sigma_b gamma in texture space):
 //     D[i][b] = sum_k basis[i][k] coef[b][k]      (BF16 x BF16 -> FP32 in TMEM)
-//     v_b[i]  = mean[i] + D[i][b]                 (FP32 epilogue)
+//     y_b[i]  = mean[i] + D[i][b]                 (FP32 epilogue)
 // One CTA owns 128 rows i of the 3N dimension and all (padded) 32 faces.  The
 // basis tile (pre-arranged at set-up in the no-swizzle K-major core-matrix
 // layout, 8 rows x 16 bytes per core matrix) and the gathered coefficient tile
@@ -59,8 +61,8 @@ FR_D bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restrict__ basis_tiles, int Kp,
                                                          const uint16_t* __restrict__ coef_tile,
-                                                         const float* __restrict__ mean, int n3,
-                                                         const DevItem* items, int n_items, int* status) {
+                                                         const float* __restrict__ mean, int n3, LinearTable t,
+                                                         int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int a_bytes = TC_M * Kp * 2, b_bytes = TC_N * Kp * 2;
     unsigned char* sA = smem;
@@ -135,7 +137,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restr
         const int row = tile * TC_M + tid;
         if (row < n3) {
             const float m = mean[row];
-            for (int b = 0; b < n_items && b < TC_N; ++b) items[b].v_model[row] = m + __uint_as_float(r[b]);
+#pragma unroll
+            for (int b = 0; b < TC_N; ++b)
+                if (b < t.n) t.out[b][row] = m + __uint_as_float(r[b]);
         }
     } else if (tid == 0) {
         // a wait gave up: report it, then give this CTA's own copies or MMAs a
@@ -160,11 +164,11 @@ FR_D uint16_t bf16_rne(float f) {
 
 // Gather the batch's coefficients into the B-operand tile: face b is row b of
 // an N x Kp K-major matrix in core-matrix layout (8 rows x 8 BF16 per 128 B).
-__global__ void k_coef_tile(const DevItem* items, int n_items, int K, int Kp, uint16_t* tile) {
+__global__ void k_coef_tile(LinearTable t, int K, int Kp, uint16_t* tile) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= TC_N * Kp) return;
     const int b = idx / Kp, k = idx % Kp;
-    const float v = (b < n_items && k < K) ? items[b].P.coef[k] : 0.0f;
+    const float v = (b < t.n && k < K) ? t.coef[b][k] : 0.0f;
     const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
     tile[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v);
 }
@@ -173,12 +177,13 @@ __global__ void k_coef_tile(const DevItem* items, int n_items, int K, int Kp, ui
 
 int morph_tc_smem_bytes(int Kp) { return TC_M * Kp * 2 + TC_N * Kp * 2; }
 
-void launch_morph_tc(const uint16_t* basis_tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int n3,
-                     const DevItem* items, int n, int* status, cudaStream_t st) {
-    k_coef_tile<<<(TC_N * Kp + 255) / 256, 256, 0, st>>>(items, n, K, Kp, coef_tile);
-    const int tiles = (n3 + TC_M - 1) / TC_M;
+void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int rows,
+                      const LinearTable& t, int* status, cudaStream_t st) {
+    if (t.n <= 0 || rows <= 0) return;
+    k_coef_tile<<<(TC_N * Kp + 255) / 256, 256, 0, st>>>(t, K, Kp, coef_tile);
+    const int n_tiles = (rows + TC_M - 1) / TC_M;
     const int smem = morph_tc_smem_bytes(Kp);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_morph_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_morph_tc<<<tiles, TC_THREADS, smem, st>>>(basis_tiles, Kp, coef_tile, mean, n3, items, n, status);
+    k_morph_tc<<<n_tiles, TC_THREADS, smem, st>>>(tiles, Kp, coef_tile, mean, rows, t, status);
     fr_count_launches(2);
 }

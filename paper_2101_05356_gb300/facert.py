@@ -40,6 +40,11 @@ class FrLightStage(ctypes.Structure):
     _fields_ = [("n_lights", ctypes.c_int32), ("records", _vp), ("d", _vp), ("a", _vp)]
 
 
+class FrAlbedoModel(ctypes.Structure):
+    _fields_ = [("k_diffuse", ctypes.c_int32), ("k_specular", ctypes.c_int32), ("mean_diffuse", _vp),
+                ("basis_diffuse", _vp), ("mean_specular", _vp), ("basis_specular", _vp)]
+
+
 PARAM_NAMES = ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness")
 
 
@@ -91,6 +96,9 @@ def lib():
         L.fr_create.argtypes = [P(_vp), P(FrConfig)]
         L.fr_set_mesh.argtypes = [_vp, P(FrMesh)]
         L.fr_set_lights.argtypes = [_vp, P(FrLightStage)]
+        L.fr_set_albedo.argtypes = [_vp, P(FrAlbedoModel)]
+        L.fr_albedo_morph.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
+        L.fr_albedo_adjoint.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
         L.fr_forward.argtypes = [_vp, P(FrParams), _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]
         L.fr_backward.argtypes = [_vp, P(FrParams), _vp, P(FrGrads), ctypes.c_uint32, ctypes.c_uint32, _vp]
         L.fr_loss.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -166,6 +174,35 @@ def fr_set_lights(ctx, records, d, a):
     a = np.ascontiguousarray(a, np.float32)
     ls = FrLightStage(records.shape[0], records.ctypes.data, d.ctypes.data, a.ctypes.data)
     check(lib().fr_set_lights(ctx, ctypes.byref(ls)), ctx)
+
+
+def fr_set_albedo(ctx, mean_diffuse, basis_diffuse, mean_specular, basis_specular):
+    """Statistical albedo model (host arrays): means [M, M, 3], bases [K, M, M, 3]."""
+    md = np.ascontiguousarray(mean_diffuse, np.float32)
+    bd = np.ascontiguousarray(basis_diffuse, np.float32)
+    ms = np.ascontiguousarray(mean_specular, np.float32)
+    bs = np.ascontiguousarray(basis_specular, np.float32)
+    m = FrAlbedoModel(bd.shape[0], bs.shape[0], md.ctypes.data, bd.ctypes.data, ms.ctypes.data, bs.ctypes.data)
+    check(lib().fr_set_albedo(ctx, ctypes.byref(m)), ctx)
+
+
+def _ptr_array(ts):
+    if ts is None:
+        return None
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+
+
+def fr_albedo_morph(ctx, beta, gamma, diffuse, specular):
+    """Lists (one entry per face) of device tensors; diffuse/specular may be None."""
+    n = len(diffuse if diffuse is not None else specular)
+    check(lib().fr_albedo_morph(ctx, n, _ptr_array(beta), _ptr_array(gamma), _ptr_array(diffuse),
+                                _ptr_array(specular), _stream()), ctx)
+
+
+def fr_albedo_adjoint(ctx, g_diffuse, g_specular, g_beta, g_gamma):
+    n = len(g_beta if g_beta is not None else g_gamma)
+    check(lib().fr_albedo_adjoint(ctx, n, _ptr_array(g_diffuse), _ptr_array(g_specular), _ptr_array(g_beta),
+                                  _ptr_array(g_gamma), _stream()), ctx)
 
 
 def _params(p):
@@ -337,6 +374,10 @@ class Renderer:
         self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed, max_batch)
         fr_set_mesh(self.ctx, scene.mean, scene.basis, scene.faces, scene.uv)
         fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a)
+        self.albedo = getattr(scene, "albedo", None)
+        if self.albedo is not None:
+            a = self.albedo
+            fr_set_albedo(self.ctx, a.mean_diffuse, a.basis_diffuse, a.mean_specular, a.basis_specular)
         self.n_edges = fr_num_edges(self.ctx)
 
     def close(self):

@@ -1,7 +1,12 @@
 """Two-stage reconstruction (Sec. 4) with device-resident state.
 
-Stage I optimises shape and expression coefficients, pose and light-stage
-intensities against E_ph + E_p + E_b (Eq. loss1); Stage II optimises the
+Stage I optimises shape and expression coefficients, pose, light-stage
+intensities and (when the scene has a statistical albedo model, Sec. 3.2) the
+albedo coefficients beta and gamma against E_ph + E_p + E_b (Eq. loss1): each
+Stage I step morphs the textures from beta, gamma (fr_albedo_morph) before the
+render and maps the texture gradients back (fr_albedo_adjoint) after it.
+Stage II starts the personalised textures from the last statistical albedos
+and optimises the
 personalised diffuse, specular and roughness textures with geometry and lights
 fixed against E_ph + symmetry + chromaticity + smoothness + box terms
 (Eq. loss3).  Every step is one fused render/loss/adjoint call (fr_render, or
@@ -15,8 +20,8 @@ import dataclasses
 
 from . import facert
 
-LR = dict(light=1e-3, identity=1e-2, expression=1e-3, rot=1e-3, trans=1e-3, texture=5e-3)
-W = dict(w_i=0.0025, w1=0.01, w2=0.3, w3=0.3, w4=0.0002, box=1.0)
+LR = dict(light=1e-3, identity=1e-2, expression=1e-3, rot=1e-3, trans=1e-3, texture=5e-3, albedo=2e-2)
+W = dict(w_i=0.0025, w_c=0.0025, w_s=0.0025, w1=0.01, w2=0.3, w3=0.3, w4=0.0002, box=1.0)
 STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE
 
 
@@ -54,11 +59,21 @@ class FaceState:
         self.it = 0
         self.ref_diffuse = None
         self.ref_specular = None
+        # statistical albedo coefficients (Stage I), zero = the mean albedo
+        am = getattr(renderer, "albedo", None)
+        self.albedo = am is not None
+        self.ab = {}
+        if self.albedo:
+            for name, k in (("beta", am.k_diffuse), ("gamma", am.k_specular)):
+                self.ab[name] = {q: torch.zeros(max(k, 1), dtype=torch.float32, device="cuda")
+                                 for q in ("x", "g", "m", "v")}
+                self.ab[name]["k"] = k
 
     def nbytes(self):
         """Device memory owned by this face's state."""
         ts = list(self.p.values()) + list(self.g.values()) + list(self.m.values()) + list(self.v.values())
         ts += [self.image, self.target]
+        ts += [t for a in self.ab.values() for q, t in a.items() if q != "k"]
         b = sum(t.numel() * t.element_size() for t in ts)
         return b + 2 * self.p["diffuse"].numel() * 4          # Stage II albedo references
 
@@ -77,6 +92,13 @@ class FaceState:
             self.ref_specular = self.p["specular"].clone()
         for t in self.g.values():
             t.zero_()
+        for a in self.ab.values():
+            a["g"].zero_()
+
+    @property
+    def stat_albedo(self):
+        """True while the textures are the statistical albedos (Stage I with a model)."""
+        return self.albedo and self.stage == 1
 
     def item_flags(self):
         return self.flags | (STAGE2_FLAGS if self.stage == 2 else 0)
@@ -106,6 +128,11 @@ class FaceState:
             out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"],
                                         aux=self.light_scale, kind=facert.GROUP_LIGHT, lr=LR["light"],
                                         w_prior=W["w1"], w_box=W["box"], step=step))
+            for name, w in (("beta", W["w_c"]), ("gamma", W["w_s"])):
+                a = self.ab.get(name)
+                if a and a["k"] > 0:
+                    out.append(facert.opt_group(a["x"], a["m"], a["v"], a["g"], kind=facert.GROUP_COEF,
+                                                lr=LR["albedo"], n_prior=a["k"], w_prior=w, step=step))
             return out
         step = self.it - self.schedule.stage1 + 1
         M = self.tex
@@ -136,7 +163,9 @@ class Reconstruction(FaceState):
             return
         self.begin_step()
         facert.fr_set_flags(self.r.ctx, self.item_flags())
+        albedo_morph(self.r, [self])
         facert.fr_render(self.r.ctx, self.p, self.target, self.image, self.loss, self.g, self.it, self.face_id)
+        albedo_adjoint(self.r, [self])
         facert.fr_adam(self.groups(), reg_energy=self.reg)
         self.it += 1
 
@@ -147,6 +176,23 @@ class Reconstruction(FaceState):
                 self.history.append((self.it, float(self.loss.item())))
         facert.fr_set_flags(self.r.ctx, self.flags)
         return self
+
+
+def albedo_morph(renderer, states):
+    """Textures of the faces in `states` that are in Stage I with a statistical
+    albedo model, from their beta and gamma (one batched call)."""
+    s1 = [st for st in states if st.stat_albedo]
+    if s1:
+        facert.fr_albedo_morph(renderer.ctx, [st.ab["beta"]["x"] for st in s1], [st.ab["gamma"]["x"] for st in s1],
+                               [st.p["diffuse"] for st in s1], [st.p["specular"] for st in s1])
+
+
+def albedo_adjoint(renderer, states):
+    """dE/dbeta, dE/dgamma of those faces from their texture gradients."""
+    s1 = [st for st in states if st.stat_albedo]
+    if s1:
+        facert.fr_albedo_adjoint(renderer.ctx, [st.g["diffuse"] for st in s1], [st.g["specular"] for st in s1],
+                                 [st.ab["beta"]["g"] for st in s1], [st.ab["gamma"]["g"] for st in s1])
 
 
 def photometric_loss(renderer, params, target, iteration=10 ** 6, face_id=0):

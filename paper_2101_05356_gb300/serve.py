@@ -19,7 +19,7 @@ import time
 
 import numpy as np
 
-from . import facert
+from . import facert, optim
 from .optim import FaceState, Schedule
 
 
@@ -103,8 +103,11 @@ class Server:
     def _step(self):
         for _, st in self.active:
             st.begin_step()
-        items = [st.item(self.edge_spp) for _, st in self.active]
+        states = [st for _, st in self.active]
+        optim.albedo_morph(self.r, states)
+        items = [st.item(self.edge_spp) for st in states]
         facert.fr_render_batch(self.r.ctx, items)
+        optim.albedo_adjoint(self.r, states)
         groups = [g for _, st in self.active for g in st.groups()]
         for k in range(0, len(groups), facert_max_groups()):
             facert.fr_adam(groups[k:k + facert_max_groups()])

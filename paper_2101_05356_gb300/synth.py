@@ -36,6 +36,26 @@ STAGE_CENTRE = (0.0, 0.0, -4.5)
 
 
 @dataclasses.dataclass
+class AlbedoModel:
+    """Statistical albedo model of Sec. 3.2 in UV texture space: diffuse
+    C = mean_diffuse + sum_k beta_k basis_diffuse[k], specular likewise with
+    gamma (synthetic stand-in for the absent AlbedoMM; coefficients ~ N(0, 1),
+    the column scale is in the basis)."""
+    mean_diffuse: np.ndarray    # float32 [M, M, 3]
+    basis_diffuse: np.ndarray   # float32 [K_r, M, M, 3]
+    mean_specular: np.ndarray   # float32 [M, M, 3]
+    basis_specular: np.ndarray  # float32 [K_b, M, M, 3]
+
+    @property
+    def k_diffuse(self) -> int:
+        return int(self.basis_diffuse.shape[0])
+
+    @property
+    def k_specular(self) -> int:
+        return int(self.basis_specular.shape[0])
+
+
+@dataclasses.dataclass
 class Scene:
     """Everything that is fixed for a reconstruction: mesh, bases, lights, image."""
     mean: np.ndarray        # float32 [N, 3] mean shape a_s (model space)
@@ -52,6 +72,7 @@ class Scene:
     spp: int
     tex_size: int           # M
     fov_deg: float
+    albedo: AlbedoModel | None = None
 
     @property
     def n_vertices(self) -> int:
@@ -391,6 +412,34 @@ def textures(rng, m):
             roughness.astype(np.float32))
 
 
+def _zero_mean_field(rng, m, sigma):
+    """Smooth zero-mean random field [m, m, 3] with unit RMS (periodic blur)."""
+    noise = rng.normal(size=(m, m, 3))
+    f, fr = np.fft.fftfreq(m), np.fft.rfftfreq(m)
+    g = np.exp(-2.0 * (math.pi * sigma) ** 2 * (f[:, None] ** 2 + fr[None, :] ** 2))
+    out = np.fft.irfft2(np.fft.rfft2(noise, axes=(0, 1)) * g[:, :, None], s=(m, m), axes=(0, 1))
+    out -= out.mean(axis=(0, 1), keepdims=True)
+    return out / max(float(np.sqrt(np.mean(out * out))), 1e-12)
+
+
+def albedo_model(rng, m, k_diffuse=80, k_specular=80):
+    """Synthetic statistical albedo model: diffuse mean a smooth field in
+    [0.35, 0.65] (skin-like, left-right symmetric), specular mean 0.05; column k
+    a smooth zero-mean field of RMS 0.08 / (1 + k) (diffuse) and
+    0.01 / (1 + k) (specular), so beta, gamma ~ N(0, 1) stay in range."""
+    md = smooth_field(rng, m, 3, m / 16.0, 0.35, 0.65)
+    md = 0.5 * (md + md[:, ::-1, :])
+    bd = np.empty((k_diffuse, m, m, 3), np.float32)
+    for k in range(k_diffuse):
+        bd[k] = _zero_mean_field(rng, m, m / 24.0) * (0.08 / (1.0 + k))
+    ms = np.full((m, m, 3), 0.05, np.float32)
+    bs = np.empty((k_specular, m, m, 3), np.float32)
+    for k in range(k_specular):
+        bs[k] = _zero_mean_field(rng, m, m / 24.0) * (0.01 / (1.0 + k))
+    return AlbedoModel(mean_diffuse=md.astype(np.float32), basis_diffuse=bd,
+                       mean_specular=ms, basis_specular=bs)
+
+
 def _f32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
 
@@ -406,7 +455,9 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
            1024x1024, 64 spp, 80 quads on a sphere, 2048^2 textures.
     tiny : a small closed mesh for fast CPU tests (162 verts / 320 tris, K = 6,
            24x24, 2 spp, 4 lights).
-    Keyword overrides replace width/height/spp/tex_size/n_lights/light kind."""
+    Keyword overrides replace width/height/spp/tex_size/n_lights/light kind;
+    albedo_k > 0 adds a statistical albedo model with that many columns per
+    albedo (Sec. 3.2; the paper's K_r = K_b = 80)."""
     rng = np.random.default_rng(seed)
     if config == "c1":
         mean, basis, faces, uv = face_icosphere(rng, 4, 20, 0)
@@ -438,11 +489,13 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
     kind = over.get("light_kind", LIGHT_QUAD)
     side = over.get("light_side", 0.5 if kind != LIGHT_DISK else 1.0)
     lights = light_stage(nl, 3.0, side, hemi, STAGE_CENTRE, kind)
+    ka = int(over.get("albedo_k", 0))
+    albedo = albedo_model(np.random.default_rng(seed + 31), m, ka, ka) if ka > 0 else None
     return Scene(mean=_f32(mean), basis=_f32(basis), n_shape=ks, n_expr=ke,
                  faces=np.ascontiguousarray(faces.astype(np.int32)), uv=_f32(uv),
                  lights=lights, light_d=np.full(nl, 3.0, np.float32),
                  light_a=np.ones(nl, np.float32), width=int(w), height=int(h),
-                 spp=int(spp), tex_size=int(m), fov_deg=30.0)
+                 spp=int(spp), tex_size=int(m), fov_deg=30.0, albedo=albedo)
 
 
 def init_params(scene: Scene, seed: int = 0) -> Params:
