@@ -327,6 +327,61 @@ def serving_bench(n_requests, iters, rate, seed=0):
     return out
 
 
+def albedo_bench(batch=8, reps=10):
+    """Statistical albedo morph (Sec. 3.2) at the paper-scale texture size
+    (512^2 texels, K = 80 per albedo, diffuse + specular in one call) as the
+    BF16 tensor-core GEMM and in FP32, and its FP64-summed transpose, for a
+    batch of faces; HBM roofline on the algorithmic bytes (basis read once,
+    means, textures or texture gradients)."""
+    import torch
+
+    from paper_2101_05356_gb300 import facert, synth
+    sc = synth.make_scene("c2", albedo_k=80)
+    M, K = sc.tex_size, 80
+    rows = 3 * M * M
+    pk, src = peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(0)
+    coefs = [torch.as_tensor(rng.normal(size=K).astype(np.float32)).cuda() for _ in range(2 * batch)]
+    tex = [torch.empty((M, M, 3), device="cuda") for _ in range(2 * batch)]
+    gco = [torch.zeros(K, device="cuda") for _ in range(2 * batch)]
+    out = {"workload": "512^2 x 3 texels, K = 80 diffuse + 80 specular, batch %d" % batch}
+
+    def timed(fn):
+        ms = []
+        for k in range(reps + 2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            if k >= 2:
+                ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    for name, flags, basis_bytes in (("morph_bf16_tc", facert.FLAG_MORPH_BF16, 2), ("morph_fp32", 0, 4)):
+        r = facert.Renderer(sc, flags=flags, max_batch=batch)
+        for n in (1, batch):
+            ms = timed(lambda: facert.fr_albedo_morph(r.ctx, coefs[:n], coefs[batch:batch + n], tex[:n],
+                                                      tex[batch:batch + n]))
+            nbytes = 2 * (rows * K * basis_bytes + rows * 4 + n * rows * 4)
+            out["%s_b%d" % (name, n)] = {"ms": ms, "GB/s": nbytes / ms / 1e6,
+                                         "frac_hbm": nbytes / ms / 1e6 / pk["hbm_gbs"]}
+        if flags == 0:
+            for n in (1, batch):
+                ms = timed(lambda: facert.fr_albedo_adjoint(r.ctx, tex[:n], tex[batch:batch + n], gco[:n],
+                                                            gco[batch:batch + n]))
+                nbytes = 2 * (rows * K * 4 + n * rows * 4)
+                out["adjoint_b%d" % n] = {"ms": ms, "GB/s": nbytes / ms / 1e6,
+                                          "frac_hbm": nbytes / ms / 1e6 / pk["hbm_gbs"]}
+        r.close()
+    out["peak_hbm_gbs"] = pk["hbm_gbs"]
+    out["peak_source"] = src
+    return out
+
+
 def cpu_baseline(sample_pixels, threads=0):
     """The FP64 oracle as it stands, on a bounded sample of the same workload:
     forward + adjoint (all terms) restricted to `sample_pixels` random pixels."""
@@ -361,6 +416,7 @@ def main():
     ap.add_argument("--retrace-steps", type=int, default=5)
     ap.add_argument("--cpu-pixels", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-albedo", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-iters", type=int, default=6)
     ap.add_argument("--serve-rate", type=float, default=40.0)
@@ -394,6 +450,8 @@ def main():
     out = gpu_arm(args, rank, world)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving_bench(args.serve_requests, args.serve_iters, args.serve_rate)
+    if rank == 0 and world == 1 and not args.no_albedo:
+        out["albedo"] = albedo_bench()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.cpu_pixels).items() if k != "seconds"}
     if world > 1:

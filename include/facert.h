@@ -154,6 +154,21 @@ typedef struct fr_albedo_model {
 } fr_albedo_model;
 fr_status fr_set_albedo(fr_ctx* ctx, const fr_albedo_model* model);
 
+/* Landmark vertices for the sparse landmark loss of Sec. 4, Eq. (landmark):
+ * n (1..256) vertex indices of the mesh (host, copied).  Requires the mesh.
+ * Errors: FR_EINVAL (index out of range), FR_ENOMEM. */
+fr_status fr_set_landmarks(fr_ctx* ctx, int32_t n, const int32_t* vertex_index);
+
+/* E_land = sum_l || Pi(Gamma(v_l)) - z_l ||^2 for the face p (coef, rot,
+ * trans, focal are read; textures and lights are not), image width x height
+ * (principal point at its centre, y down, pixel units as the camera rays use),
+ * z [L][2] target positions (device).  *loss (device double) = weight * E_land;
+ * if g != NULL, weight * dE_land/d(coef, rot, trans, focal) is ADDED into g
+ * (null members skipped); if projected != NULL it receives Pi(Gamma(v_l))
+ * [L][2] (device).  FP64 throughout, one small launch. */
+fr_status fr_landmark_loss(fr_ctx* ctx, const fr_params* p, int32_t width, int32_t height, const float* z,
+                           float weight, double* loss, fr_grads* g, float* projected, void* stream);
+
 /* Statistical albedos of n faces (1 <= n <= max_batch; host arrays of n device
  * pointers): diffuse[b] = a_r + Sigma_r beta[b] and specular[b] = a_b +
  * Sigma_b gamma[b], textures [M][M][3] (16-byte aligned), beta[b] [K_r],

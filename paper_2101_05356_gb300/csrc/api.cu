@@ -69,6 +69,8 @@ struct fr_ctx {
     LinearModel shape;                         // rows 3N
     LinearModel albedo[2];                     // diffuse, specular; rows 3 M^2 (optional)
     bool have_albedo = false;
+    int* landmarks = nullptr;                  // landmark vertex indices [n_landmarks]
+    int n_landmarks = 0;
     int4* faces = nullptr;
     float2* uv = nullptr;
     int* vf_off = nullptr;
@@ -534,6 +536,47 @@ fr_status fr_set_albedo(fr_ctx* c, const fr_albedo_model* am) {
     }
     for (int q = 0; q < 2; ++q) TRY(upload_model(c, c->albedo[q], rows, ks[q], means[q], bases[q]));
     c->have_albedo = true;
+    return FR_OK;
+}
+
+fr_status fr_set_landmarks(fr_ctx* c, int32_t n, const int32_t* idx) {
+    if (!c || !idx) return fail(c, FR_EINVAL, "null argument");
+    if (!c->have_mesh) return fail(c, FR_EINVAL, "mesh must be set first");
+    if (n < 1 || n > 256) return fail(c, FR_EINVAL, "1 <= n_landmarks <= 256");
+    for (int l = 0; l < n; ++l)
+        if (idx[l] < 0 || idx[l] >= c->N) return fail(c, FR_EINVAL, "landmark vertex out of range");
+    if (!c->landmarks) TRY(dalloc(c, &c->landmarks, 256));
+    CK(c, cudaMemcpy(c->landmarks, idx, sizeof(int) * n, cudaMemcpyHostToDevice));
+    c->n_landmarks = n;
+    return FR_OK;
+}
+
+fr_status fr_landmark_loss(fr_ctx* c, const fr_params* p, int32_t width, int32_t height, const float* z,
+                           float weight, double* loss, fr_grads* g, float* projected, void* stream) {
+    if (!c || !p || !z || !loss) return fail(c, FR_EINVAL, "null argument");
+    if (c->n_landmarks == 0) return fail(c, FR_EINVAL, "landmarks not set");
+    if (!p->rot || !p->trans || !p->focal || (c->K > 0 && !p->coef)) return fail(c, FR_EINVAL, "null parameter");
+    if (width < 1 || height < 1) return fail(c, FR_EINVAL, "bad image size");
+    LandmarkArgs a;
+    a.mean = c->shape.mean;
+    a.basis = c->shape.basis;
+    a.ld = c->shape.ld;
+    a.K = c->K;
+    a.idx = c->landmarks;
+    a.L = c->n_landmarks;
+    a.W = width;
+    a.H = height;
+    a.coef = p->coef; a.rot = p->rot; a.trans = p->trans; a.focal = p->focal;
+    a.z = z;
+    a.weight = weight;
+    a.loss = loss;
+    a.proj = projected;
+    a.g_coef = g ? g->coef : nullptr;
+    a.g_rot = g ? g->rot : nullptr;
+    a.g_trans = g ? g->trans : nullptr;
+    a.g_focal = g ? g->focal : nullptr;
+    launch_landmarks(a, S_(stream));
+    CK(c, cudaGetLastError());
     return FR_OK;
 }
 

@@ -45,6 +45,22 @@ int morph_tc_smem_bytes(int Kp);
 void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int rows,
                       const LinearTable& t, int* status, cudaStream_t st);
 
+// landmark.cu: sparse landmark loss (one block; L <= 256)
+struct LandmarkArgs {
+    const float* mean;          // shape mean [ld]
+    const float* basis;         // shape basis [K][ld]
+    int ld, K;
+    const int* idx;             // landmark vertex indices [L]
+    int L, W, H;
+    const float *coef, *rot, *trans, *focal;
+    const float* z;             // target pixel positions [L][2]
+    float weight;
+    double* loss;               // set to weight * E_land
+    float* proj;                // projected landmarks [L][2] (may be null)
+    float *g_coef, *g_rot, *g_trans, *g_focal;   // += weight * dE_land (each may be null)
+};
+void launch_landmarks(const LandmarkArgs& a, cudaStream_t st);
+
 // lbvh.cu
 void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, cudaStream_t st);
 void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);

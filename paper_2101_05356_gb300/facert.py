@@ -97,6 +97,9 @@ def lib():
         L.fr_set_mesh.argtypes = [_vp, P(FrMesh)]
         L.fr_set_lights.argtypes = [_vp, P(FrLightStage)]
         L.fr_set_albedo.argtypes = [_vp, P(FrAlbedoModel)]
+        L.fr_set_landmarks.argtypes = [_vp, ctypes.c_int32, _vp]
+        L.fr_landmark_loss.argtypes = [_vp, P(FrParams), ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_float, _vp,
+                                       P(FrGrads), _vp, _vp]
         L.fr_albedo_morph.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
         L.fr_albedo_adjoint.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
         L.fr_forward.argtypes = [_vp, P(FrParams), _vp, ctypes.c_uint32, ctypes.c_uint32, _vp]
@@ -184,6 +187,18 @@ def fr_set_albedo(ctx, mean_diffuse, basis_diffuse, mean_specular, basis_specula
     bs = np.ascontiguousarray(basis_specular, np.float32)
     m = FrAlbedoModel(bd.shape[0], bs.shape[0], md.ctypes.data, bd.ctypes.data, ms.ctypes.data, bs.ctypes.data)
     check(lib().fr_set_albedo(ctx, ctypes.byref(m)), ctx)
+
+
+def fr_set_landmarks(ctx, vertex_index):
+    idx = np.ascontiguousarray(vertex_index, np.int32)
+    check(lib().fr_set_landmarks(ctx, idx.shape[0], idx.ctypes.data), ctx)
+
+
+def fr_landmark_loss(ctx, params, width, height, z, weight, loss, grads=None, projected=None):
+    pp = _params(params)
+    gg = _grads(grads) if grads is not None else None
+    check(lib().fr_landmark_loss(ctx, ctypes.byref(pp), width, height, _ptr(z), weight, _ptr(loss),
+                                 ctypes.byref(gg) if gg is not None else None, _ptr(projected), _stream()), ctx)
 
 
 def _ptr_array(ts):
@@ -374,6 +389,9 @@ class Renderer:
         self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed, max_batch)
         fr_set_mesh(self.ctx, scene.mean, scene.basis, scene.faces, scene.uv)
         fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a)
+        self.landmarks = getattr(scene, "landmarks", None)
+        if self.landmarks is not None:
+            fr_set_landmarks(self.ctx, self.landmarks)
         self.albedo = getattr(scene, "albedo", None)
         if self.albedo is not None:
             a = self.albedo

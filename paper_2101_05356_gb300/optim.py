@@ -20,6 +20,7 @@ import dataclasses
 
 from . import facert
 
+ALPHA1 = 1.0             # weight of E_land in E_d (Sec. 5)
 LR = dict(light=1e-3, identity=1e-2, expression=1e-3, rot=1e-3, trans=1e-3, texture=5e-3, albedo=2e-2)
 W = dict(w_i=0.0025, w_c=0.0025, w_s=0.0025, w1=0.01, w2=0.3, w3=0.3, w4=0.0002, box=1.0)
 STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE
@@ -29,13 +30,14 @@ STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE
 class Schedule:
     stage1: int = 100
     stage2: int = 100
+    init: int = 0           # landmark-only pose and expression iterations before Stage I
 
 
 class FaceState:
     """Parameters, gradients, Adam moments and buffers of one face (device)."""
 
     def __init__(self, renderer, target, init_params, face_id=0, schedule=Schedule(), flags=0,
-                 width=None, height=None, spp=None):
+                 width=None, height=None, spp=None, landmarks=None):
         import torch
         self.torch = torch
         sc = renderer.scene
@@ -57,6 +59,10 @@ class FaceState:
         self.reg = torch.zeros(1, dtype=torch.float64, device="cuda")
         self.image = torch.zeros((self.height, self.width, 3), dtype=torch.float32, device="cuda")
         self.it = 0
+        # landmark targets z [L][2] (pixels of this face's image), E_land weight alpha_1
+        self.landmarks = None if landmarks is None else torch.as_tensor(landmarks, dtype=torch.float32).cuda()
+        self.n_init = schedule.init if landmarks is not None else 0   # no targets: no initialisation stage
+        self.land_loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         self.ref_diffuse = None
         self.ref_specular = None
         # statistical albedo coefficients (Stage I), zero = the mean albedo
@@ -79,14 +85,27 @@ class FaceState:
 
     @property
     def stage(self):
-        return 1 if self.it < self.schedule.stage1 else 2
+        """0: landmark-only initialisation, 1: Stage I, 2: Stage II."""
+        if self.it < self.n_init:
+            return 0
+        return 1 if self.it < self.n_init + self.schedule.stage1 else 2
 
     @property
     def done(self):
-        return self.it >= self.schedule.stage1 + self.schedule.stage2
+        return self.it >= self.n_init + self.schedule.stage1 + self.schedule.stage2
+
+    def landmark_term(self, renderer):
+        """alpha_1 E_land and its gradient (added into g) for stages 0 and 1."""
+        if self.landmarks is not None and self.stage <= 1:
+            facert.fr_landmark_loss(renderer.ctx, self.p, self.width, self.height, self.landmarks, ALPHA1,
+                                    self.land_loss, self.g)
 
     def begin_step(self):
         """Zero gradients (and take the Stage I albedos as Stage II references)."""
+        if self.stage == 1 and self.it == self.n_init > 0:
+            for n in ("rot", "trans", "coef"):     # Stage I restarts Adam after the landmark initialisation
+                self.m[n].zero_()
+                self.v[n].zero_()
         if self.stage == 2 and self.ref_diffuse is None:
             self.ref_diffuse = self.p["diffuse"].clone()
             self.ref_specular = self.p["specular"].clone()
@@ -112,8 +131,17 @@ class FaceState:
     def groups(self):
         """Adam + regulariser groups of the current stage, with this face's step."""
         p, g, m, v, ks = self.p, self.g, self.m, self.v, self.ks
-        if self.stage == 1:
+        if self.stage == 0:
             step = self.it + 1
+            out = [facert.opt_group(p["rot"], m["rot"], v["rot"], g["rot"], lr=LR["rot"], step=step),
+                   facert.opt_group(p["trans"], m["trans"], v["trans"], g["trans"], lr=LR["trans"], step=step)]
+            if p["coef"].numel() > ks:
+                out.append(facert.opt_group(p["coef"][ks:], m["coef"][ks:], v["coef"][ks:], g["coef"][ks:],
+                                            kind=facert.GROUP_COEF, lr=LR["expression"], n_prior=0,
+                                            w_box=W["box"], step=step))
+            return out
+        if self.stage == 1:
+            step = self.it - self.n_init + 1
             out = []
             if ks > 0:
                 out.append(facert.opt_group(p["coef"][:ks], m["coef"][:ks], v["coef"][:ks], g["coef"][:ks],
@@ -134,7 +162,7 @@ class FaceState:
                     out.append(facert.opt_group(a["x"], a["m"], a["v"], a["g"], kind=facert.GROUP_COEF,
                                                 lr=LR["albedo"], n_prior=a["k"], w_prior=w, step=step))
             return out
-        step = self.it - self.schedule.stage1 + 1
+        step = self.it - self.n_init - self.schedule.stage1 + 1
         M = self.tex
         return [
             facert.opt_group(p["diffuse"], m["diffuse"], v["diffuse"], g["diffuse"], aux=self.ref_diffuse,
@@ -152,8 +180,8 @@ class FaceState:
 class Reconstruction(FaceState):
     """One face reconstructed alone through the single-face calls."""
 
-    def __init__(self, renderer, target, init_params, face_id=0, schedule=Schedule(), flags=0):
-        super().__init__(renderer, target, init_params, face_id, schedule, flags)
+    def __init__(self, renderer, target, init_params, face_id=0, schedule=Schedule(), flags=0, landmarks=None):
+        super().__init__(renderer, target, init_params, face_id, schedule, flags, landmarks=landmarks)
         self.r = renderer
         self.history = []
 
@@ -162,10 +190,12 @@ class Reconstruction(FaceState):
         if self.done:
             return
         self.begin_step()
-        facert.fr_set_flags(self.r.ctx, self.item_flags())
-        albedo_morph(self.r, [self])
-        facert.fr_render(self.r.ctx, self.p, self.target, self.image, self.loss, self.g, self.it, self.face_id)
-        albedo_adjoint(self.r, [self])
+        if self.stage > 0:
+            facert.fr_set_flags(self.r.ctx, self.item_flags())
+            albedo_morph(self.r, [self])
+            facert.fr_render(self.r.ctx, self.p, self.target, self.image, self.loss, self.g, self.it, self.face_id)
+            albedo_adjoint(self.r, [self])
+        self.landmark_term(self.r)
         facert.fr_adam(self.groups(), reg_energy=self.reg)
         self.it += 1
 

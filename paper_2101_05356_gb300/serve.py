@@ -31,6 +31,7 @@ class Request:
     schedule: Schedule
     arrival: float = 0.0            # seconds after the server starts
     init: object = None             # synth.Params to start from
+    landmarks: np.ndarray = None    # float32 [L][2] landmark pixels (enables E_land and the init stage)
     # filled by the server
     admitted: float = None
     finished: float = None
@@ -95,7 +96,7 @@ class Server:
             self.queue.pop(0)
             tgt = torch.as_tensor(np.ascontiguousarray(req.target, np.float32)).cuda()
             st = FaceState(self.r, tgt, req.init, face_id=req.rid, schedule=req.schedule, flags=0,
-                           width=req.width, height=req.height, spp=req.spp)
+                           width=req.width, height=req.height, spp=req.spp, landmarks=req.landmarks)
             req.admitted = now
             self.active.append((req, st))
 
@@ -103,11 +104,13 @@ class Server:
     def _step(self):
         for _, st in self.active:
             st.begin_step()
-        states = [st for _, st in self.active]
-        optim.albedo_morph(self.r, states)
-        items = [st.item(self.edge_spp) for st in states]
-        facert.fr_render_batch(self.r.ctx, items)
-        optim.albedo_adjoint(self.r, states)
+        states = [st for _, st in self.active if st.stage > 0]     # stage 0: landmarks only, no render
+        if states:
+            optim.albedo_morph(self.r, states)
+            facert.fr_render_batch(self.r.ctx, [st.item(self.edge_spp) for st in states])
+            optim.albedo_adjoint(self.r, states)
+        for _, st in self.active:
+            st.landmark_term(self.r)
         groups = [g for _, st in self.active for g in st.groups()]
         for k in range(0, len(groups), facert_max_groups()):
             facert.fr_adam(groups[k:k + facert_max_groups()])

@@ -73,6 +73,7 @@ class Scene:
     tex_size: int           # M
     fov_deg: float
     albedo: AlbedoModel | None = None
+    landmarks: np.ndarray | None = None   # int32 [L] landmark vertex indices (Eq. landmark)
 
     @property
     def n_vertices(self) -> int:
@@ -440,6 +441,24 @@ def albedo_model(rng, m, k_diffuse=80, k_specular=80):
                        mean_specular=ms, basis_specular=bs)
 
 
+def landmark_vertices(mean, n=68):
+    """L landmark vertices on the front of the face (the paper uses L = 68
+    detector landmarks): the frontmost half of the vertices (largest z), then
+    farthest-point sampling in the image plane starting next to the centre, so
+    they spread over the face like a detector's contour, brow, eye, nose and
+    mouth points.  Deterministic."""
+    c = np.asarray(mean, np.float64) - np.mean(mean, axis=0)
+    front = np.nonzero(c[:, 2] >= np.quantile(c[:, 2], 0.5))[0]
+    pts = c[front, :2]
+    sel = [int(np.argmin(np.sum(pts * pts, axis=1)))]
+    d = np.sum((pts - pts[sel[0]]) ** 2, axis=1)
+    for _ in range(min(n, front.size) - 1):
+        j = int(np.argmax(d))
+        sel.append(j)
+        d = np.minimum(d, np.sum((pts - pts[j]) ** 2, axis=1))
+    return front[np.array(sel)].astype(np.int32)
+
+
 def _f32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
 
@@ -495,7 +514,8 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
                  faces=np.ascontiguousarray(faces.astype(np.int32)), uv=_f32(uv),
                  lights=lights, light_d=np.full(nl, 3.0, np.float32),
                  light_a=np.ones(nl, np.float32), width=int(w), height=int(h),
-                 spp=int(spp), tex_size=int(m), fov_deg=30.0, albedo=albedo)
+                 spp=int(spp), tex_size=int(m), fov_deg=30.0, albedo=albedo,
+                 landmarks=landmark_vertices(mean))
 
 
 def init_params(scene: Scene, seed: int = 0) -> Params:
