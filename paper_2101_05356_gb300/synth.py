@@ -391,6 +391,61 @@ def light_stage(n_lights, radius=3.0, side=0.5, hemisphere=False,
     return rec
 
 
+def _polyhedron(name):
+    """Unit-circumradius convex polyhedra with triangular faces, counter-
+    clockwise seen from outside: tetrahedron (4 faces), octahedron (8),
+    icosahedron (20) and the icosahedron subdivided once onto the sphere (80)."""
+    if name == "tetra":
+        v = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], np.float64)
+        f = np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]], np.int32)
+    elif name == "octa":
+        v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float64)
+        f = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4], [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]],
+                     np.int32)
+    elif name == "ico":
+        v, f = icosphere(0)
+    elif name == "sphere80":
+        v, f = icosphere(1)
+    else:
+        raise ValueError(name)
+    v = v / np.linalg.norm(v, axis=1, keepdims=True)
+    # orient every face outwards
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    flip = np.sum(np.cross(b - a, c - a) * (a + b + c), axis=1) < 0
+    f[flip] = f[flip][:, [0, 2, 1]]
+    return v, f
+
+
+def polyhedral_stage(name="ico", d=3.0, a=0.25, p=None, centre=STAGE_CENTRE):
+    """The virtual light stage of Sec. 3.3: one triangular area light per face
+    of a convex polyhedron around the head (the paper's icosahedron: 20; also
+    the tetrahedron, octahedron and 80-face sphere variants it compares).
+    Light j lies in face j's homothetic copy scaled by its distance d_j from
+    the stage centre, is that face shrunk by sqrt(a_j) (a_j = relative area in
+    [0, 1]) around the point with barycentric coordinates p_j (default the
+    centroid), stays parallel to the face and emits towards the centre.
+    Returns (records [N_L, 11] of type LIGHT_TRI, d [N_L], a [N_L])."""
+    v, f = _polyhedron(name)
+    n = f.shape[0]
+    d = np.broadcast_to(np.asarray(d, np.float64), (n,))
+    a = np.broadcast_to(np.asarray(a, np.float64), (n,))
+    p = np.full((n, 3), 1.0 / 3.0) if p is None else np.asarray(p, np.float64)
+    c0 = np.asarray(centre, np.float64)
+    rec = np.zeros((n, 11), np.float32)
+    for j in range(n):
+        A, B, C = v[f[j, 0]], v[f[j, 1]], v[f[j, 2]]
+        G = (A + B + C) / 3.0
+        P = c0 + d[j] * (p[j, 0] * A + p[j, 1] * B + p[j, 2] * C)
+        s = math.sqrt(a[j]) * d[j]
+        # vertices in the order A, C, B so that e1 x e2 points inwards
+        t0, t1, t2 = P + s * (A - G), P + s * (C - G), P + s * (B - G)
+        rec[j, 0] = LIGHT_TRI
+        rec[j, 1:4] = t0
+        rec[j, 4:7] = t1 - t0
+        rec[j, 7:10] = t2 - t0
+    return rec, d.astype(np.float32).copy(), a.astype(np.float32).copy()
+
+
 def smooth_field(rng, m, channels, sigma, lo, hi):
     """White noise blurred by a Gaussian of std `sigma` texels (periodic, FFT),
     rescaled per channel to [lo, hi]."""
@@ -475,6 +530,8 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
     tiny : a small closed mesh for fast CPU tests (162 verts / 320 tris, K = 6,
            24x24, 2 spp, 4 lights).
     Keyword overrides replace width/height/spp/tex_size/n_lights/light kind;
+    light_stage = "tetra" | "octa" | "ico" | "sphere80" replaces the lights by
+    the polyhedral virtual light stage of Sec. 3.3 (light_area = a_j);
     albedo_k > 0 adds a statistical albedo model with that many columns per
     albedo (Sec. 3.2; the paper's K_r = K_b = 80)."""
     rng = np.random.default_rng(seed)
@@ -507,13 +564,18 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
     nl = over.get("n_lights", nl)
     kind = over.get("light_kind", LIGHT_QUAD)
     side = over.get("light_side", 0.5 if kind != LIGHT_DISK else 1.0)
-    lights = light_stage(nl, 3.0, side, hemi, STAGE_CENTRE, kind)
+    stage = over.get("light_stage")
+    if stage is not None:                 # polyhedral stage: "tetra", "octa", "ico", "sphere80"
+        lights, light_d, light_a = polyhedral_stage(stage, 3.0, over.get("light_area", 0.25))
+        nl = lights.shape[0]
+    else:
+        lights = light_stage(nl, 3.0, side, hemi, STAGE_CENTRE, kind)
+        light_d, light_a = np.full(nl, 3.0, np.float32), np.ones(nl, np.float32)
     ka = int(over.get("albedo_k", 0))
     albedo = albedo_model(np.random.default_rng(seed + 31), m, ka, ka) if ka > 0 else None
     return Scene(mean=_f32(mean), basis=_f32(basis), n_shape=ks, n_expr=ke,
                  faces=np.ascontiguousarray(faces.astype(np.int32)), uv=_f32(uv),
-                 lights=lights, light_d=np.full(nl, 3.0, np.float32),
-                 light_a=np.ones(nl, np.float32), width=int(w), height=int(h),
+                 lights=lights, light_d=light_d, light_a=light_a, width=int(w), height=int(h),
                  spp=int(spp), tex_size=int(m), fov_deg=30.0, albedo=albedo,
                  landmarks=landmark_vertices(mean))
 

@@ -37,6 +37,10 @@ SCENES = {
     "box": lambda: scenes.shadow_box(),
     # 80 lights: two 64-light visibility chunks
     "many": lambda: (synth.make_scene("tiny", n_lights=80), None),
+    # the paper's icosahedral virtual light stage (20 triangular lights) and
+    # its 80-face sphere variant
+    "ico": lambda: (synth.make_scene("tiny", light_stage="ico"), None),
+    "sphere80": lambda: (synth.make_scene("c1", light_stage="sphere80"), None),
 }
 
 
@@ -124,7 +128,7 @@ def _records_and_image(sc, pr, r, dp, iteration=0):
     return img.cpu().numpy(), oi, agree, px_ok
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "ragged", "box", "many"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "ragged", "box", "many", "ico", "sphere80"])
 def test_forward_parity(name):
     sc, pr = _scene(name)
     r = _renderer(sc)
@@ -206,7 +210,7 @@ def _compare_grads(gg, go, groups, rtol=1e-3):
         assert np.linalg.norm(a - b) <= rtol * nb, (k, np.linalg.norm(a - b) / nb)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "box", "many"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "box", "many", "ico"])
 def test_interior_gradient_parity(name):
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)
@@ -230,7 +234,7 @@ def test_primary_edge_gradient_parity(name):
     _compare_grads(gg, go, ["coef", "rot", "trans", "focal"], rtol=2e-3)
 
 
-@pytest.mark.parametrize("name", ["tiny", "box", "many"])
+@pytest.mark.parametrize("name", ["tiny", "box", "many", "ico"])
 def test_shadow_edge_gradient_parity(name):
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)

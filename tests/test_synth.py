@@ -1,6 +1,8 @@
 """Input generators: the refined 100,000-triangle head of the large workload
-is a closed, consistently oriented sphere-topology mesh."""
+is a closed, consistently oriented sphere-topology mesh; the polyhedral light
+stages place each light in its homothetic face."""
 import numpy as np
+import pytest
 
 from paper_2101_05356_gb300 import synth
 
@@ -28,3 +30,29 @@ def test_large_workload_sizes():
     assert (V, T) == (50_002, 100_000) and V - E + T == 2
     assert basis.shape == (20, V, 3) and uv.shape == (V, 2)
     assert np.all((uv >= 0.0) & (uv <= 1.0))
+
+
+def test_polyhedral_light_stage():
+    """Sec. 3.3: each light is its face's homothetic copy (scale d) shrunk by
+    sqrt(a) around its barycentric centre, parallel to the face, emitting
+    towards the stage centre."""
+    centre = np.array(synth.STAGE_CENTRE)
+    for name, n in (("tetra", 4), ("octa", 8), ("ico", 20), ("sphere80", 80)):
+        v, f = synth._polyhedron(name)
+        p = np.random.default_rng(1).dirichlet([4, 4, 4], size=n)
+        d = np.linspace(2.5, 3.5, n)
+        a = np.linspace(0.1, 0.9, n)
+        rec, dd, aa = synth.polyhedral_stage(name, d, a, p)
+        assert rec.shape == (n, 11) and np.all(rec[:, 0] == synth.LIGHT_TRI)
+        assert np.allclose(dd, d) and np.allclose(aa, a)
+        for j in range(n):
+            A, B, C = (v[f[j, k]] * d[j] + centre for k in range(3))
+            t0 = rec[j, 1:4].astype(np.float64)
+            t1, t2 = t0 + rec[j, 4:7], t0 + rec[j, 7:10]
+            fn = np.cross(B - A, C - A)
+            area_face = 0.5 * np.linalg.norm(fn)
+            ln = np.cross(t1 - t0, t2 - t0)
+            assert 0.5 * np.linalg.norm(ln) == pytest.approx(a[j] * area_face, rel=1e-5)
+            assert np.dot(ln, fn) < 0 and np.linalg.norm(np.cross(ln, fn)) < 1e-5 * np.linalg.norm(ln) * np.linalg.norm(fn)
+            # centroid at the barycentric point p of the homothetic face
+            assert np.allclose((t0 + t1 + t2) / 3, p[j, 0] * A + p[j, 1] * B + p[j, 2] * C, atol=1e-5)
