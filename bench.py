@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Throughput of the differentiable ray-traced face render on GB300.
 
-One step = one pass of the hot path over one face: morph, pose + normals, LBVH
-build, camera + shadow rays with Cook-Torrance shading, blur + L1 loss, and the
+One step = one pass of the hot path over one face: morph, pose + normals, BVH
+(refit of the mesh's static SAH topology), camera + shadow rays with Cook-Torrance shading, blur + L1 loss, and the
 adjoint (interior term from the forward's per-sample hit records, shadow-boundary
 and primary-edge terms, chain to the parameters).  Workload: the paper-scale single face (35,709 vertices /
 70,789 triangles, K = 80 + 64 bases, 256 x 256, 16 spp, 40 quad lights, 512^2
@@ -15,7 +15,9 @@ Prints one JSON line.  `value` is rays traced per second over the timed steps
 traced once, the adjoint reading the forward's hit records); `e2e` is the same
 metric with host buffers copied in and the loss copied out inside the timed
 region; `retrace` times the same step with the adjoint re-tracing every camera
-and shadow ray instead (the form used when the records exceed their budget).
+and shadow ray instead (the form used when the records exceed their budget),
+`lbvh_rebuild` with an LBVH rebuilt every call instead of the refitted static
+SAH topology.
 The reference arm times the FP64 CPU oracle on a bounded sample of the same
 workload.  Under torchrun each rank renders an independent face (replicas).
 """
@@ -209,17 +211,16 @@ def gpu_arm(args, rank, world):
                                % (SMS, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src),
                 "ops_per_launch": ops_per_launch, "launch_ms": dom_ms}
 
-    # ---- the same step with the adjoint re-tracing its rays ----
-    retrace = None
-    if args.retrace_steps > 0:
-        facert.fr_set_flags(r.ctx, facert.FLAG_RECOMPUTE)
+    # ---- the same step in its alternative forms ----
+    def timed_variant(flags, n_steps):
+        facert.fr_set_flags(r.ctx, flags)
         for w in range(3):
             step(2 * 10 ** 5 + w)
         facert.fr_counters(r.ctx, reset=True)
         facert.fr_set_timing(r.ctx, True)
         torch.cuda.synchronize()
         rt, rst = [], []
-        for k in range(args.retrace_steps):
+        for k in range(n_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -233,9 +234,14 @@ def gpu_arm(args, rank, world):
         cnt3 = facert.fr_counters(r.ctx, reset=True)
         facert.fr_set_flags(r.ctx, 0)
         rays3 = sum(v["rays"] for v in cnt3.values())
-        retrace = {"ms_per_step": float(np.mean(rt)), "rays_per_step": rays3 / args.retrace_steps,
-                   "rays_per_s": rays3 / (float(np.sum(rt)) / 1000.0), "steps": args.retrace_steps,
-                   "stage_ms": {k: float(np.mean([s_[k] for s_ in rst])) for k in rst[0]}}
+        return {"ms_per_step": float(np.mean(rt)), "rays_per_step": rays3 / n_steps,
+                "rays_per_s": rays3 / (float(np.sum(rt)) / 1000.0), "steps": n_steps,
+                "stage_ms": {k: float(np.mean([s_[k] for s_ in rst])) for k in rst[0]}}
+
+    # the adjoint re-tracing every camera and shadow ray (the large-image form)
+    retrace = timed_variant(facert.FLAG_RECOMPUTE, args.retrace_steps) if args.retrace_steps > 0 else None
+    # an LBVH rebuilt every call instead of refitting the static SAH topology
+    lbvh = timed_variant(facert.FLAG_LBVH, args.retrace_steps) if args.retrace_steps > 0 else None
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -276,7 +282,7 @@ def gpu_arm(args, rank, world):
                    "steps_per_s": 1000.0 * args.steps / total_ms_max,
                    "stage_ms": {k: float(np.mean([s[k] for s in stage])) for k in stage[0]}},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-        "retrace": retrace, "status": int(status),
+        "retrace": retrace, "lbvh_rebuild": lbvh, "status": int(status),
     }
     return out
 
@@ -324,6 +330,75 @@ def serving_bench(n_requests, iters, rate, seed=0):
     out["final_loss_ratio"] = out["served"]["mean_final_loss"] / out["plain"]["mean_final_loss"]
     out["workload"] = ("%d Poisson requests (rate %.0f/s), sizes {128,192,256}^2, spp {4,8,16}, %d+%d "
                        "iterations, 35,709-vertex face, 40 lights" % (n_requests, rate, iters, iters))
+    return out
+
+
+def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slots=8):
+    """The serving workload: a Poisson stream of two-stage reconstructions of
+    the paper-scale face (35,709 vertices, 40 lights, 512^2 textures, a
+    statistical albedo model of 80 + 80 columns, 68 landmarks) with image
+    size uniform in {128, 192, 256, 384, 512}^2 and spp in {4, 8, 16, 32};
+    each request runs `init` landmark iterations, then Stage I and Stage II.
+    The arrival rate is 0.9 x the served closed-loop capacity measured first
+    on a short prefix.  Served (continuous batching, BF16 tensor-core morphs,
+    max_slots slots) and plain (one face at a time, FP32) see the same stream;
+    final losses are evaluated at 32 spp with a fixed evaluation stream."""
+    import torch
+
+    from paper_2101_05356_gb300 import facert, optim, serve, synth
+    sc = synth.make_scene("c2", albedo_k=80)
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([128, 192, 256, 384, 512], size=n_requests)
+    spps = rng.choice([4, 8, 16, 32], size=n_requests)
+    # targets and landmark targets rendered from ground-truth parameters
+    gen = facert.Renderer(sc.__class__(**{**sc.__dict__, "width": 512, "height": 512, "spp": 32, "albedo": None}))
+    targets, marks = [], []
+    zero = torch.zeros((512 * 512 * 3,), device="cuda")
+    for k in range(n_requests):
+        w, sp = int(sizes[k]), int(spps[k])
+        gt = gen.device_params(synth.random_params(sc, 700 + k, coef_scale=0.5))
+        img = torch.zeros((w, w, 3), device="cuda")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        facert.fr_render_batch(gen.ctx, [dict(width=w, height=w, spp=sp, edge_spp=1, flags=0, iteration=10 ** 7,
+                                              face_id=k, params=gt, target=zero, image=img, loss=loss)])
+        proj = torch.zeros((len(sc.landmarks), 2), device="cuda")
+        facert.fr_landmark_loss(gen.ctx, gt, w, w, torch.zeros_like(proj), 1.0, loss, None, proj)
+        targets.append(img.cpu().numpy())
+        marks.append(proj.cpu().numpy())
+    gen.close()
+    sched = optim.Schedule(stage1=stage1, stage2=stage2, init=init)
+
+    def stream(arrivals):
+        return [serve.Request(rid=k, target=targets[k], spp=int(spps[k]), schedule=sched, arrival=float(arrivals[k]),
+                              init=synth.init_params(sc), landmarks=marks[k]) for k in range(n_requests)]
+
+    def server(slots, flags):
+        return serve.Server(sc, max_slots=slots, flags=flags, max_width=512, max_height=512, max_spp=32,
+                            eval_spp=32, keep_params=False, mem_cap_bytes=64 << 30)
+
+    # closed-loop capacity of the served form on a prefix (all arrive at once)
+    n_cap = min(n_requests, 2 * max_slots)
+    srv = server(max_slots, facert.FLAG_MORPH_BF16)
+    srv.run(stream(np.zeros(n_requests))[:n_cap])
+    capacity = n_cap / srv.elapsed
+    srv.r.close()
+    rate = 0.9 * capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    out = {"workload": "%d Poisson requests, sizes {128..512}^2, spp {4,8,16,32}, %d landmark + %d + %d "
+                       "iterations, 35,709-vertex face, 40 lights, statistical albedo 80+80, 68 landmarks"
+                       % (n_requests, init, stage1, stage2),
+           "closed_loop_capacity_faces_per_s": capacity, "arrival_rate_per_s": rate}
+    for name, slots, flags in (("served", max_slots, facert.FLAG_MORPH_BF16), ("plain", 1, 0)):
+        srv = server(slots, flags)
+        reqs = srv.run(stream(arrivals))
+        lat = serve.latency_stats(reqs)
+        out[name] = dict(faces_per_s=len(reqs) / srv.elapsed, elapsed_s=srv.elapsed, p50_s=lat["p50_s"],
+                         p99_s=lat["p99_s"], mean_final_loss=float(np.mean([q.final_loss for q in reqs])),
+                         mean_batch=float(np.mean(srv.batch_sizes)), steps=srv.steps)
+        srv.r.close()
+        torch.cuda.synchronize()
+    out["faces_per_s_speedup"] = out["served"]["faces_per_s"] / out["plain"]["faces_per_s"]
+    out["final_loss_ratio"] = out["served"]["mean_final_loss"] / out["plain"]["mean_final_loss"]
     return out
 
 
@@ -417,12 +492,24 @@ def main():
     ap.add_argument("--cpu-pixels", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-albedo", action="store_true")
+    ap.add_argument("--serve-c4", type=int, default=0, help="run the serving workload with this many requests")
+    ap.add_argument("--serve-c4-stage1", type=int, default=100)
+    ap.add_argument("--serve-c4-stage2", type=int, default=100)
+    ap.add_argument("--serve-c4-init", type=int, default=20)
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-iters", type=int, default=6)
     ap.add_argument("--serve-rate", type=float, default=40.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.serve_c4 > 0:
+        # the full serving workload, reported on its own line (not the step benchmark)
+        res = serving_c4(args.serve_c4, args.serve_c4_stage1, args.serve_c4_stage2, args.serve_c4_init)
+        print(json.dumps({"metric": "faces/s (served reconstruction stream)", "value": res["served"]["faces_per_s"],
+                          "unit": "faces/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+                          "serving": res}))
+        return
 
     if args.impl == "reference":
         if rank != 0:

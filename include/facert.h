@@ -56,6 +56,10 @@ typedef int32_t fr_status;
                                          accumulate, FP32 mean); context-wide, read by every call */
 #define FR_FLAG_RECOMPUTE      256u   /* fused steps re-trace the adjoint's primary and shadow rays
                                          even when the hit records fit (see fr_render) */
+#define FR_FLAG_LBVH           512u   /* rebuild an LBVH (Morton sort + Karras tree) every call instead
+                                         of refitting the SAH topology built from the mean face at
+                                         fr_set_mesh; for deformations far from the mean face.
+                                         Context-wide, read from the context's flags */
 
 /* Per-slot budget for the hit records of a fused step (bytes): a context whose
  * width * height * spp * 20 bytes fit keeps, per slot, the forward's hit

@@ -40,6 +40,8 @@ struct Slot {
     double* pose_part = nullptr;
     float* sign = nullptr;
     float* adj_image = nullptr;
+    int* edge_perm = nullptr;        // primary-edge sample order [edge_cap]
+    long edge_cap = 0;
     int32_t* rec_tri = nullptr;      // fused-step hit records (null when over FR_RECORDS_BUDGET)
     uint64_t* rec_vis = nullptr;
     long rec_samples = 0;
@@ -69,6 +71,8 @@ struct fr_ctx {
     LinearModel shape;                         // rows 3N
     LinearModel albedo[2];                     // diffuse, specular; rows 3 M^2 (optional)
     bool have_albedo = false;
+    // static SAH topology of the mesh (refitted per call unless FR_FLAG_LBVH)
+    int *topo_child = nullptr, *topo_parent_int = nullptr, *topo_parent_leaf = nullptr, *topo_vals = nullptr;
     int* landmarks = nullptr;                  // landmark vertex indices [n_landmarks]
     int n_landmarks = 0;
     int4* faces = nullptr;
@@ -191,6 +195,13 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.EL.light_list = sl.lists + c->E;
     it.EL.light_count = sl.counts + 1;
     it.B = sl.B;
+    if (!(c->cfg.flags & FR_FLAG_LBVH)) {     // refit the static topology
+        it.B.child = c->topo_child;
+        it.B.parent_int = c->topo_parent_int;
+        it.B.parent_leaf = c->topo_parent_leaf;
+        it.B.vals = c->topo_vals;
+        it.B.keys = nullptr;
+    }
     it.nodes = sl.nodes;
     it.tris = sl.tris;
     it.v_cam = sl.v_cam;
@@ -205,6 +216,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.adj = a.adj ? a.adj : sl.adj_image;
     it.tri_rec = a.tri_rec;
     it.mask_rec = a.mask_rec;
+    if ((long)a.W * a.H * a.edge_spp <= sl.edge_cap) it.edge_perm = sl.edge_perm;
     if (a.records && sl.rec_tri && !(a.flags & FR_FLAG_RECOMPUTE) && (long)a.W * a.H * a.spp <= sl.rec_samples) {
         it.rec_tri = sl.rec_tri;
         it.rec_vis = sl.rec_vis;
@@ -316,7 +328,7 @@ void build_geometry(fr_ctx* c, int n, cudaStream_t st) {
     launch_pose(c->d_items, n, c->N, st);
     launch_faces(c->d_items, n, c->faces, c->T, st);
     launch_vertex_normals(c->d_items, n, c->vf_off, c->vf_idx, c->N, st);
-    launch_lbvh(c->d_items, n, c->faces, c->T, c->status, st);
+    launch_lbvh(c->d_items, n, c->faces, c->T, c->status, (c->cfg.flags & FR_FLAG_LBVH) != 0, st);
 }
 
 fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
@@ -340,6 +352,12 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     mark(c, 4, st);
     launch_adjoint(c->d_items, map_of(c, n, false), c->NL, st);
     mark(c, 5, st);
+    long max_edge = 0;
+    for (int k = 0; k < n; ++k) {
+        const DevScene& s = c->h_items[k].S;
+        if (!(s.flags & FR_FLAG_NO_PRIMARY_EDGE)) max_edge = std::max(max_edge, (long)s.W * s.H * s.edge_spp);
+    }
+    launch_edge_order(c->d_items, n, max_edge, st);
     launch_edge_primary(c->d_items, map_of(c, n, true), st);
     mark(c, 6, st);
     launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
@@ -399,6 +417,9 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.dm, 3 * (size_t)N));
     TRY(dalloc(c, &sl.small, 1 + 3 * FR_MAX_LIGHTS));
     TRY(dalloc(c, &sl.pose_part, 12 * (size_t)((N + 255) / 256)));
+    // processing order of the primary-edge samples (the context's edge_spp, at least 1)
+    sl.edge_cap = (long)c->cfg.width * c->cfg.height * std::max(c->cfg.edge_spp, 1);
+    TRY(dalloc(c, &sl.edge_perm, (size_t)sl.edge_cap));
     // hit records of a fused step: triangle + two visibility words per sample
     const long samples = (long)c->cfg.width * c->cfg.height * c->cfg.spp;
     if (samples * (long)(sizeof(int32_t) + 2 * sizeof(uint64_t)) <= (long)FR_RECORDS_BUDGET) {
@@ -506,6 +527,20 @@ fr_status fr_set_mesh(fr_ctx* c, const fr_mesh* m) {
     c->N = N; c->T = T; c->K = K; c->E = (int)edges.size();
     TRY(upload_model(c, c->shape, 3 * N, K, m->mean, m->basis));
     c->ld = c->shape.ld;
+    {
+        BvhTopology topo;
+        build_bvh_topology(m->mean, m->faces, T, topo);
+        TRY(dalloc(c, &c->topo_child, topo.child.size()));
+        TRY(dalloc(c, &c->topo_parent_int, topo.parent_int.size()));
+        TRY(dalloc(c, &c->topo_parent_leaf, topo.parent_leaf.size()));
+        TRY(dalloc(c, &c->topo_vals, topo.vals.size()));
+        CK(c, cudaMemcpy(c->topo_child, topo.child.data(), sizeof(int) * topo.child.size(), cudaMemcpyHostToDevice));
+        CK(c, cudaMemcpy(c->topo_parent_int, topo.parent_int.data(), sizeof(int) * topo.parent_int.size(),
+                         cudaMemcpyHostToDevice));
+        CK(c, cudaMemcpy(c->topo_parent_leaf, topo.parent_leaf.data(), sizeof(int) * topo.parent_leaf.size(),
+                         cudaMemcpyHostToDevice));
+        CK(c, cudaMemcpy(c->topo_vals, topo.vals.data(), sizeof(int) * topo.vals.size(), cudaMemcpyHostToDevice));
+    }
     TRY(dalloc(c, &c->faces, T));
     TRY(dalloc(c, &c->uv, N));
     TRY(dalloc(c, &c->vf_off, N + 1));

@@ -199,6 +199,7 @@ struct DevItem {
     uint64_t* mask_rec;
     int32_t* rec_tri;       // fused-step hit records: forward writes, adjoint reads (null: re-trace)
     uint64_t* rec_vis;      // [samples][2] visibility words, lights 0..63 and 64..127
+    int* edge_perm;         // processing order of the primary-edge samples (null: index order)
     float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
     uint32_t iteration, face;
 };

@@ -130,8 +130,10 @@ __global__ void __launch_bounds__(256) k_faces(const DevItem* items, const int4*
         const uint32_t q = min((uint32_t)(u * 1024.0f), 1023u);
         code |= spread10(q) << (2 - k);
     }
-    it.B.keys[f] = code;
-    it.B.vals[f] = f;
+    if (it.B.keys) {                         // Morton keys only for the per-call LBVH rebuild
+        it.B.keys[f] = code;
+        it.B.vals[f] = f;
+    }
 }
 
 // Vertex normal = normalised sum of its faces' un-normalised normals, gathered

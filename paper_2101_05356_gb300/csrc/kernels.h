@@ -2,6 +2,8 @@
 // C-ABI implementation.  Batched launchers take the device item table (one
 // DevItem per face) and the number of items.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 // process-wide count of kernels launched by this library (api.cu)
@@ -61,13 +63,23 @@ struct LandmarkArgs {
 };
 void launch_landmarks(const LandmarkArgs& a, cudaStream_t st);
 
-// lbvh.cu
-void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, cudaStream_t st);
+// bvh_topology.cu (host): static binned-SAH topology of a mesh, in the
+// BvhScratch encoding (child codes ~leaf slot / internal index, root 0)
+struct BvhTopology {
+    std::vector<int> child, parent_int, parent_leaf, vals;
+};
+void build_bvh_topology(const float* v, const int* faces, int T, BvhTopology& out);
+
+// lbvh.cu: rebuild = Morton sort + Karras radix tree per call; otherwise the
+// items' BvhScratch carries a fixed topology and only the boxes are refitted
+void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, bool rebuild,
+                 cudaStream_t st);
 void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);
 
 // render.cu
 void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st);
 void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, cudaStream_t st);
+void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st);
 void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri,

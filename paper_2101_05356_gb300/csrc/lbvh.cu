@@ -1,4 +1,6 @@
-// Linear BVH over the camera-space triangles, rebuilt every call: Morton keys
+// Linear BVH over the camera-space triangles (the per-call rebuild; the
+// default refits a static SAH topology built at set-up, bvh_topology.cu, with
+// the same box and pack kernels): Morton keys
 // of the centroids (geometry.cu), a stable LSD radix sort (4 x 8-bit passes),
 // the radix-tree construction of Karras (HPG 2012) with index tie-breaks, and a
 // bottom-up box pass with one atomic flag per internal node.  Leaves are single
@@ -167,6 +169,11 @@ __global__ void __launch_bounds__(256) k_karras(const DevItem* items, int n, int
     if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
 }
 
+__global__ void k_flag_reset(const DevItem* items, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n - 1) items[blockIdx.y].B.flag[i] = 0;
+}
+
 // flags 0; parents and child codes -1 (an unwritten child reads as leaf 0,
 // never as an ancestor)
 __global__ void k_bvh_init(const DevItem* items, int n) {
@@ -298,7 +305,18 @@ int nb(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, cudaStream_t st) {
+void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* status, bool rebuild,
+                 cudaStream_t st) {
+    if (!rebuild) {                                  // refit a fixed topology: reset the climb flags only
+        if (T > 1) {
+            k_flag_reset<<<dim3(nb(T - 1, 256), n), 256, 0, st>>>(items, T);
+            fr_count_launches(1);
+        }
+        k_boxes<<<dim3(nb(T, 256), n), 256, 0, st>>>(items, faces, T, status);
+        k_pack<<<dim3(nb(T > 1 ? T - 1 : 1, 256), n), 256, 0, st>>>(items, T);
+        fr_count_launches(2);
+        return;
+    }
     const int n_tiles = nb(T, SORT_TILE);
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;

@@ -368,6 +368,21 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     const bool hb = (E.y == fc.x || E.y == fc.y || E.y == fc.z);
     if (ha && hb) return;
     const float3 A = xyz(S.v[E.x]), B = xyz(S.v[E.y]);
+    // the emitter-plane projection first: it rejects almost every sample in
+    // FP32, before the FP64 silhouette test (all conditions must hold, so the
+    // order does not change which samples count)
+    const LightDev& L = S.lights[j];
+    const float t = u2;
+    const float3 e = B - A;
+    const float3 pe = A + e * t;
+    const float3 q = pe - ss.y;
+    const float den = dot(q, L.n);
+    const float num = dot(L.c - ss.y, L.n);
+    if (den == 0.0f) return;
+    const float sc = num / den;
+    if (!(sc > 1.0f)) return;
+    const float3 z = ss.y + q * sc;
+    if (!inside_emitter(L, z)) return;
     if (E.w >= 0) {
         // silhouette w.r.t. y, in FP64
         const int4 f1 = S.faces[E.z], f2 = S.faces[E.w];
@@ -385,18 +400,6 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
         }
         if (sg[0] == sg[1]) return;
     }
-    const LightDev& L = S.lights[j];
-    const float t = u2;
-    const float3 e = B - A;
-    const float3 pe = A + e * t;
-    const float3 q = pe - ss.y;
-    const float den = dot(q, L.n);
-    const float num = dot(L.c - ss.y, L.n);
-    if (den == 0.0f) return;
-    const float sc = num / den;
-    if (!(sc > 1.0f)) return;
-    const float3 z = ss.y + q * sc;
-    if (!inside_emitter(L, z)) return;
     const float3 h = light_h<false>(S.flags, L, z, ss, f3(0, 0, 0), nullptr, nullptr);
     if (h.x == 0.0f && h.y == 0.0f && h.z == 0.0f) return;
     const float3 tan = (e - q * (dot(e, L.n) / den)) * sc;
@@ -591,6 +594,70 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
 }
 
 // ---------------------------------------------------------------------------
+// processing order of the primary-edge samples
+// ---------------------------------------------------------------------------
+// Each primary-edge sample picks a random silhouette edge, so consecutive
+// samples land far apart and a warp's camera and shadow rays diverge.  Within
+// each chunk of EDGE_CHUNK consecutive samples this kernel sorts the samples
+// by the pixel their edge point projects to (samples that cannot contribute
+// last), with a bitonic sort in shared memory; k_edge_primary then processes
+// them in that order.  The set of samples, and so the estimate, is unchanged;
+// the order is a deterministic function of the inputs.
+constexpr int EDGE_CHUNK = 4096;                   // 12 bits of in-chunk index
+constexpr int EDGE_SORT_THREADS = 1024;
+
+__global__ void __launch_bounds__(EDGE_SORT_THREADS) k_edge_order(const DevItem* items) {
+    __shared__ uint32_t key[EDGE_CHUNK];
+    const DevItem& it = items[blockIdx.y];
+    const DevScene& S = it.S;
+    const long n_edge = (S.flags & FR_FLAG_NO_PRIMARY_EDGE_D) ? 0 : (long)S.W * S.H * S.edge_spp;
+    const long base = (long)blockIdx.x * EDGE_CHUNK;
+    if (base >= n_edge || !it.edge_perm) return;         // block-uniform
+    const int Sn = *it.EL.prim_count;
+    const float f = it.P.focal[0];
+    const long npx = (long)S.W * S.H;
+    for (int q = threadIdx.x; q < EDGE_CHUNK; q += EDGE_SORT_THREADS) {
+        const long e = base + q;
+        uint32_t k20 = 0xFFFFFu;                           // no contribution possible: last
+        if (e < n_edge && Sn > 0) {
+            const Sampler smp{make_uint2(S.seed, FR_STREAM_EDGE_PRIMARY), (uint32_t)e, 0u, it.iteration, it.face};
+            const uint4 blk = smp.block(0);
+            const int4 E = it.EL.edges[it.EL.prim_list[min((int)(u24(blk.x) * (float)Sn), Sn - 1)]];
+            const float3 A = xyz(S.v[E.x]), B = xyz(S.v[E.y]);
+            const float3 p = A + (B - A) * u24(blk.y);
+            if (p.z < 0.0f) {
+                const float X = 0.5f * S.W + f * p.x / -p.z, Y = 0.5f * S.H - f * p.y / -p.z;
+                if (X >= 0.0f && X < (float)S.W && Y >= 0.0f && Y < (float)S.H) {
+                    const long pix = (long)floorf(Y) * S.W + (long)floorf(X);
+                    k20 = (uint32_t)min(0xFFFFEL, pix * 0xFFFFEL / npx);     // row-major pixel, 20 bits
+                }
+            }
+        }
+        key[q] = (k20 << 12) | (uint32_t)q;                // the index makes keys distinct
+    }
+    __syncthreads();
+    for (int k = 2; k <= EDGE_CHUNK; k <<= 1)              // bitonic sort, ascending
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < EDGE_CHUNK; i += EDGE_SORT_THREADS) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint32_t a = key[i], b = key[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        key[i] = b;
+                        key[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // samples past n_edge carry the largest keys, so positions [0, count) hold
+    // exactly this chunk's samples
+    const int count = (int)min((long)EDGE_CHUNK, n_edge - base);
+    for (int q = threadIdx.x; q < count; q += EDGE_SORT_THREADS)
+        it.edge_perm[base + q] = (int)(base + (key[q] & (EDGE_CHUNK - 1)));
+}
+
+// ---------------------------------------------------------------------------
 // primary-visibility boundary term: edge samples in screen space
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary(const DevItem* items, BlockMap map) {
@@ -606,8 +673,11 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
     const uint32_t iteration = it.iteration, face = it.face;
     block_acc_init(1);
     const long n_edge = (long)S.W * S.H * S.edge_spp;
-    const long e = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
-    bool active = e < n_edge;
+    const long e0 = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
+    bool active = e0 < n_edge;
+    // samples are processed in the order k_edge_order chose (same samples, so
+    // the same estimate; nearby samples share a warp)
+    const long e = (active && it.edge_perm) ? (long)it.edge_perm[e0] : e0;
     const int Sn = *EL.prim_count;
     if (Sn == 0) active = false;
     const Sampler smp{make_uint2(S.seed, FR_STREAM_EDGE_PRIMARY), (uint32_t)(active ? e : 0), 0u, iteration, face};
@@ -843,6 +913,12 @@ void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, cudaStrea
     if (map_blocks(map) == 0) return;
     const size_t acc_bytes = sizeof(double) * RT_WARPS * (1 + 3 * (size_t)NL);
     k_adjoint<<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+    fr_count_launches(1);
+}
+
+void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st) {
+    if (n <= 0 || max_edge <= 0) return;
+    k_edge_order<<<dim3((unsigned)((max_edge + EDGE_CHUNK - 1) / EDGE_CHUNK), n), EDGE_SORT_THREADS, 0, st>>>(items);
     fr_count_launches(1);
 }
 

@@ -20,6 +20,7 @@ FLAG_GGX, FLAG_SCHLICK_LINEAR, FLAG_FLAT = 1, 2, 4
 FLAG_NO_INTERIOR, FLAG_NO_PRIMARY_EDGE, FLAG_NO_SHADOW_EDGE = 16, 32, 64
 FLAG_MORPH_BF16 = 128
 FLAG_RECOMPUTE = 256
+FLAG_LBVH = 512
 
 _vp = ctypes.c_void_p
 

@@ -50,7 +50,8 @@ class Request:
 
 class Server:
     def __init__(self, scene, max_slots=8, mem_cap_bytes=8 << 30, flags=facert.FLAG_MORPH_BF16,
-                 max_width=None, max_height=None, max_spp=None, edge_spp=1, seed=0, eval_iteration=10 ** 6):
+                 max_width=None, max_height=None, max_spp=None, edge_spp=1, seed=0, eval_iteration=10 ** 6,
+                 eval_spp=None, keep_params=True):
         import torch
         self.torch = torch
         sc = dataclasses.replace(scene, width=max_width or scene.width, height=max_height or scene.height,
@@ -62,6 +63,8 @@ class Server:
         self.flags = flags
         self.edge_spp = edge_spp
         self.eval_iteration = eval_iteration
+        self.eval_spp = eval_spp          # final loss at this spp (None: the request's own)
+        self.keep_params = keep_params    # copy each finished request's parameters to the host
         self.queue = []
         self.active = []                # (request, FaceState)
         self.done = []
@@ -130,12 +133,15 @@ class Server:
                 it = st.item(self.edge_spp)
                 it["iteration"] = self.eval_iteration
                 it["grads"] = None
+                if self.eval_spp:
+                    it["spp"] = self.eval_spp
                 items.append(it)
             facert.fr_render_batch(self.r.ctx, items)
             torch.cuda.synchronize()
             for req, st in fin:
                 req.final_loss = float(st.loss.item())
-                req.params = {k: v.detach().cpu().numpy() for k, v in st.p.items()}
+                if self.keep_params:
+                    req.params = {k: v.detach().cpu().numpy() for k, v in st.p.items()}
                 req.finished = time.perf_counter() - self.t0
                 self.done.append(req)
         for req, st in self.active:

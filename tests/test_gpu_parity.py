@@ -79,10 +79,13 @@ def test_geometry_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", ["tiny", "c1", "c2"])
-def test_bvh_is_valid(name):
+@pytest.mark.parametrize("rebuild", [False, True])
+def test_bvh_is_valid(name, rebuild):
+    """The refitted static SAH topology (default) and the per-call LBVH."""
+    from paper_2101_05356_gb300 import facert
     sc = synth.make_scene(name) if name == "c2" else _scene(name)[0]
     pr = synth.random_params(sc, 0)
-    r = _renderer(sc)
+    r = _renderer(sc, flags=facert.FLAG_LBVH if rebuild else 0)
     from paper_2101_05356_gb300 import facert
     out = torch.zeros(3, dtype=torch.int32, device="cuda")
     facert.fr_debug_bvh(r.ctx, r.device_params(pr), out)
@@ -138,6 +141,24 @@ def test_forward_parity(name):
     scale = 1e-2 * o.mean()
     err = np.abs(g - o) / np.maximum(np.abs(o), scale)
     assert np.max(err[px_ok]) <= 1e-4, np.max(err[px_ok])
+    assert r.status() == 0
+
+
+@pytest.mark.parametrize("name", ["c1", "box"])
+def test_forward_parity_with_lbvh_rebuild(name):
+    """The same records and radiance with the per-call LBVH instead of the
+    refitted topology (the closest hit and any hit do not depend on the tree)."""
+    from paper_2101_05356_gb300 import facert
+    sc, pr = _scene(name)
+    r = _renderer(sc, flags=facert.FLAG_LBVH)
+    dp = r.device_params(pr)
+    g, o, agree, px_ok = _records_and_image(sc, pr, r, dp, iteration=3)
+    assert np.mean(~agree) <= 1e-3, int(np.sum(~agree))
+    scale = 1e-2 * o.mean()
+    err = np.abs(g - o) / np.maximum(np.abs(o), scale)
+    assert np.max(err[px_ok]) <= 1e-4, np.max(err[px_ok])
+    ref = _renderer(sc)
+    assert torch.equal(ref.forward(dp, iteration=3), r.forward(dp, iteration=3))
     assert r.status() == 0
 
 

@@ -16,8 +16,9 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _requests(sc, specs, schedule):
+def _requests(sc, specs, schedule, landmarks=False):
     from paper_2101_05356_gb300 import facert, serve
+    from oracle import landmarks as olm
     reqs = []
     for rid, (w, h, spp, arrival) in enumerate(specs):
         import dataclasses
@@ -26,8 +27,9 @@ def _requests(sc, specs, schedule):
         gt = synth.random_params(s2, 50 + rid, coef_scale=0.5)
         tgt = r.forward(r.device_params(gt), iteration=10 ** 7, face_id=rid).cpu().numpy()
         r.close()
+        lm = olm.project(sc, gt, sc.landmarks, w, h).astype(np.float32) if landmarks else None
         reqs.append(serve.Request(rid=rid, target=tgt, spp=spp, schedule=schedule, arrival=arrival,
-                                  init=synth.init_params(sc)))
+                                  init=synth.init_params(sc), landmarks=lm))
     return reqs
 
 
@@ -56,6 +58,24 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         for name in ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness"):
             a, b = got.params[name], ref.params[name]
             assert np.array_equal(a, b), (k, name, float(np.abs(a.astype(np.float64) - b).max()))
+
+
+def test_full_pipeline_is_the_same_alone_and_in_the_mix():
+    """The same with every stage of a reconstruction: landmark initialisation,
+    Stage I with the statistical albedo (batched tensor-core morph and its
+    transpose) and the landmark term, Stage II."""
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("c1", albedo_k=8)
+    sched = optim.Schedule(stage1=3, stage2=2, init=2)
+    mixed = serve.Server(sc, max_slots=4, max_width=64, max_height=64, max_spp=8).run(
+        _requests(sc, SPECS, sched, landmarks=True))
+    for k in range(len(SPECS)):
+        lone_req = _requests(sc, SPECS, sched, landmarks=True)[k]
+        ref = serve.Server(sc, max_slots=1, max_width=64, max_height=64, max_spp=8).run([lone_req])[0]
+        got = mixed[k]
+        assert got.final_loss == pytest.approx(ref.final_loss, rel=1e-12)
+        for name in ("coef", "rot", "trans", "light_i", "diffuse", "specular", "roughness"):
+            assert np.array_equal(got.params[name], ref.params[name]), (k, name)
 
 
 def test_memory_cap_and_slots_bound_admission():
