@@ -350,7 +350,9 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     }
     if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, c->T, st);
     mark(c, 4, st);
-    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, st);
+    bool all_recorded = true;
+    for (int k = 0; k < n; ++k) all_recorded &= c->h_items[k].rec_tri != nullptr;
+    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_recorded, st);
     mark(c, 5, st);
     long max_edge = 0;
     for (int k = 0; k < n; ++k) {

@@ -78,7 +78,7 @@ void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);
 
 // render.cu
 void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st);
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, cudaStream_t st);
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, cudaStream_t st);
 void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st);
 void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);

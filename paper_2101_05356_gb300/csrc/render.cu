@@ -78,8 +78,11 @@ struct SampleState {
 // Primary ray through screen point (sx, sy) and the shading state at its hit.
 // rec >= -1 is this ray's recorded hit triangle (-1: miss) and replaces the
 // traversal; rec = REC_TRACE traces.
+// CAN_TRACE = false compiles the traversal out (callers that always have a
+// record).
 constexpr int REC_TRACE = -2;
 
+template <bool CAN_TRACE = true>
 FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
                         Stack st, SampleState& ss, RayStats& rs, int rec = REC_TRACE) {
     ss.hit = false;
@@ -88,7 +91,7 @@ FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, floa
     const float f = __ldg(P.focal);
     ss.d = f3((sx - 0.5f * S.W) / f, -(sy - 0.5f * S.H) / f, -1.0f);
     const RayPre r = ray_setup(f3(0.0f, 0.0f, 0.0f), ss.d);
-    const Hit h = rec == REC_TRACE ? trace_closest(S, r, 0.0f, INFINITY, st, rs) : hit_record(S, r, rec);
+    const Hit h = (CAN_TRACE && rec == REC_TRACE) ? trace_closest(S, r, 0.0f, INFINITY, st, rs) : hit_record(S, r, rec);
     if (h.tri < 0) return;
     ss.hit = true;
     ss.tri = h.tri;
@@ -422,6 +425,10 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     add_vec(d_v, E.y, g_p * (C * t), true);
 }
 
+// RECORDED: every item of the launch carries the forward's hit records, so the
+// camera and shadow traversals are compiled out (a smaller kernel); otherwise
+// each item re-traces unless it has records.
+template <bool RECORDED>
 __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
     FR_STACK_DECL
@@ -454,8 +461,8 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     RayStats rs;
     // the forward of a fused step may have recorded this sample's hit and
     // shadow visibility; otherwise both are re-traced with the same counters
-    const bool recorded = it.rec_tri != nullptr;           // block-uniform
-    primary_state(S, P, valid, sx, sy, my_stack(sh), ss, rs,
+    const bool recorded = RECORDED || it.rec_tri != nullptr;   // block-uniform
+    primary_state<!RECORDED>(S, P, valid, sx, sy, my_stack(sh), ss, rs,
                   recorded ? (valid ? it.rec_tri[qi] : -1) : REC_TRACE);
     const bool interior = !(S.flags & FR_FLAG_NO_INTERIOR_D);
     ShadeAdj g;
@@ -751,33 +758,68 @@ __device__ double3 face_normal_d(const DevScene& S, int f) {
 
 __device__ int sgn_d(double x) { return (x > 0.0) - (x < 0.0); }
 
-// Facing class of face f over emitter j (FP64): 1 = every point of the emitter
-// is in front of the face's plane, 2 = every point behind, 3 = mixed.  The
-// signed distance is linear over the emitter, so its range follows from the
-// corners (quad, triangle) or the projected radius (disk).
+// Signed-distance range [lo, hi] of emitter L over the plane of a face with
+// (unnormalised) normal n through p0: the distance is linear over the
+// emitter, so the range follows from the corners (quad, triangle) or the
+// projected radius (disk).
+template <class Real>
+FR_D void emitter_range(int type, Real base, Real g1, Real g2, Real& lo, Real& hi) {
+    if (type == 0) {
+        const Real h = (Real)0.5 * fabs(g1) + (Real)0.5 * fabs(g2);
+        lo = base - h; hi = base + h;
+    } else if (type == 1) {
+        lo = base + fmin((Real)0, fmin(g1, g2)); hi = base + fmax((Real)0, fmax(g1, g2));
+    } else {
+        const Real r = sqrt(g1 * g1 + g2 * g2);
+        lo = base - r; hi = base + r;
+    }
+}
+
+// Facing class of face f over emitter j: 1 = every point of the emitter is in
+// front of the face's plane, 2 = every point behind, 3 = mixed, decided in
+// FP64.  An FP32 evaluation decides first whenever it is farther from zero
+// than a bound on its rounding error (64 u times the sum of the magnitudes
+// involved, u = 2^-24, a generous multiple of the few roundings per term), so
+// the FP64 work runs only for nearly grazing pairs and every class equals the
+// FP64 one.
 __global__ void k_face_class(const DevItem* items) {
     const DevItem& it = items[blockIdx.y];
     const DevScene& S = it.S;
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= S.T) return;
+    const int4 tv = S.faces[f];
+    const float3 q0 = xyz(S.v[tv.x]), q1 = xyz(S.v[tv.y]), q2 = xyz(S.v[tv.z]);
+    const float3 a = q1 - q0, b = q2 - q0;
+    const float3 nf = cross(a, b);
+    const float3 na = f3(fabsf(a.y * b.z) + fabsf(a.z * b.y), fabsf(a.z * b.x) + fabsf(a.x * b.z),
+                         fabsf(a.x * b.y) + fabsf(a.y * b.x));    // bounds |n| and its rounding
     const double3 n = face_normal_d(S, f);
-    const float4 p0 = S.v[S.faces[f].x];
+    const float4 p0 = S.v[tv.x];
     const double d = n.x * p0.x + n.y * p0.y + n.z * p0.z;
     for (int j = 0; j < S.NL; ++j) {
         const LightDev& L = S.lights[j];
+        {
+            const float3 w = L.c - q0;
+            float lo32, hi32;
+            emitter_range<float>(L.type, dot(nf, w), dot(nf, L.e1), dot(nf, L.e2), lo32, hi32);
+            const float mag = na.x * (fabsf(w.x) + fabsf(L.e1.x) + fabsf(L.e2.x)) +
+                              na.y * (fabsf(w.y) + fabsf(L.e1.y) + fabsf(L.e2.y)) +
+                              na.z * (fabsf(w.z) + fabsf(L.e1.z) + fabsf(L.e2.z));
+            const float err = 64.0f * 5.9604645e-8f * mag;
+            uint8_t cls = 0;
+            if (lo32 > err) cls = 1;
+            else if (hi32 < -err) cls = 2;
+            else if (lo32 < -err && hi32 > err) cls = 3;
+            if (cls) {
+                it.sil_flags[(size_t)(1 + FR_MAX_LIGHTS) * S.E + (size_t)j * S.T + f] = cls;
+                continue;
+            }
+        }
         const double base = n.x * L.c.x + n.y * L.c.y + n.z * L.c.z - d;
         const double g1 = n.x * L.e1.x + n.y * L.e1.y + n.z * L.e1.z;
         const double g2 = n.x * L.e2.x + n.y * L.e2.y + n.z * L.e2.z;
         double lo, hi;
-        if (L.type == 0) {
-            const double h = 0.5 * fabs(g1) + 0.5 * fabs(g2);
-            lo = base - h; hi = base + h;
-        } else if (L.type == 1) {
-            lo = base + fmin(0.0, fmin(g1, g2)); hi = base + fmax(0.0, fmax(g1, g2));
-        } else {
-            const double r = sqrt(g1 * g1 + g2 * g2);
-            lo = base - r; hi = base + r;
-        }
+        emitter_range<double>(L.type, base, g1, g2, lo, hi);
         it.sil_flags[(size_t)(1 + FR_MAX_LIGHTS) * S.E + (size_t)j * S.T + f] = lo > 0.0 ? 1 : (hi < 0.0 ? 2 : 3);
     }
 }
@@ -897,7 +939,8 @@ void set_carveout() {
     static bool done = false;
     if (done || FR_CARVEOUT < 0) return;
     cudaFuncSetAttribute(k_forward, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
-    cudaFuncSetAttribute(k_adjoint, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
+    cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
+    cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
     cudaFuncSetAttribute(k_edge_primary, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
     done = true;
 }
@@ -909,10 +952,13 @@ void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) 
     fr_count_launches(1);
 }
 
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, cudaStream_t st) {
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
     const size_t acc_bytes = sizeof(double) * RT_WARPS * (1 + 3 * (size_t)NL);
-    k_adjoint<<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+    if (all_recorded)
+        k_adjoint<true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+    else
+        k_adjoint<false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
     fr_count_launches(1);
 }
 
