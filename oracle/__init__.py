@@ -43,12 +43,12 @@ class OraScene(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("spp", ctypes.c_int32), ("tex_size", ctypes.c_int32),
                 ("edge_spp", ctypes.c_int32), ("seed", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("n_threads", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("n_threads", ctypes.c_int32), ("stage", f32p)]
 
 
 class OraParams(ctypes.Structure):
     _fields_ = [(n, f32p) for n in ("coef", "rot", "trans", "focal", "light_i",
-                                    "diffuse", "specular", "roughness")]
+                                    "diffuse", "specular", "roughness", "light_d", "light_a", "light_p")]
 
 
 def build(force: bool = False) -> str:
@@ -83,13 +83,13 @@ def lib():
         L.ora_loss.argtypes = [ctypes.c_int32, ctypes.c_int32, f64p, f32p, f64p, f64p]
         L.ora_loss.restype = ctypes.c_double
         L.ora_grad.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams),
-                               ctypes.c_uint32, ctypes.c_uint32, f64p, ctypes.c_uint32] + [f64p] * 8
+                               ctypes.c_uint32, ctypes.c_uint32, f64p, ctypes.c_uint32] + [f64p] * 9
         L.ora_brdf.argtypes = [ctypes.c_uint32, f64p, f64p, f64p, f64p, f64p, ctypes.c_double, f64p]
         L.ora_brdf.restype = ctypes.c_double
         L.ora_brdf_terms.argtypes = [ctypes.c_uint32, f64p, f64p, f64p, ctypes.c_double, f64p]
         L.ora_point_light_grad.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams),
                                            f64p, f64p, ctypes.c_int32, ctypes.c_int32,
-                                           ctypes.c_uint32, f64p, f64p]
+                                           ctypes.c_uint32, f64p, f64p, f64p]
         _lib = L
     return _lib
 
@@ -119,12 +119,17 @@ class _Bound:
             scene.n_vertices, scene.n_triangles, scene.n_basis, f(scene.mean),
             f(scene.basis), faces.ctypes.data_as(i32p), f(scene.uv), scene.n_lights,
             f(scene.lights), f(scene.light_d), f(scene.light_a), scene.width, scene.height,
-            scene.spp, scene.tex_size, edge_spp, seed, flags, n_threads)
+            scene.spp, scene.tex_size, edge_spp, seed, flags, n_threads,
+            f(scene.stage) if getattr(scene, "stage", None) is not None else None)
         self.params = None
         if params is not None:
+            def opt(name):
+                x = getattr(params, name, None)
+                return f(x) if x is not None else None
             self.params = OraParams(f(params.coef), f(params.rot), f(params.trans),
                                     f(params.focal), f(params.light_i), f(params.diffuse),
-                                    f(params.specular), f(params.roughness))
+                                    f(params.specular), f(params.roughness), opt("light_d"), opt("light_a"),
+                                    opt("light_p"))
 
 
 def ray_count(reset=False):
@@ -217,10 +222,15 @@ def grad(scene, params, adjoint, iteration=0, face_id=0, terms=TERM_ALL, flags=0
              focal=np.zeros(1), light_i=np.zeros((scene.n_lights, 3)),
              diffuse=np.zeros((m, m, 3)), specular=np.zeros((m, m, 3)),
              roughness=np.zeros((m, m)))
+    geom = getattr(scene, "stage", None) is not None and getattr(params, "light_d", None) is not None
+    lg = np.zeros((scene.n_lights, 4))
     rc = lib().ora_grad(ctypes.byref(b.scene), ctypes.byref(b.params), iteration, face_id,
                         _p(adj, f64p), terms, *[_p(g[k], f64p) for k in
                                                 ("coef", "rot", "trans", "focal", "light_i",
-                                                 "diffuse", "specular", "roughness")])
+                                                 "diffuse", "specular", "roughness")],
+                        _p(lg, f64p) if geom else None)
+    if geom:   # d/d(d_j, a_j, p_j0, p_j1) of the virtual light stage
+        g["light_d"], g["light_a"], g["light_p"] = lg[:, 0].copy(), lg[:, 1].copy(), lg[:, 2:].copy()
     if rc != 0:
         raise ValueError("oracle gradient: unsupported sizes")
     return g
@@ -250,7 +260,11 @@ def point_light_grad(scene, params, y, n, n_samples, tri_self=-1, stream=7, seed
     n = np.ascontiguousarray(n, np.float64)
     val = np.zeros(3)
     g = np.zeros(scene.n_basis)
+    lg = np.zeros((scene.n_lights, 4))
+    geom = getattr(scene, "stage", None) is not None and getattr(params, "light_d", None) is not None
     lib().ora_point_light_grad(ctypes.byref(b.scene), ctypes.byref(b.params), _p(y, f64p),
                                _p(n, f64p), tri_self, n_samples, stream, _p(val, f64p),
-                               _p(g, f64p))
+                               _p(g, f64p), _p(lg, f64p) if geom else None)
+    if geom:   # channel-0 derivatives w.r.t. each light's (d, a, p0, p1)
+        return val, g, lg
     return val, g

@@ -88,7 +88,7 @@ enum { STREAM_PRIMARY = 0, STREAM_EDGE_PRIMARY = 1, STREAM_EDGE_SHADOW = 2 };
 // ---------------------------------------------------------------------------
 // Forward-mode dual numbers: value plus derivatives w.r.t. the active slots.
 // ---------------------------------------------------------------------------
-constexpr int DMAX = 176;
+constexpr int DMAX = 256;
 thread_local int g_nd = 0;  // active derivative slots on this thread (0: values only)
 
 struct D {
@@ -166,6 +166,10 @@ struct Light {
     P3 c, e1, e2, n;   // n = unit normal of the emitting side
     double area;
     double scale;      // d^2 / a of Eq. (lightIntensity)
+    // virtual light stage (Sec. 3.3): geometry built from (d, a, p) as duals
+    bool geo = false;
+    V3 cd, e1d, e2d;   // c, e1, e2 with derivatives on the light's slots
+    D aread, scaled;   // area and d^2 / a likewise
 };
 
 struct Edge { int a, b, f1, f2; };  // a < b; f2 = -1 on the boundary
@@ -176,6 +180,7 @@ struct Prep {
     int N, T, K, NL, W, H, M, spp;
     int nd;                    // active dual slots (0: values only)
     int slot_rot, slot_trans, slot_focal, slot_c, slot_s, slot_r, slot_t;
+    int slot_light;            // light j's (d, a, p0, p1) at slot_light + 4 j (-1: fixed lights)
     std::vector<P3> v;         // camera-space vertices
     std::vector<P3> vn;        // unit vertex normals
     std::vector<double> dv;    // [N][3][nd] derivatives of v (when nd > 0)
@@ -275,6 +280,56 @@ int threads_of(const OraScene* s) {
     return std::max(1, n);
 }
 
+bool stage_lights(const OraScene* s, const OraParams* p) {
+    return s->stage && p && p->light_d && p->light_a && p->light_p;
+}
+
+// Light j of the virtual light stage (Sec. 3.3) from its parameters: the face
+// (V0, V1, V2) of the unit polyhedron scaled by d_j about the stage centre C,
+// shrunk by sqrt(a_j) about the point with barycentric coordinates
+// (p0, p1, 1 - p0 - p1), parallel to the face, emitting towards C: vertices
+// P + s (V0 - G), P + s (V2 - G), P + s (V1 - G) with G the face centroid,
+// P = C + d (p0 V0 + p1 V1 + p2 V2), s = sqrt(a) d; area a d^2 F (F the unit
+// face area) and L_j = (d^2 / a) i_j.  Derivatives ride on the light's slots.
+void build_stage_light(Prep& P, int j) {
+    const float* g = P.s->stage + 12 * j;
+    const int b = P.slot_light + 4 * j;
+    D d = seed_slot(P.p->light_d[j], b), a = seed_slot(P.p->light_a[j], b + 1);
+    D p0 = seed_slot(P.p->light_p[2 * j], b + 2), p1 = seed_slot(P.p->light_p[2 * j + 1], b + 3);
+    D p2 = 1.0 - p0 - p1;
+    V3 C = v3c(g[0], g[1], g[2]);
+    V3 A = v3c(g[3], g[4], g[5]), B = v3c(g[6], g[7], g[8]), Cv = v3c(g[9], g[10], g[11]);
+    V3 G = (A + B + Cv) * (1.0 / 3.0);
+    V3 Pc = C + (A * p0 + B * p1 + Cv * p2) * d;
+    D sz = dsqrt(a) * d;
+    V3 t0 = Pc + (A - G) * sz, t1 = Pc + (Cv - G) * sz, t2 = Pc + (B - G) * sz;
+    Light L;
+    L.type = 1;
+    L.geo = true;
+    L.cd = t0;
+    L.e1d = t1 - t0;
+    L.e2d = t2 - t0;
+    L.c = val(L.cd);
+    L.e1 = val(L.e1d);
+    L.e2 = val(L.e2d);
+    P3 cr = crossp(L.e1, L.e2);
+    double cl = normp(cr);
+    L.n = cr * (1.0 / cl);                       // independent of (d, a, p)
+    V3 crd = cross(L.e1d, L.e2d);
+    L.aread = norm(crd) * 0.5;
+    L.area = L.aread.v;
+    L.scaled = d * d / a;
+    L.scale = L.scaled.v;
+    P.lights[j] = L;
+}
+
+// Emitter sample of a stage light with its derivatives (triangle mapping of
+// light_point).
+V3 light_point_d(const Light& L, double u, double v) {
+    double su = std::sqrt(u);
+    return L.cd + L.e1d * (su * (1.0 - v)) + L.e2d * (su * v);
+}
+
 void prepare(Prep& P, const OraScene* s, const OraParams* p, int nd) {
     P.s = s; P.p = p;
     P.N = s->n_vertices; P.T = s->n_triangles; P.K = s->n_basis; P.NL = s->n_lights;
@@ -282,6 +337,7 @@ void prepare(Prep& P, const OraScene* s, const OraParams* p, int nd) {
     P.nd = nd;
     P.slot_rot = P.K; P.slot_trans = P.K + 3; P.slot_focal = P.K + 6;
     P.slot_c = P.K + 7; P.slot_s = P.K + 10; P.slot_r = P.K + 13; P.slot_t = P.K + 14;
+    P.slot_light = stage_lights(s, p) ? P.K + 15 : -1;
     g_nd = nd;
     P.focal = p->focal[0];
     P.v.assign(P.N, P3{0, 0, 0});
@@ -309,6 +365,10 @@ void prepare(Prep& P, const OraScene* s, const OraParams* p, int nd) {
     parallel_for(nt, P.N, [&](int i, int) { store(P.vn, P.dn, nd, i, normalize(load(acc, dacc, nd, i))); });
     // lights
     P.lights.resize(P.NL);
+    if (stage_lights(s, p)) {
+        for (int j = 0; j < P.NL; ++j) build_stage_light(P, j);
+        return;
+    }
     for (int j = 0; j < P.NL; ++j) {
         const float* r = s->lights + 11 * j;
         Light L;
@@ -624,8 +684,16 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
     if (!(dot(ns, o).v > 0.0)) return;
     for (int j = 0; j < P.NL; ++j) {
         const Light& Lj = P.lights[j];
-        P3 z = light_point(Lj, st.u(light_dim0 + 2 * j), st.u(light_dim0 + 2 * j + 1));
-        V3 lv = v3c(z.x, z.y, z.z) - y;
+        const double uu = st.u(light_dim0 + 2 * j), vv = st.u(light_dim0 + 2 * j + 1);
+        V3 zd;
+        if (Lj.geo) {
+            zd = light_point_d(Lj, uu, vv);
+        } else {
+            P3 zp = light_point(Lj, uu, vv);
+            zd = v3c(zp.x, zp.y, zp.z);
+        }
+        P3 z = val(zd);
+        V3 lv = zd - y;
         D dist2 = dot(lv, lv);
         V3 l = lv * (1.0 / dsqrt(dist2));
         D cos_s = dot(ns, l);
@@ -638,11 +706,15 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
         out.mask[j >> 6] |= (1ull << (j & 63));
         D f[3];
         brdf(s->flags, ns, l, o, c, sp, r, f);
-        D geo = cos_s * cos_l / dist2 * Lj.area;
+        D geo = Lj.geo ? cos_s * cos_l / dist2 * Lj.aread : cos_s * cos_l / dist2 * Lj.area;
         for (int k = 0; k < 3; ++k) {
-            double I = Lj.scale * (double)P.p->light_i[3 * j + k];   // Eq. lightIntensity
             D term = f[k] * geo;
-            out.L[k] = out.L[k] + term * I;
+            if (Lj.geo) {
+                out.L[k] = out.L[k] + term * Lj.scaled * (double)P.p->light_i[3 * j + k];   // Eq. lightIntensity
+            } else {
+                double I = Lj.scale * (double)P.p->light_i[3 * j + k];
+                out.L[k] = out.L[k] + term * I;
+            }
             if (j < ORA_MAX_LIGHTS) out.dLdi[j][k] = term.v * Lj.scale;
         }
     }
@@ -689,7 +761,8 @@ void accumulate_geo(const Prep& P, const D& x, double w, double* g) {
 // of sum_j int h_k V dA via geometric slots in g.  Boundary curve = projection
 // from y of an occluder edge onto the emitter plane.
 void shadow_edge_sample(const Prep& P, const SampleOut& so, int tri_self, double u_light,
-                        double u_edge, double u_t, const double adj[3], double* g, bool* hit_out = nullptr) {
+                        double u_edge, double u_t, const double adj[3], double* g, bool* hit_out = nullptr,
+                        double* g_light = nullptr) {
     if (hit_out) *hit_out = false;
     int j = std::min((int)(u_light * P.NL), P.NL - 1);
     const std::vector<int>& cand = P.light_cand[j];
@@ -715,7 +788,7 @@ void shadow_edge_sample(const Prep& P, const SampleOut& so, int tri_self, double
     D tt = seed_slot(u_t, P.slot_t);
     V3 pe = A + (B - A) * tt;
     V3 nL = v3c(L.n.x, L.n.y, L.n.z);
-    V3 cL = v3c(L.c.x, L.c.y, L.c.z);
+    V3 cL = L.geo ? L.cd : v3c(L.c.x, L.c.y, L.c.z);   // a moving plane moves the boundary point
     D den = dot(pe - so.yd, nL);
     D num = dot(cL - so.yd, nL);
     if (den.v == 0.0) return;
@@ -739,6 +812,27 @@ void shadow_edge_sample(const Prep& P, const SampleOut& so, int tri_self, double
     if (hit_out) *hit_out = true;
     double scale = -dV * (double)P.NL * (double)S * tl;
     D vn = z.x * m.x + z.y * m.y + z.z * m.z;    // normal velocity of the boundary point
+    if (L.geo && g_light) {
+        // the emitter moves under the boundary: what counts is the boundary's
+        // velocity relative to the emitter's own points, so subtract the
+        // velocity of the emitter point at the boundary's emitter
+        // coordinates (z - c = al e1 + be e2), held fixed
+        P3 wv = zv - L.c;
+        double g11 = dotp(L.e1, L.e1), g12 = dotp(L.e1, L.e2), g22 = dotp(L.e2, L.e2);
+        double r1 = dotp(wv, L.e1), r2 = dotp(wv, L.e2), det = g11 * g22 - g12 * g12;
+        double al = (r1 * g22 - r2 * g12) / det, be = (r2 * g11 - r1 * g12) / det;
+        V3 zm = L.cd + L.e1d * al + L.e2d * be;
+        D vm = zm.x * m.x + zm.y * m.y + zm.z * m.z;
+        D rel = vn - vm;
+        for (int k = 0; k < 3; ++k) {
+            double I = L.scale * (double)P.p->light_i[3 * j + k];
+            double w = adj[k] * scale * h[k].v * I;
+            if (w == 0.0) continue;
+            accumulate_geo(P, vn, w, g);
+            for (int q = 0; q < 4 * P.NL; ++q) g_light[q] += w * rel.d[P.slot_light + q];
+        }
+        return;
+    }
     for (int k = 0; k < 3; ++k) {
         double I = L.scale * (double)P.p->light_i[3 * j + k];
         double w = adj[k] * scale * h[k].v * I;
@@ -905,20 +999,22 @@ double ora_loss(int32_t H, int32_t W, const double* image, const float* target, 
 int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t face_id,
              const double* adjoint, uint32_t terms, double* g_coef, double* g_rot, double* g_trans,
              double* g_focal, double* g_light, double* g_diffuse, double* g_specular,
-             double* g_roughness) {
-    if (s->n_basis + 15 > DMAX || s->n_lights > ORA_MAX_LIGHTS) return -1;
+             double* g_roughness, double* g_light_geom) {
+    const int n_lg = stage_lights(s, p) ? 4 * s->n_lights : 0;
+    if (s->n_basis + 15 + n_lg > DMAX || s->n_lights > ORA_MAX_LIGHTS) return -1;
     Prep P;
-    prepare(P, s, p, s->n_basis + 15);
+    prepare(P, s, p, s->n_basis + 15 + n_lg);
     classify(P);
     int nt = threads_of(s);
     int ngeo = P.slot_c;
     size_t MM = (size_t)P.M * P.M;
     struct Acc {
-        std::vector<double> geo, light, dif, spec, rough;
+        std::vector<double> geo, light, dif, spec, rough, lg;
     };
     std::vector<Acc> acc(nt);
     for (auto& a : acc) {
         a.geo.assign(ngeo, 0.0);
+        a.lg.assign((size_t)std::max(n_lg, 1), 0.0);
         a.light.assign((size_t)P.NL * 3, 0.0);
         a.dif.assign(MM * 3, 0.0);
         a.spec.assign(MM * 3, 0.0);
@@ -952,6 +1048,8 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
                 double w[3] = {adj[0] / P.spp, adj[1] / P.spp, adj[2] / P.spp};
                 if (terms & ORA_TERM_INTERIOR) {
                     for (int k = 0; k < 3; ++k) accumulate_geo(P, so.L[k], w[k], A.geo.data());
+                    for (int q = 0; q < n_lg; ++q)
+                        for (int k = 0; k < 3; ++k) A.lg[q] += w[k] * so.L[k].d[P.slot_light + q];
                     double dr = 0.0;
                     for (int k = 0; k < 3; ++k) dr += w[k] * so.L[k].d[P.slot_r];
                     for (int q = 0; q < 4; ++q) {
@@ -968,7 +1066,8 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
                 }
                 if ((terms & ORA_TERM_SHADOW) && !(s->flags & ORA_FLAT)) {
                     Stream se{s->seed, STREAM_EDGE_SHADOW, (uint32_t)pix, (uint32_t)smp, iteration, face_id};
-                    shadow_edge_sample(P, so, so.tri, se.u(0), se.u(1), se.u(2), w, A.geo.data());
+                    shadow_edge_sample(P, so, so.tri, se.u(0), se.u(1), se.u(2), w, A.geo.data(), nullptr,
+                                       n_lg ? A.lg.data() : nullptr);
                 }
             }
         });
@@ -1031,6 +1130,11 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
     }
     if (g_focal) g_focal[0] = geo[P.slot_focal];
     if (g_light) std::copy(light.begin(), light.end(), g_light);
+    if (g_light_geom && n_lg) {
+        std::fill(g_light_geom, g_light_geom + n_lg, 0.0);
+        for (auto& a : acc)
+            for (int q = 0; q < n_lg; ++q) g_light_geom[q] += a.lg[q];
+    }
     if (g_diffuse) { std::fill(g_diffuse, g_diffuse + MM * 3, 0.0); for (auto& a : acc) for (size_t q = 0; q < MM * 3; ++q) g_diffuse[q] += a.dif[q]; }
     if (g_specular) { std::fill(g_specular, g_specular + MM * 3, 0.0); for (auto& a : acc) for (size_t q = 0; q < MM * 3; ++q) g_specular[q] += a.spec[q]; }
     if (g_roughness) { std::fill(g_roughness, g_roughness + MM, 0.0); for (auto& a : acc) for (size_t q = 0; q < MM; ++q) g_roughness[q] += a.rough[q]; }
@@ -1081,15 +1185,18 @@ void ora_brdf_terms(uint32_t flags, const double* n, const double* l, const doub
 // samples.  Used to pin the shadow-edge estimator against closed forms.
 int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y, const double* n,
                          int32_t tri_self, int32_t n_samples, uint32_t seed_stream, double* value_rgb,
-                         double* g_coef) {
+                         double* g_coef, double* g_light_geom) {
     OraScene sc = *s;
     sc.flags = ORA_DIFFUSE_ONLY;
+    const int n_lg = stage_lights(s, p) ? 4 * s->n_lights : 0;
+    if (s->n_basis + 15 + n_lg > DMAX) return -1;
     Prep P;
-    prepare(P, &sc, p, s->n_basis + 15);
+    prepare(P, &sc, p, s->n_basis + 15 + n_lg);
     classify(P);
     int nt = threads_of(s);
     std::vector<std::vector<double>> gs(nt, std::vector<double>(P.slot_c, 0.0));
     std::vector<std::vector<double>> vs(nt, std::vector<double>(3, 0.0));
+    std::vector<std::vector<double>> gl(nt, std::vector<double>((size_t)std::max(n_lg, 1), 0.0));
     const D zero3[3] = {D(0.0), D(0.0), D(0.0)};
     parallel_for(nt, n_samples, [&](int i, int th) {
         SampleOut so;
@@ -1104,6 +1211,19 @@ int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
         // interior estimate: one area sample per light
         for (int j = 0; j < P.NL; ++j) {
             const Light& L = P.lights[j];
+            if (L.geo) {            // with derivatives on the light's (d, a, p), channel 0
+                V3 zd = light_point_d(L, st.u(4 + 2 * j), st.u(5 + 2 * j));
+                V3 lvd = zd - so.yd;
+                D d2 = dot(lvd, lvd);
+                V3 l = lvd * (1.0 / dsqrt(d2));
+                D cs = dot(so.ns, l), cl = -dot(v3c(L.n.x, L.n.y, L.n.z), l);
+                if (cs.v <= 0.0 || cl.v <= 0.0) continue;
+                if (occluded(P, so.y, val(zd), tri_self)) continue;
+                D g = L.scaled * cs * cl / d2 * L.aread * (1.0 / M_PI);
+                for (int k = 0; k < 3; ++k) vs[th][k] += g.v * p->light_i[3 * j + k];
+                for (int q = 0; q < n_lg; ++q) gl[th][q] += g.d[P.slot_light + q] * p->light_i[3 * j];
+                continue;
+            }
             P3 z = light_point(L, st.u(4 + 2 * j), st.u(5 + 2 * j));
             P3 lv = z - so.y;
             double d2 = dotp(lv, lv);
@@ -1116,7 +1236,8 @@ int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
         }
         double w[3] = {1.0, 0.0, 0.0};
         // light_integrand uses brdf() in diffuse-only mode: white Lambertian
-        shadow_edge_sample(P, so, tri_self, st.u(0), st.u(1), st.u(2), w, gs[th].data());
+        shadow_edge_sample(P, so, tri_self, st.u(0), st.u(1), st.u(2), w, gs[th].data(), nullptr,
+                           n_lg ? gl[th].data() : nullptr);
     });
     for (int k = 0; k < 3; ++k) {
         double a = 0.0;
@@ -1128,6 +1249,12 @@ int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
         for (int t = 0; t < nt; ++t) a += gs[t][k];
         g_coef[k] = a / n_samples;
     }
+    if (g_light_geom)
+        for (int q = 0; q < n_lg; ++q) {
+            double a = 0.0;
+            for (int t = 0; t < nt; ++t) a += gl[t][q];
+            g_light_geom[q] = a / n_samples;
+        }
     g_nd = 0;
     return 0;
 }

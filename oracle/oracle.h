@@ -39,10 +39,17 @@ typedef struct OraScene {
     int32_t width, height, spp, tex_size, edge_spp;
     uint32_t seed, flags;
     int32_t n_threads;
+    /* optional virtual light stage (Sec. 3.3), [N_L][12]: stage centre, then the
+     * unit-scale face vertices V0, V1, V2 of light j's polyhedron face; with
+     * OraParams light_d/a/p the emitters are built from them (triangles) */
+    const float* stage;
 } OraScene;
 
 typedef struct OraParams {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+    /* optional light geometry of a stage scene: distance d_j [N_L], relative
+     * area a_j [N_L], barycentric centre (p_j0, p_j1) [N_L][2] (p_j2 = 1 - both) */
+    const float *light_d, *light_a, *light_p;
 } OraParams;
 
 /* rays traced by this library since the last reset (closest-hit + shadow) */
@@ -71,7 +78,7 @@ double ora_loss(int32_t height, int32_t width, const double* image, const float*
 int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t face_id,
              const double* adjoint, uint32_t terms, double* g_coef, double* g_rot,
              double* g_trans, double* g_focal, double* g_light, double* g_diffuse,
-             double* g_specular, double* g_roughness);
+             double* g_specular, double* g_roughness, double* g_light_geom /* [N_L][4] or NULL */);
 
 double ora_brdf(uint32_t flags, const double* n, const double* l, const double* o,
                 const double* c, const double* s, double r, double* out_rgb);
@@ -81,7 +88,8 @@ void ora_brdf_terms(uint32_t flags, const double* n, const double* l, const doub
 
 int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
                          const double* n, int32_t tri_self, int32_t n_samples,
-                         uint32_t seed_stream, double* value_rgb, double* g_coef);
+                         uint32_t seed_stream, double* value_rgb, double* g_coef,
+                         double* g_light_geom /* [N_L][4] channel 0, or NULL */);
 
 #ifdef __cplusplus
 }

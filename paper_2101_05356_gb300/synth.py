@@ -74,6 +74,7 @@ class Scene:
     fov_deg: float
     albedo: AlbedoModel | None = None
     landmarks: np.ndarray | None = None   # int32 [L] landmark vertex indices (Eq. landmark)
+    stage: np.ndarray | None = None       # float32 [N_L, 12] polyhedral stage: centre, face V0, V1, V2
 
     @property
     def n_vertices(self) -> int:
@@ -107,9 +108,13 @@ class Params:
     diffuse: np.ndarray     # float32 [M, M, 3]
     specular: np.ndarray    # float32 [M, M, 3]
     roughness: np.ndarray   # float32 [M, M]
+    # virtual light stage geometry (Sec. 3.3), for scenes with a polyhedral stage
+    light_d: np.ndarray | None = None   # float32 [N_L]    distance d_j
+    light_a: np.ndarray | None = None   # float32 [N_L]    relative area a_j
+    light_p: np.ndarray | None = None   # float32 [N_L, 2] barycentric centre (p_j0, p_j1)
 
     def copy(self) -> "Params":
-        return Params(**{f.name: getattr(self, f.name).copy()
+        return Params(**{f.name: (None if getattr(self, f.name) is None else getattr(self, f.name).copy())
                          for f in dataclasses.fields(self)})
 
     def as_dict(self) -> dict:
@@ -424,7 +429,8 @@ def polyhedral_stage(name="ico", d=3.0, a=0.25, p=None, centre=STAGE_CENTRE):
     the stage centre, is that face shrunk by sqrt(a_j) (a_j = relative area in
     [0, 1]) around the point with barycentric coordinates p_j (default the
     centroid), stays parallel to the face and emits towards the centre.
-    Returns (records [N_L, 11] of type LIGHT_TRI, d [N_L], a [N_L])."""
+    Returns (records [N_L, 11] of type LIGHT_TRI, d [N_L], a [N_L]); see
+    polyhedral_stage_geometry for the per-light face data the parameters act on."""
     v, f = _polyhedron(name)
     n = f.shape[0]
     d = np.broadcast_to(np.asarray(d, np.float64), (n,))
@@ -444,6 +450,17 @@ def polyhedral_stage(name="ico", d=3.0, a=0.25, p=None, centre=STAGE_CENTRE):
         rec[j, 4:7] = t1 - t0
         rec[j, 7:10] = t2 - t0
     return rec, d.astype(np.float32).copy(), a.astype(np.float32).copy()
+
+
+def polyhedral_stage_geometry(name="ico", centre=STAGE_CENTRE):
+    """[N_L, 12] per light: the stage centre C and the unit-circumradius face
+    vertices V0, V1, V2 of its polyhedron face (the frame d_j, a_j and p_j act
+    in; see polyhedral_stage)."""
+    v, f = _polyhedron(name)
+    out = np.zeros((f.shape[0], 12), np.float32)
+    out[:, 0:3] = centre
+    out[:, 3:6], out[:, 6:9], out[:, 9:12] = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    return out
 
 
 def smooth_field(rng, m, channels, sigma, lo, hi):
@@ -565,8 +582,10 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
     kind = over.get("light_kind", LIGHT_QUAD)
     side = over.get("light_side", 0.5 if kind != LIGHT_DISK else 1.0)
     stage = over.get("light_stage")
+    stage_geo = None
     if stage is not None:                 # polyhedral stage: "tetra", "octa", "ico", "sphere80"
         lights, light_d, light_a = polyhedral_stage(stage, 3.0, over.get("light_area", 0.25))
+        stage_geo = polyhedral_stage_geometry(stage)
         nl = lights.shape[0]
     else:
         lights = light_stage(nl, 3.0, side, hemi, STAGE_CENTRE, kind)
@@ -577,7 +596,7 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
                  faces=np.ascontiguousarray(faces.astype(np.int32)), uv=_f32(uv),
                  lights=lights, light_d=light_d, light_a=light_a, width=int(w), height=int(h),
                  spp=int(spp), tex_size=int(m), fov_deg=30.0, albedo=albedo,
-                 landmarks=landmark_vertices(mean))
+                 landmarks=landmark_vertices(mean), stage=stage_geo)
 
 
 def init_params(scene: Scene, seed: int = 0) -> Params:
@@ -610,6 +629,27 @@ def random_params(scene: Scene, seed: int = 0, coef_scale: float = 1.0) -> Param
                   focal=_f32([scene.focal_px()]),
                   light_i=_f32(rng.uniform(0.2, 1.5, size=(scene.n_lights, 3))),
                   diffuse=diffuse, specular=specular, roughness=roughness)
+
+
+def with_stage_geometry(scene: Scene, params: Params, seed: int | None = None) -> Params:
+    """A copy of params whose lights are built from the virtual light stage's
+    parameters (d_j, a_j, p_j): the stage defaults (d 3, a 0.25, centroid), or
+    a seeded perturbation of them (d 3 +- 0.3, a in [0.15, 0.45], p inside the
+    face)."""
+    if scene.stage is None:
+        raise ValueError("scene has no polyhedral light stage")
+    q = params.copy()
+    n = scene.n_lights
+    if seed is None:
+        q.light_d = np.full(n, 3.0, np.float32)
+        q.light_a = np.full(n, 0.25, np.float32)
+        q.light_p = np.full((n, 2), 1.0 / 3.0, np.float32)
+    else:
+        rng = np.random.default_rng(seed + 91)
+        q.light_d = _f32(3.0 + rng.uniform(-0.3, 0.3, n))
+        q.light_a = _f32(rng.uniform(0.15, 0.45, n))
+        q.light_p = _f32(rng.dirichlet([6.0, 6.0, 6.0], size=n)[:, :2])
+    return q
 
 
 def pixel_noise(rng_seed: int, shape, sigma: float = 0.01) -> np.ndarray:
