@@ -110,15 +110,28 @@ typedef struct fr_light_stage {
     const float* records;
     const float* d;
     const float* a;
+    /* optional (NULL: the records are the lights): the virtual light stage of
+     * Sec. 3.3, [N_L][12] per light: stage centre C, then the unit-scale face
+     * V0, V1, V2 of its polyhedron face (counter-clockwise seen from outside).
+     * A call whose fr_params carries light_d, light_a and light_p builds light
+     * j from them instead of the record: the face scaled by d_j about C,
+     * shrunk by sqrt(a_j) about the point p0 V0 + p1 V1 + (1 - p0 - p1) V2
+     * (scaled), parallel to the face, emitting towards C, with emitted radiance
+     * (d_j^2 / a_j) i_j; the gradients then include d/d(d_j, a_j, p_j)
+     * (interior and moving-emitter shadow-boundary terms). */
+    const float* stage;
 } fr_light_stage;
 
 /* Parameters chi-hat of Sec. 4 (device pointers, float32):
  *   coef [K] (alpha then delta), rot [3] Euler angles with R = Rz Ry Rx,
  *   trans [3] T (pose v' = R^T (v - T), Sec. 3.1), focal [1] in pixels,
  *   light_i [N_L][3] perceived intensities i_j, diffuse [M][M][3],
- *   specular [M][M][3], roughness [M][M]. */
+ *   specular [M][M][3], roughness [M][M]; optionally (all three or none, with
+ *   a stage set by fr_set_lights) the light geometry light_d [N_L],
+ *   light_a [N_L] in (0, 1], light_p [N_L][2] (barycentric p0, p1). */
 typedef struct fr_params {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+    const float *light_d, *light_a, *light_p;
 } fr_params;
 
 /* Gradients, same shapes as fr_params (device pointers).  Every call ADDS
@@ -126,6 +139,7 @@ typedef struct fr_params {
  * output (the work is still done). */
 typedef struct fr_grads {
     float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+    float *light_d, *light_a, *light_p;
 } fr_grads;
 
 /* Create a context for one image configuration.  Allocates the image-sized

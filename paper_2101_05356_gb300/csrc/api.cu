@@ -40,6 +40,7 @@ struct Slot {
     double* pose_part = nullptr;
     float* sign = nullptr;
     float* adj_image = nullptr;
+    LightDev* lights = nullptr;      // lights built from stage parameters [FR_MAX_LIGHTS]
     int* edge_perm = nullptr;        // primary-edge sample order [edge_cap]
     long edge_cap = 0;
     int32_t* rec_tri = nullptr;      // fused-step hit records (null when over FR_RECORDS_BUDGET)
@@ -81,6 +82,7 @@ struct fr_ctx {
     int* vf_idx = nullptr;
     int4* edges = nullptr;
     LightDev* lights = nullptr;
+    float* stage = nullptr;                    // virtual light stage frame [N_L][12] (null: records only)
     std::vector<Slot> slots;
     DevItem* d_items = nullptr;                // device item table [FR_MAX_BATCH]
     std::vector<DevItem> h_items;
@@ -174,7 +176,13 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     s.v = sl.v_cam; s.vn = sl.vn; s.uv = c->uv; s.faces = c->faces; s.nodes = sl.nodes; s.tris = sl.tris;
     s.lights = c->lights; s.status = c->status; s.counters = c->counters;
     const fr_params* p = a.p;
-    it.P = DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness};
+    it.P = DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness,
+                     p->light_d, p->light_a, p->light_p};
+    if (c->stage && p->light_d && p->light_a && p->light_p) {   // lights built from (d, a, p)
+        s.stage = c->stage;
+        s.lights = sl.lights;
+        it.lights_w = sl.lights;
+    }
     it.G.d_v = sl.d_v;
     it.G.d_n = sl.d_n;
     it.G.tex = sl.tex;
@@ -188,6 +196,9 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
         it.g_trans = a.g->trans;
         it.g_focal = a.g->focal;
         it.g_light = a.g->light_i;
+        it.g_light_d = a.g->light_d;
+        it.g_light_a = a.g->light_a;
+        it.g_light_p = a.g->light_p;
     }
     it.EL.edges = c->edges;
     it.EL.prim_list = sl.lists;
@@ -322,8 +333,11 @@ fr_status upload_model(fr_ctx* c, LinearModel& m, int rows, int K, const float* 
     return FR_OK;
 }
 
-// morph -> pose -> face normals + Morton keys -> vertex normals -> LBVH
+// stage lights -> morph -> pose -> face normals + Morton keys -> vertex normals -> BVH
 void build_geometry(fr_ctx* c, int n, cudaStream_t st) {
+    bool any_stage = false;
+    for (int k = 0; k < n; ++k) any_stage |= c->h_items[k].S.stage != nullptr;
+    if (any_stage) launch_stage_lights(c->d_items, n, c->NL, st);
     morph(c, n, st);
     launch_pose(c->d_items, n, c->N, st);
     launch_faces(c->d_items, n, c->faces, c->T, st);
@@ -352,7 +366,9 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     mark(c, 4, st);
     bool all_recorded = true;
     for (int k = 0; k < n; ++k) all_recorded &= c->h_items[k].rec_tri != nullptr;
-    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_recorded, st);
+    bool any_stage = false;
+    for (int k = 0; k < n; ++k) any_stage |= c->h_items[k].S.stage != nullptr;
+    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_recorded, any_stage, st);
     mark(c, 5, st);
     long max_edge = 0;
     for (int k = 0; k < n; ++k) {
@@ -417,7 +433,8 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.d_n, 3 * (size_t)N));
     TRY(dalloc(c, &sl.tex, 7 * (size_t)c->cfg.tex_size * c->cfg.tex_size));
     TRY(dalloc(c, &sl.dm, 3 * (size_t)N));
-    TRY(dalloc(c, &sl.small, 1 + 3 * FR_MAX_LIGHTS));
+    TRY(dalloc(c, &sl.small, FR_SMALL));
+    TRY(dalloc(c, &sl.lights, FR_MAX_LIGHTS));
     TRY(dalloc(c, &sl.pose_part, 12 * (size_t)((N + 255) / 256)));
     // processing order of the primary-edge samples (the context's edge_spp, at least 1)
     sl.edge_cap = (long)c->cfg.width * c->cfg.height * std::max(c->cfg.edge_spp, 1);
@@ -695,6 +712,10 @@ fr_status fr_set_lights(fr_ctx* c, const fr_light_stage* ls) {
     }
     if (!c->lights) TRY(dalloc(c, &c->lights, FR_MAX_LIGHTS));
     CK(c, cudaMemcpy(c->lights, L.data(), sizeof(LightDev) * L.size(), cudaMemcpyHostToDevice));
+    if (ls->stage) {
+        if (!c->stage) TRY(dalloc(c, &c->stage, 12 * (size_t)FR_MAX_LIGHTS));
+        CK(c, cudaMemcpy(c->stage, ls->stage, sizeof(float) * 12 * ls->n_lights, cudaMemcpyHostToDevice));
+    }
     c->NL = ls->n_lights;
     c->have_lights = true;
     return FR_OK;

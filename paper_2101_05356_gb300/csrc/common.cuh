@@ -97,6 +97,8 @@ struct DevScene {
     const BvhNode* nodes;   // [max(T - 1, 1)]
     const float4* tris;     // [3T] triangles in BVH leaf order; tris[3s].w = id bits
     const LightDev* lights; // [NL]
+    const float* stage;     // [NL][12] virtual light stage frame (centre, unit face V0 V1 V2);
+                            // non-null when the lights are built from (d, a, p) parameters
     int* status;
     unsigned long long* counters;   // [3][3]: per kernel (forward, adjoint, primary edges) rays, nodes, triangle tests
 };
@@ -122,7 +124,13 @@ FR_D void flush_stats(unsigned long long* counters, const RayStats& rs) {
 
 struct DevParams {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
+    const float *light_d, *light_a, *light_p;   // light stage geometry [NL], [NL], [NL][2]
 };
+
+// Fixed-point accumulator layout of G.small: focal, then 3 per light
+// (intensity), then from FR_GEO_OFF 4 per light (d, a, p0, p1).
+constexpr int FR_GEO_OFF = 1 + 3 * FR_MAX_LIGHTS;
+constexpr int FR_SMALL = FR_GEO_OFF + 4 * FR_MAX_LIGHTS;
 
 // Gradient sums are kept in 64-bit fixed point (resolution 2^-32, range
 // +-2^31): integer addition is associative, so a sum does not depend on the
@@ -201,6 +209,8 @@ struct DevItem {
     uint64_t* rec_vis;      // [samples][2] visibility words, lights 0..63 and 64..127
     int* edge_perm;         // processing order of the primary-edge samples (null: index order)
     float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
+    float *g_light_d, *g_light_a, *g_light_p;            // light stage geometry gradients (may be null)
+    LightDev* lights_w;     // write side of S.lights when built from stage parameters
     uint32_t iteration, face;
 };
 

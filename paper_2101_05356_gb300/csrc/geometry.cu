@@ -42,7 +42,7 @@ __global__ void k_zero_acc(const DevItem* items, int N, int M) {
     if (i < 3L * N) { it.G.d_v[i] = 0ull; it.G.d_n[i] = 0ull; }
     if (i < 7L * M * M) it.G.tex[i] = 0ull;
     if (blockIdx.x == 0)
-        for (int k = threadIdx.x; k < 1 + 3 * FR_MAX_LIGHTS; k += blockDim.x) it.G.small[k] = 0ull;
+        for (int k = threadIdx.x; k < FR_SMALL; k += blockDim.x) it.G.small[k] = 0ull;
 }
 
 // add the fixed-point texture gradients into the caller's float gradients
@@ -275,6 +275,47 @@ __global__ void k_pose_finish(const DevItem* items, int NL, int n_blocks) {
     }
     if (it.g_light)
         for (int k = t; k < 3 * NL; k += blockDim.x) it.g_light[k] += (float)from_fix(small[1 + k]);
+    if (it.S.stage)
+        for (int k = t; k < 4 * NL; k += blockDim.x) {
+            const int j = k >> 2, q = k & 3;
+            const float g = (float)from_fix(small[FR_GEO_OFF + k]);
+            if (q == 0) { if (it.g_light_d) it.g_light_d[j] += g; }
+            else if (q == 1) { if (it.g_light_a) it.g_light_a[j] += g; }
+            else if (it.g_light_p) it.g_light_p[2 * j + q - 2] += g;
+        }
+}
+
+// Lights of the virtual light stage (Sec. 3.3) from each item's parameters:
+// light j is face j of the unit polyhedron (V0, V1, V2 about the stage centre
+// C) scaled by d_j, shrunk by sqrt(a_j) about P = C + d_j (p0 V0 + p1 V1 + p2
+// V2), p2 = 1 - p0 - p1, parallel to the face and emitting towards C: a
+// triangle with vertices P + s (V0 - G), P + s (V2 - G), P + s (V1 - G),
+// s = sqrt(a_j) d_j, G the face centroid; radiance scale d_j^2 / a_j.
+__global__ void k_stage_lights(const DevItem* items, int NL) {
+    const DevItem& it = items[blockIdx.y];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!it.S.stage || j >= NL) return;
+    const float* g = it.S.stage + 12 * j;
+    const float3 C = f3(g[0], g[1], g[2]), A = f3(g[3], g[4], g[5]), B = f3(g[6], g[7], g[8]);
+    const float3 V = f3(g[9], g[10], g[11]);
+    const float d = it.P.light_d[j], a = it.P.light_a[j];
+    const float p0 = it.P.light_p[2 * j], p1 = it.P.light_p[2 * j + 1], p2 = 1.0f - p0 - p1;
+    const float3 G = (A + B + V) * (1.0f / 3.0f);
+    const float3 P = C + (A * p0 + B * p1 + V * p2) * d;
+    const float s = sqrtf(a) * d;
+    const float3 t0 = P + (A - G) * s, t1 = P + (V - G) * s, t2 = P + (B - G) * s;
+    LightDev L;
+    L.type = 1;
+    L.pad = 0;
+    L.c = t0;
+    L.e1 = t1 - t0;
+    L.e2 = t2 - t0;
+    const float3 cr = cross(L.e1, L.e2);
+    const float cl = length(cr);
+    L.n = cr * (1.0f / cl);
+    L.area = 0.5f * cl;
+    L.scale = d * d / a;
+    it.lights_w[j] = L;
 }
 
 // dE/dcoef_k = sum_i basis[k][i] dE/dv_i, one block per (k, item), FP64 accumulation.
@@ -302,6 +343,11 @@ void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStr
 
 void launch_tex_flush(const DevItem* items, int n, int M, cudaStream_t st) {
     k_tex_flush<<<dim3(nb(7L * M * M, 256), n), 256, 0, st>>>(items, M);
+    fr_count_launches(1);
+}
+
+void launch_stage_lights(const DevItem* items, int n, int NL, cudaStream_t st) {
+    k_stage_lights<<<dim3(nb(NL, 128), n), 128, 0, st>>>(items, NL);
     fr_count_launches(1);
 }
 

@@ -14,6 +14,7 @@ void launch_set_items(const DevItem* host_items, int n, DevItem* dev_items, cuda
 void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStream_t st);
 void launch_tex_flush(const DevItem* items, int n, int M, cudaStream_t st);
 void launch_pose(const DevItem* items, int n, int N, cudaStream_t st);
+void launch_stage_lights(const DevItem* items, int n, int NL, cudaStream_t st);
 void launch_faces(const DevItem* items, int n, const int4* faces, int T, cudaStream_t st);
 void launch_vertex_normals(const DevItem* items, int n, const int* vf_off, const int* vf_idx, int N,
                            cudaStream_t st);
@@ -78,7 +79,8 @@ void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);
 
 // render.cu
 void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st);
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, cudaStream_t st);
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage,
+                    cudaStream_t st);
 void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st);
 void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);

@@ -191,7 +191,7 @@ FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sample
 // (dE/dh per channel) flows into g (n, o, c, s, r) and into gy.
 template <bool ADJ>
 FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleState& ss, float3 gh,
-                    ShadeAdj* g, float3* gy) {
+                    ShadeAdj* g, float3* gy, float3* gz = nullptr) {
     const float3 lv = z - ss.y;
     const float d2 = dot(lv, lv);
     const float inv_len = 1.0f / sqrtf(d2);
@@ -212,10 +212,34 @@ FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleSta
         g->l = keep_l;
         const float3 glv = (gl - l * dot(l, gl)) * inv_len + lv * (2.0f * gd2);
         *gy -= glv;
+        if (gz) *gz = glv;                     // lv = z - y
     } else {
         f = brdf<false>(flags, ss.ns, l, ss.o, ss.m, f3(0, 0, 0), nullptr);
     }
     return f * geo;
+}
+
+// Light j's frame in the virtual light stage and the velocities of an emitter
+// point z (held at its emitter coordinates) with respect to (d, a, p0, p1):
+// dz/dd = (z - C) / d, dz/da = (z - P) / (2 a), dz/dp0 = d (V0 - V2),
+// dz/dp1 = d (V1 - V2) (P = C + d (p0 V0 + p1 V1 + p2 V2), Sec. 3.3).
+struct StageFrame {
+    float3 C, P, dA, dB;    // stage centre, light centre, V0 - V2, V1 - V2
+    float d, a;
+};
+
+FR_D StageFrame stage_frame(const DevScene& S, const DevParams& P, int j) {
+    const float* g = S.stage + 12 * j;
+    StageFrame F;
+    F.C = f3(g[0], g[1], g[2]);
+    const float3 A = f3(g[3], g[4], g[5]), B = f3(g[6], g[7], g[8]), V = f3(g[9], g[10], g[11]);
+    F.d = P.light_d[j];
+    F.a = P.light_a[j];
+    const float p0 = P.light_p[2 * j], p1 = P.light_p[2 * j + 1];
+    F.P = F.C + (A * p0 + B * p1 + V * (1.0f - p0 - p1)) * F.d;
+    F.dA = A - V;
+    F.dB = B - V;
+    return F;
 }
 
 FR_D float3 intensity(const DevScene& S, const DevParams& P, int j) {
@@ -321,12 +345,13 @@ FR_D void block_acc_init(int n) {
     __syncthreads();
 }
 
-// per-warp partials summed in warp order, then one fixed-point add per value
-FR_D void block_acc_flush(int n, fix64* out) {
+// per-warp partials [from, from + count) of rows of n_acc, summed in warp
+// order, then one fixed-point add per value into out[0, count)
+FR_D void block_acc_flush(int n_acc, int from, int count, fix64* out) {
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += RT_THREADS) {
+    for (int i = threadIdx.x; i < count; i += RT_THREADS) {
         double s = 0.0;
-        for (int w = 0; w < RT_WARPS; ++w) s += acc_dyn[w * n + i];
+        for (int w = 0; w < RT_WARPS; ++w) s += acc_dyn[w * n_acc + from + i];
         if (s != 0.0) atomicAdd(&out[i], (fix64)to_fix_d(s));
     }
 }
@@ -358,7 +383,7 @@ FR_D void scatter_texel(fix64* base, int C, int texel, int ch, float g, bool on)
 // for visibility of the emitter, Sec. 4).  Adds C * dz/dy . m to gy and
 // scatters the edge-vertex terms.  Returns nothing; inactive lanes do nothing.
 FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL, const SampleState& ss,
-                      const Sampler& sm2, float3 w, float3& gy, fix64* d_v, Stack st, RayStats& rs) {
+                      const Sampler& sm2, float3 w, float3& gy, fix64* d_v, fix64* small, Stack st, RayStats& rs) {
     const uint4 blk = sm2.block(0);
     const float u0 = u24(blk.x), u1 = u24(blk.y), u2 = u24(blk.z);
     const int j = min((int)(u0 * (float)S.NL), S.NL - 1);
@@ -423,6 +448,19 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     gy += g_y * C;
     add_vec(d_v, E.x, g_p * (C * (1.0f - t)), true);
     add_vec(d_v, E.y, g_p * (C * t), true);
+    if (S.stage) {
+        // a stage light moves under the boundary: the boundary's normal velocity
+        // relative to the emitter's own points (the plane moves only with d)
+        const StageFrame F = stage_frame(S, P, j);
+        const float vd = mq * dot(L.n, L.c - F.C) / (F.d * den) - dot(m, z - F.C) / F.d;
+        const float va = -dot(m, z - F.P) / (2.0f * F.a);
+        const float vp0 = -F.d * dot(m, F.dA), vp1 = -F.d * dot(m, F.dB);
+        fix64* g = small + FR_GEO_OFF + 4 * j;
+        fix_add(&g[0], C * vd);
+        fix_add(&g[1], C * va);
+        fix_add(&g[2], C * vp0);
+        fix_add(&g[3], C * vp1);
+    }
 }
 
 // RECORDED: every item of the launch carries the forward's hit records, so the
@@ -440,7 +478,8 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     const EdgeLists& EL = it.EL;
     const float* adj_image = it.adj;
     const uint32_t iteration = it.iteration, face = it.face;
-    const int n_acc = 1 + 3 * S.NL;
+    const bool stage = S.stage != nullptr;                      // lights built from (d, a, p)
+    const int n_acc = 1 + 3 * S.NL + (stage ? 4 * S.NL : 0);
     block_acc_init(n_acc);
     const long total = (long)S.W * S.H * S.spp;
     const long qi = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
@@ -482,14 +521,26 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
                     vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
             }
             float3 gI = f3(0.0f, 0.0f, 0.0f);
+            float gl4[4] = {0.0f, 0.0f, 0.0f, 0.0f};            // d, a, p0, p1 of light j
             if (interior && ss.hit && ((vis >> (j & 63)) & 1ull)) {
                 const LightDev& L = S.lights[j];
                 const float2 u = dc.pair(smp, 2 + 2 * j);
                 const float3 z = light_point(L, u.x, u.y);
                 const float3 I = intensity(S, P, j);
                 const float3 gh = f3(w.x * I.x, w.y * I.y, w.z * I.z) * L.area;
-                const float3 h = light_h<true>(S.flags, L, z, ss, gh, &g, &gy);
+                float3 gz = f3(0.0f, 0.0f, 0.0f);
+                const float3 h = light_h<true>(S.flags, L, z, ss, gh, &g, &gy, stage ? &gz : nullptr);
                 gI = f3(w.x * h.x, w.y * h.y, w.z * h.z) * (L.area * L.scale);
+                if (stage) {
+                    // the sample point moves with the light; area * d^2/a = F d^4
+                    const StageFrame F = stage_frame(S, P, j);
+                    const float gIi = gI.x * __ldg(&P.light_i[3 * j]) + gI.y * __ldg(&P.light_i[3 * j + 1]) +
+                                      gI.z * __ldg(&P.light_i[3 * j + 2]);
+                    gl4[0] = (dot(gz, z - F.C) + 4.0f * gIi) / F.d;
+                    gl4[1] = dot(gz, z - F.P) / (2.0f * F.a);
+                    gl4[2] = F.d * dot(gz, F.dA);
+                    gl4[3] = F.d * dot(gz, F.dB);
+                }
             }
             const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
             if ((threadIdx.x & 31) == 0) {
@@ -498,10 +549,18 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
                 wa[1 + 3 * j + 1] += (double)sy_;
                 wa[1 + 3 * j + 2] += (double)sz_;
             }
+            if (stage) {                                       // block-uniform
+                float sg[4];
+                for (int q = 0; q < 4; ++q) sg[q] = warp_sum(gl4[q]);
+                if ((threadIdx.x & 31) == 0) {
+                    double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc + 1 + 3 * S.NL + 4 * j;
+                    for (int q = 0; q < 4; ++q) wa[q] += (double)sg[q];
+                }
+            }
         }
         if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit) {
             const Sampler sm2{make_uint2(S.seed, FR_STREAM_EDGE_SHADOW), (uint32_t)pixel, (uint32_t)s, iteration, face};
-            shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, my_stack(sh), rs);
+            shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, G.small, my_stack(sh), rs);
         }
     }
     // ---- chain rule back to the hit triangle, its normals and the camera ----
@@ -597,7 +656,8 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
     const float gf_w = warp_sum(gfocal);
     if ((threadIdx.x & 31) == 0) acc_dyn[(threadIdx.x >> 5) * n_acc] += (double)gf_w;
     flush_stats(S.counters + 3, rs);
-    block_acc_flush(n_acc, G.small);
+    block_acc_flush(n_acc, 0, 1 + 3 * S.NL, G.small);
+    if (stage) block_acc_flush(n_acc, 1 + 3 * S.NL, 4 * S.NL, G.small + FR_GEO_OFF);
 }
 
 // ---------------------------------------------------------------------------
@@ -742,7 +802,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
     scatter_vertex(G.d_v, E.y, gB, active);
     const float gw = warp_sum(gf);
     if ((threadIdx.x & 31) == 0) acc_dyn[threadIdx.x >> 5] += (double)gw;
-    block_acc_flush(1, G.small);
+    block_acc_flush(1, 0, 1, G.small);
 }
 
 // ---------------------------------------------------------------------------
@@ -952,9 +1012,10 @@ void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) 
     fr_count_launches(1);
 }
 
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, cudaStream_t st) {
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage,
+                    cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    const size_t acc_bytes = sizeof(double) * RT_WARPS * (1 + 3 * (size_t)NL);
+    const size_t acc_bytes = sizeof(double) * RT_WARPS * (1 + (any_stage ? 7 : 3) * (size_t)NL);
     if (all_recorded)
         k_adjoint<true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
     else

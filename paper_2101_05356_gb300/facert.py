@@ -38,7 +38,7 @@ class FrMesh(ctypes.Structure):
 
 
 class FrLightStage(ctypes.Structure):
-    _fields_ = [("n_lights", ctypes.c_int32), ("records", _vp), ("d", _vp), ("a", _vp)]
+    _fields_ = [("n_lights", ctypes.c_int32), ("records", _vp), ("d", _vp), ("a", _vp), ("stage", _vp)]
 
 
 class FrAlbedoModel(ctypes.Structure):
@@ -47,14 +47,17 @@ class FrAlbedoModel(ctypes.Structure):
 
 
 PARAM_NAMES = ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness")
+# optional light-stage geometry (Sec. 3.3): distance, relative area, barycentric centre
+STAGE_NAMES = ("light_d", "light_a", "light_p")
+ALL_PARAM_NAMES = PARAM_NAMES + STAGE_NAMES
 
 
 class FrParams(ctypes.Structure):
-    _fields_ = [(n, _vp) for n in PARAM_NAMES]
+    _fields_ = [(n, _vp) for n in ALL_PARAM_NAMES]
 
 
 class FrGrads(ctypes.Structure):
-    _fields_ = [(n, _vp) for n in PARAM_NAMES]
+    _fields_ = [(n, _vp) for n in ALL_PARAM_NAMES]
 
 
 GROUP_PLAIN, GROUP_COEF, GROUP_LIGHT, GROUP_TEX_RGB, GROUP_TEX_MONO = 0, 1, 2, 3, 4
@@ -172,11 +175,13 @@ def fr_set_mesh(ctx, mean, basis, faces, uv):
     check(lib().fr_set_mesh(ctx, ctypes.byref(m)), ctx)
 
 
-def fr_set_lights(ctx, records, d, a):
+def fr_set_lights(ctx, records, d, a, stage=None):
     records = np.ascontiguousarray(records, np.float32)
     d = np.ascontiguousarray(d, np.float32)
     a = np.ascontiguousarray(a, np.float32)
-    ls = FrLightStage(records.shape[0], records.ctypes.data, d.ctypes.data, a.ctypes.data)
+    st = None if stage is None else np.ascontiguousarray(stage, np.float32)
+    ls = FrLightStage(records.shape[0], records.ctypes.data, d.ctypes.data, a.ctypes.data,
+                      None if st is None else st.ctypes.data)
     check(lib().fr_set_lights(ctx, ctypes.byref(ls)), ctx)
 
 
@@ -222,11 +227,11 @@ def fr_albedo_adjoint(ctx, g_diffuse, g_specular, g_beta, g_gamma):
 
 
 def _params(p):
-    return FrParams(*[_ptr(p.get(n)) for n in PARAM_NAMES])
+    return FrParams(*[_ptr(p.get(n)) for n in ALL_PARAM_NAMES])
 
 
 def _grads(g):
-    return FrGrads(*[_ptr(g.get(n)) for n in PARAM_NAMES])
+    return FrGrads(*[_ptr(g.get(n)) for n in ALL_PARAM_NAMES])
 
 
 def fr_forward(ctx, params, image, iteration=0, face_id=0):
@@ -389,7 +394,7 @@ class Renderer:
         self.scene = scene
         self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed, max_batch)
         fr_set_mesh(self.ctx, scene.mean, scene.basis, scene.faces, scene.uv)
-        fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a)
+        fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a, getattr(scene, "stage", None))
         self.landmarks = getattr(scene, "landmarks", None)
         if self.landmarks is not None:
             fr_set_landmarks(self.ctx, self.landmarks)
@@ -411,9 +416,10 @@ class Renderer:
             pass
 
     def device_params(self, params):
+        """Device copies of the parameters (the stage geometry only when set)."""
         t = self.torch
         return {n: t.as_tensor(np.ascontiguousarray(getattr(params, n), np.float32)).cuda()
-                for n in PARAM_NAMES}
+                for n in ALL_PARAM_NAMES if getattr(params, n, None) is not None}
 
     def zero_grads(self, dparams):
         return {n: self.torch.zeros_like(v) for n, v in dparams.items()}

@@ -421,25 +421,24 @@ def _polyhedron(name):
     return v, f
 
 
-def polyhedral_stage(name="ico", d=3.0, a=0.25, p=None, centre=STAGE_CENTRE):
-    """The virtual light stage of Sec. 3.3: one triangular area light per face
-    of a convex polyhedron around the head (the paper's icosahedron: 20; also
-    the tetrahedron, octahedron and 80-face sphere variants it compares).
-    Light j lies in face j's homothetic copy scaled by its distance d_j from
-    the stage centre, is that face shrunk by sqrt(a_j) (a_j = relative area in
-    [0, 1]) around the point with barycentric coordinates p_j (default the
-    centroid), stays parallel to the face and emits towards the centre.
-    Returns (records [N_L, 11] of type LIGHT_TRI, d [N_L], a [N_L]); see
-    polyhedral_stage_geometry for the per-light face data the parameters act on."""
-    v, f = _polyhedron(name)
-    n = f.shape[0]
+def stage_records(stage, d=3.0, a=0.25, p=None):
+    """Emitter records of a virtual light stage (Sec. 3.3) from its frame
+    ([N_L, 12]: centre C, face V0, V1, V2 per light) and the lights'
+    parameters: light j lies in face j's homothetic copy scaled by d_j about C,
+    is that face shrunk by sqrt(a_j) (a_j = relative area in [0, 1]) around
+    the point with barycentric coordinates p_j (default the centroid), stays
+    parallel to the face and emits towards C.  Returns (records [N_L, 11] of
+    type LIGHT_TRI, d [N_L], a [N_L])."""
+    stage = np.asarray(stage, np.float64)
+    n = stage.shape[0]
     d = np.broadcast_to(np.asarray(d, np.float64), (n,))
     a = np.broadcast_to(np.asarray(a, np.float64), (n,))
     p = np.full((n, 3), 1.0 / 3.0) if p is None else np.asarray(p, np.float64)
-    c0 = np.asarray(centre, np.float64)
+    if p.shape[1] == 2:
+        p = np.concatenate([p, 1.0 - p.sum(axis=1, keepdims=True)], axis=1)
     rec = np.zeros((n, 11), np.float32)
     for j in range(n):
-        A, B, C = v[f[j, 0]], v[f[j, 1]], v[f[j, 2]]
+        c0, A, B, C = stage[j, 0:3], stage[j, 3:6], stage[j, 6:9], stage[j, 9:12]
         G = (A + B + C) / 3.0
         P = c0 + d[j] * (p[j, 0] * A + p[j, 1] * B + p[j, 2] * C)
         s = math.sqrt(a[j]) * d[j]
@@ -450,6 +449,13 @@ def polyhedral_stage(name="ico", d=3.0, a=0.25, p=None, centre=STAGE_CENTRE):
         rec[j, 4:7] = t1 - t0
         rec[j, 7:10] = t2 - t0
     return rec, d.astype(np.float32).copy(), a.astype(np.float32).copy()
+
+
+def polyhedral_stage(name="ico", d=3.0, a=0.25, p=None, centre=STAGE_CENTRE):
+    """The virtual light stage of Sec. 3.3 on a convex polyhedron around the
+    head (the paper's icosahedron: 20 lights; also the tetrahedron, octahedron
+    and 80-face sphere variants it compares): stage_records of its frame."""
+    return stage_records(polyhedral_stage_geometry(name, centre), d, a, p)
 
 
 def polyhedral_stage_geometry(name="ico", centre=STAGE_CENTRE):

@@ -63,3 +63,21 @@ def shadow_box(width=32, height=32, spp=4, tex=8, seed=0):
     pr.roughness = rng.uniform(0.3, 0.6, size=(tex, tex)).astype(np.float32)
     pr.coef = np.array([0.02, -0.03, 0.01, 0.05], np.float32)
     return sc, pr
+
+
+def stage_box(width=32, height=32, spp=4, tex=8, seed=0):
+    """The shadow box lit by a two-light virtual light stage (Sec. 3.3) instead:
+    two triangular lights between the occluder and the camera, each in its
+    frame's face scaled by d about a centre below the floor, so that moving
+    them (d, a, p) moves the occluder's shadow boundaries across the floor."""
+    sc, pr = shadow_box(width, height, spp, tex, seed)
+    stage = np.array([[0, 0, -4.5, -0.4, -0.3, 1.0, 0.5, -0.3, 1.0, 0.0, 0.5, 1.0],
+                      [0, 0, -4.5, -0.6, 0.2, 1.0, 0.0, 0.0, 1.0, -0.3, 0.6, 1.0]], np.float32)
+    d, a = np.array([2.7, 2.5], np.float32), np.array([0.6, 0.5], np.float32)
+    p = np.array([[0.3, 0.35], [0.4, 0.3]], np.float32)
+    rec, dd, aa = synth.stage_records(stage, d, a, p)
+    import dataclasses
+    sc = dataclasses.replace(sc, lights=rec, light_d=dd, light_a=aa, stage=stage)
+    pr.light_d, pr.light_a, pr.light_p = d.copy(), a.copy(), p.copy()
+    return sc, pr
+
