@@ -348,10 +348,19 @@ uint64_t fr_kernel_launches(void);
                                  chromaticity w_chroma * sum |kappa(X) - kappa(aux)|_1 with
                                  kappa(c) = c / (c_r + c_g + c_b + 1e-6), soft box [0, 1] (w_box) */
 #define FR_GROUP_TEX_MONO 4   /* M x M texture: smoothness, symmetry, soft box [0, 1] */
+#define FR_GROUP_STAGE    5   /* virtual light stage geometry (Sec. 3.3) of N_L lights, x = [d (N_L) |
+                                 a (N_L) | p (N_L x 2)], aux = the intensities i [N_L][3]: gradient of
+                                 the light prior above through I_j = (d_j^2 / a_j) i_j (where a_j > 0;
+                                 its energy is the LIGHT group's) and soft boxes (w_box) d_j >= 0,
+                                 a_j in [0, 1] and light j inside its homothetic face: each corner's
+                                 barycentric coordinate p_jm - sqrt(a_j) / 3 + sqrt(a_j) delta >= 0,
+                                 i.e. p_jm >= sqrt(a_j) / 3 for m = 0, 1, 2, p_j2 = 1 - p_j0 - p_j1 */
 
 /* One parameter group.  x, m, v (and g, aux when used) are device float32
  * arrays of n elements (aux: N_L scales for LIGHT, the M x M x 3 reference
- * albedo for TEX_RGB).  m and v must be zero before step 1.  After the update x
+ * albedo for TEX_RGB, the N_L x 3 intensities for STAGE).  aux2 is used by
+ * LIGHT only: when aux is NULL the scales are d_j^2 / a_j read from aux2, the
+ * x of the STAGE group ([d | a | p], 4 N_L floats) at its pre-step values.  m and v must be zero before step 1.  After the update x
  * is clamped to [clamp_lo, clamp_hi] when clamp_lo < clamp_hi.  step > 0 gives
  * this group its own Adam step count (groups of different faces in one call);
  * step = 0 uses the call's step. */
@@ -361,6 +370,7 @@ typedef struct fr_opt_group {
     float* m;
     float* v;
     const float* aux;
+    const float* aux2;
     int32_t n, kind, width, n_prior;
     float lr, w_prior, w_box, w_sym, w_chroma, w_smooth, clamp_lo, clamp_hi;
     int32_t step;

@@ -1,6 +1,7 @@
 // Fused multi-tensor Adam with the regularisers of the two-stage optimisation
 // (Sec. 4, Eq. loss1 and loss3): shape prior, light prior, soft box
-// constraints, texture symmetry, chromaticity consistency and smoothness.  One
+// constraints (expression, intensities, light-stage geometry, textures),
+// texture symmetry, chromaticity consistency and smoothness.  One
 // launch updates every parameter group of a stage; each thread owns one
 // element, adds the regulariser gradient (texture stencils read neighbours) to
 // the render gradient, and applies the Adam step with per-group learning rate.
@@ -40,7 +41,13 @@ FR_D float reg_grad(const fr_opt_group& G, int i, float x, double* energy) {
     }
     case FR_GROUP_LIGHT: {                         // w1 sum_j |I_j - m_j|^2, I = scale * i, m = mean(I) fixed
         const int j = i / 3;
-        const float sc = G.aux[j];
+        float sc;
+        if (G.aux) {
+            sc = G.aux[j];
+        } else {                                   // scale d^2 / a from the stage geometry [d | a | p]
+            const float d = G.aux2[j], a = G.aux2[G.n / 3 + j];
+            sc = a > 0.0f ? d * d / a : 0.0f;
+        }
         const float* base = G.x + 3 * j;
         const float m = sc * (base[0] + base[1] + base[2]) * (1.0f / 3.0f);
         const float d = sc * x - m;
@@ -49,6 +56,48 @@ FR_D float reg_grad(const fr_opt_group& G, int i, float x, double* energy) {
         const float lo = fminf(x, 0.0f);          // soft box i > 0
         g += 2.0f * G.w_box * lo;
         e += (double)G.w_box * lo * lo;
+        break;
+    }
+    case FR_GROUP_STAGE: {                         // light geometry [d | a | p0 p1] of N_L lights
+        const int NL = G.n / 4;
+        const float* X = G.x;
+        if (i < 2 * NL) {
+            const int j = i < NL ? i : i - NL;
+            const float d = X[j], a = X[NL + j];
+            float dE_ds = 0.0f;                    // light prior through s = d^2 / a
+            if (a > 0.0f) {
+                const float s = d * d / a;
+                const float* ij = G.aux + 3 * j;
+                const float m = s * (ij[0] + ij[1] + ij[2]) * (1.0f / 3.0f);
+                for (int c = 0; c < 3; ++c) dE_ds += (s * ij[c] - m) * ij[c];
+                dE_ds *= 2.0f * G.w_prior;
+            }
+            if (i < NL) {                          // d: prior, soft box d >= 0
+                if (a > 0.0f) g += dE_ds * 2.0f * d / a;
+                const float lo = fminf(d, 0.0f);
+                g += 2.0f * G.w_box * lo;
+                e += (double)G.w_box * lo * lo;
+            } else {                               // a: prior, soft box [0, 1], inside-face term through sqrt(a)
+                if (a > 0.0f) g += dE_ds * (-(d * d / a) / a);
+                const float lo = fminf(a, 0.0f), hi = fmaxf(a - 1.0f, 0.0f);
+                g += 2.0f * G.w_box * (lo + hi);
+                e += (double)G.w_box * (lo * lo + hi * hi);
+                if (a > 0.0f) {
+                    const float ra = sqrtf(a), r = ra * (1.0f / 3.0f);
+                    const float p0 = X[2 * NL + 2 * j], p1 = X[2 * NL + 2 * j + 1];
+                    const float in = fminf(p0 - r, 0.0f) + fminf(p1 - r, 0.0f) + fminf(1.0f - p0 - p1 - r, 0.0f);
+                    g += 2.0f * G.w_box * in * (-1.0f / (6.0f * ra));
+                }
+            }
+        } else {                                   // p_jm: corners inside the homothetic face
+            const int q = i - 2 * NL, j = q >> 1, mm = q & 1;
+            const float a = X[NL + j];
+            const float r = sqrtf(fmaxf(a, 0.0f)) * (1.0f / 3.0f);
+            const float p0 = X[2 * NL + 2 * j], p1 = X[2 * NL + 2 * j + 1];
+            const float in0 = fminf(p0 - r, 0.0f), in1 = fminf(p1 - r, 0.0f), in2 = fminf(1.0f - p0 - p1 - r, 0.0f);
+            g += 2.0f * G.w_box * ((mm == 0 ? in0 : in1) - in2);
+            if (mm == 0) e += (double)G.w_box * ((double)in0 * in0 + (double)in1 * in1 + (double)in2 * in2);
+        }
         break;
     }
     case FR_GROUP_TEX_RGB:
@@ -168,7 +217,8 @@ extern "C" fr_status fr_adam(const fr_opt_group* groups, int32_t n_groups, int32
         if ((G.kind == FR_GROUP_TEX_RGB || G.kind == FR_GROUP_TEX_MONO) &&
             (G.width < 1 || (long)G.width * G.width * (G.kind == FR_GROUP_TEX_RGB ? 3 : 1) != G.n))
             return FR_EINVAL;
-        if (G.kind == FR_GROUP_LIGHT && (!G.aux || G.n % 3 != 0)) return FR_EINVAL;
+        if (G.kind == FR_GROUP_LIGHT && ((!G.aux && !G.aux2) || G.n % 3 != 0)) return FR_EINVAL;
+        if (G.kind == FR_GROUP_STAGE && (!G.aux || G.n % 4 != 0)) return FR_EINVAL;
         T.g[k] = G;
         const int st_k = G.step > 0 ? G.step : step;
         T.bc1[k] = (float)(1.0 - pow((double)beta1, st_k));

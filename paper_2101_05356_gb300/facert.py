@@ -60,11 +60,11 @@ class FrGrads(ctypes.Structure):
     _fields_ = [(n, _vp) for n in ALL_PARAM_NAMES]
 
 
-GROUP_PLAIN, GROUP_COEF, GROUP_LIGHT, GROUP_TEX_RGB, GROUP_TEX_MONO = 0, 1, 2, 3, 4
+GROUP_PLAIN, GROUP_COEF, GROUP_LIGHT, GROUP_TEX_RGB, GROUP_TEX_MONO, GROUP_STAGE = 0, 1, 2, 3, 4, 5
 
 
 class FrOptGroup(ctypes.Structure):
-    _fields_ = [("x", _vp), ("g", _vp), ("m", _vp), ("v", _vp), ("aux", _vp),
+    _fields_ = [("x", _vp), ("g", _vp), ("m", _vp), ("v", _vp), ("aux", _vp), ("aux2", _vp),
                 ("n", ctypes.c_int32), ("kind", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("n_prior", ctypes.c_int32), ("lr", ctypes.c_float), ("w_prior", ctypes.c_float),
                 ("w_box", ctypes.c_float), ("w_sym", ctypes.c_float), ("w_chroma", ctypes.c_float),
@@ -352,12 +352,12 @@ def fr_set_flags(ctx, flags):
 
 
 def opt_group(x, m, v, g=None, aux=None, kind=GROUP_PLAIN, lr=1e-3, width=0, n_prior=0, w_prior=0.0,
-              w_box=0.0, w_sym=0.0, w_chroma=0.0, w_smooth=0.0, clamp=None, step=0):
+              w_box=0.0, w_sym=0.0, w_chroma=0.0, w_smooth=0.0, clamp=None, step=0, aux2=None):
     """One fr_opt_group over torch device tensors (views of x/g/m/v share storage)."""
     lo, hi = clamp if clamp is not None else (0.0, 0.0)
-    grp = FrOptGroup(_ptr(x), _ptr(g), _ptr(m), _ptr(v), _ptr(aux), x.numel(), kind, width, n_prior, lr,
-                     w_prior, w_box, w_sym, w_chroma, w_smooth, lo, hi, step)
-    grp._keep = (x, g, m, v, aux)
+    grp = FrOptGroup(_ptr(x), _ptr(g), _ptr(m), _ptr(v), _ptr(aux), _ptr(aux2), x.numel(), kind, width, n_prior,
+                     lr, w_prior, w_box, w_sym, w_chroma, w_smooth, lo, hi, step)
+    grp._keep = (x, g, m, v, aux, aux2)
     return grp
 
 

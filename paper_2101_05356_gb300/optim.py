@@ -1,7 +1,8 @@
 """Two-stage reconstruction (Sec. 4) with device-resident state.
 
 Stage I optimises shape and expression coefficients, pose, light-stage
-intensities and (when the scene has a statistical albedo model, Sec. 3.2) the
+intensities (and, when the parameters carry it, the light-stage geometry
+d, a, p of Sec. 3.3) and (when the scene has a statistical albedo model, Sec. 3.2) the
 albedo coefficients beta and gamma against E_ph + E_p + E_b (Eq. loss1): each
 Stage I step morphs the textures from beta, gamma (fr_albedo_morph) before the
 render and maps the texture gradients back (fr_albedo_adjoint) after it.
@@ -24,6 +25,8 @@ ALPHA1 = 1.0             # weight of E_land in E_d (Sec. 5)
 LR = dict(light=1e-3, identity=1e-2, expression=1e-3, rot=1e-3, trans=1e-3, texture=5e-3, albedo=2e-2)
 W = dict(w_i=0.0025, w_c=0.0025, w_s=0.0025, w1=0.01, w2=0.3, w3=0.3, w4=0.0002, box=1.0)
 STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE
+# hard floor on d, a and p after each update (keeps d^2/a finite; the soft boxes do the rest)
+STAGE_CLAMP = (1e-3, 1e3)
 
 
 @dataclasses.dataclass
@@ -55,6 +58,18 @@ class FaceState:
         self.ks = sc.n_shape
         self.tex = sc.tex_size
         self.light_scale = torch.as_tensor(sc.light_d ** 2 / sc.light_a, dtype=torch.float32).cuda()
+        # light-stage geometry (d, a, p) when the parameters carry it: one
+        # contiguous [d | a | p] block per state so that one STAGE group covers it
+        self.stage_block = None
+        if all(n in self.p for n in facert.STAGE_NAMES):
+            self.stage_block = {}
+            nl = self.p["light_d"].numel()
+            for q, dct in (("x", self.p), ("g", self.g), ("m", self.m), ("v", self.v)):
+                blk = torch.cat([dct["light_d"].reshape(-1), dct["light_a"].reshape(-1),
+                                 dct["light_p"].reshape(-1)]).contiguous()
+                dct["light_d"], dct["light_a"] = blk[:nl], blk[nl:2 * nl]
+                dct["light_p"] = blk[2 * nl:].view(nl, 2)
+                self.stage_block[q] = blk
         self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         self.reg = torch.zeros(1, dtype=torch.float64, device="cuda")
         self.image = torch.zeros((self.height, self.width, 3), dtype=torch.float32, device="cuda")
@@ -77,8 +92,9 @@ class FaceState:
 
     def nbytes(self):
         """Device memory owned by this face's state."""
-        ts = list(self.p.values()) + list(self.g.values()) + list(self.m.values()) + list(self.v.values())
+        ts = [t for dct in (self.p, self.g, self.m, self.v) for n, t in dct.items() if n not in facert.STAGE_NAMES]
         ts += [self.image, self.target]
+        ts += list(self.stage_block.values()) if self.stage_block else []
         ts += [t for a in self.ab.values() for q, t in a.items() if q != "k"]
         b = sum(t.numel() * t.element_size() for t in ts)
         return b + 2 * self.p["diffuse"].numel() * 4          # Stage II albedo references
@@ -153,9 +169,15 @@ class FaceState:
                                             w_box=W["box"], step=step))
             out.append(facert.opt_group(p["rot"], m["rot"], v["rot"], g["rot"], lr=LR["rot"], step=step))
             out.append(facert.opt_group(p["trans"], m["trans"], v["trans"], g["trans"], lr=LR["trans"], step=step))
+            sb = self.stage_block
             out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"],
-                                        aux=self.light_scale, kind=facert.GROUP_LIGHT, lr=LR["light"],
-                                        w_prior=W["w1"], w_box=W["box"], step=step))
+                                        aux=None if sb else self.light_scale, aux2=sb["x"] if sb else None,
+                                        kind=facert.GROUP_LIGHT, lr=LR["light"], w_prior=W["w1"], w_box=W["box"],
+                                        step=step))
+            if sb:                  # light geometry: prior through d^2/a, soft boxes (Sec. 4, E_b)
+                out.append(facert.opt_group(sb["x"], sb["m"], sb["v"], sb["g"], aux=p["light_i"],
+                                            kind=facert.GROUP_STAGE, lr=LR["light"], w_prior=W["w1"],
+                                            w_box=W["box"], clamp=STAGE_CLAMP, step=step))
             for name, w in (("beta", W["w_c"]), ("gamma", W["w_s"])):
                 a = self.ab.get(name)
                 if a and a["k"] > 0:

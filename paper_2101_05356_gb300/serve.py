@@ -88,6 +88,8 @@ class Server:
         sc = self.scene
         m2 = sc.tex_size * sc.tex_size
         n_param = sc.n_basis + 3 + 3 + 1 + 3 * sc.n_lights + 7 * m2
+        if getattr(sc, "stage", None) is not None:
+            n_param += 4 * sc.n_lights          # light-stage geometry d, a, p
         return 4 * (4 * n_param + 2 * 3 * req.width * req.height + 2 * 3 * m2) + 8 * 2
 
     def _admit(self, now):

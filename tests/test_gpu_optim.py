@@ -101,6 +101,61 @@ def test_adam_step_matches_oracle():
     assert energy.item() == pytest.approx(e_want, rel=1e-5)
 
 
+def test_stage_geometry_groups_match_oracle():
+    """FR_GROUP_STAGE (light geometry: prior through d^2/a, soft boxes) and a
+    LIGHT group whose scales come from the stage's pre-step geometry."""
+    from paper_2101_05356_gb300 import facert
+    rng = np.random.default_rng(5)
+    NL = 6
+    x = np.concatenate([rng.uniform(-0.3, 4.0, NL), rng.uniform(0.05, 1.3, NL), rng.uniform(-0.2, 0.9, 2 * NL)])
+    li = rng.uniform(-0.2, 1.5, (NL, 3))
+    gx, gl = rng.normal(size=x.size), rng.normal(size=li.shape)
+    mx, ml = rng.normal(size=x.size) * 0.1, rng.normal(size=li.shape) * 0.1
+    vx, vl = rng.uniform(0, 0.05, x.size), rng.uniform(0, 0.05, li.shape)
+    T = [_t(a) for a in (x, gx, mx, vx, li, gl, ml, vl)]
+    groups = [facert.opt_group(T[0], T[2], T[3], T[1], aux=T[4], kind=facert.GROUP_STAGE, lr=1e-3, w_prior=0.01,
+                               w_box=1.0, clamp=(1e-3, 1e3)),
+              facert.opt_group(T[4], T[6], T[7], T[5], aux2=T[0], kind=facert.GROUP_LIGHT, lr=1e-3, w_prior=0.01,
+                               w_box=1.0)]
+    energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    step = 4
+    facert.fr_adam(groups, step, reg_energy=energy)
+    torch.cuda.synchronize()
+    f = [np.asarray(a, np.float32).astype(np.float64) for a in (x, gx, mx, vx, li, gl, ml, vl)]
+    d, a, _ = ora.stage_split(f[0])
+    b = dict(b1=float(np.float32(0.9)), b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)))
+    lr = float(np.float32(1e-3))
+    xw, mw, vw = ora.adam(f[0], f[1] + ora.stage_grad(f[0], f[4], 0.01, 1.0), f[2], f[3], step, lr,
+                          clamp=(float(np.float32(1e-3)), float(np.float32(1e3))), **b)
+    lw, lmw, lvw = ora.adam(f[4], f[5] + ora.light_grad(f[4], d * d / a, 0.01, 1.0), f[6], f[7], step, lr, **b)
+    for got, want in ((T[2], mw), (T[3], vw), (T[0], xw), (T[6], lmw), (T[7], lvw), (T[4], lw)):
+        assert np.allclose(got.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
+    e_want = ora.light_energy(f[4], d * d / a, 0.01, 1.0) + ora.stage_box_energy(f[0], 1.0)
+    assert energy.item() == pytest.approx(e_want, rel=1e-5)
+
+
+def test_stage_geometry_reconstruction_stays_in_the_box():
+    """Stage I with the light geometry free: the loss falls, every light stays
+    in its homothetic face and the device status stays clean."""
+    from paper_2101_05356_gb300 import facert, optim
+    sc = synth.make_scene("tiny", light_stage="ico")
+    r = facert.Renderer(sc)
+    gt = synth.with_stage_geometry(sc, synth.random_params(sc, 3, coef_scale=0.5), seed=4)
+    target = r.forward(r.device_params(gt), iteration=10 ** 6)
+    init = synth.with_stage_geometry(sc, synth.init_params(sc))
+    rec = optim.Reconstruction(r, target, init, schedule=optim.Schedule(30, 0))
+    e0 = optim.photometric_loss(r, rec.p, target)
+    x0 = rec.stage_block["x"].cpu().numpy().copy()
+    rec.run()
+    e1 = optim.photometric_loss(r, rec.p, target)
+    x1 = rec.stage_block["x"].cpu().numpy()
+    assert r.status() == 0
+    assert e1 < e0, (e0, e1)
+    assert not np.array_equal(x0, x1)
+    assert np.all(np.isfinite(x1))
+    assert ora.stage_box_energy(x1.astype(np.float64), 1.0) < 1e-6
+
+
 def test_autograd_function_matches_adjoint_and_linearity():
     from paper_2101_05356_gb300 import autograd, facert
     sc = synth.make_scene("tiny")
