@@ -386,6 +386,109 @@ typedef struct fr_opt_group {
 fr_status fr_adam(const fr_opt_group* groups, int32_t n_groups, int32_t step, float beta1, float beta2,
                   float eps, double* reg_energy, void* stream);
 
+/* ---- native continuous-batching server ---- */
+
+/* A reconstruction server owns one context (fully set up: mesh, lights and,
+ * when used, albedo model and landmarks) and a worker thread with its own
+ * stream.  Requests (a target image, a sample count, the two-stage schedule of
+ * Sec. 4 with the optional landmark-only initialisation, initial parameters)
+ * are queued by fr_submit from any host thread.  At every step boundary the
+ * worker admits waiting requests in arrival order while a slot is free and
+ * the device state of the admitted requests stays within the memory cap, then
+ * advances every admitted request by one iteration: the Stage I statistical
+ * albedos of all of them in one fr_albedo_morph call, one fr_render_batch
+ * call, one fr_albedo_adjoint call, the landmark terms, and one fr_adam call
+ * over every request's parameter groups (the same groups, learning rates and
+ * weights as Sec. 5 gives).  A request's parameters, Adam moments and buffers
+ * stay on the device, in one allocation made at admission, until it finishes;
+ * its final photometric loss is then evaluated with a fixed Philox iteration,
+ * its parameters optionally copied to the host, and its memory freed.  Philox
+ * streams are keyed by the request id (the face id) and the request's own
+ * iteration, so a request's result does not depend on what it was batched
+ * with.  The paper serves nothing; this is the serving form of its method. */
+typedef struct fr_server fr_server;
+
+typedef struct fr_server_config {
+    int32_t max_slots;        /* requests advanced together, 1..the context's max_batch */
+    uint64_t mem_cap_bytes;   /* device bytes the admitted requests' state may hold (the first
+                                 request is admitted whatever its size) */
+    int32_t n_identity;       /* K_s: coef[0, K_s) are identity (prior), the rest expression
+                                 (soft box [0, 1]) */
+    int32_t edge_spp;         /* primary-edge samples per pixel of every step (0..64) */
+    uint32_t item_flags;      /* FR_FLAG_* bits of every render item (Stage II adds
+                                 FR_FLAG_NO_PRIMARY_EDGE | FR_FLAG_NO_SHADOW_EDGE) */
+    uint32_t eval_iteration;  /* Philox iteration of the final loss evaluation */
+    int32_t eval_spp;         /* spp of the final loss evaluation (0: the request's own) */
+    int32_t keep_params;      /* != 0: copy each finished request's parameters to the host */
+} fr_server_config;
+
+/* One request.  Host pointers, copied by fr_submit: target [height][width][3];
+ * init holds HOST pointers to the initial parameters with the shapes of
+ * fr_params (light_d/light_a/light_p all three or none; with them, and a
+ * light stage on the context, Stage I also optimises the light geometry);
+ * landmarks [n_landmarks][2] target pixels or NULL (then no E_land and no
+ * initialisation stage; n_landmarks must equal the context's). */
+typedef struct fr_request {
+    int32_t width, height, spp;
+    int32_t init_iters, stage1_iters, stage2_iters;
+    const float* target;
+    fr_params init;
+    const float* landmarks;
+    int32_t n_landmarks;
+} fr_request;
+
+#define FR_REQ_QUEUED  0
+#define FR_REQ_RUNNING 1
+#define FR_REQ_DONE    2
+#define FR_REQ_FAILED  3
+#define FR_EAGAIN      6   /* fr_poll: the request has not finished */
+
+typedef struct fr_result {
+    int32_t state;            /* FR_REQ_* */
+    int32_t iterations;       /* iterations run so far */
+    double final_loss;        /* E_ph at the final parameters (DONE) */
+    double submit_s, admit_s, finish_s;   /* seconds since fr_server_create (-1: not yet) */
+    char error[128];          /* why a request FAILED */
+} fr_result;
+
+typedef struct fr_server_stats {
+    int64_t steps;            /* batched steps run */
+    int64_t item_steps;       /* sum over steps of the admitted requests */
+    int32_t max_active;       /* most requests admitted at once */
+    int32_t active, queued;   /* now */
+    uint64_t peak_bytes;      /* most device state held by admitted requests at once */
+} fr_server_stats;
+
+/* Start a server on ctx (which must not be used otherwise until
+ * fr_server_destroy; the device current on the calling thread is the one the
+ * worker uses).  Errors: FR_EINVAL (context not set up, bad config),
+ * FR_ECUDA. */
+fr_status fr_server_create(fr_server** out, fr_ctx* ctx, const fr_server_config* cfg);
+
+/* Queue a request; *id receives its id (0, 1, 2, ... in submission order),
+ * which is also its Philox face id.  A request the server can never run
+ * (image above the context's width * height, spp above the context's, no
+ * landmarks set on the context, bad schedule) is queued as FAILED with a
+ * reason.  Errors: FR_EINVAL (null pointers). */
+fr_status fr_submit(fr_server* srv, const fr_request* req, uint64_t* id);
+
+/* State of request id.  Returns FR_OK once it is DONE or FAILED (and, if
+ * params_out is not NULL and the request is DONE with keep_params, copies its
+ * final parameters into params_out's HOST buffers, which have the shapes of
+ * fr_params; null members are skipped), FR_EAGAIN while it is queued or
+ * running, FR_EINVAL for an unknown id. */
+fr_status fr_poll(fr_server* srv, uint64_t id, fr_result* out, const fr_grads* params_out);
+
+/* Block until every submitted request is DONE or FAILED, or timeout_s
+ * seconds pass (FR_ETIMEOUT). */
+fr_status fr_server_wait(fr_server* srv, double timeout_s);
+
+fr_status fr_server_get_stats(fr_server* srv, fr_server_stats* out);
+
+/* Stop the worker (requests still queued or running are dropped), free every
+ * request's device state and the stream.  The context stays the caller's. */
+void fr_server_destroy(fr_server* srv);
+
 /* ---- allocation-free variant ---- */
 
 /* The photometric loss of fr_loss for callers that cannot allocate device

@@ -83,6 +83,7 @@ struct fr_ctx {
     int4* edges = nullptr;
     LightDev* lights = nullptr;
     float* stage = nullptr;                    // virtual light stage frame [N_L][12] (null: records only)
+    std::vector<float> light_d_h, light_a_h;   // host copies of the lights' d and a
     std::vector<Slot> slots;
     DevItem* d_items = nullptr;                // device item table [FR_MAX_BATCH]
     std::vector<DevItem> h_items;
@@ -470,6 +471,30 @@ ItemArgs single(fr_ctx* c, const fr_params* p, const fr_grads* g, float* image, 
 
 }  // namespace
 
+void ctx_info(const fr_ctx* c, CtxInfo& o) {
+    o = CtxInfo{};
+    if (!c) return;
+    o.width = c->cfg.width;
+    o.height = c->cfg.height;
+    o.spp = c->cfg.spp;
+    o.tex = c->cfg.tex_size;
+    o.K = c->K;
+    o.NL = c->NL;
+    o.max_batch = c->max_batch;
+    o.n_landmarks = c->n_landmarks;
+    o.flags = c->cfg.flags;
+    o.ready = c->have_mesh && c->have_lights;
+    o.have_albedo = c->have_albedo;
+    o.k_diffuse = c->have_albedo ? c->albedo[0].K : 0;
+    o.k_specular = c->have_albedo ? c->albedo[1].K : 0;
+    o.have_stage = c->stage != nullptr;
+    o.light_scale.resize(c->light_d_h.size());
+    for (size_t j = 0; j < c->light_d_h.size(); ++j) {
+        const float d2 = c->light_d_h[j] * c->light_d_h[j];
+        o.light_scale[j] = d2 / c->light_a_h[j];
+    }
+}
+
 extern "C" {
 
 fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
@@ -717,6 +742,8 @@ fr_status fr_set_lights(fr_ctx* c, const fr_light_stage* ls) {
         CK(c, cudaMemcpy(c->stage, ls->stage, sizeof(float) * 12 * ls->n_lights, cudaMemcpyHostToDevice));
     }
     c->NL = ls->n_lights;
+    c->light_d_h.assign(ls->d, ls->d + ls->n_lights);
+    c->light_a_h.assign(ls->a, ls->a + ls->n_lights);
     c->have_lights = true;
     return FR_OK;
 }

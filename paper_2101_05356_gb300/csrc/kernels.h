@@ -64,6 +64,17 @@ struct LandmarkArgs {
 };
 void launch_landmarks(const LandmarkArgs& a, cudaStream_t st);
 
+// api.cu: what the native server (server.cu) needs to know about a context
+struct fr_ctx;
+struct CtxInfo {
+    int width = 0, height = 0, spp = 0, tex = 0, K = 0, NL = 0, max_batch = 0, n_landmarks = 0;
+    int k_diffuse = 0, k_specular = 0;
+    uint32_t flags = 0;
+    bool ready = false, have_albedo = false, have_stage = false;
+    std::vector<float> light_scale;   // d_j^2 / a_j of the light records, in float32 arithmetic
+};
+void ctx_info(const fr_ctx* c, CtxInfo& out);
+
 // bvh_topology.cu (host): static binned-SAH topology of a mesh, in the
 // BvhScratch encoding (child codes ~leaf slot / internal index, root 0)
 struct BvhTopology {

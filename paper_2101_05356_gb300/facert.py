@@ -79,6 +79,33 @@ class FrItem(ctypes.Structure):
                 ("loss", _vp), ("grads", ctypes.POINTER(FrGrads))]
 
 
+class FrServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("mem_cap_bytes", ctypes.c_uint64), ("n_identity", ctypes.c_int32),
+                ("edge_spp", ctypes.c_int32), ("item_flags", ctypes.c_uint32), ("eval_iteration", ctypes.c_uint32),
+                ("eval_spp", ctypes.c_int32), ("keep_params", ctypes.c_int32)]
+
+
+class FrRequest(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("spp", ctypes.c_int32),
+                ("init_iters", ctypes.c_int32), ("stage1_iters", ctypes.c_int32), ("stage2_iters", ctypes.c_int32),
+                ("target", _vp), ("init", FrParams), ("landmarks", _vp), ("n_landmarks", ctypes.c_int32)]
+
+
+class FrResult(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("iterations", ctypes.c_int32), ("final_loss", ctypes.c_double),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double),
+                ("error", ctypes.c_char * 128)]
+
+
+class FrServerStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("item_steps", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("active", ctypes.c_int32), ("queued", ctypes.c_int32), ("peak_bytes", ctypes.c_uint64)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+FR_EAGAIN = 6
+
+
 class FacertError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("facert error %d: %s" % (code, msg))
@@ -137,6 +164,13 @@ def lib():
         L.fr_loss_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fr_loss_noalloc_error.argtypes = []
         L.fr_loss_noalloc_error.restype = ctypes.c_char_p
+        L.fr_server_create.argtypes = [P(_vp), _vp, P(FrServerConfig)]
+        L.fr_submit.argtypes = [_vp, P(FrRequest), P(ctypes.c_uint64)]
+        L.fr_poll.argtypes = [_vp, ctypes.c_uint64, P(FrResult), P(FrGrads)]
+        L.fr_server_wait.argtypes = [_vp, ctypes.c_double]
+        L.fr_server_get_stats.argtypes = [_vp, P(FrServerStats)]
+        L.fr_server_destroy.argtypes = [_vp]
+        L.fr_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -466,3 +500,78 @@ class Renderer:
 
     def status(self):
         return fr_sync_status(self.ctx)
+
+
+# ---- native server ------------------------------------------------------
+
+def fr_server_create(ctx, max_slots=8, mem_cap_bytes=8 << 30, n_identity=0, edge_spp=1, item_flags=0,
+                     eval_iteration=10 ** 6, eval_spp=0, keep_params=True):
+    h = ctypes.c_void_p()
+    cfg = FrServerConfig(max_slots, mem_cap_bytes, n_identity, edge_spp, item_flags, eval_iteration, eval_spp,
+                         1 if keep_params else 0)
+    code = lib().fr_server_create(ctypes.byref(h), ctx, ctypes.byref(cfg))
+    if code != FR_OK:
+        raise FacertError(code, "fr_server_create rejected its context or configuration")
+    return h
+
+
+def _host_params(params):
+    """FrParams of host float32 copies (kept alive by the returned list)."""
+    keep, ptrs = [], []
+    for n in ALL_PARAM_NAMES:
+        v = getattr(params, n, None) if not isinstance(params, dict) else params.get(n)
+        if v is None:
+            ptrs.append(None)
+            continue
+        a = np.ascontiguousarray(v, np.float32)
+        keep.append(a)
+        ptrs.append(a.ctypes.data)
+    return FrParams(*ptrs), keep
+
+
+def fr_submit(srv, target, init, spp, stage1, stage2, init_iters=0, landmarks=None):
+    """Queue one request (host arrays; copied): returns its id (= its Philox face id)."""
+    tgt = np.ascontiguousarray(target, np.float32)
+    pp, keep = _host_params(init)
+    lm = None if landmarks is None else np.ascontiguousarray(landmarks, np.float32)
+    req = FrRequest(tgt.shape[1], tgt.shape[0], spp, init_iters, stage1, stage2, tgt.ctypes.data, pp,
+                    None if lm is None else lm.ctypes.data, 0 if lm is None else lm.shape[0])
+    rid = ctypes.c_uint64()
+    code = lib().fr_submit(srv, ctypes.byref(req), ctypes.byref(rid))
+    if code != FR_OK:
+        raise FacertError(code, "fr_submit: null target or initial parameter")
+    del keep
+    return int(rid.value)
+
+
+def fr_poll(srv, rid, shapes=None):
+    """(finished, result dict, final parameters or None).  `shapes` maps
+    parameter names to the host shapes to copy back (None: no copy)."""
+    res = FrResult()
+    out, gg = None, None
+    if shapes:
+        out = {n: np.zeros(shp, np.float32) for n, shp in shapes.items()}
+        gg = FrGrads(*[None if n not in out else out[n].ctypes.data for n in ALL_PARAM_NAMES])
+    code = lib().fr_poll(srv, rid, ctypes.byref(res), None if gg is None else ctypes.byref(gg))
+    if code not in (FR_OK, FR_EAGAIN):
+        raise FacertError(code, "fr_poll: unknown request id")
+    r = {"state": res.state, "iterations": res.iterations, "final_loss": res.final_loss,
+         "submit_s": res.submit_s, "admit_s": res.admit_s, "finish_s": res.finish_s,
+         "error": res.error.decode()}
+    done = code == FR_OK
+    return done, r, (out if done and res.state == REQ_DONE else None)
+
+
+def fr_server_wait(srv, timeout_s=3600.0):
+    return lib().fr_server_wait(srv, timeout_s) == FR_OK
+
+
+def fr_server_get_stats(srv):
+    st = FrServerStats()
+    check(lib().fr_server_get_stats(srv, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in FrServerStats._fields_}
+
+
+def fr_server_destroy(srv):
+    lib().fr_server_destroy(srv)
+

@@ -173,6 +173,82 @@ class Server:
         return requests
 
 
+class NativeServer:
+    """The library's own server (fr_server_*: admission, batching, the
+    two-stage schedule and its optimiser groups run in a worker thread inside
+    libfacert.so) behind the same run() interface as Server.  Requests get ids
+    0, 1, ... in submission order, and the id is the request's Philox face id,
+    so submitting requests whose rid equals their position reproduces Server's
+    results bit for bit."""
+
+    def __init__(self, scene, max_slots=8, mem_cap_bytes=8 << 30, flags=facert.FLAG_MORPH_BF16,
+                 max_width=None, max_height=None, max_spp=None, edge_spp=1, seed=0, eval_iteration=10 ** 6,
+                 eval_spp=None, keep_params=True):
+        sc = dataclasses.replace(scene, width=max_width or scene.width, height=max_height or scene.height,
+                                 spp=max_spp or scene.spp)
+        self.r = facert.Renderer(sc, edge_spp=edge_spp, flags=flags, seed=seed, max_batch=max_slots)
+        self.scene = sc
+        self.keep_params = keep_params
+        self.srv = facert.fr_server_create(self.r.ctx, max_slots=max_slots, mem_cap_bytes=mem_cap_bytes,
+                                           n_identity=sc.n_shape, edge_spp=edge_spp, eval_iteration=eval_iteration,
+                                           eval_spp=eval_spp or 0, keep_params=keep_params)
+        self.done = []
+
+    def _shapes(self, init):
+        sc = self.scene
+        m, nl = sc.tex_size, sc.n_lights
+        shp = {"coef": (sc.n_basis,), "rot": (3,), "trans": (3,), "focal": (1,), "light_i": (nl, 3),
+               "diffuse": (m, m, 3), "specular": (m, m, 3), "roughness": (m, m)}
+        if getattr(init, "light_d", None) is not None:
+            shp.update(light_d=(nl,), light_a=(nl,), light_p=(nl, 2))
+        return shp
+
+    def run(self, requests, timeout_s=24 * 3600.0):
+        """Submit `requests` at their arrival times (seconds from now), wait
+        for all of them and fill in their results; returns them."""
+        order = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        t0 = time.perf_counter()
+        ids = []
+        for req in order:
+            wait = req.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            s = req.schedule
+            ids.append(facert.fr_submit(self.srv, req.target, req.init, req.spp, s.stage1, s.stage2,
+                                        init_iters=s.init, landmarks=req.landmarks))
+        if not facert.fr_server_wait(self.srv, timeout_s):
+            raise RuntimeError("native server did not finish in time")
+        self.elapsed = time.perf_counter() - t0
+        for req, rid in zip(order, ids):
+            _, res, params = facert.fr_poll(self.srv, rid, self._shapes(req.init) if self.keep_params else None)
+            req.native_id = rid
+            if res["state"] == facert.REQ_FAILED:
+                req.failed = res["error"]
+            else:
+                req.final_loss = res["final_loss"]
+                req.params = params
+                # server clock: latency = finish - submit, reported against the arrival
+                req.admitted = req.arrival + (res["admit_s"] - res["submit_s"])
+                req.finished = req.arrival + (res["finish_s"] - res["submit_s"])
+            self.done.append(req)
+        self.stats = facert.fr_server_get_stats(self.srv)
+        return requests
+
+    def close(self):
+        """Stop the server before its context goes away."""
+        if getattr(self, "srv", None) is not None:
+            facert.fr_server_destroy(self.srv)
+            self.srv = None
+        if getattr(self, "r", None) is not None:
+            self.r.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def facert_max_groups():
     return 128
 

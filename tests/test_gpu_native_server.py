@@ -1,0 +1,124 @@
+"""The library's native server (fr_server_create / fr_submit / fr_poll, a
+worker thread inside libfacert.so) against the Python continuous-batching
+server: the same requests give bitwise the same final parameters and the same
+final loss, through every stage of a reconstruction; admission respects the
+slot count and the memory cap; requests that cannot be served fail alone."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2101_05356_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _requests(sc, specs, schedule, landmarks=False, stage_geometry=False):
+    from oracle import landmarks as olm
+    from paper_2101_05356_gb300 import facert, serve
+    reqs = []
+    for rid, (w, h, spp) in enumerate(specs):
+        s2 = dataclasses.replace(sc, width=w, height=h, spp=spp)
+        r = facert.Renderer(s2)
+        gt = synth.random_params(s2, 70 + rid, coef_scale=0.5)
+        init = synth.init_params(sc)
+        if stage_geometry:
+            gt = synth.with_stage_geometry(s2, gt, seed=rid + 1)
+            init = synth.with_stage_geometry(sc, init)
+        tgt = r.forward(r.device_params(gt), iteration=10 ** 7, face_id=rid).cpu().numpy()
+        r.close()
+        lm = olm.project(sc, gt, sc.landmarks, w, h).astype(np.float32) if landmarks else None
+        reqs.append(serve.Request(rid=rid, target=tgt, spp=spp, schedule=schedule, init=init, landmarks=lm))
+    return reqs
+
+
+SPECS = [(64, 64, 4), (48, 40, 2), (64, 48, 8)]
+KW = dict(max_width=64, max_height=64, max_spp=8)
+
+
+def _compare(native, python, names):
+    for got, ref in zip(native, python):
+        assert got.failed is None and ref.failed is None
+        assert got.native_id == ref.rid
+        assert got.final_loss == pytest.approx(ref.final_loss, rel=1e-12)
+        for n in names:
+            a, b = got.params[n], np.asarray(ref.params[n]).reshape(got.params[n].shape)
+            assert np.array_equal(a, b), (ref.rid, n, float(np.abs(a.astype(np.float64) - b).max()))
+
+
+def test_full_pipeline_matches_the_python_server():
+    """Landmark initialisation, Stage I with the statistical albedo (batched
+    morph and transpose) and the landmark term, Stage II: three requests of
+    different sizes and sample counts in one native batch against the Python
+    server's."""
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("c1", albedo_k=8)
+    sched = optim.Schedule(stage1=3, stage2=2, init=2)
+    ref = serve.Server(sc, max_slots=4, **KW).run(_requests(sc, SPECS, sched, landmarks=True))
+    ns = serve.NativeServer(sc, max_slots=3, **KW)
+    try:
+        got = ns.run(_requests(sc, SPECS, sched, landmarks=True))
+        assert ns.stats["max_active"] >= 2
+    finally:
+        ns.close()
+    _compare(got, ref, ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness"))
+
+
+def test_light_stage_geometry_matches_the_python_server():
+    """Stage I with the virtual light stage's geometry (d, a, p) free."""
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("tiny", light_stage="ico")
+    specs = [(24, 24, 2), (20, 16, 4)]
+    sched = optim.Schedule(stage1=4, stage2=1)
+    ref = serve.Server(sc, max_slots=2, max_width=24, max_height=24, max_spp=4).run(
+        _requests(sc, specs, sched, stage_geometry=True))
+    ns = serve.NativeServer(sc, max_slots=2, max_width=24, max_height=24, max_spp=4)
+    try:
+        got = ns.run(_requests(sc, specs, sched, stage_geometry=True))
+    finally:
+        ns.close()
+    _compare(got, ref, ("coef", "rot", "trans", "light_i", "light_d", "light_a", "light_p", "diffuse"))
+    assert not np.array_equal(got[0].params["light_d"], synth.with_stage_geometry(sc, synth.init_params(sc)).light_d)
+
+
+def test_slots_and_memory_cap_bound_admission():
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("c1")
+    sched = optim.Schedule(2, 1)
+    specs = [(64, 64, 4)] * 4
+    one = serve.NativeServer(sc, max_slots=4, mem_cap_bytes=1, **KW)     # only the first fits at a time
+    try:
+        reqs = one.run(_requests(sc, specs, sched))
+        assert one.stats["max_active"] == 1 and all(r.final_loss is not None for r in reqs)
+        single = one.stats["peak_bytes"]
+    finally:
+        one.close()
+    two = serve.NativeServer(sc, max_slots=2, mem_cap_bytes=int(2.5 * single), **KW)
+    try:
+        two.run(_requests(sc, specs, sched))
+        assert two.stats["max_active"] == 2 and two.stats["peak_bytes"] <= 2.5 * single
+    finally:
+        two.close()
+
+
+def test_requests_that_cannot_run_fail_alone():
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("c1")
+    sched = optim.Schedule(1, 1)
+    reqs = _requests(sc, [(64, 64, 4), (32, 32, 2), (32, 32, 2)], sched)
+    reqs[0].target = np.zeros((128, 128, 3), np.float32)          # above the server's image size
+    reqs[2].spp = 16                                              # above the server's sample count
+    ns = serve.NativeServer(sc, max_slots=2, **KW)
+    try:
+        ns.run(reqs)
+    finally:
+        ns.close()
+    assert "larger" in reqs[0].failed and "spp" in reqs[2].failed
+    assert reqs[1].failed is None and np.isfinite(reqs[1].final_loss)
