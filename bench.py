@@ -287,6 +287,24 @@ def gpu_arm(args, rank, world):
     return out
 
 
+def _serving_summary(serve, srv, reqs):
+    lat = serve.latency_stats(reqs)
+    if hasattr(srv, "batch_sizes"):
+        steps, mean_batch = srv.steps, float(np.mean(srv.batch_sizes))
+    else:                                   # the library's native server
+        steps = int(srv.stats["steps"])
+        mean_batch = srv.stats["item_steps"] / max(steps, 1)
+    return dict(faces_per_s=len(reqs) / srv.elapsed, elapsed_s=srv.elapsed, p50_s=lat["p50_s"], p99_s=lat["p99_s"],
+                mean_final_loss=float(np.mean([q.final_loss for q in reqs])), mean_batch=mean_batch, steps=steps)
+
+
+def _close_server(srv):
+    if hasattr(srv, "batch_sizes"):
+        srv.r.close()
+    else:
+        srv.close()
+
+
 def serving_bench(n_requests, iters, rate, seed=0):
     """Served (continuous batching, BF16 tensor-core morph, 8 slots) vs plain (one
     face at a time, FP32 morph) on the same Poisson stream of two-stage
@@ -316,24 +334,24 @@ def serving_bench(n_requests, iters, rate, seed=0):
 
     out = {}
     for name, mk in (("served", lambda: serve.Server(sc, max_slots=8, max_width=256, max_height=256, max_spp=16)),
+                     ("native", lambda: serve.NativeServer(sc, max_slots=8, max_width=256, max_height=256,
+                                                           max_spp=16, keep_params=False)),
                      ("plain", lambda: serve.Server(sc, max_slots=1, flags=0, max_width=256, max_height=256,
                                                     max_spp=16))):
         srv = mk()
         reqs = srv.run(stream())
-        lat = serve.latency_stats(reqs)
-        out[name] = dict(faces_per_s=len(reqs) / srv.elapsed, elapsed_s=srv.elapsed, p50_s=lat["p50_s"],
-                         p99_s=lat["p99_s"], mean_final_loss=float(np.mean([q.final_loss for q in reqs])),
-                         mean_batch=float(np.mean(srv.batch_sizes)))
-        srv.r.close()
+        out[name] = _serving_summary(serve, srv, reqs)
+        _close_server(srv)
         torch.cuda.synchronize()
     out["faces_per_s_speedup"] = out["served"]["faces_per_s"] / out["plain"]["faces_per_s"]
+    out["native_faces_per_s_speedup"] = out["native"]["faces_per_s"] / out["plain"]["faces_per_s"]
     out["final_loss_ratio"] = out["served"]["mean_final_loss"] / out["plain"]["mean_final_loss"]
     out["workload"] = ("%d Poisson requests (rate %.0f/s), sizes {128,192,256}^2, spp {4,8,16}, %d+%d "
                        "iterations, 35,709-vertex face, 40 lights" % (n_requests, rate, iters, iters))
     return out
 
 
-def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slots=8):
+def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slots=8, c4_native=True):
     """The serving workload: a Poisson stream of two-stage reconstructions of
     the paper-scale face (35,709 vertices, 40 lights, 512^2 textures, a
     statistical albedo model of 80 + 80 columns, 68 landmarks) with image
@@ -372,9 +390,10 @@ def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slot
         return [serve.Request(rid=k, target=targets[k], spp=int(spps[k]), schedule=sched, arrival=float(arrivals[k]),
                               init=synth.init_params(sc), landmarks=marks[k]) for k in range(n_requests)]
 
-    def server(slots, flags):
-        return serve.Server(sc, max_slots=slots, flags=flags, max_width=512, max_height=512, max_spp=32,
-                            eval_spp=32, keep_params=False, mem_cap_bytes=64 << 30)
+    def server(slots, flags, native=False):
+        cls = serve.NativeServer if native else serve.Server
+        return cls(sc, max_slots=slots, flags=flags, max_width=512, max_height=512, max_spp=32,
+                   eval_spp=32, keep_params=False, mem_cap_bytes=64 << 30)
 
     # closed-loop capacity of the served form on a prefix (all arrive at once)
     n_cap = min(n_requests, 2 * max_slots)
@@ -388,14 +407,15 @@ def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slot
                        "iterations, 35,709-vertex face, 40 lights, statistical albedo 80+80, 68 landmarks"
                        % (n_requests, init, stage1, stage2),
            "closed_loop_capacity_faces_per_s": capacity, "arrival_rate_per_s": rate}
-    for name, slots, flags in (("served", max_slots, facert.FLAG_MORPH_BF16), ("plain", 1, 0)):
-        srv = server(slots, flags)
+    for name, slots, flags, native in (("served", max_slots, facert.FLAG_MORPH_BF16, False),
+                                       ("native", max_slots, facert.FLAG_MORPH_BF16, True),
+                                       ("plain", 1, 0, False)):
+        if native and not c4_native:
+            continue
+        srv = server(slots, flags, native)
         reqs = srv.run(stream(arrivals))
-        lat = serve.latency_stats(reqs)
-        out[name] = dict(faces_per_s=len(reqs) / srv.elapsed, elapsed_s=srv.elapsed, p50_s=lat["p50_s"],
-                         p99_s=lat["p99_s"], mean_final_loss=float(np.mean([q.final_loss for q in reqs])),
-                         mean_batch=float(np.mean(srv.batch_sizes)), steps=srv.steps)
-        srv.r.close()
+        out[name] = _serving_summary(serve, srv, reqs)
+        _close_server(srv)
         torch.cuda.synchronize()
     out["faces_per_s_speedup"] = out["served"]["faces_per_s"] / out["plain"]["faces_per_s"]
     out["final_loss_ratio"] = out["served"]["mean_final_loss"] / out["plain"]["mean_final_loss"]
