@@ -49,7 +49,7 @@ def test_records_and_radiance_at_sampled_pixels(c2):
     gt = tri_np[pix]
     gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp)[pix]
     agree = (gt == ot) & (gm == om)
-    assert np.mean(~agree) <= 2e-3, int(np.sum(~agree))
+    assert np.mean(~agree) <= 1e-4, int(np.sum(~agree))
     ok = agree.all(axis=1)
     g = img.cpu().numpy().reshape(-1, 3)[pix]
     o = oi.reshape(-1, 3)[pix]

@@ -137,7 +137,7 @@ def test_forward_parity(name):
     r = _renderer(sc)
     dp = r.device_params(pr)
     g, o, agree, px_ok = _records_and_image(sc, pr, r, dp, iteration=3)
-    assert np.mean(~agree) <= 1e-3, int(np.sum(~agree))
+    assert np.mean(~agree) <= 1e-4, int(np.sum(~agree))
     scale = 1e-2 * o.mean()
     err = np.abs(g - o) / np.maximum(np.abs(o), scale)
     assert np.max(err[px_ok]) <= 1e-4, np.max(err[px_ok])
@@ -153,7 +153,7 @@ def test_forward_parity_with_lbvh_rebuild(name):
     r = _renderer(sc, flags=facert.FLAG_LBVH)
     dp = r.device_params(pr)
     g, o, agree, px_ok = _records_and_image(sc, pr, r, dp, iteration=3)
-    assert np.mean(~agree) <= 1e-3, int(np.sum(~agree))
+    assert np.mean(~agree) <= 1e-4, int(np.sum(~agree))
     scale = 1e-2 * o.mean()
     err = np.abs(g - o) / np.maximum(np.abs(o), scale)
     assert np.max(err[px_ok]) <= 1e-4, np.max(err[px_ok])
