@@ -228,19 +228,27 @@ FR_D int item_of_block(const BlockMap& m) {
 
 FR_D void set_status(int* status, int bit) { atomicOr(status, bit); }
 
-// Warp-aggregated fixed-point add: lanes sharing `key` sum in lane order, one
-// lane adds the sum.
-FR_D void warp_agg_add(fix64* addr, float val, uint32_t key, uint32_t active) {
+// Warp-aggregated fixed-point add of N values that share one key (the
+// channels of one texel, the coordinates of one vertex): one match over the
+// warp, then each value summed over the lanes sharing the key in lane order,
+// and the sums added to addr[n] by the first of those lanes.
+template <int N>
+FR_D void warp_agg_add_n(fix64* const (&addr)[N], const float (&val)[N], uint32_t key, uint32_t active) {
     const uint32_t peers = __match_any_sync(active, key);
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    // reduce over the peer set by shuffling along the set bits
-    float sum = 0.0f;
+    float sum[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) sum[n] = 0.0f;
     uint32_t m = peers;
     while (m) {
         const int src = __ffs(m) - 1;
-        sum += __shfl_sync(peers, val, src);
+#pragma unroll
+        for (int n = 0; n < N; ++n) sum[n] += __shfl_sync(peers, val[n], src);
         m &= m - 1;
     }
-    if (lane == leader) fix_add(addr, sum);
+    if (lane == __ffs(peers) - 1) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) fix_add(addr[n], sum[n]);
+    }
 }
+

@@ -368,15 +368,9 @@ FR_D void add_vec(fix64* base, int vertex, float3 g, bool on) {
 FR_D void scatter_vertex(fix64* base, int vertex, float3 g, bool on) {
     const unsigned act = __ballot_sync(FULL, on);
     if (!on) return;
-    warp_agg_add(&base[3 * vertex + 0], g.x, (uint32_t)vertex, act);
-    warp_agg_add(&base[3 * vertex + 1], g.y, (uint32_t)vertex, act);
-    warp_agg_add(&base[3 * vertex + 2], g.z, (uint32_t)vertex, act);
-}
-
-FR_D void scatter_texel(fix64* base, int C, int texel, int ch, float g, bool on) {
-    const unsigned act = __ballot_sync(FULL, on);
-    if (!on) return;
-    warp_agg_add(&base[texel * C + ch], g, (uint32_t)texel, act);
+    fix64* const a[3] = {&base[3 * vertex + 0], &base[3 * vertex + 1], &base[3 * vertex + 2]};
+    const float v[3] = {g.x, g.y, g.z};
+    warp_agg_add_n<3>(a, v, (uint32_t)vertex, act);
 }
 
 // One shadow-boundary edge sample at this lane's shading point (edge sampling
@@ -542,19 +536,25 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
                     gl4[3] = F.d * dot(gz, F.dB);
                 }
             }
-            const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
-            if ((threadIdx.x & 31) == 0) {
-                double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc;
-                wa[1 + 3 * j] += (double)sx_;
-                wa[1 + 3 * j + 1] += (double)sy_;
-                wa[1 + 3 * j + 2] += (double)sz_;
-            }
-            if (stage) {                                       // block-uniform
-                float sg[4];
-                for (int q = 0; q < 4; ++q) sg[q] = warp_sum(gl4[q]);
+            // a light no lane of the warp saw adds exact zeros: skip its reductions
+            const bool any = __any_sync(0xffffffffu, gI.x != 0.0f || gI.y != 0.0f || gI.z != 0.0f ||
+                                                         gl4[0] != 0.0f || gl4[1] != 0.0f || gl4[2] != 0.0f ||
+                                                         gl4[3] != 0.0f);
+            if (any) {
+                const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
                 if ((threadIdx.x & 31) == 0) {
-                    double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc + 1 + 3 * S.NL + 4 * j;
-                    for (int q = 0; q < 4; ++q) wa[q] += (double)sg[q];
+                    double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc;
+                    wa[1 + 3 * j] += (double)sx_;
+                    wa[1 + 3 * j + 1] += (double)sy_;
+                    wa[1 + 3 * j + 2] += (double)sz_;
+                }
+                if (stage) {                                   // block-uniform
+                    float sg[4];
+                    for (int q = 0; q < 4; ++q) sg[q] = warp_sum(gl4[q]);
+                    if ((threadIdx.x & 31) == 0) {
+                        double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc + 1 + 3 * S.NL + 4 * j;
+                        for (int q = 0; q < 4; ++q) wa[q] += (double)sg[q];
+                    }
                 }
             }
         }
@@ -633,25 +633,41 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
         const float f = P.focal[0];
         gfocal = -(gd.x * ss.d.x + gd.y * ss.d.y) / f;
     }
-    scatter_vertex(G.d_v, fc.x, gv0, on);
-    scatter_vertex(G.d_v, fc.y, gv1, on);
-    scatter_vertex(G.d_v, fc.z, gv2, on);
-    scatter_vertex(G.d_n, fc.x, gn0, on);
-    scatter_vertex(G.d_n, fc.y, gn1, on);
-    scatter_vertex(G.d_n, fc.z, gn2, on);
-    // bilinear texture scatter (4 taps), warp-aggregated by texel
+    // vertex position and normal gradients, warp-aggregated by vertex
+    {
+        const unsigned act = __ballot_sync(FULL, on);
+        if (on) {
+            const int vx[3] = {fc.x, fc.y, fc.z};
+            const float3 gvv[3] = {gv0, gv1, gv2}, gnn[3] = {gn0, gn1, gn2};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                fix64* const a[6] = {&G.d_v[3 * vx[k]], &G.d_v[3 * vx[k] + 1], &G.d_v[3 * vx[k] + 2],
+                                     &G.d_n[3 * vx[k]], &G.d_n[3 * vx[k] + 1], &G.d_n[3 * vx[k] + 2]};
+                const float v[6] = {gvv[k].x, gvv[k].y, gvv[k].z, gnn[k].x, gnn[k].y, gnn[k].z};
+                warp_agg_add_n<6>(a, v, (uint32_t)vx[k], act);
+            }
+        }
+    }
+    // bilinear texture scatter (4 taps), warp-aggregated by texel: the 3 diffuse,
+    // 3 specular and 1 roughness channels of a tap together
     const bool tex_on = on && interior;
     const size_t M2 = (size_t)S.M * S.M;
     const int taps[4] = {ss.tap.i00, ss.tap.i10, ss.tap.i01, ss.tap.i11};
     const float tw[4] = {(1.0f - ss.tap.fx) * (1.0f - ss.tap.fy), ss.tap.fx * (1.0f - ss.tap.fy),
                          (1.0f - ss.tap.fx) * ss.tap.fy, ss.tap.fx * ss.tap.fy};
+    {
+        const unsigned act = __ballot_sync(FULL, tex_on);
+        if (tex_on) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        for (int ch = 0; ch < 3; ++ch) {
-            scatter_texel(G.tex, 3, taps[k], ch, gtex[ch] * tw[k], tex_on);
-            scatter_texel(G.tex + 3 * M2, 3, taps[k], ch, gtex[3 + ch] * tw[k], tex_on);
+            for (int k = 0; k < 4; ++k) {
+                const size_t t3 = 3 * (size_t)taps[k];
+                fix64* const a[7] = {&G.tex[t3], &G.tex[t3 + 1], &G.tex[t3 + 2], &G.tex[3 * M2 + t3],
+                                     &G.tex[3 * M2 + t3 + 1], &G.tex[3 * M2 + t3 + 2], &G.tex[6 * M2 + taps[k]]};
+                const float v[7] = {gtex[0] * tw[k], gtex[1] * tw[k], gtex[2] * tw[k], gtex[3] * tw[k],
+                                    gtex[4] * tw[k], gtex[5] * tw[k], gtex[6] * tw[k]};
+                warp_agg_add_n<7>(a, v, (uint32_t)taps[k], act);
+            }
         }
-        scatter_texel(G.tex + 6 * M2, 1, taps[k], 0, gtex[6] * tw[k], tex_on);
     }
     const float gf_w = warp_sum(gfocal);
     if ((threadIdx.x & 31) == 0) acc_dyn[(threadIdx.x >> 5) * n_acc] += (double)gf_w;

@@ -337,10 +337,13 @@ struct fr_server {
 
     // One iteration of every admitted request.  Returns "" or what failed.
     std::string step() {
+        std::vector<Request*> run;                      // requests with iterations left
         for (Request* r : active)
+            if (!r->done()) run.push_back(r);
+        for (Request* r : run)
             if (!begin_step(*r)) return "enqueueing the start of a step failed";
         std::vector<Request*> rend, stat;
-        for (Request* r : active)
+        for (Request* r : run)
             if (r->stage() > 0) {
                 rend.push_back(r);
                 if (r->stage() == 1 && info.have_albedo) stat.push_back(r);
@@ -378,7 +381,7 @@ struct fr_server {
             if (fr_albedo_adjoint(ctx, (int)stat.size(), gd.data(), gsp.data(), gb.data(), gc.data(), st) != FR_OK)
                 return std::string("albedo adjoint: ") + fr_last_error(ctx);
         }
-        for (Request* r : active)
+        for (Request* r : run)
             if (r->landmarks && r->stage() <= 1) {
                 const fr_params p = params(*r);
                 fr_grads g = grads(*r);
@@ -386,7 +389,7 @@ struct fr_server {
                     return std::string("landmark loss: ") + fr_last_error(ctx);
             }
         std::vector<fr_opt_group> gr;
-        for (Request* r : active) groups(*r, gr);
+        for (Request* r : run) groups(*r, gr);
         for (size_t k = 0; k < gr.size(); k += FR_MAX_OPT_GROUPS) {
             const int n = (int)std::min<size_t>(FR_MAX_OPT_GROUPS, gr.size() - k);
             if (fr_adam(gr.data() + k, n, 1, ADAM_B1, ADAM_B2, ADAM_EPS, nullptr, st) != FR_OK)
@@ -395,9 +398,11 @@ struct fr_server {
         const fr_status s = fr_sync_status(ctx, st);
         if (s != FR_OK) return std::string("device status after a step: ") + fr_last_error(ctx);
         std::lock_guard<std::mutex> lk(mu);
-        for (Request* r : active) r->it++;
-        stats.steps++;
-        stats.item_steps += (int64_t)active.size();
+        for (Request* r : run) r->it++;
+        if (!run.empty()) {
+            stats.steps++;
+            stats.item_steps += (int64_t)run.size();
+        }
         return "";
     }
 

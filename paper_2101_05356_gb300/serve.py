@@ -107,22 +107,24 @@ class Server:
 
     # ---- one step for every admitted request ------------------------------
     def _step(self):
-        for _, st in self.active:
+        run = [st for _, st in self.active if not st.done]         # requests with iterations left
+        for st in run:
             st.begin_step()
-        states = [st for _, st in self.active if st.stage > 0]     # stage 0: landmarks only, no render
+        states = [st for st in run if st.stage > 0]                 # stage 0: landmarks only, no render
         if states:
             optim.albedo_morph(self.r, states)
             facert.fr_render_batch(self.r.ctx, [st.item(self.edge_spp) for st in states])
             optim.albedo_adjoint(self.r, states)
-        for _, st in self.active:
+        for st in run:
             st.landmark_term(self.r)
-        groups = [g for _, st in self.active for g in st.groups()]
+        groups = [g for st in run for g in st.groups()]
         for k in range(0, len(groups), facert_max_groups()):
             facert.fr_adam(groups[k:k + facert_max_groups()])
-        for _, st in self.active:
+        for st in run:
             st.it += 1
-        self.steps += 1
-        self.batch_sizes.append(len(self.active))
+        if run:
+            self.steps += 1
+            self.batch_sizes.append(len(run))
 
     def _finish(self, now):
         torch = self.torch

@@ -122,3 +122,22 @@ def test_requests_that_cannot_run_fail_alone():
         ns.close()
     assert "larger" in reqs[0].failed and "spp" in reqs[2].failed
     assert reqs[1].failed is None and np.isfinite(reqs[1].final_loss)
+
+
+def test_a_request_without_iterations_is_evaluated_at_its_initial_parameters():
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("c1")
+    reqs = _requests(sc, [(32, 32, 2), (32, 32, 2)], optim.Schedule(0, 0))
+    reqs[1].schedule = optim.Schedule(1, 0)
+    ns = serve.NativeServer(sc, max_slots=2, **KW)
+    try:
+        got = ns.run(reqs)
+    finally:
+        ns.close()
+    ref = serve.Server(sc, max_slots=2, **KW).run(_requests(sc, [(32, 32, 2), (32, 32, 2)], optim.Schedule(0, 0))[:1])
+    init = synth.init_params(sc)
+    for n in ("coef", "rot", "trans", "diffuse"):
+        assert np.array_equal(got[0].params[n], np.asarray(getattr(init, n), np.float32).reshape(got[0].params[n].shape))
+        assert np.array_equal(ref[0].params[n].reshape(got[0].params[n].shape), got[0].params[n])
+    assert got[0].final_loss == pytest.approx(ref[0].final_loss, rel=1e-12)
+    assert not np.array_equal(got[1].params["coef"], got[0].params["coef"])
