@@ -82,7 +82,7 @@ typedef struct fr_config {
     int32_t edge_spp;        /* primary-edge samples per pixel (0..64) */
     uint32_t flags;          /* FR_FLAG_* */
     uint32_t seed;           /* Philox key word 0 */
-    int32_t max_batch;       /* faces per fr_render_batch call, 0..32 (0 means 1); each gets a slot
+    int32_t max_batch;       /* faces per fr_render_batch call, 0..64 (0 means 1); each gets a slot
                                 of scratch sized for width x height pixels */
 } fr_config;
 

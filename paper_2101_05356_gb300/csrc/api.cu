@@ -56,7 +56,7 @@ struct LinearModel {
     float* mean = nullptr;
     float* basis = nullptr;
     uint16_t* tiles = nullptr;           // [ceil(rows / 128)][128][Kp] BF16, no-swizzle K-major core matrices
-    uint16_t* coef_tile = nullptr;       // BF16 [32][Kp] gathered coefficients
+    uint16_t* coef_tile = nullptr;       // BF16 [64][Kp] gathered coefficients
     double* part = nullptr;              // [FR_MAX_BATCH][K][linear_adj_chunks(rows)]
 };
 
@@ -329,7 +329,7 @@ fr_status upload_model(fr_ctx* c, LinearModel& m, int rows, int K, const float* 
             }
         }
     TRY(dalloc(c, &m.tiles, bt.size()));
-    TRY(dalloc(c, &m.coef_tile, (size_t)32 * m.Kp));
+    TRY(dalloc(c, &m.coef_tile, (size_t)morph_tc_coef_tile_elems(m.Kp)));
     CK(c, cudaMemcpy(m.tiles, bt.data(), sizeof(uint16_t) * bt.size(), cudaMemcpyHostToDevice));
     return FR_OK;
 }

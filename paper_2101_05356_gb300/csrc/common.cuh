@@ -179,7 +179,7 @@ struct EdgeLists {
     int* light_count;    // [NL]
 };
 
-constexpr int FR_MAX_BATCH = 32;
+constexpr int FR_MAX_BATCH = 64;
 
 // Everything one face of a batched call needs: its slot's geometry and scratch,
 // its image configuration, its parameters and where its results go.  The table

@@ -20,9 +20,13 @@ FR_D void euler_R(const float* rot, float R[9]) {
     R[6] = -sy;     R[7] = cy * sx;                R[8] = cy * cx;
 }
 
+// Items per k_set_items launch: 32 x 632-byte items stay under the 32 KB
+// kernel-parameter limit.
+constexpr int ITEMS_PER_LAUNCH = 32;
+
 struct ItemsParam {
     int n;
-    DevItem it[FR_MAX_BATCH];
+    DevItem it[ITEMS_PER_LAUNCH];
 };
 
 __global__ void k_set_items(ItemsParam p, DevItem* out) {
@@ -329,11 +333,14 @@ int nb(long n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 void launch_set_items(const DevItem* host_items, int n, DevItem* dev_items, cudaStream_t st) {
-    ItemsParam p;
-    p.n = n;
-    for (int k = 0; k < n; ++k) p.it[k] = host_items[k];
-    k_set_items<<<1, 256, 0, st>>>(p, dev_items);
-    fr_count_launches(1);
+    // the table travels as kernel parameters, ITEMS_PER_LAUNCH items per launch
+    for (int k0 = 0; k0 < n; k0 += ITEMS_PER_LAUNCH) {
+        ItemsParam p;
+        p.n = std::min(ITEMS_PER_LAUNCH, n - k0);
+        for (int k = 0; k < p.n; ++k) p.it[k] = host_items[k0 + k];
+        k_set_items<<<1, 256, 0, st>>>(p, dev_items + k0);
+        fr_count_launches(1);
+    }
 }
 
 void launch_zero_accumulators(const DevItem* items, int n, int N, int M, cudaStream_t st) {

@@ -27,7 +27,7 @@ def _exact(sc, pr):
     return v
 
 
-@pytest.mark.parametrize("name,nfaces", [("c1", 3), ("c2", 5), ("c1", 32)])
+@pytest.mark.parametrize("name,nfaces", [("c1", 3), ("c2", 5), ("c1", 32), ("c1", 33), ("c1", 64), ("c2", 64)])
 def test_tensor_core_morph_within_bf16_bound(name, nfaces):
     from paper_2101_05356_gb300 import facert
     sc = synth.make_scene(name)
