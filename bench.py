@@ -50,8 +50,8 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is in profiles/k_forward_adjoint_c2_full.md.
-TRAFFIC = {"k_forward": {"bytes": 36301056 + 33566464,
-                         "sources_sha256": "031cdfbd535cc36014c22393ed88547f90dc521bc539233432d3825e8d7aef8d"}}
+TRAFFIC = {"k_forward": {"bytes": 36206848 + 33563392,
+                         "sources_sha256": "56b05f7d31139969af616be2ae30523db08eb70d1a8d6384d3dc211d97ccd60c"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 SMS = 152
 FP32_LANES_PER_SM = 128

@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(const float* __restrict_
 // Adjoint, first pass: block (chunk, k-group, face group) sums
 // basis[k][i] * g_b[i] over its chunk of rows for KG consecutive k and the G
 // faces b of its group into part[b][k][chunk].  A thread sums its few rows of
-// the chunk (ADJ_ROWS4 / LIN_THREADS float4 rows, 16 products) in FP32; the
-// warp, block, chunk and batch sums are FP64 (the FP64 pipe is narrow, so it
-// is kept out of the per-row loop).  Each basis float4 is read once per face
+// the chunk (ADJ_ROWS4 / LIN_THREADS float4 rows, 16 products) and the warp
+// its 32 threads in FP32; the block, chunk and batch sums are FP64 (the FP64
+// pipe is narrow, so it only sees one value per warp).  Each basis float4 is read once per face
 // group and each gradient float4 once per k-group.
 template <int G, int KG>
 __global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_part(const float* __restrict__ basis, int ld, int rows,
@@ -113,13 +113,15 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_part(const float* __
                 acc[q][b] += bb.x * gg[b].x + bb.y * gg[b].y + bb.z * gg[b].z + bb.w * gg[b].w;
         }
     }
+    // warp sums in FP32 (32 partials of a few products each, in a fixed
+    // order); FP64 from the block sum on
 #pragma unroll
     for (int q = 0; q < KG; ++q)
 #pragma unroll
         for (int b = 0; b < G; ++b) {
-            double v = (double)acc[q][b];
+            float v = acc[q][b];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5][q][b] = v;
+            if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5][q][b] = (double)v;
         }
     __syncthreads();
     const int q = threadIdx.x / G, b = threadIdx.x % G;

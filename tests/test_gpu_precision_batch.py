@@ -90,6 +90,8 @@ def test_64_face_batch_per_result_error(name):
     print("%s x %d: morph worst error / BF16 bound %.3f; image rel. error vs FP64 oracle on face pixels: median %.2e, "
           "99th pct %.2e; loss vs FP32 morph %.2e; coef gradient vs FP32 morph %.2e"
           % (name, N_FACES, worst, np.median(rel), np.percentile(rel, 99), max(dl), max(dg)))
-    assert np.median(rel) <= 1e-4
+    # the BF16 morph moves every vertex by up to 2^-7 sum_k |c_k||B_ki| (pinned above), so the image
+    # differs from the FP64-morph oracle by more than the FP32 path's 1e-4: report it, bound it loosely
+    assert np.median(rel) <= 1e-3
     assert max(dl) <= 1e-3
     assert max(dg) <= 0.5           # edge-sampling estimates differ where a silhouette flips
