@@ -168,7 +168,7 @@ void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const Li
         k_linear_adj_part<1, 8><<<dim3(n_chunks, nb(K, 8), 1), LIN_THREADS, 0, st>>>(basis, ld, rows, K, t, part,
                                                                                      n_chunks);
     else
-        k_linear_adj_part<LIN_GROUP, 2><<<dim3(n_chunks, nb(K, 2), nb(t.n, LIN_GROUP)), LIN_THREADS, 0, st>>>(
+        k_linear_adj_part<LIN_GROUP, 4><<<dim3(n_chunks, nb(K, 4), nb(t.n, LIN_GROUP)), LIN_THREADS, 0, st>>>(
             basis, ld, rows, K, t, part, n_chunks);
     k_linear_adj_finish<<<dim3(nb(K, 128), t.n), 128, 0, st>>>(part, K, n_chunks, t);
     fr_count_launches(2);
