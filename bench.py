@@ -147,6 +147,20 @@ def make_workload(face_seed):
     return sc, params, target_params
 
 
+def job_totals(total_ms, units, world, device="cuda"):
+    """Whole-job totals of the replicas: the slowest rank's timed milliseconds
+    (max over ranks) and the units every rank processed (sum over ranks)."""
+    if world <= 1:
+        return float(total_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms), float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def gpu_arm(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -207,14 +221,7 @@ def gpu_arm(args, rank, world):
     status = r.status()
     total_ms = float(np.sum(times))
     rays = sum(v["rays"] for v in cnt.values())
-    if world > 1:
-        t = torch.tensor([total_ms, float(rays)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, rays_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_max, rays_all = total_ms, float(rays)
+    total_ms_max, rays_all = job_totals(total_ms, rays, world, "cuda")
     value = rays_all / (total_ms_max / 1000.0)
 
     # ---- dominant kernel roofline ----
