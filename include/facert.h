@@ -296,6 +296,13 @@ fr_status fr_debug_records(fr_ctx* ctx, const fr_params* p, float* image, int32_
                            uint64_t* mask_rec, uint32_t iteration, uint32_t face_id,
                            void* stream);
 
+/* The bounded-wait error path without a fault: one CTA waits on an mbarrier
+ * that nothing completes, with the poll loop of the tensor-core morph's
+ * waits, gives up after `polls` polls (1..2^22) and sets the status word, so
+ * the next fr_sync_status returns FR_ETIMEOUT and clears it; the context
+ * stays usable. */
+fr_status fr_debug_wait_timeout(fr_ctx* ctx, uint32_t polls, void* stream);
+
 /* Ordered silhouette lists after a forward pass for p: prim [E] primary
  * silhouette edge ids, n_prim [1]; per_light [N_L][E] shadow candidates,
  * counts [N_L] (all device int32). */
@@ -401,8 +408,10 @@ fr_status fr_adam(const fr_opt_group* groups, int32_t n_groups, int32_t step, fl
  * over every request's parameter groups (the same groups, learning rates and
  * weights as Sec. 5 gives).  A request's parameters, Adam moments and buffers
  * stay on the device, in one allocation made at admission, until it finishes;
- * its final photometric loss is then evaluated with a fixed Philox iteration,
- * its parameters optionally copied to the host, and its memory freed.  Philox
+ * its final photometric loss is then evaluated with a fixed Philox iteration
+ * (a request whose loss or parameters are not finite, e.g. from NaN initial
+ * parameters, ends FAILED), its parameters optionally kept on the host, and
+ * its memory freed.  Philox
  * streams are keyed by the request id (the face id) and the request's own
  * iteration, so a request's result does not depend on what it was batched
  * with.  The paper serves nothing; this is the serving form of its method. */
@@ -484,6 +493,13 @@ fr_status fr_poll(fr_server* srv, uint64_t id, fr_result* out, const fr_grads* p
 fr_status fr_server_wait(fr_server* srv, double timeout_s);
 
 fr_status fr_server_get_stats(fr_server* srv, fr_server_stats* out);
+
+/* Cancel request id: a queued request becomes FAILED ("cancelled") at once; a
+ * running one is retired at the next step boundary (its device state freed,
+ * no final evaluation) as FAILED ("cancelled").  Other requests are not
+ * affected.  Returns FR_OK, or FR_EINVAL for an unknown id or one already
+ * DONE or FAILED. */
+fr_status fr_cancel(fr_server* srv, uint64_t id);
 
 /* Stop the worker (requests still queued or running are dropped), free every
  * request's device state and the stream.  The context stays the caller's. */

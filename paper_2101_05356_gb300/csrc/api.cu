@@ -855,6 +855,13 @@ fr_status fr_set_flags(fr_ctx* c, uint32_t flags) {
     return FR_OK;
 }
 
+fr_status fr_debug_wait_timeout(fr_ctx* c, uint32_t polls, void* stream) {
+    if (!c || polls < 1 || polls > (1u << 22)) return fail(c, FR_EINVAL, "1 <= polls <= 2^22");
+    launch_wait_probe(polls, c->status, S_(stream));
+    CK(c, cudaGetLastError());
+    return FR_OK;
+}
+
 fr_status fr_sync_status(fr_ctx* c, void* stream) {
     if (!c) return fail(nullptr, FR_EINVAL, "null context");
     CK(c, cudaStreamSynchronize(S_(stream)));

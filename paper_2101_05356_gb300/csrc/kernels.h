@@ -46,6 +46,7 @@ void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const Li
 // (tiles: the basis as [ceil(rows / 128)][128][Kp] BF16 operand tiles)
 int morph_tc_smem_bytes(int Kp);
 int morph_tc_coef_tile_elems(int Kp);
+void launch_wait_probe(unsigned limit, int* status, cudaStream_t st);
 void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int rows,
                       const LinearTable& t, int* status, cudaStream_t st);
 

@@ -49,9 +49,9 @@ FR_D void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-FR_D bool mbar_wait(uint64_t* bar, uint32_t parity) {
+FR_D bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit = SPIN_LIMIT) {
     const uint32_t a = smem_u32(bar);
-    for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -170,6 +170,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restr
     }
 }
 
+// The bounded-wait error path on its own: one CTA waits on an mbarrier that
+// nothing arrives at, gives up after `limit` polls with the same loop as the
+// morph kernel's waits, and reports FR_STATUS_TIMEOUT.
+__global__ void k_wait_probe(unsigned limit, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, limit);
+    if (!ok && threadIdx.x == 0) set_status(status, FR_STATUS_TIMEOUT);
+}
+
 FR_D uint16_t bf16_rne(float f) {
     uint32_t u = __float_as_uint(f);
     u += 0x7FFFu + ((u >> 16) & 1u);
@@ -207,4 +221,9 @@ void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile,
         k_morph_tc<64><<<n_tiles, TC_THREADS, smem, st>>>(tiles, Kp, coef_tile, mean, rows, t, status);
     }
     fr_count_launches(2);
+}
+
+void launch_wait_probe(unsigned limit, int* status, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(limit, status);
+    fr_count_launches(1);
 }

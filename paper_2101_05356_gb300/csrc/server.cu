@@ -20,6 +20,7 @@
 // iteration, so a request's result does not depend on its batch.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -74,6 +75,7 @@ struct Request {
     float *d_target = nullptr, *image = nullptr, *ref_d = nullptr, *ref_s = nullptr, *d_lm = nullptr;
     double *loss = nullptr, *land_loss = nullptr;
     bool refs_taken = false;
+    bool cancel = false;                                // set by fr_cancel while running
 
     int stage() const { return it < n_init ? 0 : (it < n_init + s1 ? 1 : 2); }
     bool done() const { return it >= n_init + s1 + s2; }
@@ -338,8 +340,11 @@ struct fr_server {
     // One iteration of every admitted request.  Returns "" or what failed.
     std::string step() {
         std::vector<Request*> run;                      // requests with iterations left
-        for (Request* r : active)
-            if (!r->done()) run.push_back(r);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (Request* r : active)
+                if (!r->done() && !r->cancel) run.push_back(r);
+        }
         for (Request* r : run)
             if (!begin_step(*r)) return "enqueueing the start of a step failed";
         std::vector<Request*> rend, stat;
@@ -408,9 +413,30 @@ struct fr_server {
 
     // Final loss of the finished requests (one batched forward), results, release.
     std::string retire() {
-        std::vector<Request*> fin;
-        for (Request* r : active)
-            if (r->done()) fin.push_back(r);
+        std::vector<Request*> fin, cancelled;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (Request* r : active) {
+                if (r->cancel) cancelled.push_back(r);
+                else if (r->done()) fin.push_back(r);
+            }
+        }
+        // cancelled requests leave at the step boundary without an evaluation
+        for (Request* r : cancelled) {
+            release(*r);
+            std::lock_guard<std::mutex> lk(mu);
+            r->state = FR_REQ_FAILED;
+            r->err = "cancelled";
+            r->t_finish = now_s(t0);
+            used -= r->bytes;
+            finished++;
+        }
+        if (!cancelled.empty()) {
+            active.erase(std::remove_if(active.begin(), active.end(),
+                                        [](Request* r) { return r->state == FR_REQ_FAILED; }),
+                         active.end());
+            idle.notify_all();
+        }
         if (fin.empty()) return "";
         std::vector<fr_item> items;
         for (Request* r : fin)
@@ -424,22 +450,29 @@ struct fr_server {
             double loss = 0.0;
             if (cudaMemcpy(&loss, r->loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
                 return "reading a final loss failed";
-            std::vector<float> keep;
-            if (cfg.keep_params) {
-                keep.resize(r->n_par);
-                if (cudaMemcpy(keep.data(), r->x, sizeof(float) * r->n_par, cudaMemcpyDeviceToHost) != cudaSuccess)
-                    return "reading final parameters failed";
-            }
+            // the final parameters are read back to check them (and kept if asked)
+            std::vector<float> keep(r->n_par);
+            if (cudaMemcpy(keep.data(), r->x, sizeof(float) * r->n_par, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return "reading final parameters failed";
+            bool finite = std::isfinite(loss);
+            for (size_t i = 0; finite && i < keep.size(); ++i) finite = std::isfinite(keep[i]);
+            if (!cfg.keep_params || !finite) keep.clear();
             release(*r);
             std::lock_guard<std::mutex> lk(mu);
             r->final_loss = loss;
             r->out.swap(keep);
-            r->state = FR_REQ_DONE;
+            if (finite) {
+                r->state = FR_REQ_DONE;
+            } else {
+                r->state = FR_REQ_FAILED;
+                r->err = "the final loss or parameters are not finite";
+            }
             r->t_finish = now_s(t0);
             used -= r->bytes;
             finished++;
         }
-        active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->state == FR_REQ_DONE; }),
+        active.erase(std::remove_if(active.begin(), active.end(),
+                                    [](Request* r) { return r->state == FR_REQ_DONE || r->state == FR_REQ_FAILED; }),
                      active.end());
         idle.notify_all();
         return "";
@@ -474,6 +507,7 @@ struct fr_server {
                     const size_t b = layout(*r);
                     if (!(active.empty() && admit.empty()) && planned + b > cfg.mem_cap_bytes) break;
                     queue.pop_front();
+                    r->state = FR_REQ_RUNNING;          // from here fr_cancel flags it instead
                     planned += b;
                     admit.push_back(r);
                 }
@@ -482,7 +516,6 @@ struct fr_server {
                 const bool ok = admit_one(*r);
                 std::lock_guard<std::mutex> lk(mu);
                 if (ok) {
-                    r->state = FR_REQ_RUNNING;
                     r->t_admit = now_s(t0);
                     used += r->bytes;
                     stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, used);
@@ -620,6 +653,25 @@ fr_status fr_poll(fr_server* s, uint64_t id, fr_result* out, const fr_grads* par
             if (params_out->light_a) std::memcpy(params_out->light_a, g + I.NL, sizeof(float) * I.NL);
             if (params_out->light_p) std::memcpy(params_out->light_p, g + 2 * I.NL, sizeof(float) * 2 * I.NL);
         }
+    }
+    return FR_OK;
+}
+
+fr_status fr_cancel(fr_server* s, uint64_t id) {
+    if (!s) return FR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (id >= s->all.size()) return FR_EINVAL;
+    Request* r = s->all[id].get();
+    if (r->state == FR_REQ_DONE || r->state == FR_REQ_FAILED) return FR_EINVAL;
+    if (r->state == FR_REQ_QUEUED) {
+        s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), r), s->queue.end());
+        r->state = FR_REQ_FAILED;
+        r->err = "cancelled";
+        r->t_finish = now_s(s->t0);
+        s->finished++;
+        s->idle.notify_all();
+    } else {
+        r->cancel = true;                              // the worker retires it at the next step boundary
     }
     return FR_OK;
 }

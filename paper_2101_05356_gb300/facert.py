@@ -169,6 +169,8 @@ def lib():
         L.fr_poll.argtypes = [_vp, ctypes.c_uint64, P(FrResult), P(FrGrads)]
         L.fr_server_wait.argtypes = [_vp, ctypes.c_double]
         L.fr_server_get_stats.argtypes = [_vp, P(FrServerStats)]
+        L.fr_cancel.argtypes = [_vp, ctypes.c_uint64]
+        L.fr_debug_wait_timeout.argtypes = [_vp, ctypes.c_uint32, _vp]
         L.fr_server_destroy.argtypes = [_vp]
         L.fr_server_destroy.restype = None
         _lib = L
@@ -574,4 +576,13 @@ def fr_server_get_stats(srv):
 
 def fr_server_destroy(srv):
     lib().fr_server_destroy(srv)
+
+
+def fr_cancel(srv, rid):
+    """Cancel a request; False if it had already finished or the id is unknown."""
+    return lib().fr_cancel(srv, rid) == FR_OK
+
+
+def fr_debug_wait_timeout(ctx, polls):
+    check(lib().fr_debug_wait_timeout(ctx, polls, _stream()), ctx)
 

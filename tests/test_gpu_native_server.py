@@ -141,3 +141,65 @@ def test_a_request_without_iterations_is_evaluated_at_its_initial_parameters():
         assert np.array_equal(ref[0].params[n].reshape(got[0].params[n].shape), got[0].params[n])
     assert got[0].final_loss == pytest.approx(ref[0].final_loss, rel=1e-12)
     assert not np.array_equal(got[1].params["coef"], got[0].params["coef"])
+
+
+def test_cancelled_and_non_finite_requests_fail_alone():
+    """Host-side faults: a request cancelled while queued, one cancelled while
+    running, and one with NaN initial parameters (its final loss is not
+    finite) each fail with their reason; the others' results are bitwise
+    those of the Python server."""
+    import time
+    from paper_2101_05356_gb300 import facert, optim, serve
+    sc = synth.make_scene("c1")
+    specs = [(32, 32, 2)] * 5
+    sched = optim.Schedule(3, 1)
+    reqs = _requests(sc, specs, sched)
+    reqs[2].init.coef[0] = np.nan
+    reqs[3].schedule = optim.Schedule(400, 0)            # long enough to be cancelled while running
+    ns = serve.NativeServer(sc, max_slots=1, **KW)
+    try:
+        ids = [facert.fr_submit(ns.srv, q.target, q.init, q.spp, q.schedule.stage1, q.schedule.stage2)
+               for q in reqs]
+        assert facert.fr_cancel(ns.srv, ids[1])           # queued behind request 0 (one slot)
+        t0 = time.time()
+        while facert.fr_poll(ns.srv, ids[3])[1]["iterations"] < 1 and time.time() - t0 < 120:
+            time.sleep(0.002)
+        assert facert.fr_cancel(ns.srv, ids[3])
+        assert facert.fr_server_wait(ns.srv, 600.0)
+        res = [facert.fr_poll(ns.srv, i, ns._shapes(q.init)) for i, q in zip(ids, reqs)]
+        stats = facert.fr_server_get_stats(ns.srv)
+        assert not facert.fr_cancel(ns.srv, ids[0])       # already done
+    finally:
+        ns.close()
+    assert res[1][1]["state"] == facert.REQ_FAILED and res[1][1]["error"] == "cancelled"
+    assert res[1][1]["iterations"] == 0
+    assert res[2][1]["state"] == facert.REQ_FAILED and "finite" in res[2][1]["error"]
+    assert res[3][1]["state"] == facert.REQ_FAILED and res[3][1]["error"] == "cancelled"
+    assert 0 < res[3][1]["iterations"] < 400
+    assert stats["active"] == 0 and stats["queued"] == 0
+    ok = [0, 4]
+    ref = serve.Server(sc, max_slots=1, **KW).run([_requests(sc, specs, sched)[k] for k in ok])
+    for k, rr in zip(ok, ref):
+        done, r, params = res[k]
+        assert done and r["state"] == facert.REQ_DONE
+        assert r["final_loss"] == pytest.approx(rr.final_loss, rel=1e-12)
+        for n in ("coef", "rot", "trans", "light_i", "diffuse"):
+            assert np.array_equal(params[n], np.asarray(rr.params[n]).reshape(params[n].shape)), (k, n)
+
+
+def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
+    """A device wait that nothing satisfies gives up after its poll limit and
+    reports through the status word (FR_ETIMEOUT, then cleared); renders on
+    the same context afterwards are unchanged."""
+    from paper_2101_05356_gb300 import facert
+    sc = synth.make_scene("tiny")
+    r = facert.Renderer(sc, flags=facert.FLAG_MORPH_BF16)
+    dp = r.device_params(synth.random_params(sc, 2))
+    before = r.forward(dp, iteration=5)
+    facert.fr_debug_wait_timeout(r.ctx, 1 << 12)
+    assert facert.fr_sync_status(r.ctx) == facert.FR_ETIMEOUT
+    assert r.status() == 0                               # read and cleared
+    after = r.forward(dp, iteration=5)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+    assert r.status() == 0
