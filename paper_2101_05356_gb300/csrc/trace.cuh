@@ -1,4 +1,5 @@
-// Ray traversal of the LBVH with a per-thread stack in shared memory, and the
+// Ray traversal of the binary BVH (the mesh's static SAH topology refitted per
+// call, or an LBVH rebuilt per call) with a per-thread stack, and the
 // watertight ray/triangle test of Woop, Benthin and Wald (JCGT 2013): FP32 edge
 // functions, re-evaluated in FP64 when one of them is exactly zero.
 #pragma once
@@ -87,7 +88,8 @@ FR_D void load_node(const BvhNode* nodes, int i, float3& lo0, float3& hi0, float
     c1 = d.y;
 }
 
-// stack: this thread's column of a [FR_STACK][blockDim] shared array.
+// A thread's traversal stack: its own local array (stride 1, the default) or
+// its column of a [FR_STACK][blockDim] shared array.
 struct Stack {
     int* base;
     int stride;
