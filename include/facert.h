@@ -56,6 +56,11 @@ typedef int32_t fr_status;
                                          accumulate, FP32 mean); context-wide, read by every call */
 #define FR_FLAG_RECOMPUTE      256u   /* fused steps re-trace the adjoint's primary and shadow rays
                                          even when the hit records fit (see fr_render) */
+#define FR_FLAG_VIEW_CUTOFF   1024u   /* zero every contribution where the shading normal faces away from
+                                         the camera (n_s . o <= 0), the diffuse term included; by default
+                                         only the specular lobe needs n_s . o > 0.  This cutoff is a
+                                         discontinuity inside triangles that edge sampling does not
+                                         sample, so its gradients miss that curve's motion */
 #define FR_FLAG_LBVH           512u   /* rebuild an LBVH (Morton sort + Karras tree) every call instead
                                          of refitting the SAH topology built from the mean face at
                                          fr_set_mesh; for deformations far from the mean face.

@@ -22,6 +22,7 @@ SRC = os.path.join(HERE, "oracle.cpp")
 LIB = os.path.join(HERE, "liboracle.so")
 
 GGX, SCHLICK_LINEAR, FLAT, DIFFUSE_ONLY = 1, 2, 4, 8
+VIEW_CUTOFF = 1024      # the literal grazing reading: every contribution zero where n_s . o <= 0
 TERM_INTERIOR, TERM_PRIMARY, TERM_SHADOW = 1, 2, 4
 TERM_ALL = 7
 

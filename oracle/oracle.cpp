@@ -17,8 +17,12 @@
 //  * h (Eq. halfVector): (l + o)/|l + o|.
 //  * F (Eq. brdf_f): Schlick's approximation with the fifth power (flag
 //    ORA_SCHLICK_LINEAR gives the printed linear form).
-//  * Contributions vanish unless n.l > 0 and n.o > 0 (the denominator of
-//    Eq. brdf_spec).
+//  * Contributions vanish unless n_s.l > 0; the specular lobe also needs
+//    n_s.o > 0 (the denominator of Eq. brdf_spec); the Lambert term does not
+//    depend on the view.  Surfaces are one-sided: a hit on a triangle whose
+//    geometric normal faces away from the camera reflects nothing.  (Zeroing
+//    every contribution where n_s.o <= 0, flag ORA_VIEW_CUTOFF, would put a
+//    discontinuity inside triangles that edge sampling does not sample.)
 //  * Eq. lightIntensity: emitted radiance L_j = (d_j^2 / a_j) i_j; emitter
 //    geometry is given explicitly in camera space and does not depend on pose.
 //  * One area sample per light per pixel sample (light-area importance
@@ -545,12 +549,15 @@ D smith_g1_ggx(const D& nv, const D& hv, const D& r) {
     return 2.0 * nv / (nv + dsqrt(a2 + (1.0 - a2) * nv * nv));
 }
 
-// f_r for unit n, l, o; returns the RGB BRDF value.  Zero unless n.l > 0, n.o > 0.
+// f_r for unit n, l, o; returns the RGB BRDF value.  Zero unless n.l > 0; the
+// specular part only where n.o > 0.
 void brdf(uint32_t flags, const V3& n, const V3& l, const V3& o, const D c[3], const D s[3],
           const D& r, D out[3]) {
     D nl = dot(n, l), no = dot(n, o);
-    if (!(nl.v > 0.0) || !(no.v > 0.0)) { for (int k = 0; k < 3; ++k) out[k] = D(0.0); return; }
-    if (flags & ORA_DIFFUSE_ONLY) { for (int k = 0; k < 3; ++k) out[k] = c[k] / M_PI; return; }
+    if (!(nl.v > 0.0)) { for (int k = 0; k < 3; ++k) out[k] = D(0.0); return; }
+    // the specular lobe needs n.o > 0 (its denominator and the Delta of Eq. brdf_g1);
+    // the Lambert term does not depend on the view
+    if ((flags & ORA_DIFFUSE_ONLY) || !(no.v > 0.0)) { for (int k = 0; k < 3; ++k) out[k] = c[k] / M_PI; return; }
     V3 h = normalize(l + o);                           // Eq. halfVector (reading)
     D nh = dot(n, h), oh = dot(o, h), lh = dot(l, h);
     D Dterm, G;
@@ -612,6 +619,8 @@ struct SampleOut {
     V3 yd;                      // hit point as duals
     V3 ns;                      // shading normal
     V3 o;                       // view direction
+    bool lit = false;           // the hit is shaded: its triangle faces the camera (and, with
+                                // ORA_VIEW_CUTOFF, n_s . o > 0)
     D cc[3], ss[3], rr;         // albedos at the hit
 };
 
@@ -681,7 +690,14 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
         for (int k = 0; k < 3; ++k) out.L[k] = c[k];
         return;
     }
-    if (!(dot(ns, o).v > 0.0)) return;
+    {
+        // one-sided surfaces: a triangle seen from behind reflects nothing (the change
+        // happens at geometric silhouettes, which the primary-edge term samples)
+        V3 v0 = load(P.v, P.dv, P.nd, t[0]), v1 = load(P.v, P.dv, P.nd, t[1]), v2 = load(P.v, P.dv, P.nd, t[2]);
+        if (!(dot(cross(v1 - v0, v2 - v0), o).v > 0.0)) return;
+    }
+    if ((s->flags & ORA_VIEW_CUTOFF) && !(dot(ns, o).v > 0.0)) return;
+    out.lit = true;
     for (int j = 0; j < P.NL; ++j) {
         const Light& Lj = P.lights[j];
         const double uu = st.u(light_dim0 + 2 * j), vv = st.u(light_dim0 + 2 * j + 1);
@@ -729,7 +745,7 @@ void light_integrand(const Prep& P, const SampleOut& so, int j, const V3& z, D h
     V3 l = lv * (1.0 / dsqrt(dist2));
     D cos_s = dot(so.ns, l);
     D cos_l = -dot(v3c(Lj.n.x, Lj.n.y, Lj.n.z), l);
-    if (!(cos_s.v > 0.0) || !(cos_l.v > 0.0) || !(dot(so.ns, so.o).v > 0.0)) {
+    if (!(cos_s.v > 0.0) || !(cos_l.v > 0.0) || !so.lit) {
         for (int k = 0; k < 3; ++k) h[k] = D(0.0);
         return;
     }
@@ -1064,7 +1080,7 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
                     for (int j = 0; j < P.NL; ++j)
                         for (int k = 0; k < 3; ++k) A.light[3 * j + k] += w[k] * so.dLdi[j][k];
                 }
-                if ((terms & ORA_TERM_SHADOW) && !(s->flags & ORA_FLAT)) {
+                if ((terms & ORA_TERM_SHADOW) && !(s->flags & ORA_FLAT) && so.lit) {
                     Stream se{s->seed, STREAM_EDGE_SHADOW, (uint32_t)pix, (uint32_t)smp, iteration, face_id};
                     shadow_edge_sample(P, so, so.tri, se.u(0), se.u(1), se.u(2), w, A.geo.data(), nullptr,
                                        n_lg ? A.lg.data() : nullptr);
@@ -1205,6 +1221,7 @@ int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
         so.yd = v3c(y[0], y[1], y[2]);
         so.ns = v3c(n[0], n[1], n[2]);
         so.o = v3c(n[0], n[1], n[2]);
+        so.lit = true;
         for (int k = 0; k < 3; ++k) { so.cc[k] = D(1.0); so.ss[k] = zero3[k]; }
         so.rr = D(0.5);
         Stream st{s->seed, seed_stream, (uint32_t)i, 0u, 0u, 0u};

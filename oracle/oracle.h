@@ -20,6 +20,8 @@ extern "C" {
 #define ORA_SCHLICK_LINEAR 2u   /* Fresnel exactly as printed in App. A, without the 5th power */
 #define ORA_FLAT           4u   /* debug: radiance = diffuse albedo at the hit, no lights */
 #define ORA_DIFFUSE_ONLY   8u   /* debug: f_r = c / pi (no specular lobe) */
+#define ORA_VIEW_CUTOFF 1024u   /* every contribution zero where n_s . o <= 0 (the grazing cutoff applied to
+                                   the diffuse term too; its gradient misses that curve's motion) */
 
 /* gradient terms */
 #define ORA_TERM_INTERIOR  1u

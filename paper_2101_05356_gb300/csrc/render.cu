@@ -66,6 +66,8 @@ FR_D Stack my_stack(RtShared& sh) { return Stack{&sh.stack[threadIdx.x], RT_THRE
 
 struct SampleState {
     bool hit;
+    bool lit;          // shaded: the hit triangle faces the camera (and, with the view
+                       // cutoff flag, n_s . o > 0); otherwise it reflects nothing
     int tri;
     float b1, b2;
     float3 d;          // camera ray direction (not normalised)
@@ -86,6 +88,7 @@ template <bool CAN_TRACE = true>
 FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
                         Stack st, SampleState& ss, RayStats& rs, int rec = REC_TRACE) {
     ss.hit = false;
+    ss.lit = false;
     ss.tri = -1;
     if (!active) return;
     const float f = __ldg(P.focal);
@@ -105,6 +108,10 @@ FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, floa
     const float3 m = n0 * b0 + n1 * h.b1 + n2 * h.b2;
     ss.ns = m * (1.0f / length(m));
     ss.o = -ss.d * (1.0f / length(ss.d));
+    // one-sided surfaces: seen from behind, a triangle reflects nothing (that
+    // change happens at geometric silhouettes, which the primary-edge term samples)
+    ss.lit = dot(cross(v1 - v0, v2 - v0), ss.o) > 0.0f &&
+             (!(S.flags & FR_FLAG_VIEW_CUTOFF_D) || dot(ss.ns, ss.o) > 0.0f);
     const float2 t0 = __ldg(&S.uv[fc.x]), t1 = __ldg(&S.uv[fc.y]), t2 = __ldg(&S.uv[fc.z]);
     ss.uv = make_float2(b0 * t0.x + h.b1 * t1.x + h.b2 * t2.x, b0 * t0.y + h.b1 * t1.y + h.b2 * t2.y);
     ss.tap = make_tap(S.M, ss.uv.x, ss.uv.y);
@@ -155,7 +162,7 @@ FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sample
     const int lane = threadIdx.x & 31;
     q.vis[lane] = 0ull;
     __syncwarp();
-    const bool want = ss.hit && dot(ss.ns, ss.o) > 0.0f && !(S.flags & FR_FLAG_FLAT_D);
+    const bool want = ss.hit && ss.lit && !(S.flags & FR_FLAG_FLAT_D);
     int head = 0, count = 0;
     DimCache dc;
     const int j1 = min(S.NL, j0 + 64);
@@ -197,7 +204,7 @@ FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleSta
     const float inv_len = 1.0f / sqrtf(d2);
     const float3 l = lv * inv_len;
     const float cos_s = dot(ss.ns, l), cos_l = -dot(L.n, l);
-    if (!(cos_s > 0.0f) || !(cos_l > 0.0f) || !(dot(ss.ns, ss.o) > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    if (!(cos_s > 0.0f) || !(cos_l > 0.0f) || !ss.lit) return f3(0.0f, 0.0f, 0.0f);
     const float geo = cos_s * cos_l / d2;
     float3 f;
     if (ADJ) {
@@ -558,7 +565,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const
                 }
             }
         }
-        if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit) {
+        if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit && ss.lit) {
             const Sampler sm2{make_uint2(S.seed, FR_STREAM_EDGE_SHADOW), (uint32_t)pixel, (uint32_t)s, iteration, face};
             shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, G.small, my_stack(sh), rs);
         }

@@ -9,6 +9,7 @@
 #define FR_FLAG_NO_INTERIOR_D 16u
 #define FR_FLAG_NO_PRIMARY_EDGE_D 32u
 #define FR_FLAG_NO_SHADOW_EDGE_D 64u
+#define FR_FLAG_VIEW_CUTOFF_D 1024u
 
 // Uniform area sample of an emitter.
 FR_D float3 light_point(const LightDev& L, float u, float v) {
@@ -114,13 +115,19 @@ struct ShadeAdj {
     float r;
 };
 
-// f_r = f_d + f_s (Eq. brdf).  Zero unless n.l > 0 and n.o > 0.  With ADJ,
-// propagates the upstream gradient gf (d/d f_r per channel) into g.
+// f_r = f_d + f_s (Eq. brdf).  Zero unless n.l > 0; the specular lobe only
+// where n.o > 0 (its denominator, Eq. brdf_spec), the Lambert term whatever
+// the view.  With ADJ, propagates the upstream gradient gf (d/d f_r per
+// channel) into g.
 template <bool ADJ>
 FR_D float3 brdf(uint32_t flags, float3 n, float3 l, float3 o, const Material& m, float3 gf,
                  ShadeAdj* g) {
     const float nl = dot(n, l), no = dot(n, o);
-    if (!(nl > 0.0f) || !(no > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    if (!(nl > 0.0f)) return f3(0.0f, 0.0f, 0.0f);
+    if (!(no > 0.0f)) {                                      // Lambert term alone
+        if (ADJ) g->c += gf * (1.0f / FR_PI);
+        return m.c * (1.0f / FR_PI);
+    }
     const float3 hv = l + o;
     const float hlen = length(hv);
     const float3 h = hv * (1.0f / hlen);                     // Eq. halfVector (reading)

@@ -21,6 +21,7 @@ FLAG_NO_INTERIOR, FLAG_NO_PRIMARY_EDGE, FLAG_NO_SHADOW_EDGE = 16, 32, 64
 FLAG_MORPH_BF16 = 128
 FLAG_RECOMPUTE = 256
 FLAG_LBVH = 512
+FLAG_VIEW_CUTOFF = 1024
 
 _vp = ctypes.c_void_p
 

@@ -162,7 +162,7 @@ def test_forward_parity_with_lbvh_rebuild(name):
     assert r.status() == 0
 
 
-@pytest.mark.parametrize("flags", [oracle.GGX, oracle.SCHLICK_LINEAR, oracle.FLAT])
+@pytest.mark.parametrize("flags", [oracle.GGX, oracle.SCHLICK_LINEAR, oracle.FLAT, oracle.VIEW_CUTOFF])
 def test_forward_parity_modes(flags):
     sc, pr = _scene("tiny")
     r = _renderer(sc, flags=flags)       # library flag bits equal the oracle's
