@@ -203,3 +203,30 @@ def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
     torch.cuda.synchronize()
     assert torch.equal(before, after)
     assert r.status() == 0
+
+
+def test_results_are_the_same_alone_and_in_a_batch_of_40():
+    """40 requests advanced together (the tensor-core morph then runs one
+    64-wide MMA over the batch) against the same requests served alone
+    (a 32-wide MMA): each result is bitwise the same."""
+    from paper_2101_05356_gb300 import optim, serve
+    sc = synth.make_scene("tiny")
+    specs = [(24, 24, 2)] * 40
+    sched = optim.Schedule(4, 2)        # long enough for all 40 to be admitted while the first still runs
+    kw = dict(max_width=24, max_height=24, max_spp=2)
+    ns = serve.NativeServer(sc, max_slots=40, mem_cap_bytes=1 << 40, **kw)
+    try:
+        got = ns.run(_requests(sc, specs, sched))
+        assert ns.stats["max_active"] > 32
+    finally:
+        ns.close()
+    for k in (0, 17, 39):
+        lone = serve.NativeServer(sc, max_slots=1, **kw)
+        try:
+            req = _requests(sc, specs, sched)
+            ref = lone.run(req[:k + 1])[k]          # ids 0..k so that request k keeps its face id
+        finally:
+            lone.close()
+        assert got[k].final_loss == ref.final_loss
+        for n in ("coef", "rot", "trans", "light_i", "diffuse", "specular", "roughness"):
+            assert np.array_equal(got[k].params[n], ref.params[n]), (k, n)
