@@ -455,6 +455,57 @@ def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slot
     return out
 
 
+def large_bench(batch=8, steps=2, warmup=1):
+    """The large workload: a batch of `batch` faces of the 100,000-triangle
+    mesh (K = 20), 1024 x 1024, 64 spp, 80 lights, 2048^2 textures, BF16
+    tensor-core morph, one fused forward + loss + adjoint call per step
+    (fr_render_batch); the hit records exceed their budget, so the adjoint
+    re-traces every camera and shadow ray.  Device-resident inputs, CUDA events
+    around each step."""
+    import torch
+
+    from paper_2101_05356_gb300 import facert, synth
+    sc = synth.make_scene("c5")
+    r = facert.Renderer(sc, edge_spp=1, flags=facert.FLAG_MORPH_BF16, max_batch=batch)
+    items = []
+    rng = np.random.default_rng(3)
+    for k in range(batch):
+        dp = r.device_params(synth.random_params(sc, 800 + k))
+        tgt = r.forward(r.device_params(synth.random_params(sc, 900 + k)), iteration=10 ** 7, face_id=k)
+        tgt = (tgt + torch.as_tensor(rng.normal(0.0, 0.01, tuple(tgt.shape)), dtype=torch.float32).cuda()).contiguous()
+        items.append(dict(width=sc.width, height=sc.height, spp=sc.spp, edge_spp=1, flags=0, iteration=0, face_id=k,
+                          params=dp, target=tgt, image=torch.zeros_like(tgt),
+                          loss=torch.zeros(1, dtype=torch.float64, device="cuda"), grads=r.zero_grads(dp)))
+    stream = torch.cuda.current_stream()
+    ms, stages = [], []
+    facert.fr_counters(r.ctx, reset=True)
+    for k in range(warmup + steps):
+        for it in items:
+            it["iteration"] = k
+            for g in it["grads"].values():
+                g.zero_()
+        if k == warmup:
+            facert.fr_counters(r.ctx, reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        facert.fr_render_batch(r.ctx, items)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    cnt = facert.fr_counters(r.ctx, reset=True)
+    rays = sum(v["rays"] for v in cnt.values()) / steps
+    status = r.status()
+    r.close()
+    torch.cuda.empty_cache()
+    s_step = float(np.mean(ms)) / 1000.0
+    return {"workload": "batch of %d faces: 50,002 verts / 100,000 tris, K = 20, 1024 x 1024, 64 spp, 80 lights, "
+                        "2048^2 textures, BF16 morph, adjoint re-tracing" % batch,
+            "s_per_step": s_step, "rays_per_step": rays, "rays_per_s": rays / s_step,
+            "face_steps_per_s": batch / s_step, "steps": steps, "status": int(status)}
+
+
 def albedo_bench(batch=8, reps=10):
     """Statistical albedo morph (Sec. 3.2) at the paper-scale texture size
     (512^2 texels, K = 80 per albedo, diffuse + specular in one call) as the
@@ -552,12 +603,21 @@ def main():
     ap.add_argument("--serve-c4-forms", default="served,native,plain",
                     help="which forms of the serving workload to run (comma-separated: served = the Python "
                          "server, native = the library's server, plain = one face at a time)")
+    ap.add_argument("--large", action="store_true",
+                    help="run the large workload (batch of 8 faces, 1024^2, 64 spp, 100,000 triangles) on its own line")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-iters", type=int, default=6)
     ap.add_argument("--serve-rate", type=float, default=40.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.large:
+        res = large_bench()
+        print(json.dumps({"metric": "rays/s fwd+adjoint (large workload)", "value": res["rays_per_s"],
+                          "unit": "rays/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+                          "large": res}))
+        return
 
     if args.serve_c4 > 0:
         # the full serving workload, reported on its own line (not the step benchmark)
