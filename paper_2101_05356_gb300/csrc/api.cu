@@ -245,7 +245,8 @@ BlockMap map_of(const fr_ctx* c, int n, bool edges) {
     for (int k = 0; k < n; ++k) {
         const DevScene& s = c->h_items[k].S;
         m.block0[k] = b;
-        long work = (long)s.W * s.H * (edges ? ((s.flags & FR_FLAG_NO_PRIMARY_EDGE) ? 0 : s.edge_spp) : s.spp);
+        // primary-edge samples take two threads each (one per side of the edge)
+        long work = (long)s.W * s.H * (edges ? ((s.flags & FR_FLAG_NO_PRIMARY_EDGE) ? 0 : 2 * s.edge_spp) : s.spp);
         b += (int)((work + 127) / 128);
     }
     m.block0[n] = b;

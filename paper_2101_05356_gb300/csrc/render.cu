@@ -763,7 +763,12 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
     const uint32_t iteration = it.iteration, face = it.face;
     block_acc_init(1);
     const long n_edge = (long)S.W * S.H * S.edge_spp;
-    const long e0 = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
+    // two lanes per edge sample: the even one evaluates the radiance on the
+    // + side of the edge, the odd one on the - side (twice the warps of one
+    // lane doing both in turn; the same samples and the same arithmetic)
+    const long t0 = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
+    const long e0 = t0 >> 1;
+    const int side = (int)(t0 & 1);
     bool active = e0 < n_edge;
     // samples are processed in the order k_edge_order chose (same samples, so
     // the same estimate; nearby samples share a warp)
@@ -803,12 +808,14 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
             my = tx / tl;
         }
     }
-    const float eps = 1e-3f;
-    SampleState ssp, ssm;
-    uint64_t visp[2], vism[2];
+    const float eps = side ? -1e-3f : 1e-3f;
+    SampleState ss;
+    uint64_t vis[2];
     RayStats rs;
-    const float3 Lp = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, my_stack(sh), ssp, visp, rs);
-    const float3 Lm = radiance_at(S, P, active, X - eps * mx, Y - eps * my, smp, 4, sh, my_stack(sh), ssm, vism, rs);
+    const float3 L = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, my_stack(sh), ss, vis, rs);
+    const float3 Lo = f3(__shfl_xor_sync(FULL, L.x, 1), __shfl_xor_sync(FULL, L.y, 1), __shfl_xor_sync(FULL, L.z, 1));
+    const float3 Lp = side ? Lo : L, Lm = side ? L : Lo;
+    if (side) active = false;                          // the even lane adds the pair's term
     flush_stats(S.counters + 6, rs);
     float gf = 0.0f;
     float3 gA = f3(0, 0, 0), gB = f3(0, 0, 0);
