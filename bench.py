@@ -50,8 +50,8 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is in profiles/k_forward_adjoint_c2_full.md.
-TRAFFIC = {"k_forward": {"bytes": 33999872 + 38772736,
-                         "sources_sha256": "e9aec35635bef47e87cfa973ed71b1ef589baee2a944ff14f47287f0ce265f29"}}
+TRAFFIC = {"k_forward": {"bytes": 34303744 + 39164416,
+                         "sources_sha256": "a79e2326c2c26eab885e8fae651b86e460e9fec6124113f89408640363f0f31e"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 SMS = 152
 FP32_LANES_PER_SM = 128
