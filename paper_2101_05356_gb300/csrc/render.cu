@@ -27,15 +27,20 @@ constexpr int RT_WARPS = RT_THREADS / 32;
 #endif
 // minimum resident blocks per SM requested from the compiler (register cap).
 // Measured on GB300 (paper-scale face): the forward is fastest at 10 blocks
-// (3.65 ms; 8: 3.86 ms, 12: 4.11 ms), the primary-edge kernel at 8.
+// (3.11 ms; 8: 3.28 ms, 12: 3.47 ms), the primary-edge kernel at 8, the
+// adjoint reading hit records at 5 (0.601 ms; 6: 0.618 ms, 8: 0.637 ms) and
+// the re-tracing adjoint at 8 (4.20 ms; 6: 4.38 ms, 5: 4.65 ms).
 #ifndef FR_FWD_MIN_BLOCKS
 #define FR_FWD_MIN_BLOCKS 10
 #endif
 #ifndef FR_EDGE_MIN_BLOCKS
 #define FR_EDGE_MIN_BLOCKS 8
 #endif
+#ifndef FR_ADJ_REC_MIN_BLOCKS
+#define FR_ADJ_REC_MIN_BLOCKS 5
+#endif
 #ifndef FR_ADJ_MIN_BLOCKS
-#define FR_ADJ_MIN_BLOCKS 6
+#define FR_ADJ_MIN_BLOCKS 8
 #endif
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float SHADOW_EPS = 1e-4f;     // shadow segment trimmed to (eps, 1 - eps)
@@ -468,7 +473,8 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
 // camera and shadow traversals are compiled out (a smaller kernel); otherwise
 // each item re-traces unless it has records.
 template <bool RECORDED>
-__global__ void __launch_bounds__(RT_THREADS, FR_ADJ_MIN_BLOCKS) k_adjoint(const DevItem* items, BlockMap map) {
+__global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS : FR_ADJ_MIN_BLOCKS)
+    k_adjoint(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
     FR_STACK_DECL
     const int item = item_of_block(map);
