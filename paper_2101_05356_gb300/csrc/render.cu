@@ -111,8 +111,8 @@ FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, floa
     const float3 n0 = xyz(__ldg(&S.vn[fc.x])), n1 = xyz(__ldg(&S.vn[fc.y])), n2 = xyz(__ldg(&S.vn[fc.z]));
     ss.y = v0 * b0 + v1 * h.b1 + v2 * h.b2;
     const float3 m = n0 * b0 + n1 * h.b1 + n2 * h.b2;
-    ss.ns = m * (1.0f / length(m));
-    ss.o = -ss.d * (1.0f / length(ss.d));
+    ss.ns = m * rsqrtf(dot(m, m));
+    ss.o = -ss.d * rsqrtf(dot(ss.d, ss.d));
     // one-sided surfaces: seen from behind, a triangle reflects nothing (that
     // change happens at geometric silhouettes, which the primary-edge term samples)
     ss.lit = dot(cross(v1 - v0, v2 - v0), ss.o) > 0.0f &&
@@ -206,11 +206,12 @@ FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleSta
                     ShadeAdj* g, float3* gy, float3* gz = nullptr) {
     const float3 lv = z - ss.y;
     const float d2 = dot(lv, lv);
-    const float inv_len = 1.0f / sqrtf(d2);
+    const float inv_len = rsqrtf(d2);
+    const float inv_d2 = inv_len * inv_len;
     const float3 l = lv * inv_len;
     const float cos_s = dot(ss.ns, l), cos_l = -dot(L.n, l);
     if (!(cos_s > 0.0f) || !(cos_l > 0.0f) || !ss.lit) return f3(0.0f, 0.0f, 0.0f);
-    const float geo = cos_s * cos_l / d2;
+    const float geo = cos_s * cos_l * inv_d2;
     float3 f;
     if (ADJ) {
         const float3 gf = f3(gh.x * geo, gh.y * geo, gh.z * geo);
@@ -218,7 +219,7 @@ FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleSta
         g->l = f3(0.0f, 0.0f, 0.0f);
         f = brdf<true>(flags, ss.ns, l, ss.o, ss.m, gf, g);
         const float ggeo = gh.x * f.x + gh.y * f.y + gh.z * f.z;
-        const float gcs = ggeo * cos_l / d2, gcl = ggeo * cos_s / d2, gd2 = -ggeo * geo / d2;
+        const float gcs = ggeo * cos_l * inv_d2, gcl = ggeo * cos_s * inv_d2, gd2 = -ggeo * geo * inv_d2;
         g->n += l * gcs;
         const float3 gl = g->l + ss.ns * gcs - L.n * gcl;
         g->l = keep_l;
@@ -591,8 +592,8 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         // intersection quantities (Moller-Trumbore form, ray origin at the camera)
         const float3 e1 = v1 - v0, e2 = v2 - v0, sv = -v0;
         const float3 pv = cross(ss.d, e2), qv = cross(sv, e1);
-        const float det = dot(e1, pv);
-        const float b1 = dot(sv, pv) / det, b2 = dot(ss.d, qv) / det, b0 = 1.0f - b1 - b2;
+        const float det = dot(e1, pv), inv_det = __fdividef(1.0f, det);
+        const float b1 = dot(sv, pv) * inv_det, b2 = dot(ss.d, qv) * inv_det, b0 = 1.0f - b1 - b2;
         // textures: value gradients and d/d(uv)
         float gu = 0.0f, gvv = 0.0f;
         for (int ch = 0; ch < 3; ++ch) {
@@ -615,7 +616,7 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         float gb0 = gu * t0.x + gvv * t0.y, gb1 = gu * t1.x + gvv * t1.y, gb2 = gu * t2.x + gvv * t2.y;
         // shading normal ns = m / |m|, m = sum b_k n_k
         const float3 mm = n0 * b0 + n1 * b1 + n2 * b2;
-        const float inv_m = 1.0f / length(mm);
+        const float inv_m = rsqrtf(dot(mm, mm));
         const float3 nsh = mm * inv_m;
         const float3 gm = (g.n - nsh * dot(nsh, g.n)) * inv_m;
         gn0 = gm * b0; gn1 = gm * b1; gn2 = gm * b2;
@@ -624,12 +625,12 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         gv0 = gy * b0; gv1 = gy * b1; gv2 = gy * b2;
         gb0 += dot(v0, gy); gb1 += dot(v1, gy); gb2 += dot(v2, gy);
         // view direction o = -d / |d|
-        const float inv_d = 1.0f / length(ss.d);
+        const float inv_d = rsqrtf(dot(ss.d, ss.d));
         const float3 od = -ss.d * inv_d;
         float3 gd = -(g.o - od * dot(od, g.o)) * inv_d;
         // barycentrics from the intersection
         const float G1 = gb1 - gb0, G2 = gb2 - gb0;
-        const float gsp = G1 / det, gdq = G2 / det, gdet = -(G1 * b1 + G2 * b2) / det;
+        const float gsp = G1 * inv_det, gdq = G2 * inv_det, gdet = -(G1 * b1 + G2 * b2) * inv_det;
         float3 gs = pv * gsp;
         float3 gp = sv * gsp + e1 * gdet;
         gd += qv * gdq;

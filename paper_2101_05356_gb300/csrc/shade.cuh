@@ -78,35 +78,43 @@ struct Material {
 };
 
 // ---------------------------------------------------------------------------
-// Smith masking G1 with its partials w.r.t. n.v and r (App. A, Eq. brdf_g1)
+// Smith masking G1 with its partials w.r.t. n.v and r (App. A, Eq. brdf_g1).
+// Shading arithmetic uses the hardware's approximate divide, reciprocal
+// square root, power and logarithm (a few ulp: far inside the 1e-4 radiance
+// and 1e-3 gradient tolerances); the ray-triangle and traversal arithmetic
+// stays IEEE.
 // ---------------------------------------------------------------------------
+// callers pass n.v > 0, so Delta(h.v / n.v) (Eq. brdf_g1_chi) is h.v > 0
 FR_D float g1_walter(float nv, float hv, float r, float& d_nv, float& d_r) {
     d_nv = d_r = 0.0f;
-    if (!(hv / nv > 0.0f)) return 0.0f;            // Delta(h.v / n.v), Eq. brdf_g1_chi
+    if (!(hv > 0.0f)) return 0.0f;
     const float s2 = 1.0f - nv * nv;
     if (s2 <= 0.0f) return 1.0f;
-    const float sq = sqrtf(s2);
-    const float a = nv / (r * sq);                 // Eq. brdf_g1_a
+    const float rs = rsqrtf(s2);                   // 1 / sin
+    const float a = __fdividef(nv * rs, r);        // Eq. brdf_g1_a: cot / r
     if (a >= 1.6f) return 1.0f;
     const float num = 3.535f * a + 2.181f * a * a;
     const float den = 1.0f + 2.276f * a + 2.577f * a * a;
-    const float dG_da = ((3.535f + 4.362f * a) * den - num * (2.276f + 5.154f * a)) / (den * den);
-    d_nv = dG_da / (r * s2 * sq);
-    d_r = -dG_da * a / r;
-    return num / den;
+    const float inv_den = __fdividef(1.0f, den);
+    const float dG_da = ((3.535f + 4.362f * a) * den - num * (2.276f + 5.154f * a)) * inv_den * inv_den;
+    d_nv = __fdividef(dG_da * rs * rs * rs, r);    // da/d(n.v) = 1 / (r sin^3)
+    d_r = -__fdividef(dG_da * a, r);
+    return num * inv_den;
 }
 
 FR_D float g1_ggx(float nv, float hv, float r, float& d_nv, float& d_r) {
     d_nv = d_r = 0.0f;
-    if (!(hv / nv > 0.0f)) return 0.0f;
+    if (!(hv > 0.0f)) return 0.0f;
     const float a2 = r * r;
-    const float S = sqrtf(a2 + (1.0f - a2) * nv * nv);
+    const float S2 = a2 + (1.0f - a2) * nv * nv;
+    const float iS = rsqrtf(S2), S = S2 * iS;
     const float den = nv + S;
-    const float dS_dnv = (1.0f - a2) * nv / S;
-    const float dS_dr = r * (1.0f - nv * nv) / S;
-    d_nv = 2.0f * (S - nv * dS_dnv) / (den * den);
-    d_r = -2.0f * nv * dS_dr / (den * den);
-    return 2.0f * nv / den;
+    const float inv_den2 = __fdividef(1.0f, den * den);
+    const float dS_dnv = (1.0f - a2) * nv * iS;
+    const float dS_dr = r * (1.0f - nv * nv) * iS;
+    d_nv = 2.0f * (S - nv * dS_dnv) * inv_den2;
+    d_r = -2.0f * nv * dS_dr * inv_den2;
+    return __fdividef(2.0f * nv, den);
 }
 
 // Reverse-mode accumulators of one shading point.
@@ -129,8 +137,8 @@ FR_D float3 brdf(uint32_t flags, float3 n, float3 l, float3 o, const Material& m
         return m.c * (1.0f / FR_PI);
     }
     const float3 hv = l + o;
-    const float hlen = length(hv);
-    const float3 h = hv * (1.0f / hlen);                     // Eq. halfVector (reading)
+    const float inv_hlen = rsqrtf(dot(hv, hv));
+    const float3 h = hv * inv_hlen;                          // Eq. halfVector (reading)
     const float nh = dot(n, h), oh = dot(o, h), lh = dot(l, h);
     float Dt, dD_dnh, dD_dr;
     const float r = m.r;
@@ -138,18 +146,24 @@ FR_D float3 brdf(uint32_t flags, float3 n, float3 l, float3 o, const Material& m
     if (flags & FR_FLAG_GGX_D) {
         const float a2 = r * r;
         const float den = nh * nh * (a2 - 1.0f) + 1.0f;
-        Dt = a2 / (FR_PI * den * den);
-        dD_dnh = -4.0f * a2 * nh * (a2 - 1.0f) / (FR_PI * den * den * den);
-        dD_dr = 2.0f * r / (FR_PI * den * den) - 4.0f * a2 * r * nh * nh / (FR_PI * den * den * den);
+        const float i2 = __fdividef(1.0f, FR_PI * den * den), i3 = __fdividef(i2, den);
+        Dt = a2 * i2;
+        dD_dnh = -4.0f * a2 * nh * (a2 - 1.0f) * i3;
+        dD_dr = 2.0f * r * i2 - 4.0f * a2 * r * nh * nh * i3;
         G1o = g1_ggx(no, oh, r, dG1o_dno, dG1o_dr);
         G1l = g1_ggx(nl, lh, r, dG1l_dnl, dG1l_dr);
     } else {
         // Eq. brdf_d (reading): (alpha + 2)/(2 pi) (n.h)^alpha, alpha = 2/r - 2
-        const float alpha = 2.0f / r - 2.0f;
-        const float p = powf(nh, alpha);
-        Dt = p / (FR_PI * r);
-        dD_dnh = Dt * alpha / nh;
-        dD_dr = Dt * (-1.0f / r - 2.0f * logf(nh) / (r * r));
+        const float ir = __fdividef(1.0f, r);
+        const float alpha = 2.0f * ir - 2.0f;
+        const float p = __powf(nh, alpha);                   // n.h > 0 here (n.l, n.o > 0)
+        Dt = p * ir * (1.0f / FR_PI);
+        if (ADJ) {
+            dD_dnh = __fdividef(Dt * alpha, nh);
+            dD_dr = Dt * (-ir - 2.0f * __logf(nh) * ir * ir);
+        } else {
+            dD_dnh = dD_dr = 0.0f;
+        }
         G1o = g1_walter(no, oh, r, dG1o_dno, dG1o_dr);     // Eq. brdf_g
         G1l = g1_walter(nl, lh, r, dG1l_dnl, dG1l_dr);
     }
@@ -158,8 +172,8 @@ FR_D float3 brdf(uint32_t flags, float3 n, float3 l, float3 o, const Material& m
     const bool lin = (flags & FR_FLAG_SCHLICK_LINEAR_D) != 0;
     const float b2 = base * base;
     const float w5 = lin ? base : b2 * b2 * base;            // Eq. brdf_f (Schlick)
-    const float denom = 4.0f * no * nl;                      // Eq. brdf_spec
-    const float Q = Dt * G / denom;
+    const float inv_denom = __fdividef(1.0f, 4.0f * no * nl);   // Eq. brdf_spec
+    const float Q = Dt * G * inv_denom;
     const float3 F = f3(m.s.x + (1.0f - m.s.x) * w5, m.s.y + (1.0f - m.s.y) * w5,
                         m.s.z + (1.0f - m.s.z) * w5);
     const float inv_pi = 1.0f / FR_PI;
@@ -170,8 +184,8 @@ FR_D float3 brdf(uint32_t flags, float3 n, float3 l, float3 o, const Material& m
         g->s += f3(gf.x * Q * (1.0f - w5), gf.y * Q * (1.0f - w5), gf.z * Q * (1.0f - w5));
         const float gw5 = Q * (gf.x * (1.0f - m.s.x) + gf.y * (1.0f - m.s.y) + gf.z * (1.0f - m.s.z));
         const float goh_f = gw5 * (lin ? -1.0f : -5.0f * b2 * b2);
-        const float gDt = gQ * G / denom, gG = gQ * Dt / denom;
-        float gno = -gQ * Q / no, gnl = -gQ * Q / nl;
+        const float gDt = gQ * G * inv_denom, gG = gQ * Dt * inv_denom;
+        float gno = -__fdividef(gQ * Q, no), gnl = -__fdividef(gQ * Q, nl);
         const float gG1o = gG * G1l, gG1l = gG * G1o;
         gno += gG1o * dG1o_dno;
         gnl += gG1l * dG1l_dnl;
@@ -180,7 +194,7 @@ FR_D float3 brdf(uint32_t flags, float3 n, float3 l, float3 o, const Material& m
         const float3 gh = n * gnh + o * goh_f;
         g->n += h * gnh;
         g->o += h * goh_f;
-        const float3 ghv = (gh - h * dot(h, gh)) * (1.0f / hlen);
+        const float3 ghv = (gh - h * dot(h, gh)) * inv_hlen;
         g->l += ghv;
         g->o += ghv;
         g->n += o * gno + l * gnl;
