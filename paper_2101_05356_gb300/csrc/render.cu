@@ -57,9 +57,12 @@ struct RtShared {
     WarpQueue wq[RT_WARPS];
 };
 
-// Per-warp focal / light-intensity partials of the adjoint kernels live in
-// dynamic shared memory: RT_WARPS rows of n = 1 + 3 N_L doubles.
-extern __shared__ double acc_dyn[];
+// Per-warp focal / light partials of the adjoint kernels live in dynamic
+// shared memory: RT_WARPS rows of n values.  Each warp writes each of its
+// values once (an FP32 warp sum), so they are kept in FP32 and turned to FP64
+// only by the block sum: the same doubles as converting each at once, without
+// the narrow FP64 pipe in the per-light loop.
+extern __shared__ float acc_dyn[];
 
 #if FR_STACK_LOCAL
 #define FR_STACK_DECL int lstack_[FR_STACK];
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
 // adjoint
 // ---------------------------------------------------------------------------
 FR_D void block_acc_init(int n) {
-    for (int i = threadIdx.x; i < RT_WARPS * n; i += RT_THREADS) acc_dyn[i] = 0.0;
+    for (int i = threadIdx.x; i < RT_WARPS * n; i += RT_THREADS) acc_dyn[i] = 0.0f;
     __syncthreads();
 }
 
@@ -364,7 +367,7 @@ FR_D void block_acc_flush(int n_acc, int from, int count, fix64* out) {
     __syncthreads();
     for (int i = threadIdx.x; i < count; i += RT_THREADS) {
         double s = 0.0;
-        for (int w = 0; w < RT_WARPS; ++w) s += acc_dyn[w * n_acc + from + i];
+        for (int w = 0; w < RT_WARPS; ++w) s += (double)acc_dyn[w * n_acc + from + i];
         if (s != 0.0) atomicAdd(&out[i], (fix64)to_fix_d(s));
     }
 }
@@ -557,17 +560,17 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
             if (any) {
                 const float sx_ = warp_sum(gI.x), sy_ = warp_sum(gI.y), sz_ = warp_sum(gI.z);
                 if ((threadIdx.x & 31) == 0) {
-                    double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc;
-                    wa[1 + 3 * j] += (double)sx_;
-                    wa[1 + 3 * j + 1] += (double)sy_;
-                    wa[1 + 3 * j + 2] += (double)sz_;
+                    float* wa = acc_dyn + (threadIdx.x >> 5) * n_acc;
+                    wa[1 + 3 * j] = sx_;
+                    wa[1 + 3 * j + 1] = sy_;
+                    wa[1 + 3 * j + 2] = sz_;
                 }
                 if (stage) {                                   // block-uniform
                     float sg[4];
                     for (int q = 0; q < 4; ++q) sg[q] = warp_sum(gl4[q]);
                     if ((threadIdx.x & 31) == 0) {
-                        double* wa = acc_dyn + (threadIdx.x >> 5) * n_acc + 1 + 3 * S.NL + 4 * j;
-                        for (int q = 0; q < 4; ++q) wa[q] += (double)sg[q];
+                        float* wa = acc_dyn + (threadIdx.x >> 5) * n_acc + 1 + 3 * S.NL + 4 * j;
+                        for (int q = 0; q < 4; ++q) wa[q] = sg[q];
                     }
                 }
             }
@@ -684,7 +687,7 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         }
     }
     const float gf_w = warp_sum(gfocal);
-    if ((threadIdx.x & 31) == 0) acc_dyn[(threadIdx.x >> 5) * n_acc] += (double)gf_w;
+    if ((threadIdx.x & 31) == 0) acc_dyn[(threadIdx.x >> 5) * n_acc] = gf_w;
     flush_stats(S.counters + 3, rs);
     block_acc_flush(n_acc, 0, 1 + 3 * S.NL, G.small);
     if (stage) block_acc_flush(n_acc, 1 + 3 * S.NL, 4 * S.NL, G.small + FR_GEO_OFF);
@@ -838,7 +841,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
     scatter_vertex(G.d_v, E.x, gA, active);
     scatter_vertex(G.d_v, E.y, gB, active);
     const float gw = warp_sum(gf);
-    if ((threadIdx.x & 31) == 0) acc_dyn[threadIdx.x >> 5] += (double)gw;
+    if ((threadIdx.x & 31) == 0) acc_dyn[threadIdx.x >> 5] = gw;
     block_acc_flush(1, 0, 1, G.small);
 }
 
@@ -1052,7 +1055,7 @@ void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) 
 void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage,
                     cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    const size_t acc_bytes = sizeof(double) * RT_WARPS * (1 + (any_stage ? 7 : 3) * (size_t)NL);
+    const size_t acc_bytes = sizeof(float) * RT_WARPS * (1 + (any_stage ? 7 : 3) * (size_t)NL);
     if (all_recorded)
         k_adjoint<true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
     else
@@ -1068,7 +1071,7 @@ void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t 
 
 void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    k_edge_primary<<<map_blocks(map), RT_THREADS, sizeof(double) * RT_WARPS, st>>>(items, map);
+    k_edge_primary<<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
     fr_count_launches(1);
 }
 
