@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(const float* __restrict_
 #pragma unroll
     for (int b = 0; b < G; ++b) acc[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const float4* bp = reinterpret_cast<const float4*>(basis) + i;
+    // unrolled so that several basis rows are in flight per thread (the grid
+    // of one face is small: 3N / 4 threads)
+#pragma unroll 8
     for (int k = 0; k < K; ++k) {
         const float4 bk = __ldg(bp + (size_t)k * ld4);
 #pragma unroll
@@ -153,8 +156,8 @@ void launch_linear(const float* mean, const float* basis, int ld, int rows, int 
                    cudaStream_t st) {
     if (t.n <= 0 || rows <= 0) return;
     const dim3 grid(nb((rows + 3) / 4, LIN_THREADS), nb(t.n, LIN_GROUP));
-    if (t.n == 1)
-        k_linear<1><<<dim3(grid.x, 1), LIN_THREADS, 0, st>>>(mean, basis, ld, rows, K, t);
+    if (t.n == 1)      // one face: smaller blocks spread its few rows over more SMs
+        k_linear<1><<<nb((rows + 3) / 4, LIN_THREADS / 2), LIN_THREADS / 2, 0, st>>>(mean, basis, ld, rows, K, t);
     else
         k_linear<LIN_GROUP><<<grid, LIN_THREADS, 0, st>>>(mean, basis, ld, rows, K, t);
     fr_count_launches(1);
