@@ -44,12 +44,14 @@ class OraScene(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("spp", ctypes.c_int32), ("tex_size", ctypes.c_int32),
                 ("edge_spp", ctypes.c_int32), ("seed", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("n_threads", ctypes.c_int32), ("stage", f32p)]
+                ("flags", ctypes.c_uint32), ("n_threads", ctypes.c_int32), ("stage", f32p),
+                ("env_size", ctypes.c_int32)]
 
 
 class OraParams(ctypes.Structure):
     _fields_ = [(n, f32p) for n in ("coef", "rot", "trans", "focal", "light_i",
-                                    "diffuse", "specular", "roughness", "light_d", "light_a", "light_p")]
+                                    "diffuse", "specular", "roughness", "light_d", "light_a", "light_p",
+                                    "env")]
 
 
 def build(force: bool = False) -> str:
@@ -84,7 +86,7 @@ def lib():
         L.ora_loss.argtypes = [ctypes.c_int32, ctypes.c_int32, f64p, f32p, f64p, f64p]
         L.ora_loss.restype = ctypes.c_double
         L.ora_grad.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams),
-                               ctypes.c_uint32, ctypes.c_uint32, f64p, ctypes.c_uint32] + [f64p] * 9
+                               ctypes.c_uint32, ctypes.c_uint32, f64p, ctypes.c_uint32] + [f64p] * 10
         L.ora_brdf.argtypes = [ctypes.c_uint32, f64p, f64p, f64p, f64p, f64p, ctypes.c_double, f64p]
         L.ora_brdf.restype = ctypes.c_double
         L.ora_brdf_terms.argtypes = [ctypes.c_uint32, f64p, f64p, f64p, ctypes.c_double, f64p]
@@ -121,7 +123,8 @@ class _Bound:
             f(scene.basis), faces.ctypes.data_as(i32p), f(scene.uv), scene.n_lights,
             f(scene.lights), f(scene.light_d), f(scene.light_a), scene.width, scene.height,
             scene.spp, scene.tex_size, edge_spp, seed, flags, n_threads,
-            f(scene.stage) if getattr(scene, "stage", None) is not None else None)
+            f(scene.stage) if getattr(scene, "stage", None) is not None else None,
+            int(getattr(scene, "env_size", 0) or 0))
         self.params = None
         if params is not None:
             def opt(name):
@@ -130,7 +133,7 @@ class _Bound:
             self.params = OraParams(f(params.coef), f(params.rot), f(params.trans),
                                     f(params.focal), f(params.light_i), f(params.diffuse),
                                     f(params.specular), f(params.roughness), opt("light_d"), opt("light_a"),
-                                    opt("light_p"))
+                                    opt("light_p"), opt("env"))
 
 
 def ray_count(reset=False):
@@ -225,11 +228,14 @@ def grad(scene, params, adjoint, iteration=0, face_id=0, terms=TERM_ALL, flags=0
              roughness=np.zeros((m, m)))
     geom = getattr(scene, "stage", None) is not None and getattr(params, "light_d", None) is not None
     lg = np.zeros((scene.n_lights, 4))
+    me = int(getattr(scene, "env_size", 0) or 0)
+    if me:   # environment-map radiance [M_e, M_e, 3]
+        g["env"] = np.zeros((me, me, 3))
     rc = lib().ora_grad(ctypes.byref(b.scene), ctypes.byref(b.params), iteration, face_id,
                         _p(adj, f64p), terms, *[_p(g[k], f64p) for k in
                                                 ("coef", "rot", "trans", "focal", "light_i",
                                                  "diffuse", "specular", "roughness")],
-                        _p(lg, f64p) if geom else None)
+                        _p(lg, f64p) if geom else None, _p(g.get("env"), f64p))
     if geom:   # d/d(d_j, a_j, p_j0, p_j1) of the virtual light stage
         g["light_d"], g["light_a"], g["light_p"] = lg[:, 0].copy(), lg[:, 1].copy(), lg[:, 2:].copy()
     if rc != 0:

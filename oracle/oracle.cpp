@@ -37,6 +37,16 @@
 //  * Shadow rays skip the shading triangle and count occluders with
 //    1e-4 < t < 1 - 1e-4 along the segment y -> z.
 //  * Closest-hit ties go to the lower triangle index.
+//  * Environment map (Sec. 7, environment map vs light stage): each texel of
+//    an M_e x M_e latitude-longitude map is a light at infinity whose
+//    radiance is the texel's RGB value.  The map is split into blocks of
+//    texels, one emitter record each; every camera sample draws one direction
+//    per block: a texel uniformly among the block's, then a direction uniform
+//    in solid angle inside it (estimator weight = texels x texel solid angle).
+//    Shadow rays follow the direction with t > 1e-4.  The visibility boundary
+//    lies on the sphere of directions: the projection from y of the occluder's
+//    silhouette edges, with the same edge-sampling estimator as the area
+//    lights (arc length and normal velocity measured on the unit sphere).
 #include "oracle.h"
 
 #include <algorithm>
@@ -174,6 +184,8 @@ struct Light {
     bool geo = false;
     V3 cd, e1d, e2d;   // c, e1, e2 with derivatives on the light's slots
     D aread, scaled;   // area and d^2 / a likewise
+    // environment block (type ORA_LIGHT_ENV): texel rows [i0, i1), columns [j0, j1)
+    int i0 = 0, i1 = 0, j0 = 0, j1 = 0;
 };
 
 struct Edge { int a, b, f1, f2; };  // a < b; f2 = -1 on the boundary
@@ -334,6 +346,88 @@ V3 light_point_d(const Light& L, double u, double v) {
     return L.cd + L.e1d * (su * (1.0 - v)) + L.e2d * (su * v);
 }
 
+// ---------------------------------------------------------------------------
+// Environment-map emitters (Sec. 7): row i of the M_e x M_e map covers polar
+// angles [i, i + 1] pi / M_e from +y, column j azimuths [j, j + 1] 2 pi / M_e
+// from +z towards +x; w(theta, phi) = (sin theta sin phi, cos theta,
+// sin theta cos phi).
+// ---------------------------------------------------------------------------
+double band_cos(int i, int Me) { return std::cos(M_PI * i / Me); }
+
+// Exact range [lo, hi] of n . w over the directions of an environment block
+// (rows [i0, i1), columns [j0, j1)).  With w = (sin t sin p, cos t, sin t cos p),
+// n . w = n_y cos t + sin t A(p), A(p) = n_x sin p + n_z cos p.  A ranges over
+// its values at the azimuth ends and at its extremes p = atan2(n_x, n_z) + k pi
+// inside; sin t >= 0, so the minimum over the block takes A's minimum and the
+// maximum A's maximum, and each is then a sinusoid in t whose extremes over
+// [t0, t1] are at the ends or at its stationary points atan2(A, n_y) + k pi.
+void env_range(const Light& L, int Me, P3 n, double& lo, double& hi) {
+    const double t0 = M_PI * L.i0 / Me, t1 = M_PI * L.i1 / Me;
+    const double f0 = 2.0 * M_PI * L.j0 / Me, f1 = 2.0 * M_PI * L.j1 / Me;
+    auto A = [&](double p) { return n.x * std::sin(p) + n.z * std::cos(p); };
+    double a_lo = std::min(A(f0), A(f1)), a_hi = std::max(A(f0), A(f1));
+    const double pa = std::atan2(n.x, n.z);
+    for (int k = -2; k <= 3; ++k) {
+        const double p = pa + k * M_PI;
+        if (p > f0 && p < f1) { a_lo = std::min(a_lo, A(p)); a_hi = std::max(a_hi, A(p)); }
+    }
+    auto g_ext = [&](double a, bool want_min) {
+        auto g = [&](double t) { return n.y * std::cos(t) + a * std::sin(t); };
+        double r = want_min ? std::min(g(t0), g(t1)) : std::max(g(t0), g(t1));
+        const double tc = std::atan2(a, n.y);
+        for (int k = -1; k <= 2; ++k) {
+            const double t = tc + k * M_PI;
+            if (t > t0 && t < t1) r = want_min ? std::min(r, g(t)) : std::max(r, g(t));
+        }
+        return r;
+    };
+    lo = g_ext(a_lo, true);
+    hi = g_ext(a_hi, false);
+}
+
+// One direction of an environment block: a texel uniformly among the block's
+// R x C (row = floor(k_u R / 2^24) from the 24-bit integer k_u behind u, the
+// remainder placing the sample inside the row; columns likewise from v), then
+// uniform in solid angle inside the texel (cos theta and phi uniform).
+// weight = 1 / pdf = R C Omega_texel, Omega_texel = (cos top - cos bottom) 2 pi / M_e.
+struct EnvSample { int row, col; P3 w; double weight; };
+EnvSample env_sample(const Light& L, int Me, double u, double v) {
+    const uint64_t ku = (uint64_t)(u * 16777216.0), kv = (uint64_t)(v * 16777216.0);
+    const int R = L.i1 - L.i0, C = L.j1 - L.j0;
+    const uint64_t pu = ku * (uint64_t)R, pv = kv * (uint64_t)C;
+    EnvSample e;
+    e.row = L.i0 + (int)(pu >> 24);
+    e.col = L.j0 + (int)(pv >> 24);
+    const double fu = (double)(pu & 0xFFFFFFu) / 16777216.0, fv = (double)(pv & 0xFFFFFFu) / 16777216.0;
+    const double zt = band_cos(e.row, Me), zb = band_cos(e.row + 1, Me);
+    const double y = zt + fu * (zb - zt);
+    const double sn = std::sqrt(std::max(0.0, 1.0 - y * y));
+    const double phi = 2.0 * M_PI * (e.col + fv) / Me;
+    e.w = p3(sn * std::sin(phi), y, sn * std::cos(phi));
+    e.weight = (double)R * C * (zt - zb) * (2.0 * M_PI / Me);
+    return e;
+}
+
+// Texel of the map that contains unit direction w.
+void env_texel_of(P3 w, int Me, int& row, int& col) {
+    const double th = std::acos(std::min(1.0, std::max(-1.0, w.y)));
+    double ph = std::atan2(w.x, w.z);
+    if (ph < 0.0) ph += 2.0 * M_PI;
+    row = std::min(Me - 1, std::max(0, (int)std::floor(th * Me / M_PI)));
+    col = std::min(Me - 1, std::max(0, (int)std::floor(ph * Me / (2.0 * M_PI))));
+}
+
+bool inside_env_block(const Light& L, int Me, P3 w) {
+    int r, c;
+    env_texel_of(w, Me, r, c);
+    return r >= L.i0 && r < L.i1 && c >= L.j0 && c < L.j1;
+}
+
+// radiance of texel (row, col), channel k
+double env_value(const Prep& P, int row, int col, int k) {
+    return (double)P.p->env[3 * ((size_t)row * P.s->env_size + col) + k];
+}
+
 void prepare(Prep& P, const OraScene* s, const OraParams* p, int nd) {
     P.s = s; P.p = p;
     P.N = s->n_vertices; P.T = s->n_triangles; P.K = s->n_basis; P.NL = s->n_lights;
@@ -377,6 +471,13 @@ void prepare(Prep& P, const OraScene* s, const OraParams* p, int nd) {
         const float* r = s->lights + 11 * j;
         Light L;
         L.type = (int)r[0];
+        if (L.type == ORA_LIGHT_ENV) {
+            L.i0 = (int)r[1]; L.i1 = (int)r[2]; L.j0 = (int)r[3]; L.j1 = (int)r[4];
+            L.area = 0.0;
+            L.scale = 1.0;
+            P.lights[j] = L;
+            continue;
+        }
         L.c = p3(r[1], r[2], r[3]);
         L.e1 = p3(r[4], r[5], r[6]);
         L.e2 = p3(r[7], r[8], r[9]);
@@ -446,6 +547,11 @@ void classify(Prep& P) {
             double lo[2], hi[2];
             P3 nn[2] = {n1, n2};
             for (int q = 0; q < 2; ++q) {
+                if (L.type == ORA_LIGHT_ENV) {
+                    // a point at infinity in direction w is in front of the face iff n . w > 0
+                    env_range(L, P.s->env_size, nn[q], lo[q], hi[q]);
+                    continue;
+                }
                 double base = dotp(nn[q], L.c - a);
                 if (L.type == 0) {
                     double h1 = 0.5 * std::fabs(dotp(nn[q], L.e1)), h2 = 0.5 * std::fabs(dotp(nn[q], L.e2));
@@ -515,6 +621,19 @@ bool occluded(const Prep& P, P3 y, P3 z, int skip) {
         double t, b1, b2;
         if (intersect(y, d, P.v[tr[0]], P.v[tr[1]], P.v[tr[2]], t, b1, b2) && t > 1e-4 && t < 1.0 - 1e-4)
             return true;
+    }
+    return false;
+}
+
+// Shadow ray from y towards a light at infinity in unit direction w: occluded
+// if any triangle other than `skip` crosses it at t > 1e-4.
+bool occluded_dir(const Prep& P, P3 y, P3 w, int skip) {
+    g_rays.fetch_add(1, std::memory_order_relaxed);
+    for (int f = 0; f < P.T; ++f) {
+        if (f == skip) continue;
+        const int* tr = P.s->faces + 3 * f;
+        double t, b1, b2;
+        if (intersect(y, w, P.v[tr[0]], P.v[tr[1]], P.v[tr[2]], t, b1, b2) && t > 1e-4) return true;
     }
     return false;
 }
@@ -613,7 +732,9 @@ struct SampleOut {
     int tri = -1;
     uint64_t mask[2] = {0, 0};  // bit j of word j / 64: shadow ray to light j traced and unoccluded
     D L[3];                     // radiance (duals when gradients are requested)
-    double dLdi[ORA_MAX_LIGHTS][3];  // d L / d i_j per channel (visible lights only)
+    double dLdi[ORA_MAX_LIGHTS][3];  // d L / d i_j per channel (visible lights only); for an
+                                     // environment block d L / d (radiance of its sampled texel)
+    int env_tex[ORA_MAX_LIGHTS];     // environment block j: index row * M_e + col of its texel
     Tap tap;                    // bilinear taps at the hit (texture gradients)
     P3 y;                       // hit point
     V3 yd;                      // hit point as duals
@@ -663,7 +784,10 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
     out.tri = tri;
     out.mask[0] = out.mask[1] = 0;
     for (int k = 0; k < 3; ++k) out.L[k] = D(0.0);
-    for (int j = 0; j < P.NL && j < ORA_MAX_LIGHTS; ++j) out.dLdi[j][0] = out.dLdi[j][1] = out.dLdi[j][2] = 0.0;
+    for (int j = 0; j < P.NL && j < ORA_MAX_LIGHTS; ++j) {
+        out.dLdi[j][0] = out.dLdi[j][1] = out.dLdi[j][2] = 0.0;
+        out.env_tex[j] = 0;
+    }
     if (tri < 0) return;
     D b1, b2;
     V3 y;
@@ -701,6 +825,27 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
     for (int j = 0; j < P.NL; ++j) {
         const Light& Lj = P.lights[j];
         const double uu = st.u(light_dim0 + 2 * j), vv = st.u(light_dim0 + 2 * j + 1);
+        if (Lj.type == ORA_LIGHT_ENV) {       // a light at infinity: l fixed, no distance term
+            const EnvSample es = env_sample(Lj, s->env_size, uu, vv);
+            const V3 l = v3c(es.w.x, es.w.y, es.w.z);
+            const D cos_s = dot(ns, l);
+            if (!(cos_s.v > 0.0)) continue;
+            bool vis;
+            if (fixed_tri == -2) vis = !occluded_dir(P, val(y), es.w, tri);
+            else vis = (fixed_mask[j >> 6] >> (j & 63)) & 1ull;
+            if (!vis) continue;
+            out.mask[j >> 6] |= (1ull << (j & 63));
+            D f[3];
+            brdf(s->flags, ns, l, o, c, sp, r, f);
+            const D geo = cos_s * es.weight;
+            if (j < ORA_MAX_LIGHTS) out.env_tex[j] = es.row * s->env_size + es.col;
+            for (int k = 0; k < 3; ++k) {
+                const D term = f[k] * geo;
+                out.L[k] = out.L[k] + term * env_value(P, es.row, es.col, k);
+                if (j < ORA_MAX_LIGHTS) out.dLdi[j][k] = term.v;
+            }
+            continue;
+        }
         V3 zd;
         if (Lj.geo) {
             zd = light_point_d(Lj, uu, vv);
@@ -740,6 +885,17 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
 // light j, from shading state already computed in `so`.
 void light_integrand(const Prep& P, const SampleOut& so, int j, const V3& z, D h[3]) {
     const Light& Lj = P.lights[j];
+    if (Lj.type == ORA_LIGHT_ENV) {           // z is the unit direction w: h = f_r cos_s
+        const D cos_s = dot(so.ns, z);
+        if (!(cos_s.v > 0.0) || !so.lit) {
+            for (int k = 0; k < 3; ++k) h[k] = D(0.0);
+            return;
+        }
+        D f[3];
+        brdf(P.s->flags, so.ns, z, so.o, so.cc, so.ss, so.rr, f);
+        for (int k = 0; k < 3; ++k) h[k] = f[k] * cos_s;
+        return;
+    }
     V3 lv = z - so.yd;
     D dist2 = dot(lv, lv);
     V3 l = lv * (1.0 / dsqrt(dist2));
@@ -803,6 +959,36 @@ void shadow_edge_sample(const Prep& P, const SampleOut& so, int tri_self, double
     V3 A = load(P.v, P.dv, P.nd, E.a), B = load(P.v, P.dv, P.nd, E.b);
     D tt = seed_slot(u_t, P.slot_t);
     V3 pe = A + (B - A) * tt;
+    if (L.type == ORA_LIGHT_ENV) {
+        // boundary on the sphere of directions: w(t) = (p(t) - y) / |p(t) - y|
+        const int Me = P.s->env_size;
+        const V3 wd = normalize(pe - so.yd);
+        const P3 wv = val(wd);
+        if (!inside_env_block(L, Me, wv)) return;
+        D h[3];
+        light_integrand(P, so, j, wd, h);
+        if (h[0].v == 0.0 && h[1].v == 0.0 && h[2].v == 0.0) return;
+        const P3 tan = p3(wd.x.d[P.slot_t], wd.y.d[P.slot_t], wd.z.d[P.slot_t]);
+        const double tl = normp(tan);
+        if (!(tl > 0.0)) return;
+        const P3 m = crossp(wv, tan) * (1.0 / tl);   // unit normal of the curve, tangent to the sphere
+        const double eps = 1e-4;
+        const P3 wp = wv + m * eps, wm = wv - m * eps;
+        const bool vp = !occluded_dir(P, y, wp * (1.0 / normp(wp)), tri_self);
+        const bool vm = !occluded_dir(P, y, wm * (1.0 / normp(wm)), tri_self);
+        const double dV = (double)vp - (double)vm;
+        if (dV == 0.0) return;
+        if (hit_out) *hit_out = true;
+        const double scale = -dV * (double)P.NL * (double)S * tl;
+        const D vn = wd.x * m.x + wd.y * m.y + wd.z * m.z;   // normal velocity of the boundary direction
+        int row, col;
+        env_texel_of(wv, Me, row, col);
+        for (int k = 0; k < 3; ++k) {
+            const double w = adj[k] * scale * h[k].v * env_value(P, row, col, k);
+            if (w != 0.0) accumulate_geo(P, vn, w, g);
+        }
+        return;
+    }
     V3 nL = v3c(L.n.x, L.n.y, L.n.z);
     V3 cL = L.geo ? L.cd : v3c(L.c.x, L.c.y, L.c.z);   // a moving plane moves the boundary point
     D den = dot(pe - so.yd, nL);
@@ -1015,7 +1201,7 @@ double ora_loss(int32_t H, int32_t W, const double* image, const float* target, 
 int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t face_id,
              const double* adjoint, uint32_t terms, double* g_coef, double* g_rot, double* g_trans,
              double* g_focal, double* g_light, double* g_diffuse, double* g_specular,
-             double* g_roughness, double* g_light_geom) {
+             double* g_roughness, double* g_light_geom, double* g_env) {
     const int n_lg = stage_lights(s, p) ? 4 * s->n_lights : 0;
     if (s->n_basis + 15 + n_lg > DMAX || s->n_lights > ORA_MAX_LIGHTS) return -1;
     Prep P;
@@ -1024,11 +1210,13 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
     int nt = threads_of(s);
     int ngeo = P.slot_c;
     size_t MM = (size_t)P.M * P.M;
+    const size_t n_env = (size_t)s->env_size * s->env_size * 3;
     struct Acc {
-        std::vector<double> geo, light, dif, spec, rough, lg;
+        std::vector<double> geo, light, dif, spec, rough, lg, env;
     };
     std::vector<Acc> acc(nt);
     for (auto& a : acc) {
+        a.env.assign(std::max<size_t>(n_env, 1), 0.0);
         a.geo.assign(ngeo, 0.0);
         a.lg.assign((size_t)std::max(n_lg, 1), 0.0);
         a.light.assign((size_t)P.NL * 3, 0.0);
@@ -1077,8 +1265,13 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
                         }
                         A.rough[ti] += tw * dr;
                     }
-                    for (int j = 0; j < P.NL; ++j)
+                    for (int j = 0; j < P.NL; ++j) {
+                        if (P.lights[j].type == ORA_LIGHT_ENV) {     // the sampled texel's radiance
+                            for (int k = 0; k < 3; ++k) A.env[3 * (size_t)so.env_tex[j] + k] += w[k] * so.dLdi[j][k];
+                            continue;
+                        }
                         for (int k = 0; k < 3; ++k) A.light[3 * j + k] += w[k] * so.dLdi[j][k];
+                    }
                 }
                 if ((terms & ORA_TERM_SHADOW) && !(s->flags & ORA_FLAT) && so.lit) {
                     Stream se{s->seed, STREAM_EDGE_SHADOW, (uint32_t)pix, (uint32_t)smp, iteration, face_id};
@@ -1154,6 +1347,7 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
     if (g_diffuse) { std::fill(g_diffuse, g_diffuse + MM * 3, 0.0); for (auto& a : acc) for (size_t q = 0; q < MM * 3; ++q) g_diffuse[q] += a.dif[q]; }
     if (g_specular) { std::fill(g_specular, g_specular + MM * 3, 0.0); for (auto& a : acc) for (size_t q = 0; q < MM * 3; ++q) g_specular[q] += a.spec[q]; }
     if (g_roughness) { std::fill(g_roughness, g_roughness + MM, 0.0); for (auto& a : acc) for (size_t q = 0; q < MM; ++q) g_roughness[q] += a.rough[q]; }
+    if (g_env && n_env) { std::fill(g_env, g_env + n_env, 0.0); for (auto& a : acc) for (size_t q = 0; q < n_env; ++q) g_env[q] += a.env[q]; }
     g_nd = 0;
     return 0;
 }
@@ -1239,6 +1433,14 @@ int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
                 D g = L.scaled * cs * cl / d2 * L.aread * (1.0 / M_PI);
                 for (int k = 0; k < 3; ++k) vs[th][k] += g.v * p->light_i[3 * j + k];
                 for (int q = 0; q < n_lg; ++q) gl[th][q] += g.d[P.slot_light + q] * p->light_i[3 * j];
+                continue;
+            }
+            if (L.type == ORA_LIGHT_ENV) {
+                const EnvSample es = env_sample(L, s->env_size, st.u(4 + 2 * j), st.u(5 + 2 * j));
+                const double cs = dotp(p3(n[0], n[1], n[2]), es.w);
+                if (cs <= 0.0) continue;
+                if (occluded_dir(P, so.y, es.w, tri_self)) continue;
+                for (int k = 0; k < 3; ++k) vs[th][k] += env_value(P, es.row, es.col, k) * cs * es.weight / M_PI;
                 continue;
             }
             P3 z = light_point(L, st.u(4 + 2 * j), st.u(5 + 2 * j));

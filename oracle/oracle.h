@@ -23,6 +23,15 @@ extern "C" {
 #define ORA_VIEW_CUTOFF 1024u   /* every contribution zero where n_s . o <= 0 (the grazing cutoff applied to
                                    the diffuse term too; its gradient misses that curve's motion) */
 
+/* emitter type of a light record (the other types are 0 quad, 1 triangle, 2 disk):
+ * a block of texels of an environment map of lights at infinity (Sec. 7,
+ * environment map vs light stage).  Record {3, i0, i1, j0, j1, unused...}: rows
+ * [i0, i1) x columns [j0, j1) of the env_size x env_size map; row i holds the
+ * polar angles [i, i + 1] pi / env_size from camera-space +y, column j the
+ * azimuths [j, j + 1] 2 pi / env_size from +z towards +x.  The radiance from
+ * direction w is the map's texel containing w (OraParams.env, RGB). */
+#define ORA_LIGHT_ENV 3
+
 /* gradient terms */
 #define ORA_TERM_INTERIOR  1u
 #define ORA_TERM_PRIMARY   2u
@@ -45,6 +54,7 @@ typedef struct OraScene {
      * unit-scale face vertices V0, V1, V2 of light j's polyhedron face; with
      * OraParams light_d/a/p the emitters are built from them (triangles) */
     const float* stage;
+    int32_t env_size;       /* texels per side of the environment map (0: no ORA_LIGHT_ENV records) */
 } OraScene;
 
 typedef struct OraParams {
@@ -52,6 +62,8 @@ typedef struct OraParams {
     /* optional light geometry of a stage scene: distance d_j [N_L], relative
      * area a_j [N_L], barycentric centre (p_j0, p_j1) [N_L][2] (p_j2 = 1 - both) */
     const float *light_d, *light_a, *light_p;
+    /* environment-map radiance [env_size][env_size][3] (scenes with ORA_LIGHT_ENV records) */
+    const float* env;
 } OraParams;
 
 /* rays traced by this library since the last reset (closest-hit + shadow) */
@@ -80,7 +92,8 @@ double ora_loss(int32_t height, int32_t width, const double* image, const float*
 int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t face_id,
              const double* adjoint, uint32_t terms, double* g_coef, double* g_rot,
              double* g_trans, double* g_focal, double* g_light, double* g_diffuse,
-             double* g_specular, double* g_roughness, double* g_light_geom /* [N_L][4] or NULL */);
+             double* g_specular, double* g_roughness, double* g_light_geom /* [N_L][4] or NULL */,
+             double* g_env /* [env_size][env_size][3] or NULL */);
 
 double ora_brdf(uint32_t flags, const double* n, const double* l, const double* o,
                 const double* c, const double* s, double r, double* out_rgb);

@@ -19,6 +19,11 @@ type 1 = tri   : vertices c, c + e1, c + e2
 type 2 = disk  : centre c, orthogonal radius vectors e1, e2 (|e1| = |e2| = R)
 The emitting side is the one that e1 x e2 points to.  Each light also carries
 its distance d_j and relative area a_j of Eq. (lightIntensity).
+type 3 = environment block: [3, i0, i1, j0, j1, 0...], texel rows [i0, i1) and
+columns [j0, j1) of an M_e x M_e latitude-longitude map of lights at infinity
+(the environment-map alternative of Sec. 7): row i spans polar angles
+[i, i + 1] pi / M_e from camera-space +y, column j azimuths [j, j + 1] 2 pi / M_e
+from +z towards +x; the radiance is the map's texel (Params.env).
 """
 from __future__ import annotations
 
@@ -27,7 +32,7 @@ import math
 
 import numpy as np
 
-LIGHT_QUAD, LIGHT_TRI, LIGHT_DISK = 0, 1, 2
+LIGHT_QUAD, LIGHT_TRI, LIGHT_DISK, LIGHT_ENV = 0, 1, 2, 3
 
 # Camera translation that places the head in front of the camera (Sec. 3.1).
 DEFAULT_T = (0.0, 0.0, 4.5)
@@ -75,6 +80,7 @@ class Scene:
     albedo: AlbedoModel | None = None
     landmarks: np.ndarray | None = None   # int32 [L] landmark vertex indices (Eq. landmark)
     stage: np.ndarray | None = None       # float32 [N_L, 12] polyhedral stage: centre, face V0, V1, V2
+    env_size: int = 0                     # M_e of an environment map (type-3 records), 0: none
 
     @property
     def n_vertices(self) -> int:
@@ -112,6 +118,8 @@ class Params:
     light_d: np.ndarray | None = None   # float32 [N_L]    distance d_j
     light_a: np.ndarray | None = None   # float32 [N_L]    relative area a_j
     light_p: np.ndarray | None = None   # float32 [N_L, 2] barycentric centre (p_j0, p_j1)
+    # environment-map radiance, for scenes with environment blocks
+    env: np.ndarray | None = None       # float32 [M_e, M_e, 3]
 
     def copy(self) -> "Params":
         return Params(**{f.name: (None if getattr(self, f.name) is None else getattr(self, f.name).copy())
@@ -396,6 +404,33 @@ def light_stage(n_lights, radius=3.0, side=0.5, hemisphere=False,
     return rec
 
 
+def env_blocks(env_size=32, block=4):
+    """Emitter records splitting an env_size x env_size environment map into
+    square blocks of block x block texels (one camera-sample direction per
+    block), row-major over the blocks; d = a = 1."""
+    if env_size % block:
+        raise ValueError("block must divide env_size")
+    nb = env_size // block
+    rec = np.zeros((nb * nb, 11), np.float32)
+    for bi in range(nb):
+        for bj in range(nb):
+            rec[bi * nb + bj, :5] = (LIGHT_ENV, bi * block, (bi + 1) * block, bj * block, (bj + 1) * block)
+    n = rec.shape[0]
+    return rec, np.ones(n, np.float32), np.ones(n, np.float32)
+
+
+def env_map(rng, env_size=32, lo=0.1, hi=0.6, n_suns=2, sun=6.0):
+    """Environment radiance [M_e, M_e, 3]: a smooth coloured field in [lo, hi]
+    plus n_suns bright texels (sun x a random colour) in the upper front
+    quarter of the sphere, so that shadows have sharp edges."""
+    env = smooth_field(rng, env_size, 3, env_size / 8.0, lo, hi)
+    for _ in range(n_suns):
+        i = int(rng.integers(env_size // 8, env_size // 2))
+        j = int(rng.integers(0, env_size // 4)) if rng.uniform() < 0.5 else int(rng.integers(3 * env_size // 4, env_size))
+        env[i, j] += sun * rng.uniform(0.5, 1.0, size=3)
+    return env.astype(np.float32)
+
+
 def _polyhedron(name):
     """Unit-circumradius convex polyhedra with triangular faces, counter-
     clockwise seen from outside: tetrahedron (4 faces), octahedron (8),
@@ -556,7 +591,9 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
     light_stage = "tetra" | "octa" | "ico" | "sphere80" replaces the lights by
     the polyhedral virtual light stage of Sec. 3.3 (light_area = a_j);
     albedo_k > 0 adds a statistical albedo model with that many columns per
-    albedo (Sec. 3.2; the paper's K_r = K_b = 80)."""
+    albedo (Sec. 3.2; the paper's K_r = K_b = 80); env = (M_e, block) replaces
+    the lights by an M_e x M_e environment map in blocks of block x block
+    texels (Sec. 7; the paper's map is 32 x 32)."""
     rng = np.random.default_rng(seed)
     if config == "c1":
         mean, basis, faces, uv = face_icosphere(rng, 4, 20, 0)
@@ -589,7 +626,13 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
     side = over.get("light_side", 0.5 if kind != LIGHT_DISK else 1.0)
     stage = over.get("light_stage")
     stage_geo = None
-    if stage is not None:                 # polyhedral stage: "tetra", "octa", "ico", "sphere80"
+    env = over.get("env")                 # (M_e, block): environment map of lights at infinity
+    env_size = 0
+    if env is not None:
+        env_size = int(env[0])
+        lights, light_d, light_a = env_blocks(env_size, int(env[1]))
+        nl = lights.shape[0]
+    elif stage is not None:                 # polyhedral stage: "tetra", "octa", "ico", "sphere80"
         lights, light_d, light_a = polyhedral_stage(stage, 3.0, over.get("light_area", 0.25))
         stage_geo = polyhedral_stage_geometry(stage)
         nl = lights.shape[0]
@@ -602,7 +645,7 @@ def make_scene(config: str = "c1", seed: int = 0, **over) -> Scene:
                  faces=np.ascontiguousarray(faces.astype(np.int32)), uv=_f32(uv),
                  lights=lights, light_d=light_d, light_a=light_a, width=int(w), height=int(h),
                  spp=int(spp), tex_size=int(m), fov_deg=30.0, albedo=albedo,
-                 landmarks=landmark_vertices(mean), stage=stage_geo)
+                 landmarks=landmark_vertices(mean), stage=stage_geo, env_size=env_size)
 
 
 def init_params(scene: Scene, seed: int = 0) -> Params:
@@ -618,7 +661,9 @@ def init_params(scene: Scene, seed: int = 0) -> Params:
                   light_i=np.full((scene.n_lights, 3), 0.8, np.float32),
                   diffuse=np.full((m, m, 3), 0.5, np.float32),
                   specular=np.full((m, m, 3), 0.05, np.float32),
-                  roughness=np.full((m, m), 0.45, np.float32))
+                  roughness=np.full((m, m), 0.45, np.float32),
+                  env=(np.full((scene.env_size, scene.env_size, 3), 0.3, np.float32)
+                       if scene.env_size else None))
 
 
 def random_params(scene: Scene, seed: int = 0, coef_scale: float = 1.0) -> Params:
@@ -634,7 +679,9 @@ def random_params(scene: Scene, seed: int = 0, coef_scale: float = 1.0) -> Param
                   trans=_f32(np.array(DEFAULT_T) + rng.normal(0.0, 0.03, size=3)),
                   focal=_f32([scene.focal_px()]),
                   light_i=_f32(rng.uniform(0.2, 1.5, size=(scene.n_lights, 3))),
-                  diffuse=diffuse, specular=specular, roughness=roughness)
+                  diffuse=diffuse, specular=specular, roughness=roughness,
+                  env=(env_map(np.random.default_rng(seed + 53), scene.env_size)
+                       if scene.env_size else None))
 
 
 def with_stage_geometry(scene: Scene, params: Params, seed: int | None = None) -> Params:
