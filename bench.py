@@ -50,8 +50,8 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is in profiles/k_forward_adjoint_c2_full.md.
-TRAFFIC = {"k_forward": {"bytes": 31639808 + 28963328,
-                         "sources_sha256": "45ec36f1fb601bd98e9583914afa4dd946b4f26b1638f160831bdd3e1bf61b0d"}}
+TRAFFIC = {"k_forward": {"bytes": 31548672 + 28748288,
+                         "sources_sha256": "2a721343f1a0d5bb871101dfe53732d7fb8dcf7e5ebf2b3c8378b958d6af638e"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 SMS = 152
 FP32_LANES_PER_SM = 128

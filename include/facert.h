@@ -77,6 +77,8 @@ typedef int32_t fr_status;
 #define FR_LIGHT_QUAD 0
 #define FR_LIGHT_TRI  1
 #define FR_LIGHT_DISK 2
+#define FR_LIGHT_ENV  3   /* block of an environment map of lights at infinity (Sec. 7) */
+#define FR_MAX_ENV   64   /* largest environment map: FR_MAX_ENV x FR_MAX_ENV texels */
 
 typedef struct fr_ctx fr_ctx;
 
@@ -109,7 +111,21 @@ typedef struct fr_mesh {
  *   (v-1/2) e2; triangle: c, c+e1, c+e2; disk: centre c, radius vectors e1, e2.
  *   The emitting side is the one e1 x e2 points to.  Geometry is in camera space.
  *   d [N_L], a [N_L]: distance and relative area of Eq. (lightIntensity); the
- *   emitted radiance is (d^2 / a) * i_j.  N_L <= 128. */
+ *   emitted radiance is (d^2 / a) * i_j.  N_L <= 128.
+ *   FR_LIGHT_ENV records {3, i0, i1, j0, j1, unused...} replace the light stage
+ *   by an environment map of lights at infinity (the alternative the paper
+ *   compares in Sec. 7): the record is the block of texel rows [i0, i1) and
+ *   columns [j0, j1) of an env_size x env_size latitude-longitude map, row i
+ *   spanning polar angles [i, i + 1] pi / env_size from camera-space +y and
+ *   column j azimuths [j, j + 1] 2 pi / env_size from +z towards +x.  The
+ *   radiance arriving from direction w is the texel of fr_params.env containing
+ *   w (d, a and i_j are not used).  Each camera sample draws one direction per
+ *   block: a texel uniformly among the block's (from the 24-bit integers behind
+ *   the block's two uniforms: row = i0 + floor(k_u R / 2^24), the remainder
+ *   placing the sample inside the row; columns likewise), then a direction
+ *   uniform in solid angle inside the texel; its shadow ray runs from the hit
+ *   point along w with t > 1e-4.  Blocks may be mixed with area emitters, not
+ *   with a virtual light stage. */
 typedef struct fr_light_stage {
     int32_t n_lights;
     const float* records;
@@ -125,6 +141,9 @@ typedef struct fr_light_stage {
      * (d_j^2 / a_j) i_j; the gradients then include d/d(d_j, a_j, p_j)
      * (interior and moving-emitter shadow-boundary terms). */
     const float* stage;
+    /* texels per side of the environment map of FR_LIGHT_ENV records,
+     * 1..FR_MAX_ENV (0: no such records) */
+    int32_t env_size;
 } fr_light_stage;
 
 /* Parameters chi-hat of Sec. 4 (device pointers, float32):
@@ -133,10 +152,13 @@ typedef struct fr_light_stage {
  *   light_i [N_L][3] perceived intensities i_j, diffuse [M][M][3],
  *   specular [M][M][3], roughness [M][M]; optionally (all three or none, with
  *   a stage set by fr_set_lights) the light geometry light_d [N_L],
- *   light_a [N_L] in (0, 1], light_p [N_L][2] (barycentric p0, p1). */
+ *   light_a [N_L] in (0, 1], light_p [N_L][2] (barycentric p0, p1); env
+ *   [env_size][env_size][3] the environment map's radiance (required when the
+ *   lights include FR_LIGHT_ENV records, else ignored). */
 typedef struct fr_params {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
     const float *light_d, *light_a, *light_p;
+    const float* env;
 } fr_params;
 
 /* Gradients, same shapes as fr_params (device pointers).  Every call ADDS
@@ -145,6 +167,7 @@ typedef struct fr_params {
 typedef struct fr_grads {
     float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
     float *light_d, *light_a, *light_p;
+    float* env;
 } fr_grads;
 
 /* Create a context for one image configuration.  Allocates the image-sized
@@ -158,7 +181,9 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg);
  * non-manifold edge, T < 1, K > 256), FR_ENOMEM, FR_ECUDA. */
 fr_status fr_set_mesh(fr_ctx* ctx, const fr_mesh* mesh);
 
-/* Copy the light-stage emitters (Sec. 3.3).  Synchronous.  Errors: FR_EINVAL. */
+/* Copy the light-stage emitters (Sec. 3.3).  Synchronous.  Errors: FR_EINVAL
+ * (unknown type, N_L out of range, an FR_LIGHT_ENV block outside the map or
+ * env_size out of range, environment blocks together with a stage). */
 fr_status fr_set_lights(fr_ctx* ctx, const fr_light_stage* stage);
 
 /* Statistical albedo model of Sec. 3.2 in UV texture space (host pointers,

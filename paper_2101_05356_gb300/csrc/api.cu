@@ -84,6 +84,8 @@ struct fr_ctx {
     LightDev* lights = nullptr;
     float* stage = nullptr;                    // virtual light stage frame [N_L][12] (null: records only)
     std::vector<float> light_d_h, light_a_h;   // host copies of the lights' d and a
+    int env_size = 0;                          // environment map side (0: no environment blocks)
+    bool use_stage = false;                    // the last fr_set_lights gave a light-stage frame
     std::vector<Slot> slots;
     DevItem* d_items = nullptr;                // device item table [FR_MAX_BATCH]
     std::vector<DevItem> h_items;
@@ -150,6 +152,7 @@ fr_status check_params(fr_ctx* c, const fr_params* p) {
     if (!p || !p->rot || !p->trans || !p->focal || !p->light_i || !p->diffuse || !p->specular || !p->roughness ||
         (c->K > 0 && !p->coef))
         return fail(c, FR_EINVAL, "null parameter pointer");
+    if (c->env_size > 0 && !p->env) return fail(c, FR_EINVAL, "environment blocks need the env parameter");
     return FR_OK;
 }
 
@@ -178,8 +181,9 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     s.lights = c->lights; s.status = c->status; s.counters = c->counters;
     const fr_params* p = a.p;
     it.P = DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness,
-                     p->light_d, p->light_a, p->light_p};
-    if (c->stage && p->light_d && p->light_a && p->light_p) {   // lights built from (d, a, p)
+                     p->light_d, p->light_a, p->light_p, c->env_size > 0 ? p->env : nullptr};
+    s.env_size = c->env_size;
+    if (c->use_stage && p->light_d && p->light_a && p->light_p) {   // lights built from (d, a, p)
         s.stage = c->stage;
         s.lights = sl.lights;
         it.lights_w = sl.lights;
@@ -200,6 +204,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
         it.g_light_d = a.g->light_d;
         it.g_light_a = a.g->light_a;
         it.g_light_p = a.g->light_p;
+        it.g_env = c->env_size > 0 ? a.g->env : nullptr;
     }
     it.EL.edges = c->edges;
     it.EL.prim_list = sl.lists;
@@ -352,7 +357,7 @@ fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
         const DevItem& it = c->h_items[k];
         if (it.S.spp > 32) CK(c, cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)it.S.W * it.S.H, st));
     }
-    launch_forward(c->d_items, map_of(c, n, false), st);
+    launch_forward(c->d_items, map_of(c, n, false), c->env_size > 0, st);
     return FR_OK;
 }
 
@@ -370,7 +375,7 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     for (int k = 0; k < n; ++k) all_recorded &= c->h_items[k].rec_tri != nullptr;
     bool any_stage = false;
     for (int k = 0; k < n; ++k) any_stage |= c->h_items[k].S.stage != nullptr;
-    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_recorded, any_stage, st);
+    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_recorded, any_stage, c->env_size > 0, st);
     mark(c, 5, st);
     long max_edge = 0;
     for (int k = 0; k < n; ++k) {
@@ -378,7 +383,7 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
         if (!(s.flags & FR_FLAG_NO_PRIMARY_EDGE)) max_edge = std::max(max_edge, (long)s.W * s.H * s.edge_spp);
     }
     launch_edge_order(c->d_items, n, max_edge, st);
-    launch_edge_primary(c->d_items, map_of(c, n, true), st);
+    launch_edge_primary(c->d_items, map_of(c, n, true), c->env_size > 0, st);
     mark(c, 6, st);
     launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
@@ -488,7 +493,7 @@ void ctx_info(const fr_ctx* c, CtxInfo& o) {
     o.have_albedo = c->have_albedo;
     o.k_diffuse = c->have_albedo ? c->albedo[0].K : 0;
     o.k_specular = c->have_albedo ? c->albedo[1].K : 0;
-    o.have_stage = c->stage != nullptr;
+    o.have_stage = c->use_stage;
     o.light_scale.resize(c->light_d_h.size());
     for (size_t j = 0; j < c->light_d_h.size(); ++j) {
         const float d2 = c->light_d_h[j] * c->light_d_h[j];
@@ -715,11 +720,28 @@ fr_status fr_set_lights(fr_ctx* c, const fr_light_stage* ls) {
     if (!c || !ls || !ls->records || !ls->d || !ls->a) return fail(c, FR_EINVAL, "null argument");
     if (ls->n_lights < 1 || ls->n_lights > FR_MAX_LIGHTS) return fail(c, FR_EINVAL, "1 <= n_lights <= 128");
     std::vector<LightDev> L(ls->n_lights);
+    bool any_env = false;
     for (int j = 0; j < ls->n_lights; ++j) {
         const float* r = ls->records + 11 * j;
         LightDev& d = L[j];
         d.type = (int)r[0];
-        if (d.type < 0 || d.type > 2) return fail(c, FR_EINVAL, "unknown emitter type");
+        if (d.type < 0 || d.type > 3) return fail(c, FR_EINVAL, "unknown emitter type");
+        if (d.type == FR_LIGHT_ENV) {             // environment block: integer texel ranges
+            const int me = ls->env_size;
+            if (me < 1 || me > FR_MAX_ENV) return fail(c, FR_EINVAL, "env_size must be 1..64 with environment blocks");
+            const int i0 = (int)r[1], i1 = (int)r[2], j0 = (int)r[3], j1 = (int)r[4];
+            if ((float)i0 != r[1] || (float)i1 != r[2] || (float)j0 != r[3] || (float)j1 != r[4] || i0 < 0 ||
+                i1 <= i0 || i1 > me || j0 < 0 || j1 <= j0 || j1 > me)
+                return fail(c, FR_EINVAL, "environment block outside the map");
+            d.c = f3((float)i0, (float)i1, (float)j0);
+            d.e1 = f3((float)j1, 0.0f, 0.0f);
+            d.e2 = d.n = f3(0.0f, 0.0f, 0.0f);
+            d.area = (float)((i1 - i0) * (j1 - j0));
+            d.scale = 1.0f;
+            d.env = me;
+            any_env = true;
+            continue;
+        }
         d.c = f3(r[1], r[2], r[3]);
         d.e1 = f3(r[4], r[5], r[6]);
         d.e2 = f3(r[7], r[8], r[9]);
@@ -734,10 +756,13 @@ fr_status fr_set_lights(fr_ctx* c, const fr_light_stage* ls) {
         else if (d.type == 1) d.area = (float)(0.5 * cl);
         else d.area = (float)(3.14159265358979323846 * ((double)d.e1.x * d.e1.x + (double)d.e1.y * d.e1.y + (double)d.e1.z * d.e1.z));
         d.scale = (float)((double)ls->d[j] * ls->d[j] / ls->a[j]);
-        d.pad = 0;
+        d.env = 0;
     }
+    if (any_env && ls->stage) return fail(c, FR_EINVAL, "environment blocks cannot be combined with a light stage");
     if (!c->lights) TRY(dalloc(c, &c->lights, FR_MAX_LIGHTS));
     CK(c, cudaMemcpy(c->lights, L.data(), sizeof(LightDev) * L.size(), cudaMemcpyHostToDevice));
+    c->env_size = any_env ? ls->env_size : 0;
+    c->use_stage = ls->stage != nullptr;
     if (ls->stage) {
         if (!c->stage) TRY(dalloc(c, &c->stage, 12 * (size_t)FR_MAX_LIGHTS));
         CK(c, cudaMemcpy(c->stage, ls->stage, sizeof(float) * 12 * ls->n_lights, cudaMemcpyHostToDevice));

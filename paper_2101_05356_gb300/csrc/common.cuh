@@ -12,6 +12,7 @@
 #define FR_STATUS_BAD_BVH 4
 
 constexpr int FR_MAX_LIGHTS = 128;
+constexpr int FR_MAX_ENV_D = 64;       // environment map side (FR_MAX_ENV of the C interface)
 constexpr int FR_MAX_BASIS = 256;
 constexpr int FR_STACK = 64;           // traversal stack entries per thread
 constexpr float FR_PI = 3.14159265358979323846f;
@@ -73,10 +74,14 @@ struct Sampler {
 // ---------------------------------------------------------------------------
 // device-side scene description (plain pointers, passed by value to kernels)
 // ---------------------------------------------------------------------------
+// Area emitters (types 0-2) use c, e1, e2, n, area and scale.  An environment
+// block (type 3, lights at infinity, Sec. 7) keeps its texel rows [i0, i1) and
+// columns [j0, j1) as small integers in c = (i0, i1, j0) and e1.x = j1, the
+// map's side in `env`; area = texels in the block, scale = 1.
 struct LightDev {
     float3 c, e1, e2, n;   // n: unit normal of the emitting side
     float area, scale;     // scale = d^2 / a  (Eq. lightIntensity)
-    int type, pad;
+    int type, env;
 };
 
 // Binary BVH node holding both children's boxes (64 B, four 16-B loads).
@@ -99,6 +104,7 @@ struct DevScene {
     const LightDev* lights; // [NL]
     const float* stage;     // [NL][12] virtual light stage frame (centre, unit face V0 V1 V2);
                             // non-null when the lights are built from (d, a, p) parameters
+    int env_size;           // side of the environment map (0: no environment blocks)
     int* status;
     unsigned long long* counters;   // [3][3]: per kernel (forward, adjoint, primary edges) rays, nodes, triangle tests
 };
@@ -125,12 +131,15 @@ FR_D void flush_stats(unsigned long long* counters, const RayStats& rs) {
 struct DevParams {
     const float *coef, *rot, *trans, *focal, *light_i, *diffuse, *specular, *roughness;
     const float *light_d, *light_a, *light_p;   // light stage geometry [NL], [NL], [NL][2]
+    const float* env;                           // environment radiance [env][env][3]
 };
 
 // Fixed-point accumulator layout of G.small: focal, then 3 per light
-// (intensity), then from FR_GEO_OFF 4 per light (d, a, p0, p1).
+// (intensity), then from FR_GEO_OFF 4 per light (d, a, p0, p1), then from
+// FR_ENV_OFF 3 per environment texel.
 constexpr int FR_GEO_OFF = 1 + 3 * FR_MAX_LIGHTS;
-constexpr int FR_SMALL = FR_GEO_OFF + 4 * FR_MAX_LIGHTS;
+constexpr int FR_ENV_OFF = FR_GEO_OFF + 4 * FR_MAX_LIGHTS;
+constexpr int FR_SMALL = FR_ENV_OFF + 3 * FR_MAX_ENV_D * FR_MAX_ENV_D;
 
 // Gradient sums are kept in 64-bit fixed point (resolution 2^-32, range
 // +-2^31): integer addition is associative, so a sum does not depend on the
@@ -210,6 +219,7 @@ struct DevItem {
     int* edge_perm;         // processing order of the primary-edge samples (null: index order)
     float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
     float *g_light_d, *g_light_a, *g_light_p;            // light stage geometry gradients (may be null)
+    float* g_env;                                         // environment radiance gradient (may be null)
     LightDev* lights_w;     // write side of S.lights when built from stage parameters
     uint32_t iteration, face;
 };

@@ -45,8 +45,10 @@ __global__ void k_zero_acc(const DevItem* items, int N, int M) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 3L * N) { it.G.d_v[i] = 0ull; it.G.d_n[i] = 0ull; }
     if (i < 7L * M * M) it.G.tex[i] = 0ull;
-    if (blockIdx.x == 0)
-        for (int k = threadIdx.x; k < FR_SMALL; k += blockDim.x) it.G.small[k] = 0ull;
+    if (blockIdx.x == 0) {
+        const int n_small = FR_ENV_OFF + 3 * it.S.env_size * it.S.env_size;
+        for (int k = threadIdx.x; k < n_small; k += blockDim.x) it.G.small[k] = 0ull;
+    }
 }
 
 // add the fixed-point texture gradients into the caller's float gradients
@@ -279,6 +281,9 @@ __global__ void k_pose_finish(const DevItem* items, int NL, int n_blocks) {
     }
     if (it.g_light)
         for (int k = t; k < 3 * NL; k += blockDim.x) it.g_light[k] += (float)from_fix(small[1 + k]);
+    if (it.g_env)
+        for (int k = t; k < 3 * it.S.env_size * it.S.env_size; k += blockDim.x)
+            it.g_env[k] += (float)from_fix(small[FR_ENV_OFF + k]);
     if (it.S.stage)
         for (int k = t; k < 4 * NL; k += blockDim.x) {
             const int j = k >> 2, q = k & 3;
@@ -310,7 +315,7 @@ __global__ void k_stage_lights(const DevItem* items, int NL) {
     const float3 t0 = P + (A - G) * s, t1 = P + (V - G) * s, t2 = P + (B - G) * s;
     LightDev L;
     L.type = 1;
-    L.pad = 0;
+    L.env = 0;
     L.c = t0;
     L.e1 = t1 - t0;
     L.e2 = t2 - t0;

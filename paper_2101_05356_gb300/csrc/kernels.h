@@ -91,11 +91,11 @@ void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* sta
 void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);
 
 // render.cu
-void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st);
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage,
+void launch_forward(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st);
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage, bool env,
                     cudaStream_t st);
 void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st);
-void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st);
+void launch_edge_primary(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri,
                        float* t, cudaStream_t st);

@@ -46,7 +46,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float SHADOW_EPS = 1e-4f;     // shadow segment trimmed to (eps, 1 - eps)
 
 struct WarpQueue {
-    float4 job[64][2];                  // (y.xyz, z.x) (z.y, z.z, skip, owner | light << 8)
+    float4 job[64][2];                  // (y.xyz, z.x) (z.y, z.z, skip, owner | light << 8 | distant << 16)
     unsigned long long vis[32];
 };
 
@@ -149,15 +149,21 @@ FR_D bool light_visible_geometry(const LightDev& L, float3 z, const SampleState&
 }
 
 // Trace the queued jobs [head, head + n) of this warp's ring (lane k takes job k).
+// ENV: the launch may hold environment blocks (lights at infinity); otherwise
+// their code is compiled out.
+template <bool ENV>
 FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st, RayStats& rs) {
     const int lane = threadIdx.x & 31;
     if (lane < n) {
         const float4 a = q.job[(head + lane) & 63][0], b = q.job[(head + lane) & 63][1];
         const float3 y = f3(a.x, a.y, a.z), z = f3(a.w, b.x, b.y);
         const int skip = __float_as_int(b.z), tag = __float_as_int(b.w);
-        const RayPre r = ray_setup(y, z - y);
-        if (!trace_any(S, r, SHADOW_EPS, 1.0f - SHADOW_EPS, skip, st, rs))
-            atomicOr(&q.vis[tag & 31], 1ull << (tag >> 8));
+        // a segment y -> z to an area emitter, or a ray along the direction z
+        // to a light at infinity
+        const bool distant = ENV && ((tag >> 16) & 1);
+        const RayPre r = ray_setup(y, distant ? z : z - y);
+        if (!trace_any(S, r, SHADOW_EPS, distant ? INFINITY : 1.0f - SHADOW_EPS, skip, st, rs))
+            atomicOr(&q.vis[tag & 31], 1ull << ((tag >> 8) & 63));
     }
     __syncwarp();
 }
@@ -165,6 +171,7 @@ FR_D void drain(const DevScene& S, WarpQueue& q, int head, int n, Stack st, RayS
 // Warp-cooperative shadow visibility for the lights [j0, j0 + 64): bit j - j0
 // is set when the shadow ray to this lane's light-j sample is traced and
 // unoccluded.  All 32 lanes must call this together.
+template <bool ENV>
 FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sampler& smp, int dim0,
                           WarpQueue& q, Stack st, RayStats& rs, int j0) {
     const int lane = threadIdx.x & 31;
@@ -177,27 +184,34 @@ FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sample
     for (int j = j0; j < j1; ++j) {
         bool need = false;
         float3 z = f3(0.0f, 0.0f, 0.0f);
+        const bool distant = ENV && S.lights[j].type == FR_LIGHT_ENV_D;      // warp-uniform
         if (want) {
             const LightDev& L = S.lights[j];
             const float2 u = dc.pair(smp, dim0 + 2 * j);
-            z = light_point(L, u.x, u.y);
-            need = light_visible_geometry(L, z, ss);
+            if (distant) {                       // z = the direction of the sample
+                z = env_sample(L, u.x, u.y).w;
+                need = dot(ss.ns, z) > 0.0f;
+            } else {
+                z = light_point(L, u.x, u.y);
+                need = light_visible_geometry(L, z, ss);
+            }
         }
         const unsigned ballot = __ballot_sync(FULL, need);
         if (need) {
             const int slot = (head + count + __popc(ballot & ((1u << lane) - 1u))) & 63;
             q.job[slot][0] = make_float4(ss.y.x, ss.y.y, ss.y.z, z.x);
-            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.tri), __int_as_float(lane | ((j - j0) << 8)));
+            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.tri),
+                                         __int_as_float(lane | ((j - j0) << 8) | ((int)distant << 16)));
         }
         count += __popc(ballot);
         __syncwarp();
         if (count >= 32) {
-            drain(S, q, head, 32, st, rs);
+            drain<ENV>(S, q, head, 32, st, rs);
             head = (head + 32) & 63;
             count -= 32;
         }
     }
-    if (count > 0) drain(S, q, head, count, st, rs);
+    if (count > 0) drain<ENV>(S, q, head, count, st, rs);
     return q.vis[lane];
 }
 
@@ -235,6 +249,29 @@ FR_D float3 light_h(uint32_t flags, const LightDev& L, float3 z, const SampleSta
     return f * geo;
 }
 
+// Unoccluded contribution of a light at infinity in direction l (without the
+// 1/pdf weight): h = f_r cos_s.  l does not depend on the parameters; with ADJ
+// the upstream gradient gh flows into g's n, o, c, s and r.
+template <bool ADJ>
+FR_D float3 light_h_env(uint32_t flags, float3 l, const SampleState& ss, float3 gh, ShadeAdj* g) {
+    const float cos_s = dot(ss.ns, l);
+    if (!(cos_s > 0.0f) || !ss.lit) return f3(0.0f, 0.0f, 0.0f);
+    float3 f;
+    if (ADJ) {
+        const float3 keep_l = g->l;
+        f = brdf<true>(flags, ss.ns, l, ss.o, ss.m, gh * cos_s, g);
+        g->l = keep_l;
+        g->n += l * (gh.x * f.x + gh.y * f.y + gh.z * f.z);
+    } else {
+        f = brdf<false>(flags, ss.ns, l, ss.o, ss.m, f3(0, 0, 0), nullptr);
+    }
+    return f * cos_s;
+}
+
+FR_D float3 env_radiance(const DevParams& P, int texel) {
+    return f3(__ldg(&P.env[3 * texel]), __ldg(&P.env[3 * texel + 1]), __ldg(&P.env[3 * texel + 2]));
+}
+
 // Light j's frame in the virtual light stage and the velocities of an emitter
 // point z (held at its emitter coordinates) with respect to (d, a, p0, p1):
 // dz/dd = (z - C) / d, dz/da = (z - P) / (2 a), dz/dp0 = d (V0 - V2),
@@ -264,6 +301,7 @@ FR_D float3 intensity(const DevScene& S, const DevParams& P, int j) {
 }
 
 // Radiance of this lane's sample given its state and visibility mask.
+template <bool ENV>
 FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleState& ss, uint64_t vis,
                           const Sampler& smp, int dim0, int j0) {
     float3 Lo = f3(0.0f, 0.0f, 0.0f);
@@ -275,6 +313,13 @@ FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleSta
         if (!((vis >> (j - j0)) & 1ull)) continue;
         const LightDev& L = S.lights[j];
         const float2 u = dc.pair(smp, dim0 + 2 * j);
+        if (ENV && L.type == FR_LIGHT_ENV_D) {
+            const EnvDir ed = env_sample(L, u.x, u.y);
+            const float3 h = light_h_env<false>(S.flags, ed.w, ss, f3(0, 0, 0), nullptr);
+            const float3 E = env_radiance(P, ed.texel);
+            Lo += f3(h.x * E.x, h.y * E.y, h.z * E.z) * ed.weight;
+            continue;
+        }
         const float3 z = light_point(L, u.x, u.y);
         const float3 h = light_h<false>(S.flags, L, z, ss, f3(0, 0, 0), nullptr, nullptr);
         const float3 I = intensity(S, P, j);
@@ -284,6 +329,7 @@ FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleSta
 }
 
 // Full warp-cooperative radiance evaluation at screen point (sx, sy).
+template <bool ENV>
 FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
                         const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t* vis,
                         RayStats& rs) {
@@ -291,9 +337,9 @@ FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, floa
     float3 Lo = f3(0.0f, 0.0f, 0.0f);
     vis[0] = vis[1] = 0ull;
     for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) {          // lights in chunks of 64 (warp-uniform)
-        const uint64_t v = shadow_mask(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
+        const uint64_t v = shadow_mask<ENV>(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
         vis[j0 >> 6] = v;
-        Lo += radiance_from(S, P, ss, v, smp, dim0, j0);
+        Lo += radiance_from<ENV>(S, P, ss, v, smp, dim0, j0);
     }
     return Lo;
 }
@@ -310,6 +356,7 @@ FR_D float group_sum(float v, int width) {
     return v;
 }
 
+template <bool ENV>
 __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
     FR_STACK_DECL
@@ -331,7 +378,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
     SampleState ss;
     uint64_t vis[2];
     RayStats rs;
-    const float3 Lo = radiance_at(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
+    const float3 Lo = radiance_at<ENV>(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
                                   smp, 2, sh, my_stack(sh), ss, vis, rs);
     flush_stats(S.counters + 0, rs);
     if (valid && tri_rec) tri_rec[q] = ss.tri;
@@ -389,9 +436,67 @@ FR_D void scatter_vertex(fix64* base, int vertex, float3 g, bool on) {
     warp_agg_add_n<3>(a, v, (uint32_t)vertex, act);
 }
 
+// Is edge E (first vertex A) a silhouette seen from y?  Boundary edges always
+// are; an interior edge is when y lies strictly on different sides of its two
+// faces' planes (FP64).
+FR_D bool silhouette_from(const DevScene& S, int4 E, float3 A, float3 y) {
+    if (E.w < 0) return true;
+    const int4 ff[2] = {S.faces[E.z], S.faces[E.w]};
+    const double yx = (double)y.x - A.x, yy = (double)y.y - A.y, yz = (double)y.z - A.z;
+    int sg[2];
+    for (int k = 0; k < 2; ++k) {
+        const float4 p0 = S.v[ff[k].x], p1 = S.v[ff[k].y], p2 = S.v[ff[k].z];
+        const double e1x = (double)p1.x - p0.x, e1y = (double)p1.y - p0.y, e1z = (double)p1.z - p0.z;
+        const double e2x = (double)p2.x - p0.x, e2y = (double)p2.y - p0.y, e2z = (double)p2.z - p0.z;
+        const double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+        const double dd = nx * yx + ny * yy + nz * yz;
+        sg[k] = (dd > 0.0) - (dd < 0.0);
+    }
+    return sg[0] != sg[1];
+}
+
+// Shadow-boundary sample for a light at infinity: the boundary lies on the
+// sphere of directions, w(t) = (p(t) - y) / |p(t) - y| for the edge point
+// p(t) = A + t (B - A).  Its normal velocity is m . (dp - dy) / |p - y| with m
+// the curve's unit normal tangent to the sphere, and arc length |dw/dt| dt.
+FR_D void shadow_edge_env(const DevScene& S, const DevParams& P, const LightDev& L, const SampleState& ss, int4 E,
+                          float3 A, float3 B, float t, int Sj, float3 w, float3& gy, fix64* d_v, Stack st,
+                          RayStats& rs) {
+    const float3 e = B - A;
+    const float3 q = A + e * t - ss.y;
+    const float r2 = dot(q, q);
+    if (!(r2 > 0.0f)) return;
+    const float inv_r = 1.0f / sqrtf(r2);
+    const float3 wv = q * inv_r;
+    int row, col;
+    env_texel_of(wv, L.env, row, col);
+    if (!env_block_has(L, row, col)) return;
+    if (!silhouette_from(S, E, A, ss.y)) return;
+    const float3 h = light_h_env<false>(S.flags, wv, ss, f3(0, 0, 0), nullptr);
+    if (h.x == 0.0f && h.y == 0.0f && h.z == 0.0f) return;
+    const float3 tan = (e - wv * dot(wv, e)) * inv_r;     // dw/dt
+    const float tl = length(tan);
+    if (!(tl > 0.0f)) return;
+    const float3 m = cross(wv, tan) * (1.0f / tl);
+    float3 wp = wv + m * SHADOW_EPS, wm = wv - m * SHADOW_EPS;
+    wp = wp * (1.0f / length(wp));
+    wm = wm * (1.0f / length(wm));
+    const bool vp = !trace_any(S, ray_setup(ss.y, wp), SHADOW_EPS, INFINITY, ss.tri, st, rs);
+    const bool vm = !trace_any(S, ray_setup(ss.y, wm), SHADOW_EPS, INFINITY, ss.tri, st, rs);
+    const float dV = (float)vp - (float)vm;
+    if (dV == 0.0f) return;
+    const float3 Le = env_radiance(P, row * L.env + col);
+    const float C = -dV * (float)S.NL * (float)Sj * tl * (w.x * h.x * Le.x + w.y * h.y * Le.y + w.z * h.z * Le.z);
+    const float3 gp = m * (C * inv_r);
+    gy -= gp;
+    add_vec(d_v, E.x, gp * (1.0f - t), true);
+    add_vec(d_v, E.y, gp * t, true);
+}
+
 // One shadow-boundary edge sample at this lane's shading point (edge sampling
 // for visibility of the emitter, Sec. 4).  Adds C * dz/dy . m to gy and
 // scatters the edge-vertex terms.  Returns nothing; inactive lanes do nothing.
+template <bool ENV>
 FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL, const SampleState& ss,
                       const Sampler& sm2, float3 w, float3& gy, fix64* d_v, fix64* small, Stack st, RayStats& rs) {
     const uint4 blk = sm2.block(0);
@@ -411,6 +516,10 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     // order does not change which samples count)
     const LightDev& L = S.lights[j];
     const float t = u2;
+    if (ENV && L.type == FR_LIGHT_ENV_D) {
+        shadow_edge_env(S, P, L, ss, E, A, B, t, Sj, w, gy, d_v, st, rs);
+        return;
+    }
     const float3 e = B - A;
     const float3 pe = A + e * t;
     const float3 q = pe - ss.y;
@@ -421,23 +530,7 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     if (!(sc > 1.0f)) return;
     const float3 z = ss.y + q * sc;
     if (!inside_emitter(L, z)) return;
-    if (E.w >= 0) {
-        // silhouette w.r.t. y, in FP64
-        const int4 f1 = S.faces[E.z], f2 = S.faces[E.w];
-        const double ax = A.x, ay = A.y, az = A.z;
-        const double yx = (double)ss.y.x - ax, yy = (double)ss.y.y - ay, yz = (double)ss.y.z - az;
-        int sg[2];
-        const int4 ff[2] = {f1, f2};
-        for (int k = 0; k < 2; ++k) {
-            const float4 p0 = S.v[ff[k].x], p1 = S.v[ff[k].y], p2 = S.v[ff[k].z];
-            const double e1x = (double)p1.x - p0.x, e1y = (double)p1.y - p0.y, e1z = (double)p1.z - p0.z;
-            const double e2x = (double)p2.x - p0.x, e2y = (double)p2.y - p0.y, e2z = (double)p2.z - p0.z;
-            const double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-            const double dd = nx * yx + ny * yy + nz * yz;
-            sg[k] = (dd > 0.0) - (dd < 0.0);
-        }
-        if (sg[0] == sg[1]) return;
-    }
+    if (!silhouette_from(S, E, A, ss.y)) return;
     const float3 h = light_h<false>(S.flags, L, z, ss, f3(0, 0, 0), nullptr, nullptr);
     if (h.x == 0.0f && h.y == 0.0f && h.z == 0.0f) return;
     const float3 tan = (e - q * (dot(e, L.n) / den)) * sc;
@@ -476,7 +569,7 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
 // RECORDED: every item of the launch carries the forward's hit records, so the
 // camera and shadow traversals are compiled out (a smaller kernel); otherwise
 // each item re-traces unless it has records.
-template <bool RECORDED>
+template <bool RECORDED, bool ENV>
 __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS : FR_ADJ_MIN_BLOCKS)
     k_adjoint(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
@@ -529,7 +622,29 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
                 if (recorded)
                     vis = valid ? it.rec_vis[2 * qi + (j >> 6)] : 0ull;
                 else
-                    vis = shadow_mask(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
+                    vis = shadow_mask<ENV>(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
+            }
+            if (ENV && S.lights[j].type == FR_LIGHT_ENV_D) {    // warp-uniform
+                // a light at infinity: the radiance gradient goes to the sampled texel
+                float3 ge = f3(0.0f, 0.0f, 0.0f);
+                int texel = 0;
+                if (interior && ss.hit && ((vis >> (j & 63)) & 1ull)) {
+                    const float2 u = dc.pair(smp, 2 + 2 * j);
+                    const EnvDir ed = env_sample(S.lights[j], u.x, u.y);
+                    const float3 E = env_radiance(P, ed.texel);
+                    const float3 h = light_h_env<true>(S.flags, ed.w, ss, f3(w.x * E.x, w.y * E.y, w.z * E.z) * ed.weight, &g);
+                    ge = f3(w.x * h.x, w.y * h.y, w.z * h.z) * ed.weight;
+                    texel = ed.texel;
+                }
+                const bool add = ge.x != 0.0f || ge.y != 0.0f || ge.z != 0.0f;
+                const unsigned act = __ballot_sync(FULL, add);
+                if (add) {
+                    fix64* const a[3] = {&G.small[FR_ENV_OFF + 3 * texel], &G.small[FR_ENV_OFF + 3 * texel + 1],
+                                         &G.small[FR_ENV_OFF + 3 * texel + 2]};
+                    const float v[3] = {ge.x, ge.y, ge.z};
+                    warp_agg_add_n<3>(a, v, (uint32_t)texel, act);
+                }
+                continue;
             }
             float3 gI = f3(0.0f, 0.0f, 0.0f);
             float gl4[4] = {0.0f, 0.0f, 0.0f, 0.0f};            // d, a, p0, p1 of light j
@@ -577,7 +692,7 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         }
         if (!(S.flags & FR_FLAG_NO_SHADOW_EDGE_D) && ss.hit && ss.lit) {
             const Sampler sm2{make_uint2(S.seed, FR_STREAM_EDGE_SHADOW), (uint32_t)pixel, (uint32_t)s, iteration, face};
-            shadow_edge(S, P, EL, ss, sm2, w, gy, G.d_v, G.small, my_stack(sh), rs);
+            shadow_edge<ENV>(S, P, EL, ss, sm2, w, gy, G.d_v, G.small, my_stack(sh), rs);
         }
     }
     // ---- chain rule back to the hit triangle, its normals and the camera ----
@@ -760,6 +875,7 @@ __global__ void __launch_bounds__(EDGE_SORT_THREADS) k_edge_order(const DevItem*
 // ---------------------------------------------------------------------------
 // primary-visibility boundary term: edge samples in screen space
 // ---------------------------------------------------------------------------
+template <bool ENV>
 __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary(const DevItem* items, BlockMap map) {
     __shared__ RtShared sh;
     FR_STACK_DECL
@@ -822,7 +938,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
     SampleState ss;
     uint64_t vis[2];
     RayStats rs;
-    const float3 L = radiance_at(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, my_stack(sh), ss, vis, rs);
+    const float3 L = radiance_at<ENV>(S, P, active, X + eps * mx, Y + eps * my, smp, 4, sh, my_stack(sh), ss, vis, rs);
     const float3 Lo = f3(__shfl_xor_sync(FULL, L.x, 1), __shfl_xor_sync(FULL, L.y, 1), __shfl_xor_sync(FULL, L.z, 1));
     const float3 Lp = side ? Lo : L, Lm = side ? L : Lo;
     if (side) active = false;                          // the even lane adds the pair's term
@@ -875,6 +991,43 @@ FR_D void emitter_range(int type, Real base, Real g1, Real g2, Real& lo, Real& h
     }
 }
 
+// Range [lo, hi] of n . w over the directions w of environment block L, in
+// FP64: n . w = n_y cos t + sin t A(p), A(p) = n_x sin p + n_z cos p.  A's range
+// over the block's azimuths comes from the ends and its extremes at
+// p = atan2(n_x, n_z) + k pi; as sin t >= 0 the minimum (maximum) over the
+// block is that of n_y cos t + A_min sin t (A_max) over the polar range, a
+// sinusoid whose extremes lie at the ends or at atan2(A, n_y) + k pi.
+__device__ void env_range(const LightDev& L, double3 n, double& lo, double& hi) {
+    const double Me = L.env;
+    const double t0 = 3.14159265358979323846 * (double)L.c.x / Me, t1 = 3.14159265358979323846 * (double)L.c.y / Me;
+    const double f0 = 6.28318530717958647692 * (double)L.c.z / Me, f1 = 6.28318530717958647692 * (double)L.e1.x / Me;
+    const double A0 = n.x * sin(f0) + n.z * cos(f0), A1 = n.x * sin(f1) + n.z * cos(f1);
+    double a_lo = fmin(A0, A1), a_hi = fmax(A0, A1);
+    const double pa = atan2(n.x, n.z);
+    for (int k = -2; k <= 3; ++k) {
+        const double p = pa + k * 3.14159265358979323846;
+        if (p > f0 && p < f1) {
+            const double Ap = n.x * sin(p) + n.z * cos(p);
+            a_lo = fmin(a_lo, Ap);
+            a_hi = fmax(a_hi, Ap);
+        }
+    }
+    for (int side = 0; side < 2; ++side) {
+        const double a = side ? a_hi : a_lo;
+        const double g0 = n.y * cos(t0) + a * sin(t0), g1 = n.y * cos(t1) + a * sin(t1);
+        double r = side ? fmax(g0, g1) : fmin(g0, g1);
+        const double tc = atan2(a, n.y);
+        for (int k = -1; k <= 2; ++k) {
+            const double t = tc + k * 3.14159265358979323846;
+            if (t > t0 && t < t1) {
+                const double g = n.y * cos(t) + a * sin(t);
+                r = side ? fmax(r, g) : fmin(r, g);
+            }
+        }
+        if (side) hi = r; else lo = r;
+    }
+}
+
 // Facing class of face f over emitter j: 1 = every point of the emitter is in
 // front of the face's plane, 2 = every point behind, 3 = mixed, decided in
 // FP64.  An FP32 evaluation decides first whenever it is farther from zero
@@ -898,6 +1051,12 @@ __global__ void k_face_class(const DevItem* items) {
     const double d = n.x * p0.x + n.y * p0.y + n.z * p0.z;
     for (int j = 0; j < S.NL; ++j) {
         const LightDev& L = S.lights[j];
+        if (L.type == FR_LIGHT_ENV_D) {        // a point at infinity along w is in front iff n . w > 0
+            double lo, hi;
+            env_range(L, n, lo, hi);
+            it.sil_flags[(size_t)(1 + FR_MAX_LIGHTS) * S.E + (size_t)j * S.T + f] = lo > 0.0 ? 1 : (hi < 0.0 ? 2 : 3);
+            continue;
+        }
         {
             const float3 w = L.c - q0;
             float lo32, hi32;
@@ -1035,31 +1194,46 @@ int map_blocks(const BlockMap& m) { return m.block0[m.n]; }
 #ifndef FR_CARVEOUT
 #define FR_CARVEOUT -1
 #endif
+template <bool ENV>
 void set_carveout() {
     static bool done = false;
     if (done || FR_CARVEOUT < 0) return;
-    cudaFuncSetAttribute(k_forward, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
-    cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
-    cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
-    cudaFuncSetAttribute(k_edge_primary, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
+    cudaFuncSetAttribute(k_forward<ENV>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
+    cudaFuncSetAttribute(k_adjoint<false, ENV>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
+    cudaFuncSetAttribute(k_adjoint<true, ENV>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
+    cudaFuncSetAttribute(k_edge_primary<ENV>, cudaFuncAttributePreferredSharedMemoryCarveout, FR_CARVEOUT);
     done = true;
 }
 
-void launch_forward(const DevItem* items, const BlockMap& map, cudaStream_t st) {
+// env: some item of the launch has environment blocks (the kernels compiled
+// with their code); otherwise the light-stage-only instantiation runs.
+void launch_forward(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    set_carveout();
-    k_forward<<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+    if (env) {
+        set_carveout<true>();
+        k_forward<true><<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+    } else {
+        set_carveout<false>();
+        k_forward<false><<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+    }
     fr_count_launches(1);
 }
 
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage,
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage, bool env,
                     cudaStream_t st) {
     if (map_blocks(map) == 0) return;
     const size_t acc_bytes = sizeof(float) * RT_WARPS * (1 + (any_stage ? 7 : 3) * (size_t)NL);
-    if (all_recorded)
-        k_adjoint<true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
-    else
-        k_adjoint<false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+    if (env) {
+        if (all_recorded)
+            k_adjoint<true, true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+        else
+            k_adjoint<false, true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+    } else {
+        if (all_recorded)
+            k_adjoint<true, false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+        else
+            k_adjoint<false, false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+    }
     fr_count_launches(1);
 }
 
@@ -1069,9 +1243,12 @@ void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t 
     fr_count_launches(1);
 }
 
-void launch_edge_primary(const DevItem* items, const BlockMap& map, cudaStream_t st) {
+void launch_edge_primary(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
-    k_edge_primary<<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
+    if (env)
+        k_edge_primary<true><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
+    else
+        k_edge_primary<false><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
     fr_count_launches(1);
 }
 

@@ -10,6 +10,7 @@
 #define FR_FLAG_NO_PRIMARY_EDGE_D 32u
 #define FR_FLAG_NO_SHADOW_EDGE_D 64u
 #define FR_FLAG_VIEW_CUTOFF_D 1024u
+#define FR_LIGHT_ENV_D 3
 
 // Uniform area sample of an emitter.
 FR_D float3 light_point(const LightDev& L, float u, float v) {
@@ -34,6 +35,55 @@ FR_D bool inside_emitter(const LightDev& L, float3 z) {
     const float a = (r1 * g22 - r2 * g12) / det, b = (r2 * g11 - r1 * g12) / det;
     if (L.type == 0) return fabsf(a) <= 0.5f && fabsf(b) <= 0.5f;
     return a >= 0.0f && b >= 0.0f && a + b <= 1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Environment blocks: lights at infinity (Sec. 7).  Row i of the M_e x M_e map
+// spans polar angles [i, i + 1] pi / M_e from +y, column j azimuths
+// [j, j + 1] 2 pi / M_e from +z towards +x, w = (sin t sin p, cos t, sin t cos p).
+// ---------------------------------------------------------------------------
+struct EnvDir {
+    float3 w;       // unit direction towards the light
+    float weight;   // 1 / pdf: texels in the block x the texel's solid angle
+    int texel;      // row * M_e + column
+};
+
+// A texel uniformly among the block's R x C, from the 24-bit integers k behind
+// the uniforms (row = i0 + floor(k_u R / 2^24); the remainder places the sample
+// inside the row, columns likewise), then a direction uniform in solid angle
+// inside the texel (cos t and p uniform).
+FR_D EnvDir env_sample(const LightDev& L, float u, float v) {
+    const int Me = L.env;
+    const uint32_t i0 = (uint32_t)L.c.x, R = (uint32_t)L.c.y - i0;
+    const uint32_t j0 = (uint32_t)L.c.z, C = (uint32_t)L.e1.x - j0;
+    const uint64_t pu = (uint64_t)__float2uint_rz(u * 16777216.0f) * R;   // u = k_u 2^-24 exactly
+    const uint64_t pv = (uint64_t)__float2uint_rz(v * 16777216.0f) * C;
+    const int row = (int)i0 + (int)(pu >> 24), col = (int)j0 + (int)(pv >> 24);
+    const float fu = (float)(uint32_t)(pu & 0xFFFFFFu) * (1.0f / 16777216.0f);
+    const float fv = (float)(uint32_t)(pv & 0xFFFFFFu) * (1.0f / 16777216.0f);
+    const float zt = cospif((float)row / (float)Me), zb = cospif((float)(row + 1) / (float)Me);
+    const float y = zt + fu * (zb - zt);
+    const float sn = sqrtf(fmaxf(0.0f, (1.0f - y) * (1.0f + y)));
+    float sp, cp;
+    sincospif(2.0f * ((float)col + fv) / (float)Me, &sp, &cp);
+    EnvDir e;
+    e.w = f3(sn * sp, y, sn * cp);
+    e.weight = L.area * (zt - zb) * (2.0f * FR_PI / (float)Me);
+    e.texel = row * Me + col;
+    return e;
+}
+
+// Texel (row, col) containing unit direction w.
+FR_D void env_texel_of(float3 w, int Me, int& row, int& col) {
+    const float th = acosf(fminf(1.0f, fmaxf(-1.0f, w.y)));
+    float ph = atan2f(w.x, w.z);
+    if (ph < 0.0f) ph += 2.0f * FR_PI;
+    row = min(Me - 1, max(0, (int)floorf(th * (float)Me / FR_PI)));
+    col = min(Me - 1, max(0, (int)floorf(ph * (float)Me / (2.0f * FR_PI))));
+}
+
+FR_D bool env_block_has(const LightDev& L, int row, int col) {
+    return row >= (int)L.c.x && row < (int)L.c.y && col >= (int)L.c.z && col < (int)L.e1.x;
 }
 
 // Bilinear footprint: texel centres at u*M - 1/2, clamp-to-edge.

@@ -39,7 +39,8 @@ class FrMesh(ctypes.Structure):
 
 
 class FrLightStage(ctypes.Structure):
-    _fields_ = [("n_lights", ctypes.c_int32), ("records", _vp), ("d", _vp), ("a", _vp), ("stage", _vp)]
+    _fields_ = [("n_lights", ctypes.c_int32), ("records", _vp), ("d", _vp), ("a", _vp), ("stage", _vp),
+                ("env_size", ctypes.c_int32)]
 
 
 class FrAlbedoModel(ctypes.Structure):
@@ -50,7 +51,9 @@ class FrAlbedoModel(ctypes.Structure):
 PARAM_NAMES = ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness")
 # optional light-stage geometry (Sec. 3.3): distance, relative area, barycentric centre
 STAGE_NAMES = ("light_d", "light_a", "light_p")
-ALL_PARAM_NAMES = PARAM_NAMES + STAGE_NAMES
+# environment-map radiance [M_e, M_e, 3] (lights at infinity, Sec. 7)
+ENV_NAMES = ("env",)
+ALL_PARAM_NAMES = PARAM_NAMES + STAGE_NAMES + ENV_NAMES
 
 
 class FrParams(ctypes.Structure):
@@ -212,13 +215,13 @@ def fr_set_mesh(ctx, mean, basis, faces, uv):
     check(lib().fr_set_mesh(ctx, ctypes.byref(m)), ctx)
 
 
-def fr_set_lights(ctx, records, d, a, stage=None):
+def fr_set_lights(ctx, records, d, a, stage=None, env_size=0):
     records = np.ascontiguousarray(records, np.float32)
     d = np.ascontiguousarray(d, np.float32)
     a = np.ascontiguousarray(a, np.float32)
     st = None if stage is None else np.ascontiguousarray(stage, np.float32)
     ls = FrLightStage(records.shape[0], records.ctypes.data, d.ctypes.data, a.ctypes.data,
-                      None if st is None else st.ctypes.data)
+                      None if st is None else st.ctypes.data, int(env_size))
     check(lib().fr_set_lights(ctx, ctypes.byref(ls)), ctx)
 
 
@@ -431,7 +434,8 @@ class Renderer:
         self.scene = scene
         self.ctx = fr_create(scene.width, scene.height, scene.spp, scene.tex_size, edge_spp, flags, seed, max_batch)
         fr_set_mesh(self.ctx, scene.mean, scene.basis, scene.faces, scene.uv)
-        fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a, getattr(scene, "stage", None))
+        fr_set_lights(self.ctx, scene.lights, scene.light_d, scene.light_a, getattr(scene, "stage", None),
+                      getattr(scene, "env_size", 0))
         self.landmarks = getattr(scene, "landmarks", None)
         if self.landmarks is not None:
             fr_set_landmarks(self.ctx, self.landmarks)

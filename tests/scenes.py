@@ -81,3 +81,20 @@ def stage_box(width=32, height=32, spp=4, tex=8, seed=0):
     pr.light_d, pr.light_a, pr.light_p = d.copy(), a.copy(), p.copy()
     return sc, pr
 
+
+
+def env_box(width=32, height=32, spp=4, tex=8, seed=0, env_size=8, block=2):
+    """The shadow box lit by an environment map of lights at infinity (Sec. 7)
+    instead of area emitters: env_size^2 texels in blocks of block x block, a
+    dim coloured sky and one bright texel towards the camera side, so that the
+    occluder casts a sharp shadow on the floor."""
+    import dataclasses
+    sc, pr = shadow_box(width, height, spp, tex, seed)
+    rec, d, a = synth.env_blocks(env_size, block)
+    sc = dataclasses.replace(sc, lights=rec, light_d=d, light_a=a, env_size=env_size)
+    rng = np.random.default_rng(seed + 3)
+    env = rng.uniform(0.1, 0.4, size=(env_size, env_size, 3))
+    env[(3 * env_size) // 8, 0] = (6.0, 5.0, 4.0)   # polar 67.5-90 degrees, azimuth 0-45 degrees: +z side
+    pr.env = env.astype(np.float32)
+    pr.light_i = np.ones((rec.shape[0], 3), np.float32)
+    return sc, pr

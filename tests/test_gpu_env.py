@@ -1,0 +1,121 @@
+"""Environment-map lighting (lights at infinity, Sec. 7) on the GPU against
+the FP64 oracle: the rendered image and its hit and visibility records, and
+the gradients of the interior, primary-edge and shadow-boundary terms with
+respect to the geometry, the textures and the map's radiance."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from paper_2101_05356_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _case(name):
+    if name == "box":               # occluder shadow on a floor under a bright texel
+        return scenes.env_box()
+    sc = synth.make_scene("tiny", env=(8, 2))
+    return sc, synth.random_params(sc, 2)
+
+
+def _records(sc, pr, r, dp, iteration):
+    img, tri, mask = r.records(dp, iteration=iteration)
+    oi, ot, om = oracle.render(sc, pr, records=True, iteration=iteration)
+    agree = (tri.cpu().numpy() == ot) & (mask.cpu().numpy().view(np.uint64) == om)
+    px_ok = agree.reshape(-1, sc.spp).all(axis=1).reshape(sc.height, sc.width)
+    return img.cpu().numpy(), oi, agree, px_ok
+
+
+@pytest.mark.parametrize("name", ["tiny", "box"])
+def test_env_forward_parity(name):
+    """Pixels whose samples agree on hit and visibility match within 1e-4;
+    at most a couple of samples (FP32 vs FP64 directions grazing an edge) may
+    disagree."""
+    from paper_2101_05356_gb300 import facert
+    sc, pr = _case(name)
+    r = facert.Renderer(sc)
+    dp = r.device_params(pr)
+    g, o, agree, px_ok = _records(sc, pr, r, dp, 3)
+    assert np.sum(~agree) <= max(2, 1e-4 * agree.size), int(np.sum(~agree))
+    assert o.max() > 0.05
+    err = np.abs(g - o) / np.maximum(np.abs(o), 1e-2 * o.mean())
+    assert np.max(err[px_ok]) <= 1e-4, float(np.max(err[px_ok]))
+    assert r.status() == 0
+
+
+def test_env_shadow_lists_match_the_oracle():
+    """Per-block shadow-candidate lists (exact range of n . w over the block, FP64)."""
+    from paper_2101_05356_gb300 import facert
+    sc, pr = _case("tiny")
+    r = facert.Renderer(sc)
+    E = r.n_edges
+    prim = torch.empty(E, dtype=torch.int32, device="cuda")
+    npr = torch.empty(1, dtype=torch.int32, device="cuda")
+    per = torch.empty((sc.n_lights, E), dtype=torch.int32, device="cuda")
+    cnt = torch.empty(sc.n_lights, dtype=torch.int32, device="cuda")
+    facert.fr_debug_silhouettes(r.ctx, r.device_params(pr), prim, npr, per, cnt)
+    po, lo = oracle.silhouettes(sc, pr)
+    assert np.array_equal(prim.cpu().numpy()[: int(npr.item())], po)
+    c = cnt.cpu().numpy()
+    per = per.cpu().numpy()
+    for j in range(sc.n_lights):
+        assert 0 < c[j] < E, j
+        assert np.array_equal(per[j, : c[j]], lo[j]), j
+
+
+def _compare(gg, go, groups, rtol):
+    for k in groups:
+        a = gg[k].cpu().numpy().astype(np.float64).ravel()
+        b = np.asarray(go[k], np.float64).ravel()
+        nb = np.linalg.norm(b)
+        assert nb > 0.0, k
+        assert np.linalg.norm(a - b) <= rtol * nb, (k, float(np.linalg.norm(a - b) / nb))
+
+
+@pytest.mark.parametrize("name,term", [("tiny", "interior"), ("box", "interior"), ("box", "shadow"),
+                                       ("box", "primary"), ("tiny", "primary"), ("tiny", "all"), ("box", "all")])
+def test_env_gradient_parity(name, term):
+    from paper_2101_05356_gb300 import facert
+    sc, pr = _case(name)
+    flags = {"interior": facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE,
+             "shadow": facert.FLAG_NO_INTERIOR | facert.FLAG_NO_PRIMARY_EDGE,
+             "primary": facert.FLAG_NO_INTERIOR | facert.FLAG_NO_SHADOW_EDGE, "all": 0}[term]
+    terms = {"interior": oracle.TERM_INTERIOR, "shadow": oracle.TERM_SHADOW, "primary": oracle.TERM_PRIMARY,
+             "all": oracle.TERM_ALL}[term]
+    r = facert.Renderer(sc, flags=flags)
+    dp = r.device_params(pr)
+    _, _, _, px_ok = _records(sc, pr, r, dp, 0)
+    adj = np.random.default_rng(11).uniform(0.2, 1.0, (sc.height, sc.width, 3)) * px_ok[..., None]
+    gg = r.backward(dp, torch.as_tensor(adj, dtype=torch.float32).cuda())
+    go = oracle.grad(sc, pr, adj.astype(np.float32).astype(np.float64), terms=terms)
+    groups = {"interior": ["env", "coef", "rot", "trans", "focal", "diffuse", "roughness"],
+              "shadow": ["coef", "rot"], "primary": ["coef", "focal"],
+              "all": ["env", "coef", "rot", "trans", "diffuse"]}[term]
+    _compare(gg, go, groups, 1e-3 if term == "interior" else 2e-3)
+    assert np.all(gg["light_i"].cpu().numpy() == 0.0)
+    assert r.status() == 0
+
+
+def test_env_blocks_are_validated():
+    from paper_2101_05356_gb300 import facert
+    sc, pr = _case("tiny")
+    ctx = facert.fr_create(sc.width, sc.height, sc.spp, sc.tex_size, 1, 0, 0, 1)
+    try:
+        facert.fr_set_mesh(ctx, sc.mean, sc.basis, sc.faces, sc.uv)
+        bad = sc.lights.copy()
+        bad[0, 2] = 9                  # row range past the 8 x 8 map
+        with pytest.raises(facert.FacertError):
+            facert.fr_set_lights(ctx, bad, sc.light_d, sc.light_a, None, 8)
+        with pytest.raises(facert.FacertError):   # env_size missing
+            facert.fr_set_lights(ctx, sc.lights, sc.light_d, sc.light_a, None, 0)
+        facert.fr_set_lights(ctx, sc.lights, sc.light_d, sc.light_a, None, 8)
+    finally:
+        facert.fr_destroy(ctx)
