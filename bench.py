@@ -273,6 +273,9 @@ def gpu_arm(args, rank, world):
     # an LBVH rebuilt every call instead of refitting the static SAH topology
     lbvh = timed_variant(facert.FLAG_LBVH, args.retrace_steps) if args.retrace_steps > 0 else None
 
+    # the same face under the paper's 32 x 32 environment map (Sec. 7) instead of the light stage
+    env = env_variant(sc, params, tparams, args.retrace_steps, flush, stream) if args.retrace_steps > 0 else None
+
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if args.e2e_steps > 0:
@@ -312,9 +315,64 @@ def gpu_arm(args, rank, world):
                    "steps_per_s": 1000.0 * args.steps / total_ms_max,
                    "stage_ms": {k: float(np.mean([s[k] for s in stage])) for k in stage[0]}},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-        "retrace": retrace, "lbvh_rebuild": lbvh, "status": int(status),
+        "retrace": retrace, "lbvh_rebuild": lbvh, "environment_map": env, "status": int(status),
     }
     return out
+
+
+def env_variant(sc, params, tparams, n_steps, flush, stream, env_size=32, block=4):
+    """Fused steps of the same face and image configuration lit by an
+    env_size x env_size environment map of lights at infinity in blocks of
+    block x block texels (one direction per block per camera sample) instead
+    of the light stage."""
+    import dataclasses
+
+    import torch
+
+    from paper_2101_05356_gb300 import facert, synth
+    rec, d, a = synth.env_blocks(env_size, block)
+    sce = dataclasses.replace(sc, lights=rec, light_d=d, light_a=a, env_size=env_size)
+    re_ = facert.Renderer(sce, edge_spp=1)
+    p, tp = params.copy(), tparams.copy()
+    for q in (p, tp):
+        q.light_i = np.ones((rec.shape[0], 3), np.float32)
+    p.env = np.full((env_size, env_size, 3), 0.3, np.float32)
+    tp.env = synth.env_map(np.random.default_rng(5), env_size)
+    dp, dt = re_.device_params(p), re_.device_params(tp)
+    tgt = re_.forward(dt, iteration=10 ** 6)
+    grads = re_.zero_grads(dp)
+
+    def step(it):
+        for g in grads.values():
+            g.zero_()
+        re_.render(dp, tgt, iteration=it, grads=grads)
+
+    for w in range(3):
+        step(w)
+    facert.fr_counters(re_.ctx, reset=True)
+    facert.fr_set_timing(re_.ctx, True)
+    torch.cuda.synchronize()
+    rt, rst = [], []
+    for k in range(n_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(100 + k)
+        e1.record(stream)
+        e1.synchronize()
+        rt.append(e0.elapsed_time(e1))
+        rst.append(facert.fr_get_timing(re_.ctx))
+    facert.fr_set_timing(re_.ctx, False)
+    cnt = facert.fr_counters(re_.ctx, reset=True)
+    status = re_.status()
+    re_.close()
+    rays = sum(v["rays"] for v in cnt.values())
+    return {"workload": "C2 face, 256^2 x 16 spp, %d x %d environment map in %d blocks of %d x %d texels"
+                        % (env_size, env_size, rec.shape[0], block, block),
+            "ms_per_step": float(np.mean(rt)), "rays_per_step": rays / n_steps,
+            "rays_per_s": rays / (float(np.sum(rt)) / 1000.0), "steps": n_steps, "status": int(status),
+            "stage_ms": {k: float(np.mean([s_[k] for s_ in rst])) for k in rst[0]}}
 
 
 def _serving_summary(serve, srv, reqs):

@@ -500,7 +500,8 @@ typedef struct fr_server_stats {
 
 /* Start a server on ctx (which must not be used otherwise until
  * fr_server_destroy; the device current on the calling thread is the one the
- * worker uses).  Errors: FR_EINVAL (context not set up, bad config),
+ * worker uses).  Errors: FR_EINVAL (context not set up, bad config, a
+ * context lit by FR_LIGHT_ENV blocks: requests carry no environment map),
  * FR_ECUDA. */
 fr_status fr_server_create(fr_server** out, fr_ctx* ctx, const fr_server_config* cfg);
 

@@ -494,6 +494,7 @@ void ctx_info(const fr_ctx* c, CtxInfo& o) {
     o.k_diffuse = c->have_albedo ? c->albedo[0].K : 0;
     o.k_specular = c->have_albedo ? c->albedo[1].K : 0;
     o.have_stage = c->use_stage;
+    o.env_size = c->env_size;
     o.light_scale.resize(c->light_d_h.size());
     for (size_t j = 0; j < c->light_d_h.size(); ++j) {
         const float d2 = c->light_d_h[j] * c->light_d_h[j];

@@ -73,6 +73,7 @@ struct CtxInfo {
     int k_diffuse = 0, k_specular = 0;
     uint32_t flags = 0;
     bool ready = false, have_albedo = false, have_stage = false;
+    int env_size = 0;                 // environment map side (0: no environment blocks)
     std::vector<float> light_scale;   // d_j^2 / a_j of the light records, in float32 arithmetic
 };
 void ctx_info(const fr_ctx* c, CtxInfo& out);

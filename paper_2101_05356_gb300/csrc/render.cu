@@ -991,36 +991,38 @@ FR_D void emitter_range(int type, Real base, Real g1, Real g2, Real& lo, Real& h
     }
 }
 
-// Range [lo, hi] of n . w over the directions w of environment block L, in
-// FP64: n . w = n_y cos t + sin t A(p), A(p) = n_x sin p + n_z cos p.  A's range
+// Range [lo, hi] of n . w over the directions w of environment block L:
+// n . w = n_y cos t + sin t A(p), A(p) = n_x sin p + n_z cos p.  A's range
 // over the block's azimuths comes from the ends and its extremes at
 // p = atan2(n_x, n_z) + k pi; as sin t >= 0 the minimum (maximum) over the
 // block is that of n_y cos t + A_min sin t (A_max) over the polar range, a
 // sinusoid whose extremes lie at the ends or at atan2(A, n_y) + k pi.
-__device__ void env_range(const LightDev& L, double3 n, double& lo, double& hi) {
-    const double Me = L.env;
-    const double t0 = 3.14159265358979323846 * (double)L.c.x / Me, t1 = 3.14159265358979323846 * (double)L.c.y / Me;
-    const double f0 = 6.28318530717958647692 * (double)L.c.z / Me, f1 = 6.28318530717958647692 * (double)L.e1.x / Me;
-    const double A0 = n.x * sin(f0) + n.z * cos(f0), A1 = n.x * sin(f1) + n.z * cos(f1);
-    double a_lo = fmin(A0, A1), a_hi = fmax(A0, A1);
-    const double pa = atan2(n.x, n.z);
+// Real = float for the fast first pass, double for the decision itself.
+template <class Real>
+__device__ void env_range(const LightDev& L, Real nx, Real ny, Real nz, Real& lo, Real& hi) {
+    const Real pi = (Real)3.14159265358979323846, Me = (Real)L.env;
+    const Real t0 = pi * (Real)L.c.x / Me, t1 = pi * (Real)L.c.y / Me;
+    const Real f0 = 2 * pi * (Real)L.c.z / Me, f1 = 2 * pi * (Real)L.e1.x / Me;
+    const Real A0 = nx * sin(f0) + nz * cos(f0), A1 = nx * sin(f1) + nz * cos(f1);
+    Real a_lo = fmin(A0, A1), a_hi = fmax(A0, A1);
+    const Real pa = atan2(nx, nz);
     for (int k = -2; k <= 3; ++k) {
-        const double p = pa + k * 3.14159265358979323846;
+        const Real p = pa + (Real)k * pi;
         if (p > f0 && p < f1) {
-            const double Ap = n.x * sin(p) + n.z * cos(p);
+            const Real Ap = nx * sin(p) + nz * cos(p);
             a_lo = fmin(a_lo, Ap);
             a_hi = fmax(a_hi, Ap);
         }
     }
     for (int side = 0; side < 2; ++side) {
-        const double a = side ? a_hi : a_lo;
-        const double g0 = n.y * cos(t0) + a * sin(t0), g1 = n.y * cos(t1) + a * sin(t1);
-        double r = side ? fmax(g0, g1) : fmin(g0, g1);
-        const double tc = atan2(a, n.y);
+        const Real a = side ? a_hi : a_lo;
+        const Real g0 = ny * cos(t0) + a * sin(t0), g1 = ny * cos(t1) + a * sin(t1);
+        Real r = side ? fmax(g0, g1) : fmin(g0, g1);
+        const Real tc = atan2(a, ny);
         for (int k = -1; k <= 2; ++k) {
-            const double t = tc + k * 3.14159265358979323846;
+            const Real t = tc + (Real)k * pi;
             if (t > t0 && t < t1) {
-                const double g = n.y * cos(t) + a * sin(t);
+                const Real g = ny * cos(t) + a * sin(t);
                 r = side ? fmax(r, g) : fmin(r, g);
             }
         }
@@ -1052,9 +1054,21 @@ __global__ void k_face_class(const DevItem* items) {
     for (int j = 0; j < S.NL; ++j) {
         const LightDev& L = S.lights[j];
         if (L.type == FR_LIGHT_ENV_D) {        // a point at infinity along w is in front iff n . w > 0
-            double lo, hi;
-            env_range(L, n, lo, hi);
-            it.sil_flags[(size_t)(1 + FR_MAX_LIGHTS) * S.E + (size_t)j * S.T + f] = lo > 0.0 ? 1 : (hi < 0.0 ? 2 : 3);
+            // FP32 first: it decides whenever it is farther from zero than a
+            // generous bound on its error (64 u times the bound on |n|); else FP64
+            float lo32, hi32;
+            env_range<float>(L, nf.x, nf.y, nf.z, lo32, hi32);
+            const float err = 64.0f * 5.9604645e-8f * (na.x + na.y + na.z);
+            uint8_t cls = 0;
+            if (lo32 > err) cls = 1;
+            else if (hi32 < -err) cls = 2;
+            else if (lo32 < -err && hi32 > err) cls = 3;
+            if (!cls) {
+                double lo, hi;
+                env_range<double>(L, n.x, n.y, n.z, lo, hi);
+                cls = lo > 0.0 ? 1 : (hi < 0.0 ? 2 : 3);
+            }
+            it.sil_flags[(size_t)(1 + FR_MAX_LIGHTS) * S.E + (size_t)j * S.T + f] = cls;
             continue;
         }
         {

@@ -550,6 +550,7 @@ fr_status fr_server_create(fr_server** out, fr_ctx* ctx, const fr_server_config*
     ctx_info(ctx, s->info);
     const CtxInfo& I = s->info;
     if (!I.ready) return FR_EINVAL;
+    if (I.env_size > 0) return FR_EINVAL;          // requests carry no environment map
     if (cfg->max_slots < 1 || cfg->max_slots > I.max_batch) return FR_EINVAL;
     if (cfg->n_identity < 0 || cfg->n_identity > I.K) return FR_EINVAL;
     if (cfg->edge_spp < 0 || cfg->edge_spp > 64) return FR_EINVAL;

@@ -2,7 +2,8 @@
 
 Stage I optimises shape and expression coefficients, pose, light-stage
 intensities (and, when the parameters carry it, the light-stage geometry
-d, a, p of Sec. 3.3) and (when the scene has a statistical albedo model, Sec. 3.2) the
+d, a, p of Sec. 3.3; under an environment map of Sec. 7 its texels, each a
+light with the same prior and box) and (when the scene has a statistical albedo model, Sec. 3.2) the
 albedo coefficients beta and gamma against E_ph + E_p + E_b (Eq. loss1): each
 Stage I step morphs the textures from beta, gamma (fr_albedo_morph) before the
 render and maps the texture gradients back (fr_albedo_adjoint) after it.
@@ -58,6 +59,10 @@ class FaceState:
         self.ks = sc.n_shape
         self.tex = sc.tex_size
         self.light_scale = torch.as_tensor(sc.light_d ** 2 / sc.light_a, dtype=torch.float32).cuda()
+        # environment-map texels are lights of scale 1 (Sec. 7); light_i is used by the area lights only
+        self.area_lights = bool((sc.lights[:, 0] != 3).any())
+        self.env_scale = (torch.ones(self.p["env"].numel() // 3, dtype=torch.float32, device="cuda")
+                          if "env" in self.p else None)
         # light-stage geometry (d, a, p) when the parameters carry it: one
         # contiguous [d | a | p] block per state so that one STAGE group covers it
         self.stage_block = None
@@ -170,10 +175,15 @@ class FaceState:
             out.append(facert.opt_group(p["rot"], m["rot"], v["rot"], g["rot"], lr=LR["rot"], step=step))
             out.append(facert.opt_group(p["trans"], m["trans"], v["trans"], g["trans"], lr=LR["trans"], step=step))
             sb = self.stage_block
-            out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"],
-                                        aux=None if sb else self.light_scale, aux2=sb["x"] if sb else None,
-                                        kind=facert.GROUP_LIGHT, lr=LR["light"], w_prior=W["w1"], w_box=W["box"],
-                                        step=step))
+            if self.area_lights:
+                out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"],
+                                            aux=None if sb else self.light_scale, aux2=sb["x"] if sb else None,
+                                            kind=facert.GROUP_LIGHT, lr=LR["light"], w_prior=W["w1"],
+                                            w_box=W["box"], step=step))
+            if "env" in p:          # environment map (Sec. 7): each texel a light with the light prior
+                out.append(facert.opt_group(p["env"], m["env"], v["env"], g["env"], aux=self.env_scale,
+                                            kind=facert.GROUP_LIGHT, lr=LR["light"], w_prior=W["w1"],
+                                            w_box=W["box"], step=step))
             if sb:                  # light geometry: prior through d^2/a, soft boxes (Sec. 4, E_b)
                 out.append(facert.opt_group(sb["x"], sb["m"], sb["v"], sb["g"], aux=p["light_i"],
                                             kind=facert.GROUP_STAGE, lr=LR["light"], w_prior=W["w1"],
