@@ -50,8 +50,8 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is in profiles/k_forward_adjoint_c2_full.md.
-TRAFFIC = {"k_forward": {"bytes": 31548672 + 28748288,
-                         "sources_sha256": "2a721343f1a0d5bb871101dfe53732d7fb8dcf7e5ebf2b3c8378b958d6af638e"}}
+TRAFFIC = {"k_forward": {"bytes": 31684352 + 28991488,
+                         "sources_sha256": "5ab1fcf3a8b917d4239b1c443af1ee8851a16a00baee432f1097b8a678c26928"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 SMS = 152
 FP32_LANES_PER_SM = 128
