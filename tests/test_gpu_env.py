@@ -149,3 +149,54 @@ def test_native_server_rejects_environment_contexts():
     r = facert.Renderer(sc, max_batch=2)
     with pytest.raises(facert.FacertError):
         facert.fr_server_create(r.ctx, max_slots=2)
+
+
+def test_env_batch_matches_single_renders():
+    """fr_render_batch over faces of mixed size and spp under an environment
+    map: every face gets the image, loss and gradients of its single render."""
+    import dataclasses
+    from paper_2101_05356_gb300 import facert
+    base = synth.make_scene("tiny", env=(8, 2))
+    cases = [(24, 24, 2, 1, 0, 0), (16, 20, 4, 2, 5, 1), (8, 8, 8, 4, 2, 2)]
+    big = facert.Renderer(base, max_batch=len(cases))
+    items, expect = [], []
+    for (w, h, spp, seed, it, face) in cases:
+        sc = dataclasses.replace(base, width=w, height=h, spp=spp)
+        prm = synth.random_params(sc, seed)
+        tgt = torch.as_tensor(np.random.default_rng(seed).uniform(0, 0.1, (h, w, 3)), dtype=torch.float32).cuda()
+        solo = facert.Renderer(sc)
+        dp = solo.device_params(prm)
+        img, loss, g = solo.render(dp, tgt, iteration=it, face_id=face)
+        expect.append((img.cpu().numpy(), loss.item(), {k: v.cpu().numpy() for k, v in g.items()}))
+        solo.close()
+        dpb = big.device_params(prm)
+        items.append(dict(width=w, height=h, spp=spp, edge_spp=1, flags=0, iteration=it, face_id=face, params=dpb,
+                          target=tgt, image=torch.zeros((h, w, 3), device="cuda"),
+                          loss=torch.zeros(1, dtype=torch.float64, device="cuda"), grads=big.zero_grads(dpb)))
+    facert.fr_render_batch(big.ctx, items)
+    torch.cuda.synchronize()
+    assert big.status() == 0
+    for it, (img, loss, g) in zip(items, expect):
+        assert np.array_equal(it["image"].cpu().numpy(), img)
+        assert it["loss"].item() == pytest.approx(loss, rel=1e-12)
+        assert np.abs(g["env"]).max() > 0.0
+        for k in g:
+            a = it["grads"][k].cpu().numpy()
+            assert np.allclose(a, g[k], rtol=1e-4, atol=1e-5 * max(np.abs(g[k]).max(), 1e-12)), k
+
+
+def test_env_autograd_function_gives_the_map_gradient():
+    """RenderFn carries the environment map: its gradient through autograd
+    equals the adjoint call's for the same samples."""
+    from paper_2101_05356_gb300 import autograd, facert
+    sc, pr = _case("box")
+    r = facert.Renderer(sc)
+    dp = r.device_params(pr)
+    adj = torch.as_tensor(np.random.default_rng(2).uniform(0.2, 1.0, (sc.height, sc.width, 3)),
+                          dtype=torch.float32).cuda()
+    want = r.backward(dp, adj, iteration=4)
+    p = {k: v.clone().requires_grad_(k in ("env", "coef")) for k, v in dp.items()}
+    img = autograd.render(r, p, iteration=4)
+    (img * adj).sum().backward()
+    assert torch.equal(p["env"].grad, want["env"])
+    assert torch.equal(p["coef"].grad, want["coef"])
