@@ -22,6 +22,9 @@ FLAG_MORPH_BF16 = 128
 FLAG_RECOMPUTE = 256
 FLAG_LBVH = 512
 FLAG_VIEW_CUTOFF = 1024
+# emitter types of the light records (FR_LIGHT_*)
+LIGHT_QUAD, LIGHT_TRI, LIGHT_DISK, LIGHT_ENV = 0, 1, 2, 3
+FR_MAX_ENV = 64
 
 _vp = ctypes.c_void_p
 

@@ -60,7 +60,7 @@ class FaceState:
         self.tex = sc.tex_size
         self.light_scale = torch.as_tensor(sc.light_d ** 2 / sc.light_a, dtype=torch.float32).cuda()
         # environment-map texels are lights of scale 1 (Sec. 7); light_i is used by the area lights only
-        self.area_lights = bool((sc.lights[:, 0] != 3).any())
+        self.area_lights = bool((sc.lights[:, 0] != facert.LIGHT_ENV).any())
         self.env_scale = (torch.ones(self.p["env"].numel() // 3, dtype=torch.float32, device="cuda")
                           if "env" in self.p else None)
         # light-stage geometry (d, a, p) when the parameters carry it: one
