@@ -98,3 +98,19 @@ def env_box(width=32, height=32, spp=4, tex=8, seed=0, env_size=8, block=2):
     pr.env = env.astype(np.float32)
     pr.light_i = np.ones((rec.shape[0], 3), np.float32)
     return sc, pr
+
+
+def mixed_box(width=32, height=32, spp=4, tex=8, seed=0):
+    """The shadow box lit by its two area emitters and, together with them, a
+    dim 8 x 8 environment map in four blocks with one bright texel."""
+    import dataclasses
+    sc, pr = shadow_box(width, height, spp, tex, seed)
+    rec, d, a = synth.env_blocks(8, 4)
+    lights = np.concatenate([sc.lights, rec])
+    sc = dataclasses.replace(sc, lights=lights, light_d=np.concatenate([sc.light_d, d]),
+                             light_a=np.concatenate([sc.light_a, a]), env_size=8)
+    env = np.random.default_rng(seed + 3).uniform(0.05, 0.2, size=(8, 8, 3))
+    env[3, 0] = (3.0, 2.5, 2.0)
+    pr.env = env.astype(np.float32)
+    pr.light_i = np.concatenate([pr.light_i, np.ones((rec.shape[0], 3), np.float32)])
+    return sc, pr

@@ -22,6 +22,8 @@ def _cuda():
 def _case(name):
     if name == "box":               # occluder shadow on a floor under a bright texel
         return scenes.env_box()
+    if name == "mixed":             # area emitters and environment blocks together
+        return scenes.mixed_box()
     sc = synth.make_scene("tiny", env=(8, 2))
     return sc, synth.random_params(sc, 2)
 
@@ -34,7 +36,7 @@ def _records(sc, pr, r, dp, iteration):
     return img.cpu().numpy(), oi, agree, px_ok
 
 
-@pytest.mark.parametrize("name", ["tiny", "box"])
+@pytest.mark.parametrize("name", ["tiny", "box", "mixed"])
 def test_env_forward_parity(name):
     """Pixels whose samples agree on hit and visibility match within 1e-4;
     at most a couple of samples (FP32 vs FP64 directions grazing an edge) may
@@ -81,7 +83,8 @@ def _compare(gg, go, groups, rtol):
 
 
 @pytest.mark.parametrize("name,term", [("tiny", "interior"), ("box", "interior"), ("box", "shadow"),
-                                       ("box", "primary"), ("tiny", "primary"), ("tiny", "all"), ("box", "all")])
+                                       ("box", "primary"), ("tiny", "primary"), ("tiny", "all"), ("box", "all"),
+                                       ("mixed", "interior"), ("mixed", "shadow"), ("mixed", "all")])
 def test_env_gradient_parity(name, term):
     from paper_2101_05356_gb300 import facert
     sc, pr = _case(name)
@@ -99,8 +102,11 @@ def test_env_gradient_parity(name, term):
     groups = {"interior": ["env", "coef", "rot", "trans", "focal", "diffuse", "roughness"],
               "shadow": ["coef", "rot"], "primary": ["coef", "focal"],
               "all": ["env", "coef", "rot", "trans", "diffuse"]}[term]
+    if name == "mixed" and term != "shadow":
+        groups = groups + ["light_i"]
     _compare(gg, go, groups, 1e-3 if term == "interior" else 2e-3)
-    assert np.all(gg["light_i"].cpu().numpy() == 0.0)
+    env_lights = sc.lights[:, 0] == synth.LIGHT_ENV
+    assert np.all(gg["light_i"].cpu().numpy()[env_lights] == 0.0)
     assert r.status() == 0
 
 
