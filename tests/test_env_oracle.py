@@ -60,13 +60,14 @@ def _texel_cos_integral(i, j, me, n):
     return v
 
 
-@pytest.mark.parametrize("i,j", [(1, 0), (3, 1), (2, 6), (5, 7), (3, 4)])
-def test_env_single_texel_orientation(i, j):
+@pytest.mark.parametrize("i,j,me", [(1, 0, 8), (3, 1, 8), (2, 6, 8), (5, 7, 8), (3, 4, 8), (0, 1, 8), (7, 0, 8),
+                                    (4, 1, 12), (0, 11, 12)])
+def test_env_single_texel_orientation(i, j, me):
     """One texel as its own block: the oracle's estimate of (1/pi) int n.w dw
     over the texel matches quadrature, which fixes the polar axis (+y), the
-    azimuth origin (+z) and direction (towards +x) and the texel's solid angle.
-    Texel (3, 4) faces away from n (zero)."""
-    me = 8
+    azimuth origin (+z) and direction (towards +x) and the texel's solid angle,
+    also at the poles and for a map side that is not a power of two.  Texels
+    (3, 4) and (7, 0) face away from n (zero)."""
     env = np.zeros((me, me, 3))
     env[i, j] = (2.0, 1.0, 0.5)
     sc, pr = _env_scene([_block(i, i + 1, j, j + 1)], me, env)
