@@ -24,6 +24,9 @@ def _case(name):
         return scenes.env_box()
     if name == "mixed":             # area emitters and environment blocks together
         return scenes.mixed_box()
+    if name == "tiny12":            # a map side that is not a power of two
+        sc = synth.make_scene("tiny", env=(12, 3))
+        return sc, synth.random_params(sc, 6)
     sc = synth.make_scene("tiny", env=(8, 2))
     return sc, synth.random_params(sc, 2)
 
@@ -36,7 +39,7 @@ def _records(sc, pr, r, dp, iteration):
     return img.cpu().numpy(), oi, agree, px_ok
 
 
-@pytest.mark.parametrize("name", ["tiny", "box", "mixed"])
+@pytest.mark.parametrize("name", ["tiny", "box", "mixed", "tiny12"])
 def test_env_forward_parity(name):
     """Pixels whose samples agree on hit and visibility match within 1e-4;
     at most a couple of samples (FP32 vs FP64 directions grazing an edge) may
@@ -84,7 +87,8 @@ def _compare(gg, go, groups, rtol):
 
 @pytest.mark.parametrize("name,term", [("tiny", "interior"), ("box", "interior"), ("box", "shadow"),
                                        ("box", "primary"), ("tiny", "primary"), ("tiny", "all"), ("box", "all"),
-                                       ("mixed", "interior"), ("mixed", "shadow"), ("mixed", "all")])
+                                       ("mixed", "interior"), ("mixed", "shadow"), ("mixed", "all"),
+                                       ("tiny12", "interior"), ("tiny12", "all")])
 def test_env_gradient_parity(name, term):
     from paper_2101_05356_gb300 import facert
     sc, pr = _case(name)
