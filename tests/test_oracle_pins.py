@@ -375,11 +375,40 @@ def test_closest_hit_known_square():
 
 
 def test_render_records_agree_with_brute_force():
+    """Every camera sample's recorded hit triangle equals an independent
+    brute-force closest hit: the morphed mesh posed with scipy's R = Rz Ry Rx,
+    the jittered camera ray of the sample (Philox dims 0, 1), and a vectorised
+    Moller-Trumbore test against all 320 triangles (ties to the lower index)."""
+    from scipy.spatial.transform import Rotation
     sc = synth.make_scene("tiny", width=12, height=12, spp=2)
     pr = synth.random_params(sc, 1)
     img, tri, _ = oracle.render(sc, pr, records=True)
     assert img.shape == (12, 12, 3) and np.all(img >= 0)
+    v = sc.mean.astype(np.float64) + np.tensordot(pr.coef.astype(np.float64), sc.basis.astype(np.float64), axes=1)
+    R = Rotation.from_euler("xyz", pr.rot.astype(np.float64)).as_matrix()
+    v = (v - pr.trans.astype(np.float64)) @ R                     # rows of R^T (v - T)
+    F = np.asarray(sc.faces)
+    v0, e1, e2 = v[F[:, 0]], v[F[:, 1]] - v[F[:, 0]], v[F[:, 2]] - v[F[:, 0]]
+    W, H, f = sc.width, sc.height, float(pr.focal[0])
+    want = np.empty_like(tri)
+    for q in range(W * H * sc.spp):
+        p, s_ = divmod(q, sc.spp)
+        w = oracle.philox(0, 0, p, s_ << 16, 0, 0)
+        sx = p % W + (int(w[0]) >> 8) / 16777216.0
+        sy = p // W + (int(w[1]) >> 8) / 16777216.0
+        d = np.array([(sx - 0.5 * W) / f, -(sy - 0.5 * H) / f, -1.0])
+        pv = np.cross(d, e2)
+        det = np.einsum("ij,ij->i", e1, pv)
+        sv = -v0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            b1 = np.einsum("ij,ij->i", sv, pv) / det
+            qv = np.cross(sv, e1)
+            b2 = (qv @ d) / det
+            t = np.einsum("ij,ij->i", e2, qv) / det
+        ok = (det != 0) & (b1 >= 0) & (b2 >= 0) & (b1 + b2 <= 1) & (t > 0)
+        want[q] = int(np.flatnonzero(ok)[np.argmin(t[ok])]) if ok.any() else -1
     assert 0.2 < np.mean(tri >= 0) < 0.9
+    assert np.array_equal(tri, want), int(np.sum(tri != want))
 
 
 # ---------------------------------------------------------------------------
