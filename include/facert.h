@@ -84,7 +84,7 @@ typedef struct fr_ctx fr_ctx;
 
 typedef struct fr_config {
     int32_t width, height;   /* image size, 1..8192 each */
-    int32_t spp;             /* camera samples per pixel: a power of two, 1..1024 */
+    int32_t spp;             /* camera samples per pixel: a power of two, 1..256 */
     int32_t tex_size;        /* M: textures are M x M, 1..8192 */
     int32_t edge_spp;        /* primary-edge samples per pixel (0..64) */
     uint32_t flags;          /* FR_FLAG_* */
@@ -251,8 +251,10 @@ fr_status fr_backward(fr_ctx* ctx, const fr_params* p, const float* adj_image, f
                       uint32_t iteration, uint32_t face_id, void* stream);
 
 /* Photometric loss of Sec. 4: blurred = G3x3 * image (sigma 1, normalised,
- * replicate border); *loss = sum |blurred - target| (FP64 reduction, device
- * double); adj_image = dloss/dimage.  blurred may be NULL. */
+ * replicate border); *loss = sum |blurred - target| (device double, stored, not
+ * accumulated); adj_image = dloss/dimage.  blurred may be NULL.  The sum is an
+ * FP64 reduction in a fixed order (per-block partials added in block order),
+ * so repeated calls give bitwise the same loss. */
 fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* loss,
                   float* adj_image, float* blurred, void* stream);
 
@@ -266,7 +268,7 @@ fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float*
                     void* stream);
 
 /* One face of a batched call: its image configuration (width * height at most
- * the context's width * height; spp a power of two <= 1024; edge_spp <= 64),
+ * the context's width * height; spp a power of two <= 256; edge_spp <= 64),
  * flags, Philox iteration and face id, parameters (device), target image,
  * output image [height][width][3], loss (device double) and gradients (NULL:
  * forward + loss only; otherwise ADDED into, like fr_grads). */
@@ -293,7 +295,11 @@ fr_status fr_render_batch(fr_ctx* ctx, const fr_item* items, int32_t n, void* st
 fr_status fr_set_flags(fr_ctx* ctx, uint32_t flags);
 
 /* Synchronise `stream`, read and clear the device status word.
- * Returns FR_OK, FR_EOVERFLOW or FR_ETIMEOUT (or FR_ECUDA). */
+ * Returns FR_OK, FR_EOVERFLOW or FR_ETIMEOUT (or FR_ECUDA).  FR_ETIMEOUT after a
+ * wait whose CTA could not also drain its own copies or tensor-core MMAs in a
+ * second bounded wait marks the context unusable: a late write could land in
+ * memory that has since been reused, so every later compute call on it returns
+ * FR_ECUDA; destroy it and create a new one. */
 fr_status fr_sync_status(fr_ctx* ctx, void* stream);
 
 /* Human-readable description of the last error on ctx (never NULL). */
@@ -496,6 +502,8 @@ typedef struct fr_server_stats {
     int32_t max_active;       /* most requests admitted at once */
     int32_t active, queued;   /* now */
     uint64_t peak_bytes;      /* most device state held by admitted requests at once */
+    uint64_t used_bytes;      /* device state held by admitted requests now */
+    uint64_t finished;        /* requests that reached DONE or FAILED */
 } fr_server_stats;
 
 /* Start a server on ctx (which must not be used otherwise until
@@ -536,6 +544,13 @@ fr_status fr_cancel(fr_server* srv, uint64_t id);
  * request's device state and the stream.  The context stays the caller's. */
 void fr_server_destroy(fr_server* srv);
 
+/* Test hook for the server's error path, with no device fault: the n-th
+ * device-to-host read of a result from now (n = 0: the next one; a final loss
+ * or a request's final parameters) is treated as failed on the host.  The
+ * requests of that step then fail with the read's message; those retired
+ * before the failed read keep their results.  FR_EINVAL if n < 0. */
+fr_status fr_server_inject_read_failure(fr_server* srv, int32_t n);
+
 /* ---- allocation-free variant ---- */
 
 /* The photometric loss of fr_loss for callers that cannot allocate device
@@ -544,12 +559,15 @@ void fr_server_destroy(fr_server* srv);
  * loop that cannot absorb an allocation.  The paper has no counterpart; this is
  * an interface convenience.  No context is needed: the caller passes the image
  * size (height * width <= 512 * 512, else FR_EINVAL) and its own buffers, with
- * the same meaning and results as fr_loss.  The only scratch is a static device
- * array (3 MiB, held by every GPU that loads the library until exit) shared by
- * all calls: calls whose kernels overlap on the GPU race on it.  The first call
- * on each device looks up the array's device address once, with that device
- * current; make that first call before any stream capture.  Allocates nothing:
- * no cudaMalloc, cudaFree or allocating library routine. */
+ * the same meaning and results as fr_loss.  The only scratch is two static
+ * device arrays (3 MiB of residual signs and 8 KiB of partial sums, held by
+ * every GPU that loads the library until exit) shared by all calls: calls whose
+ * kernels overlap on the GPU race on them.  Every call looks up the arrays'
+ * device addresses with the current device; the first call on a device may load
+ * the library's module there, so make it before any stream capture.  If a CUDA
+ * error from an earlier call is pending, returns FR_ECUDA without launching and
+ * leaves that error in place.  Allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine. */
 fr_status fr_loss_noalloc(int32_t height, int32_t width, const float* image, const float* target,
                           double* loss, float* adj_image, float* blurred, void* stream);
 

@@ -39,6 +39,7 @@ struct Slot {
     fix64* small = nullptr;
     double* pose_part = nullptr;
     float* sign = nullptr;
+    double* loss_part = nullptr;     // per-block loss partials [FR_LOSS_PARTS]
     float* adj_image = nullptr;
     LightDev* lights = nullptr;      // lights built from stage parameters [FR_MAX_LIGHTS]
     int* edge_perm = nullptr;        // primary-edge sample order [edge_cap]
@@ -67,6 +68,7 @@ struct fr_ctx {
     int max_batch = 1;
     int N = 0, T = 0, K = 0, NL = 0, E = 0, ld = 0;   // ld = shape.ld
     bool have_mesh = false, have_lights = false;
+    bool poisoned = false;                     // a device wait gave up unsafely: refuse further work
     std::string err;
     // mesh and lights (shared by all slots)
     LinearModel shape;                         // rows 3N
@@ -148,6 +150,7 @@ void mark(fr_ctx* c, int k, cudaStream_t st) {
 
 fr_status check_params(fr_ctx* c, const fr_params* p) {
     if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (c->poisoned) return fail(c, FR_ECUDA, "context unusable after an unsafe device timeout");
     if (!c->have_mesh || !c->have_lights) return fail(c, FR_EINVAL, "mesh and lights must be set first");
     if (!p || !p->rot || !p->trans || !p->focal || !p->light_i || !p->diffuse || !p->specular || !p->roughness ||
         (c->K > 0 && !p->coef))
@@ -355,7 +358,9 @@ void build_geometry(fr_ctx* c, int n, cudaStream_t st) {
 fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
     for (int k = 0; k < n; ++k) {
         const DevItem& it = c->h_items[k];
-        if (it.S.spp > 32) CK(c, cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)it.S.W * it.S.H, st));
+        // a pixel's samples span two blocks only at spp = 256: their two partial
+        // sums are added onto zero (exact in either order)
+        if (it.S.spp > 128) CK(c, cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)it.S.W * it.S.H, st));
     }
     launch_forward(c->d_items, map_of(c, n, false), c->env_size > 0, st);
     return FR_OK;
@@ -400,7 +405,7 @@ LossTable loss_table(fr_ctx* c, int n, const float* const* targets, double* cons
     for (int k = 0; k < n; ++k) {
         const DevItem& it = c->h_items[k];
         const Slot& sl = c->slots[k];
-        t.it[k] = LossItem{it.S.H, it.S.W, it.image, targets[k], losses[k], sl.sign, nullptr,
+        t.it[k] = LossItem{it.S.H, it.S.W, it.image, targets[k], losses[k], sl.sign, sl.loss_part, nullptr,
                            adjoint ? sl.adj_image : nullptr};
         t.max_px3 = std::max(t.max_px3, it.S.H * it.S.W * 3);
     }
@@ -459,7 +464,7 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
 fr_status check_image_args(fr_ctx* c, int W, int H, int spp, int edge_spp) {
     if (W < 1 || H < 1 || (long)W * H > (long)c->cfg.width * c->cfg.height)
         return fail(c, FR_EINVAL, "item image larger than the context's width x height");
-    if (!is_pow2(spp) || spp > 1024) return fail(c, FR_EINVAL, "spp must be a power of two <= 1024");
+    if (!is_pow2(spp) || spp > FR_MAX_SPP) return fail(c, FR_EINVAL, "spp must be a power of two <= 256");
     if (edge_spp < 0 || edge_spp > 64) return fail(c, FR_EINVAL, "edge_spp out of range");
     if ((long)W * H * spp > (1L << 31) - 1024) return fail(c, FR_EINVAL, "too many samples per item");
     return FR_OK;
@@ -509,7 +514,8 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
     *out = nullptr;
     if (cfg->width < 1 || cfg->width > 8192 || cfg->height < 1 || cfg->height > 8192)
         return fail(nullptr, FR_EINVAL, "image size out of range");
-    if (!is_pow2(cfg->spp) || cfg->spp > 1024) return fail(nullptr, FR_EINVAL, "spp must be a power of two <= 1024");
+    if (!is_pow2(cfg->spp) || cfg->spp > FR_MAX_SPP)
+        return fail(nullptr, FR_EINVAL, "spp must be a power of two <= 256");
     if (cfg->tex_size < 1 || cfg->tex_size > 8192) return fail(nullptr, FR_EINVAL, "tex_size out of range");
     if (cfg->edge_spp < 0 || cfg->edge_spp > 64) return fail(nullptr, FR_EINVAL, "edge_spp out of range");
     if ((long)cfg->width * cfg->height * cfg->spp > (1L << 31) - 1024)
@@ -526,7 +532,8 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
               cudaMemset(c->counters, 0, 9 * sizeof(unsigned long long)) == cudaSuccess &&
               dalloc(c, &c->d_items, FR_MAX_BATCH) == FR_OK;
     for (int k = 0; ok && k < c->max_batch; ++k)
-        ok = dalloc(c, &c->slots[k].sign, px) == FR_OK && dalloc(c, &c->slots[k].adj_image, px) == FR_OK;
+        ok = dalloc(c, &c->slots[k].sign, px) == FR_OK && dalloc(c, &c->slots[k].adj_image, px) == FR_OK &&
+             dalloc(c, &c->slots[k].loss_part, FR_LOSS_PARTS) == FR_OK;
     if (!ok) {
         g_err = c->err;
         free_all(c);
@@ -641,6 +648,7 @@ fr_status fr_landmark_loss(fr_ctx* c, const fr_params* p, int32_t width, int32_t
                            float weight, double* loss, fr_grads* g, float* projected, void* stream) {
     if (!c || !p || !z || !loss) return fail(c, FR_EINVAL, "null argument");
     if (c->n_landmarks == 0) return fail(c, FR_EINVAL, "landmarks not set");
+    if (c->poisoned) return fail(c, FR_ECUDA, "context unusable after an unsafe device timeout");
     if (!p->rot || !p->trans || !p->focal || (c->K > 0 && !p->coef)) return fail(c, FR_EINVAL, "null parameter");
     if (width < 1 || height < 1) return fail(c, FR_EINVAL, "bad image size");
     LandmarkArgs a;
@@ -671,6 +679,7 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 fr_status fr_albedo_morph(fr_ctx* c, int32_t n, const float* const* beta, const float* const* gamma,
                           float* const* diffuse, float* const* specular, void* stream) {
     if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (c->poisoned) return fail(c, FR_ECUDA, "context unusable after an unsafe device timeout");
     if (!c->have_albedo) return fail(c, FR_EINVAL, "albedo model not set");
     if (n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch faces required");
     const float* const* coefs[2] = {beta, gamma};
@@ -696,6 +705,7 @@ fr_status fr_albedo_morph(fr_ctx* c, int32_t n, const float* const* beta, const 
 fr_status fr_albedo_adjoint(fr_ctx* c, int32_t n, const float* const* g_diffuse, const float* const* g_specular,
                             float* const* g_beta, float* const* g_gamma, void* stream) {
     if (!c) return fail(nullptr, FR_EINVAL, "null context");
+    if (c->poisoned) return fail(c, FR_ECUDA, "context unusable after an unsafe device timeout");
     if (!c->have_albedo) return fail(c, FR_EINVAL, "albedo model not set");
     if (n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch faces required");
     const float* const* gs[2] = {g_diffuse, g_specular};
@@ -804,7 +814,9 @@ fr_status fr_backward(fr_ctx* c, const fr_params* p, const float* adj_image, fr_
 fr_status fr_loss(fr_ctx* c, const float* image, const float* target, double* loss, float* adj_image,
                   float* blurred, void* stream) {
     if (!c || !image || !target || !loss) return fail(c, FR_EINVAL, "null argument");
-    launch_loss(c->cfg.height, c->cfg.width, image, target, loss, c->slots[0].sign, blurred, adj_image, S_(stream));
+    if (c->poisoned) return fail(c, FR_ECUDA, "context unusable after an unsafe device timeout");
+    launch_loss(c->cfg.height, c->cfg.width, image, target, loss, c->slots[0].sign, c->slots[0].loss_part, blurred,
+                adj_image, S_(stream));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -895,6 +907,11 @@ fr_status fr_sync_status(fr_ctx* c, void* stream) {
     int s = 0;
     CK(c, cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost));
     CK(c, cudaMemset(c->status, 0, sizeof(int)));
+    if (s & FR_STATUS_TIMEOUT_UNSAFE) {
+        c->poisoned = true;
+        return fail(c, FR_ETIMEOUT, "bounded wait gave up and copies or MMAs may still be in flight: "
+                                    "the context is unusable");
+    }
     if (s & FR_STATUS_STACK_OVERFLOW) return fail(c, FR_EOVERFLOW, "traversal stack overflow");
     if (s & FR_STATUS_TIMEOUT) return fail(c, FR_ETIMEOUT, "bounded wait gave up");
     if (s & FR_STATUS_BAD_BVH) return fail(c, FR_EOVERFLOW, "invalid BVH (construction check failed)");
@@ -995,6 +1012,7 @@ fr_status fr_debug_bvh(fr_ctx* c, const fr_params* p, int32_t* out, void* stream
 
 fr_status fr_debug_morph(fr_ctx* c, const fr_params* params, int32_t n, float* out, void* stream) {
     if (!c || !params || !out || n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "bad argument");
+    if (c->poisoned) return fail(c, FR_ECUDA, "context unusable after an unsafe device timeout");
     const cudaStream_t st = S_(stream);
     for (int k = 0; k < n; ++k) {
         TRY(check_params(c, &params[k]));

@@ -10,11 +10,15 @@
 #define FR_STATUS_STACK_OVERFLOW 1
 #define FR_STATUS_TIMEOUT 2
 #define FR_STATUS_BAD_BVH 4
+// a bounded wait gave up and so did the second wait for the CTA's own copies or
+// MMAs in flight: a late write may still land, so the context is unusable
+#define FR_STATUS_TIMEOUT_UNSAFE 8
 
 constexpr int FR_MAX_LIGHTS = 128;
 constexpr int FR_MAX_ENV_D = 64;       // environment map side (FR_MAX_ENV of the C interface)
 constexpr int FR_MAX_BASIS = 256;
 constexpr int FR_STACK = 64;           // traversal stack entries per thread
+constexpr int FR_MAX_SPP = 256;        // camera samples per pixel
 constexpr float FR_PI = 3.14159265358979323846f;
 
 // ---------------------------------------------------------------------------

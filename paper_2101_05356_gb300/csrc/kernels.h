@@ -101,13 +101,16 @@ void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStre
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri,
                        float* t, cudaStream_t st);
 
-// loss.cu: per-image arguments passed by value (no device table needed)
+// loss.cu: per-image arguments passed by value (no device table needed).
+// part: FR_LOSS_PARTS doubles of scratch for the per-block partial sums.
+constexpr int FR_LOSS_PARTS = 1024;
 struct LossItem {
     int H, W;
     const float* image;
     const float* target;
     double* loss;
     float* sign;
+    double* part;
     float* blurred;
     float* adj;
 };
@@ -117,7 +120,7 @@ struct LossTable {
     LossItem it[FR_MAX_BATCH];
 };
 void launch_loss(const LossTable& t, cudaStream_t st);
-void launch_loss(int H, int W, const float* image, const float* target, double* loss, float* sign,
+void launch_loss(int H, int W, const float* image, const float* target, double* loss, float* sign, double* part,
                  float* blurred, float* adj_image, cudaStream_t st);
 
 // misc

@@ -3,10 +3,18 @@
 // loss = sum |blurred - target| reduced in FP64, and its adjoint
 // dloss/dimage = G^T * sign(blurred - target) by gather (no atomics).
 // Batched over images through blockIdx.y; arguments travel by value.
+//
+// The loss sum does not depend on how blocks are scheduled: block b of an
+// image always sums the same elements (a grid-stride loop over a fixed number
+// of blocks per image) in the same order, writes its FP64 partial to its own
+// slot, and a finishing kernel adds the partials in block order and stores the
+// result.  Repeated calls therefore give bitwise the same loss.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace {
+
+constexpr int LOSS_THREADS = 256;
 
 FR_D float gw(int dx, int dy) {
     const float e1 = expf(-0.5f), e2 = expf(-1.0f);
@@ -15,17 +23,19 @@ FR_D float gw(int dx, int dy) {
     return (r2 == 0 ? 1.0f : (r2 == 1 ? e1 : e2)) / z;
 }
 
-__global__ void k_loss_zero(LossTable t) {
-    if (threadIdx.x < t.n) *t.it[threadIdx.x].loss = 0.0;
+FR_HD int loss_blocks(int px3) {
+    const int nb = (px3 + LOSS_THREADS - 1) / LOSS_THREADS;
+    return nb < FR_LOSS_PARTS ? (nb > 0 ? nb : 1) : FR_LOSS_PARTS;
 }
 
-__global__ void __launch_bounds__(256) k_blur_loss(LossTable t) {
-    __shared__ double part[8];
+__global__ void __launch_bounds__(LOSS_THREADS) k_blur_loss(LossTable t) {
+    __shared__ double part[LOSS_THREADS / 32];
     const LossItem& L = t.it[blockIdx.y];
-    const int H = L.H, W = L.W;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // over H * W * 3
+    const int H = L.H, W = L.W, n = H * W * 3;
+    const int nb = loss_blocks(n);
+    if ((int)blockIdx.x >= nb) return;                  // block-uniform
     double l = 0.0;
-    if (i < H * W * 3) {
+    for (int i = blockIdx.x * LOSS_THREADS + threadIdx.x; i < n; i += nb * LOSS_THREADS) {
         const int k = i % 3, p = i / 3, x = p % W, y = p / W;
         float acc = 0.0f;
         for (int dy = -1; dy <= 1; ++dy)
@@ -34,7 +44,7 @@ __global__ void __launch_bounds__(256) k_blur_loss(LossTable t) {
                 acc += gw(dx, dy) * L.image[3 * (yy * W + xx) + k];
             }
         const float r = acc - L.target[i];
-        l = fabs((double)r);
+        l += fabs((double)r);
         L.sign[i] = (float)((r > 0.0f) - (r < 0.0f));
         if (L.blurred) L.blurred[i] = acc;
     }
@@ -43,13 +53,29 @@ __global__ void __launch_bounds__(256) k_blur_loss(LossTable t) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        if (s != 0.0) atomicAdd(L.loss, s);
+        for (int w = 0; w < LOSS_THREADS / 32; ++w) s += part[w];
+        L.part[blockIdx.x] = s;
     }
 }
 
+// loss = sum of the image's block partials in block order (one block per image)
+__global__ void __launch_bounds__(LOSS_THREADS) k_loss_finish(LossTable t) {
+    __shared__ double part[LOSS_THREADS];
+    const LossItem& L = t.it[blockIdx.x];
+    const int nb = loss_blocks(L.H * L.W * 3);
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += LOSS_THREADS) s += L.part[b];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = LOSS_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *L.loss = part[0];
+}
+
 // adj_q = sum over (p, delta) with clamp(p + delta) == q of w(delta) sgn_p
-__global__ void __launch_bounds__(256) k_blur_adjoint(LossTable t) {
+__global__ void __launch_bounds__(LOSS_THREADS) k_blur_adjoint(LossTable t) {
     const LossItem& L = t.it[blockIdx.y];
     if (!L.adj) return;
     const int H = L.H, W = L.W;
@@ -71,18 +97,17 @@ __global__ void __launch_bounds__(256) k_blur_adjoint(LossTable t) {
 
 void launch_loss(const LossTable& t, cudaStream_t st) {
     if (t.n <= 0) return;
-    const dim3 grid((t.max_px3 + 255) / 256, t.n);
-    k_loss_zero<<<1, 32, 0, st>>>(t);
-    k_blur_loss<<<grid, 256, 0, st>>>(t);
-    k_blur_adjoint<<<grid, 256, 0, st>>>(t);
+    k_blur_loss<<<dim3(loss_blocks(t.max_px3), t.n), LOSS_THREADS, 0, st>>>(t);
+    k_loss_finish<<<t.n, LOSS_THREADS, 0, st>>>(t);
+    k_blur_adjoint<<<dim3((t.max_px3 + LOSS_THREADS - 1) / LOSS_THREADS, t.n), LOSS_THREADS, 0, st>>>(t);
     fr_count_launches(3);
 }
 
-void launch_loss(int H, int W, const float* image, const float* target, double* loss, float* sign,
+void launch_loss(int H, int W, const float* image, const float* target, double* loss, float* sign, double* part,
                  float* blurred, float* adj_image, cudaStream_t st) {
     LossTable t;
     t.n = 1;
     t.max_px3 = H * W * 3;
-    t.it[0] = LossItem{H, W, image, target, loss, sign, blurred, adj_image};
+    t.it[0] = LossItem{H, W, image, target, loss, sign, part, blurred, adj_image};
     launch_loss(t, st);
 }

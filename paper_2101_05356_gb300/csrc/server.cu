@@ -19,6 +19,7 @@
 // >= 1e-3); Philox streams are keyed by the request id and its own
 // iteration, so a request's result does not depend on its batch.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -108,6 +109,7 @@ struct fr_server {
     size_t used = 0;
     uint64_t finished = 0;
     bool stop = false;
+    std::atomic<int> inject_read_fail{-1};              // test hook: fail the n-th result read from now
     fr_server_stats stats{};
     std::thread worker;
 
@@ -446,14 +448,21 @@ struct fr_server {
         if (fr_render_batch(ctx, items.data(), (int)items.size(), st) != FR_OK)
             return std::string("final evaluation: ") + fr_last_error(ctx);
         if (fr_sync_status(ctx, st) != FR_OK) return std::string("device status after evaluation: ") + fr_last_error(ctx);
+        // a failed read stops the loop; the requests retired before it leave
+        // `active` here, so the caller's fail_active handles only the others
+        std::string err;
         for (Request* r : fin) {
             double loss = 0.0;
-            if (cudaMemcpy(&loss, r->loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-                return "reading a final loss failed";
+            if (!read_back(&loss, r->loss, sizeof(double))) {
+                err = "reading a final loss failed";
+                break;
+            }
             // the final parameters are read back to check them (and kept if asked)
             std::vector<float> keep(r->n_par);
-            if (cudaMemcpy(keep.data(), r->x, sizeof(float) * r->n_par, cudaMemcpyDeviceToHost) != cudaSuccess)
-                return "reading final parameters failed";
+            if (!read_back(keep.data(), r->x, sizeof(float) * r->n_par)) {
+                err = "reading final parameters failed";
+                break;
+            }
             bool finite = std::isfinite(loss);
             for (size_t i = 0; finite && i < keep.size(); ++i) finite = std::isfinite(keep[i]);
             if (!cfg.keep_params || !finite) keep.clear();
@@ -475,13 +484,25 @@ struct fr_server {
                                     [](Request* r) { return r->state == FR_REQ_DONE || r->state == FR_REQ_FAILED; }),
                      active.end());
         idle.notify_all();
-        return "";
+        return err;
+    }
+
+    // Device-to-host read of a result.  A test can make the n-th read from now
+    // fail on the host (fr_server_inject_read_failure) to exercise the error
+    // path without a device fault.
+    bool read_back(void* dst, const void* src, size_t bytes) {
+        int n = inject_read_fail.load();
+        while (n >= 0 && !inject_read_fail.compare_exchange_weak(n, n - 1)) {
+        }
+        if (n == 0) return false;
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
     }
 
     void fail_active(const std::string& why) {
         for (Request* r : active) release(*r);
         std::lock_guard<std::mutex> lk(mu);
         for (Request* r : active) {
+            if (r->state == FR_REQ_DONE || r->state == FR_REQ_FAILED) continue;   // already accounted for
             r->state = FR_REQ_FAILED;
             r->err = why;
             r->t_finish = now_s(t0);
@@ -685,6 +706,12 @@ fr_status fr_server_wait(fr_server* s, double timeout_s) {
     return ok ? FR_OK : FR_ETIMEOUT;
 }
 
+fr_status fr_server_inject_read_failure(fr_server* s, int32_t n) {
+    if (!s || n < 0) return FR_EINVAL;
+    s->inject_read_fail.store(n);
+    return FR_OK;
+}
+
 fr_status fr_server_get_stats(fr_server* s, fr_server_stats* out) {
     if (!s || !out) return FR_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -693,6 +720,8 @@ fr_status fr_server_get_stats(fr_server* s, fr_server_stats* out) {
     int32_t running = 0;
     for (const auto& r : s->all) running += r->state == FR_REQ_RUNNING;
     out->active = running;
+    out->used_bytes = s->used;
+    out->finished = s->finished;
     return FR_OK;
 }
 

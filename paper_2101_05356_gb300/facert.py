@@ -106,7 +106,8 @@ class FrResult(ctypes.Structure):
 
 class FrServerStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("item_steps", ctypes.c_int64), ("max_active", ctypes.c_int32),
-                ("active", ctypes.c_int32), ("queued", ctypes.c_int32), ("peak_bytes", ctypes.c_uint64)]
+                ("active", ctypes.c_int32), ("queued", ctypes.c_int32), ("peak_bytes", ctypes.c_uint64),
+                ("used_bytes", ctypes.c_uint64), ("finished", ctypes.c_uint64)]
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -177,6 +178,7 @@ def lib():
         L.fr_server_wait.argtypes = [_vp, ctypes.c_double]
         L.fr_server_get_stats.argtypes = [_vp, P(FrServerStats)]
         L.fr_cancel.argtypes = [_vp, ctypes.c_uint64]
+        L.fr_server_inject_read_failure.argtypes = [_vp, ctypes.c_int32]
         L.fr_debug_wait_timeout.argtypes = [_vp, ctypes.c_uint32, _vp]
         L.fr_server_destroy.argtypes = [_vp]
         L.fr_server_destroy.restype = None
@@ -584,6 +586,12 @@ def fr_server_get_stats(srv):
 
 def fr_server_destroy(srv):
     lib().fr_server_destroy(srv)
+
+
+def fr_server_inject_read_failure(srv, n):
+    """Test hook: the n-th device-to-host result read of the server from now
+    fails on the host (no device fault)."""
+    check(lib().fr_server_inject_read_failure(srv, n))
 
 
 def fr_cancel(srv, rid):

@@ -230,3 +230,39 @@ def test_results_are_the_same_alone_and_in_a_batch_of_40():
         assert got[k].final_loss == ref.final_loss
         for n in ("coef", "rot", "trans", "light_i", "diffuse", "specular", "roughness"):
             assert np.array_equal(got[k].params[n], ref.params[n]), (k, n)
+
+
+def test_a_failed_result_read_fails_only_the_unread_requests():
+    """Host-side fault in the retirement of a step: three requests finish in the
+    same step and the third device-to-host read (the second request's final
+    loss) is made to fail on the host.  The first request keeps its result
+    (bitwise the Python server's); the other two fail with the read's message;
+    every request is counted once and the admitted-state bytes return to zero
+    (a request retired before the failure is not released a second time)."""
+    from paper_2101_05356_gb300 import facert, optim, serve
+    sc = synth.make_scene("c1")
+    specs = [(32, 32, 2)] * 3
+    sched = optim.Schedule(2, 1)
+    reqs = _requests(sc, specs, sched)
+    ns = serve.NativeServer(sc, max_slots=3, **KW)
+    try:
+        # reads of a retiring request: its final loss, then its parameters
+        facert.fr_server_inject_read_failure(ns.srv, 2)
+        ids = [facert.fr_submit(ns.srv, q.target, q.init, q.spp, q.schedule.stage1, q.schedule.stage2)
+               for q in reqs]
+        assert facert.fr_server_wait(ns.srv, 600.0)
+        res = [facert.fr_poll(ns.srv, i, ns._shapes(q.init)) for i, q in zip(ids, reqs)]
+        stats = facert.fr_server_get_stats(ns.srv)
+    finally:
+        ns.close()
+    assert res[0][1]["state"] == facert.REQ_DONE
+    for k in (1, 2):
+        assert res[k][1]["state"] == facert.REQ_FAILED
+        assert res[k][1]["error"] == "reading a final loss failed"
+    assert stats["finished"] == 3
+    assert stats["used_bytes"] == 0
+    assert stats["active"] == 0 and stats["queued"] == 0
+    ref = serve.Server(sc, max_slots=3, **KW).run(_requests(sc, specs, sched))
+    assert res[0][1]["final_loss"] == pytest.approx(ref[0].final_loss, rel=1e-12)
+    for n in ("coef", "rot", "trans", "light_i", "diffuse"):
+        assert np.array_equal(res[0][2][n], np.asarray(ref[0].params[n]).reshape(res[0][2][n].shape)), n
