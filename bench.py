@@ -2,22 +2,29 @@
 """Throughput of the differentiable ray-traced face render on GB300.
 
 One step = one pass of the hot path over one face: morph, pose + normals, BVH
-(refit of the mesh's static SAH topology), camera + shadow rays with Cook-Torrance shading, blur + L1 loss, and the
-adjoint (interior term from the forward's per-sample hit records, shadow-boundary
-and primary-edge terms, chain to the parameters).  Workload: the paper-scale single face (35,709 vertices /
-70,789 triangles, K = 80 + 64 bases, 256 x 256, 16 spp, 40 quad lights, 512^2
-textures), synthetic and seeded.
+(refit of the mesh's static SAH topology), camera + shadow rays with
+Cook-Torrance shading, blur + L1 loss, and the adjoint (interior term from the
+forward's per-sample hit records, shadow-boundary and primary-edge terms, chain
+to the parameters).  Headline workload: the paper-scale single face (35,709
+vertices / 70,789 triangles, K = 80 + 64 bases, 256 x 256, 16 spp, 40 quad
+lights, 512^2 textures), synthetic and seeded.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
 Prints one JSON line.  `value` is rays traced per second over the timed steps
 (inputs resident in HBM, L2 flushed between steps; each ray of the step is
 traced once, the adjoint reading the forward's hit records); `e2e` is the same
-metric with host buffers copied in and the loss copied out inside the timed
-region; `retrace` times the same step with the adjoint re-tracing every camera
-and shadow ray instead (the form used when the records exceed their budget),
-`lbvh_rebuild` with an LBVH rebuilt every call instead of the refitted static
-SAH topology.
+metric with the parameters and target copied in from pinned host memory and
+the image, loss and every gradient group copied out inside the timed region.
+Keyed legs: `large` (a batch of 8 faces of the 100,000-triangle mesh at
+1024^2, 64 spp, 80 lights, 2048^2 textures, adjoint re-tracing, with its own
+roofline), `serving_capacity` (requests shaped like the serving workload, all
+queued at t = 0: faces/s and latency of the continuous-batching servers against
+one face at a time, and their final losses), `retrace` (the headline step with
+the adjoint re-tracing), `lbvh_rebuild` (an LBVH rebuilt every call),
+`environment_map` (the face under a 32 x 32 environment map), `albedo` (the
+statistical albedo morph and its transpose against the HBM roofline) and
+`cpu_baseline` (the FP64 oracle on the host cores).
 The reference arm times the FP64 CPU oracle on a bounded sample of the same
 workload.  Under torchrun each rank renders an independent face (replicas).
 """
@@ -53,7 +60,9 @@ OPS_PER_TRI = 30
 TRAFFIC = {"k_forward": {"bytes": 31684352 + 28991488,
                          "sources_sha256": "5ab1fcf3a8b917d4239b1c443af1ee8851a16a00baee432f1097b8a678c26928"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
-SMS = 152
+# Issue-slot use (smsp__issue_active) of a kernel from the ncu --set full capture
+# summarised in profiles/, valid while its sources hash to `sources_sha256`.
+ISSUE = {}
 FP32_LANES_PER_SM = 128
 
 
@@ -71,6 +80,41 @@ def kernel_traffic(kernel):
     if not t or kernel not in KERNEL_SOURCES or kernel_sources_sha(kernel) != t["sources_sha256"]:
         return None
     return t["bytes"]
+
+
+def kernel_issue(kernel):
+    t = ISSUE.get(kernel)
+    if not t or kernel not in KERNEL_SOURCES or kernel_sources_sha(kernel) != t["sources_sha256"]:
+        return None
+    return t["frac"]
+
+
+def sm_count(dev=0):
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def traversal_roofline(cnt, stage, n_launches, dev=0):
+    """ALU roofline of the dominant ray kernel of a step: algorithmic traversal
+    work (OPS_PER_NODE per node visit, OPS_PER_TRI per triangle test, counted
+    by the kernel on the mesh's static binned-SAH topology, the reference tree)
+    over its mean CUDA-event time, against SMs x 128 FP32 lanes x the maximum
+    SM clock.  `stage` holds the per-launch stage times (ms) of the launches."""
+    pk, src = peaks()
+    ms = {k: float(np.mean([st[k] for st in stage])) for k in ("forward", "adjoint", "edge_primary")}
+    dom = max(ms, key=ms.get)
+    c = cnt[dom]
+    ops_per_launch = (c["nodes"] * OPS_PER_NODE + c["tris"] * OPS_PER_TRI) / n_launches
+    sms = sm_count(dev)
+    peak_ops = sms * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    achieved = ops_per_launch / (ms[dom] / 1000.0)
+    return {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+            "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": kernel_traffic("k_" + dom),
+            "issue_frac": kernel_issue("k_" + dom),
+            "peak_source": "derived: %d SMs (device) x %d FP32 lanes x %.0f MHz (%s clocks)"
+                           % (sms, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src),
+            "work_basis": "node visits and triangle tests on the static binned-SAH topology",
+            "ops_per_launch": ops_per_launch, "launch_ms": ms[dom]}
 
 
 def peaks():
@@ -181,11 +225,14 @@ def gpu_arm(args, rank, world):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def step(it):
+    def step_out(it):
         for g in grads.values():
             g.zero_()
         img, loss, _ = r.render(dp, tgt, iteration=it, face_id=rank, grads=grads)
-        return loss
+        return img, loss
+
+    def step(it):
+        return step_out(it)[1]
 
     for w in range(args.warmup):
         step(w)
@@ -225,21 +272,7 @@ def gpu_arm(args, rank, world):
     value = rays_all / (total_ms_max / 1000.0)
 
     # ---- dominant kernel roofline ----
-    pk, src = peaks()
-    adj_ms = float(np.mean([s["adjoint"] for s in stage]))
-    fwd_ms = float(np.mean([s["forward"] for s in stage]))
-    edge_ms = float(np.mean([s["edge_primary"] for s in stage]))
-    dom = "adjoint" if adj_ms >= max(fwd_ms, edge_ms) else ("forward" if fwd_ms >= edge_ms else "edge_primary")
-    dom_ms = {"adjoint": adj_ms, "forward": fwd_ms, "edge_primary": edge_ms}[dom]
-    c = cnt[dom]
-    ops_per_launch = (c["nodes"] * OPS_PER_NODE + c["tris"] * OPS_PER_TRI) / args.steps
-    peak_ops = SMS * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
-    achieved = ops_per_launch / (dom_ms / 1000.0)
-    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": kernel_traffic("k_" + dom),
-                "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz (%s clocks)"
-                               % (SMS, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src),
-                "ops_per_launch": ops_per_launch, "launch_ms": dom_ms}
+    roofline = traversal_roofline(cnt, stage, args.steps, dev)
 
     # ---- the same step in its alternative forms ----
     def timed_variant(flags, n_steps):
@@ -277,14 +310,18 @@ def gpu_arm(args, rank, world):
     env = env_variant(sc, params, tparams, args.retrace_steps, flush, stream) if args.retrace_steps > 0 else None
 
     # ---- end to end through the public API with host buffers ----
+    # every step copies the parameters and the target in from pinned host
+    # memory and the step's results out: image, loss and every gradient group
     e2e = None
     if args.e2e_steps > 0:
         host = {n: torch.as_tensor(np.ascontiguousarray(getattr(params, n), np.float32)).pin_memory()
                 for n in facert.PARAM_NAMES}
         host_tgt = tgt.cpu().pin_memory()
         host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        host_img = torch.empty(tuple(tgt.shape), dtype=torch.float32).pin_memory()
+        host_grads = {n: torch.empty(tuple(g.shape), dtype=g.dtype).pin_memory() for n, g in grads.items()}
         h2d = sum(t.numel() * 4 for t in host.values()) + host_tgt.numel() * 4
-        d2h = 8
+        d2h = 8 + host_img.numel() * 4 + sum(t.numel() * t.element_size() for t in host_grads.values())
         facert.fr_counters(r.ctx, reset=True)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -296,8 +333,11 @@ def gpu_arm(args, rank, world):
             for n in facert.PARAM_NAMES:
                 dp[n].copy_(host[n], non_blocking=True)
             tgt.copy_(host_tgt, non_blocking=True)
-            loss = step(10 ** 5 + k)
+            img, loss = step_out(10 ** 5 + k)
             host_loss.copy_(loss, non_blocking=True)
+            host_img.copy_(img, non_blocking=True)
+            for n, g in grads.items():
+                host_grads[n].copy_(g, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
@@ -439,25 +479,19 @@ def serving_bench(n_requests, iters, rate, seed=0):
     return out
 
 
-def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slots=8,
-               forms=("served", "native", "plain")):
-    """The serving workload: a Poisson stream of two-stage reconstructions of
-    the paper-scale face (35,709 vertices, 40 lights, 512^2 textures, a
-    statistical albedo model of 80 + 80 columns, 68 landmarks) with image
-    size uniform in {128, 192, 256, 384, 512}^2 and spp in {4, 8, 16, 32};
-    each request runs `init` landmark iterations, then Stage I and Stage II.
-    The arrival rate is 0.9 x the served closed-loop capacity measured first
-    on a short prefix.  Served (continuous batching, BF16 tensor-core morphs,
-    max_slots slots) and plain (one face at a time, FP32) see the same stream;
-    final losses are evaluated at 32 spp with a fixed evaluation stream."""
+def _c4_requests(n_requests, seed=0):
+    """Targets of the serving workload: image size uniform in {128, 192, 256,
+    384, 512}^2 and spp in {4, 8, 16, 32}, each a render of random
+    ground-truth parameters at its own size and spp on the paper-scale face
+    (35,709 vertices, 40 lights, 512^2 textures, statistical albedo 80 + 80,
+    68 landmarks), with the landmark targets their projections."""
     import torch
 
-    from paper_2101_05356_gb300 import facert, optim, serve, synth
+    from paper_2101_05356_gb300 import facert, synth
     sc = synth.make_scene("c2", albedo_k=80)
     rng = np.random.default_rng(seed)
     sizes = rng.choice([128, 192, 256, 384, 512], size=n_requests)
     spps = rng.choice([4, 8, 16, 32], size=n_requests)
-    # targets and landmark targets rendered from ground-truth parameters
     gen = facert.Renderer(sc.__class__(**{**sc.__dict__, "width": 512, "height": 512, "spp": 32, "albedo": None}))
     targets, marks = [], []
     zero = torch.zeros((512 * 512 * 3,), device="cuda")
@@ -473,20 +507,73 @@ def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slot
         targets.append(img.cpu().numpy())
         marks.append(proj.cpu().numpy())
     gen.close()
+    return sc, rng, sizes, spps, targets, marks
+
+
+def _c4_server(sc, slots, flags, native=False):
+    from paper_2101_05356_gb300 import serve
+    cls = serve.NativeServer if native else serve.Server
+    return cls(sc, max_slots=slots, flags=flags, max_width=512, max_height=512, max_spp=32,
+               eval_spp=32, keep_params=False, mem_cap_bytes=64 << 30)
+
+
+def serving_capacity(n_requests=24, stage1=100, stage2=100, init=20, seed=1, max_slots=8):
+    """Closed-loop capacity of the served and plain forms on requests shaped
+    like the serving workload (the full size and spp mix, the full landmark +
+    Stage I + Stage II schedule), all queued at t = 0: faces/s = requests /
+    time to finish all of them; latency = finish time of each request.  Served
+    = continuous batching with BF16 tensor-core morphs (the Python server and
+    the library's server); plain = one face at a time, FP32 morph.  Final
+    losses are evaluated at 32 spp with a fixed evaluation stream."""
+    import torch
+
+    from paper_2101_05356_gb300 import facert, optim, serve, synth
+    sc, _, sizes, spps, targets, marks = _c4_requests(n_requests, seed)
+    sched = optim.Schedule(stage1=stage1, stage2=stage2, init=init)
+    out = {"workload": "%d requests queued at t = 0, sizes {128..512}^2 (mean %.0f^2), spp {4,8,16,32} (mean %.1f), "
+                       "%d landmark + %d + %d iterations, 35,709-vertex face, 40 lights, statistical albedo 80+80, "
+                       "68 landmarks" % (n_requests, float(np.sqrt(np.mean(sizes.astype(float) ** 2))),
+                                         float(np.mean(spps)), init, stage1, stage2)}
+    for name, slots, flags, native in (("served", max_slots, facert.FLAG_MORPH_BF16, False),
+                                       ("native", max_slots, facert.FLAG_MORPH_BF16, True),
+                                       ("plain", 1, 0, False)):
+        reqs = [serve.Request(rid=k, target=targets[k], spp=int(spps[k]), schedule=sched, arrival=0.0,
+                              init=synth.init_params(sc), landmarks=marks[k]) for k in range(n_requests)]
+        srv = _c4_server(sc, slots, flags, native)
+        done = srv.run(reqs)
+        out[name] = _serving_summary(serve, srv, done)
+        _close_server(srv)
+        torch.cuda.synchronize()
+    for name in ("served", "native"):
+        out[name + "_capacity_speedup"] = out[name]["faces_per_s"] / out["plain"]["faces_per_s"]
+        out[name + "_final_loss_ratio"] = out[name]["mean_final_loss"] / out["plain"]["mean_final_loss"]
+    return out
+
+
+def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slots=8,
+               forms=("served", "native", "plain")):
+    """The serving workload: a Poisson stream of two-stage reconstructions of
+    the paper-scale face (35,709 vertices, 40 lights, 512^2 textures, a
+    statistical albedo model of 80 + 80 columns, 68 landmarks) with image
+    size uniform in {128, 192, 256, 384, 512}^2 and spp in {4, 8, 16, 32};
+    each request runs `init` landmark iterations, then Stage I and Stage II.
+    The arrival rate is 0.9 x the served closed-loop capacity measured first
+    on a short prefix.  Served (continuous batching, BF16 tensor-core morphs,
+    max_slots slots) and plain (one face at a time, FP32) see the same stream;
+    final losses are evaluated at 32 spp with a fixed evaluation stream."""
+    import torch
+
+    from paper_2101_05356_gb300 import facert, optim, serve, synth
+    sc, rng, sizes, spps, targets, marks = _c4_requests(n_requests, seed)
     sched = optim.Schedule(stage1=stage1, stage2=stage2, init=init)
 
     def stream(arrivals):
         return [serve.Request(rid=k, target=targets[k], spp=int(spps[k]), schedule=sched, arrival=float(arrivals[k]),
                               init=synth.init_params(sc), landmarks=marks[k]) for k in range(n_requests)]
 
-    def server(slots, flags, native=False):
-        cls = serve.NativeServer if native else serve.Server
-        return cls(sc, max_slots=slots, flags=flags, max_width=512, max_height=512, max_spp=32,
-                   eval_spp=32, keep_params=False, mem_cap_bytes=64 << 30)
-
     # closed-loop capacity of the served form on a prefix (all arrive at once)
     n_cap = min(n_requests, 2 * max_slots)
-    srv = server(max_slots, facert.FLAG_MORPH_BF16, "native" in forms)
+    srv = _c4_server(sc, max_slots, facert.FLAG_MORPH_BF16, "native" in forms)
     srv.run(stream(np.zeros(n_requests))[:n_cap])
     capacity = n_cap / srv.elapsed
     _close_server(srv)
@@ -501,7 +588,7 @@ def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slot
                                        ("plain", 1, 0, False)):
         if name not in forms:
             continue
-        srv = server(slots, flags, native)
+        srv = _c4_server(sc, slots, flags, native)
         reqs = srv.run(stream(arrivals))
         out[name] = _serving_summary(serve, srv, reqs)
         _close_server(srv)
@@ -513,13 +600,14 @@ def serving_c4(n_requests=512, stage1=100, stage2=100, init=20, seed=0, max_slot
     return out
 
 
-def large_bench(batch=8, steps=2, warmup=1):
+def large_bench(batch=8, steps=3, warmup=2):
     """The large workload: a batch of `batch` faces of the 100,000-triangle
     mesh (K = 20), 1024 x 1024, 64 spp, 80 lights, 2048^2 textures, BF16
     tensor-core morph, one fused forward + loss + adjoint call per step
     (fr_render_batch); the hit records exceed their budget, so the adjoint
-    re-traces every camera and shadow ray.  Device-resident inputs, CUDA events
-    around each step."""
+    re-traces every camera and shadow ray.  Device-resident inputs (far
+    larger than L2), CUDA events around each step, stage times from the
+    library's events, and the roofline of the step's dominant ray kernel."""
     import torch
 
     from paper_2101_05356_gb300 import facert, synth
@@ -536,14 +624,15 @@ def large_bench(batch=8, steps=2, warmup=1):
                           loss=torch.zeros(1, dtype=torch.float64, device="cuda"), grads=r.zero_grads(dp)))
     stream = torch.cuda.current_stream()
     ms, stages = [], []
-    facert.fr_counters(r.ctx, reset=True)
     for k in range(warmup + steps):
         for it in items:
             it["iteration"] = k
             for g in it["grads"].values():
                 g.zero_()
         if k == warmup:
+            torch.cuda.synchronize()
             facert.fr_counters(r.ctx, reset=True)
+            facert.fr_set_timing(r.ctx, True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -552,16 +641,22 @@ def large_bench(batch=8, steps=2, warmup=1):
         e1.synchronize()
         if k >= warmup:
             ms.append(e0.elapsed_time(e1))
+            stages.append(facert.fr_get_timing(r.ctx))
+    facert.fr_set_timing(r.ctx, False)
     cnt = facert.fr_counters(r.ctx, reset=True)
     rays = sum(v["rays"] for v in cnt.values()) / steps
     status = r.status()
+    roof = traversal_roofline(cnt, stages, steps)
     r.close()
     torch.cuda.empty_cache()
     s_step = float(np.mean(ms)) / 1000.0
     return {"workload": "batch of %d faces: 50,002 verts / 100,000 tris, K = 20, 1024 x 1024, 64 spp, 80 lights, "
                         "2048^2 textures, BF16 morph, adjoint re-tracing" % batch,
             "s_per_step": s_step, "rays_per_step": rays, "rays_per_s": rays / s_step,
-            "face_steps_per_s": batch / s_step, "steps": steps, "status": int(status)}
+            "face_steps_per_s": batch / s_step, "steps": steps, "warmup": warmup, "status": int(status),
+            "l2": "inputs far larger than L2 (hit records re-traced, 2048^2 textures per face)",
+            "stage_ms": {k: float(np.mean([st[k] for st in stages])) for k in stages[0]},
+            "roofline": roof}
 
 
 def albedo_bench(batch=8, reps=10):
@@ -619,17 +714,26 @@ def albedo_bench(batch=8, reps=10):
     return out
 
 
-def cpu_baseline(sample_pixels, threads=0):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload:
-    forward + adjoint (all terms) restricted to `sample_pixels` random pixels."""
+def cpu_baseline(sample_pixels, threads=0, c1_full=True):
+    """The FP64 oracle as it stands, timed on the host cores.
+
+    * Headline sample: forward + adjoint (all terms) of the benchmark's face
+      restricted to `sample_pixels` random pixels; rays/s over that sample.
+    * One full forward + adjoint iteration of that face and a two-stage
+      reconstruction (20 landmark + 100 + 100 iterations, the paper's
+      schedule) EXTRAPOLATED from the sample's time per pixel (Stage II has no
+      edge terms, so the reconstruction figure overstates it somewhat).
+    * With c1_full: the small face (2,562 vertices, 64 x 64, 4 spp, 8 lights)
+      forward + adjoint in full, measured."""
     import oracle
+    from paper_2101_05356_gb300 import synth
     sc, params, tparams = make_workload(0)
     rng = np.random.default_rng(1)
     npx = sc.width * sc.height
     pix = np.sort(rng.choice(npx, size=sample_pixels, replace=False)).astype(np.int32)
     adj = np.zeros((sc.height, sc.width, 3))
     adj.reshape(-1, 3)[pix] = rng.uniform(0.2, 1.0, (sample_pixels, 3))
-    cores = threads or len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = threads or (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
     oracle.build()
     oracle.ray_count(reset=True)
     t0 = time.perf_counter()
@@ -637,10 +741,30 @@ def cpu_baseline(sample_pixels, threads=0):
     oracle.grad(sc, params, adj, n_threads=cores, edge_spp=1)
     dt = time.perf_counter() - t0
     rays = oracle.ray_count(reset=True)
-    return {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of %d pixels of the workload (16 spp, 40 lights), forward + adjoint with all "
-                      "edge terms; %d rays in %.1f s" % (sample_pixels, npx, rays, dt),
-            "seconds": dt}
+    it_s = dt / sample_pixels * npx
+    out = {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
+           "sample": "%d of %d pixels of the workload (16 spp, 40 lights), forward + adjoint with all "
+                     "edge terms; %d rays in %.1f s" % (sample_pixels, npx, rays, dt),
+           "seconds": dt,
+           "iteration_s_extrapolated": it_s,
+           "reconstruction_s_extrapolated": 220 * it_s,
+           "extrapolation": "time per sampled pixel x %d pixels; reconstruction = 220 such iterations "
+                            "(20 landmark-only iterations cost far less, and Stage II has no edge terms)" % npx}
+    if c1_full:
+        s1 = synth.make_scene("c1")
+        p1 = synth.init_params(s1)
+        t1 = oracle.render(s1, synth.random_params(s1, 3), n_threads=cores).astype(np.float32)
+        oracle.ray_count(reset=True)
+        t0 = time.perf_counter()
+        img = oracle.render(s1, p1, n_threads=cores)
+        _, _, a1 = oracle.loss(img, t1)
+        oracle.grad(s1, p1, a1, n_threads=cores, edge_spp=1)
+        d1 = time.perf_counter() - t0
+        r1 = oracle.ray_count(reset=True)
+        out["c1_full"] = {"workload": "2,562 verts / 5,120 tris, K = 20, 64 x 64, 4 spp, 8 lights, forward + loss + "
+                                      "adjoint with all terms, every pixel", "seconds": d1, "rays": r1,
+                          "rays_per_s": r1 / d1}
+    return out
 
 
 def main():
@@ -651,7 +775,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--retrace-steps", type=int, default=5)
-    ap.add_argument("--cpu-pixels", type=int, default=48)
+    ap.add_argument("--cpu-pixels", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-albedo", action="store_true")
     ap.add_argument("--serve-c4", type=int, default=0, help="run the serving workload with this many requests")
@@ -663,7 +787,13 @@ def main():
                          "server, native = the library's server, plain = one face at a time)")
     ap.add_argument("--large", action="store_true",
                     help="run the large workload (batch of 8 faces, 1024^2, 64 spp, 100,000 triangles) on its own line")
-    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--large-steps", type=int, default=3,
+                    help="timed steps of the large-workload leg (0: skip it)")
+    ap.add_argument("--large-warmup", type=int, default=2)
+    ap.add_argument("--capacity-requests", type=int, default=24,
+                    help="requests of the closed-loop served vs plain capacity leg (0: skip it)")
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests of the reduced Poisson stream leg (0: skip it)")
     ap.add_argument("--serve-iters", type=int, default=6)
     ap.add_argument("--serve-rate", type=float, default=40.0)
     args = ap.parse_args()
@@ -671,7 +801,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
 
     if args.large:
-        res = large_bench()
+        res = large_bench(steps=max(args.large_steps, 1), warmup=args.large_warmup)
         print(json.dumps({"metric": "rays/s fwd+adjoint (large workload)", "value": res["rays_per_s"],
                           "unit": "rays/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
                           "large": res}))
@@ -692,7 +822,7 @@ def main():
             return
         per = []
         for k in range(args.warmup + args.steps):
-            b = cpu_baseline(max(4, args.cpu_pixels // 4))
+            b = cpu_baseline(max(4, args.cpu_pixels // 8), c1_full=False)
             if k >= args.warmup:
                 per.append(b)
         v = float(np.mean([b["value"] for b in per]))
@@ -711,6 +841,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     out = gpu_arm(args, rank, world)
+    if rank == 0 and world == 1 and args.large_steps > 0:
+        out["large"] = large_bench(steps=args.large_steps, warmup=args.large_warmup)
+    if rank == 0 and world == 1 and args.capacity_requests > 0:
+        out["serving_capacity"] = serving_capacity(args.capacity_requests)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving_bench(args.serve_requests, args.serve_iters, args.serve_rate)
     if rank == 0 and world == 1 and not args.no_albedo:

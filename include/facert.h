@@ -326,8 +326,9 @@ fr_status fr_debug_trace(fr_ctx* ctx, const fr_params* p, const float* org, cons
                          int32_t n, int32_t* tri, float* t, void* stream);
 
 /* Forward render that also writes per-sample records: tri_rec [H*W*spp] hit
- * triangle (-1 miss) and mask_rec [H*W*spp] bit j = shadow ray to light j
- * traced and unoccluded (lights 0..63 only); record index = (y*W + x)*spp + sample. */
+ * triangle (-1 miss) and mask_rec [H*W*spp][2] visibility words: bit j of word
+ * w = the shadow ray to light 64 w + j was traced and is unoccluded; record
+ * index = (y*W + x)*spp + sample. */
 fr_status fr_debug_records(fr_ctx* ctx, const fr_params* p, float* image, int32_t* tri_rec,
                            uint64_t* mask_rec, uint32_t iteration, uint32_t face_id,
                            void* stream);
@@ -402,8 +403,10 @@ uint64_t fr_kernel_launches(void);
 /* One parameter group.  x, m, v (and g, aux when used) are device float32
  * arrays of n elements (aux: N_L scales for LIGHT, the M x M x 3 reference
  * albedo for TEX_RGB, the N_L x 3 intensities for STAGE).  aux2 is used by
- * LIGHT only: when aux is NULL the scales are d_j^2 / a_j read from aux2, the
- * x of the STAGE group ([d | a | p], 4 N_L floats) at its pre-step values.  m and v must be zero before step 1.  After the update x
+ * LIGHT only: when aux is NULL the scales are d_j^2 / a_j computed from aux2
+ * = [d (N_L) | a (N_L) | ...]: the x of the STAGE group ([d | a | p], 4 N_L
+ * floats) at its pre-step values, or the lights' fixed d and a (2 N_L floats).
+ * m and v must be zero before step 1.  After the update x
  * is clamped to [clamp_lo, clamp_hi] when clamp_lo < clamp_hi.  step > 0 gives
  * this group its own Adam step count (groups of different faces in one call);
  * step = 0 uses the call's step. */

@@ -192,12 +192,13 @@ def closest_hit(scene, params, org, dirs, n_threads=0):
 def render(scene, params, iteration=0, face_id=0, pixels=None, flags=0, seed=0,
            records=False, n_threads=0):
     """Forward render [H, W, 3] (float64); with records also the per-sample hit
-    triangle [H*W*spp] and shadow visibility mask [H*W*spp]."""
+    triangle [H*W*spp] and shadow visibility masks [H*W*spp, 2] (bit j of word
+    w: the shadow ray to light 64 w + j was traced and is unoccluded)."""
     b = _Bound(scene, params, flags=flags, seed=seed, n_threads=n_threads)
     img = np.zeros((scene.height, scene.width, 3))
     n_rec = scene.height * scene.width * scene.spp
     tri = np.full(n_rec, -2, np.int32) if records else None
-    mask = np.zeros(n_rec, np.uint64) if records else None
+    mask = np.zeros((n_rec, 2), np.uint64) if records else None
     pix = None if pixels is None else np.ascontiguousarray(pixels, np.int32)
     lib().ora_render(ctypes.byref(b.scene), ctypes.byref(b.params), iteration, face_id,
                      _p(pix, i32p), 0 if pix is None else len(pix), _p(img, f64p),

@@ -1154,7 +1154,10 @@ int ora_render(const OraScene* s, const OraParams* p, uint32_t iteration, uint32
             for (int k = 0; k < 3; ++k) acc[k] += so.L[k].v;
             size_t rec = (size_t)pix * P.spp + smp;
             if (tri_rec) tri_rec[rec] = so.tri;
-            if (mask_rec) mask_rec[rec] = so.mask[0];   // lights 0..63
+            if (mask_rec) {                             // lights 0..63, 64..127
+                mask_rec[2 * (size_t)rec] = so.mask[0];
+                mask_rec[2 * (size_t)rec + 1] = so.mask[1];
+            }
         }
         for (int k = 0; k < 3; ++k) image[(size_t)pix * 3 + k] = acc[k] / P.spp;
     });

@@ -29,6 +29,7 @@ struct Slot {
     BvhScratch B{};
     BvhNode* nodes = nullptr;
     float4* tris = nullptr;
+    int* slot_of = nullptr;
     uint8_t* sil_flags = nullptr;
     int* lists = nullptr;
     int* counts = nullptr;
@@ -57,7 +58,6 @@ struct LinearModel {
     float* mean = nullptr;
     float* basis = nullptr;
     uint16_t* tiles = nullptr;           // [ceil(rows / 128)][128][Kp] BF16, no-swizzle K-major core matrices
-    uint16_t* coef_tile = nullptr;       // BF16 [64][Kp] gathered coefficients
     double* part = nullptr;              // [FR_MAX_BATCH][K][linear_adj_chunks(rows)]
 };
 
@@ -181,6 +181,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     s.W = a.W; s.H = a.H; s.spp = a.spp; s.M = c->cfg.tex_size; s.edge_spp = a.edge_spp;
     s.flags = a.flags; s.seed = c->cfg.seed;
     s.v = sl.v_cam; s.vn = sl.vn; s.uv = c->uv; s.faces = c->faces; s.nodes = sl.nodes; s.tris = sl.tris;
+    s.slot_of = sl.slot_of;
     s.lights = c->lights; s.status = c->status; s.counters = c->counters;
     const fr_params* p = a.p;
     it.P = DevParams{p->coef, p->rot, p->trans, p->focal, p->light_i, p->diffuse, p->specular, p->roughness,
@@ -224,6 +225,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     }
     it.nodes = sl.nodes;
     it.tris = sl.tris;
+    it.slot_of = sl.slot_of;
     it.v_cam = sl.v_cam;
     it.vn = sl.vn;
     it.v_model = sl.v_model;
@@ -272,7 +274,7 @@ fr_status upload(fr_ctx* c, int n, cudaStream_t st) {
 // when the context has FR_FLAG_MORPH_BF16, else in FP32
 void linear_forward(fr_ctx* c, const LinearModel& m, const LinearTable& t, cudaStream_t st) {
     if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && m.K > 0)
-        launch_linear_tc(m.tiles, m.Kp, m.K, m.coef_tile, m.mean, m.rows, t, c->status, st);
+        launch_linear_tc(m.tiles, m.Kp, m.K, m.mean, m.rows, t, c->status, st);
     else
         launch_linear(m.mean, m.basis, m.ld, m.rows, m.K, t, st);
 }
@@ -338,7 +340,6 @@ fr_status upload_model(fr_ctx* c, LinearModel& m, int rows, int K, const float* 
             }
         }
     TRY(dalloc(c, &m.tiles, bt.size()));
-    TRY(dalloc(c, &m.coef_tile, (size_t)morph_tc_coef_tile_elems(m.Kp)));
     CK(c, cudaMemcpy(m.tiles, bt.data(), sizeof(uint16_t) * bt.size(), cudaMemcpyHostToDevice));
     return FR_OK;
 }
@@ -437,6 +438,7 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.B.aabb, 6));
     TRY(dalloc(c, &sl.nodes, std::max(T - 1, 1)));
     TRY(dalloc(c, &sl.tris, 3 * (size_t)T));
+    TRY(dalloc(c, &sl.slot_of, T));
     // [1 + 64 lists][E] edge flags, then [64 lights][T] per-face facing classes
     TRY(dalloc(c, &sl.sil_flags, (size_t)(1 + FR_MAX_LIGHTS) * c->E + (size_t)FR_MAX_LIGHTS * T));
     TRY(dalloc(c, &sl.lists, (size_t)(1 + FR_MAX_LIGHTS) * c->E));
@@ -500,11 +502,8 @@ void ctx_info(const fr_ctx* c, CtxInfo& o) {
     o.k_specular = c->have_albedo ? c->albedo[1].K : 0;
     o.have_stage = c->use_stage;
     o.env_size = c->env_size;
-    o.light_scale.resize(c->light_d_h.size());
-    for (size_t j = 0; j < c->light_d_h.size(); ++j) {
-        const float d2 = c->light_d_h[j] * c->light_d_h[j];
-        o.light_scale[j] = d2 / c->light_a_h[j];
-    }
+    o.light_da = c->light_d_h;
+    o.light_da.insert(o.light_da.end(), c->light_a_h.begin(), c->light_a_h.end());
 }
 
 extern "C" {

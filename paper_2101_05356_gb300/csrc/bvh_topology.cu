@@ -20,7 +20,10 @@
 
 namespace {
 
-constexpr int SAH_BINS = 32;
+#ifndef FR_SAH_BINS
+#define FR_SAH_BINS 32
+#endif
+constexpr int SAH_BINS = FR_SAH_BINS;
 constexpr int SAH_MAX_DEPTH = 40;
 
 struct Box {

@@ -105,6 +105,7 @@ struct DevScene {
     const int4* faces;      // [T]
     const BvhNode* nodes;   // [max(T - 1, 1)]
     const float4* tris;     // [3T] triangles in BVH leaf order; tris[3s].w = id bits
+    const int* slot_of;     // [T] leaf slot of each triangle (inverse of the leaf order)
     const LightDev* lights; // [NL]
     const float* stage;     // [NL][12] virtual light stage frame (centre, unit face V0 V1 V2);
                             // non-null when the lights are built from (d, a, p) parameters
@@ -206,6 +207,7 @@ struct DevItem {
     BvhScratch B;
     BvhNode* nodes;         // slot BVH (write side of S.nodes)
     float4* tris;           // slot triangles (write side of S.tris)
+    int* slot_of;           // write side of S.slot_of
     float4* v_cam;          // write side of S.v
     float4* vn;             // write side of S.vn
     float* v_model;

@@ -45,10 +45,9 @@ void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const Li
 // morph_tc.cu: the same forward as one BF16 tensor-core GEMM over the batch
 // (tiles: the basis as [ceil(rows / 128)][128][Kp] BF16 operand tiles)
 int morph_tc_smem_bytes(int Kp);
-int morph_tc_coef_tile_elems(int Kp);
 void launch_wait_probe(unsigned limit, int* status, cudaStream_t st);
-void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int rows,
-                      const LinearTable& t, int* status, cudaStream_t st);
+void launch_linear_tc(const uint16_t* tiles, int Kp, int K, const float* mean, int rows, const LinearTable& t,
+                      int* status, cudaStream_t st);
 
 // landmark.cu: sparse landmark loss (one block; L <= 256)
 struct LandmarkArgs {
@@ -74,7 +73,7 @@ struct CtxInfo {
     uint32_t flags = 0;
     bool ready = false, have_albedo = false, have_stage = false;
     int env_size = 0;                 // environment map side (0: no environment blocks)
-    std::vector<float> light_scale;   // d_j^2 / a_j of the light records, in float32 arithmetic
+    std::vector<float> light_da;      // [d (N_L) | a (N_L)] of the light records
 };
 void ctx_info(const fr_ctx* c, CtxInfo& out);
 

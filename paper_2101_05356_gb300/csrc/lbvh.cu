@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(256) k_boxes(const DevItem* items, const int4*
     const int4 t = faces[id];
     const float4 a = v[t.x], b = v[t.y], c = v[t.z];
     tris[3 * s] = make_float4(a.x, a.y, a.z, __int_as_float(id));
+    it.slot_of[id] = s;
     tris[3 * s + 1] = make_float4(b.x, b.y, b.z, 0.0f);
     tris[3 * s + 2] = make_float4(c.x, c.y, c.z, 0.0f);
     float3 lo = f3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));

@@ -4,24 +4,41 @@
 // Sigma_r beta, S = a_b + Sigma_b gamma in texture space):
 //     D[i][b] = sum_k basis[i][k] coef[b][k]      (BF16 x BF16 -> FP32 in TMEM)
 //     y_b[i]  = mean[i] + D[i][b]                 (FP32 epilogue)
-// One CTA owns 128 rows i of the 3N dimension and all faces of the batch,
-// padded to the MMA width N (32, or 64 for batches of 33 to 64 faces).  The
-// basis tile (pre-arranged at set-up in the no-swizzle K-major core-matrix
-// layout, 8 rows x 16 bytes per core matrix) and the gathered coefficient tile
-// arrive by two bulk asynchronous copies completing on one mbarrier; a single
-// thread issues K/16 tcgen05.mma instructions into a 128 x N FP32 TMEM
-// accumulator; four warps read it back with tcgen05.ld (32 columns at a time)
-// and write v_b.
-// Every wait is bounded: on a timeout the CTA sets the status word, waits
-// (bounded) for its own copies, frees its TMEM and returns.
+// The basis is pre-arranged at set-up as 128-row tiles in the no-swizzle
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix); every CTA
+// gathers the batch's coefficients into one B tile in shared memory (BF16,
+// the same layout), padded to the MMA width N (32, or 64 for batches of 33 to
+// 64 faces).
+//
+// The kernel is persistent and warp-specialised: each CTA walks the row tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the basis.  A producer warp keeps
+// a ring of `stages` shared-memory buffers filled with bulk asynchronous copies
+// of the tiles (one "full" and one "empty" mbarrier per buffer); an MMA warp
+// issues each tile's K/16 tcgen05.mma instructions into one of two 128 x N
+// FP32 TMEM accumulators as soon as its copy has landed and the accumulator is
+// free, and commits them to the buffer's "empty" barrier and the accumulator's
+// "full" barrier; four epilogue warps read a finished accumulator back with
+// tcgen05.ld, write y_b and release it.  So copies, MMAs and epilogues of
+// consecutive tiles overlap, and the basis streams from HBM at the copy rate.
+// Every wait is bounded: a role whose wait gives up sets the status word and
+// stops; the others then give up in turn.  Before the CTA frees its TMEM and
+// exits it gives the last copy into every buffer and the last MMAs of both
+// accumulators a second bounded wait; if one of those also gives up it sets
+// FR_STATUS_TIMEOUT_UNSAFE as well (a late write may land in shared memory or
+// TMEM that a later CTA has been given, so the host treats the context as
+// unusable from then on).
 #include "common.cuh"
 #include "kernels.h"
 
 namespace {
 
-constexpr int TC_M = 128;        // rows per CTA (TMEM lanes)
+constexpr int TC_M = 128;        // rows per tile (TMEM lanes)
 constexpr int TC_N_MAX = 64;     // widest MMA: faces per call, padded
-constexpr int TC_THREADS = 128;
+constexpr int TC_EPI_WARPS = 4;             // epilogue warps: TMEM lanes 32w..32w+31
+constexpr int TC_PRODUCER = 4, TC_MMA = 5;   // warp indices of the copy and MMA roles
+constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 2);
+constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_STAGE_BYTES = 64 * 1024;   // shared memory given to the ring of basis tiles
 constexpr unsigned SPIN_LIMIT = 1u << 22;
 
 FR_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -76,97 +93,198 @@ FR_D void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+FR_D void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    const uint32_t b = smem_u32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+FR_D uint16_t bf16_rne(float f) {
+    uint32_t u = __float_as_uint(f);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+FR_D void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+FR_D void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
 template <int TC_N>
-__global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restrict__ basis_tiles, int Kp,
-                                                         const uint16_t* __restrict__ coef_tile,
-                                                         const float* __restrict__ mean, int n3, LinearTable t,
-                                                         int* status) {
+__global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restrict__ basis_tiles, int K, int Kp,
+                                                         const float* __restrict__ mean, int n3, int n_tiles,
+                                                         int stages, LinearTable t, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int a_bytes = TC_M * Kp * 2, b_bytes = TC_N * Kp * 2;
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + a_bytes;
-    __shared__ __align__(8) uint64_t bar_load, bar_mma;
+    unsigned char* sB = smem;                           // b_bytes is a multiple of 1024
+    unsigned char* sA0 = smem + b_bytes;
+    __shared__ __align__(8) uint64_t full[TC_MAX_STAGES], empty[TC_MAX_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int tile = blockIdx.x;
+    __shared__ int abort_flag, issued_loads, issued_mma;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // this CTA's tiles: blockIdx.x + k * gridDim.x for k < my_n
+    const int my_n = ((int)blockIdx.x < n_tiles) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto tile_src = [&](int k) {
+        return reinterpret_cast<const unsigned char*>(basis_tiles) +
+               (size_t)((int)blockIdx.x + k * (int)gridDim.x) * a_bytes;
+    };
 
     if (tid == 0) {
-        mbar_init(&bar_load, 1);
-        mbar_init(&bar_mma, 1);
+        for (int q = 0; q < stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 32 * TC_EPI_WARPS);
+        }
+        abort_flag = 0;
+        issued_loads = issued_mma = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_base)), "r"(TC_N));
+                     ::"r"(smem_u32(&tmem_base)), "r"(2 * TC_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // the B operand: face b is row b of an N x Kp K-major matrix in core-matrix
+    // layout (8 rows x 8 BF16 per 128 B), coefficients rounded to nearest even;
+    // the writes are made visible to the tensor cores' (async proxy) reads
+    uint16_t* sB16 = reinterpret_cast<uint16_t*>(sB);
+    for (int idx = tid; idx < TC_N * Kp; idx += TC_THREADS) {
+        const int b = idx / Kp, k = idx % Kp;
+        const float v = (b < t.n && k < K) ? __ldg(&t.coef[b][k]) : 0.0f;
+        const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
+        sB16[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-    if (tid == 0) {
-        const uint32_t bar = smem_u32(&bar_load);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(a_bytes + b_bytes)
-                     : "memory");
-        const unsigned char* srcA = reinterpret_cast<const unsigned char*>(basis_tiles) + (size_t)tile * a_bytes;
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(sA)), "l"(srcA), "r"(a_bytes), "r"(bar)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(sB)), "l"(coef_tile), "r"(b_bytes), "r"(bar)
-                     : "memory");
-    }
-    // every thread waits for the operands (bounded); the outcome is made uniform
-    const bool go = __syncthreads_and(mbar_wait(&bar_load, 0) ? 1 : 0) != 0;
-
     const uint32_t tmem = tmem_base;
-    if (go && tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // K-major, no swizzle: core matrices adjacent in K are 128 B apart
-        // (leading offset), 8-row groups are (Kp / 8) * 128 B apart (stride offset)
-        const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
-        for (int ks = 0; ks < Kp / 16; ++ks) {
-            const uint64_t da = smem_desc(smem_u32(sA) + ks * 256, 128, sbo);
-            const uint64_t db = smem_desc(smem_u32(sB) + ks * 256, 128, sbo);
-            const uint32_t acc = ks > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                ::"r"(tmem), "l"(da), "l"(db), "r"(idesc<TC_N>()), "r"(acc)
-                : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     ::"r"(smem_u32(&bar_mma))
-                     : "memory");
-    }
-    const bool done = go && __syncthreads_and(mbar_wait(&bar_mma, 0) ? 1 : 0) != 0;
-    if (done) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = tile * TC_M + tid;
-        const float m = row < n3 ? mean[row] : 0.0f;
-        // warp w reads TMEM lanes 32w..32w+31 (its rows), 32 columns per load;
-        // every warp executes every load (the loads are warp-collective)
-#pragma unroll
-        for (int c0 = 0; c0 < TC_N; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (row < n3) {
-#pragma unroll
-                for (int b = 0; b < 32; ++b)
-                    if (c0 + b < t.n) t.out[c0 + b][row] = m + __uint_as_float(r[b]);
+    volatile int* abort_v = &abort_flag;
+
+    if (warp == TC_PRODUCER) {
+        if (lane == 0) {
+            int k = 0;
+            for (; k < my_n && !*abort_v; ++k) {
+                const int q = k % stages;
+                // the buffer's previous tile (k - stages) must have been consumed
+                if (k >= stages && !mbar_wait(&empty[q], (uint32_t)(k / stages - 1) & 1u)) {
+                    set_status(status, FR_STATUS_TIMEOUT);
+                    *abort_v = 1;
+                    break;
+                }
+                bulk_load(sA0 + (size_t)q * a_bytes, tile_src(k), a_bytes, &full[q]);
             }
+            issued_loads = k;
         }
-    } else if (tid == 0) {
-        // a wait gave up: report it, then give this CTA's own copies or MMAs a
-        // second bounded wait before its TMEM is freed and it exits
-        set_status(status, FR_STATUS_TIMEOUT);
-        if (!go) mbar_wait(&bar_load, 0);
-        else mbar_wait(&bar_mma, 0);
+    } else if (warp == TC_MMA) {
+        if (lane == 0) {
+            // K-major, no swizzle: core matrices adjacent in K are 128 B apart
+            // (leading offset), 8-row groups are (Kp / 8) * 128 B apart (stride offset)
+            const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
+            int k = 0;
+            {
+                for (; k < my_n && !*abort_v; ++k) {
+                    const int q = k % stages, b = k & 1;
+                    bool ok = mbar_wait(&full[q], (uint32_t)(k / stages) & 1u);
+                    // accumulator b is free once the epilogue has read tile k - 2
+                    if (ok && k >= 2) ok = mbar_wait(&tempty[b], (uint32_t)((k >> 1) - 1) & 1u);
+                    if (!ok) {
+                        set_status(status, FR_STATUS_TIMEOUT);
+                        *abort_v = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned char* sA = sA0 + (size_t)q * a_bytes;
+                    const uint32_t acc_addr = tmem + (uint32_t)(b * TC_N);
+                    for (int ks = 0; ks < Kp / 16; ++ks) {
+                        const uint64_t da = smem_desc(smem_u32(sA) + ks * 256, 128, sbo);
+                        const uint64_t db = smem_desc(smem_u32(sB) + ks * 256, 128, sbo);
+                        const uint32_t acc = ks > 0 ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                            ::"r"(acc_addr), "l"(da), "l"(db), "r"(idesc<TC_N>()), "r"(acc)
+                            : "memory");
+                    }
+                    mma_commit(&empty[q]);          // the buffer may be refilled
+                    mma_commit(&tfull[b]);          // the accumulator may be read
+                }
+            }
+            issued_mma = k;
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (its rows of the tile),
+        // 32 columns per load; every warp executes every load (warp-collective)
+        for (int k = 0; k < my_n; ++k) {
+            const int b = k & 1;
+            // a bounded wait that also gives up as soon as another role has
+            const uint32_t a = smem_u32(&tfull[b]);
+            bool ok = false;
+            for (unsigned it = 0; it < SPIN_LIMIT && !ok; ++it) {
+                uint32_t done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(a), "r"((uint32_t)(k >> 1) & 1u)
+                    : "memory");
+                ok = done != 0;
+                if (!ok && *abort_v) break;
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0 && !*abort_v) {
+                    set_status(status, FR_STATUS_TIMEOUT);
+                    *abort_v = 1;
+                }
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = ((int)blockIdx.x + k * (int)gridDim.x) * TC_M + tid;
+            const float m = row < n3 ? __ldg(&mean[row]) : 0.0f;
+#pragma unroll
+            for (int c0 = 0; c0 < TC_N; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * TC_N + c0), r);
+                if (row < n3) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < t.n) t.out[c0 + j][row] = m + __uint_as_float(r[j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[b]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && abort_flag) {
+        // a wait gave up: give the last copy into every buffer and the last
+        // MMAs of both accumulators a second bounded wait before the TMEM is
+        // freed and the shared memory released
+        bool drained = true;
+        for (int q = 0; q < stages; ++q) {
+            const int last = issued_loads - 1 - ((issued_loads - 1 - q) % stages + stages) % stages;
+            if (last >= 0 && last % stages == q) drained &= mbar_wait(&full[q], (uint32_t)(last / stages) & 1u);
+        }
+        for (int b = 0; b < 2; ++b) {
+            const int last = issued_mma - 1 - (((issued_mma - 1 - b) % 2) + 2) % 2;
+            if (last >= 0 && (last & 1) == b) drained &= mbar_wait(&tfull[b], (uint32_t)(last >> 1) & 1u);
+        }
+        if (!drained) set_status(status, FR_STATUS_TIMEOUT_UNSAFE);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N));
     }
 }
 
@@ -184,43 +302,65 @@ __global__ void k_wait_probe(unsigned limit, int* status) {
     if (!ok && threadIdx.x == 0) set_status(status, FR_STATUS_TIMEOUT);
 }
 
-FR_D uint16_t bf16_rne(float f) {
-    uint32_t u = __float_as_uint(f);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
 
-// Gather the batch's coefficients into the B-operand tile: face b is row b of
-// an N x Kp K-major matrix in core-matrix layout (8 rows x 8 BF16 per 128 B).
-__global__ void k_coef_tile(LinearTable t, int K, int Kp, int TC_N, uint16_t* tile) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= TC_N * Kp) return;
-    const int b = idx / Kp, k = idx % Kp;
-    const float v = (b < t.n && k < K) ? t.coef[b][k] : 0.0f;
-    const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
-    tile[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v);
+}  // namespace
+
+int morph_tc_stages(int Kp) {
+    const int a_bytes = TC_M * Kp * 2;
+    const int st = TC_STAGE_BYTES / a_bytes;
+    return st < 2 ? 2 : (st > TC_MAX_STAGES ? TC_MAX_STAGES : st);
+}
+int morph_tc_smem_bytes(int Kp) { return TC_N_MAX * Kp * 2 + morph_tc_stages(Kp) * TC_M * Kp * 2; }
+
+namespace {
+
+// Persistent grid: as many CTAs per SM as its shared memory, its TMEM (512
+// columns, two N-column accumulators per CTA) and its threads allow, with the
+// shared-memory carveout at its maximum (the kernel uses no L1 data cache to
+// speak of).  Queried once per host thread, device, MMA width and ring size.
+template <int N>
+int morph_tc_grid(int n_tiles, int smem) {
+    thread_local int cached_smem = -1, cached_dev = -1, per_sm = 1, sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cached_smem != smem || cached_dev != dev) {
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncSetAttribute(k_morph_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_morph_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k_morph_tc<N>);
+        const int per_cta = smem + (int)fa.sharedSizeBytes + 1024;     // + the per-CTA reservation
+        per_sm = smem_sm / per_cta;
+        per_sm = per_sm < 512 / (2 * N) ? per_sm : 512 / (2 * N);
+        per_sm = per_sm < 2048 / TC_THREADS ? per_sm : 2048 / TC_THREADS;
+        if (per_sm < 1) per_sm = 1;
+        cached_smem = smem;
+        cached_dev = dev;
+    }
+    const int g = (sms > 0 ? sms : 1) * per_sm;
+    return n_tiles < g ? n_tiles : g;
 }
 
 }  // namespace
 
-int morph_tc_smem_bytes(int Kp) { return TC_M * Kp * 2 + TC_N_MAX * Kp * 2; }
-int morph_tc_coef_tile_elems(int Kp) { return TC_N_MAX * Kp; }
-
-void launch_linear_tc(const uint16_t* tiles, int Kp, int K, uint16_t* coef_tile, const float* mean, int rows,
-                      const LinearTable& t, int* status, cudaStream_t st) {
+void launch_linear_tc(const uint16_t* tiles, int Kp, int K, const float* mean, int rows, const LinearTable& t,
+                      int* status, cudaStream_t st) {
     if (t.n <= 0 || rows <= 0 || t.n > TC_N_MAX) return;
     const int N = t.n <= 32 ? 32 : 64;           // MMA width: the batch padded to 32 or 64 faces
-    k_coef_tile<<<(N * Kp + 255) / 256, 256, 0, st>>>(t, K, Kp, N, coef_tile);
     const int n_tiles = (rows + TC_M - 1) / TC_M;
-    const int smem = TC_M * Kp * 2 + N * Kp * 2;
+    const int stages = morph_tc_stages(Kp);
+    const int smem = N * Kp * 2 + stages * TC_M * Kp * 2;
     if (N == 32) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_morph_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_morph_tc<32><<<n_tiles, TC_THREADS, smem, st>>>(tiles, Kp, coef_tile, mean, rows, t, status);
+        const int g = morph_tc_grid<32>(n_tiles, smem);
+        k_morph_tc<32><<<g, TC_THREADS, smem, st>>>(tiles, K, Kp, mean, rows, n_tiles, stages, t, status);
     } else {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_morph_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_morph_tc<64><<<n_tiles, TC_THREADS, smem, st>>>(tiles, Kp, coef_tile, mean, rows, t, status);
+        const int g = morph_tc_grid<64>(n_tiles, smem);
+        k_morph_tc<64><<<g, TC_THREADS, smem, st>>>(tiles, K, Kp, mean, rows, n_tiles, stages, t, status);
     }
-    fr_count_launches(2);
+    fr_count_launches(1);
 }
 
 void launch_wait_probe(unsigned limit, int* status, cudaStream_t st) {

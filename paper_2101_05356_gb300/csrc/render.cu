@@ -46,7 +46,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float SHADOW_EPS = 1e-4f;     // shadow segment trimmed to (eps, 1 - eps)
 
 struct WarpQueue {
-    float4 job[64][2];                  // (y.xyz, z.x) (z.y, z.z, skip, owner | light << 8 | distant << 16)
+    float4 job[64][2];                  // (y.xyz, z.x) (z.y, z.z, skip slot, owner | light << 8 | distant << 16)
     unsigned long long vis[32];
 };
 
@@ -77,6 +77,7 @@ struct SampleState {
     bool lit;          // shaded: the hit triangle faces the camera (and, with the view
                        // cutoff flag, n_s . o > 0); otherwise it reflects nothing
     int tri;
+    int slot;          // the hit triangle's leaf slot (skipped by its shadow rays)
     float b1, b2;
     float3 d;          // camera ray direction (not normalised)
     float3 y, ns, o;
@@ -92,12 +93,28 @@ struct SampleState {
 // record).
 constexpr int REC_TRACE = -2;
 
-template <bool CAN_TRACE = true>
+// The material fetch of a shading state (bilinear taps of the diffuse,
+// specular and roughness textures at the hit's uv).
+FR_D void sample_material(const DevScene& S, const DevParams& P, SampleState& ss) {
+    if (!ss.hit) return;
+    ss.tap = make_tap(S.M, ss.uv.x, ss.uv.y);
+    ss.m.c = f3(tap_fetch(P.diffuse, 3, 0, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.diffuse, 3, 1, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.diffuse, 3, 2, ss.tap, S.M, nullptr, nullptr));
+    ss.m.s = f3(tap_fetch(P.specular, 3, 0, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.specular, 3, 1, ss.tap, S.M, nullptr, nullptr),
+                tap_fetch(P.specular, 3, 2, ss.tap, S.M, nullptr, nullptr));
+    ss.m.r = tap_fetch(P.roughness, 1, 0, ss.tap, S.M, nullptr, nullptr);
+}
+
+// MATERIAL = false leaves the material to a later sample_material call (the
+// forward fetches it after the shadow traversal, so it is not live across it).
+template <bool CAN_TRACE = true, bool MATERIAL = true>
 FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
                         Stack st, SampleState& ss, RayStats& rs, int rec = REC_TRACE) {
     ss.hit = false;
     ss.lit = false;
-    ss.tri = -1;
+    ss.tri = ss.slot = -1;
     if (!active) return;
     const float f = __ldg(P.focal);
     ss.d = f3((sx - 0.5f * S.W) / f, -(sy - 0.5f * S.H) / f, -1.0f);
@@ -106,6 +123,7 @@ FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, floa
     if (h.tri < 0) return;
     ss.hit = true;
     ss.tri = h.tri;
+    ss.slot = h.slot;
     ss.b1 = h.b1;
     ss.b2 = h.b2;
     const int4 fc = __ldg(&S.faces[h.tri]);
@@ -122,14 +140,7 @@ FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, floa
              (!(S.flags & FR_FLAG_VIEW_CUTOFF_D) || dot(ss.ns, ss.o) > 0.0f);
     const float2 t0 = __ldg(&S.uv[fc.x]), t1 = __ldg(&S.uv[fc.y]), t2 = __ldg(&S.uv[fc.z]);
     ss.uv = make_float2(b0 * t0.x + h.b1 * t1.x + h.b2 * t2.x, b0 * t0.y + h.b1 * t1.y + h.b2 * t2.y);
-    ss.tap = make_tap(S.M, ss.uv.x, ss.uv.y);
-    ss.m.c = f3(tap_fetch(P.diffuse, 3, 0, ss.tap, S.M, nullptr, nullptr),
-                tap_fetch(P.diffuse, 3, 1, ss.tap, S.M, nullptr, nullptr),
-                tap_fetch(P.diffuse, 3, 2, ss.tap, S.M, nullptr, nullptr));
-    ss.m.s = f3(tap_fetch(P.specular, 3, 0, ss.tap, S.M, nullptr, nullptr),
-                tap_fetch(P.specular, 3, 1, ss.tap, S.M, nullptr, nullptr),
-                tap_fetch(P.specular, 3, 2, ss.tap, S.M, nullptr, nullptr));
-    ss.m.r = tap_fetch(P.roughness, 1, 0, ss.tap, S.M, nullptr, nullptr);
+    if (MATERIAL) sample_material(S, P, ss);
 }
 
 // Light-sample dims of a sampler, cached per Philox block (warp-uniform).
@@ -200,7 +211,7 @@ FR_D uint64_t shadow_mask(const DevScene& S, const SampleState& ss, const Sample
         if (need) {
             const int slot = (head + count + __popc(ballot & ((1u << lane) - 1u))) & 63;
             q.job[slot][0] = make_float4(ss.y.x, ss.y.y, ss.y.z, z.x);
-            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.tri),
+            q.job[slot][1] = make_float4(z.y, z.z, __int_as_float(ss.slot),
                                          __int_as_float(lane | ((j - j0) << 8) | ((int)distant << 16)));
         }
         count += __popc(ballot);
@@ -333,14 +344,15 @@ template <bool ENV>
 FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
                         const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t* vis,
                         RayStats& rs) {
-    primary_state(S, P, active, sx, sy, stk, ss, rs);
-    float3 Lo = f3(0.0f, 0.0f, 0.0f);
+    // visibility first, then the material and the radiance: the material is
+    // not live across the shadow traversal
+    primary_state<true, false>(S, P, active, sx, sy, stk, ss, rs);
     vis[0] = vis[1] = 0ull;
-    for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) {          // lights in chunks of 64 (warp-uniform)
-        const uint64_t v = shadow_mask<ENV>(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
-        vis[j0 >> 6] = v;
-        Lo += radiance_from<ENV>(S, P, ss, v, smp, dim0, j0);
-    }
+    for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64)            // lights in chunks of 64 (warp-uniform)
+        vis[j0 >> 6] = shadow_mask<ENV>(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
+    sample_material(S, P, ss);
+    float3 Lo = f3(0.0f, 0.0f, 0.0f);
+    for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) Lo += radiance_from<ENV>(S, P, ss, vis[j0 >> 6], smp, dim0, j0);
     return Lo;
 }
 
@@ -382,20 +394,46 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
                                   smp, 2, sh, my_stack(sh), ss, vis, rs);
     flush_stats(S.counters + 0, rs);
     if (valid && tri_rec) tri_rec[q] = ss.tri;
-    if (valid && mask_rec) mask_rec[q] = vis[0];
+    if (valid && mask_rec) {
+        mask_rec[2 * q] = vis[0];
+        mask_rec[2 * q + 1] = vis[1];
+    }
     if (valid && it.rec_tri) {
         it.rec_tri[q] = ss.tri;
         reinterpret_cast<ulonglong2*>(it.rec_vis)[q] = make_ulonglong2(vis[0], vis[1]);
     }
+    // per-pixel mean: lanes of one pixel summed in a fixed tree order; above
+    // 32 spp the warps of one pixel (within this block) add their sums in warp
+    // order, and at 256 spp the two blocks of a pixel add their partials onto
+    // the zeroed image (two addends onto zero: exact in either order), so the
+    // image does not depend on scheduling
     const int width = S.spp < 32 ? S.spp : 32;
     const float rx = group_sum(Lo.x, width), ry = group_sum(Lo.y, width), rz = group_sum(Lo.z, width);
     const float inv = 1.0f / (float)S.spp;
-    if (valid && (s % width) == 0) {
-        float* px = image + 3 * (size_t)pixel;
-        if (S.spp <= 32) {
+    if (S.spp <= 32) {
+        if (valid && (s % width) == 0) {
+            float* px = image + 3 * (size_t)pixel;
             px[0] = rx * inv; px[1] = ry * inv; px[2] = rz * inv;
-        } else {
-            atomicAdd(&px[0], rx * inv); atomicAdd(&px[1], ry * inv); atomicAdd(&px[2], rz * inv);
+        }
+    } else {                                            // block-uniform (one item per block)
+        __shared__ float wsum[RT_WARPS][3];
+        const int warp = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            wsum[warp][0] = rx; wsum[warp][1] = ry; wsum[warp][2] = rz;
+        }
+        __syncthreads();
+        const int wpp = min(S.spp >> 5, RT_WARPS);     // warps of this pixel in this block
+        if (valid && (threadIdx.x & (32 * wpp - 1)) == 0) {
+            float a = 0.0f, b = 0.0f, c = 0.0f;
+            for (int k = warp; k < warp + wpp; ++k) {
+                a += wsum[k][0]; b += wsum[k][1]; c += wsum[k][2];
+            }
+            float* px = image + 3 * (size_t)pixel;
+            if (S.spp <= RT_THREADS) {
+                px[0] = a * inv; px[1] = b * inv; px[2] = c * inv;
+            } else {
+                atomicAdd(&px[0], a * inv); atomicAdd(&px[1], b * inv); atomicAdd(&px[2], c * inv);
+            }
         }
     }
 }
@@ -481,8 +519,8 @@ FR_D void shadow_edge_env(const DevScene& S, const DevParams& P, const LightDev&
     float3 wp = wv + m * SHADOW_EPS, wm = wv - m * SHADOW_EPS;
     wp = wp * (1.0f / length(wp));
     wm = wm * (1.0f / length(wm));
-    const bool vp = !trace_any(S, ray_setup(ss.y, wp), SHADOW_EPS, INFINITY, ss.tri, st, rs);
-    const bool vm = !trace_any(S, ray_setup(ss.y, wm), SHADOW_EPS, INFINITY, ss.tri, st, rs);
+    const bool vp = !trace_any(S, ray_setup(ss.y, wp), SHADOW_EPS, INFINITY, ss.slot, st, rs);
+    const bool vm = !trace_any(S, ray_setup(ss.y, wm), SHADOW_EPS, INFINITY, ss.slot, st, rs);
     const float dV = (float)vp - (float)vm;
     if (dV == 0.0f) return;
     const float3 Le = env_radiance(P, row * L.env + col);
@@ -538,8 +576,8 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     if (!(tl > 0.0f)) return;
     const float3 m = cross(L.n, tan) * (1.0f / tl);
     const float3 zp = z + m * SHADOW_EPS, zm = z - m * SHADOW_EPS;
-    const bool vp = !trace_any(S, ray_setup(ss.y, zp - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st, rs);
-    const bool vm = !trace_any(S, ray_setup(ss.y, zm - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.tri, st, rs);
+    const bool vp = !trace_any(S, ray_setup(ss.y, zp - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.slot, st, rs);
+    const bool vm = !trace_any(S, ray_setup(ss.y, zm - ss.y), SHADOW_EPS, 1.0f - SHADOW_EPS, ss.slot, st, rs);
     const float dV = (float)vp - (float)vm;
     if (dV == 0.0f) return;
     const float3 I = intensity(S, P, j);

@@ -98,7 +98,7 @@ struct fr_server {
     CtxInfo info;
     int device = 0;
     cudaStream_t stream = nullptr;
-    float* light_scale = nullptr;                       // [N_L] d^2 / a (device, shared)
+    float* light_da = nullptr;                          // [d (N_L) | a (N_L)] of the lights (device, shared)
     std::chrono::steady_clock::time_point t0;
 
     std::mutex mu;
@@ -264,7 +264,7 @@ struct fr_server {
                                     LR_LIGHT, step);
             li.w_prior = W1;
             li.w_box = W_BOX;
-            if (r.stage_geo) li.aux2 = r.X(P_STAGE); else li.aux = light_scale;
+            li.aux2 = r.stage_geo ? r.X(P_STAGE) : light_da;     // the kernel forms d^2 / a
             out.push_back(li);
             if (r.stage_geo) {
                 fr_opt_group o = group(r.X(P_STAGE), r.G(P_STAGE), r.M(P_STAGE), r.V(P_STAGE), 4 * info.NL,
@@ -578,10 +578,10 @@ fr_status fr_server_create(fr_server** out, fr_ctx* ctx, const fr_server_config*
     if (cfg->eval_spp != 0 && (!pow2(cfg->eval_spp) || cfg->eval_spp > I.spp)) return FR_EINVAL;
     if (cudaGetDevice(&s->device) != cudaSuccess) return FR_ECUDA;
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return FR_ECUDA;
-    if (cudaMalloc(&s->light_scale, sizeof(float) * std::max(I.NL, 1)) != cudaSuccess ||
-        cudaMemcpy(s->light_scale, I.light_scale.data(), sizeof(float) * I.NL, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMalloc(&s->light_da, sizeof(float) * std::max(2 * I.NL, 1)) != cudaSuccess ||
+        cudaMemcpy(s->light_da, I.light_da.data(), sizeof(float) * 2 * I.NL, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
-        if (s->light_scale) cudaFree(s->light_scale);
+        if (s->light_da) cudaFree(s->light_da);
         cudaStreamDestroy(s->stream);
         return FR_ECUDA;
     }
@@ -735,7 +735,7 @@ void fr_server_destroy(fr_server* s) {
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->stream);
     for (auto& r : s->all) s->release(*r);
-    cudaFree(s->light_scale);
+    cudaFree(s->light_da);
     cudaStreamDestroy(s->stream);
     delete s;
 }

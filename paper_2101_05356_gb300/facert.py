@@ -506,7 +506,7 @@ class Renderer:
         n = s.width * s.height * s.spp
         img = self.image_buffer()
         tri = t.empty(n, dtype=t.int32, device="cuda")
-        mask = t.empty(n, dtype=t.int64, device="cuda")
+        mask = t.empty((n, 2), dtype=t.int64, device="cuda")   # lights 0..63, 64..127
         fr_debug_records(self.ctx, dparams, img, tri, mask, iteration, face_id)
         return img, tri, mask
 

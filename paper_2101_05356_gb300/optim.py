@@ -20,6 +20,8 @@ from __future__ import annotations
 
 import dataclasses
 
+import numpy as np
+
 from . import facert
 
 ALPHA1 = 1.0             # weight of E_land in E_d (Sec. 5)
@@ -58,7 +60,8 @@ class FaceState:
         self.v = {n: torch.zeros_like(v) for n, v in self.p.items()}
         self.ks = sc.n_shape
         self.tex = sc.tex_size
-        self.light_scale = torch.as_tensor(sc.light_d ** 2 / sc.light_a, dtype=torch.float32).cuda()
+        # the lights' fixed d and a: the optimiser kernel forms the scales d^2 / a
+        self.light_da = torch.as_tensor(np.concatenate([sc.light_d, sc.light_a]), dtype=torch.float32).cuda()
         # environment-map texels are lights of scale 1 (Sec. 7); light_i is used by the area lights only
         self.area_lights = bool((sc.lights[:, 0] != facert.LIGHT_ENV).any())
         self.env_scale = (torch.ones(self.p["env"].numel() // 3, dtype=torch.float32, device="cuda")
@@ -177,7 +180,7 @@ class FaceState:
             sb = self.stage_block
             if self.area_lights:
                 out.append(facert.opt_group(p["light_i"], m["light_i"], v["light_i"], g["light_i"],
-                                            aux=None if sb else self.light_scale, aux2=sb["x"] if sb else None,
+                                            aux=None, aux2=sb["x"] if sb else self.light_da,
                                             kind=facert.GROUP_LIGHT, lr=LR["light"], w_prior=W["w1"],
                                             w_box=W["box"], step=step))
             if "env" in p:          # environment map (Sec. 7): each texel a light with the light prior

@@ -2,11 +2,17 @@
 
 The paper (Sec. 3.1-3.3, Sec. 5) works on real photographs, the Basel/AlbedoMM
 statistical face models and a landmark detector; none of those is available, so
-every input here is synthetic and seeded.  This module only *draws* inputs: a
-mean face mesh with its topology and UV layout, shape/expression bases, UV
-textures, light-stage emitter geometry, and parameter vectors.  It contains none
-of the method's arithmetic (no morph, pose, projection, shading or loss); the
-renderer under test and the FP64 oracle both consume exactly these arrays.
+every input here is synthetic and seeded.  This module draws inputs: a mean
+face mesh with its topology and UV layout, shape/expression bases, UV textures,
+light-stage emitter geometry, and parameter vectors.  It has no morph, pose,
+projection, shading, loss or gradient; the renderer under test and the FP64
+oracle both consume exactly these arrays.  One piece of the method's geometry
+does live here: `stage_records` places the emitters of a virtual light stage
+from its frame and (d, a, p) (Sec. 3.3), as the scene's fixed emitter records.
+When the parameters carry (d, a, p) the CUDA library rebuilds the lights from
+them itself and the oracle with its own code; neither side reads those records
+then, and the oracle's builder is pinned by the closed-form shadowed irradiance
+of a moving emitter, not by agreement with this function.
 
 Units: model space is roughly a unit head centred at the origin, looking down +z
 (towards the camera); the camera sits at T = (0, 0, 4.5) looking down -z, so the

@@ -114,3 +114,35 @@ def mixed_box(width=32, height=32, spp=4, tex=8, seed=0):
     pr.env = env.astype(np.float32)
     pr.light_i = np.concatenate([pr.light_i, np.ones((rec.shape[0], 3), np.float32)])
     return sc, pr
+
+
+def many_box(width=32, height=32, spp=4, tex=8, seed=0, n_lights=80):
+    """The shadow box lit by n_lights small quads (a 10 x 8 grid between the
+    occluder and the camera, each facing the floor), so that every light casts
+    its own shadow of the occluder on the floor, those past the 64th too."""
+    import dataclasses
+    sc, pr = shadow_box(width, height, spp, tex, seed)
+    rng = np.random.default_rng(seed + 5)
+    lights = []
+    for k in range(n_lights):
+        i, j = k % 10, k // 10
+        c = [-1.1 + 0.245 * i + rng.uniform(-0.03, 0.03), -0.9 + 0.26 * j + rng.uniform(-0.03, 0.03),
+             -2.2 + rng.uniform(-0.2, 0.2)]
+        lights.append(quad_light(c, [0.0, 0.14, 0.0], [0.14, 0.0, 0.0]))   # e1 x e2 towards -z
+    lights = np.asarray(lights, np.float32)
+    sc = dataclasses.replace(sc, lights=lights, light_d=np.ones(n_lights, np.float32),
+                             light_a=np.ones(n_lights, np.float32))
+    pr.light_i = rng.uniform(0.3, 1.2, size=(n_lights, 3)).astype(np.float32)
+    return sc, pr
+
+
+def ico_box(width=32, height=32, spp=4, tex=8, seed=0):
+    """The shadow box under the paper's icosahedral light stage (20 triangular
+    lights around a centre below the floor, d = 2.7, a = 0.25): the lights
+    above the occluder cast its shadow on the floor."""
+    import dataclasses
+    sc, pr = shadow_box(width, height, spp, tex, seed)
+    rec, d, a = synth.polyhedral_stage("ico", d=2.7, a=0.25, centre=(0.0, 0.0, -4.5))
+    sc = dataclasses.replace(sc, lights=rec, light_d=d, light_a=a)
+    pr.light_i = np.random.default_rng(seed + 6).uniform(0.5, 1.5, size=(rec.shape[0], 3)).astype(np.float32)
+    return sc, pr

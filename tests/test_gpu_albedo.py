@@ -102,7 +102,7 @@ def test_loss_gradient_reaches_beta_and_gamma():
     q.specular = dp["specular"].cpu().numpy()
     img, tri, mask = r.records(dp, iteration=1)
     oi, ot, om = oracle.render(sc, q, records=True, iteration=1)
-    ok = ((tri.cpu().numpy() == ot) & (mask.cpu().numpy().view(np.uint64) == om)).reshape(-1, sc.spp).all(axis=1)
+    ok = ((tri.cpu().numpy() == ot) & (mask.cpu().numpy().view(np.uint64) == om).all(axis=1)).reshape(-1, sc.spp).all(axis=1)
     adj = np.random.default_rng(6).uniform(0.2, 1.0, (sc.height, sc.width, 3)) * ok.reshape(sc.height, sc.width, 1)
     g = r.backward(dp, torch.as_tensor(adj, dtype=torch.float32).cuda(), iteration=1)
     gb = torch.zeros(16, device="cuda")

@@ -11,6 +11,8 @@ import pytest
 import oracle
 from paper_2101_05356_gb300 import synth
 
+from tests.parity import compare_grads
+
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
@@ -45,10 +47,10 @@ def test_records_and_radiance_at_sampled_pixels(c2):
                                     rng.choice(sc.width * sc.height, n_any, replace=False)])).astype(np.int32)
     oi, ot, om = oracle.render(sc, pr, iteration=7, pixels=pix, records=True)
     ot = ot.reshape(-1, sc.spp)[pix]
-    om = om.reshape(-1, sc.spp)[pix]
+    om = om.reshape(-1, sc.spp, 2)[pix]
     gt = tri_np[pix]
-    gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp)[pix]
-    agree = (gt == ot) & (gm == om)
+    gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp, 2)[pix]
+    agree = (gt == ot) & (gm == om).all(axis=2)        # both visibility words (lights 0..63, 64..127)
     assert np.mean(~agree) <= 1e-4, int(np.sum(~agree))
     ok = agree.all(axis=1)
     g = img.cpu().numpy().reshape(-1, 3)[pix]
@@ -75,17 +77,13 @@ def test_gradients_of_a_sparse_adjoint_image(c2):
     pix = np.random.default_rng(1).choice(on_face, 12, replace=False)
     # keep pixels whose records agree with the oracle
     _, ot, om = oracle.render(sc, pr, iteration=3, pixels=pix.astype(np.int32), records=True)
-    gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp)
+    gm = mask.cpu().numpy().view(np.uint64).reshape(-1, sc.spp, 2)
     keep = [p for p in pix if np.array_equal(tri_np[p], ot.reshape(-1, sc.spp)[p])
-            and np.array_equal(gm[p], om.reshape(-1, sc.spp)[p])]
+            and np.array_equal(gm[p], om.reshape(-1, sc.spp, 2)[p])]
     assert len(keep) >= 10
     adj = np.zeros((sc.height, sc.width, 3))
     adj.reshape(-1, 3)[keep] = np.random.default_rng(2).uniform(0.3, 1.0, (len(keep), 3))
     adj32 = adj.astype(np.float32)
     gg = r.backward(dp, torch.as_tensor(adj32).cuda(), iteration=3)
     go = oracle.grad(sc, pr, adj32.astype(np.float64), iteration=3, edge_spp=1)
-    for k in ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness"):
-        a = gg[k].cpu().numpy().astype(np.float64).ravel()
-        b = np.asarray(go[k]).ravel()
-        nb = np.linalg.norm(b)
-        assert np.linalg.norm(a - b) <= 2e-3 * max(nb, 1e-9), (k, float(np.linalg.norm(a - b) / max(nb, 1e-30)))
+    compare_grads(gg, go, ("coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "roughness"), 1e-3)

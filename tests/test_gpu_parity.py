@@ -4,13 +4,16 @@ Both sides draw the same Philox samples, so the comparison is per sample:
 hit triangles and shadow masks must agree except for rare FP32/FP64 flips at
 edges; radiance and gradients are compared where the records agree.
 Tolerances: radiance 1e-4 relative (per pixel, floor 1e-2 x mean), gradients
-1e-3 relative per parameter group (norm), as fixed for the FP32 path."""
+1e-3 relative per parameter group (norm) and per element on the entries of
+at least 1e-2 of the group's largest, as fixed for the FP32 path, for every
+term (interior, primary-visibility and shadow-boundary) and the fused step."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2101_05356_gb300 import synth
 from tests import scenes
+from tests.parity import compare_grads
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +44,10 @@ SCENES = {
     # its 80-face sphere variant
     "ico": lambda: (synth.make_scene("tiny", light_stage="ico"), None),
     "sphere80": lambda: (synth.make_scene("c1", light_stage="sphere80"), None),
+    # scenes where shadow boundaries are sampled often: the shadow box under 80
+    # small quads (the second visibility word in use) and under the icosahedral stage
+    "many_box": lambda: scenes.many_box(),
+    "ico_box": lambda: scenes.ico_box(),
 }
 
 
@@ -126,12 +133,12 @@ def _records_and_image(sc, pr, r, dp, iteration=0):
     oi, ot, om = oracle.render(sc, pr, records=True, iteration=iteration)
     tri_g = tri.cpu().numpy()
     mask_g = mask.cpu().numpy().view(np.uint64)
-    agree = (tri_g == ot) & (mask_g == om)
+    agree = (tri_g == ot) & (mask_g == om).all(axis=1)     # both visibility words
     px_ok = agree.reshape(-1, sc.spp).all(axis=1).reshape(sc.height, sc.width)
     return img.cpu().numpy(), oi, agree, px_ok
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "ragged", "box", "many", "ico", "sphere80"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "ragged", "box", "many", "ico", "sphere80", "many_box", "ico_box"])
 def test_forward_parity(name):
     sc, pr = _scene(name)
     r = _renderer(sc)
@@ -169,7 +176,7 @@ def test_forward_parity_modes(flags):
     dp = r.device_params(pr)
     img, tri, mask = r.records(dp)
     oi, ot, om = oracle.render(sc, pr, records=True, flags=flags)
-    agree = (tri.cpu().numpy() == ot) & (mask.cpu().numpy().view(np.uint64) == om)
+    agree = (tri.cpu().numpy() == ot) & (mask.cpu().numpy().view(np.uint64) == om).all(axis=1)
     px_ok = agree.reshape(-1, sc.spp).all(axis=1).reshape(sc.height, sc.width)
     g = img.cpu().numpy()
     err = np.abs(g - oi) / np.maximum(np.abs(oi), 1e-2 * oi.mean())
@@ -221,17 +228,10 @@ GROUPS = ["coef", "rot", "trans", "focal", "light_i", "diffuse", "specular", "ro
 
 
 def _compare_grads(gg, go, groups, rtol=1e-3):
-    for k in groups:
-        a = gg[k].cpu().numpy().astype(np.float64).ravel()
-        b = np.asarray(go[k], np.float64).ravel()
-        nb = np.linalg.norm(b)
-        if nb == 0.0:
-            assert np.linalg.norm(a) <= 1e-6, k
-            continue
-        assert np.linalg.norm(a - b) <= rtol * nb, (k, np.linalg.norm(a - b) / nb)
+    compare_grads(gg, go, groups, rtol)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "box", "many", "ico"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "box", "many", "ico", "many_box"])
 def test_interior_gradient_parity(name):
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)
@@ -252,11 +252,14 @@ def test_primary_edge_gradient_parity(name):
     adj = _masked_adjoint(sc, pr, r, dp)
     gg = r.backward(dp, torch.as_tensor(adj, dtype=torch.float32).cuda())
     go = oracle.grad(sc, pr, adj.astype(np.float32).astype(np.float64), terms=oracle.TERM_PRIMARY, edge_spp=2)
-    _compare_grads(gg, go, ["coef", "rot", "trans", "focal"], rtol=2e-3)
+    _compare_grads(gg, go, ["coef", "rot", "trans", "focal"])
 
 
-@pytest.mark.parametrize("name", ["tiny", "box", "many", "ico"])
+@pytest.mark.parametrize("name", ["box", "many_box", "ico_box"])
 def test_shadow_edge_gradient_parity(name):
+    """The shadow-boundary term on scenes whose occluder casts shadows from every
+    light (on convex meshes and on the small faces it is exactly zero: no
+    boundary sample lands on an emitter)."""
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)
     r = _renderer(sc, flags=facert.FLAG_NO_INTERIOR | facert.FLAG_NO_PRIMARY_EDGE)
@@ -264,7 +267,8 @@ def test_shadow_edge_gradient_parity(name):
     adj = _masked_adjoint(sc, pr, r, dp)
     gg = r.backward(dp, torch.as_tensor(adj, dtype=torch.float32).cuda())
     go = oracle.grad(sc, pr, adj.astype(np.float32).astype(np.float64), terms=oracle.TERM_SHADOW)
-    _compare_grads(gg, go, ["coef", "rot", "trans", "focal"], rtol=2e-3)
+    assert np.linalg.norm(go["coef"]) > 0.0
+    _compare_grads(gg, go, ["coef", "rot", "trans", "focal"])
 
 
 def test_full_gradient_and_render_step_c1():
@@ -278,10 +282,7 @@ def test_full_gradient_and_render_step_c1():
     lo, _, ado = oracle.loss(img.cpu().numpy().astype(np.float64), tgt)
     assert loss.item() == pytest.approx(lo, rel=1e-6)
     go = oracle.grad(sc, pr, ado, iteration=2)
-    # records may disagree on a handful of samples; require tight agreement
-    # on the groups and report the largest relative deviation
-    for k in GROUPS:
-        a = gg[k].cpu().numpy().astype(np.float64).ravel()
-        b = np.asarray(go[k]).ravel()
-        assert np.linalg.norm(a - b) <= 5e-3 * max(np.linalg.norm(b), 1e-9), k
-    assert np.allclose(img.cpu().numpy(), oi, rtol=1e-3, atol=1e-3 * oi.mean())
+    # every term at once, on the unmasked loss adjoint: the same bars as the terms alone
+    _compare_grads(gg, go, GROUPS)
+    err = np.abs(img.cpu().numpy() - oi) / np.maximum(np.abs(oi), 1e-2 * oi.mean())
+    assert np.max(err) <= 1e-4, float(np.max(err))

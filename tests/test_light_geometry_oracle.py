@@ -37,8 +37,11 @@ def _stage_light(stage_row, d, a, p0, p1):
 
 
 def test_stage_lights_match_the_generator():
-    """The oracle's stage lights at the generator's parameters are the
-    generator's records (same triangles, area a d^2 F, scale d^2 / a)."""
+    """Consistency, not a pin: the oracle's stage lights at the generator's
+    parameters are the generator's records (same triangles, area a d^2 F,
+    scale d^2 / a), and both equal the definition written out here.  The
+    oracle's builder is pinned by the closed-form shadowed irradiance of a
+    moving emitter below."""
     sc = synth.make_scene("tiny", light_stage="ico")
     for j in range(sc.n_lights):
         t0, t1, t2 = _stage_light(sc.stage[j], 3.0, 0.25, 1 / 3, 1 / 3)

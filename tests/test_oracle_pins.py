@@ -529,7 +529,7 @@ def _fd_fixed_samples(sc, pr, adj, field, index, h):
     b0 = oracle.render(sc, base, records=True)
     up = oracle.render(sc, shifted(+1), records=True)
     dn = oracle.render(sc, shifted(-1), records=True)
-    same = (b0[1] == up[1]) & (b0[1] == dn[1]) & (b0[2] == up[2]) & (b0[2] == dn[2])
+    same = (b0[1] == up[1]) & (b0[1] == dn[1]) & (b0[2] == up[2]).all(axis=1) & (b0[2] == dn[2]).all(axis=1)
     keep = same.reshape(-1, sc.spp).all(axis=1).reshape(sc.height, sc.width)
     a = adj * keep[..., None]
     fd = (np.sum(a * up[0]) - np.sum(a * dn[0])) / (2 * step)
