@@ -54,8 +54,9 @@ typedef int32_t fr_status;
 #define FR_FLAG_NO_SHADOW_EDGE  64u   /* gradient: skip the shadow boundary term */
 #define FR_FLAG_MORPH_BF16     128u   /* morph as one BF16 tensor-core GEMM over the batch (FP32
                                          accumulate, FP32 mean); context-wide, read by every call */
-#define FR_FLAG_RECOMPUTE      256u   /* fused steps re-trace the adjoint's primary and shadow rays
-                                         even when the hit records fit (see fr_render) */
+#define FR_FLAG_RECOMPUTE      256u   /* the adjoint re-traces its camera and shadow rays inside the
+                                         adjoint kernel, neither reading the forward's hit records nor
+                                         recomputing them in tiles (see fr_render) */
 #define FR_FLAG_VIEW_CUTOFF   1024u   /* zero every contribution where the shading normal faces away from
                                          the camera (n_s . o <= 0), the diffuse term included; by default
                                          only the specular lobe needs n_s . o > 0.  This cutoff is a
@@ -66,11 +67,14 @@ typedef int32_t fr_status;
                                          fr_set_mesh; for deformations far from the mean face.
                                          Context-wide, read from the context's flags */
 
-/* Per-slot budget for the hit records of a fused step (bytes): a context whose
- * width * height * spp * 20 bytes fit keeps, per slot, the forward's hit
- * triangle and two 64-bit light-visibility words per camera sample, and the
- * adjoint of the same step reads them instead of re-tracing.  Larger images
- * recompute them (the adjoint re-traces with the same Philox counters). */
+/* Per-slot budget for hit records (bytes): the hit triangle and two 64-bit
+ * light-visibility words per camera sample (20 bytes).  When the context's
+ * width * height * spp records fit, a fused step's forward writes them and its
+ * adjoint reads them instead of re-tracing.  Larger images are split into equal
+ * tiles that fit (whole pixels, whole 128-sample blocks): for each tile the
+ * adjoint recomputes the records with a visibility-only forward pass (the same
+ * Philox counters, no shading) and then reads them.  The gradient is the same
+ * either way. */
 #define FR_RECORDS_BUDGET (256u << 20)
 
 /* emitter types in light records */
@@ -261,8 +265,10 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
 /* One full step of the hot path: fr_forward, fr_loss against `target`, and (if
  * g != NULL) fr_backward with the loss adjoint.  loss is a device double.
  * Within the step the adjoint reuses the forward's per-sample hit records
- * (hit triangle and shadow visibility) when they fit FR_RECORDS_BUDGET and
- * FR_FLAG_RECOMPUTE is clear; the gradient is the same either way. */
+ * (hit triangle and shadow visibility) when they fit FR_RECORDS_BUDGET, else
+ * recomputes them tile by tile; with FR_FLAG_RECOMPUTE it re-traces every
+ * sample inside the adjoint kernel instead.  The gradient is the same either
+ * way. */
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);
@@ -293,6 +299,13 @@ fr_status fr_render_batch(fr_ctx* ctx, const fr_item* items, int32_t n, void* st
 /* Replace the FR_FLAG_* set of ctx for the following calls (e.g. drop the edge
  * terms when only textures are optimised).  Errors: FR_EINVAL. */
 fr_status fr_set_flags(fr_ctx* ctx, uint32_t flags);
+
+/* Test hook: recompute hit records in tiles of `samples` camera samples
+ * (rounded down to a multiple of max(128, spp), at most the slots' record
+ * buffer) instead of the buffer's full size, so that small images exercise
+ * the tiled adjoint; 0 restores the default.  Images whose records no longer
+ * fit one tile are then not recorded by the forward.  FR_EINVAL if samples < 0. */
+fr_status fr_debug_record_tile(fr_ctx* ctx, int64_t samples);
 
 /* Synchronise `stream`, read and clear the device status word.
  * Returns FR_OK, FR_EOVERFLOW or FR_ETIMEOUT (or FR_ECUDA).  FR_ETIMEOUT after a

@@ -45,9 +45,9 @@ struct Slot {
     LightDev* lights = nullptr;      // lights built from stage parameters [FR_MAX_LIGHTS]
     int* edge_perm = nullptr;        // primary-edge sample order [edge_cap]
     long edge_cap = 0;
-    int32_t* rec_tri = nullptr;      // fused-step hit records (null when over FR_RECORDS_BUDGET)
+    int32_t* rec_tri = nullptr;      // hit records: a whole image, or one tile of a larger one
     uint64_t* rec_vis = nullptr;
-    long rec_samples = 0;
+    long rec_cap = 0;                // camera samples the record buffer holds
 };
 
 // A linear model y = mean + basis * coef (shape morph, statistical albedo):
@@ -69,6 +69,7 @@ struct fr_ctx {
     int N = 0, T = 0, K = 0, NL = 0, E = 0, ld = 0;   // ld = shape.ld
     bool have_mesh = false, have_lights = false;
     bool poisoned = false;                     // a device wait gave up unsafely: refuse further work
+    long rec_tile = 0;                         // record tile in camera samples (0: the slots' capacity)
     std::string err;
     // mesh and lights (shared by all slots)
     LinearModel shape;                         // rows 3N
@@ -239,13 +240,35 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.tri_rec = a.tri_rec;
     it.mask_rec = a.mask_rec;
     if ((long)a.W * a.H * a.edge_spp <= sl.edge_cap) it.edge_perm = sl.edge_perm;
-    if (a.records && sl.rec_tri && !(a.flags & FR_FLAG_RECOMPUTE) && (long)a.W * a.H * a.spp <= sl.rec_samples) {
+    // hit records: a fused step's forward writes them when the whole image fits
+    // the buffer; otherwise the adjoint recomputes them tile by tile into it.
+    // FR_FLAG_RECOMPUTE keeps the adjoint re-tracing every sample instead.
+    if (sl.rec_tri && !(a.flags & FR_FLAG_RECOMPUTE)) {
         it.rec_tri = sl.rec_tri;
         it.rec_vis = sl.rec_vis;
+        it.rec_cap = c->rec_tile > 0 ? std::min(c->rec_tile, sl.rec_cap) : sl.rec_cap;
+        it.rec_full = a.records && (long)a.W * a.H * a.spp <= it.rec_cap ? 1 : 0;
     }
     it.iteration = a.iteration;
     it.face = a.face;
     return it;
+}
+
+// Blocks of a launch over camera samples [q0, q0 + cap) of each item, for the
+// items `take` accepts (the others get no blocks).
+template <class F>
+BlockMap tile_map(const fr_ctx* c, int n, long q0, long cap, F take) {
+    BlockMap m;
+    m.n = n;
+    int b = 0;
+    for (int k = 0; k < n; ++k) {
+        const DevScene& s = c->h_items[k].S;
+        m.block0[k] = b;
+        const long left = (long)s.W * s.H * s.spp - q0;
+        if (take(c->h_items[k]) && left > 0) b += (int)((std::min(left, cap) + 127) / 128);
+    }
+    m.block0[n] = b;
+    return m;
 }
 
 BlockMap map_of(const fr_ctx* c, int n, bool edges) {
@@ -273,10 +296,12 @@ fr_status upload(fr_ctx* c, int n, cudaStream_t st) {
 // out_b = mean + basis * coef_b for the n faces of `t`, on the tensor cores
 // when the context has FR_FLAG_MORPH_BF16, else in FP32
 void linear_forward(fr_ctx* c, const LinearModel& m, const LinearTable& t, cudaStream_t st) {
-    if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && m.K > 0)
-        launch_linear_tc(m.tiles, m.Kp, m.K, m.mean, m.rows, t, c->status, st);
-    else
+    if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && m.K > 0) {
+        const TcModel tm{m.tiles, m.Kp, m.K, m.mean, m.rows, t};
+        launch_linear_tc(&tm, 1, c->status, st);
+    } else {
         launch_linear(m.mean, m.basis, m.ld, m.rows, m.K, t, st);
+    }
 }
 
 void morph(fr_ctx* c, int n, cudaStream_t st) {
@@ -363,7 +388,7 @@ fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
         // sums are added onto zero (exact in either order)
         if (it.S.spp > 128) CK(c, cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)it.S.W * it.S.H, st));
     }
-    launch_forward(c->d_items, map_of(c, n, false), c->env_size > 0, st);
+    launch_forward(c->d_items, map_of(c, n, false), c->env_size > 0, 0, false, st);
     return FR_OK;
 }
 
@@ -377,11 +402,36 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     }
     if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, c->T, st);
     mark(c, 4, st);
-    bool all_recorded = true;
-    for (int k = 0; k < n; ++k) all_recorded &= c->h_items[k].rec_tri != nullptr;
-    bool any_stage = false;
-    for (int k = 0; k < n; ++k) any_stage |= c->h_items[k].S.stage != nullptr;
-    launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_recorded, any_stage, c->env_size > 0, st);
+    bool all_full = true, any_retrace = false, any_stage = false;
+    long cap = 0, n_tiles = 1;
+    for (int k = 0; k < n; ++k) {
+        const DevItem& it = c->h_items[k];
+        all_full &= it.rec_full != 0;
+        any_retrace |= it.rec_tri == nullptr;
+        any_stage |= it.S.stage != nullptr;
+        if (it.rec_tri) cap = it.rec_cap;
+    }
+    const bool env = c->env_size > 0;
+    if (all_full || any_retrace) {
+        // records of the whole image from this step's forward, or (some item
+        // asked for it) re-tracing in the adjoint itself
+        launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_full, any_stage, env, 0, st);
+    } else {
+        // recomputed records: per tile of `cap` camera samples, a records-only
+        // forward pass over the items whose forward did not record them, then
+        // the recorded adjoint over the same tile of every item
+        for (int k = 0; k < n; ++k) {
+            const DevScene& s = c->h_items[k].S;
+            n_tiles = std::max(n_tiles, ((long)s.W * s.H * s.spp + cap - 1) / cap);
+        }
+        for (long t = 0; t < n_tiles; ++t) {
+            const long q0 = t * cap;
+            launch_forward(c->d_items, tile_map(c, n, q0, cap, [](const DevItem& it) { return !it.rec_full; }), env,
+                           q0, true, st);
+            launch_adjoint(c->d_items, tile_map(c, n, q0, cap, [](const DevItem&) { return true; }), c->NL, true,
+                           any_stage, env, q0, st);
+        }
+    }
     mark(c, 5, st);
     long max_edge = 0;
     for (int k = 0; k < n; ++k) {
@@ -453,13 +503,16 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     // processing order of the primary-edge samples (the context's edge_spp, at least 1)
     sl.edge_cap = (long)c->cfg.width * c->cfg.height * std::max(c->cfg.edge_spp, 1);
     TRY(dalloc(c, &sl.edge_perm, (size_t)sl.edge_cap));
-    // hit records of a fused step: triangle + two visibility words per sample
+    // hit records (triangle + two visibility words per camera sample): the whole
+    // image when it fits FR_RECORDS_BUDGET, else equal tiles of it that do, in
+    // whole pixels and whole 128-thread blocks (a multiple of max(128, spp))
     const long samples = (long)c->cfg.width * c->cfg.height * c->cfg.spp;
-    if (samples * (long)(sizeof(int32_t) + 2 * sizeof(uint64_t)) <= (long)FR_RECORDS_BUDGET) {
-        TRY(dalloc(c, &sl.rec_tri, (size_t)samples));
-        TRY(dalloc(c, &sl.rec_vis, 2 * (size_t)samples));
-        sl.rec_samples = samples;
-    }
+    const long per = (long)(sizeof(int32_t) + 2 * sizeof(uint64_t));
+    const long unit = std::max(128, c->cfg.spp);
+    const long n_rec = (samples * per + (long)FR_RECORDS_BUDGET - 1) / (long)FR_RECORDS_BUDGET;
+    sl.rec_cap = ((samples + n_rec - 1) / n_rec + unit - 1) / unit * unit;
+    TRY(dalloc(c, &sl.rec_tri, (size_t)sl.rec_cap));
+    TRY(dalloc(c, &sl.rec_vis, 2 * (size_t)sl.rec_cap));
     return FR_OK;
 }
 
@@ -683,11 +736,12 @@ fr_status fr_albedo_morph(fr_ctx* c, int32_t n, const float* const* beta, const 
     if (n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch faces required");
     const float* const* coefs[2] = {beta, gamma};
     float* const* outs[2] = {diffuse, specular};
+    LinearTable tab[2];
     for (int q = 0; q < 2; ++q) {
         if (!outs[q]) continue;
         const LinearModel& m = c->albedo[q];
         if (m.K > 0 && !coefs[q]) return fail(c, FR_EINVAL, "null coefficient array");
-        LinearTable t;
+        LinearTable& t = tab[q];
         t.n = n;
         for (int k = 0; k < n; ++k) {
             if (!outs[q][k] || !aligned16(outs[q][k])) return fail(c, FR_EINVAL, "null or misaligned texture");
@@ -695,8 +749,20 @@ fr_status fr_albedo_morph(fr_ctx* c, int32_t n, const float* const* beta, const 
             t.coef[k] = m.K > 0 ? coefs[q][k] : nullptr;
             t.out[k] = outs[q][k];
         }
-        linear_forward(c, m, t, S_(stream));
     }
+    // on the tensor cores both albedos go in one launch; the FP32 path and
+    // models without columns (mean only) go one model at a time
+    TcModel tm[2];
+    int n_tc = 0;
+    for (int q = 0; q < 2; ++q) {
+        if (!outs[q]) continue;
+        const LinearModel& m = c->albedo[q];
+        if ((c->cfg.flags & FR_FLAG_MORPH_BF16) && m.K > 0)
+            tm[n_tc++] = TcModel{m.tiles, m.Kp, m.K, m.mean, m.rows, tab[q]};
+        else
+            linear_forward(c, m, tab[q], S_(stream));
+    }
+    if (n_tc > 0) launch_linear_tc(tm, n_tc, c->status, S_(stream));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -897,6 +963,17 @@ fr_status fr_debug_wait_timeout(fr_ctx* c, uint32_t polls, void* stream) {
     if (!c || polls < 1 || polls > (1u << 22)) return fail(c, FR_EINVAL, "1 <= polls <= 2^22");
     launch_wait_probe(polls, c->status, S_(stream));
     CK(c, cudaGetLastError());
+    return FR_OK;
+}
+
+fr_status fr_debug_record_tile(fr_ctx* c, int64_t samples) {
+    if (!c || samples < 0) return fail(c, FR_EINVAL, "bad argument");
+    if (samples == 0) {
+        c->rec_tile = 0;
+        return FR_OK;
+    }
+    const long unit = std::max(128, c->cfg.spp);
+    c->rec_tile = std::max(unit, (long)samples / unit * unit);
     return FR_OK;
 }
 

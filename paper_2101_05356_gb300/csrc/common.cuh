@@ -220,8 +220,10 @@ struct DevItem {
     const float* adj;       // image-space adjoint read by the ray kernels
     int32_t* tri_rec;
     uint64_t* mask_rec;
-    int32_t* rec_tri;       // fused-step hit records: forward writes, adjoint reads (null: re-trace)
-    uint64_t* rec_vis;      // [samples][2] visibility words, lights 0..63 and 64..127
+    int32_t* rec_tri;       // hit records [rec_cap] (null: the adjoint re-traces every sample)
+    uint64_t* rec_vis;      // [rec_cap][2] visibility words, lights 0..63 and 64..127
+    long rec_cap;           // camera samples the record buffer holds (a tile of the image)
+    int rec_full;           // this call's forward writes the records of the whole image (it fits)
     int* edge_perm;         // processing order of the primary-edge samples (null: index order)
     float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
     float *g_light_d, *g_light_a, *g_light_p;            // light stage geometry gradients (may be null)

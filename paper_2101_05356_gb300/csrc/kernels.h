@@ -43,11 +43,18 @@ void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const Li
                            cudaStream_t st);
 
 // morph_tc.cu: the same forward as one BF16 tensor-core GEMM over the batch
-// (tiles: the basis as [ceil(rows / 128)][128][Kp] BF16 operand tiles)
+// (tiles: the basis as [ceil(rows / 128)][128][Kp] BF16 operand tiles); one
+// launch takes up to two models (the diffuse and specular albedos)
+struct TcModel {
+    const uint16_t* tiles;
+    int Kp, K;
+    const float* mean;
+    int rows;
+    LinearTable t;
+};
 int morph_tc_smem_bytes(int Kp);
 void launch_wait_probe(unsigned limit, int* status, cudaStream_t st);
-void launch_linear_tc(const uint16_t* tiles, int Kp, int K, const float* mean, int rows, const LinearTable& t,
-                      int* status, cudaStream_t st);
+void launch_linear_tc(const TcModel* models, int n_models, int* status, cudaStream_t st);
 
 // landmark.cu: sparse landmark loss (one block; L <= 256)
 struct LandmarkArgs {
@@ -91,9 +98,12 @@ void launch_lbvh(const DevItem* items, int n, const int4* faces, int T, int* sta
 void launch_bvh_check(const DevItem* items, int T, int* out, cudaStream_t st);
 
 // render.cu
-void launch_forward(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st);
-void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage, bool env,
+// the ray kernels process camera samples [q0, q0 + count) of each item, count
+// from the block map; records_only: the adjoint's records of that tile only
+void launch_forward(const DevItem* items, const BlockMap& map, bool env, long q0, bool records_only,
                     cudaStream_t st);
+void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage, bool env,
+                    long q0, cudaStream_t st);
 void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st);
 void launch_edge_primary(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);

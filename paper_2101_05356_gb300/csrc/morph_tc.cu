@@ -117,23 +117,35 @@ FR_D void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// The models of one launch (up to two, e.g. the diffuse and specular
+// albedos): row tiles are numbered across them, model 0's first.
+struct TcLaunch {
+    int n;                       // models (1 or 2)
+    int tiles0;                  // row tiles of model 0 (model 1's follow)
+    const uint16_t* basis[2];    // operand tiles [ceil(rows / 128)][128][Kp]
+    const float* mean[2];
+    int K[2], Kp[2], rows[2];
+    LinearTable t[2];
+};
+
 template <int TC_N>
-__global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restrict__ basis_tiles, int K, int Kp,
-                                                         const float* __restrict__ mean, int n3, int n_tiles,
-                                                         int stages, LinearTable t, int* status) {
+__global__ void __launch_bounds__(TC_THREADS) k_morph_tc(TcLaunch L, int n_tiles, int stage_bytes, int stages,
+                                                         int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int a_bytes = TC_M * Kp * 2, b_bytes = TC_N * Kp * 2;
-    unsigned char* sB = smem;                           // b_bytes is a multiple of 1024
-    unsigned char* sA0 = smem + b_bytes;
+    // one B tile per model ([N][Kp] BF16, each a multiple of 1024 bytes), then
+    // the ring of stage_bytes buffers for the basis tiles
+    unsigned char* sB[2] = {smem, smem + TC_N * L.Kp[0] * 2};
+    unsigned char* sA0 = smem + TC_N * L.Kp[0] * 2 + (L.n > 1 ? TC_N * L.Kp[1] * 2 : 0);
     __shared__ __align__(8) uint64_t full[TC_MAX_STAGES], empty[TC_MAX_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, issued_loads, issued_mma;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // this CTA's tiles: blockIdx.x + k * gridDim.x for k < my_n
     const int my_n = ((int)blockIdx.x < n_tiles) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto tile_src = [&](int k) {
-        return reinterpret_cast<const unsigned char*>(basis_tiles) +
-               (size_t)((int)blockIdx.x + k * (int)gridDim.x) * a_bytes;
+    auto tile_of = [&](int k, int& model) {             // local tile index and model of tile k
+        const int g = (int)blockIdx.x + k * (int)gridDim.x;
+        model = g < L.tiles0 ? 0 : 1;
+        return model ? g - L.tiles0 : g;
     };
 
     if (tid == 0) {
@@ -154,15 +166,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restr
                      ::"r"(smem_u32(&tmem_base)), "r"(2 * TC_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // the B operand: face b is row b of an N x Kp K-major matrix in core-matrix
+    // the B operands: face b is row b of an N x Kp K-major matrix in core-matrix
     // layout (8 rows x 8 BF16 per 128 B), coefficients rounded to nearest even;
     // the writes are made visible to the tensor cores' (async proxy) reads
-    uint16_t* sB16 = reinterpret_cast<uint16_t*>(sB);
-    for (int idx = tid; idx < TC_N * Kp; idx += TC_THREADS) {
-        const int b = idx / Kp, k = idx % Kp;
-        const float v = (b < t.n && k < K) ? __ldg(&t.coef[b][k]) : 0.0f;
-        const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
-        sB16[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v);
+    for (int mdl = 0; mdl < L.n; ++mdl) {
+        uint16_t* sB16 = reinterpret_cast<uint16_t*>(sB[mdl]);
+        const int Kp = L.Kp[mdl], K = L.K[mdl];
+        const LinearTable& t = L.t[mdl];
+        for (int idx = tid; idx < TC_N * Kp; idx += TC_THREADS) {
+            const int b = idx / Kp, k = idx % Kp;
+            const float v = (b < t.n && k < K) ? __ldg(&t.coef[b][k]) : 0.0f;
+            const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
+            sB16[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v);
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -181,43 +197,49 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restr
                     *abort_v = 1;
                     break;
                 }
-                bulk_load(sA0 + (size_t)q * a_bytes, tile_src(k), a_bytes, &full[q]);
+                int mdl;
+                const int lt = tile_of(k, mdl);
+                const int a_bytes = TC_M * L.Kp[mdl] * 2;
+                bulk_load(sA0 + (size_t)q * stage_bytes,
+                          reinterpret_cast<const unsigned char*>(L.basis[mdl]) + (size_t)lt * a_bytes, a_bytes,
+                          &full[q]);
             }
             issued_loads = k;
         }
     } else if (warp == TC_MMA) {
         if (lane == 0) {
-            // K-major, no swizzle: core matrices adjacent in K are 128 B apart
-            // (leading offset), 8-row groups are (Kp / 8) * 128 B apart (stride offset)
-            const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
             int k = 0;
-            {
-                for (; k < my_n && !*abort_v; ++k) {
-                    const int q = k % stages, b = k & 1;
-                    bool ok = mbar_wait(&full[q], (uint32_t)(k / stages) & 1u);
-                    // accumulator b is free once the epilogue has read tile k - 2
-                    if (ok && k >= 2) ok = mbar_wait(&tempty[b], (uint32_t)((k >> 1) - 1) & 1u);
-                    if (!ok) {
-                        set_status(status, FR_STATUS_TIMEOUT);
-                        *abort_v = 1;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned char* sA = sA0 + (size_t)q * a_bytes;
-                    const uint32_t acc_addr = tmem + (uint32_t)(b * TC_N);
-                    for (int ks = 0; ks < Kp / 16; ++ks) {
-                        const uint64_t da = smem_desc(smem_u32(sA) + ks * 256, 128, sbo);
-                        const uint64_t db = smem_desc(smem_u32(sB) + ks * 256, 128, sbo);
-                        const uint32_t acc = ks > 0 ? 1u : 0u;
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                            ::"r"(acc_addr), "l"(da), "l"(db), "r"(idesc<TC_N>()), "r"(acc)
-                            : "memory");
-                    }
-                    mma_commit(&empty[q]);          // the buffer may be refilled
-                    mma_commit(&tfull[b]);          // the accumulator may be read
+            for (; k < my_n && !*abort_v; ++k) {
+                const int q = k % stages, b = k & 1;
+                bool ok = mbar_wait(&full[q], (uint32_t)(k / stages) & 1u);
+                // accumulator b is free once the epilogue has read tile k - 2
+                if (ok && k >= 2) ok = mbar_wait(&tempty[b], (uint32_t)((k >> 1) - 1) & 1u);
+                if (!ok) {
+                    set_status(status, FR_STATUS_TIMEOUT);
+                    *abort_v = 1;
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                int mdl;
+                tile_of(k, mdl);
+                const int Kp = L.Kp[mdl];
+                // K-major, no swizzle: core matrices adjacent in K are 128 B apart
+                // (leading offset), 8-row groups are (Kp / 8) * 128 B apart (stride offset)
+                const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
+                const unsigned char* sA = sA0 + (size_t)q * stage_bytes;
+                const uint32_t acc_addr = tmem + (uint32_t)(b * TC_N);
+                for (int ks = 0; ks < Kp / 16; ++ks) {
+                    const uint64_t da = smem_desc(smem_u32(sA) + ks * 256, 128, sbo);
+                    const uint64_t db = smem_desc(smem_u32(sB[mdl]) + ks * 256, 128, sbo);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                        ::"r"(acc_addr), "l"(da), "l"(db), "r"(idesc<TC_N>()), "r"(acc)
+                        : "memory");
+                }
+                mma_commit(&empty[q]);          // the buffer may be refilled
+                mma_commit(&tfull[b]);          // the accumulator may be read
             }
             issued_mma = k;
         }
@@ -248,8 +270,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(const uint16_t* __restr
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = ((int)blockIdx.x + k * (int)gridDim.x) * TC_M + tid;
-            const float m = row < n3 ? __ldg(&mean[row]) : 0.0f;
+            int mdl;
+            const int row = tile_of(k, mdl) * TC_M + tid;
+            const int n3 = L.rows[mdl];
+            const LinearTable& t = L.t[mdl];
+            const float m = row < n3 ? __ldg(&L.mean[mdl][row]) : 0.0f;
 #pragma unroll
             for (int c0 = 0; c0 < TC_N; c0 += 32) {
                 uint32_t r[32];
@@ -310,7 +335,7 @@ int morph_tc_stages(int Kp) {
     const int st = TC_STAGE_BYTES / a_bytes;
     return st < 2 ? 2 : (st > TC_MAX_STAGES ? TC_MAX_STAGES : st);
 }
-int morph_tc_smem_bytes(int Kp) { return TC_N_MAX * Kp * 2 + morph_tc_stages(Kp) * TC_M * Kp * 2; }
+int morph_tc_smem_bytes(int Kp) { return 2 * TC_N_MAX * Kp * 2 + morph_tc_stages(Kp) * TC_M * Kp * 2; }
 
 namespace {
 
@@ -346,19 +371,32 @@ int morph_tc_grid(int n_tiles, int smem) {
 
 }  // namespace
 
-void launch_linear_tc(const uint16_t* tiles, int Kp, int K, const float* mean, int rows, const LinearTable& t,
-                      int* status, cudaStream_t st) {
-    if (t.n <= 0 || rows <= 0 || t.n > TC_N_MAX) return;
-    const int N = t.n <= 32 ? 32 : 64;           // MMA width: the batch padded to 32 or 64 faces
-    const int n_tiles = (rows + TC_M - 1) / TC_M;
-    const int stages = morph_tc_stages(Kp);
-    const int smem = N * Kp * 2 + stages * TC_M * Kp * 2;
+void launch_linear_tc(const TcModel* models, int n_models, int* status, cudaStream_t st) {
+    TcLaunch L{};
+    int n_faces = 0, max_kp = 0, n_tiles = 0;
+    for (int q = 0; q < n_models && L.n < 2; ++q) {
+        const TcModel& m = models[q];
+        if (m.t.n <= 0 || m.rows <= 0 || m.t.n > TC_N_MAX || m.K <= 0) continue;
+        const int i = L.n++;
+        L.basis[i] = m.tiles; L.mean[i] = m.mean; L.K[i] = m.K; L.Kp[i] = m.Kp; L.rows[i] = m.rows; L.t[i] = m.t;
+        const int nt = (m.rows + TC_M - 1) / TC_M;
+        if (i == 0) L.tiles0 = nt;
+        n_tiles += nt;
+        n_faces = n_faces > m.t.n ? n_faces : m.t.n;
+        max_kp = max_kp > m.Kp ? max_kp : m.Kp;
+    }
+    if (L.n == 0) return;
+    const int N = n_faces <= 32 ? 32 : 64;       // MMA width: the batch padded to 32 or 64 faces
+    const int stages = morph_tc_stages(max_kp);
+    const int stage_bytes = TC_M * max_kp * 2;
+    int smem = stages * stage_bytes;
+    for (int i = 0; i < L.n; ++i) smem += N * L.Kp[i] * 2;
     if (N == 32) {
         const int g = morph_tc_grid<32>(n_tiles, smem);
-        k_morph_tc<32><<<g, TC_THREADS, smem, st>>>(tiles, K, Kp, mean, rows, n_tiles, stages, t, status);
+        k_morph_tc<32><<<g, TC_THREADS, smem, st>>>(L, n_tiles, stage_bytes, stages, status);
     } else {
         const int g = morph_tc_grid<64>(n_tiles, smem);
-        k_morph_tc<64><<<g, TC_THREADS, smem, st>>>(tiles, K, Kp, mean, rows, n_tiles, stages, t, status);
+        k_morph_tc<64><<<g, TC_THREADS, smem, st>>>(L, n_tiles, stage_bytes, stages, status);
     }
     fr_count_launches(1);
 }

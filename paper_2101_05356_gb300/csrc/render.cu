@@ -339,21 +339,37 @@ FR_D float3 radiance_from(const DevScene& S, const DevParams& P, const SampleSta
     return Lo;
 }
 
-// Full warp-cooperative radiance evaluation at screen point (sx, sy).
+// Warp-cooperative visibility at screen point (sx, sy): the camera ray's hit
+// (without the material) and both shadow-visibility words.
 template <bool ENV>
-FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
+FR_D void visibility_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
                         const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t* vis,
                         RayStats& rs) {
-    // visibility first, then the material and the radiance: the material is
-    // not live across the shadow traversal
     primary_state<true, false>(S, P, active, sx, sy, stk, ss, rs);
     vis[0] = vis[1] = 0ull;
     for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64)            // lights in chunks of 64 (warp-uniform)
         vis[j0 >> 6] = shadow_mask<ENV>(S, ss, smp, dim0, sh.wq[threadIdx.x >> 5], stk, rs, j0);
+}
+
+// Radiance of a sample whose visibility is known: the material, then the lights.
+template <bool ENV>
+FR_D float3 shade_visible(const DevScene& S, const DevParams& P, const Sampler& smp, int dim0, SampleState& ss,
+                          const uint64_t* vis) {
     sample_material(S, P, ss);
     float3 Lo = f3(0.0f, 0.0f, 0.0f);
     for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) Lo += radiance_from<ENV>(S, P, ss, vis[j0 >> 6], smp, dim0, j0);
     return Lo;
+}
+
+// Full warp-cooperative radiance evaluation at screen point (sx, sy):
+// visibility first, then the material and the radiance, so that the material
+// is not live across the shadow traversal.
+template <bool ENV>
+FR_D float3 radiance_at(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
+                        const Sampler& smp, int dim0, RtShared& sh, Stack stk, SampleState& ss, uint64_t* vis,
+                        RayStats& rs) {
+    visibility_at<ENV>(S, P, active, sx, sy, smp, dim0, sh, stk, ss, vis, rs);
+    return shade_visible<ENV>(S, P, smp, dim0, ss, vis);
 }
 
 FR_D float warp_sum(float v) {
@@ -368,8 +384,14 @@ FR_D float group_sum(float v, int width) {
     return v;
 }
 
+// Camera samples [q0, q0 + the block map's count) of each item.  records_only
+// (a tile of the adjoint's recomputed records): trace the camera ray and the
+// shadow rays, write the hit records of the tile at q - q0, and shade
+// nothing.  Otherwise: the forward render, writing the records of the whole
+// image when it.rec_full (q0 = 0).
 template <bool ENV>
-__global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const DevItem* items, BlockMap map) {
+__global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const DevItem* items, BlockMap map,
+                                                                           long q0, int records_only) {
     __shared__ RtShared sh;
     FR_STACK_DECL
     const int item = item_of_block(map);
@@ -381,7 +403,8 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
     uint64_t* mask_rec = it.mask_rec;
     const uint32_t iteration = it.iteration, face = it.face;
     const long total = (long)S.W * S.H * S.spp;
-    const long q = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
+    const long ql = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
+    const long q = q0 + ql;
     const bool valid = q < total;
     const int pixel = valid ? (int)(q / S.spp) : 0;
     const int s = valid ? (int)(q % S.spp) : 0;
@@ -390,15 +413,24 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
     SampleState ss;
     uint64_t vis[2];
     RayStats rs;
-    const float3 Lo = radiance_at<ENV>(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y,
-                                  smp, 2, sh, my_stack(sh), ss, vis, rs);
+    visibility_at<ENV>(S, P, valid, (float)(pixel % S.W) + jit.x, (float)(pixel / S.W) + jit.y, smp, 2, sh,
+                       my_stack(sh), ss, vis, rs);
+    if (records_only) {                                 // launch-uniform
+        flush_stats(S.counters + 3, rs);                // the adjoint's rays
+        if (valid) {
+            it.rec_tri[ql] = ss.tri;
+            reinterpret_cast<ulonglong2*>(it.rec_vis)[ql] = make_ulonglong2(vis[0], vis[1]);
+        }
+        return;
+    }
+    const float3 Lo = shade_visible<ENV>(S, P, smp, 2, ss, vis);
     flush_stats(S.counters + 0, rs);
     if (valid && tri_rec) tri_rec[q] = ss.tri;
     if (valid && mask_rec) {
         mask_rec[2 * q] = vis[0];
         mask_rec[2 * q + 1] = vis[1];
     }
-    if (valid && it.rec_tri) {
+    if (valid && it.rec_full) {
         it.rec_tri[q] = ss.tri;
         reinterpret_cast<ulonglong2*>(it.rec_vis)[q] = make_ulonglong2(vis[0], vis[1]);
     }
@@ -604,12 +636,15 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
     }
 }
 
-// RECORDED: every item of the launch carries the forward's hit records, so the
-// camera and shadow traversals are compiled out (a smaller kernel); otherwise
-// each item re-traces unless it has records.
+// Camera samples [q0, q0 + the block map's count) of each item.  RECORDED:
+// every item of the launch has the hit records of these samples in its record
+// buffer at q - q0 (written by the forward of the same step, or by the
+// records-only forward pass of this tile), so the camera and shadow
+// traversals are compiled out (a smaller kernel); otherwise each item re-traces
+// unless its forward recorded the whole image (q0 = 0).
 template <bool RECORDED, bool ENV>
 __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS : FR_ADJ_MIN_BLOCKS)
-    k_adjoint(const DevItem* items, BlockMap map) {
+    k_adjoint(const DevItem* items, BlockMap map, long q0) {
     __shared__ RtShared sh;
     FR_STACK_DECL
     const int item = item_of_block(map);
@@ -624,7 +659,8 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
     const int n_acc = 1 + 3 * S.NL + (stage ? 4 * S.NL : 0);
     block_acc_init(n_acc);
     const long total = (long)S.W * S.H * S.spp;
-    const long qi = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;
+    const long ql = (long)(blockIdx.x - map.block0[item]) * RT_THREADS + threadIdx.x;   // record index
+    const long qi = q0 + ql;
     bool valid = qi < total;
     const int pixel = valid ? (int)(qi / S.spp) : 0;
     const int s = valid ? (int)(qi % S.spp) : 0;
@@ -642,9 +678,22 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
     RayStats rs;
     // the forward of a fused step may have recorded this sample's hit and
     // shadow visibility; otherwise both are re-traced with the same counters
-    const bool recorded = RECORDED || it.rec_tri != nullptr;   // block-uniform
-    primary_state<!RECORDED>(S, P, valid, sx, sy, my_stack(sh), ss, rs,
-                  recorded ? (valid ? it.rec_tri[qi] : -1) : REC_TRACE);
+    const bool recorded = RECORDED || it.rec_full;             // block-uniform
+    primary_state<!RECORDED, false>(S, P, valid, sx, sy, my_stack(sh), ss, rs,
+                                    recorded ? (valid ? it.rec_tri[ql] : -1) : REC_TRACE);
+    // the visibility words of every 64-light chunk (recorded, or re-traced with
+    // the forward's counters) before the material fetch, so that the material
+    // is not live across the shadow traversal
+    uint64_t vis_w[2] = {0ull, 0ull};
+    if (!(S.flags & FR_FLAG_FLAT_D)) {
+        for (int j0 = 0; j0 < S.NL; j0 += 64) {                // warp-uniform
+            if (recorded)
+                vis_w[j0 >> 6] = valid ? it.rec_vis[2 * ql + (j0 >> 6)] : 0ull;
+            else
+                vis_w[j0 >> 6] = shadow_mask<ENV>(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j0);
+        }
+    }
+    sample_material(S, P, ss);
     const bool interior = !(S.flags & FR_FLAG_NO_INTERIOR_D);
     ShadeAdj g;
     g.n = g.l = g.o = g.c = g.s = f3(0.0f, 0.0f, 0.0f);
@@ -656,12 +705,7 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         DimCache dc;
         uint64_t vis = 0ull;
         for (int j = 0; j < S.NL; ++j) {                       // warp-uniform loop
-            if ((j & 63) == 0) {                               // lights in chunks of 64
-                if (recorded)
-                    vis = valid ? it.rec_vis[2 * qi + (j >> 6)] : 0ull;
-                else
-                    vis = shadow_mask<ENV>(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j);
-            }
+            if ((j & 63) == 0) vis = vis_w[j >> 6];            // lights in chunks of 64
             if (ENV && S.lights[j].type == FR_LIGHT_ENV_D) {    // warp-uniform
                 // a light at infinity: the radiance gradient goes to the sampled texel
                 float3 ge = f3(0.0f, 0.0f, 0.0f);
@@ -1259,32 +1303,33 @@ void set_carveout() {
 
 // env: some item of the launch has environment blocks (the kernels compiled
 // with their code); otherwise the light-stage-only instantiation runs.
-void launch_forward(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st) {
+void launch_forward(const DevItem* items, const BlockMap& map, bool env, long q0, bool records_only,
+                    cudaStream_t st) {
     if (map_blocks(map) == 0) return;
     if (env) {
         set_carveout<true>();
-        k_forward<true><<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+        k_forward<true><<<map_blocks(map), RT_THREADS, 0, st>>>(items, map, q0, records_only ? 1 : 0);
     } else {
         set_carveout<false>();
-        k_forward<false><<<map_blocks(map), RT_THREADS, 0, st>>>(items, map);
+        k_forward<false><<<map_blocks(map), RT_THREADS, 0, st>>>(items, map, q0, records_only ? 1 : 0);
     }
     fr_count_launches(1);
 }
 
 void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_recorded, bool any_stage, bool env,
-                    cudaStream_t st) {
+                    long q0, cudaStream_t st) {
     if (map_blocks(map) == 0) return;
     const size_t acc_bytes = sizeof(float) * RT_WARPS * (1 + (any_stage ? 7 : 3) * (size_t)NL);
     if (env) {
         if (all_recorded)
-            k_adjoint<true, true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+            k_adjoint<true, true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map, q0);
         else
-            k_adjoint<false, true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+            k_adjoint<false, true><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map, q0);
     } else {
         if (all_recorded)
-            k_adjoint<true, false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+            k_adjoint<true, false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map, q0);
         else
-            k_adjoint<false, false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map);
+            k_adjoint<false, false><<<map_blocks(map), RT_THREADS, acc_bytes, st>>>(items, map, q0);
     }
     fr_count_launches(1);
 }

@@ -165,6 +165,7 @@ def lib():
         L.fr_kernel_launches.argtypes = []
         L.fr_kernel_launches.restype = ctypes.c_uint64
         L.fr_set_flags.argtypes = [_vp, ctypes.c_uint32]
+        L.fr_debug_record_tile.argtypes = [_vp, ctypes.c_int64]
         L.fr_debug_morph.argtypes = [_vp, _vp, ctypes.c_int32, _vp, _vp]
         L.fr_render_batch.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
         L.fr_adam.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -421,6 +422,12 @@ def fr_loss_noalloc(height, width, image, target, loss, adj_image=None, blurred=
     if code != FR_OK:
         msg = lib().fr_loss_noalloc_error()
         raise FacertError(code, msg.decode() if msg else "")
+
+
+def fr_debug_record_tile(ctx, samples):
+    """Test hook: recompute the adjoint's hit records in tiles of `samples`
+    camera samples (0: the record buffer's full size)."""
+    check(lib().fr_debug_record_tile(ctx, int(samples)), ctx)
 
 
 def fr_kernel_launches():
