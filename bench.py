@@ -56,13 +56,14 @@ OPS_PER_TRI = 30
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
-# null); the capture command is in profiles/k_forward_adjoint_c2_full.md.
-TRAFFIC = {"k_forward": {"bytes": 31684352 + 28991488,
-                         "sources_sha256": "5ab1fcf3a8b917d4239b1c443af1ee8851a16a00baee432f1097b8a678c26928"}}
+# null); the capture command is recorded beside the kernel's profile summary.
+TRAFFIC = {"k_forward": {"bytes": 26555392 + 17296896,
+                         "sources_sha256": "6abde9074a2c3fc90f3edec191dcb1a6c7a66901309a7464006483b8d878690b"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
-# Issue-slot use (smsp__issue_active) of a kernel from the ncu --set full capture
-# summarised in profiles/, valid while its sources hash to `sources_sha256`.
-ISSUE = {}
+# Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
+# valid while its sources hash to `sources_sha256`.
+ISSUE = {"k_forward": {"frac": 0.6976,
+                       "sources_sha256": "6abde9074a2c3fc90f3edec191dcb1a6c7a66901309a7464006483b8d878690b"}}
 FP32_LANES_PER_SM = 128
 
 

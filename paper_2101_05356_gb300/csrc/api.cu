@@ -58,7 +58,7 @@ struct LinearModel {
     float* mean = nullptr;
     float* basis = nullptr;
     uint16_t* tiles = nullptr;           // [ceil(rows / 128)][128][Kp] BF16, no-swizzle K-major core matrices
-    double* part = nullptr;              // [FR_MAX_BATCH][K][linear_adj_chunks(rows)]
+    double* part = nullptr;              // [linear_adj_chunks(rows)][FR_MAX_BATCH][K] (chunk-major)
 };
 
 }  // namespace

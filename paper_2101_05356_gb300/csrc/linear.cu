@@ -15,7 +15,6 @@
 namespace {
 
 constexpr int LIN_THREADS = 256;
-constexpr int ADJ_ROWS4 = 1024;          // float4 rows summed by one adjoint block
 
 // Faces per pass over the basis: a launch reads each basis float4 once per
 // group of LIN_GROUP faces (blockIdx.y is the group), so a batch streams the
@@ -71,79 +70,151 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(const float* __restrict_
     }
 }
 
-// Adjoint, first pass: block (chunk, k-group, face group) sums
-// basis[k][i] * g_b[i] over its chunk of rows for KG consecutive k and the G
-// faces b of its group into part[b][k][chunk].  A thread sums its few rows of
-// the chunk (ADJ_ROWS4 / LIN_THREADS float4 rows, 16 products) and the warp
-// its 32 threads in FP32; the block, chunk and batch sums are FP64 (the FP64
-// pipe is narrow, so it only sees one value per warp).  Each basis float4 is read once per face
-// group and each gradient float4 once per k-group.
-template <int G, int KG>
-__global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_part(const float* __restrict__ basis, int ld, int rows,
-                                                                 int K, LinearAdjTable t, double* part,
-                                                                 int n_chunks) {
-    __shared__ double w[LIN_THREADS / 32][KG][G];
-    const int chunk = blockIdx.x, k0 = blockIdx.y * KG, b0 = blockIdx.z * G;
-    const int nb_ = min(G, t.n - b0), nk = min(KG, K - k0);
-    float acc[KG][G];
-#pragma unroll
-    for (int q = 0; q < KG; ++q)
-#pragma unroll
-        for (int b = 0; b < G; ++b) acc[q][b] = 0.0f;
-    const int lo = chunk * ADJ_ROWS4, hi = std::min(lo + ADJ_ROWS4, (rows + 3) / 4);
-    for (int i = lo + (int)threadIdx.x; i < hi; i += LIN_THREADS) {
-        const int e = 4 * i;
-        float4 gg[G];
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-            gg[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (b >= nb_ || !t.g_coef[b0 + b]) continue;
+// Adjoint, first pass.  Block (chunk of ADJ_ROWS4 float4 rows, face group of
+// G, k-slice z) stages the chunk's gradients g_b of its faces in shared memory
+// once; its warp w takes the column groups z * 8 + w, then every 8 * gridDim.z
+// after, of KG consecutive k, and sums basis[k][i] * g_b[i] over the chunk (a
+// lane its ADJ_ROWS4 / 32 rows in order, the warp its lanes by a butterfly, all
+// FP32) into part[chunk][b][k] (FP64; chunk-major, so that the second pass
+// reads it coalesced).  Each basis float4 is read once per face group and each
+// gradient float4 once per k-slice.  The order of every (face, k) sum depends
+// only on the chunking, not on G, KG or the k-split, so the one-face kernel
+// below, which keeps that order, gives a face's gradient bitwise the same
+// alone and in a batch.
+constexpr int ADJ_ROWS4 = 256;
+template <int G, int KG, int MIN_BLOCKS>
+__global__ void __launch_bounds__(LIN_THREADS, MIN_BLOCKS) k_linear_adj_part(const float* __restrict__ basis, int ld,
+                                                                   int rows, int K, LinearAdjTable t, double* part) {
+    __shared__ float4 gs[G][ADJ_ROWS4];
+    const int chunk = blockIdx.x, b0 = blockIdx.y * G;
+    const int nb_ = min(G, t.n - b0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rows4 = (rows + 3) / 4, lo = chunk * ADJ_ROWS4;
+    for (int q = threadIdx.x; q < G * ADJ_ROWS4; q += LIN_THREADS) {
+        const int b = q / ADJ_ROWS4, r = q % ADJ_ROWS4, i = lo + r, e = 4 * i;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (b < nb_ && t.g_coef[b0 + b] && i < rows4) {
             const float* g = t.g[b0 + b];
             if (e + 4 <= rows) {
-                gg[b] = *reinterpret_cast<const float4*>(g + e);
+                v = *reinterpret_cast<const float4*>(g + e);
             } else {                                   // ragged tail
-                gg[b].x = g[e];
-                if (e + 1 < rows) gg[b].y = g[e + 1];
-                if (e + 2 < rows) gg[b].z = g[e + 2];
+                v.x = g[e];
+                if (e + 1 < rows) v.y = g[e + 1];
+                if (e + 2 < rows) v.z = g[e + 2];
             }
         }
-#pragma unroll
-        for (int q = 0; q < KG; ++q) {
-            if (q >= nk) break;
-            const float4 bb = __ldg(reinterpret_cast<const float4*>(basis + (size_t)(k0 + q) * ld) + i);
-#pragma unroll
-            for (int b = 0; b < G; ++b)
-                acc[q][b] += bb.x * gg[b].x + bb.y * gg[b].y + bb.z * gg[b].z + bb.w * gg[b].w;
-        }
+        gs[b][r] = v;
     }
-    // warp sums in FP32 (32 partials of a few products each, in a fixed
-    // order); FP64 from the block sum on
-#pragma unroll
-    for (int q = 0; q < KG; ++q)
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-            float v = acc[q][b];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5][q][b] = (double)v;
-        }
     __syncthreads();
-    const int q = threadIdx.x / G, b = threadIdx.x % G;
-    if (q < nk && b < nb_) {
-        double s = 0.0;
-        for (int r = 0; r < LIN_THREADS / 32; ++r) s += w[r][q][b];
-        part[((size_t)(b0 + b) * K + k0 + q) * n_chunks + chunk] = s;
+    const int n_kg = (K + KG - 1) / KG, warps = LIN_THREADS / 32;
+    for (int kg = blockIdx.z * warps + warp; kg < n_kg; kg += warps * gridDim.z) {
+        const int k0 = kg * KG, nk = min(KG, K - k0);
+        float acc[KG][G];
+#pragma unroll
+        for (int q = 0; q < KG; ++q)
+#pragma unroll
+            for (int b = 0; b < G; ++b) acc[q][b] = 0.0f;
+#pragma unroll 1
+        for (int r = lane; r < ADJ_ROWS4; r += 32) {
+            const int i = lo + r;
+            if (i >= rows4) break;
+            float4 bb[KG];
+#pragma unroll
+            for (int q = 0; q < KG; ++q)
+                bb[q] = q < nk ? __ldg(reinterpret_cast<const float4*>(basis + (size_t)(k0 + q) * ld) + i)
+                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                const float4 gg = gs[b][r];
+#pragma unroll
+                for (int q = 0; q < KG; ++q)
+                    acc[q][b] += bb[q].x * gg.x + bb[q].y * gg.y + bb[q].z * gg.z + bb[q].w * gg.w;
+            }
+        }
+        // the butterfly leaves the same sum, bitwise, on every lane
+#pragma unroll
+        for (int q = 0; q < KG; ++q)
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                float v = acc[q][b];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == ((q * G + b) & 31) && q < nk && b < nb_)
+                    part[((size_t)chunk * t.n + b0 + b) * K + k0 + q] = (double)v;
+            }
     }
 }
 
-// Adjoint, second pass: g_coef_b[k] += sum of the chunk partials in chunk
-// order (a fixed order, so the result does not depend on scheduling).
-__global__ void k_linear_adj_finish(const double* __restrict__ part, int K, int n_chunks, LinearAdjTable t) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
-    if (k >= K || !t.g_coef[b]) return;
-    const double* p = part + ((size_t)b * K + k) * n_chunks;
+// Adjoint of one face, first pass: warp (chunk, column group of KG) sums
+// basis[k][i] * g[i] over the chunk exactly as the batched kernel above does
+// for each of its faces (the same rows per lane, the same expressions, the
+// same butterfly), so the partials are bitwise those of the face in a batch.
+// The gradient is read from global memory (consecutive warps share a chunk, so
+// it is an L1 hit after the first), which leaves no shared staging to balance
+// over the block's warps.
+template <int KG>
+__global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_one(const float* __restrict__ basis, int ld, int rows,
+                                                                int K, LinearAdjTable t, double* part, int n_chunks) {
+    const int lane = threadIdx.x & 31;
+    const int n_kg = (K + KG - 1) / KG;
+    const long item = (long)blockIdx.x * (LIN_THREADS / 32) + (threadIdx.x >> 5);
+    if (item >= (long)n_chunks * n_kg || !t.g_coef[0]) return;      // warp-uniform
+    const int chunk = (int)(item / n_kg), k0 = (int)(item % n_kg) * KG, nk = min(KG, K - k0);
+    const int rows4 = (rows + 3) / 4, lo = chunk * ADJ_ROWS4;
+    const float* g = t.g[0];
+    float acc[KG];
+#pragma unroll
+    for (int q = 0; q < KG; ++q) acc[q] = 0.0f;
+#pragma unroll 1
+    for (int r = lane; r < ADJ_ROWS4; r += 32) {
+        const int i = lo + r, e = 4 * i;
+        if (i >= rows4) break;
+        float4 gg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (e + 4 <= rows) {
+            gg = *reinterpret_cast<const float4*>(g + e);
+        } else {                                       // ragged tail
+            gg.x = g[e];
+            if (e + 1 < rows) gg.y = g[e + 1];
+            if (e + 2 < rows) gg.z = g[e + 2];
+        }
+        float4 bb[KG];
+#pragma unroll
+        for (int q = 0; q < KG; ++q)
+            bb[q] = q < nk ? __ldg(reinterpret_cast<const float4*>(basis + (size_t)(k0 + q) * ld) + i)
+                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < KG; ++q) acc[q] += bb[q].x * gg.x + bb[q].y * gg.y + bb[q].z * gg.z + bb[q].w * gg.w;
+    }
+#pragma unroll
+    for (int q = 0; q < KG; ++q) {
+        float v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == (q & 31) && q < nk) part[((size_t)chunk * t.n) * K + k0 + q] = (double)v;
+    }
+}
+
+// Adjoint, second pass: g_coef_b[k] += the sum of the chunk partials.  Block
+// (FIN_K consecutive k, face b): FIN_STREAMS streams per k each sum the chunks
+// stream + FIN_STREAMS * m in order (FP64; a warp reads four chunks' rows of
+// FIN_K partials), then a fixed tree over the streams: a fixed order, so the
+// result does not depend on scheduling.
+constexpr int FIN_THREADS = 1024, FIN_K = 8, FIN_STREAMS = FIN_THREADS / FIN_K;
+__global__ void __launch_bounds__(FIN_THREADS) k_linear_adj_finish(const double* __restrict__ part, int K,
+                                                                   int n_chunks, LinearAdjTable t) {
+    __shared__ double ws[FIN_STREAMS][FIN_K];
+    const int kk = threadIdx.x % FIN_K, stream = threadIdx.x / FIN_K;
+    const int k = blockIdx.x * FIN_K + kk, b = blockIdx.y;
     double s = 0.0;
-    for (int c = 0; c < n_chunks; ++c) s += p[c];
-    t.g_coef[b][k] += (float)s;
+    if (k < K) {
+#pragma unroll 4
+        for (int c = stream; c < n_chunks; c += FIN_STREAMS) s += part[((size_t)c * t.n + b) * K + k];
+    }
+    ws[stream][kk] = s;
+    __syncthreads();
+    for (int h = FIN_STREAMS / 2; h > 0; h >>= 1) {
+        if (stream < h) ws[stream][kk] += ws[stream + h][kk];
+        __syncthreads();
+    }
+    if (stream == 0 && k < K && t.g_coef[b]) t.g_coef[b][k] += (float)ws[0][kk];
 }
 
 int nb(long n, int t) { return (int)((n + t - 1) / t); }
@@ -156,7 +227,11 @@ void launch_linear(const float* mean, const float* basis, int ld, int rows, int 
                    cudaStream_t st) {
     if (t.n <= 0 || rows <= 0) return;
     const dim3 grid(nb((rows + 3) / 4, LIN_THREADS), nb(t.n, LIN_GROUP));
-    if (t.n == 1)      // one face: smaller blocks spread its few rows over more SMs
+    // one face: smaller blocks spread its few rows over more SMs.  (Splitting
+    // the columns over several threads per row would keep more loads in flight,
+    // but its sums would differ from the batched kernel's in the last bits, and
+    // a face must render bitwise the same alone and in a batch.)
+    if (t.n == 1)
         k_linear<1><<<nb((rows + 3) / 4, LIN_THREADS / 2), LIN_THREADS / 2, 0, st>>>(mean, basis, ld, rows, K, t);
     else
         k_linear<LIN_GROUP><<<grid, LIN_THREADS, 0, st>>>(mean, basis, ld, rows, K, t);
@@ -166,13 +241,28 @@ void launch_linear(const float* mean, const float* basis, int ld, int rows, int 
 void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const LinearAdjTable& t, double* part,
                            cudaStream_t st) {
     if (t.n <= 0 || K <= 0 || rows <= 0) return;
-    const int n_chunks = linear_adj_chunks(rows);
-    if (t.n == 1)
-        k_linear_adj_part<1, 8><<<dim3(n_chunks, nb(K, 8), 1), LIN_THREADS, 0, st>>>(basis, ld, rows, K, t, part,
-                                                                                     n_chunks);
-    else
-        k_linear_adj_part<LIN_GROUP, 4><<<dim3(n_chunks, nb(K, 4), nb(t.n, LIN_GROUP)), LIN_THREADS, 0, st>>>(
-            basis, ld, rows, K, t, part, n_chunks);
-    k_linear_adj_finish<<<dim3(nb(K, 128), t.n), 128, 0, st>>>(part, K, n_chunks, t);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int n_chunks = linear_adj_chunks(rows), n_groups = nb(t.n, LIN_GROUP);
+    // batches: split the columns over grid.z until about eight blocks per SM are in
+    // flight (measured on GB300, albedo batch 8: two columns per warp, five blocks
+    // per SM and the k-split 0.183 ms against 0.203 ms for four columns at three)
+    auto split = [&](int kg_cols) {
+        const int most = nb(nb(K, kg_cols), LIN_THREADS / 32);
+        return std::max(1, std::min(most, nb(8L * sms, n_chunks * n_groups)));
+    };
+    if (t.n == 1) {
+        const long warps = (long)n_chunks * nb(K, 8);
+        k_linear_adj_one<8><<<nb(warps, LIN_THREADS / 32), LIN_THREADS, 0, st>>>(basis, ld, rows, K, t, part, n_chunks);
+    } else {
+        k_linear_adj_part<LIN_GROUP, 2, 5><<<dim3(n_chunks, n_groups, split(2)), LIN_THREADS, 0, st>>>(
+            basis, ld, rows, K, t, part);
+    }
+    k_linear_adj_finish<<<dim3(nb(K, FIN_K), t.n), FIN_THREADS, 0, st>>>(part, K, n_chunks, t);
     fr_count_launches(2);
 }
