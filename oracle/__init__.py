@@ -24,7 +24,8 @@ LIB = os.path.join(HERE, "liboracle.so")
 GGX, SCHLICK_LINEAR, FLAT, DIFFUSE_ONLY = 1, 2, 4, 8
 VIEW_CUTOFF = 1024      # the literal grazing reading: every contribution zero where n_s . o <= 0
 TERM_INTERIOR, TERM_PRIMARY, TERM_SHADOW = 1, 2, 4
-TERM_ALL = 7
+TERM_SPECULAR = 8       # boundary of the specular lobe inside triangles (the curve n_s . o = 0)
+TERM_ALL = 15
 
 _lock = threading.Lock()
 _lib = None
@@ -93,6 +94,8 @@ def lib():
         L.ora_point_light_grad.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams),
                                            f64p, f64p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_uint32, f64p, f64p, f64p]
+        L.ora_spec_crossings.argtypes = [ctypes.POINTER(OraScene), ctypes.POINTER(OraParams), ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, i32p, f64p]
         _lib = L
     return _lib
 
@@ -242,6 +245,20 @@ def grad(scene, params, adjoint, iteration=0, face_id=0, terms=TERM_ALL, flags=0
     if rc != 0:
         raise ValueError("oracle gradient: unsupported sizes")
     return g
+
+
+def spec_crossings(scene, params, scan, iteration=0, face_id=0, edge_spp=1, seed=0, max_count=4096):
+    """Crossings of image scanline `scan` (rows first, then columns) with the
+    curve n_s . o = 0 inside front-facing triangles: ([n, 2] (triangle, root
+    index along the line), [n, 2] screen (x, y))."""
+    b = _Bound(scene, params, edge_spp=edge_spp, seed=seed)
+    tr = np.zeros((max_count, 2), np.int32)
+    xy = np.zeros((max_count, 2))
+    n = lib().ora_spec_crossings(ctypes.byref(b.scene), ctypes.byref(b.params), iteration, face_id, scan,
+                                 max_count, _p(tr, i32p), _p(xy, f64p))
+    if n < 0:
+        raise ValueError("scanline out of range")
+    return tr[:min(n, max_count)].copy(), xy[:min(n, max_count)].copy()
 
 
 def brdf(n, l, o, c, s, r, flags=0):

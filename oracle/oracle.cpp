@@ -20,9 +20,17 @@
 //  * Contributions vanish unless n_s.l > 0; the specular lobe also needs
 //    n_s.o > 0 (the denominator of Eq. brdf_spec); the Lambert term does not
 //    depend on the view.  Surfaces are one-sided: a hit on a triangle whose
-//    geometric normal faces away from the camera reflects nothing.  (Zeroing
-//    every contribution where n_s.o <= 0, flag ORA_VIEW_CUTOFF, would put a
-//    discontinuity inside triangles that edge sampling does not sample.)
+//    geometric normal faces away from the camera reflects nothing.  (Flag
+//    ORA_VIEW_CUTOFF zeroes every contribution where n_s.o <= 0.)
+//  * The lobe does not vanish as n_s.o -> 0+ (G1(o) / (n_s.o) has a finite
+//    limit), so the image jumps on the curve n_s.o = 0 inside front-facing
+//    triangles whose interpolated normals turn away from the camera.  Edge
+//    sampling (Sec. 4) is applied to that curve too (ORA_TERM_SPECULAR): it is
+//    found along image scanlines (one horizontal line per pixel row and one
+//    vertical line per pixel column, edge_spp of each, at uniform offsets), and
+//    each crossing is weighted by the share (n_x^2 on rows, n_y^2 on columns)
+//    of the curve's unit normal n, so that the two families sum to the line
+//    integral with a bounded weight everywhere on the curve.
 //  * Eq. lightIntensity: emitted radiance L_j = (d_j^2 / a_j) i_j; emitter
 //    geometry is given explicitly in camera space and does not depend on pose.
 //  * One area sample per light per pixel sample (light-area importance
@@ -97,7 +105,7 @@ struct Stream {
     }
 };
 
-enum { STREAM_PRIMARY = 0, STREAM_EDGE_PRIMARY = 1, STREAM_EDGE_SHADOW = 2 };
+enum { STREAM_PRIMARY = 0, STREAM_EDGE_PRIMARY = 1, STREAM_EDGE_SHADOW = 2, STREAM_EDGE_SPECULAR = 3 };
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual numbers: value plus derivatives w.r.t. the active slots.
@@ -196,6 +204,7 @@ struct Prep {
     int N, T, K, NL, W, H, M, spp;
     int nd;                    // active dual slots (0: values only)
     int slot_rot, slot_trans, slot_focal, slot_c, slot_s, slot_r, slot_t;
+    int slot_sx, slot_sy;      // screen coordinates of a fixed image point (boundary of the lobe)
     int slot_light;            // light j's (d, a, p0, p1) at slot_light + 4 j (-1: fixed lights)
     std::vector<P3> v;         // camera-space vertices
     std::vector<P3> vn;        // unit vertex normals
@@ -435,7 +444,8 @@ void prepare(Prep& P, const OraScene* s, const OraParams* p, int nd) {
     P.nd = nd;
     P.slot_rot = P.K; P.slot_trans = P.K + 3; P.slot_focal = P.K + 6;
     P.slot_c = P.K + 7; P.slot_s = P.K + 10; P.slot_r = P.K + 13; P.slot_t = P.K + 14;
-    P.slot_light = stage_lights(s, p) ? P.K + 15 : -1;
+    P.slot_sx = P.K + 15; P.slot_sy = P.K + 16;
+    P.slot_light = stage_lights(s, p) ? P.K + 17 : -1;
     g_nd = nd;
     P.focal = p->focal[0];
     P.v.assign(P.N, P3{0, 0, 0});
@@ -1043,6 +1053,150 @@ void shadow_edge_sample(const Prep& P, const SampleOut& so, int tri_self, double
 }
 
 // ---------------------------------------------------------------------------
+// The curve n_s . o = 0 inside front-facing triangles, where the specular lobe
+// (App. A, Eq. brdf_spec) switches on and off, met along image scanlines.
+// ---------------------------------------------------------------------------
+struct Crossing {
+    int tri, root;      // triangle; 0 / 1 in order along the scanline
+    double x, y;        // screen point (the scanline's own coordinate exact)
+};
+
+// Scanline `scan`: rows first (y = (i + u) / k for row line i), then columns
+// (x = (i + u) / k), k = max(edge_spp, 1), u the line's uniform offset.
+bool scanline(const Prep& P, int scan, uint32_t iteration, uint32_t face_id, double& c) {
+    const int k = std::max(P.s->edge_spp, 1);
+    const bool row = scan < P.H * k;
+    const int idx = row ? scan : scan - P.H * k;
+    Stream so{P.s->seed, STREAM_EDGE_SPECULAR, 0xFFFFFFFFu, (uint32_t)scan, iteration, face_id};
+    c = (idx + so.u(0)) / k;
+    return row;
+}
+
+// Every crossing of scanline `scan` with the curve q(b) = m(b) . (-p(b)) = 0
+// (m = sum b_i n_i the unnormalised shading normal, p = sum b_i v_i the
+// surface point: q has the sign of n_s . o) inside the front-facing triangles,
+// in triangle order.  The rays of the scanline fill a plane through the camera
+// centre; it cuts a triangle along a chord whose barycentrics are linear in the
+// chord parameter s, so q is an exact quadratic in s.
+void spec_crossings(const Prep& P, int scan, uint32_t iteration, uint32_t face_id, std::vector<Crossing>& out) {
+    double c;
+    const bool row = scanline(P, scan, iteration, face_id, c);
+    const double f = P.focal;
+    // plane normal: rows hold the directions (x, -(c - H/2)/f, -1), columns ((c - W/2)/f, y, -1)
+    const P3 nrm = row ? p3(0.0, 1.0, -(c - 0.5 * P.H) / f) : p3(1.0, 0.0, (c - 0.5 * P.W) / f);
+    for (int t = 0; t < P.T; ++t) {
+        const int* fv = P.s->faces + 3 * t;
+        const P3 v[3] = {P.v[fv[0]], P.v[fv[1]], P.v[fv[2]]};
+        const P3 n[3] = {P.vn[fv[0]], P.vn[fv[1]], P.vn[fv[2]]};
+        if (!(v[0].z < 0.0 && v[1].z < 0.0 && v[2].z < 0.0)) continue;        // in front of the camera
+        if (!(dotp(crossp(v[1] - v[0], v[2] - v[0]), v[0]) < 0.0)) continue;  // faces the camera
+        double ph[3];
+        for (int i = 0; i < 3; ++i) ph[i] = dotp(nrm, v[i]);
+        double bc[2][3];
+        int ne = 0;
+        for (int e = 0; e < 3 && ne < 2; ++e) {        // chord ends: edges whose ends straddle the plane
+            const int i = e, j = (e + 1) % 3;
+            if ((ph[i] > 0.0) == (ph[j] > 0.0)) continue;
+            const double tt = ph[i] / (ph[i] - ph[j]);
+            bc[ne][0] = bc[ne][1] = bc[ne][2] = 0.0;
+            bc[ne][i] = 1.0 - tt;
+            bc[ne][j] = tt;
+            ++ne;
+        }
+        if (ne != 2) continue;
+        double Q[3][3];                                // q(b) = sum_ij b_i b_j Q_ij
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Q[i][j] = -dotp(n[i], v[j]);
+        auto form = [&](const double* a, const double* b) {
+            double r = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) r += a[i] * b[j] * Q[i][j];
+            return r;
+        };
+        const double dl[3] = {bc[1][0] - bc[0][0], bc[1][1] - bc[0][1], bc[1][2] - bc[0][2]};
+        const double a2 = form(dl, dl), a1 = form(bc[0], dl) + form(dl, bc[0]), a0 = form(bc[0], bc[0]);
+        double sr[2];
+        int nr = 0;
+        if (a2 == 0.0) {
+            if (a1 != 0.0) sr[nr++] = -a0 / a1;
+        } else {
+            const double disc = a1 * a1 - 4.0 * a2 * a0;
+            if (disc > 0.0) {                          // a double root touches the curve without crossing it
+                const double sq = std::sqrt(disc);
+                const double qq = -0.5 * (a1 + (a1 >= 0.0 ? sq : -sq));
+                sr[nr++] = qq / a2;
+                sr[nr++] = a0 / qq;
+            }
+        }
+        Crossing cr[2];
+        int m = 0;
+        for (int r = 0; r < nr; ++r) {
+            if (!(sr[r] >= 0.0 && sr[r] <= 1.0)) continue;
+            double b[3];
+            for (int i = 0; i < 3; ++i) b[i] = bc[0][i] + sr[r] * dl[i];
+            const P3 pt = v[0] * b[0] + v[1] * b[1] + v[2] * b[2];
+            Crossing x;
+            x.tri = t;
+            x.x = row ? 0.5 * P.W + f * pt.x / -pt.z : c;
+            x.y = row ? c : 0.5 * P.H - f * pt.y / -pt.z;
+            cr[m++] = x;
+        }
+        if (m == 2 && (row ? cr[1].x < cr[0].x : cr[1].y < cr[0].y)) std::swap(cr[0], cr[1]);
+        for (int r = 0; r < m; ++r) {
+            cr[r].root = r;
+            out.push_back(cr[r]);
+        }
+    }
+}
+
+// Camera ray direction through a screen point given as duals.
+V3 camera_dir_d(const Prep& P, const D& sx, const D& sy) {
+    D f = seed_slot(P.focal, P.slot_focal);
+    return v3((sx - 0.5 * P.W) / f, -(sy - 0.5 * P.H) / f, D(-1.0));
+}
+
+// Boundary term of the curve n_s . o = 0 at one crossing (edge sampling,
+// Sec. 4): with G = n_s . o at the fixed screen point x (duals on the
+// parameters and on x), the curve moves along its unit normal n = grad G /
+// |grad G| (towards G > 0, where the lobe is on) at speed -G_theta / |grad G|,
+// and the image changes by -(L(x + eps n) - L(x - eps n)) per unit of that
+// motion.  The scanline family's share n_x^2 (rows) or n_y^2 (columns) and its
+// line density k turn the line integral into a sum over crossings:
+// d/dtheta += sum_k adj_k (L+ - L-)_k G_theta |n_x| / (|grad G| k) on rows.
+void spec_boundary_sample(const Prep& P, const Crossing& c, int scan, bool row, uint32_t iteration,
+                          uint32_t face_id, const double adj[3], double* g) {
+    const int* t = P.s->faces + 3 * c.tri;
+    D sx = seed_slot(c.x, P.slot_sx), sy = seed_slot(c.y, P.slot_sy);
+    V3 d = camera_dir_d(P, sx, sy);
+    D b1, b2;
+    V3 y;
+    hit_duals(P, c.tri, d, b1, b2, y);
+    D b0 = 1.0 - b1 - b2;
+    V3 n0 = load(P.vn, P.dn, P.nd, t[0]), n1 = load(P.vn, P.dn, P.nd, t[1]), n2 = load(P.vn, P.dn, P.nd, t[2]);
+    V3 ns = normalize(n0 * b0 + n1 * b1 + n2 * b2);
+    V3 o = normalize(v3c(0, 0, 0) - d);
+    D G = dot(ns, o);
+    const double gx = G.d[P.slot_sx], gy = G.d[P.slot_sy], g2 = gx * gx + gy * gy;
+    if (!(g2 > 0.0)) return;
+    const double gl = std::sqrt(g2), mx = gx / gl, my = gy / gl;
+    const double eps = 1e-3;
+    Stream st{P.s->seed, STREAM_EDGE_SPECULAR, (uint32_t)(2 * c.tri + c.root), (uint32_t)scan, iteration, face_id};
+    SampleOut sp, sm;
+    {
+        int keep = g_nd;
+        g_nd = 0;
+        shade_sample(P, c.x + eps * mx, c.y + eps * my, st, 4, sp);
+        shade_sample(P, c.x - eps * mx, c.y - eps * my, st, 4, sm);
+        g_nd = keep;
+    }
+    double jump = 0.0;
+    for (int k = 0; k < 3; ++k) jump += adj[k] * (sp.L[k].v - sm.L[k].v);
+    const int k = std::max(P.s->edge_spp, 1);
+    const double w = jump * (row ? std::fabs(gx) : std::fabs(gy)) / (g2 * k);
+    if (w != 0.0) accumulate_geo(P, G, w, g);
+}
+
+// ---------------------------------------------------------------------------
 // Blur + L1 loss (Sec. 4 Eq. energy and "Variance Reduction").
 // ---------------------------------------------------------------------------
 void gauss3(double w[3][3]) {
@@ -1206,9 +1360,9 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
              double* g_focal, double* g_light, double* g_diffuse, double* g_specular,
              double* g_roughness, double* g_light_geom, double* g_env) {
     const int n_lg = stage_lights(s, p) ? 4 * s->n_lights : 0;
-    if (s->n_basis + 15 + n_lg > DMAX || s->n_lights > ORA_MAX_LIGHTS) return -1;
+    if (s->n_basis + 17 + n_lg > DMAX || s->n_lights > ORA_MAX_LIGHTS) return -1;
     Prep P;
-    prepare(P, s, p, s->n_basis + 15 + n_lg);
+    prepare(P, s, p, s->n_basis + 17 + n_lg);
     classify(P);
     int nt = threads_of(s);
     int ngeo = P.slot_c;
@@ -1329,6 +1483,23 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
             }
         });
     }
+    // boundary term of the specular lobe: crossings of image scanlines with the
+    // curve n_s . o = 0
+    if ((terms & ORA_TERM_SPECULAR) && !(s->flags & ORA_FLAT)) {
+        const int n_scan = (P.H + P.W) * std::max(s->edge_spp, 1);
+        parallel_for(nt, n_scan, [&](int scan, int th) {
+            std::vector<Crossing> cr;
+            spec_crossings(P, scan, iteration, face_id, cr);
+            double c;
+            const bool row = scanline(P, scan, iteration, face_id, c);
+            for (const Crossing& x : cr) {
+                if (!(x.x >= 0.0 && x.x < P.W && x.y >= 0.0 && x.y < P.H)) continue;
+                double adj[3];
+                if (!adj_of((int)std::floor(x.y) * P.W + (int)std::floor(x.x), adj)) continue;
+                spec_boundary_sample(P, x, scan, row, iteration, face_id, adj, acc[th].geo.data());
+            }
+        });
+    }
     // reduce
     std::vector<double> geo(ngeo, 0.0), light((size_t)P.NL * 3, 0.0);
     for (auto& a : acc) {
@@ -1353,6 +1524,25 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
     if (g_env && n_env) { std::fill(g_env, g_env + n_env, 0.0); for (auto& a : acc) for (size_t q = 0; q < n_env; ++q) g_env[q] += a.env[q]; }
     g_nd = 0;
     return 0;
+}
+
+// Crossings of scanline `scan` with the curve n_s . o = 0 (values only): up to
+// `max` of them as (triangle, root) and screen (x, y); returns their count.
+int ora_spec_crossings(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t face_id, int32_t scan,
+                       int32_t max, int32_t* tri_root, double* xy) {
+    Prep P;
+    prepare(P, s, p, 0);
+    const int n_scan = (P.H + P.W) * std::max(s->edge_spp, 1);
+    if (scan < 0 || scan >= n_scan) return -1;
+    std::vector<Crossing> cr;
+    spec_crossings(P, scan, iteration, face_id, cr);
+    for (int i = 0; i < (int)cr.size() && i < max; ++i) {
+        tri_root[2 * i] = cr[i].tri;
+        tri_root[2 * i + 1] = cr[i].root;
+        xy[2 * i] = cr[i].x;
+        xy[2 * i + 1] = cr[i].y;
+    }
+    return (int)cr.size();
 }
 
 double ora_brdf(uint32_t flags, const double* n, const double* l, const double* o, const double* c,
@@ -1402,9 +1592,9 @@ int ora_point_light_grad(const OraScene* s, const OraParams* p, const double* y,
     OraScene sc = *s;
     sc.flags = ORA_DIFFUSE_ONLY;
     const int n_lg = stage_lights(s, p) ? 4 * s->n_lights : 0;
-    if (s->n_basis + 15 + n_lg > DMAX) return -1;
+    if (s->n_basis + 17 + n_lg > DMAX) return -1;
     Prep P;
-    prepare(P, &sc, p, s->n_basis + 15 + n_lg);
+    prepare(P, &sc, p, s->n_basis + 17 + n_lg);
     classify(P);
     int nt = threads_of(s);
     std::vector<std::vector<double>> gs(nt, std::vector<double>(P.slot_c, 0.0));

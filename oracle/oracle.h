@@ -21,7 +21,8 @@ extern "C" {
 #define ORA_FLAT           4u   /* debug: radiance = diffuse albedo at the hit, no lights */
 #define ORA_DIFFUSE_ONLY   8u   /* debug: f_r = c / pi (no specular lobe) */
 #define ORA_VIEW_CUTOFF 1024u   /* every contribution zero where n_s . o <= 0 (the grazing cutoff applied to
-                                   the diffuse term too; its gradient misses that curve's motion) */
+                                   the diffuse term too); the boundary term of the curve n_s . o = 0
+                                   (ORA_TERM_SPECULAR) then carries the whole jump there */
 
 /* emitter type of a light record (the other types are 0 quad, 1 triangle, 2 disk):
  * a block of texels of an environment map of lights at infinity (Sec. 7,
@@ -36,6 +37,7 @@ extern "C" {
 #define ORA_TERM_INTERIOR  1u
 #define ORA_TERM_PRIMARY   2u
 #define ORA_TERM_SHADOW    4u
+#define ORA_TERM_SPECULAR  8u   /* boundary of the specular lobe inside triangles: the curve n_s . o = 0 */
 
 typedef struct OraScene {
     int32_t n_vertices, n_triangles, n_basis;
@@ -94,6 +96,15 @@ int ora_grad(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t
              double* g_trans, double* g_focal, double* g_light, double* g_diffuse,
              double* g_specular, double* g_roughness, double* g_light_geom /* [N_L][4] or NULL */,
              double* g_env /* [env_size][env_size][3] or NULL */);
+
+/* Crossings of image scanline `scan` with the curve n_s . o = 0 inside the
+ * front-facing triangles (the boundary of the specular lobe): scanlines
+ * 0 .. H*k-1 are rows y = (i + u)/k, then W*k columns, k = max(edge_spp, 1),
+ * u a uniform offset per line from the specular-edge stream.  Writes up to
+ * `max` crossings as (triangle, root index along the line) pairs and screen
+ * points (x, y); returns their count (-1: scan out of range). */
+int ora_spec_crossings(const OraScene* s, const OraParams* p, uint32_t iteration, uint32_t face_id, int32_t scan,
+                       int32_t max, int32_t* tri_root, double* xy);
 
 double ora_brdf(uint32_t flags, const double* n, const double* l, const double* o,
                 const double* c, const double* s, double r, double* out_rgb);

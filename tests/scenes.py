@@ -146,3 +146,31 @@ def ico_box(width=32, height=32, spp=4, tex=8, seed=0):
     sc = dataclasses.replace(sc, lights=rec, light_d=d, light_a=a)
     pr.light_i = np.random.default_rng(seed + 6).uniform(0.5, 1.5, size=(rec.shape[0], 3)).astype(np.float32)
     return sc, pr
+
+
+def tube(width=32, height=32, spp=16, tex=4, sides=8):
+    """An open prism of `sides` faces around the y axis through (0, 0, -4),
+    taller than the view, vertex angles 42.5 + 360 k / sides degrees from +z.
+    With eight sides the front-facing faces next to the silhouettes (centred
+    at +-65 degrees) have one vertex normal turned towards the camera and one
+    turned away, so the curve n_s . o = 0 runs through them; two quad lights
+    at the sides light them at grazing angles, with a strong specular lobe.
+    The basis moves every vertex radially (the prism's radius)."""
+    ang = np.deg2rad(42.5 + 360.0 / sides * np.arange(sides))
+    ring = np.stack([np.sin(ang), np.zeros(sides), np.cos(ang)], 1)
+    verts = np.concatenate([ring + [0.0, -3.0, -4.0], ring + [0.0, 3.0, -4.0]])
+    faces = []
+    for k in range(sides):
+        a, b = k, (k + 1) % sides
+        faces += [[a, b, sides + b], [a, sides + b, sides + a]]
+    basis = np.zeros((1, 2 * sides, 3))
+    basis[0] = np.concatenate([ring, ring]) * 0.5
+    lights = [quad_light([3.0, 0.0, -3.0], [0.6, 0.0, 1.2], [0.0, 1.5, 0.0]),
+              quad_light([-3.0, 0.0, -3.0], [0.0, 1.5, 0.0], [-0.6, 0.0, 1.2])]
+    sc, pr = make(verts, faces, basis, lights, width=width, height=height, spp=spp, tex=tex,
+                  light_i=[(3.0, 2.6, 2.2), (2.2, 2.6, 3.0)], diffuse=(0.1, 0.1, 0.1))
+    pr.focal = np.array([float(width)], np.float32)
+    pr.specular = np.full((tex, tex, 3), 0.6, np.float32)
+    pr.roughness = np.full((tex, tex), 0.4, np.float32)
+    pr.coef = np.array([0.04], np.float32)
+    return sc, pr
