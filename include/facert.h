@@ -52,6 +52,8 @@ typedef int32_t fr_status;
 #define FR_FLAG_NO_INTERIOR     16u   /* gradient: skip the interior (visibility-fixed) term */
 #define FR_FLAG_NO_PRIMARY_EDGE 32u   /* gradient: skip the primary-visibility boundary term */
 #define FR_FLAG_NO_SHADOW_EDGE  64u   /* gradient: skip the shadow boundary term */
+#define FR_FLAG_NO_SPECULAR_EDGE 2048u /* gradient: skip the boundary term of the specular lobe's
+                                         cutoff curve n_s . o = 0 inside triangles */
 #define FR_FLAG_MORPH_BF16     128u   /* morph as one BF16 tensor-core GEMM over the batch (FP32
                                          accumulate, FP32 mean); context-wide, read by every call */
 #define FR_FLAG_RECOMPUTE      256u   /* the adjoint re-traces its camera and shadow rays inside the
@@ -59,9 +61,9 @@ typedef int32_t fr_status;
                                          recomputing them in tiles (see fr_render) */
 #define FR_FLAG_VIEW_CUTOFF   1024u   /* zero every contribution where the shading normal faces away from
                                          the camera (n_s . o <= 0), the diffuse term included; by default
-                                         only the specular lobe needs n_s . o > 0.  This cutoff is a
-                                         discontinuity inside triangles that edge sampling does not
-                                         sample, so its gradients miss that curve's motion */
+                                         only the specular lobe needs n_s . o > 0.  Either way the image
+                                         jumps on the curve n_s . o = 0 inside triangles, which the
+                                         specular-boundary term samples */
 #define FR_FLAG_LBVH           512u   /* rebuild an LBVH (Morton sort + Karras tree) every call instead
                                          of refitting the SAH topology built from the mean face at
                                          fr_set_mesh; for deformations far from the mean face.
@@ -250,7 +252,11 @@ fr_status fr_forward(fr_ctx* ctx, const fr_params* p, float* image, uint32_t ite
 /* Adjoint of fr_forward: adds d(sum adj_image * image)/dchi into g.  Re-traces
  * with the same Philox counters instead of storing hit records, and includes
  * the primary-visibility and shadow boundary terms (edge sampling, Sec. 4)
- * unless disabled by flags.  adj_image [H][W][3] (device). */
+ * and the boundary term of the specular lobe's cutoff inside triangles (the
+ * curve n_s . o = 0 of App. A, Eq. brdf_spec, met along one row line per
+ * pixel row and one column line per pixel column, edge_spp of each, rows
+ * first; (W + H) * max(edge_spp, 1) <= 65535) unless disabled by flags.
+ * adj_image [H][W][3] (device). */
 fr_status fr_backward(fr_ctx* ctx, const fr_params* p, const float* adj_image, fr_grads* g,
                       uint32_t iteration, uint32_t face_id, void* stream);
 
@@ -378,15 +384,16 @@ int32_t fr_num_edges(const fr_ctx* ctx);
 /* Traversal work accumulated on ctx since the last reset, per kernel: out[3k+0]
  * rays traced, out[3k+1] BVH nodes visited, out[3k+2] ray/triangle tests, for
  * k = 0 forward, 1 adjoint (re-trace + shadow-boundary rays), 2 primary-edge
- * rays (host uint64[9]).  Synchronises `stream`; reset != 0 zeroes them. */
+ * and specular-boundary rays (host uint64[9]).  Synchronises `stream`; reset != 0 zeroes them. */
 fr_status fr_counters(fr_ctx* ctx, uint64_t* out, int32_t reset, void* stream);
 
 /* Enable (on != 0) CUDA-event marks between the stages of fr_render. */
 fr_status fr_set_timing(fr_ctx* ctx, int32_t on);
 
 /* Milliseconds of the stages of the last timed fr_render (synchronises):
- * out[8] = {geometry+LBVH, forward, loss, classify, adjoint, primary edges,
- * chain to parameters, total}. */
+ * out[8] = {geometry+LBVH, forward, loss, classify, adjoint, screen-space
+ * boundary terms (primary edges and the specular lobe's boundary), chain to
+ * parameters, total}. */
 fr_status fr_get_timing(fr_ctx* ctx, float* out);
 
 /* Number of kernels this library has launched in this process. */
@@ -477,7 +484,8 @@ typedef struct fr_server_config {
                                  (soft box [0, 1]) */
     int32_t edge_spp;         /* primary-edge samples per pixel of every step (0..64) */
     uint32_t item_flags;      /* FR_FLAG_* bits of every render item (Stage II adds
-                                 FR_FLAG_NO_PRIMARY_EDGE | FR_FLAG_NO_SHADOW_EDGE) */
+                                 FR_FLAG_NO_PRIMARY_EDGE | FR_FLAG_NO_SHADOW_EDGE |
+                                 FR_FLAG_NO_SPECULAR_EDGE: the geometry is fixed there) */
     uint32_t eval_iteration;  /* Philox iteration of the final loss evaluation */
     int32_t eval_spp;         /* spp of the final loss evaluation (0: the request's own) */
     int32_t keep_params;      /* != 0: copy each finished request's parameters to the host */

@@ -779,9 +779,12 @@ void hit_duals(const Prep& P, int tri, const V3& d, D& b1, D& b2, V3& y) {
 
 // Radiance of the camera ray through screen point (sx, sy).  `st` supplies the
 // light dimensions starting at `light_dim0`.  If `fixed_tri` >= 0 the hit
-// triangle and the visibility mask `fixed_mask` are imposed (gradient pass).
+// triangle is imposed (the ray meets its plane), and the visibility mask
+// `fixed_mask` too when given (gradient pass); without it the shadow rays are
+// traced.  view_side = +-1 shades with the view direction tilted just to that
+// side of the curve n_s . o = 0 (the two one-sided limits there).
 void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim0, SampleOut& out,
-                  int fixed_tri = -2, const uint64_t* fixed_mask = nullptr) {
+                  int fixed_tri = -2, const uint64_t* fixed_mask = nullptr, int view_side = 0) {
     const OraScene* s = P.s;
     V3 dd = camera_dir(P, sx, sy);
     int tri;
@@ -807,6 +810,10 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
     V3 n0 = load(P.vn, P.dn, P.nd, t[0]), n1 = load(P.vn, P.dn, P.nd, t[1]), n2 = load(P.vn, P.dn, P.nd, t[2]);
     V3 ns = normalize(n0 * b0 + n1 * b1 + n2 * b2);
     V3 o = normalize(v3c(0, 0, 0) - dd);
+    if (view_side) {        // one side of the curve n_s . o = 0: o tilted to n_s . o = +-1e-5
+        const V3 om = o - ns * dot(ns, o);
+        o = normalize(om + ns * (view_side > 0 ? 1e-5 : -1e-5));
+    }
     D u = b0 * (double)s->uv[2 * t[0]] + b1 * (double)s->uv[2 * t[1]] + b2 * (double)s->uv[2 * t[2]];
     D v = b0 * (double)s->uv[2 * t[0] + 1] + b1 * (double)s->uv[2 * t[1] + 1] + b2 * (double)s->uv[2 * t[2] + 1];
     D c[3], sp[3], r;
@@ -841,7 +848,7 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
             const D cos_s = dot(ns, l);
             if (!(cos_s.v > 0.0)) continue;
             bool vis;
-            if (fixed_tri == -2) vis = !occluded_dir(P, val(y), es.w, tri);
+            if (fixed_tri == -2 || !fixed_mask) vis = !occluded_dir(P, val(y), es.w, tri);
             else vis = (fixed_mask[j >> 6] >> (j & 63)) & 1ull;
             if (!vis) continue;
             out.mask[j >> 6] |= (1ull << (j & 63));
@@ -871,7 +878,7 @@ void shade_sample(const Prep& P, double sx, double sy, Stream& st, int light_dim
         D cos_l = -dot(v3c(Lj.n.x, Lj.n.y, Lj.n.z), l);
         if (!(cos_s.v > 0.0) || !(cos_l.v > 0.0)) continue;
         bool vis;
-        if (fixed_tri == -2) vis = !occluded(P, val(y), z, tri);
+        if (fixed_tri == -2 || !fixed_mask) vis = !occluded(P, val(y), z, tri);
         else vis = (fixed_mask[j >> 6] >> (j & 63)) & 1ull;
         if (!vis) continue;
         out.mask[j >> 6] |= (1ull << (j & 63));
@@ -1159,10 +1166,16 @@ V3 camera_dir_d(const Prep& P, const D& sx, const D& sy) {
 // Sec. 4): with G = n_s . o at the fixed screen point x (duals on the
 // parameters and on x), the curve moves along its unit normal n = grad G /
 // |grad G| (towards G > 0, where the lobe is on) at speed -G_theta / |grad G|,
-// and the image changes by -(L(x + eps n) - L(x - eps n)) per unit of that
-// motion.  The scanline family's share n_x^2 (rows) or n_y^2 (columns) and its
-// line density k turn the line integral into a sum over crossings:
-// d/dtheta += sum_k adj_k (L+ - L-)_k G_theta |n_x| / (|grad G| k) on rows.
+// and the image changes by -(L+ - L-) per unit of that motion, L+- the two
+// one-sided limits of the radiance of the crossing's own triangle at x (the
+// same hit, shadow rays and light samples; the view direction tilted to
+// n_s . o = +-1e-5): the jump of the cutoff alone, with no part of the
+// continuous change across the curve and nothing of a silhouette that the
+// curve may run next to.  The curve is seen only where that triangle is the
+// visible surface: nothing along the camera ray is nearer.  The scanline
+// family's share n_x^2 (rows) or n_y^2 (columns) and its line density k turn
+// the line integral into a sum over crossings:
+// d/dtheta += sum_k adj_k (L+ - L-)_k G_theta |n_x| / (|grad G|^2 k) on rows.
 void spec_boundary_sample(const Prep& P, const Crossing& c, int scan, bool row, uint32_t iteration,
                           uint32_t face_id, const double adj[3], double* g) {
     const int* t = P.s->faces + 3 * c.tri;
@@ -1178,15 +1191,15 @@ void spec_boundary_sample(const Prep& P, const Crossing& c, int scan, bool row, 
     D G = dot(ns, o);
     const double gx = G.d[P.slot_sx], gy = G.d[P.slot_sy], g2 = gx * gx + gy * gy;
     if (!(g2 > 0.0)) return;
-    const double gl = std::sqrt(g2), mx = gx / gl, my = gy / gl;
-    const double eps = 1e-3;
+    double t_near;
+    if (closest_hit(P, p3(0, 0, 0), val(d), t_near) >= 0 && t_near < -y.z.v * (1.0 - 1e-9)) return;
     Stream st{P.s->seed, STREAM_EDGE_SPECULAR, (uint32_t)(2 * c.tri + c.root), (uint32_t)scan, iteration, face_id};
     SampleOut sp, sm;
     {
         int keep = g_nd;
         g_nd = 0;
-        shade_sample(P, c.x + eps * mx, c.y + eps * my, st, 4, sp);
-        shade_sample(P, c.x - eps * mx, c.y - eps * my, st, 4, sm);
+        shade_sample(P, c.x, c.y, st, 4, sp, c.tri, nullptr, +1);
+        shade_sample(P, c.x, c.y, st, 4, sm, c.tri, nullptr, -1);
         g_nd = keep;
     }
     double jump = 0.0;

@@ -45,6 +45,10 @@ struct Slot {
     LightDev* lights = nullptr;      // lights built from stage parameters [FR_MAX_LIGHTS]
     int* edge_perm = nullptr;        // primary-edge sample order [edge_cap]
     long edge_cap = 0;
+    int* spec_list = nullptr;        // specular-boundary candidates [T], their boxes, counts
+    float4* spec_box = nullptr;
+    int* spec_hist = nullptr;
+    int* spec_count = nullptr;
     int32_t* rec_tri = nullptr;      // hit records: a whole image, or one tile of a larger one
     uint64_t* rec_vis = nullptr;
     long rec_cap = 0;                // camera samples the record buffer holds
@@ -240,6 +244,10 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.tri_rec = a.tri_rec;
     it.mask_rec = a.mask_rec;
     if ((long)a.W * a.H * a.edge_spp <= sl.edge_cap) it.edge_perm = sl.edge_perm;
+    it.spec_list = sl.spec_list;
+    it.spec_box = sl.spec_box;
+    it.spec_hist = sl.spec_hist;
+    it.spec_count = sl.spec_count;
     // hit records: a fused step's forward writes them when the whole image fits
     // the buffer; otherwise the adjoint recomputes them tile by tile into it.
     // FR_FLAG_RECOMPUTE keeps the adjoint re-tracing every sample instead.
@@ -281,6 +289,21 @@ BlockMap map_of(const fr_ctx* c, int n, bool edges) {
         // primary-edge samples take two threads each (one per side of the edge)
         long work = (long)s.W * s.H * (edges ? ((s.flags & FR_FLAG_NO_PRIMARY_EDGE) ? 0 : 2 * s.edge_spp) : s.spp);
         b += (int)((work + 127) / 128);
+    }
+    m.block0[n] = b;
+    return m;
+}
+
+// One block per scanline of the specular-boundary term for each item that has
+// the term: (W + H) * max(edge_spp, 1) rows and columns.
+BlockMap spec_map(const fr_ctx* c, int n) {
+    BlockMap m;
+    m.n = n;
+    int b = 0;
+    for (int k = 0; k < n; ++k) {
+        const DevScene& s = c->h_items[k].S;
+        m.block0[k] = b;
+        if (!(s.flags & (FR_FLAG_NO_SPECULAR_EDGE | FR_FLAG_FLAT))) b += (s.W + s.H) * std::max(s.edge_spp, 1);
     }
     m.block0[n] = b;
     return m;
@@ -440,6 +463,7 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     }
     launch_edge_order(c->d_items, n, max_edge, st);
     launch_edge_primary(c->d_items, map_of(c, n, true), c->env_size > 0, st);
+    launch_edge_specular(c->d_items, n, c->T, spec_map(c, n), c->env_size > 0, st);
     mark(c, 6, st);
     launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
@@ -503,6 +527,10 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     // processing order of the primary-edge samples (the context's edge_spp, at least 1)
     sl.edge_cap = (long)c->cfg.width * c->cfg.height * std::max(c->cfg.edge_spp, 1);
     TRY(dalloc(c, &sl.edge_perm, (size_t)sl.edge_cap));
+    TRY(dalloc(c, &sl.spec_list, (size_t)T));
+    TRY(dalloc(c, &sl.spec_box, (size_t)T));
+    TRY(dalloc(c, &sl.spec_hist, (size_t)(T + 1023) / 1024 + 1));
+    TRY(dalloc(c, &sl.spec_count, 1));
     // hit records (triangle + two visibility words per camera sample): the whole
     // image when it fits FR_RECORDS_BUDGET, else equal tiles of it that do, in
     // whole pixels and whole 128-thread blocks (a multiple of max(128, spp))
@@ -521,6 +549,8 @@ fr_status check_image_args(fr_ctx* c, int W, int H, int spp, int edge_spp) {
         return fail(c, FR_EINVAL, "item image larger than the context's width x height");
     if (!is_pow2(spp) || spp > FR_MAX_SPP) return fail(c, FR_EINVAL, "spp must be a power of two <= 256");
     if (edge_spp < 0 || edge_spp > 64) return fail(c, FR_EINVAL, "edge_spp out of range");
+    if ((long)(W + H) * std::max(edge_spp, 1) > 65535)
+        return fail(c, FR_EINVAL, "more than 65535 scanlines for the specular-boundary term");
     if ((long)W * H * spp > (1L << 31) - 1024) return fail(c, FR_EINVAL, "too many samples per item");
     return FR_OK;
 }

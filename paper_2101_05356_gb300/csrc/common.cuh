@@ -60,7 +60,7 @@ FR_D float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
 // Sample stream: key (seed, tag), counter (index, (sample << 16) | block,
 // iteration, face).  Dimension d lives in word d % 4 of block d / 4.
-enum { FR_STREAM_PRIMARY = 0, FR_STREAM_EDGE_PRIMARY = 1, FR_STREAM_EDGE_SHADOW = 2 };
+enum { FR_STREAM_PRIMARY = 0, FR_STREAM_EDGE_PRIMARY = 1, FR_STREAM_EDGE_SHADOW = 2, FR_STREAM_EDGE_SPECULAR = 3 };
 
 struct Sampler {
     uint2 key;
@@ -225,6 +225,10 @@ struct DevItem {
     long rec_cap;           // camera samples the record buffer holds (a tile of the image)
     int rec_full;           // this call's forward writes the records of the whole image (it fits)
     int* edge_perm;         // processing order of the primary-edge samples (null: index order)
+    int* spec_list;         // candidate triangles of the specular-boundary term [T] (ordered)
+    float4* spec_box;       // their screen boxes (x0, x1, y0, y1) [T]
+    int* spec_hist;         // per-chunk candidate counts, then offsets [ceil(T / 1024)]
+    int* spec_count;        // [1]
     float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
     float *g_light_d, *g_light_a, *g_light_p;            // light stage geometry gradients (may be null)
     float* g_env;                                         // environment radiance gradient (may be null)

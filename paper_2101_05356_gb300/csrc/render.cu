@@ -109,9 +109,10 @@ FR_D void sample_material(const DevScene& S, const DevParams& P, SampleState& ss
 
 // MATERIAL = false leaves the material to a later sample_material call (the
 // forward fetches it after the shadow traversal, so it is not live across it).
+// `given` (non-null) imposes the hit instead (its triangle, slot and barycentrics).
 template <bool CAN_TRACE = true, bool MATERIAL = true>
 FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, float sx, float sy,
-                        Stack st, SampleState& ss, RayStats& rs, int rec = REC_TRACE) {
+                        Stack st, SampleState& ss, RayStats& rs, int rec = REC_TRACE, const Hit* given = nullptr) {
     ss.hit = false;
     ss.lit = false;
     ss.tri = ss.slot = -1;
@@ -119,7 +120,9 @@ FR_D void primary_state(const DevScene& S, const DevParams& P, bool active, floa
     const float f = __ldg(P.focal);
     ss.d = f3((sx - 0.5f * S.W) / f, -(sy - 0.5f * S.H) / f, -1.0f);
     const RayPre r = ray_setup(f3(0.0f, 0.0f, 0.0f), ss.d);
-    const Hit h = (CAN_TRACE && rec == REC_TRACE) ? trace_closest(S, r, 0.0f, INFINITY, st, rs) : hit_record(S, r, rec);
+    const Hit h = given ? *given
+                        : (CAN_TRACE && rec == REC_TRACE) ? trace_closest(S, r, 0.0f, INFINITY, st, rs)
+                                                          : hit_record(S, r, rec);
     if (h.tri < 0) return;
     ss.hit = true;
     ss.tri = h.tri;
@@ -642,6 +645,57 @@ FR_D void shadow_edge(const DevScene& S, const DevParams& P, const EdgeLists& EL
 // records-only forward pass of this tile), so the camera and shadow
 // traversals are compiled out (a smaller kernel); otherwise each item re-traces
 // unless its forward recorded the whole image (q0 = 0).
+// Chain rule from a camera sample's shading state back to its hit triangle's
+// vertices and vertex normals and to the camera ray direction d: given the
+// gradients w.r.t. the shading normal ns = m / |m| (m = sum b_k n_k), the view
+// direction o = -d / |d|, the hit point y = sum b_k v_k and the barycentrics
+// (gb, e.g. from texture coordinates), with the barycentrics of the ray from
+// the camera centre along d (Moller-Trumbore form).
+struct HitChain {
+    float3 gv[3], gn[3], gd;
+};
+
+FR_D HitChain hit_chain(float3 v0, float3 v1, float3 v2, float3 n0, float3 n1, float3 n2, float3 d, float3 g_ns,
+                        float3 g_o, float3 gy, float gb0, float gb1, float gb2) {
+    HitChain h;
+    // intersection quantities (ray origin at the camera)
+    const float3 e1 = v1 - v0, e2 = v2 - v0, sv = -v0;
+    const float3 pv = cross(d, e2), qv = cross(sv, e1);
+    const float det = dot(e1, pv), inv_det = __fdividef(1.0f, det);
+    const float b1 = dot(sv, pv) * inv_det, b2 = dot(d, qv) * inv_det, b0 = 1.0f - b1 - b2;
+    // shading normal ns = m / |m|
+    const float3 mm = n0 * b0 + n1 * b1 + n2 * b2;
+    const float inv_m = rsqrtf(dot(mm, mm));
+    const float3 nsh = mm * inv_m;
+    const float3 gm = (g_ns - nsh * dot(nsh, g_ns)) * inv_m;
+    h.gn[0] = gm * b0; h.gn[1] = gm * b1; h.gn[2] = gm * b2;
+    gb0 += dot(n0, gm); gb1 += dot(n1, gm); gb2 += dot(n2, gm);
+    // y = sum b_k v_k
+    float3 gv0 = gy * b0, gv1 = gy * b1, gv2 = gy * b2;
+    gb0 += dot(v0, gy); gb1 += dot(v1, gy); gb2 += dot(v2, gy);
+    // view direction o = -d / |d|
+    const float inv_d = rsqrtf(dot(d, d));
+    const float3 od = -d * inv_d;
+    float3 gd = -(g_o - od * dot(od, g_o)) * inv_d;
+    // barycentrics from the intersection
+    const float G1 = gb1 - gb0, G2 = gb2 - gb0;
+    const float gsp = G1 * inv_det, gdq = G2 * inv_det, gdet = -(G1 * b1 + G2 * b2) * inv_det;
+    float3 gs = pv * gsp;
+    float3 gp = sv * gsp + e1 * gdet;
+    gd += qv * gdq;
+    const float3 gq = d * gdq;
+    float3 ge1 = pv * gdet;
+    gs += cross(e1, gq);
+    ge1 += cross(gq, sv);
+    gd += cross(e2, gp);
+    const float3 ge2 = cross(gp, d);
+    h.gv[0] = gv0 + (-gs - ge1 - ge2);
+    h.gv[1] = gv1 + ge1;
+    h.gv[2] = gv2 + ge2;
+    h.gd = gd;
+    return h;
+}
+
 template <bool RECORDED, bool ENV>
 __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS : FR_ADJ_MIN_BLOCKS)
     k_adjoint(const DevItem* items, BlockMap map, long q0) {
@@ -789,11 +843,6 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
         const float3 v0 = xyz(S.v[fc.x]), v1 = xyz(S.v[fc.y]), v2 = xyz(S.v[fc.z]);
         const float3 n0 = xyz(S.vn[fc.x]), n1 = xyz(S.vn[fc.y]), n2 = xyz(S.vn[fc.z]);
         const float2 t0 = S.uv[fc.x], t1 = S.uv[fc.y], t2 = S.uv[fc.z];
-        // intersection quantities (Moller-Trumbore form, ray origin at the camera)
-        const float3 e1 = v1 - v0, e2 = v2 - v0, sv = -v0;
-        const float3 pv = cross(ss.d, e2), qv = cross(sv, e1);
-        const float det = dot(e1, pv), inv_det = __fdividef(1.0f, det);
-        const float b1 = dot(sv, pv) * inv_det, b2 = dot(ss.d, qv) * inv_det, b0 = 1.0f - b1 - b2;
         // textures: value gradients and d/d(uv)
         float gu = 0.0f, gvv = 0.0f;
         for (int ch = 0; ch < 3; ++ch) {
@@ -813,39 +862,13 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
             gu += g.r * du; gvv += g.r * dv;
             gtex[6] = g.r;
         }
-        float gb0 = gu * t0.x + gvv * t0.y, gb1 = gu * t1.x + gvv * t1.y, gb2 = gu * t2.x + gvv * t2.y;
-        // shading normal ns = m / |m|, m = sum b_k n_k
-        const float3 mm = n0 * b0 + n1 * b1 + n2 * b2;
-        const float inv_m = rsqrtf(dot(mm, mm));
-        const float3 nsh = mm * inv_m;
-        const float3 gm = (g.n - nsh * dot(nsh, g.n)) * inv_m;
-        gn0 = gm * b0; gn1 = gm * b1; gn2 = gm * b2;
-        gb0 += dot(n0, gm); gb1 += dot(n1, gm); gb2 += dot(n2, gm);
-        // y = sum b_k v_k
-        gv0 = gy * b0; gv1 = gy * b1; gv2 = gy * b2;
-        gb0 += dot(v0, gy); gb1 += dot(v1, gy); gb2 += dot(v2, gy);
-        // view direction o = -d / |d|
-        const float inv_d = rsqrtf(dot(ss.d, ss.d));
-        const float3 od = -ss.d * inv_d;
-        float3 gd = -(g.o - od * dot(od, g.o)) * inv_d;
-        // barycentrics from the intersection
-        const float G1 = gb1 - gb0, G2 = gb2 - gb0;
-        const float gsp = G1 * inv_det, gdq = G2 * inv_det, gdet = -(G1 * b1 + G2 * b2) * inv_det;
-        float3 gs = pv * gsp;
-        float3 gp = sv * gsp + e1 * gdet;
-        gd += qv * gdq;
-        const float3 gq = ss.d * gdq;
-        float3 ge1 = pv * gdet;
-        gs += cross(e1, gq);
-        ge1 += cross(gq, sv);
-        gd += cross(e2, gp);
-        const float3 ge2 = cross(gp, ss.d);
-        gv0 += -gs - ge1 - ge2;
-        gv1 += ge1;
-        gv2 += ge2;
+        const float gb0 = gu * t0.x + gvv * t0.y, gb1 = gu * t1.x + gvv * t1.y, gb2 = gu * t2.x + gvv * t2.y;
+        const HitChain hc = hit_chain(v0, v1, v2, n0, n1, n2, ss.d, g.n, g.o, gy, gb0, gb1, gb2);
+        gv0 = hc.gv[0]; gv1 = hc.gv[1]; gv2 = hc.gv[2];
+        gn0 = hc.gn[0]; gn1 = hc.gn[1]; gn2 = hc.gn[2];
         // d = ((sx - W/2)/f, -(sy - H/2)/f, -1)
         const float f = P.focal[0];
-        gfocal = -(gd.x * ss.d.x + gd.y * ss.d.y) / f;
+        gfocal = -(hc.gd.x * ss.d.x + hc.gd.y * ss.d.y) / f;
     }
     // vertex position and normal gradients, warp-aggregated by vertex
     {
@@ -1041,6 +1064,410 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
     const float gw = warp_sum(gf);
     if ((threadIdx.x & 31) == 0) acc_dyn[threadIdx.x >> 5] = gw;
     block_acc_flush(1, 0, 1, G.small);
+}
+
+// ---------------------------------------------------------------------------
+// boundary of the specular lobe inside triangles: the curve n_s . o = 0
+// ---------------------------------------------------------------------------
+// The lobe (App. A, Eq. brdf_spec) needs n_s . o > 0 and does not vanish as
+// n_s . o -> 0+, so the image jumps on the curve n_s . o = 0 inside
+// front-facing triangles whose interpolated normals turn away from the
+// camera.  Edge sampling (Sec. 4) meets that curve along image scanlines:
+// per pixel row and per pixel column edge_spp lines at uniform offsets (rows
+// first).  The rays of a line fill a plane through the camera centre; it cuts
+// a triangle along a chord with linear barycentrics, on which q(b) = m(b) .
+// (-p(b)) (m = sum b_i n_i, p = sum b_i v_i; q has the sign of n_s . o) is an
+// exact quadratic.  A crossing x contributes adj . (L+ - L-) G_theta |n_x| /
+// (|grad G|^2 k) on rows (|n_y| on columns), L+- the one-sided limits of the
+// radiance there, G = n_s . o at the fixed screen point, grad G its screen
+// gradient: the two families' shares n_x^2 and n_y^2 of the line integral,
+// each with a bounded weight.
+
+// Candidate triangles: in front of the camera, facing it, and q not of one
+// sign over the triangle.  q's degree-2 Bernstein coefficients over the
+// triangle (q_ii = -n_i . v_i at the corners, (q_ij + q_ji) / 2 on the edges)
+// bound it, so a triangle whose six coefficients share a strict sign has no
+// crossing.  FP64, so that it agrees with the FP64 crossings below.
+__device__ bool spec_candidate(const DevScene& S, int f) {
+    const int4 t = S.faces[f];
+    const int id[3] = {t.x, t.y, t.z};
+    double v[3][3], n[3][3];
+    for (int i = 0; i < 3; ++i) {
+        const float4 a = S.v[id[i]], b = S.vn[id[i]];
+        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z;
+        n[i][0] = b.x; n[i][1] = b.y; n[i][2] = b.z;
+    }
+    if (!(v[0][2] < 0.0 && v[1][2] < 0.0 && v[2][2] < 0.0)) return false;
+    const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+    const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+    const double nf[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    if (!(nf[0] * v[0][0] + nf[1] * v[0][1] + nf[2] * v[0][2] < 0.0)) return false;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            const double qij = -(n[i][0] * v[j][0] + n[i][1] * v[j][1] + n[i][2] * v[j][2]);
+            const double qji = -(n[j][0] * v[i][0] + n[j][1] * v[i][1] + n[j][2] * v[i][2]);
+            const double b = 0.5 * (qij + qji);
+            lo = fmin(lo, b);
+            hi = fmax(hi, b);
+        }
+    return lo <= 0.0 && hi > 0.0;
+}
+
+constexpr int SPEC_CHUNK = 1024;
+
+// per-chunk candidate counts
+__global__ void __launch_bounds__(SPEC_CHUNK) k_spec_count(const DevItem* items) {
+    __shared__ int warp_tot[SPEC_CHUNK / 32];
+    const DevItem& it = items[blockIdx.y];
+    const DevScene& S = it.S;
+    const int f = blockIdx.x * SPEC_CHUNK + threadIdx.x;
+    const bool want = !(S.flags & (FR_FLAG_NO_SPECULAR_EDGE_D | FR_FLAG_FLAT_D));
+    if ((long)blockIdx.x * SPEC_CHUNK >= S.T) return;          // block-uniform
+    const bool on = want && f < S.T && spec_candidate(S, f);
+    const unsigned b = __ballot_sync(FULL, on);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < SPEC_CHUNK / 32; ++w) t += warp_tot[w];
+        it.spec_hist[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_spec_scan(const DevItem* items) {
+    const DevItem& it = items[blockIdx.x];
+    if (threadIdx.x != 0) return;
+    const int n_chunks = (it.S.T + SPEC_CHUNK - 1) / SPEC_CHUNK;
+    int run = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const int v = it.spec_hist[c];
+        it.spec_hist[c] = run;
+        run += v;
+    }
+    *it.spec_count = run;
+}
+
+// ordered candidate list (triangle index order) with each candidate's screen
+// bounding box (x0, x1, y0, y1), widened by a hair
+__global__ void __launch_bounds__(SPEC_CHUNK) k_spec_scatter(const DevItem* items) {
+    __shared__ int warp_off[SPEC_CHUNK / 32];
+    const DevItem& it = items[blockIdx.y];
+    const DevScene& S = it.S;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int f = blockIdx.x * SPEC_CHUNK + threadIdx.x;
+    const bool want = !(S.flags & (FR_FLAG_NO_SPECULAR_EDGE_D | FR_FLAG_FLAT_D));
+    if ((long)blockIdx.x * SPEC_CHUNK >= S.T) return;          // block-uniform
+    const bool on = want && f < S.T && spec_candidate(S, f);
+    const unsigned b = __ballot_sync(FULL, on);
+    if (lane == 0) warp_off[wid] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = it.spec_hist[blockIdx.x];
+        for (int w = 0; w < SPEC_CHUNK / 32; ++w) {
+            const int v = warp_off[w];
+            warp_off[w] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    if (on) {
+        const int slot = warp_off[wid] + __popc(b & ((1u << lane) - 1u));
+        const int4 t = S.faces[f];
+        const float fl = it.P.focal[0];
+        float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+        const int id[3] = {t.x, t.y, t.z};
+        for (int i = 0; i < 3; ++i) {
+            const float4 p = S.v[id[i]];
+            const float X = 0.5f * S.W + fl * p.x / -p.z, Y = 0.5f * S.H - fl * p.y / -p.z;
+            x0 = fminf(x0, X); x1 = fmaxf(x1, X); y0 = fminf(y0, Y); y1 = fmaxf(y1, Y);
+        }
+        const float m = 1e-3f + 1e-5f * fmaxf(fabsf(x0) + fabsf(x1), fabsf(y0) + fabsf(y1));
+        it.spec_list[slot] = f;
+        it.spec_box[slot] = make_float4(x0 - m, x1 + m, y0 - m, y1 + m);
+    }
+}
+
+// Scanline `scan` of an item: (row?, coordinate c in pixels), c = (i + u) / k.
+FR_D bool spec_scanline(const DevScene& S, uint32_t iteration, uint32_t face, int scan, double& c) {
+    const int k = max(S.edge_spp, 1);
+    const bool row = scan < S.H * k;
+    const int idx = row ? scan : scan - S.H * k;
+    const Sampler sm{make_uint2(S.seed, FR_STREAM_EDGE_SPECULAR), 0xFFFFFFFFu, (uint32_t)scan, iteration, face};
+    c = ((double)idx + (double)u24(sm.block(0).x)) / (double)k;
+    return row;
+}
+
+// Crossings of the line (row?, c) with the curve inside triangle f, in order
+// along the line: screen points (x, y); returns their count (0..2).  FP64.
+FR_D int spec_roots(const DevScene& S, int f, bool row, double c, double fl, double2 out[2]) {
+    const int4 t = S.faces[f];
+    const int id[3] = {t.x, t.y, t.z};
+    double v[3][3], n[3][3];
+    for (int i = 0; i < 3; ++i) {
+        const float4 a = S.v[id[i]], b = S.vn[id[i]];
+        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z;
+        n[i][0] = b.x; n[i][1] = b.y; n[i][2] = b.z;
+    }
+    const double nrm[3] = {row ? 0.0 : 1.0, row ? 1.0 : 0.0, row ? -(c - 0.5 * S.H) / fl : (c - 0.5 * S.W) / fl};
+    double ph[3];
+    for (int i = 0; i < 3; ++i) ph[i] = nrm[0] * v[i][0] + nrm[1] * v[i][1] + nrm[2] * v[i][2];
+    double bc[2][3];
+    int ne = 0;
+    for (int e = 0; e < 3 && ne < 2; ++e) {           // chord ends: edges straddling the plane
+        const int i = e, j = e == 2 ? 0 : e + 1;
+        if ((ph[i] > 0.0) == (ph[j] > 0.0)) continue;
+        const double tt = ph[i] / (ph[i] - ph[j]);
+        bc[ne][0] = bc[ne][1] = bc[ne][2] = 0.0;
+        bc[ne][i] = 1.0 - tt;
+        bc[ne][j] = tt;
+        ++ne;
+    }
+    if (ne != 2) return 0;
+    double Q[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Q[i][j] = -(n[i][0] * v[j][0] + n[i][1] * v[j][1] + n[i][2] * v[j][2]);
+    const double dl[3] = {bc[1][0] - bc[0][0], bc[1][1] - bc[0][1], bc[1][2] - bc[0][2]};
+    double a2 = 0.0, a1 = 0.0, a0 = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            a2 += dl[i] * dl[j] * Q[i][j];
+            a1 += bc[0][i] * dl[j] * Q[i][j];
+            a0 += bc[0][i] * bc[0][j] * Q[i][j];
+        }
+    double a1b = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) a1b += dl[i] * bc[0][j] * Q[i][j];
+    a1 += a1b;
+    double sr[2];
+    int nr = 0;
+    if (a2 == 0.0) {
+        if (a1 != 0.0) sr[nr++] = -a0 / a1;
+    } else {
+        const double disc = a1 * a1 - 4.0 * a2 * a0;
+        if (disc > 0.0) {
+            const double sq = sqrt(disc);
+            const double qq = -0.5 * (a1 + (a1 >= 0.0 ? sq : -sq));
+            sr[nr++] = qq / a2;
+            sr[nr++] = a0 / qq;
+        }
+    }
+    int m = 0;
+    for (int r = 0; r < nr; ++r) {
+        if (!(sr[r] >= 0.0 && sr[r] <= 1.0)) continue;
+        double p[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < 3; ++i) {
+            const double b = bc[0][i] + sr[r] * dl[i];
+            p[0] += b * v[i][0]; p[1] += b * v[i][1]; p[2] += b * v[i][2];
+        }
+        out[m++] = row ? make_double2(0.5 * S.W + fl * p[0] / -p[2], c) : make_double2(c, 0.5 * S.H - fl * p[1] / -p[2]);
+    }
+    if (m == 2 && (row ? out[1].x < out[0].x : out[1].y < out[0].y)) {
+        const double2 tmp = out[0];
+        out[0] = out[1];
+        out[1] = tmp;
+    }
+    return m;
+}
+
+constexpr int SPEC_QUEUE = 128;          // crossings queued per warp (< 32 wait before a chunk adds <= 64)
+
+struct SpecQueue {
+    int code[SPEC_QUEUE];                // 2 * triangle + root
+    float x[SPEC_QUEUE], y[SPEC_QUEUE];
+};
+
+// Evaluate the queued crossings [head, head + n) (n <= 32), one lane each:
+// the jump of the cutoff at the crossing x is the difference of the two
+// one-sided limits of the radiance of the crossing's own triangle there (the
+// same hit, shadow rays and light samples; the view direction tilted to
+// n_s . o = +-1e-5), with no part of the continuous change across the curve
+// and nothing of a silhouette the curve may run next to; the curve is seen
+// only where that triangle is the visible surface (nothing along the camera
+// ray is nearer).  All 32 lanes call this together.
+template <bool ENV>
+FR_D void spec_eval(const DevItem& it, const SpecQueue& q, int head, int n, int scan, bool row, RtShared& sh,
+                    Stack stk, RayStats& rs, float& gfocal) {
+    const DevScene& S = it.S;
+    const DevParams& P = it.P;
+    const int lane = threadIdx.x & 31;
+    bool active = lane < n;
+    const int code = active ? q.code[(head + lane) & (SPEC_QUEUE - 1)] : 0;
+    const float X = active ? q.x[(head + lane) & (SPEC_QUEUE - 1)] : 0.0f;
+    const float Y = active ? q.y[(head + lane) & (SPEC_QUEUE - 1)] : 0.0f;
+    const int tri = code >> 1;
+    const float f = P.focal[0];
+    float3 adj = f3(0, 0, 0);
+    HitChain hc;
+    int4 fc = make_int4(0, 0, 0, 0);
+    float gx = 0.0f, gy = 0.0f, g2 = 0.0f;
+    bool front = false;
+    float3 d = f3(0, 0, 0);
+    Hit own;                        // the ray on the crossing's own triangle's plane
+    own.tri = own.slot = -1;
+    own.t = own.b1 = own.b2 = 0.0f;
+    if (active) {
+        const int pix = (int)floorf(Y) * S.W + (int)floorf(X);
+        adj = f3(it.adj[3 * (size_t)pix], it.adj[3 * (size_t)pix + 1], it.adj[3 * (size_t)pix + 2]);
+        if (adj.x == 0.0f && adj.y == 0.0f && adj.z == 0.0f) active = false;
+    }
+    if (active) {
+        // G = n_s . o at the crossing and its gradients: d/dns = o, d/do = ns
+        fc = S.faces[tri];
+        const float3 v0 = xyz(S.v[fc.x]), v1 = xyz(S.v[fc.y]), v2 = xyz(S.v[fc.z]);
+        const float3 n0 = xyz(S.vn[fc.x]), n1 = xyz(S.vn[fc.y]), n2 = xyz(S.vn[fc.z]);
+        d = f3((X - 0.5f * S.W) / f, -(Y - 0.5f * S.H) / f, -1.0f);
+        const float3 e1 = v1 - v0, e2 = v2 - v0, sv = -v0;
+        const float3 pv = cross(d, e2), qv = cross(sv, e1);
+        const float inv_det = __fdividef(1.0f, dot(e1, pv));
+        const float b1 = dot(sv, pv) * inv_det, b2 = dot(d, qv) * inv_det, b0 = 1.0f - b1 - b2;
+        const float t_own = dot(e2, qv) * inv_det;                 // along d to the triangle's plane
+        own.t = t_own;
+        own.b1 = b1;
+        own.b2 = b2;
+        own.tri = tri;
+        own.slot = __ldg(&S.slot_of[tri]);
+        const float3 mm = n0 * b0 + n1 * b1 + n2 * b2;
+        const float3 ns = mm * rsqrtf(dot(mm, mm));
+        const float3 o = -d * rsqrtf(dot(d, d));
+        front = dot(cross(e1, e2), o) > 0.0f;
+        hc = hit_chain(v0, v1, v2, n0, n1, n2, d, o, ns, f3(0, 0, 0), 0.0f, 0.0f, 0.0f);
+        // d = ((X - W/2)/f, -(Y - H/2)/f, -1): dG/dX = gd.x / f, dG/dY = -gd.y / f
+        gx = hc.gd.x / f;
+        gy = -hc.gd.y / f;
+        g2 = gx * gx + gy * gy;
+        if (!(g2 > 0.0f)) active = false;
+        if (active) {
+            // (the traversal's own distance to a grazing triangle is only good to
+            // ~1e-4 relative, so the triangle itself never hides the crossing)
+            const Hit h = trace_closest(S, ray_setup(f3(0.0f, 0.0f, 0.0f), d), 0.0f, INFINITY, stk, rs);
+            if (h.tri >= 0 && h.tri != tri && h.t < t_own * (1.0f - 1e-5f)) active = false;
+        }
+    }
+    const Sampler smp{make_uint2(S.seed, FR_STREAM_EDGE_SPECULAR), (uint32_t)code, (uint32_t)scan, it.iteration,
+                      it.face};
+    // the crossing's own triangle at x (imposed: on a grazing sliver the
+    // watertight test could reject a point of it); its shadow rays are those
+    // of the lit side
+    SampleState ss;
+    primary_state<true, false>(S, P, active, X, Y, stk, ss, rs, REC_TRACE, &own);
+    if (ss.hit) ss.lit = front;
+    uint64_t vis[2] = {0ull, 0ull};
+    for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64)                  // warp-uniform
+        vis[j0 >> 6] = shadow_mask<ENV>(S, ss, smp, 4, sh.wq[threadIdx.x >> 5], stk, rs, j0);
+    float3 Lp = f3(0.0f, 0.0f, 0.0f), Lm = f3(0.0f, 0.0f, 0.0f);
+    if (active && ss.hit) {
+        sample_material(S, P, ss);
+        const float3 om = ss.o - ss.ns * dot(ss.ns, ss.o);
+        SampleState sp = ss, sm = ss;
+        const float3 op = om + ss.ns * 1e-5f, on = om - ss.ns * 1e-5f;
+        sp.o = op * rsqrtf(dot(op, op));
+        sm.o = on * rsqrtf(dot(on, on));
+        if (S.flags & FR_FLAG_VIEW_CUTOFF_D) sm.lit = false;        // the cut-everything reading
+        for (int j0 = 0; j0 < max(S.NL, 1); j0 += 64) {
+            Lp += radiance_from<ENV>(S, P, sp, vis[j0 >> 6], smp, 4, j0);
+            Lm += radiance_from<ENV>(S, P, sm, vis[j0 >> 6], smp, 4, j0);
+        }
+    } else {
+        active = false;
+    }
+    float wg = 0.0f;
+    if (active) {
+        const float jump = adj.x * (Lp.x - Lm.x) + adj.y * (Lp.y - Lm.y) + adj.z * (Lp.z - Lm.z);
+        wg = jump * (row ? fabsf(gx) : fabsf(gy)) / (g2 * (float)max(S.edge_spp, 1));
+        if (wg == 0.0f) active = false;
+    }
+    const unsigned act = __ballot_sync(FULL, active);
+    if (active) {
+        const int vx[3] = {fc.x, fc.y, fc.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            fix64* const a[6] = {&it.G.d_v[3 * vx[k]], &it.G.d_v[3 * vx[k] + 1], &it.G.d_v[3 * vx[k] + 2],
+                                 &it.G.d_n[3 * vx[k]], &it.G.d_n[3 * vx[k] + 1], &it.G.d_n[3 * vx[k] + 2]};
+            const float v[6] = {wg * hc.gv[k].x, wg * hc.gv[k].y, wg * hc.gv[k].z,
+                                wg * hc.gn[k].x, wg * hc.gn[k].y, wg * hc.gn[k].z};
+            warp_agg_add_n<6>(a, v, (uint32_t)vx[k], act);
+        }
+        gfocal += wg * -(hc.gd.x * d.x + hc.gd.y * d.y) / f;
+    }
+}
+
+// One block per scanline of an item; its warps take the item's candidates in
+// chunks of 32 (warp w: chunks w, w + 4, ...), queue the chunk's crossings in
+// candidate order and evaluate them 32 at a time.
+template <bool ENV>
+__global__ void __launch_bounds__(RT_THREADS, 4) k_edge_specular(const DevItem* items, BlockMap map) {
+    __shared__ RtShared sh;
+    __shared__ SpecQueue sq[RT_WARPS];
+    FR_STACK_DECL
+    const int item = item_of_block(map);
+    const DevItem& it = items[item];
+    const DevScene& S = it.S;
+    block_acc_init(1);
+    const int scan = blockIdx.x - map.block0[item];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double c;
+    const bool row = spec_scanline(S, it.iteration, it.face, scan, c);
+    const double fl = (double)it.P.focal[0];
+    const int n_cand = *it.spec_count;
+    SpecQueue& q = sq[warp];
+    int head = 0, count = 0;
+    RayStats rs;
+    float gfocal = 0.0f;
+    for (int c0 = warp * 32; c0 < n_cand; c0 += RT_THREADS) {          // warp-uniform
+        const int i = c0 + lane;
+        int nc = 0;
+        double2 xs[2];
+        if (i < n_cand) {
+            const float4 box = it.spec_box[i];
+            const float cf = (float)c;
+            if (row ? (cf >= box.z && cf <= box.w) : (cf >= box.x && cf <= box.y))
+                nc = spec_roots(S, it.spec_list[i], row, c, fl, xs);
+        }
+        // keep the crossings inside the image
+        int keep = 0;
+        float kx[2], ky[2];
+        int kc[2];
+        for (int r = 0; r < nc; ++r) {
+            if (!(xs[r].x >= 0.0 && xs[r].x < S.W && xs[r].y >= 0.0 && xs[r].y < S.H)) continue;
+            const float fx = (float)xs[r].x, fy = (float)xs[r].y;
+            if (!(fx < (float)S.W && fy < (float)S.H)) continue;      // rounded onto the far edge
+            kx[keep] = fx;
+            ky[keep] = fy;
+            kc[keep] = 2 * it.spec_list[i] + r;
+            ++keep;
+        }
+        // append in candidate order
+        int before = keep;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, before, o);
+            if (lane >= o) before += v;
+        }
+        const int total = __shfl_sync(FULL, before, 31);
+        before -= keep;
+        for (int r = 0; r < keep; ++r) {
+            const int slot = (head + count + before + r) & (SPEC_QUEUE - 1);
+            q.code[slot] = kc[r];
+            q.x[slot] = kx[r];
+            q.y[slot] = ky[r];
+        }
+        count += total;
+        __syncwarp();
+        while (count >= 32) {
+            spec_eval<ENV>(it, q, head, 32, scan, row, sh, my_stack(sh), rs, gfocal);
+            head = (head + 32) & (SPEC_QUEUE - 1);
+            count -= 32;
+            __syncwarp();
+        }
+    }
+    if (count > 0) {                                                    // warp-uniform
+        spec_eval<ENV>(it, q, head, count, scan, row, sh, my_stack(sh), rs, gfocal);
+        __syncwarp();
+    }
+    flush_stats(S.counters + 6, rs);
+    const float gw = warp_sum(gfocal);
+    if (lane == 0) acc_dyn[warp] = gw;
+    block_acc_flush(1, 0, 1, it.G.small);
 }
 
 // ---------------------------------------------------------------------------
@@ -1347,6 +1774,21 @@ void launch_edge_primary(const DevItem* items, const BlockMap& map, bool env, cu
     else
         k_edge_primary<false><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
     fr_count_launches(1);
+}
+
+// Candidates of the specular-boundary term (ordered list per item), then one
+// block per scanline of each item (`map`).
+void launch_edge_specular(const DevItem* items, int n, int T, const BlockMap& map, bool env, cudaStream_t st) {
+    if (n <= 0 || map_blocks(map) == 0) return;
+    const int n_chunks = blocks_for(T, SPEC_CHUNK);
+    k_spec_count<<<dim3(n_chunks, n), SPEC_CHUNK, 0, st>>>(items);
+    k_spec_scan<<<n, 32, 0, st>>>(items);
+    k_spec_scatter<<<dim3(n_chunks, n), SPEC_CHUNK, 0, st>>>(items);
+    if (env)
+        k_edge_specular<true><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
+    else
+        k_edge_specular<false><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
+    fr_count_launches(4);
 }
 
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st) {

@@ -46,7 +46,7 @@ constexpr float W_BOX = 1.0f;
 constexpr float ALPHA1 = 1.0f;                          // weight of E_land in E_d
 constexpr float ROUGH_LO = 0.02f, ROUGH_HI = 1.5f;      // roughness range after each step (keeps D finite)
 constexpr float STAGE_LO = 1e-3f, STAGE_HI = 1e3f;      // floor of d, a, p after each step (keeps d^2/a finite)
-constexpr uint32_t STAGE2_FLAGS = FR_FLAG_NO_PRIMARY_EDGE | FR_FLAG_NO_SHADOW_EDGE;
+constexpr uint32_t STAGE2_FLAGS = FR_FLAG_NO_PRIMARY_EDGE | FR_FLAG_NO_SHADOW_EDGE | FR_FLAG_NO_SPECULAR_EDGE;
 constexpr float ADAM_B1 = 0.9f, ADAM_B2 = 0.999f, ADAM_EPS = 1e-8f;
 
 // Parameter segments of a request's parameter vector (and of its gradient and

@@ -9,6 +9,7 @@
 #define FR_FLAG_NO_INTERIOR_D 16u
 #define FR_FLAG_NO_PRIMARY_EDGE_D 32u
 #define FR_FLAG_NO_SHADOW_EDGE_D 64u
+#define FR_FLAG_NO_SPECULAR_EDGE_D 2048u
 #define FR_FLAG_VIEW_CUTOFF_D 1024u
 #define FR_LIGHT_ENV_D 3
 

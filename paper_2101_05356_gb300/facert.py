@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libfacert.so")
 FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EOVERFLOW, FR_ETIMEOUT = 0, 1, 2, 3, 4, 5
 FLAG_GGX, FLAG_SCHLICK_LINEAR, FLAG_FLAT = 1, 2, 4
 FLAG_NO_INTERIOR, FLAG_NO_PRIMARY_EDGE, FLAG_NO_SHADOW_EDGE = 16, 32, 64
+FLAG_NO_SPECULAR_EDGE = 2048
 FLAG_MORPH_BF16 = 128
 FLAG_RECOMPUTE = 256
 FLAG_LBVH = 512

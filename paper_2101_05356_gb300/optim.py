@@ -27,7 +27,7 @@ from . import facert
 ALPHA1 = 1.0             # weight of E_land in E_d (Sec. 5)
 LR = dict(light=1e-3, identity=1e-2, expression=1e-3, rot=1e-3, trans=1e-3, texture=5e-3, albedo=2e-2)
 W = dict(w_i=0.0025, w_c=0.0025, w_s=0.0025, w1=0.01, w2=0.3, w3=0.3, w4=0.0002, box=1.0)
-STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE
+STAGE2_FLAGS = facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE | facert.FLAG_NO_SPECULAR_EDGE
 # hard floor on d, a and p after each update (keeps d^2/a finite; the soft boxes do the rest)
 STAGE_CLAMP = (1e-3, 1e3)
 

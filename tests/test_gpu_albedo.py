@@ -91,7 +91,8 @@ def test_loss_gradient_reaches_beta_and_gamma():
     from paper_2101_05356_gb300 import facert
     sc = synth.make_scene("c1", albedo_k=16)
     pr = synth.random_params(sc, 3)
-    r = facert.Renderer(sc, flags=facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE)
+    r = facert.Renderer(sc, flags=facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE |
+                         facert.FLAG_NO_SPECULAR_EDGE)
     betas, gammas = _coefs(sc, 1, 4)
     dp = r.device_params(pr)
     facert.fr_albedo_morph(r.ctx, [torch.as_tensor(betas[0]).cuda()], [torch.as_tensor(gammas[0]).cuda()],

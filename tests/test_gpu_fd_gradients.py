@@ -1,5 +1,6 @@
 """The autograd.Function's gradients (interior + primary-visibility +
-shadow-boundary terms, through the hand-written adjoint) against central
+shadow-boundary terms + the boundary term of the specular lobe's cutoff
+inside triangles, through the hand-written adjoint) against central
 finite differences of the GPU's own rendered image with common random
 numbers: the derivative of the expected image, so the two must agree within
 their combined Monte Carlo error over repeated Philox iterations, while the
@@ -38,7 +39,8 @@ def _z_scores(sc, pr, fields):
     W = _weights(sc)
     out = {}
     for interior_only in (False, True):
-        flags = (facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE) if interior_only else 0
+        flags = (facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE |
+                 facert.FLAG_NO_SPECULAR_EDGE) if interior_only else 0
         r = facert.Renderer(sc, flags=flags)
         dp = r.device_params(pr)
         grads = {f: [] for f in fields}
@@ -94,14 +96,10 @@ def test_autograd_gradient_matches_finite_differences(case):
     z = _z_scores(sc, pr, fields)
     print(case, {"%s[%d]" % (f[0], f[1]): (round(a, 2), round(b, 2)) for f, (a, b) in z.items()})
     for f, (z_full, _) in z.items():
-        if f[0] == "focal":
-            continue
         assert abs(z_full) <= 3.5, (f, z_full)
     assert max(abs(z_int) for _, z_int in z.values()) > 6.0         # the boundary terms matter here
     if case == "face":
-        # the specular lobe does not vanish at grazing view (Walter's G1 over n.o tends to about
-        # 3.5 / r), so it keeps a jump on the curve n_s.o = 0 inside the front-facing triangles along
-        # the silhouette whose interpolated normals turn away; edge sampling does not sample that
-        # curve, and zooming moves it most: the focal-length gradient stays within a few percent
+        # zooming moves the curve n_s.o = 0 inside the silhouette's front-facing triangles most (the
+        # specular lobe jumps there): with its boundary term the focal-length gradient is within 3%
         f = ("focal", 0, 0.2)
-        assert abs(_MEANS[f][1] - _MEANS[f][0]) <= 0.06 * abs(_MEANS[f][0]), _MEANS[f]
+        assert abs(_MEANS[f][1] - _MEANS[f][0]) <= 0.03 * abs(_MEANS[f][0]), _MEANS[f]

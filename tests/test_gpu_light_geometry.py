@@ -73,8 +73,9 @@ def _compare(gg, go, groups, rtol=1e-3):
 def test_light_geometry_gradient_parity(name, term):
     from paper_2101_05356_gb300 import facert
     sc, pr = _case(name)
-    flags = {"interior": facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE,
-             "shadow": facert.FLAG_NO_INTERIOR | facert.FLAG_NO_PRIMARY_EDGE, "all": 0}[term]
+    nse = facert.FLAG_NO_SPECULAR_EDGE
+    flags = {"interior": facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE | nse,
+             "shadow": facert.FLAG_NO_INTERIOR | facert.FLAG_NO_PRIMARY_EDGE | nse, "all": 0}[term]
     terms = {"interior": oracle.TERM_INTERIOR, "shadow": oracle.TERM_SHADOW, "all": oracle.TERM_ALL}[term]
     r = facert.Renderer(sc, flags=flags)
     dp = r.device_params(pr)
