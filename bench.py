@@ -57,13 +57,13 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is recorded beside the kernel's profile summary.
-TRAFFIC = {"k_forward": {"bytes": 26555392 + 17296896,
-                         "sources_sha256": "6abde9074a2c3fc90f3edec191dcb1a6c7a66901309a7464006483b8d878690b"}}
+TRAFFIC = {"k_forward": {"bytes": 26632960 + 17365248,
+                         "sources_sha256": "da385f1a0bb4c00d134bed0ec01d9f82f1b27040b7f7399facea07c2a1cbaa4f"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 # Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
 # valid while its sources hash to `sources_sha256`.
-ISSUE = {"k_forward": {"frac": 0.6976,
-                       "sources_sha256": "6abde9074a2c3fc90f3edec191dcb1a6c7a66901309a7464006483b8d878690b"}}
+ISSUE = {"k_forward": {"frac": 0.6992,
+                       "sources_sha256": "da385f1a0bb4c00d134bed0ec01d9f82f1b27040b7f7399facea07c2a1cbaa4f"}}
 FP32_LANES_PER_SM = 128
 
 
