@@ -73,10 +73,11 @@ typedef int32_t fr_status;
  * light-visibility words per camera sample (20 bytes).  When the context's
  * width * height * spp records fit, a fused step's forward writes them and its
  * adjoint reads them instead of re-tracing.  Larger images are split into equal
- * tiles that fit (whole pixels, whole 128-sample blocks): for each tile the
- * adjoint recomputes the records with a visibility-only forward pass (the same
- * Philox counters, no shading) and then reads them.  The gradient is the same
- * either way. */
+ * tiles that fit (whole pixels, whole 128-sample blocks): the forward keeps the
+ * records of the image's last tile, and the adjoint, from the last tile to the
+ * first, reads those and recomputes every other tile's records with a
+ * visibility-only forward pass (the same Philox counters, no shading) before
+ * reading them.  The gradient is the same either way. */
 #define FR_RECORDS_BUDGET (256u << 20)
 
 /* emitter types in light records */
@@ -272,8 +273,9 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
  * g != NULL) fr_backward with the loss adjoint.  loss is a device double.
  * Within the step the adjoint reuses the forward's per-sample hit records
  * (hit triangle and shadow visibility) when they fit FR_RECORDS_BUDGET, else
- * recomputes them tile by tile; with FR_FLAG_RECOMPUTE it re-traces every
- * sample inside the adjoint kernel instead.  The gradient is the same either
+ * those of the image's last tile and recomputes the others tile by tile; with
+ * FR_FLAG_RECOMPUTE it re-traces every sample inside the adjoint kernel
+ * instead.  The gradient is the same either
  * way. */
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,

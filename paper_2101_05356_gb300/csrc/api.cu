@@ -49,6 +49,7 @@ struct Slot {
     float4* spec_box = nullptr;
     int* spec_hist = nullptr;
     int* spec_count = nullptr;
+    uint8_t* spec_flag = nullptr;
     int32_t* rec_tri = nullptr;      // hit records: a whole image, or one tile of a larger one
     uint64_t* rec_vis = nullptr;
     long rec_cap = 0;                // camera samples the record buffer holds
@@ -181,6 +182,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     const Slot& sl = c->slots[k];
     DevItem it;
     std::memset(&it, 0, sizeof(it));
+    it.rec_from = -1;                       // the forward keeps no records unless set below
     DevScene& s = it.S;
     s.N = c->N; s.T = c->T; s.K = c->K; s.NL = c->NL; s.E = c->E;
     s.W = a.W; s.H = a.H; s.spp = a.spp; s.M = c->cfg.tex_size; s.edge_spp = a.edge_spp;
@@ -248,6 +250,7 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
     it.spec_box = sl.spec_box;
     it.spec_hist = sl.spec_hist;
     it.spec_count = sl.spec_count;
+    it.spec_flag = sl.spec_flag;
     // hit records: a fused step's forward writes them when the whole image fits
     // the buffer; otherwise the adjoint recomputes them tile by tile into it.
     // FR_FLAG_RECOMPUTE keeps the adjoint re-tracing every sample instead.
@@ -255,7 +258,12 @@ DevItem make_item(const fr_ctx* c, int k, const ItemArgs& a) {
         it.rec_tri = sl.rec_tri;
         it.rec_vis = sl.rec_vis;
         it.rec_cap = c->rec_tile > 0 ? std::min(c->rec_tile, sl.rec_cap) : sl.rec_cap;
-        it.rec_full = a.records && (long)a.W * a.H * a.spp <= it.rec_cap ? 1 : 0;
+        const long total = (long)a.W * a.H * a.spp;
+        it.rec_full = a.records && total <= it.rec_cap ? 1 : 0;
+        // a larger image: the forward keeps the records of its last tile, which
+        // the adjoint (walking the tiles from the last) reads before it
+        // recomputes the others into the same buffer
+        it.rec_from = a.records ? (total - 1) / it.rec_cap * it.rec_cap : -1;
     }
     it.iteration = a.iteration;
     it.face = a.face;
@@ -344,7 +352,8 @@ void morph_adjoint(fr_ctx* c, int n, cudaStream_t st) {
         t.g[k] = c->slots[k].d_vmodel;
         t.g_coef[k] = c->h_items[k].g_coef;
     }
-    launch_linear_adjoint(c->shape.basis, c->shape.ld, c->shape.rows, c->shape.K, t, c->shape.part, st);
+    const LinearAdjModel md{c->shape.basis, c->shape.ld, c->shape.rows, c->shape.K, c->shape.part, t};
+    launch_linear_adjoint(&md, 1, st);
 }
 
 // Upload a linear model (host mean [rows], basis [K][rows]) and build its
@@ -440,17 +449,20 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
         // asked for it) re-tracing in the adjoint itself
         launch_adjoint(c->d_items, map_of(c, n, false), c->NL, all_full, any_stage, env, 0, st);
     } else {
-        // recomputed records: per tile of `cap` camera samples, a records-only
-        // forward pass over the items whose forward did not record them, then
-        // the recorded adjoint over the same tile of every item
+        // recomputed records: per tile of `cap` camera samples, from the last
+        // tile to the first, a records-only forward pass over the items whose
+        // forward did not keep that tile's records (it kept each image's last
+        // tile, the first this order meets), then the recorded adjoint over the
+        // same tile of every item
         for (int k = 0; k < n; ++k) {
             const DevScene& s = c->h_items[k].S;
             n_tiles = std::max(n_tiles, ((long)s.W * s.H * s.spp + cap - 1) / cap);
         }
-        for (long t = 0; t < n_tiles; ++t) {
+        for (long t = n_tiles - 1; t >= 0; --t) {
             const long q0 = t * cap;
-            launch_forward(c->d_items, tile_map(c, n, q0, cap, [](const DevItem& it) { return !it.rec_full; }), env,
-                           q0, true, st);
+            launch_forward(c->d_items,
+                           tile_map(c, n, q0, cap, [q0](const DevItem& it) { return !it.rec_full && it.rec_from != q0; }),
+                           env, q0, true, st);
             launch_adjoint(c->d_items, tile_map(c, n, q0, cap, [](const DevItem&) { return true; }), c->NL, true,
                            any_stage, env, q0, st);
         }
@@ -531,6 +543,7 @@ fr_status alloc_slot(fr_ctx* c, Slot& sl) {
     TRY(dalloc(c, &sl.spec_box, (size_t)T));
     TRY(dalloc(c, &sl.spec_hist, (size_t)(T + 1023) / 1024 + 1));
     TRY(dalloc(c, &sl.spec_count, 1));
+    TRY(dalloc(c, &sl.spec_flag, (size_t)T));
     // hit records (triangle + two visibility words per camera sample): the whole
     // image when it fits FR_RECORDS_BUDGET, else equal tiles of it that do, in
     // whole pixels and whole 128-thread blocks (a multiple of max(128, spp))
@@ -805,7 +818,9 @@ fr_status fr_albedo_adjoint(fr_ctx* c, int32_t n, const float* const* g_diffuse,
     if (n < 1 || n > c->max_batch) return fail(c, FR_EINVAL, "1 <= n <= max_batch faces required");
     const float* const* gs[2] = {g_diffuse, g_specular};
     float* const* outs[2] = {g_beta, g_gamma};
-    for (int q = 0; q < 2; ++q) {
+    LinearAdjModel md[2];
+    int n_md = 0;
+    for (int q = 0; q < 2; ++q) {                      // both albedos in one launch
         const LinearModel& m = c->albedo[q];
         if (!outs[q] || m.K == 0) continue;
         if (!gs[q]) return fail(c, FR_EINVAL, "null texture-gradient array");
@@ -816,8 +831,9 @@ fr_status fr_albedo_adjoint(fr_ctx* c, int32_t n, const float* const* g_diffuse,
             t.g[k] = gs[q][k];
             t.g_coef[k] = outs[q][k];
         }
-        launch_linear_adjoint(m.basis, m.ld, m.rows, m.K, t, m.part, S_(stream));
+        md[n_md++] = LinearAdjModel{m.basis, m.ld, m.rows, m.K, m.part, t};
     }
+    launch_linear_adjoint(md, n_md, S_(stream));
     CK(c, cudaGetLastError());
     return FR_OK;
 }

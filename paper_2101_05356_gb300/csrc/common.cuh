@@ -224,11 +224,14 @@ struct DevItem {
     uint64_t* rec_vis;      // [rec_cap][2] visibility words, lights 0..63 and 64..127
     long rec_cap;           // camera samples the record buffer holds (a tile of the image)
     int rec_full;           // this call's forward writes the records of the whole image (it fits)
+    long rec_from;          // the forward writes the records of samples >= rec_from (0 with rec_full,
+                            // else the first sample of the image's last tile; -1: none)
     int* edge_perm;         // processing order of the primary-edge samples (null: index order)
     int* spec_list;         // candidate triangles of the specular-boundary term [T] (ordered)
     float4* spec_box;       // their screen boxes (x0, x1, y0, y1) [T]
     int* spec_hist;         // per-chunk candidate counts, then offsets [ceil(T / 1024)]
     int* spec_count;        // [1]
+    uint8_t* spec_flag;     // each triangle a candidate? [T]
     float *g_coef, *g_rot, *g_trans, *g_focal, *g_light;   // caller gradient outputs (may be null)
     float *g_light_d, *g_light_a, *g_light_p;            // light stage geometry gradients (may be null)
     float* g_env;                                         // environment radiance gradient (may be null)

@@ -39,8 +39,15 @@ struct LinearAdjTable {
 int linear_adj_chunks(int rows);         // size of the adjoint's FP64 partials: n * K * chunks
 void launch_linear(const float* mean, const float* basis, int ld, int rows, int K, const LinearTable& t,
                    cudaStream_t st);
-void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const LinearAdjTable& t, double* part,
-                           cudaStream_t st);
+// One linear model's transpose: part = its FP64 partials [linear_adj_chunks(rows)][FR_MAX_BATCH][K].
+struct LinearAdjModel {
+    const float* basis;
+    int ld, rows, K;
+    double* part;
+    LinearAdjTable t;
+};
+// g_coef_b += basis^T g_b for every model (at most two per launch, the same faces).
+void launch_linear_adjoint(const LinearAdjModel* models, int n_models, cudaStream_t st);
 
 // morph_tc.cu: the same forward as one BF16 tensor-core GEMM over the batch
 // (tiles: the basis as [ceil(rows / 128)][128][Kp] BF16 operand tiles); one

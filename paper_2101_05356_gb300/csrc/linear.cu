@@ -82,11 +82,32 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(const float* __restrict_
 // below, which keeps that order, gives a face's gradient bitwise the same
 // alone and in a batch.
 constexpr int ADJ_ROWS4 = 256;
+
+// The models of one transpose launch (up to two: the two statistical albedos
+// share one).  start[m] is model m's first block (first pass of a batch) or
+// first warp item (one face); the kernels read the table in place.
+struct AdjLaunch {
+    int n_models;
+    int start[3];
+    const float* basis[2];
+    int ld[2], rows[2], K[2], chunks[2];
+    double* part[2];
+    LinearAdjTable t[2];
+};
+
+template <int NM>
+__device__ __forceinline__ int adj_model(const AdjLaunch& L, long x) {
+    return (NM > 1 && x >= L.start[1]) ? 1 : 0;
+}
 template <int G, int KG, int MIN_BLOCKS>
-__global__ void __launch_bounds__(LIN_THREADS, MIN_BLOCKS) k_linear_adj_part(const float* __restrict__ basis, int ld,
-                                                                   int rows, int K, LinearAdjTable t, double* part) {
+__global__ void __launch_bounds__(LIN_THREADS, MIN_BLOCKS) k_linear_adj_part(const __grid_constant__ AdjLaunch L) {
     __shared__ float4 gs[G][ADJ_ROWS4];
-    const int chunk = blockIdx.x, b0 = blockIdx.y * G;
+    const int m = adj_model<2>(L, blockIdx.x);
+    const float* __restrict__ basis = L.basis[m];
+    const int ld = L.ld[m], rows = L.rows[m], K = L.K[m];
+    const LinearAdjTable& t = L.t[m];
+    double* part = L.part[m];
+    const int chunk = blockIdx.x - L.start[m], b0 = blockIdx.y * G;
     const int nb_ = min(G, t.n - b0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rows4 = (rows + 3) / 4, lo = chunk * ADJ_ROWS4;
@@ -152,11 +173,16 @@ __global__ void __launch_bounds__(LIN_THREADS, MIN_BLOCKS) k_linear_adj_part(con
 // it is an L1 hit after the first), which leaves no shared staging to balance
 // over the block's warps.
 template <int KG>
-__global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_one(const float* __restrict__ basis, int ld, int rows,
-                                                                int K, LinearAdjTable t, double* part, int n_chunks) {
+__global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_one(const __grid_constant__ AdjLaunch L) {
     const int lane = threadIdx.x & 31;
+    const long gitem = (long)blockIdx.x * (LIN_THREADS / 32) + (threadIdx.x >> 5);
+    const int m = adj_model<1>(L, gitem);       // one model per launch (see the launcher)
+    const float* __restrict__ basis = L.basis[m];
+    const int ld = L.ld[m], rows = L.rows[m], K = L.K[m], n_chunks = L.chunks[m];
+    const LinearAdjTable& t = L.t[m];
+    double* part = L.part[m];
     const int n_kg = (K + KG - 1) / KG;
-    const long item = (long)blockIdx.x * (LIN_THREADS / 32) + (threadIdx.x >> 5);
+    const long item = gitem - L.start[m];
     if (item >= (long)n_chunks * n_kg || !t.g_coef[0]) return;      // warp-uniform
     const int chunk = (int)(item / n_kg), k0 = (int)(item % n_kg) * KG, nk = min(KG, K - k0);
     const int rows4 = (rows + 3) / 4, lo = chunk * ADJ_ROWS4;
@@ -198,9 +224,12 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear_adj_one(const float* __r
 // FIN_K partials), then a fixed tree over the streams: a fixed order, so the
 // result does not depend on scheduling.
 constexpr int FIN_THREADS = 1024, FIN_K = 8, FIN_STREAMS = FIN_THREADS / FIN_K;
-__global__ void __launch_bounds__(FIN_THREADS) k_linear_adj_finish(const double* __restrict__ part, int K,
-                                                                   int n_chunks, LinearAdjTable t) {
+__global__ void __launch_bounds__(FIN_THREADS) k_linear_adj_finish(const __grid_constant__ AdjLaunch L) {
     __shared__ double ws[FIN_STREAMS][FIN_K];
+    const int m = blockIdx.z;
+    const double* __restrict__ part = L.part[m];
+    const int K = L.K[m], n_chunks = L.chunks[m];
+    const LinearAdjTable& t = L.t[m];
     const int kk = threadIdx.x % FIN_K, stream = threadIdx.x / FIN_K;
     const int k = blockIdx.x * FIN_K + kk, b = blockIdx.y;
     double s = 0.0;
@@ -238,9 +267,25 @@ void launch_linear(const float* mean, const float* basis, int ld, int rows, int 
     fr_count_launches(1);
 }
 
-void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const LinearAdjTable& t, double* part,
-                           cudaStream_t st) {
-    if (t.n <= 0 || K <= 0 || rows <= 0) return;
+void launch_linear_adjoint(const LinearAdjModel* models, int n_models, cudaStream_t st) {
+    AdjLaunch L;
+    L.n_models = 0;
+    int n = 0, kmax = 0;
+    for (int q = 0; q < n_models && L.n_models < 2; ++q) {
+        const LinearAdjModel& md = models[q];
+        if (md.t.n <= 0 || md.K <= 0 || md.rows <= 0) continue;
+        const int m = L.n_models++;
+        L.basis[m] = md.basis;
+        L.ld[m] = md.ld;
+        L.rows[m] = md.rows;
+        L.K[m] = md.K;
+        L.chunks[m] = linear_adj_chunks(md.rows);
+        L.part[m] = md.part;
+        L.t[m] = md.t;
+        n = md.t.n;                                   // the same faces for every model of a launch
+        kmax = std::max(kmax, md.K);
+    }
+    if (L.n_models == 0) return;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -248,21 +293,30 @@ void launch_linear_adjoint(const float* basis, int ld, int rows, int K, const Li
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    const int n_chunks = linear_adj_chunks(rows), n_groups = nb(t.n, LIN_GROUP);
-    // batches: split the columns over grid.z until about eight blocks per SM are in
-    // flight (measured on GB300, albedo batch 8: two columns per warp, five blocks
-    // per SM and the k-split 0.183 ms against 0.203 ms for four columns at three)
-    auto split = [&](int kg_cols) {
-        const int most = nb(nb(K, kg_cols), LIN_THREADS / 32);
-        return std::max(1, std::min(most, nb(8L * sms, n_chunks * n_groups)));
-    };
-    if (t.n == 1) {
-        const long warps = (long)n_chunks * nb(K, 8);
-        k_linear_adj_one<8><<<nb(warps, LIN_THREADS / 32), LIN_THREADS, 0, st>>>(basis, ld, rows, K, t, part, n_chunks);
+    const int n_groups = nb(n, LIN_GROUP);
+    L.start[0] = 0;
+    if (n == 1) {
+        // one launch per model: the model's table is then constant in the kernel
+        // (48 registers; selecting the model per warp took 57 and measured slower)
+        for (int m = 0; m < L.n_models; ++m) {
+            AdjLaunch L1 = L;
+            L1.n_models = 1;
+            L1.basis[0] = L.basis[m]; L1.ld[0] = L.ld[m]; L1.rows[0] = L.rows[m]; L1.K[0] = L.K[m];
+            L1.chunks[0] = L.chunks[m]; L1.part[0] = L.part[m]; L1.t[0] = L.t[m];
+            L1.start[0] = 0;
+            L1.start[1] = L.chunks[m] * nb(L.K[m], 8);
+            k_linear_adj_one<8><<<nb(L1.start[1], LIN_THREADS / 32), LIN_THREADS, 0, st>>>(L1);
+        }
+        fr_count_launches(L.n_models - 1);
     } else {
-        k_linear_adj_part<LIN_GROUP, 2, 5><<<dim3(n_chunks, n_groups, split(2)), LIN_THREADS, 0, st>>>(
-            basis, ld, rows, K, t, part);
+        for (int m = 0; m < L.n_models; ++m) L.start[m + 1] = L.start[m] + L.chunks[m];
+        // split the columns over grid.z until about eight blocks per SM are in flight
+        // (measured on GB300, albedo batch 8: two columns per warp, five blocks per SM
+        // and the k-split 0.183 ms against 0.203 ms for four columns at three)
+        const int most = nb(nb(kmax, 2), LIN_THREADS / 32);
+        const int z = std::max(1, std::min(most, nb(8L * sms, (long)L.start[L.n_models] * n_groups)));
+        k_linear_adj_part<LIN_GROUP, 2, 5><<<dim3(L.start[L.n_models], n_groups, z), LIN_THREADS, 0, st>>>(L);
     }
-    k_linear_adj_finish<<<dim3(nb(K, FIN_K), t.n), FIN_THREADS, 0, st>>>(part, K, n_chunks, t);
+    k_linear_adj_finish<<<dim3(nb(kmax, FIN_K), n, L.n_models), FIN_THREADS, 0, st>>>(L);
     fr_count_launches(2);
 }

@@ -390,8 +390,9 @@ FR_D float group_sum(float v, int width) {
 // Camera samples [q0, q0 + the block map's count) of each item.  records_only
 // (a tile of the adjoint's recomputed records): trace the camera ray and the
 // shadow rays, write the hit records of the tile at q - q0, and shade
-// nothing.  Otherwise: the forward render, writing the records of the whole
-// image when it.rec_full (q0 = 0).
+// nothing.  Otherwise: the forward render, writing the records of samples
+// q >= it.rec_from at q - it.rec_from (the whole image when it fits the
+// record buffer, else its last tile; it.rec_from < 0: none).
 template <bool ENV>
 __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const DevItem* items, BlockMap map,
                                                                            long q0, int records_only) {
@@ -433,9 +434,9 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
         mask_rec[2 * q] = vis[0];
         mask_rec[2 * q + 1] = vis[1];
     }
-    if (valid && it.rec_full) {
-        it.rec_tri[q] = ss.tri;
-        reinterpret_cast<ulonglong2*>(it.rec_vis)[q] = make_ulonglong2(vis[0], vis[1]);
+    if (valid && it.rec_from >= 0 && q >= it.rec_from) {
+        it.rec_tri[q - it.rec_from] = ss.tri;
+        reinterpret_cast<ulonglong2*>(it.rec_vis)[q - it.rec_from] = make_ulonglong2(vis[0], vis[1]);
     }
     // per-pixel mean: lanes of one pixel summed in a fixed tree order; above
     // 32 spp the warps of one pixel (within this block) add their sums in warp
@@ -1087,15 +1088,14 @@ __global__ void __launch_bounds__(RT_THREADS, FR_EDGE_MIN_BLOCKS) k_edge_primary
 // sign over the triangle.  q's degree-2 Bernstein coefficients over the
 // triangle (q_ii = -n_i . v_i at the corners, (q_ij + q_ji) / 2 on the edges)
 // bound it, so a triangle whose six coefficients share a strict sign has no
-// crossing.  FP64, so that it agrees with the FP64 crossings below.
-__device__ bool spec_candidate(const DevScene& S, int f) {
-    const int4 t = S.faces[f];
-    const int id[3] = {t.x, t.y, t.z};
+// crossing.  Decided in FP64 (so that it agrees with the FP64 crossings
+// below); FP32 first, taken whenever it is farther from zero than a generous
+// bound on its error (64 u times the sum of the magnitudes of the products).
+__device__ bool spec_candidate64(const float4 (&p)[3], const float4 (&q)[3]) {
     double v[3][3], n[3][3];
     for (int i = 0; i < 3; ++i) {
-        const float4 a = S.v[id[i]], b = S.vn[id[i]];
-        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z;
-        n[i][0] = b.x; n[i][1] = b.y; n[i][2] = b.z;
+        v[i][0] = p[i].x; v[i][1] = p[i].y; v[i][2] = p[i].z;
+        n[i][0] = q[i].x; n[i][1] = q[i].y; n[i][2] = q[i].z;
     }
     if (!(v[0][2] < 0.0 && v[1][2] < 0.0 && v[2][2] < 0.0)) return false;
     const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
@@ -1114,9 +1114,39 @@ __device__ bool spec_candidate(const DevScene& S, int f) {
     return lo <= 0.0 && hi > 0.0;
 }
 
+__device__ bool spec_candidate(const DevScene& S, int f) {
+    const int4 t = S.faces[f];
+    const float4 p[3] = {S.v[t.x], S.v[t.y], S.v[t.z]};
+    const float4 q[3] = {S.vn[t.x], S.vn[t.y], S.vn[t.z]};
+    if (!(p[0].z < 0.0f && p[1].z < 0.0f && p[2].z < 0.0f)) return false;
+    constexpr float U64 = 64.0f * 5.9604645e-8f;
+    const float3 e1 = xyz(p[1]) - xyz(p[0]), e2 = xyz(p[2]) - xyz(p[0]), v0 = xyz(p[0]);
+    const float3 nf = cross(e1, e2);
+    const float3 na = f3(fabsf(e1.y * e2.z) + fabsf(e1.z * e2.y), fabsf(e1.z * e2.x) + fabsf(e1.x * e2.z),
+                         fabsf(e1.x * e2.y) + fabsf(e1.y * e2.x));
+    const float fv = dot(nf, v0);
+    const float fe = U64 * (na.x * fabsf(v0.x) + na.y * fabsf(v0.y) + na.z * fabsf(v0.z));
+    if (fv > fe) return false;                                  // faces away, surely
+    if (!(fv < -fe)) return spec_candidate64(p, q);
+    float lo = INFINITY, hi = -INFINITY, err = 0.0f;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            const float3 ni = xyz(q[i]), nj = xyz(q[j]), vi = xyz(p[i]), vj = xyz(p[j]);
+            const float b = -0.5f * (dot(ni, vj) + dot(nj, vi));
+            const float m = 0.5f * (fabsf(ni.x * vj.x) + fabsf(ni.y * vj.y) + fabsf(ni.z * vj.z) +
+                                    fabsf(nj.x * vi.x) + fabsf(nj.y * vi.y) + fabsf(nj.z * vi.z));
+            lo = fminf(lo, b);
+            hi = fmaxf(hi, b);
+            err = fmaxf(err, U64 * m);
+        }
+    if (lo > err || hi < -err) return false;                    // one strict sign, surely
+    if (lo < -err && hi > err) return true;
+    return spec_candidate64(p, q);
+}
+
 constexpr int SPEC_CHUNK = 1024;
 
-// per-chunk candidate counts
+// per-chunk candidate counts; each triangle's flag kept for the scatter
 __global__ void __launch_bounds__(SPEC_CHUNK) k_spec_count(const DevItem* items) {
     __shared__ int warp_tot[SPEC_CHUNK / 32];
     const DevItem& it = items[blockIdx.y];
@@ -1125,6 +1155,7 @@ __global__ void __launch_bounds__(SPEC_CHUNK) k_spec_count(const DevItem* items)
     const bool want = !(S.flags & (FR_FLAG_NO_SPECULAR_EDGE_D | FR_FLAG_FLAT_D));
     if ((long)blockIdx.x * SPEC_CHUNK >= S.T) return;          // block-uniform
     const bool on = want && f < S.T && spec_candidate(S, f);
+    if (f < S.T) it.spec_flag[f] = on ? 1 : 0;
     const unsigned b = __ballot_sync(FULL, on);
     if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = __popc(b);
     __syncthreads();
@@ -1135,17 +1166,27 @@ __global__ void __launch_bounds__(SPEC_CHUNK) k_spec_count(const DevItem* items)
     }
 }
 
+// exclusive scan of the chunk counts: one warp, each lane a run of chunks
 __global__ void k_spec_scan(const DevItem* items) {
     const DevItem& it = items[blockIdx.x];
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     const int n_chunks = (it.S.T + SPEC_CHUNK - 1) / SPEC_CHUNK;
-    int run = 0;
-    for (int c = 0; c < n_chunks; ++c) {
+    const int per = (n_chunks + 31) / 32, c0 = lane * per, c1 = min(n_chunks, c0 + per);
+    int own = 0;
+    for (int c = c0; c < c1; ++c) own += it.spec_hist[c];
+    int incl = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int run = incl - own;
+    for (int c = c0; c < c1; ++c) {
         const int v = it.spec_hist[c];
         it.spec_hist[c] = run;
         run += v;
     }
-    *it.spec_count = run;
+    if (lane == 31) *it.spec_count = incl;
 }
 
 // ordered candidate list (triangle index order) with each candidate's screen
@@ -1156,9 +1197,8 @@ __global__ void __launch_bounds__(SPEC_CHUNK) k_spec_scatter(const DevItem* item
     const DevScene& S = it.S;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int f = blockIdx.x * SPEC_CHUNK + threadIdx.x;
-    const bool want = !(S.flags & (FR_FLAG_NO_SPECULAR_EDGE_D | FR_FLAG_FLAT_D));
     if ((long)blockIdx.x * SPEC_CHUNK >= S.T) return;          // block-uniform
-    const bool on = want && f < S.T && spec_candidate(S, f);
+    const bool on = f < S.T && it.spec_flag[f];
     const unsigned b = __ballot_sync(FULL, on);
     if (lane == 0) warp_off[wid] = __popc(b);
     __syncthreads();
