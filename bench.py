@@ -57,13 +57,13 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is recorded beside the kernel's profile summary.
-TRAFFIC = {"k_forward": {"bytes": 26632960 + 17365248,
-                         "sources_sha256": "da385f1a0bb4c00d134bed0ec01d9f82f1b27040b7f7399facea07c2a1cbaa4f"}}
+TRAFFIC = {"k_forward": {"bytes": 26589184 + 17825792,
+                         "sources_sha256": "2b52663ae0d90390b0d8b86e9c498bb6c9829765ae4ff2fb1864398af9dfa47c"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 # Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
 # valid while its sources hash to `sources_sha256`.
-ISSUE = {"k_forward": {"frac": 0.6992,
-                       "sources_sha256": "da385f1a0bb4c00d134bed0ec01d9f82f1b27040b7f7399facea07c2a1cbaa4f"}}
+ISSUE = {"k_forward": {"frac": 0.6977,
+                       "sources_sha256": "2b52663ae0d90390b0d8b86e9c498bb6c9829765ae4ff2fb1864398af9dfa47c"}}
 FP32_LANES_PER_SM = 128
 
 
