@@ -275,14 +275,20 @@ def test_shadow_edge_gradient_parity(name):
     _compare_grads(gg, go, ["coef", "rot", "trans", "focal"])
 
 
-@pytest.mark.parametrize("name,edge_spp", [("tube", 1), ("tube", 2), ("tiny", 1), ("c1", 2)])
-def test_specular_boundary_gradient_parity(name, edge_spp):
+@pytest.mark.parametrize("name,edge_spp,mode", [("tube", 1, ""), ("tube", 2, ""), ("tiny", 1, ""), ("c1", 2, ""),
+                                                ("tube", 1, "ggx"), ("tube", 1, "cutoff")])
+def test_specular_boundary_gradient_parity(name, edge_spp, mode):
     """The boundary term of the specular lobe's cutoff inside triangles (the
-    curve n_s . o = 0 met along scanlines) against the oracle's, per element."""
+    curve n_s . o = 0 met along scanlines) against the oracle's, per element;
+    also with the GGX lobe (its jump G1(o) / (n . o) -> 2 / alpha) and under
+    the reading that cuts every contribution there (the jump is the whole
+    radiance)."""
     from paper_2101_05356_gb300 import facert
     sc, pr = _scene(name)
+    extra, oflags = {"": (0, 0), "ggx": (facert.FLAG_GGX, oracle.GGX),
+                     "cutoff": (facert.FLAG_VIEW_CUTOFF, oracle.VIEW_CUTOFF)}[mode]
     r = _renderer(sc, edge_spp=edge_spp,
-                  flags=facert.FLAG_NO_INTERIOR | facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE)
+                  flags=facert.FLAG_NO_INTERIOR | facert.FLAG_NO_PRIMARY_EDGE | facert.FLAG_NO_SHADOW_EDGE | extra)
     dp = r.device_params(pr)
     adj = _masked_adjoint(sc, pr, r, dp)
     groups = ["coef", "rot", "trans", "focal"]
@@ -291,7 +297,7 @@ def test_specular_boundary_gradient_parity(name, edge_spp):
         gg = r.backward(dp, torch.as_tensor(a, dtype=torch.float32).cuda())
         assert r.status() == 0
         return gg, oracle.grad(sc, pr, a.astype(np.float32).astype(np.float64), terms=oracle.TERM_SPECULAR,
-                               edge_spp=edge_spp)
+                               edge_spp=edge_spp, flags=oflags)
 
     # every crossing: group norms
     gg, go = both(adj)
