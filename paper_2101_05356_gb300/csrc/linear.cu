@@ -311,11 +311,12 @@ void launch_linear_adjoint(const LinearAdjModel* models, int n_models, cudaStrea
     } else {
         for (int m = 0; m < L.n_models; ++m) L.start[m + 1] = L.start[m] + L.chunks[m];
         // split the columns over grid.z until about eight blocks per SM are in flight
-        // (measured on GB300, albedo batch 8: two columns per warp, five blocks per SM
-        // and the k-split 0.183 ms against 0.203 ms for four columns at three)
+        // (measured on GB300, albedo batch 8, both models: two columns per warp at six
+        // blocks per SM (40 registers) 0.163 ms; at five 0.183-0.189 ms, at seven or
+        // eight (spilling) 0.228 ms, four columns at four 0.185 ms)
         const int most = nb(nb(kmax, 2), LIN_THREADS / 32);
         const int z = std::max(1, std::min(most, nb(8L * sms, (long)L.start[L.n_models] * n_groups)));
-        k_linear_adj_part<LIN_GROUP, 2, 5><<<dim3(L.start[L.n_models], n_groups, z), LIN_THREADS, 0, st>>>(L);
+        k_linear_adj_part<LIN_GROUP, 2, 6><<<dim3(L.start[L.n_models], n_groups, z), LIN_THREADS, 0, st>>>(L);
     }
     k_linear_adj_finish<<<dim3(nb(kmax, FIN_K), n, L.n_models), FIN_THREADS, 0, st>>>(L);
     fr_count_launches(2);
