@@ -57,13 +57,13 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is recorded beside the kernel's profile summary.
-TRAFFIC = {"k_forward": {"bytes": 26589184 + 17825792,
-                         "sources_sha256": "2b52663ae0d90390b0d8b86e9c498bb6c9829765ae4ff2fb1864398af9dfa47c"}}
+TRAFFIC = {"k_forward": {"bytes": 26515200 + 12098304,
+                         "sources_sha256": "67f3e1905eaf1759a00047533859ef18bd9f394affc1734b3fdc091f1415d3b8"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 # Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
 # valid while its sources hash to `sources_sha256`.
-ISSUE = {"k_forward": {"frac": 0.6977,
-                       "sources_sha256": "2b52663ae0d90390b0d8b86e9c498bb6c9829765ae4ff2fb1864398af9dfa47c"}}
+ISSUE = {"k_forward": {"frac": 0.6962,
+                       "sources_sha256": "67f3e1905eaf1759a00047533859ef18bd9f394affc1734b3fdc091f1415d3b8"}}
 FP32_LANES_PER_SM = 128
 
 

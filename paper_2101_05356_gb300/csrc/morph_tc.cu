@@ -38,7 +38,10 @@ constexpr int TC_EPI_WARPS = 4;             // epilogue warps: TMEM lanes 32w..3
 constexpr int TC_PRODUCER = 4, TC_MMA = 5;   // warp indices of the copy and MMA roles
 constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 2);
 constexpr int TC_MAX_STAGES = 8;
-constexpr int TC_STAGE_BYTES = 64 * 1024;   // shared memory given to the ring of basis tiles
+constexpr int TC_STAGE_BYTES = 32 * 1024;   // shared memory given to the ring of basis tiles (at
+                                            // least two; measured on GB300, albedo K = 80: two 20 KB
+                                            // stages and four CTAs per SM 0.060 ms, three stages 0.062,
+                                            // four 0.066, six 0.089)
 constexpr unsigned SPIN_LIMIT = 1u << 22;
 
 FR_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
         flush_stats(S.counters + 3, rs);                // the adjoint's rays
         if (valid) {
             it.rec_tri[ql] = ss.tri;
-            reinterpret_cast<ulonglong2*>(it.rec_vis)[ql] = make_ulonglong2(vis[0], vis[1]);
+            if (ss.hit) reinterpret_cast<ulonglong2*>(it.rec_vis)[ql] = make_ulonglong2(vis[0], vis[1]);
         }
         return;
     }
@@ -434,9 +434,10 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
         mask_rec[2 * q] = vis[0];
         mask_rec[2 * q + 1] = vis[1];
     }
+    // (a sample that misses the face has no visibility to record: nothing reads it)
     if (valid && it.rec_from >= 0 && q >= it.rec_from) {
         it.rec_tri[q - it.rec_from] = ss.tri;
-        reinterpret_cast<ulonglong2*>(it.rec_vis)[q - it.rec_from] = make_ulonglong2(vis[0], vis[1]);
+        if (ss.hit) reinterpret_cast<ulonglong2*>(it.rec_vis)[q - it.rec_from] = make_ulonglong2(vis[0], vis[1]);
     }
     // per-pixel mean: lanes of one pixel summed in a fixed tree order; above
     // 32 spp the warps of one pixel (within this block) add their sums in warp
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
     if (!(S.flags & FR_FLAG_FLAT_D)) {
         for (int j0 = 0; j0 < S.NL; j0 += 64) {                // warp-uniform
             if (recorded)
-                vis_w[j0 >> 6] = valid ? it.rec_vis[2 * ql + (j0 >> 6)] : 0ull;
+                vis_w[j0 >> 6] = (valid && ss.hit) ? it.rec_vis[2 * ql + (j0 >> 6)] : 0ull;
             else
                 vis_w[j0 >> 6] = shadow_mask<ENV>(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j0);
         }
