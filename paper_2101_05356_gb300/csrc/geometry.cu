@@ -235,21 +235,30 @@ __global__ void __launch_bounds__(256) k_pose_adj(const DevItem* items, int N) {
 }
 
 // dE/dtheta_a = sum_rc M'[r][c] dR[c][r]/dtheta_a ; dE/dT = -R sum g; plus the
-// FP64 focal and light-intensity accumulators.  One block per item.
+// FP64 focal and light-intensity accumulators.  One block of 192 threads per item.
 __global__ void k_pose_finish(const DevItem* items, int NL, int n_blocks) {
     __shared__ double acc12[12];
     const DevItem& it = items[blockIdx.x];
     const int t = threadIdx.x;
-    if (t < 12) {
+    // the 12 sums over the blocks' partials: 16 lanes per value (a half warp),
+    // lane l summing blocks l, l + 16, ... in order, then a fixed butterfly
+    if (t < 12 * 16) {
+        const int k = t >> 4, l = t & 15;
         double s = 0.0;
-        for (int b = 0; b < n_blocks; ++b) s += it.pose_part[b * 12 + t];
-        acc12[t] = s;
+        for (int b = l; b < n_blocks; b += 16) s += it.pose_part[b * 12 + k];
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (l == 0) acc12[k] = s;
     }
     __syncthreads();
     const fix64* small = it.G.small;
     if (t == 0) {
-        const double a = it.P.rot[0], b = it.P.rot[1], c = it.P.rot[2];
-        const double sx = sin(a), cx = cos(a), sy = sin(b), cy = cos(b), sz = sin(c), cz = cos(c);
+        // the angles' sines and cosines in FP32 (~1e-7 relative; FP64 transcendentals
+        // run on the narrow FP64 pipe), the contractions in FP64
+        float fsx, fcx, fsy, fcy, fsz, fcz;
+        sincosf(it.P.rot[0], &fsx, &fcx);
+        sincosf(it.P.rot[1], &fsy, &fcy);
+        sincosf(it.P.rot[2], &fsz, &fcz);
+        const double sx = fsx, cx = fcx, sy = fsy, cy = fcy, sz = fsz, cz = fcz;
         double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx}, dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
         double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy}, dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
         double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1}, dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
@@ -393,7 +402,7 @@ void launch_pose_adjoint(const DevItem* items, int n, int N, cudaStream_t st) {
 }
 
 void launch_pose_finish(const DevItem* items, int n, int NL, int N, cudaStream_t st) {
-    k_pose_finish<<<n, 64, 0, st>>>(items, NL, nb(N, 256));
+    k_pose_finish<<<n, 12 * 16, 0, st>>>(items, NL, nb(N, 256));
     fr_count_launches(1);
 }
 

@@ -188,8 +188,19 @@ __global__ void k_bvh_init(const DevItem* items, int n) {
     if (i < n) B.parent_leaf[i] = -1;
 }
 
+// Arrival count at a node, with release (this thread's box writes happen
+// before it) and acquire (the sibling's box writes, released by its own
+// arrival, are visible after it) at GPU scope: one round trip per level
+// instead of an atomic between two full fences.
+__device__ __forceinline__ int arrive_acq_rel(int* flag) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(flag) : "memory");
+    return old;
+}
+
 // Leaf boxes + sorted triangle records, then climb: the second child to arrive
-// at a node merges both boxes and continues upward.
+// at a node merges its own box with the sibling's (read from memory) and
+// continues upward.
 __global__ void __launch_bounds__(256) k_boxes(const DevItem* items, const int4* __restrict__ faces, int n,
                                                int* status) {
     const DevItem& it = items[blockIdx.y];
@@ -219,24 +230,21 @@ __global__ void __launch_bounds__(256) k_boxes(const DevItem* items, const int4*
     box_leaf[2 * s] = make_float4(lo.x, lo.y, lo.z, 0.0f);
     box_leaf[2 * s + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     if (n == 1) return;
-    __threadfence();
+    int me = ~s;                                        // child code of the box in (lo, hi)
     int node = parent_leaf[s];
     for (int guard = 0; node >= 0; ++guard) {
         if (guard > 128 || node >= n - 1) { set_status(status, FR_STATUS_BAD_BVH); return; }
-        if (atomicAdd(&flag[node], 1) == 0) return;     // sibling not done yet
-        __threadfence();
-        float3 l2 = f3(INFINITY, INFINITY, INFINITY), h2 = f3(-INFINITY, -INFINITY, -INFINITY);
-        for (int q = 0; q < 2; ++q) {
-            const int ch = child[2 * node + q];
-            if (ch >= n - 1 || ~ch >= n) { set_status(status, FR_STATUS_BAD_BVH); return; }
-            const float4* bx = ch < 0 ? &box_leaf[2 * (~ch)] : &box_int[2 * ch];
-            const float4 cl = __ldcg(bx), chh = __ldcg(bx + 1);
-            l2 = f3(fminf(l2.x, cl.x), fminf(l2.y, cl.y), fminf(l2.z, cl.z));
-            h2 = f3(fmaxf(h2.x, chh.x), fmaxf(h2.y, chh.y), fmaxf(h2.z, chh.z));
-        }
-        __stcg(&box_int[2 * node], make_float4(l2.x, l2.y, l2.z, 0.0f));
-        __stcg(&box_int[2 * node + 1], make_float4(h2.x, h2.y, h2.z, 0.0f));
-        __threadfence();
+        if (arrive_acq_rel(&flag[node]) == 0) return;   // sibling not done yet
+        const int c0 = child[2 * node], c1 = child[2 * node + 1];
+        const int ch = c0 == me ? c1 : c0;
+        if ((c0 != me && c1 != me) || ch >= n - 1 || ~ch >= n) { set_status(status, FR_STATUS_BAD_BVH); return; }
+        const float4* bx = ch < 0 ? &box_leaf[2 * (~ch)] : &box_int[2 * ch];
+        const float4 cl = __ldcg(bx), chh = __ldcg(bx + 1);
+        lo = f3(fminf(lo.x, cl.x), fminf(lo.y, cl.y), fminf(lo.z, cl.z));
+        hi = f3(fmaxf(hi.x, chh.x), fmaxf(hi.y, chh.y), fmaxf(hi.z, chh.z));
+        __stcg(&box_int[2 * node], make_float4(lo.x, lo.y, lo.z, 0.0f));
+        __stcg(&box_int[2 * node + 1], make_float4(hi.x, hi.y, hi.z, 0.0f));
+        me = node;
         node = node == 0 ? -1 : parent_int[node];
     }
 }

@@ -44,15 +44,37 @@ __global__ void __launch_bounds__(LIN_THREADS) k_linear(const float* __restrict_
 #pragma unroll
     for (int b = 0; b < G; ++b) acc[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const float4* bp = reinterpret_cast<const float4*>(basis) + i;
-    // unrolled so that several basis rows are in flight per thread (the grid
-    // of one face is small: 3N / 4 threads)
+    // One face: U basis rows are loaded before any is summed, so that U loads
+    // are in flight per thread (its grid is small, 3N / 4 threads, a few warps
+    // per SM, and its time is the K / U dependent round trips to HBM).  A group
+    // keeps many warps per SM and unrolls by 8.  The sums run over k in order
+    // either way, so a face's result is the same in both.
+    if constexpr (G > 1) {
 #pragma unroll 8
-    for (int k = 0; k < K; ++k) {
-        const float4 bk = __ldg(bp + (size_t)k * ld4);
+        for (int k = 0; k < K; ++k) {
+            const float4 bk = __ldg(bp + (size_t)k * ld4);
 #pragma unroll
-        for (int b = 0; b < G; ++b) {
-            const float ck = c[b][k];
-            acc[b].x += ck * bk.x; acc[b].y += ck * bk.y; acc[b].z += ck * bk.z; acc[b].w += ck * bk.w;
+            for (int b = 0; b < G; ++b) {
+                const float ck = c[b][k];
+                acc[b].x += ck * bk.x; acc[b].y += ck * bk.y; acc[b].z += ck * bk.z; acc[b].w += ck * bk.w;
+            }
+        }
+    } else {
+        constexpr int U = 36;
+        for (int k0 = 0; k0 < K; k0 += U) {
+            float4 bk[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k0 + u < K) bk[u] = __ldg(bp + (size_t)(k0 + u) * ld4);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (k0 + u >= K) break;
+#pragma unroll
+                for (int b = 0; b < G; ++b) {
+                    const float ck = c[b][k0 + u];
+                    acc[b].x += ck * bk[u].x; acc[b].y += ck * bk[u].y; acc[b].z += ck * bk[u].z; acc[b].w += ck * bk[u].w;
+                }
+            }
         }
     }
 #pragma unroll
@@ -256,12 +278,12 @@ void launch_linear(const float* mean, const float* basis, int ld, int rows, int 
                    cudaStream_t st) {
     if (t.n <= 0 || rows <= 0) return;
     const dim3 grid(nb((rows + 3) / 4, LIN_THREADS), nb(t.n, LIN_GROUP));
-    // one face: smaller blocks spread its few rows over more SMs.  (Splitting
+    // one face: small blocks spread its few rows evenly over the SMs.  (Splitting
     // the columns over several threads per row would keep more loads in flight,
     // but its sums would differ from the batched kernel's in the last bits, and
     // a face must render bitwise the same alone and in a batch.)
     if (t.n == 1)
-        k_linear<1><<<nb((rows + 3) / 4, LIN_THREADS / 2), LIN_THREADS / 2, 0, st>>>(mean, basis, ld, rows, K, t);
+        k_linear<1><<<nb((rows + 3) / 4, LIN_THREADS / 4), LIN_THREADS / 4, 0, st>>>(mean, basis, ld, rows, K, t);
     else
         k_linear<LIN_GROUP><<<grid, LIN_THREADS, 0, st>>>(mean, basis, ld, rows, K, t);
     fr_count_launches(1);

@@ -928,8 +928,23 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
 constexpr int EDGE_CHUNK = 4096;                   // 12 bits of in-chunk index
 constexpr int EDGE_SORT_THREADS = 1024;
 
+// Bitonic compare-exchange seen from element i (partner i ^ j) of the
+// sequence stage (k, j): the lower index of an ascending pair keeps the
+// smaller key, as does the upper index of a descending pair.
+__device__ __forceinline__ uint32_t bitonic_pick(uint32_t mine, uint32_t other, int i, int j, int k) {
+    const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+    return keep_min ? min(mine, other) : max(mine, other);
+}
+
+// Thread t holds keys 4t .. 4t + 3 in registers: the stages with j <= 2 run
+// inside the thread, those with 4 <= j <= 64 between the lanes of a warp
+// (partner lane t ^ j / 4), and only those with j >= 128 go through shared
+// memory (15 of the 78 stages for 4096 keys).  The keys are distinct, so the
+// result is the one sorted order.
 __global__ void __launch_bounds__(EDGE_SORT_THREADS) k_edge_order(const DevItem* items) {
-    __shared__ uint32_t key[EDGE_CHUNK];
+    static_assert(EDGE_CHUNK == 4 * EDGE_SORT_THREADS, "four keys per thread");
+    __shared__ uint4 key4[EDGE_SORT_THREADS];
+    uint32_t* key = reinterpret_cast<uint32_t*>(key4);
     const DevItem& it = items[blockIdx.y];
     const DevScene& S = it.S;
     const long n_edge = (S.flags & FR_FLAG_NO_PRIMARY_EDGE_D) ? 0 : (long)S.W * S.H * S.edge_spp;
@@ -938,7 +953,11 @@ __global__ void __launch_bounds__(EDGE_SORT_THREADS) k_edge_order(const DevItem*
     const int Sn = *it.EL.prim_count;
     const float f = it.P.focal[0];
     const long npx = (long)S.W * S.H;
-    for (int q = threadIdx.x; q < EDGE_CHUNK; q += EDGE_SORT_THREADS) {
+    const int t = threadIdx.x;
+    uint32_t r[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int q = 4 * t + m;
         const long e = base + q;
         uint32_t k20 = 0xFFFFFu;                           // no contribution possible: last
         if (e < n_edge && Sn > 0) {
@@ -955,28 +974,53 @@ __global__ void __launch_bounds__(EDGE_SORT_THREADS) k_edge_order(const DevItem*
                 }
             }
         }
-        key[q] = (k20 << 12) | (uint32_t)q;                // the index makes keys distinct
+        r[m] = (k20 << 12) | (uint32_t)q;                  // the index makes keys distinct
     }
-    __syncthreads();
-    for (int k = 2; k <= EDGE_CHUNK; k <<= 1)              // bitonic sort, ascending
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < EDGE_CHUNK; i += EDGE_SORT_THREADS) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint32_t a = key[i], b = key[ixj];
-                    if ((a > b) == ((i & k) == 0)) {
-                        key[i] = b;
-                        key[ixj] = a;
+    for (int k = 2; k <= EDGE_CHUNK; k <<= 1) {            // bitonic sort, ascending
+        int j = k >> 1;
+        if (j >= 128) {                                    // across warps: shared memory
+            key4[t] = make_uint4(r[0], r[1], r[2], r[3]);
+            __syncthreads();
+            for (; j >= 128; j >>= 1) {
+                for (int i = t; i < EDGE_CHUNK; i += EDGE_SORT_THREADS) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint32_t a = key[i], b = key[ixj];
+                        if ((a > b) == ((i & k) == 0)) {
+                            key[i] = b;
+                            key[ixj] = a;
+                        }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
+            const uint4 v = key4[t];
+            r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+            __syncthreads();                               // before key4 is written again
         }
+        for (; j >= 4; j >>= 1) {                          // within the warp
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const uint32_t o = __shfl_xor_sync(FULL, r[m], j >> 2);
+                r[m] = bitonic_pick(r[m], o, 4 * t + m, j, k);
+            }
+        }
+        // within the thread: j = 2 (when k >= 4), then j = 1
+        if (k >= 4) {
+            const uint32_t n0 = bitonic_pick(r[0], r[2], 4 * t, 2, k), n1 = bitonic_pick(r[1], r[3], 4 * t + 1, 2, k);
+            const uint32_t n2 = bitonic_pick(r[2], r[0], 4 * t + 2, 2, k), n3 = bitonic_pick(r[3], r[1], 4 * t + 3, 2, k);
+            r[0] = n0; r[1] = n1; r[2] = n2; r[3] = n3;
+        }
+        const uint32_t n0 = bitonic_pick(r[0], r[1], 4 * t, 1, k), n1 = bitonic_pick(r[1], r[0], 4 * t + 1, 1, k);
+        const uint32_t n2 = bitonic_pick(r[2], r[3], 4 * t + 2, 1, k), n3 = bitonic_pick(r[3], r[2], 4 * t + 3, 1, k);
+        r[0] = n0; r[1] = n1; r[2] = n2; r[3] = n3;
+    }
     // samples past n_edge carry the largest keys, so positions [0, count) hold
     // exactly this chunk's samples
     const int count = (int)min((long)EDGE_CHUNK, n_edge - base);
-    for (int q = threadIdx.x; q < count; q += EDGE_SORT_THREADS)
-        it.edge_perm[base + q] = (int)(base + (key[q] & (EDGE_CHUNK - 1)));
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (4 * t + m < count) it.edge_perm[base + 4 * t + m] = (int)(base + (r[m] & (EDGE_CHUNK - 1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1586,22 +1630,33 @@ __device__ void env_range(const LightDev& L, Real nx, Real ny, Real nz, Real& lo
 // than a bound on its rounding error (64 u times the sum of the magnitudes
 // involved, u = 2^-24, a generous multiple of the few roundings per term), so
 // the FP64 work runs only for nearly grazing pairs and every class equals the
-// FP64 one.
+// FP64 one.  Thread (face f, group blockIdx.y of CLS_LIGHTS emitters).
+constexpr int CLS_LIGHTS = 8;
+
 __global__ void k_face_class(const DevItem* items) {
-    const DevItem& it = items[blockIdx.y];
+    const DevItem& it = items[blockIdx.z];
     const DevScene& S = it.S;
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= S.T) return;
+    const int j0 = blockIdx.y * CLS_LIGHTS, j1 = min(S.NL, j0 + CLS_LIGHTS);
+    if (f >= S.T || j0 >= j1) return;
     const int4 tv = S.faces[f];
     const float3 q0 = xyz(S.v[tv.x]), q1 = xyz(S.v[tv.y]), q2 = xyz(S.v[tv.z]);
     const float3 a = q1 - q0, b = q2 - q0;
     const float3 nf = cross(a, b);
     const float3 na = f3(fabsf(a.y * b.z) + fabsf(a.z * b.y), fabsf(a.z * b.x) + fabsf(a.x * b.z),
                          fabsf(a.x * b.y) + fabsf(a.y * b.x));    // bounds |n| and its rounding
-    const double3 n = face_normal_d(S, f);
-    const float4 p0 = S.v[tv.x];
-    const double d = n.x * p0.x + n.y * p0.y + n.z * p0.z;
-    for (int j = 0; j < S.NL; ++j) {
+    // the FP64 plane, computed on first need
+    bool have64 = false;
+    double3 n = make_double3(0.0, 0.0, 0.0);
+    double d = 0.0;
+    auto plane64 = [&]() {
+        if (have64) return;
+        n = face_normal_d(S, f);
+        const float4 p0 = S.v[tv.x];
+        d = n.x * p0.x + n.y * p0.y + n.z * p0.z;
+        have64 = true;
+    };
+    for (int j = j0; j < j1; ++j) {
         const LightDev& L = S.lights[j];
         if (L.type == FR_LIGHT_ENV_D) {        // a point at infinity along w is in front iff n . w > 0
             // FP32 first: it decides whenever it is farther from zero than a
@@ -1614,6 +1669,7 @@ __global__ void k_face_class(const DevItem* items) {
             else if (hi32 < -err) cls = 2;
             else if (lo32 < -err && hi32 > err) cls = 3;
             if (!cls) {
+                plane64();
                 double lo, hi;
                 env_range<double>(L, n.x, n.y, n.z, lo, hi);
                 cls = lo > 0.0 ? 1 : (hi < 0.0 ? 2 : 3);
@@ -1638,6 +1694,7 @@ __global__ void k_face_class(const DevItem* items) {
                 continue;
             }
         }
+        plane64();
         const double base = n.x * L.c.x + n.y * L.c.y + n.z * L.c.z - d;
         const double g1 = n.x * L.e1.x + n.y * L.e1.y + n.z * L.e1.z;
         const double g2 = n.x * L.e2.x + n.y * L.e2.y + n.z * L.e2.z;
@@ -1647,69 +1704,83 @@ __global__ void k_face_class(const DevItem* items) {
     }
 }
 
+// Ordered compaction of the flagged edge ids of every list, in three parallel
+// passes: flags and per-chunk counts, per-list exclusive scan of the counts,
+// scatter.
+constexpr int CMP_CHUNK = 1024;
+constexpr int CLS_LISTS = 8;
+
 // flags[list][E]: list 0 = primary silhouettes (w.r.t. the camera centre,
 // FP64 per edge), list 1 + j = conservative shadow candidates of light j
 // (edges whose two faces are not both entirely in front of or both entirely
-// behind emitter j).
-__global__ void k_classify(const DevItem* items) {
-    const DevItem& it = items[blockIdx.y];
-    const DevScene& S = it.S;
-    const int4* edges = it.EL.edges;
-    uint8_t* flags = it.sil_flags;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= S.E) return;
-    const int4 E = edges[e];
-    if (E.w < 0) {
-        for (int l = 0; l <= S.NL; ++l) flags[(size_t)l * S.E + e] = 1;
-        return;
-    }
-    const float4 pa = S.v[E.x];
-    const double ax = pa.x, ay = pa.y, az = pa.z;
-    const double3 n1 = face_normal_d(S, E.z), n2 = face_normal_d(S, E.w);
-    flags[e] = sgn_d(-(n1.x * ax + n1.y * ay + n1.z * az)) != sgn_d(-(n2.x * ax + n2.y * ay + n2.z * az));
-    const uint8_t* cls = flags + (size_t)(1 + FR_MAX_LIGHTS) * S.E;
-    for (int j = 0; j < S.NL; ++j) {
-        const uint8_t c1 = cls[(size_t)j * S.T + E.z], c2 = cls[(size_t)j * S.T + E.w];
-        flags[(size_t)(1 + j) * S.E + e] = !((c1 == 1 && c2 == 1) || (c1 == 2 && c2 == 2));
-    }
-}
-
-// Ordered compaction of the flagged edge ids of every list, in three parallel
-// passes: per-chunk counts, per-list exclusive scan of the counts, scatter.
-constexpr int CMP_CHUNK = 1024;
-
-__global__ void __launch_bounds__(CMP_CHUNK) k_compact_count(const DevItem* items, int E, int n_chunks) {
-    __shared__ int warp_tot[32];
+// behind emitter j).  Block (chunk of CMP_CHUNK edges, group blockIdx.y of
+// CLS_LISTS lists) also writes each list's count of flagged edges in the
+// chunk to hist[list][chunk] (the radix-sort histogram is free here).
+__global__ void __launch_bounds__(CMP_CHUNK) k_classify(const DevItem* items, int n_chunks) {
+    __shared__ int warp_cnt[CLS_LISTS][CMP_CHUNK / 32];
     const DevItem& it = items[blockIdx.z];
-    const int list = blockIdx.y, chunk = blockIdx.x;
-    const int i = chunk * CMP_CHUNK + threadIdx.x;
-    const bool on = i < E && it.sil_flags[(size_t)list * E + i];
-    const unsigned b = __ballot_sync(FULL, on);
-    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = __popc(b);
+    const DevScene& S = it.S;
+    const int l0 = blockIdx.y * CLS_LISTS, l1 = min(1 + S.NL, l0 + CLS_LISTS);
+    if (l0 >= l1) return;                                // the whole block
+    uint8_t* flags = it.sil_flags;
+    const uint8_t* cls = flags + (size_t)(1 + FR_MAX_LIGHTS) * S.E;
+    const int e = blockIdx.x * CMP_CHUNK + threadIdx.x;
+    const bool in = e < S.E;
+    const int4 E = in ? it.EL.edges[e] : make_int4(0, 0, 0, 0);
+    for (int l = l0; l < l1; ++l) {
+        bool on = false;
+        if (in) {
+            if (E.w < 0) {
+                on = true;                               // a boundary edge is in every list
+            } else if (l == 0) {
+                const float4 pa = S.v[E.x];
+                const double ax = pa.x, ay = pa.y, az = pa.z;
+                const double3 n1 = face_normal_d(S, E.z), n2 = face_normal_d(S, E.w);
+                on = sgn_d(-(n1.x * ax + n1.y * ay + n1.z * az)) != sgn_d(-(n2.x * ax + n2.y * ay + n2.z * az));
+            } else {
+                const size_t j = (size_t)(l - 1) * S.T;
+                const uint8_t c1 = cls[j + E.z], c2 = cls[j + E.w];
+                on = !((c1 == 1 && c2 == 1) || (c1 == 2 && c2 == 2));
+            }
+            flags[(size_t)l * S.E + e] = on;
+        }
+        const unsigned bal = __ballot_sync(FULL, on);
+        if ((threadIdx.x & 31) == 0) warp_cnt[l - l0][threadIdx.x >> 5] = __popc(bal);
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < CMP_CHUNK / 32; ++w) t += warp_tot[w];
-        it.B.hist[list * n_chunks + chunk] = t;      // the radix-sort histogram is free here
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < l1 - l0) {                                   // warp w: list l0 + w, its 32 warp counts
+        int v = warp_cnt[w][lane];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (lane == 0) it.B.hist[(l0 + w) * n_chunks + blockIdx.x] = v;
     }
 }
 
+// Exclusive scan of each list's chunk counts in place, one warp per list (32
+// chunks a round, carried), and the list's total.
 __global__ void k_compact_scan(const DevItem* items, int n_lists, int n_chunks) {
     const DevItem& it = items[blockIdx.x];
-    for (int list = threadIdx.x; list < n_lists; list += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int list = threadIdx.x >> 5; list < n_lists; list += blockDim.x >> 5) {
         int* h = it.B.hist + list * n_chunks;
-        int run = 0;
-        for (int c = 0; c < n_chunks; ++c) {
-            const int v = h[c];
-            h[c] = run;
-            run += v;
+        int carry = 0;
+        for (int c0 = 0; c0 < n_chunks; c0 += 32) {
+            const int c = c0 + lane;
+            const int v = c < n_chunks ? h[c] : 0;
+            int x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            if (c < n_chunks) h[c] = carry + x - v;
+            carry += __shfl_sync(FULL, x, 31);
         }
-        it.EL.prim_count[list] = run;
+        if (lane == 0) it.EL.prim_count[list] = carry;
     }
 }
 
 __global__ void __launch_bounds__(CMP_CHUNK) k_compact_scatter(const DevItem* items, int E, int n_chunks) {
-    __shared__ int warp_off[32];
+    __shared__ int warp_off[CMP_CHUNK / 32];
     const DevItem& it = items[blockIdx.z];
     const int list = blockIdx.y, chunk = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1718,13 +1789,14 @@ __global__ void __launch_bounds__(CMP_CHUNK) k_compact_scatter(const DevItem* it
     const unsigned b = __ballot_sync(FULL, on);
     if (lane == 0) warp_off[wid] = __popc(b);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = it.B.hist[list * n_chunks + chunk];
-        for (int w = 0; w < CMP_CHUNK / 32; ++w) {
-            const int v = warp_off[w];
-            warp_off[w] = run;
-            run += v;
+    if (wid == 0) {                                      // exclusive scan of the 32 warp counts
+        const int v = warp_off[lane];
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
         }
+        warp_off[lane] = it.B.hist[list * n_chunks + chunk] + x - v;
     }
     __syncthreads();
     if (on) it.EL.prim_list[(size_t)list * E + warp_off[wid] + __popc(b & ((1u << lane) - 1u))] = i;
@@ -1833,13 +1905,15 @@ void launch_edge_specular(const DevItem* items, int n, int T, const BlockMap& ma
 }
 
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st) {
-    k_face_class<<<dim3(blocks_for(T, 256), n), 256, 0, st>>>(items);
-    k_classify<<<dim3(blocks_for(E, 256), n), 256, 0, st>>>(items);
+    if (NL > 0) {
+        k_face_class<<<dim3(blocks_for(T, 256), blocks_for(NL, CLS_LIGHTS), n), 256, 0, st>>>(items);
+        fr_count_launches(1);
+    }
     const int n_chunks = blocks_for(E, CMP_CHUNK);
-    k_compact_count<<<dim3(n_chunks, 1 + NL, n), CMP_CHUNK, 0, st>>>(items, E, n_chunks);
-    k_compact_scan<<<n, 128, 0, st>>>(items, 1 + NL, n_chunks);
+    k_classify<<<dim3(n_chunks, blocks_for(1 + NL, CLS_LISTS), n), CMP_CHUNK, 0, st>>>(items, n_chunks);
+    k_compact_scan<<<n, 32 * std::min(32, 1 + NL), 0, st>>>(items, 1 + NL, n_chunks);
     k_compact_scatter<<<dim3(n_chunks, 1 + NL, n), CMP_CHUNK, 0, st>>>(items, E, n_chunks);
-    fr_count_launches(5);
+    fr_count_launches(3);
 }
 
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri, float* t,

@@ -437,6 +437,24 @@ def fr_kernel_launches():
 
 # ---- convenience: one context bound to a synthetic scene ------------------
 
+class Grads(dict):
+    """Gradient tensors by parameter name, views of one flat FP32 device buffer
+    (`flat`) so that one fill clears them all.  An entry rebound to a tensor of
+    other storage is cleared on its own."""
+
+    def __init__(self, flat, views):
+        super().__init__(views)
+        self.flat = flat
+
+    def zero_(self):
+        self.flat.zero_()
+        base = self.flat.untyped_storage().data_ptr()
+        for v in self.values():
+            if v.untyped_storage().data_ptr() != base:
+                v.zero_()
+        return self
+
+
 class Renderer:
     """A library context for one scene (mesh, light stage, image config),
     with torch device buffers for parameters, images and gradients."""
@@ -476,7 +494,17 @@ class Renderer:
                 for n in ALL_PARAM_NAMES if getattr(params, n, None) is not None}
 
     def zero_grads(self, dparams):
-        return {n: self.torch.zeros_like(v) for n, v in dparams.items()}
+        """Zeroed gradient buffers shaped like `dparams`, as views of one
+        device buffer (each view 256-byte aligned): `.zero_()` clears them all
+        with one fill."""
+        t = self.torch
+        sizes = {n: v.numel() for n, v in dparams.items()}
+        offs, total = {}, 0
+        for n, k in sizes.items():
+            offs[n] = total
+            total += (k + 63) // 64 * 64
+        flat = t.zeros(max(total, 1), dtype=t.float32, device="cuda")
+        return Grads(flat, {n: flat[offs[n]:offs[n] + sizes[n]].view(v.shape) for n, v in dparams.items()})
 
     def image_buffer(self):
         s = self.scene

@@ -133,8 +133,7 @@ class FaceState:
         if self.stage == 2 and self.ref_diffuse is None:
             self.ref_diffuse = self.p["diffuse"].clone()
             self.ref_specular = self.p["specular"].clone()
-        for t in self.g.values():
-            t.zero_()
+        self.g.zero_()                  # the gradient views share one buffer: one fill
         for a in self.ab.values():
             a["g"].zero_()
 
