@@ -70,7 +70,8 @@ typedef int32_t fr_status;
                                          Context-wide, read from the context's flags */
 
 /* Per-slot budget for hit records (bytes): the hit triangle and two 64-bit
- * light-visibility words per camera sample (20 bytes).  When the context's
+ * light-visibility words per camera sample (20 bytes; with at most 64 lights
+ * only the first word is written and read).  When the context's
  * width * height * spp records fit, a fused step's forward writes them and its
  * adjoint reads them instead of re-tracing.  Larger images are split into equal
  * tiles that fit (whole pixels, whole 128-sample blocks): the forward keeps the

@@ -221,7 +221,8 @@ struct DevItem {
     int32_t* tri_rec;
     uint64_t* mask_rec;
     int32_t* rec_tri;       // hit records [rec_cap] (null: the adjoint re-traces every sample)
-    uint64_t* rec_vis;      // [rec_cap][2] visibility words, lights 0..63 and 64..127 (samples that hit)
+    uint64_t* rec_vis;      // [rec_cap][1 or 2] visibility words, lights 0..63 (and 64..127 when there
+                            // are more than 64), written for samples that hit
     long rec_cap;           // camera samples the record buffer holds (a tile of the image)
     int rec_full;           // this call's forward writes the records of the whole image (it fits)
     long rec_from;          // the forward writes the records of samples >= rec_from (0 with rec_full,

@@ -387,6 +387,14 @@ FR_D float group_sum(float v, int width) {
     return v;
 }
 
+// Visibility words a hit record holds: one for up to 64 lights, else two.
+FR_D int vis_words(const DevScene& S) { return S.NL > 64 ? 2 : 1; }
+
+FR_D void store_vis(const DevScene& S, uint64_t* rec_vis, long i, const uint64_t* vis) {
+    if (S.NL > 64) reinterpret_cast<ulonglong2*>(rec_vis)[i] = make_ulonglong2(vis[0], vis[1]);
+    else rec_vis[i] = vis[0];
+}
+
 // Camera samples [q0, q0 + the block map's count) of each item.  records_only
 // (a tile of the adjoint's recomputed records): trace the camera ray and the
 // shadow rays, write the hit records of the tile at q - q0, and shade
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
         flush_stats(S.counters + 3, rs);                // the adjoint's rays
         if (valid) {
             it.rec_tri[ql] = ss.tri;
-            if (ss.hit) reinterpret_cast<ulonglong2*>(it.rec_vis)[ql] = make_ulonglong2(vis[0], vis[1]);
+            if (ss.hit) store_vis(S, it.rec_vis, ql, vis);
         }
         return;
     }
@@ -437,7 +445,7 @@ __global__ void __launch_bounds__(RT_THREADS, FR_FWD_MIN_BLOCKS) k_forward(const
     // (a sample that misses the face has no visibility to record: nothing reads it)
     if (valid && it.rec_from >= 0 && q >= it.rec_from) {
         it.rec_tri[q - it.rec_from] = ss.tri;
-        if (ss.hit) reinterpret_cast<ulonglong2*>(it.rec_vis)[q - it.rec_from] = make_ulonglong2(vis[0], vis[1]);
+        if (ss.hit) store_vis(S, it.rec_vis, q - it.rec_from, vis);
     }
     // per-pixel mean: lanes of one pixel summed in a fixed tree order; above
     // 32 spp the warps of one pixel (within this block) add their sums in warp
@@ -744,7 +752,7 @@ __global__ void __launch_bounds__(RT_THREADS, RECORDED ? FR_ADJ_REC_MIN_BLOCKS :
     if (!(S.flags & FR_FLAG_FLAT_D)) {
         for (int j0 = 0; j0 < S.NL; j0 += 64) {                // warp-uniform
             if (recorded)
-                vis_w[j0 >> 6] = (valid && ss.hit) ? it.rec_vis[2 * ql + (j0 >> 6)] : 0ull;
+                vis_w[j0 >> 6] = (valid && ss.hit) ? it.rec_vis[vis_words(S) * ql + (j0 >> 6)] : 0ull;
             else
                 vis_w[j0 >> 6] = shadow_mask<ENV>(S, ss, smp, 2, sh.wq[threadIdx.x >> 5], my_stack(sh), rs, j0);
         }
