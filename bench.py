@@ -57,13 +57,13 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is recorded beside the kernel's profile summary.
-TRAFFIC = {"k_forward": {"bytes": 26125056 + 15553792,
-                         "sources_sha256": "358b2d0aea34a0e04e8d8c78430524a0eea05f1de31c9fef1c05f3973d44e132"}}
+TRAFFIC = {"k_forward": {"bytes": 25985024 + 13262080,
+                         "sources_sha256": "ed3cfba5e55ad18feb5d1bf171fd55089f3fa139a7dc5aa435d701e1805f2804"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 # Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
 # valid while its sources hash to `sources_sha256`.
-ISSUE = {"k_forward": {"frac": 0.6893,
-                       "sources_sha256": "358b2d0aea34a0e04e8d8c78430524a0eea05f1de31c9fef1c05f3973d44e132"}}
+ISSUE = {"k_forward": {"frac": 0.6890,
+                       "sources_sha256": "ed3cfba5e55ad18feb5d1bf171fd55089f3fa139a7dc5aa435d701e1805f2804"}}
 FP32_LANES_PER_SM = 128
 
 
