@@ -169,18 +169,53 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(TcLaunch L, int n_tiles
                      ::"r"(smem_u32(&tmem_base)), "r"(2 * TC_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    __syncthreads();                                    // the barriers are initialised
+    // the ring's first copies wait on nothing: issue them before the coefficient
+    // gather below, so that their latency overlaps the gather's
+    const int pre = my_n < stages ? my_n : stages;
+    if (warp == TC_PRODUCER && lane == 0) {
+        for (int k = 0; k < pre; ++k) {
+            int mdl;
+            const int lt = tile_of(k, mdl);
+            const int a_bytes = TC_M * L.Kp[mdl] * 2;
+            bulk_load(sA0 + (size_t)k * stage_bytes,
+                      reinterpret_cast<const unsigned char*>(L.basis[mdl]) + (size_t)lt * a_bytes, a_bytes, &full[k]);
+        }
+    }
     // the B operands: face b is row b of an N x Kp K-major matrix in core-matrix
     // layout (8 rows x 8 BF16 per 128 B), coefficients rounded to nearest even;
-    // the writes are made visible to the tensor cores' (async proxy) reads
-    for (int mdl = 0; mdl < L.n; ++mdl) {
-        uint16_t* sB16 = reinterpret_cast<uint16_t*>(sB[mdl]);
-        const int Kp = L.Kp[mdl], K = L.K[mdl];
-        const LinearTable& t = L.t[mdl];
-        for (int idx = tid; idx < TC_N * Kp; idx += TC_THREADS) {
-            const int b = idx / Kp, k = idx % Kp;
-            const float v = (b < t.n && k < K) ? __ldg(&t.coef[b][k]) : 0.0f;
-            const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
-            sB16[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v);
+    // the loads of both models are issued before any store (one round trip for
+    // batches of up to 4 * TC_THREADS / Kp faces); the writes are made visible
+    // to the tensor cores' (async proxy) reads
+    constexpr int GU = 4;
+    const int g_total = TC_N * (L.Kp[0] > L.Kp[1] || L.n < 2 ? L.Kp[0] : L.Kp[1]);
+    for (int base = 0; base < g_total; base += GU * TC_THREADS) {
+        float v[2][GU];
+#pragma unroll
+        for (int mdl = 0; mdl < 2; ++mdl) {
+            const int Kp = mdl < L.n ? L.Kp[mdl] : 16, K = L.K[mdl];     // (no second model: no loads)
+            const LinearTable& t = L.t[mdl];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int idx = base + u * TC_THREADS + tid;
+                const int b = idx / Kp, k = idx - b * Kp;
+                v[mdl][u] = (mdl < L.n && idx < TC_N * Kp && b < t.n && k < K) ? __ldg(&t.coef[b][k]) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int mdl = 0; mdl < 2; ++mdl) {
+            if (mdl >= L.n) break;
+            uint16_t* sB16 = reinterpret_cast<uint16_t*>(sB[mdl]);
+            const int Kp = L.Kp[mdl];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int idx = base + u * TC_THREADS + tid;
+                if (idx < TC_N * Kp) {
+                    const int b = idx / Kp, k = idx - b * Kp;
+                    const int g = b >> 3, r = b & 7, c = k >> 3, kk = k & 7;
+                    sB16[((g * (Kp / 8) + c) * 128 + r * 16 + kk * 2) / 2] = bf16_rne(v[mdl][u]);
+                }
+            }
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -191,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_morph_tc(TcLaunch L, int n_tiles
 
     if (warp == TC_PRODUCER) {
         if (lane == 0) {
-            int k = 0;
+            int k = pre;
             for (; k < my_n && !*abort_v; ++k) {
                 const int q = k % stages;
                 // the buffer's previous tile (k - stages) must have been consumed

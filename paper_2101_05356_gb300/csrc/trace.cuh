@@ -61,6 +61,32 @@ FR_D bool hit_triangle(const RayPre& r, float3 v0, float3 v1, float3 v2, float t
     return true;
 }
 
+// The same watertight test for an any-hit query: true when the ray hits the
+// triangle at some t in the open interval (tmin, tmax).  T and det share their
+// sign at a hit, so the bounds are checked on T against tmin * det and
+// tmax * det, without the division (the decision can differ from comparing
+// T / det only within rounding of an end of the interval).
+FR_D bool hit_triangle_any(const RayPre& r, float3 v0, float3 v1, float3 v2, float tmin, float tmax) {
+    const float3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
+    const float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    const float Ax = comp(A, r.kx) - r.Sx * Akz, Ay = comp(A, r.ky) - r.Sy * Akz;
+    const float Bx = comp(B, r.kx) - r.Sx * Bkz, By = comp(B, r.ky) - r.Sy * Bkz;
+    const float Cx = comp(C, r.kx) - r.Sx * Ckz, Cy = comp(C, r.ky) - r.Sy * Ckz;
+    float U = Cx * By - Cy * Bx;
+    float V = Ax * Cy - Ay * Cx;
+    float W = Bx * Ay - By * Ax;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    const float det = U + V + W;
+    if (det == 0.0f) return false;
+    const float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    return det > 0.0f ? (T > tmin * det && T < tmax * det) : (T < tmin * det && T > tmax * det);
+}
+
 FR_D bool box_hit(const RayPre& r, float3 lo, float3 hi, float tmin, float tmax, float& tnear) {
     const float tx0 = fmaf(lo.x, r.inv.x, r.ood.x), tx1 = fmaf(hi.x, r.inv.x, r.ood.x);
     const float ty0 = fmaf(lo.y, r.inv.y, r.ood.y), ty1 = fmaf(hi.y, r.inv.y, r.ood.y);
@@ -213,9 +239,8 @@ FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, 
             if (slot != skip_slot) {
                 const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]),
                              c = __ldg(&s.tris[3 * slot + 2]);
-                float t, b1, b2;
                 rs.tris++;
-                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
+                if (hit_triangle_any(r, xyz(a), xyz(b), xyz(c), tmin, tmax)) return true;
             }
             h0 = false;
         }
@@ -224,9 +249,8 @@ FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, 
             if (slot != skip_slot) {
                 const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]),
                              c = __ldg(&s.tris[3 * slot + 2]);
-                float t, b1, b2;
                 rs.tris++;
-                if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, tmax, t, b1, b2) && t < tmax) return true;
+                if (hit_triangle_any(r, xyz(a), xyz(b), xyz(c), tmin, tmax)) return true;
             }
             h1 = false;
         }
