@@ -29,6 +29,9 @@ CASES = {
     "box": lambda: shadow_box()[0],
     "many": lambda: synth.make_scene("tiny", n_lights=80),
     "spp64": lambda: synth.make_scene("tiny", width=20, height=12, spp=64),
+    # a record holds one visibility word up to 64 lights, two from 65
+    "l64": lambda: synth.make_scene("tiny", n_lights=64),
+    "l65": lambda: synth.make_scene("tiny", n_lights=65),
 }
 
 
@@ -59,7 +62,7 @@ def test_recorded_adjoint_equals_retraced(name):
     assert ca["forward"] == cb["forward"]
 
 
-@pytest.mark.parametrize("name", ["c1", "box", "many", "spp64"])
+@pytest.mark.parametrize("name", ["c1", "box", "many", "spp64", "l64", "l65"])
 def test_tiled_recomputed_records_equal_retraced(name):
     """Records recomputed in about four tiles per image (the last one partial)
     against the re-tracing adjoint:
