@@ -58,12 +58,12 @@ OPS_PER_TRI = 30
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is recorded beside the kernel's profile summary.
 TRAFFIC = {"k_forward": {"bytes": 24865536 + 9646592,
-                         "sources_sha256": "407d56c3bce16cda9675cff6b71e262f2f3f9c1de031ade95dbe2247880798ec"}}
+                         "sources_sha256": "86b1f665e93b378527bdbf5d8c8501aef0660952a6f91d9a1ce0088a7d5b27d1"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 # Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
 # valid while its sources hash to `sources_sha256`.
 ISSUE = {"k_forward": {"frac": 0.7000,
-                       "sources_sha256": "407d56c3bce16cda9675cff6b71e262f2f3f9c1de031ade95dbe2247880798ec"}}
+                       "sources_sha256": "86b1f665e93b378527bdbf5d8c8501aef0660952a6f91d9a1ce0088a7d5b27d1"}}
 FP32_LANES_PER_SM = 128
 
 

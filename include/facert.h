@@ -277,7 +277,11 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
  * those of the image's last tile and recomputes the others tile by tile; with
  * FR_FLAG_RECOMPUTE it re-traces every sample inside the adjoint kernel
  * instead.  The gradient is the same either
- * way. */
+ * way.  With g, the part of the adjoint that needs only the posed geometry
+ * runs on a stream of the context, forked from `stream` after the geometry
+ * is built and joined back into it before the adjoint (event waits only: the
+ * call still returns without synchronising, and a stream capture of it records
+ * the fork and join). */
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);

@@ -101,6 +101,10 @@ struct fr_ctx {
     unsigned long long* counters = nullptr;   // [kernel][rays, nodes, triangle tests]
     bool timing = false;
     cudaEvent_t ev[9] = {};
+    // a fused step runs the geometry-only part of its reverse pass on `side`,
+    // forked from and joined back into the caller's stream, beside the forward
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<void*> owned;
 };
 
@@ -145,6 +149,14 @@ void free_all(fr_ctx* c) {
 }
 
 cudaStream_t S_(void* s) { return static_cast<cudaStream_t>(s); }
+
+void destroy_side(fr_ctx* c) {
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side) cudaStreamDestroy(c->side);
+    c->fork_ev = c->join_ev = nullptr;
+    c->side = nullptr;
+}
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
@@ -424,15 +436,26 @@ fr_status forward_pass(fr_ctx* c, int n, cudaStream_t st) {
     return FR_OK;
 }
 
-// reverse pass for items [0, n) whose geometry is built
-void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
+// The part of the reverse pass for items [0, n) that needs only their built
+// geometry (not the forward's image or records): the accumulators zeroed, the
+// silhouette classification, the order of the primary-edge samples and the
+// specular-boundary candidates.
+void adjoint_prep(fr_ctx* c, int n, cudaStream_t st) {
     launch_zero_accumulators(c->d_items, n, c->N, c->cfg.tex_size, st);
     bool need_edges = false;
+    long max_edge = 0;
     for (int k = 0; k < n; ++k) {
-        const uint32_t f = c->h_items[k].S.flags;
-        need_edges |= !(f & FR_FLAG_NO_PRIMARY_EDGE) || !(f & FR_FLAG_NO_SHADOW_EDGE);
+        const DevScene& s = c->h_items[k].S;
+        need_edges |= !(s.flags & FR_FLAG_NO_PRIMARY_EDGE) || !(s.flags & FR_FLAG_NO_SHADOW_EDGE);
+        if (!(s.flags & FR_FLAG_NO_PRIMARY_EDGE)) max_edge = std::max(max_edge, (long)s.W * s.H * s.edge_spp);
     }
     if (need_edges) launch_classify(c->d_items, n, c->E, c->NL, c->T, st);
+    launch_edge_order(c->d_items, n, max_edge, st);
+    launch_spec_candidates(c->d_items, n, c->T, spec_map(c, n), st);
+}
+
+// The rest of the reverse pass, after adjoint_prep and the loss.
+void adjoint_main(fr_ctx* c, int n, cudaStream_t st) {
     mark(c, 4, st);
     bool all_full = true, any_retrace = false, any_stage = false;
     long cap = 0, n_tiles = 1;
@@ -468,14 +491,8 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
         }
     }
     mark(c, 5, st);
-    long max_edge = 0;
-    for (int k = 0; k < n; ++k) {
-        const DevScene& s = c->h_items[k].S;
-        if (!(s.flags & FR_FLAG_NO_PRIMARY_EDGE)) max_edge = std::max(max_edge, (long)s.W * s.H * s.edge_spp);
-    }
-    launch_edge_order(c->d_items, n, max_edge, st);
     launch_edge_primary(c->d_items, map_of(c, n, true), c->env_size > 0, st);
-    launch_edge_specular(c->d_items, n, c->T, spec_map(c, n), c->env_size > 0, st);
+    launch_edge_specular(c->d_items, spec_map(c, n), c->env_size > 0, st);
     mark(c, 6, st);
     launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
@@ -483,6 +500,30 @@ void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     launch_pose_finish(c->d_items, n, c->NL, c->N, st);
     morph_adjoint(c, n, st);
     mark(c, 7, st);
+}
+
+// reverse pass for items [0, n) whose geometry is built, all on `st`
+void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
+    adjoint_prep(c, n, st);
+    adjoint_main(c, n, st);
+}
+
+// Fork adjoint_prep onto the context's side stream after the work already on
+// `st` (the built geometry); join_prep makes `st` wait for it.  Between the two
+// the caller's stream runs the forward and the loss, which share no buffer
+// with adjoint_prep.  Under stream capture the fork and join are part of the
+// captured graph.
+fr_status fork_prep(fr_ctx* c, int n, cudaStream_t st) {
+    CK(c, cudaEventRecord(c->fork_ev, st));
+    CK(c, cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    adjoint_prep(c, n, c->side);
+    CK(c, cudaEventRecord(c->join_ev, c->side));
+    return FR_OK;
+}
+
+fr_status join_prep(fr_ctx* c, cudaStream_t st) {
+    CK(c, cudaStreamWaitEvent(st, c->join_ev, 0));
+    return FR_OK;
 }
 
 LossTable loss_table(fr_ctx* c, int n, const float* const* targets, double* const* losses, bool adjoint) {
@@ -634,6 +675,15 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
         free_all(c);
         delete c;
         return FR_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        const fr_status st = fail(nullptr, FR_ECUDA, "side stream or events could not be created");
+        destroy_side(c);
+        free_all(c);
+        delete c;
+        return st;
     }
     *out = c;
     return FR_OK;
@@ -944,13 +994,17 @@ fr_status fr_render(fr_ctx* c, const fr_params* p, const float* target, float* i
     TRY(upload(c, 1, st));
     build_geometry(c, 1, st);
     mark(c, 1, st);
+    if (g) TRY(fork_prep(c, 1, st));
     TRY(forward_pass(c, 1, st));
     mark(c, 2, st);
     const float* tg[1] = {target};
     double* ls[1] = {loss};
     launch_loss(loss_table(c, 1, tg, ls, g != nullptr), st);
     mark(c, 3, st);
-    if (g) adjoint_pass(c, 1, st);
+    if (g) {
+        TRY(join_prep(c, st));
+        adjoint_main(c, 1, st);
+    }
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -982,6 +1036,7 @@ fr_status fr_render_batch(fr_ctx* c, const fr_item* items, int32_t n, void* stre
     TRY(upload(c, n, st));
     build_geometry(c, n, st);
     mark(c, 1, st);
+    if (any_grad) TRY(fork_prep(c, n, st));
     TRY(forward_pass(c, n, st));
     mark(c, 2, st);
     launch_loss(loss_table(c, n, tg, ls, any_grad), st);
@@ -993,7 +1048,8 @@ fr_status fr_render_batch(fr_ctx* c, const fr_item* items, int32_t n, void* stre
             if (!items[k].grads)
                 CK(c, cudaMemsetAsync(c->slots[k].adj_image, 0,
                                       sizeof(float) * 3 * (size_t)items[k].width * items[k].height, st));
-        adjoint_pass(c, n, st);
+        TRY(join_prep(c, st));
+        adjoint_main(c, n, st);
     }
     CK(c, cudaGetLastError());
     return FR_OK;
@@ -1047,6 +1103,7 @@ void fr_destroy(fr_ctx* c) {
     cudaDeviceSynchronize();
     for (cudaEvent_t& e : c->ev)
         if (e) cudaEventDestroy(e);
+    destroy_side(c);
     free_all(c);
     delete c;
 }

@@ -114,7 +114,8 @@ void launch_adjoint(const DevItem* items, const BlockMap& map, int NL, bool all_
 void launch_edge_order(const DevItem* items, int n, long max_edge, cudaStream_t st);
 void launch_edge_primary(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st);
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st);
-void launch_edge_specular(const DevItem* items, int n, int T, const BlockMap& map, bool env, cudaStream_t st);
+void launch_spec_candidates(const DevItem* items, int n, int T, const BlockMap& map, cudaStream_t st);
+void launch_edge_specular(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st);
 void launch_trace_rays(const DevItem* items, const float* org, const float* dir, int n, int32_t* tri,
                        float* t, cudaStream_t st);
 

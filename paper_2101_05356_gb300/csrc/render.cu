@@ -1903,19 +1903,26 @@ void launch_edge_primary(const DevItem* items, const BlockMap& map, bool env, cu
     fr_count_launches(1);
 }
 
-// Candidates of the specular-boundary term (ordered list per item), then one
-// block per scanline of each item (`map`).
-void launch_edge_specular(const DevItem* items, int n, int T, const BlockMap& map, bool env, cudaStream_t st) {
+// Candidates of the specular-boundary term (ordered list per item); they need
+// only the posed geometry and the camera.  `map` is the boundary kernel's.
+void launch_spec_candidates(const DevItem* items, int n, int T, const BlockMap& map, cudaStream_t st) {
     if (n <= 0 || map_blocks(map) == 0) return;
     const int n_chunks = blocks_for(T, SPEC_CHUNK);
     k_spec_count<<<dim3(n_chunks, n), SPEC_CHUNK, 0, st>>>(items);
     k_spec_scan<<<n, 32, 0, st>>>(items);
     k_spec_scatter<<<dim3(n_chunks, n), SPEC_CHUNK, 0, st>>>(items);
+    fr_count_launches(3);
+}
+
+// The specular-boundary term over the candidates: one block per scanline of
+// each item (`map`).
+void launch_edge_specular(const DevItem* items, const BlockMap& map, bool env, cudaStream_t st) {
+    if (map_blocks(map) == 0) return;
     if (env)
         k_edge_specular<true><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
     else
         k_edge_specular<false><<<map_blocks(map), RT_THREADS, sizeof(float) * RT_WARPS, st>>>(items, map);
-    fr_count_launches(4);
+    fr_count_launches(1);
 }
 
 void launch_classify(const DevItem* items, int n, int E, int NL, int T, cudaStream_t st) {
