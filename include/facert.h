@@ -258,7 +258,9 @@ fr_status fr_forward(fr_ctx* ctx, const fr_params* p, float* image, uint32_t ite
  * curve n_s . o = 0 of App. A, Eq. brdf_spec, met along one row line per
  * pixel row and one column line per pixel column, edge_spp of each, rows
  * first; (W + H) * max(edge_spp, 1) <= 65535) unless disabled by flags.
- * adj_image [H][W][3] (device). */
+ * adj_image [H][W][3] (device).  The boundary terms of the primary edges and
+ * of the specular cutoff run on a stream of the context, forked from `stream`
+ * and joined back into it with events. */
 fr_status fr_backward(fr_ctx* ctx, const fr_params* p, const float* adj_image, fr_grads* g,
                       uint32_t iteration, uint32_t face_id, void* stream);
 
@@ -278,10 +280,11 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
  * FR_FLAG_RECOMPUTE it re-traces every sample inside the adjoint kernel
  * instead.  The gradient is the same either
  * way.  With g, the part of the adjoint that needs only the posed geometry
- * runs on a stream of the context, forked from `stream` after the geometry
- * is built and joined back into it before the adjoint (event waits only: the
- * call still returns without synchronising, and a stream capture of it records
- * the fork and join). */
+ * runs on a stream of the context beside the forward, and the boundary terms
+ * of the primary edges and of the specular lobe's cutoff run there beside the
+ * interior term; each is forked from `stream` and joined back into it with
+ * events (the call still returns without synchronising, and a stream capture
+ * of it records the forks and joins). */
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);

@@ -454,9 +454,19 @@ void adjoint_prep(fr_ctx* c, int n, cudaStream_t st) {
     launch_spec_candidates(c->d_items, n, c->T, spec_map(c, n), st);
 }
 
-// The rest of the reverse pass, after adjoint_prep and the loss.
-void adjoint_main(fr_ctx* c, int n, cudaStream_t st) {
+// The rest of the reverse pass, after adjoint_prep and the loss.  The boundary
+// terms (primary edges, the specular lobe's cutoff) and the interior term
+// (with the shadow-boundary term) only add into the fixed-point accumulators
+// with integer atomics, whose sums do not depend on their order, and read
+// nothing the others write: the boundary terms run on the side stream while
+// the interior term runs on `st`, and `st` waits for them before the chain.
+fr_status adjoint_main(fr_ctx* c, int n, cudaStream_t st) {
     mark(c, 4, st);
+    CK(c, cudaEventRecord(c->fork_ev, st));
+    CK(c, cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    launch_edge_primary(c->d_items, map_of(c, n, true), c->env_size > 0, c->side);
+    launch_edge_specular(c->d_items, spec_map(c, n), c->env_size > 0, c->side);
+    CK(c, cudaEventRecord(c->join_ev, c->side));
     bool all_full = true, any_retrace = false, any_stage = false;
     long cap = 0, n_tiles = 1;
     for (int k = 0; k < n; ++k) {
@@ -491,8 +501,7 @@ void adjoint_main(fr_ctx* c, int n, cudaStream_t st) {
         }
     }
     mark(c, 5, st);
-    launch_edge_primary(c->d_items, map_of(c, n, true), c->env_size > 0, st);
-    launch_edge_specular(c->d_items, spec_map(c, n), c->env_size > 0, st);
+    CK(c, cudaStreamWaitEvent(st, c->join_ev, 0));
     mark(c, 6, st);
     launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
@@ -500,12 +509,13 @@ void adjoint_main(fr_ctx* c, int n, cudaStream_t st) {
     launch_pose_finish(c->d_items, n, c->NL, c->N, st);
     morph_adjoint(c, n, st);
     mark(c, 7, st);
+    return FR_OK;
 }
 
-// reverse pass for items [0, n) whose geometry is built, all on `st`
-void adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
+// reverse pass for items [0, n) whose geometry is built (adjoint_prep on `st`)
+fr_status adjoint_pass(fr_ctx* c, int n, cudaStream_t st) {
     adjoint_prep(c, n, st);
-    adjoint_main(c, n, st);
+    return adjoint_main(c, n, st);
 }
 
 // Fork adjoint_prep onto the context's side stream after the work already on
@@ -967,7 +977,7 @@ fr_status fr_backward(fr_ctx* c, const fr_params* p, const float* adj_image, fr_
     c->h_items[0] = make_item(c, 0, single(c, p, g, nullptr, adj_image, iteration, face_id));
     TRY(upload(c, 1, st));
     build_geometry(c, 1, st);
-    adjoint_pass(c, 1, st);
+    TRY(adjoint_pass(c, 1, st));
     CK(c, cudaGetLastError());
     return FR_OK;
 }
@@ -1003,7 +1013,7 @@ fr_status fr_render(fr_ctx* c, const fr_params* p, const float* target, float* i
     mark(c, 3, st);
     if (g) {
         TRY(join_prep(c, st));
-        adjoint_main(c, 1, st);
+        TRY(adjoint_main(c, 1, st));
     }
     CK(c, cudaGetLastError());
     return FR_OK;
@@ -1049,7 +1059,7 @@ fr_status fr_render_batch(fr_ctx* c, const fr_item* items, int32_t n, void* stre
                 CK(c, cudaMemsetAsync(c->slots[k].adj_image, 0,
                                       sizeof(float) * 3 * (size_t)items[k].width * items[k].height, st));
         TRY(join_prep(c, st));
-        adjoint_main(c, n, st);
+        TRY(adjoint_main(c, n, st));
     }
     CK(c, cudaGetLastError());
     return FR_OK;
