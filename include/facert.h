@@ -403,7 +403,10 @@ fr_status fr_set_timing(fr_ctx* ctx, int32_t on);
 /* Milliseconds of the stages of the last timed fr_render (synchronises):
  * out[8] = {geometry+LBVH, forward, loss, classify, adjoint, screen-space
  * boundary terms (primary edges and the specular lobe's boundary), chain to
- * parameters, total}. */
+ * parameters, total}.  The marks are events on the caller's stream: work on
+ * the context's side stream counts in the stage it overlaps (the
+ * classification in the forward's, the boundary terms in the adjoint's), and
+ * its own stage holds only what is left of it after that stage ends. */
 fr_status fr_get_timing(fr_ctx* ctx, float* out);
 
 /* Number of kernels this library has launched in this process. */
