@@ -154,30 +154,30 @@ FR_D Hit trace_closest(const DevScene& s, const RayPre& r, float tmin, float tma
         float tn0, tn1;
         bool h0 = box_hit(r, lo0, hi0, tmin, h.t, tn0);
         bool h1 = box_hit(r, lo1, hi1, tmin, h.t, tn1);
-        // leaves are single triangles: test them right away
+        // leaves are single triangles: test the ones this ray enters right away,
+        // in child order, by one loop (lanes entering different leaves test
+        // them together)
+        int leaf = -1, leaf2 = -1;
         if (h0 && c0 < 0) {
-            const int slot = ~c0;
-            const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
-            float t, b1, b2;
-            const int id = __float_as_int(a.w);
-            rs.tris++;
-            if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
-                (t < h.t || id < h.tri || h.tri < 0)) {
-                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id; h.slot = slot;
-            }
+            leaf = ~c0;
             h0 = false;
         }
         if (h1 && c1 < 0) {
-            const int slot = ~c1;
-            const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]), c = __ldg(&s.tris[3 * slot + 2]);
+            if (leaf < 0) leaf = ~c1;
+            else leaf2 = ~c1;
+            h1 = false;
+        }
+        while (leaf >= 0) {
+            const float4 a = __ldg(&s.tris[3 * leaf]), b = __ldg(&s.tris[3 * leaf + 1]), c = __ldg(&s.tris[3 * leaf + 2]);
             float t, b1, b2;
             const int id = __float_as_int(a.w);
             rs.tris++;
             if (hit_triangle(r, xyz(a), xyz(b), xyz(c), tmin, h.t, t, b1, b2) &&
                 (t < h.t || id < h.tri || h.tri < 0)) {
-                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id; h.slot = slot;
+                h.t = t; h.b1 = b1; h.b2 = b2; h.tri = id; h.slot = leaf;
             }
-            h1 = false;
+            leaf = leaf2;
+            leaf2 = -1;
         }
         if (h0 && tn0 > h.t) h0 = false;
         if (h1 && tn1 > h.t) h1 = false;
@@ -234,25 +234,27 @@ FR_D bool trace_any(const DevScene& s, const RayPre& r, float tmin, float tmax, 
         float tn0, tn1;
         bool h0 = box_hit(r, lo0, hi0, tmin, tmax, tn0);
         bool h1 = box_hit(r, lo1, hi1, tmin, tmax, tn1);
+        // the leaf children this ray enters, tested in child order by one loop,
+        // so that lanes entering different leaves test them together
+        int leaf = -1, leaf2 = -1;
         if (h0 && c0 < 0) {
-            const int slot = ~c0;
-            if (slot != skip_slot) {
-                const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]),
-                             c = __ldg(&s.tris[3 * slot + 2]);
-                rs.tris++;
-                if (hit_triangle_any(r, xyz(a), xyz(b), xyz(c), tmin, tmax)) return true;
-            }
+            leaf = ~c0;
             h0 = false;
         }
         if (h1 && c1 < 0) {
-            const int slot = ~c1;
-            if (slot != skip_slot) {
-                const float4 a = __ldg(&s.tris[3 * slot]), b = __ldg(&s.tris[3 * slot + 1]),
-                             c = __ldg(&s.tris[3 * slot + 2]);
+            if (leaf < 0) leaf = ~c1;
+            else leaf2 = ~c1;
+            h1 = false;
+        }
+        while (leaf >= 0) {
+            if (leaf != skip_slot) {
+                const float4 a = __ldg(&s.tris[3 * leaf]), b = __ldg(&s.tris[3 * leaf + 1]),
+                             c = __ldg(&s.tris[3 * leaf + 2]);
                 rs.tris++;
                 if (hit_triangle_any(r, xyz(a), xyz(b), xyz(c), tmin, tmax)) return true;
             }
-            h1 = false;
+            leaf = leaf2;
+            leaf2 = -1;
         }
         if (h0 && h1) {
             if (ts.full()) { set_status(s.status, FR_STATUS_STACK_OVERFLOW); return false; }
