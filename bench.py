@@ -57,13 +57,13 @@ OPS_PER_TRI = 30
 # kernel from one ncu capture of this benchmark's workload, valid while the
 # sources that make up the kernel hash to `sources_sha256` (else reported as
 # null); the capture command is recorded beside the kernel's profile summary.
-TRAFFIC = {"k_forward": {"bytes": 24865536 + 9646592,
-                         "sources_sha256": "86b1f665e93b378527bdbf5d8c8501aef0660952a6f91d9a1ce0088a7d5b27d1"}}
+TRAFFIC = {"k_forward": {"bytes": 23236864 + 9601280,
+                         "sources_sha256": "292936dfbfa4dd07bcb5f6f205eda95c504a32d0849ea664c071a481b62b02fe"}}
 KERNEL_SOURCES = {"k_forward": ("render.cu", "trace.cuh", "shade.cuh", "common.cuh")}
 # Issue-slot use (smsp__issue_active) of a kernel from its ncu --set full capture,
 # valid while its sources hash to `sources_sha256`.
-ISSUE = {"k_forward": {"frac": 0.7000,
-                       "sources_sha256": "86b1f665e93b378527bdbf5d8c8501aef0660952a6f91d9a1ce0088a7d5b27d1"}}
+ISSUE = {"k_forward": {"frac": 0.7020,
+                       "sources_sha256": "292936dfbfa4dd07bcb5f6f205eda95c504a32d0849ea664c071a481b62b02fe"}}
 FP32_LANES_PER_SM = 128
 
 
