@@ -104,7 +104,7 @@ struct fr_ctx {
     // a fused step runs the geometry-only part of its reverse pass on `side`,
     // forked from and joined back into the caller's stream, beside the forward
     cudaStream_t side = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, tail_ev = nullptr;
     std::vector<void*> owned;
 };
 
@@ -153,8 +153,9 @@ cudaStream_t S_(void* s) { return static_cast<cudaStream_t>(s); }
 void destroy_side(fr_ctx* c) {
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->tail_ev) cudaEventDestroy(c->tail_ev);
     if (c->side) cudaStreamDestroy(c->side);
-    c->fork_ev = c->join_ev = nullptr;
+    c->fork_ev = c->join_ev = c->tail_ev = nullptr;
     c->side = nullptr;
 }
 
@@ -501,13 +502,20 @@ fr_status adjoint_main(fr_ctx* c, int n, cudaStream_t st) {
         }
     }
     mark(c, 5, st);
+    // the texture gradients are complete once the interior term is (the
+    // boundary terms add none): they are flushed on the side stream, after the
+    // boundary terms there, while `st` runs the vertex chain
+    CK(c, cudaEventRecord(c->fork_ev, st));
+    CK(c, cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    launch_tex_flush(c->d_items, n, c->cfg.tex_size, c->side);
+    CK(c, cudaEventRecord(c->tail_ev, c->side));
     CK(c, cudaStreamWaitEvent(st, c->join_ev, 0));
     mark(c, 6, st);
-    launch_tex_flush(c->d_items, n, c->cfg.tex_size, st);
     launch_normals_adjoint(c->d_items, n, c->faces, c->vf_off, c->vf_idx, c->N, st);
     launch_pose_adjoint(c->d_items, n, c->N, st);
     launch_pose_finish(c->d_items, n, c->NL, c->N, st);
     morph_adjoint(c, n, st);
+    CK(c, cudaStreamWaitEvent(st, c->tail_ev, 0));
     mark(c, 7, st);
     return FR_OK;
 }
@@ -688,7 +696,8 @@ fr_status fr_create(fr_ctx** out, const fr_config* cfg) {
     }
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->tail_ev, cudaEventDisableTiming) != cudaSuccess) {
         const fr_status st = fail(nullptr, FR_ECUDA, "side stream or events could not be created");
         destroy_side(c);
         free_all(c);
