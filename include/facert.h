@@ -259,8 +259,8 @@ fr_status fr_forward(fr_ctx* ctx, const fr_params* p, float* image, uint32_t ite
  * pixel row and one column line per pixel column, edge_spp of each, rows
  * first; (W + H) * max(edge_spp, 1) <= 65535) unless disabled by flags.
  * adj_image [H][W][3] (device).  The boundary terms of the primary edges and
- * of the specular cutoff run on a stream of the context, forked from `stream`
- * and joined back into it with events. */
+ * of the specular cutoff, and the texture-gradient flush, run on a stream of
+ * the context, forked from `stream` and joined back into it with events. */
 fr_status fr_backward(fr_ctx* ctx, const fr_params* p, const float* adj_image, fr_grads* g,
                       uint32_t iteration, uint32_t face_id, void* stream);
 
@@ -280,11 +280,13 @@ fr_status fr_loss(fr_ctx* ctx, const float* image, const float* target, double* 
  * FR_FLAG_RECOMPUTE it re-traces every sample inside the adjoint kernel
  * instead.  The gradient is the same either
  * way.  With g, the part of the adjoint that needs only the posed geometry
- * runs on a stream of the context beside the forward, and the boundary terms
- * of the primary edges and of the specular lobe's cutoff run there beside the
- * interior term; each is forked from `stream` and joined back into it with
- * events (the call still returns without synchronising, and a stream capture
- * of it records the forks and joins). */
+ * runs on a stream of the context beside the forward, the boundary terms of
+ * the primary edges and of the specular lobe's cutoff run there beside the
+ * interior term, and the texture gradients are flushed there beside the chain
+ * to the vertex parameters; each piece is forked from `stream` and joined back
+ * into it with events before the call's last work on `stream` (the call still
+ * returns without synchronising, and a stream capture of it records the forks
+ * and joins). */
 fr_status fr_render(fr_ctx* ctx, const fr_params* p, const float* target, float* image,
                     double* loss, fr_grads* g, uint32_t iteration, uint32_t face_id,
                     void* stream);
