@@ -17,7 +17,10 @@
  *    Argument checks happen synchronously before anything is enqueued.
  *    fr_last_error() describes the last failure of a context.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *    Compute calls only enqueue work on it and return; they never allocate.
+ *    Compute calls only enqueue work and return; they never allocate.  The
+ *    reverse pass also uses a stream the context owns (created at fr_create),
+ *    forked from `stream` and joined back into it with events inside the call,
+ *    so all of a call's work is ordered before later work on `stream`.
  *  - Device-side problems (traversal stack overflow, bounded waits that ran
  *    out) set a status word that fr_sync_status() reads; no kernel traps.
  *  - Ownership: the caller owns every buffer it passes (parameters, targets,
@@ -311,7 +314,8 @@ typedef struct fr_item {
  * (morph, pose and normals, LBVH build, forward, loss, adjoint, edge terms,
  * chain to parameters) is one launch over all items, so faces of different
  * sizes and sample counts share the GPU inside one launch.  Results equal n
- * separate fr_render calls with the same arguments. */
+ * separate fr_render calls with the same arguments; the reverse pass uses the
+ * context's second stream as fr_render does. */
 fr_status fr_render_batch(fr_ctx* ctx, const fr_item* items, int32_t n, void* stream);
 
 /* Replace the FR_FLAG_* set of ctx for the following calls (e.g. drop the edge
